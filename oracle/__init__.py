@@ -1,0 +1,381 @@
+"""Plain FP64 CPU oracle for the immersed-boundary projection method of
+Ong & Miura (arXiv 1807.10504).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library and never imports it.  The arithmetic lives in
+``ib_oracle.c`` (built with ``-O2 -ffp-contract=off``); this module is argument
+marshalling plus the composition of one time step (Section 2.1 fractional
+step with the force in the projection, Section 3.2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ib_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+IB_OK, IB_EINVAL, IB_ENOMEM, IB_ENOTCONV, IB_ENAN, IB_EMARKER = 0, 1, 2, 3, 4, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, no contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ib_oracle.h"))
+    ):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i, _d = C.c_int, C.c_double
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        sig = {
+            "or_phi": (_d, [_i, _d]),
+            "or_heaviside_profile": (_d, [_d]),
+            "or_coeffs": (None, [_i, _i, _d, _d, _d, _d, _D, _D, _D, _D, _D]),
+            "or_apply_A": (None, [_i, _i, _d, _D, _D, _D, _D]),
+            "or_residual": (None, [_i, _i, _d, _D, _D, _D, _D, _D]),
+            "or_rbgs": (None, [_i, _i, _d, _D, _D, _D, _D, _i]),
+            "or_restrict": (None, [_i, _i, _D, _D]),
+            "or_coarsen_beta": (None, [_i, _i, _D, _D, _D, _D]),
+            "or_prolong_add": (None, [_i, _i, _D, _D]),
+            "or_mg_levels": (_i, [_i, _i, _I32, _I32, _i]),
+            "or_dense_solve": (_i, [_i, _i, _d, _D, _D, _D, _D]),
+            "or_mg_solve": (_i, [_i, _i, _d, _D, _D, _D, _D, _i, _d, _i, _i, _i,
+                                 C.POINTER(_i), C.POINTER(_d), _D]),
+            "or_rhs": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D]),
+            "or_correct": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+            "or_divergence": (None, [_i, _i, _d, _D, _D, _D]),
+            "or_predictor": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _i, _d, _d,
+                                    _D, _D, _D, _D]),
+            "or_cell_keys": (None, [_i, _D, _D, _d, _d, _d, _i, _i, _U32]),
+            "or_marker_sort": (None, [_i, _U32, _U32]),
+            "or_interp": (None, [_i, _i, _i, _d, _d, _d, _D, _D, _i, _D, _D, _D, _D]),
+            "or_spread_conv": (None, [_i, _i, _i, _d, _d, _d, _i, _D, _D, _D, _D, _D, _D,
+                                      _D, _D]),
+            "or_curvature": (None, [_i, _D, _D, _i, _I32, _D, _D, _D, _D]),
+            "or_inside": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D]),
+            "or_heaviside": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D]),
+            "or_heaviside_cell": (_d, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _d]),
+            "or_spread_irrot": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D, _D,
+                                       _D, _D]),
+            "or_bspline_relocate": (_i, [_i, _D, _D, _i, _I32, _d, _D, _D]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ds(drop_start):
+    return np.ascontiguousarray(drop_start, dtype=np.int32)
+
+
+# --------------------------------------------------------------------------
+# Kernels and profiles (Section 2.2 Eq. (cherby), Section 3.2 Eq. (new_hea))
+def phi(r, kernel: int = 0):
+    return np.vectorize(lambda x: lib().or_phi(kernel, float(x)))(np.asarray(r, float))
+
+
+def heaviside_profile(r):
+    return np.vectorize(lambda x: lib().or_heaviside_profile(float(x)))(np.asarray(r, float))
+
+
+# --------------------------------------------------------------------------
+# Grid operators (Section 2.1)
+def coeffs(H, rho_g, rho_l, mu_g, mu_l):
+    ny, nx = H.shape
+    rho, mu = np.empty((ny, nx)), np.empty((ny, nx))
+    bx, by = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_coeffs(nx, ny, rho_g, rho_l, mu_g, mu_l, _f64(H), rho, mu, bx, by)
+    return rho, mu, bx, by
+
+
+def apply_A(bx, by, p, h):
+    ny, nx = p.shape
+    out = np.empty((ny, nx))
+    lib().or_apply_A(nx, ny, h, _f64(bx), _f64(by), _f64(p), out)
+    return out
+
+
+def residual(bx, by, b, p, h):
+    ny, nx = p.shape
+    r = np.empty((ny, nx))
+    lib().or_residual(nx, ny, h, _f64(bx), _f64(by), _f64(b), _f64(p), r)
+    return r
+
+
+def rbgs(bx, by, b, p, h, nsweeps=1):
+    p = _f64(p).copy()
+    ny, nx = p.shape
+    lib().or_rbgs(nx, ny, h, _f64(bx), _f64(by), _f64(b), p, nsweeps)
+    return p
+
+
+def restrict(r):
+    ny, nx = r.shape
+    rc = np.empty((ny // 2, nx // 2))
+    lib().or_restrict(nx, ny, _f64(r), rc)
+    return rc
+
+
+def coarsen_beta(bx, by):
+    ny, nx1 = bx.shape
+    nx = nx1 - 1
+    bxc, byc = np.empty((ny // 2, nx // 2 + 1)), np.empty((ny // 2 + 1, nx // 2))
+    lib().or_coarsen_beta(nx, ny, _f64(bx), _f64(by), bxc, byc)
+    return bxc, byc
+
+
+def prolong_add(ec, ef):
+    ef = _f64(ef).copy()
+    nyc, nxc = ec.shape
+    lib().or_prolong_add(nxc, nyc, _f64(ec), ef)
+    return ef
+
+
+def mg_levels(nx, ny):
+    a, b = np.zeros(32, np.int32), np.zeros(32, np.int32)
+    L = lib().or_mg_levels(nx, ny, a, b, 32)
+    return [(int(a[k]), int(b[k])) for k in range(L)]
+
+
+def dense_solve(bx, by, b, h):
+    ny, nx = b.shape
+    p = np.empty((ny, nx))
+    st = lib().or_dense_solve(nx, ny, h, _f64(bx), _f64(by), _f64(b), p)
+    if st != 0:
+        raise RuntimeError("singular dense system")
+    return p
+
+
+@dataclass
+class MGResult:
+    p: np.ndarray
+    status: int
+    cycles: int
+    relres: float
+    hist: np.ndarray
+
+
+def mg_solve(bx, by, b, h, p0=None, precision=0, tol=1e-10, max_cycles=100,
+             nu1=2, nu2=2) -> MGResult:
+    ny, nx = b.shape
+    p = np.zeros((ny, nx)) if p0 is None else _f64(p0).copy()
+    cyc, rel = _i(0), _d(0.0)
+    hist = np.zeros(max_cycles + 1)
+    st = lib().or_mg_solve(nx, ny, h, _f64(bx), _f64(by), _f64(b), p, precision, tol,
+                           max_cycles, nu1, nu2, C.byref(cyc), C.byref(rel), hist)
+    return MGResult(p, st, cyc.value, rel.value, hist[: cyc.value + 1])
+
+
+def rhs(us, vs, Fx, Fy, bx, by, h, dt):
+    ny, nx = us.shape[0], vs.shape[1]
+    b = np.empty((ny, nx))
+    lib().or_rhs(nx, ny, h, dt, _f64(us), _f64(vs), _f64(Fx), _f64(Fy), _f64(bx),
+                 _f64(by), b)
+    return b
+
+
+def correct(us, vs, p, Fx, Fy, bx, by, h, dt):
+    ny, nx = p.shape
+    u, v = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_correct(nx, ny, h, dt, _f64(us), _f64(vs), _f64(p), _f64(Fx), _f64(Fy),
+                     _f64(bx), _f64(by), u, v)
+    return u, v
+
+
+def divergence(u, v, h):
+    ny, nx = u.shape[0], v.shape[1]
+    d = np.empty((ny, nx))
+    lib().or_divergence(nx, ny, h, _f64(u), _f64(v), d)
+    return d
+
+
+def predictor(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0)):
+    ny, nx = rho.shape
+    have = au_prev is not None
+    aup = _f64(au_prev) if have else np.zeros((ny, nx + 1))
+    avp = _f64(av_prev) if have else np.zeros((ny + 1, nx))
+    us, vs = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    au, av = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_predictor(nx, ny, h, dt, _f64(rho), _f64(mu), _f64(u), _f64(v), aup, avp,
+                       int(have), float(g[0]), float(g[1]), us, vs, au, av)
+    return us, vs, au, av
+
+
+# --------------------------------------------------------------------------
+# Markers (Sections 2.2, 3, 4)
+def cell_keys(X, Y, x0, y0, h, nx, ny):
+    key = np.empty(len(X), np.uint32)
+    lib().or_cell_keys(len(X), _f64(X), _f64(Y), x0, y0, h, nx, ny, key)
+    return key
+
+
+def marker_sort(key):
+    order = np.empty(len(key), np.uint32)
+    lib().or_marker_sort(len(key), np.ascontiguousarray(key, np.uint32), order)
+    return order
+
+
+def interp(u, v, X, Y, h, x0=0.0, y0=0.0, kernel=0):
+    ny, nx = u.shape[0], v.shape[1]
+    U, V = np.empty(len(X)), np.empty(len(X))
+    lib().or_interp(kernel, nx, ny, h, x0, y0, _f64(u), _f64(v), len(X), _f64(X), _f64(Y),
+                    U, V)
+    return U, V
+
+
+def curvature(X, Y, drop_start):
+    M = len(X)
+    k, nxm, nym, ds = (np.empty(M) for _ in range(4))
+    lib().or_curvature(M, _f64(X), _f64(Y), len(drop_start) - 1, _ds(drop_start), k, nxm,
+                       nym, ds)
+    return k, nxm, nym, ds
+
+
+def spread_conv(X, Y, fmag, nxm, nym, ds, nx, ny, h, x0=0.0, y0=0.0, kernel=0):
+    Fx, Fy = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_spread_conv(kernel, nx, ny, h, x0, y0, len(X), _f64(X), _f64(Y), _f64(fmag),
+                         _f64(nxm), _f64(nym), _f64(ds), Fx, Fy)
+    return Fx, Fy
+
+
+def inside(X, Y, drop_start, nx, ny, h, x0=0.0, y0=0.0):
+    chi = np.empty((ny, nx))
+    lib().or_inside(nx, ny, h, x0, y0, len(X), _f64(X), _f64(Y), len(drop_start) - 1,
+                    _ds(drop_start), chi)
+    return chi
+
+
+def heaviside(X, Y, drop_start, nx, ny, h, x0=0.0, y0=0.0):
+    H = np.empty((ny, nx))
+    lib().or_heaviside(nx, ny, h, x0, y0, len(X), _f64(X), _f64(Y), len(drop_start) - 1,
+                       _ds(drop_start), H)
+    return H
+
+
+def heaviside_cell(i, j, X, Y, drop_start, h, chi, x0=0.0, y0=0.0):
+    return lib().or_heaviside_cell(int(i), int(j), h, x0, y0, len(X), _f64(X), _f64(Y),
+                                   len(drop_start) - 1, _ds(drop_start), float(chi))
+
+
+def spread_irrot(X, Y, drop_start, fmag, H, h, x0=0.0, y0=0.0):
+    ny, nx = H.shape
+    Fx, Fy = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_spread_irrot(nx, ny, h, x0, y0, len(X), _f64(X), _f64(Y), len(drop_start) - 1,
+                          _ds(drop_start), _f64(fmag), _f64(H), Fx, Fy)
+    return Fx, Fy
+
+
+def bspline_relocate(X, Y, drop_start, h):
+    Xo, Yo = np.empty(len(X)), np.empty(len(X))
+    st = lib().or_bspline_relocate(len(X), _f64(X), _f64(Y), len(drop_start) - 1,
+                                   _ds(drop_start), h, Xo, Yo)
+    if st != 0:
+        raise RuntimeError("B-spline least-squares system not positive definite")
+    return Xo, Yo
+
+
+# --------------------------------------------------------------------------
+# One time step (Section 2.1 fractional step, force in the projection as in
+# Section 3.2 Eq. (ns2_new)); the order of the stages is that of the method:
+# relocate markers (every `relocate_every` steps), curvature, Heaviside and
+# properties at the current marker positions, predictor, spreading,
+# pressure solve, correction, marker advection by interpolated velocity.
+@dataclass
+class Config:
+    nx: int
+    ny: int
+    h: float
+    x0: float = 0.0
+    y0: float = 0.0
+    rho_g: float = 1e-3
+    rho_l: float = 1.0
+    mu_g: float = 1e-4
+    mu_l: float = 1e-2
+    sigma: float = 1.0
+    gx: float = 0.0
+    gy: float = 0.0
+    kernel: int = 0          # 0 cosine (Eq. cherby), 1 Peskin 4-point
+    spread: int = 1          # 0 conventional (Eq. delta_vec), 1 irrotational
+    precision: int = 0       # 0 FP64 multigrid, 1 FP32 cycles in FP64 refinement
+    tol: float = 1e-10
+    max_cycles: int = 100
+    nu1: int = 2
+    nu2: int = 2
+    relocate_every: int = 10  # 0 = never
+
+
+@dataclass
+class State:
+    u: np.ndarray
+    v: np.ndarray
+    p: np.ndarray
+    X: np.ndarray
+    Y: np.ndarray
+    drop_start: np.ndarray
+    au: np.ndarray | None = None
+    av: np.ndarray | None = None
+    step: int = 0
+    last: dict = field(default_factory=dict)
+
+
+def init_state(cfg: Config, X, Y, drop_start) -> State:
+    return State(u=np.zeros((cfg.ny, cfg.nx + 1)), v=np.zeros((cfg.ny + 1, cfg.nx)),
+                 p=np.zeros((cfg.ny, cfg.nx)), X=_f64(X).copy(), Y=_f64(Y).copy(),
+                 drop_start=_ds(drop_start).copy())
+
+
+def ns_step(cfg: Config, st: State, dt: float) -> State:
+    h = cfg.h
+    if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
+        st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
+    kap, nxm, nym, ds = curvature(st.X, st.Y, st.drop_start)
+    fmag = cfg.sigma * kap
+    H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, cfg.x0, cfg.y0)
+    rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
+    us, vs, au, av = predictor(rho, mu, st.u, st.v, h, dt, st.au, st.av, (cfg.gx, cfg.gy))
+    if cfg.spread == 0:
+        Fx, Fy = spread_conv(st.X, st.Y, fmag, nxm, nym, ds, cfg.nx, cfg.ny, h, cfg.x0,
+                             cfg.y0, cfg.kernel)
+    else:
+        Fx, Fy = spread_irrot(st.X, st.Y, st.drop_start, fmag, H, h, cfg.x0, cfg.y0)
+    b = rhs(us, vs, Fx, Fy, bx, by, h, dt)
+    res = mg_solve(bx, by, b, h, st.p, cfg.precision, cfg.tol, cfg.max_cycles, cfg.nu1,
+                   cfg.nu2)
+    u, v = correct(us, vs, res.p, Fx, Fy, bx, by, h, dt)
+    U, V = interp(u, v, st.X, st.Y, h, cfg.x0, cfg.y0, cfg.kernel)
+    st.u, st.v, st.p, st.au, st.av = u, v, res.p, au, av
+    st.X = st.X + dt * U
+    st.Y = st.Y + dt * V
+    st.step += 1
+    st.last = dict(H=H, rho=rho, bx=bx, by=by, Fx=Fx, Fy=Fy, b=b, cycles=res.cycles,
+                   relres=res.relres, status=res.status, kappa=kap)
+    return st
