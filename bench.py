@@ -1,0 +1,311 @@
+"""Benchmark: time steps/s of the immersed-boundary projection step on one
+GB300, plus pressure-solve ms (FP64 multigrid vs FP32-inner defect
+correction at equal 1e-10 residual) and the fine-level sweep's roofline.
+
+Workload (default): 1024 x 1024 unit box, 64 seeded non-overlapping drops,
+radii U[0.01, 0.03], 256 markers each (16384), density ratio 1000, viscosity
+ratio 100, sigma = 1, irrotational spreading, B-spline relocation every 10
+steps, pressure solved to ||r||/||b|| <= 1e-10 from the previous pressure.
+A step = one ns_step (all stages of the time step).  L2 is flushed (256 MiB
+write) before every timed step, outside the step's events.
+
+--impl reference times the plain FP64 CPU oracle on the host cores on the
+same workload (each step one oracle time step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = ("pressure-solve ms & steps/s, FP64 MG vs mixed/NN-start at equal residual; %HBM")
+WORKLOADS = {
+    "multidrop1024": dict(n=1024, kind="multi"),
+    "multidrop2048": dict(n=2048, kind="multi"),
+    "oscillating256": dict(n=256, kind="osc"),
+    "static64": dict(n=64, kind="static"),
+}
+
+
+def make_markers(name, seed_offset=0):
+    wl = WORKLOADS[name]
+    if wl["kind"] == "multi":
+        return W.multidrop(wl["n"], seed=1811 + seed_offset)
+    if wl["kind"] == "osc":
+        return W.oscillating_drop(seed=1808 + seed_offset)
+    return W.static_drop(wl["n"], 0.25, 128)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(name, steps=1):
+    import oracle as O
+    O.build()
+    mk = make_markers(name)
+    n = WORKLOADS[name]["n"]
+    cfg = O.Config(nx=n, ny=n, h=1.0 / n, precision=1, spread=1, relocate_every=10)
+    st = O.init_state(cfg, mk.X, mk.Y, mk.drop_start)
+    dt = W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.ns_step(cfg, st, dt)
+    t = time.perf_counter() - t0
+    return steps / t, t
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    name = args.workload
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; each step below is a full oracle step
+    value, t = cpu_baseline(name, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": name, "solver": "FP32 V(2,2) in FP64 defect correction",
+                   "tol": 1e-10},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle time steps of {name}"},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1807_10504_gb300 as ib
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ib.lib()
+    name = args.workload
+    n = WORKLOADS[name]["n"]
+    h = 1.0 / n
+    mk = make_markers(name, seed_offset=rank)  # independent problem per rank
+    cfg = ib.Config(nx=n, ny=n, h=h, precision=args.precision, spread=1, relocate_every=10,
+                    tol=1e-10, max_cycles=200)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    dt = W.capillary_dt(h, cfg.rho_l, cfg.rho_g, cfg.sigma, cfg.mu_l, cfg.mu_g)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.ns_step(dt, 1, 1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sweep_kind = ib.PROF_SWEEP32 if args.precision == 1 else ib.PROF_SWEEP64
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cycles = []
+    barrier()
+    clk = Clocks(local)
+    l0 = ib.launch_count()
+    ib.profile_begin(sweep_kind)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        c, _ = ctx.ns_step(dt, 1, 1)
+        ev[k][1].record(stream)
+        cycles.append(c)
+    barrier()
+    launches = ib.launch_count() - l0
+    sweep_ms, sweep_n = ib.profile_end()
+    clocks = clk.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ws * args.steps / (t_ms / 1e3)
+
+    # pressure solve alone, cold start, on this state's system: FP64 vs mixed
+    b = ctx.get("b")
+    solve = {}
+    pk, pk_kind = peaks()
+    roof64 = None
+    for prec, label in ((0, "fp64"), (1, "mixed")):
+        times, cyc = [], None
+        if prec == 0:
+            ib.profile_begin(ib.PROF_SWEEP64)
+        for rep in range(3 + 5):
+            p = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, cyc, rr = ctx.mg_solve(b, p, prec, 1e-10, 200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 3:
+                times.append(e0.elapsed_time(e1))
+        if prec == 0:
+            s64_ms, s64_n = ib.profile_end()
+            avg = s64_ms / max(s64_n, 1)
+            ach = 40.0 * n * n / (avg * 1e-3) / 1e9
+            roof64 = {"kernel": "k_rbgs_sweep<double> (fine level)", "bound": "hbm",
+                      "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": ach / pk["hbm_gbs"], "traffic": None,
+                      "avg_launch_us": avg * 1e3, "launches": s64_n,
+                      "algorithmic_bytes_per_cell": 40}
+        solve[label] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr}
+
+    # end to end through the C ABI with host buffers: markers in, pressure out
+    Xh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
+    Yh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
+    ph = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
+    ctx.get_markers_host(Xh, Yh)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_markers_host(Xh, Yh)
+        ctx.ns_step(dt, 1, 1)
+        ctx.get_host("p", ph)
+        ctx.get_markers_host(Xh, Yh)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+
+    avg_sweep = sweep_ms / max(sweep_n, 1)
+    bpc = 20.0 if sweep_kind == ib.PROF_SWEEP32 else 40.0
+    ach = bpc * n * n / (avg_sweep * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if args.precision == 1 else "f64", "data": "synthetic",
+        "config": {"workload": name, "nx": n, "ny": n, "drops": int(mk.ndrops),
+                   "markers": int(mk.M), "density_ratio": 1000, "viscosity_ratio": 100,
+                   "spread": "irrotational", "relocate_every": 10, "tol": 1e-10,
+                   "solver": ("FP32 V(2,2) in FP64 defect correction" if args.precision == 1
+                              else "FP64 V(2,2)"),
+                   "warm_start": "previous pressure", "l2": "flushed before each step (256 MiB)",
+                   "mean_vcycles_per_step": statistics.mean(cycles)},
+        "pressure_solve_ms": solve,
+        "clocks": clocks,
+        "e2e": {"value": ws * e2e_steps / e2e_t, "unit": "steps/s",
+                "h2d_bytes_per_step": int(2 * ctx.M * 8),
+                "d2h_bytes_per_step": int(n * n * 8 + 2 * ctx.M * 8)},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": ("k_rbgs_sweep<float> (fine level)" if sweep_kind == 1
+                                else "k_rbgs_sweep<double> (fine level)"),
+                     "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / pk["hbm_gbs"], "traffic": None,
+                     "peak_source": pk_kind, "avg_launch_us": avg_sweep * 1e3,
+                     "launches": sweep_n, "algorithmic_bytes_per_cell": bpc},
+        "roofline_fp64_sweep": roof64,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, t = cpu_baseline(name, 1)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"1 oracle time step of {name} ({t:.1f} s)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="multidrop1024", choices=list(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * ib.h -- C ABI of the GB300 (sm_103a) immersed-boundary projection library:
+ * the per-time-step variable-density projection of Ong & Miura's one-fluid
+ * immersed-boundary method (arXiv 1807.10504) and the marker kernels it
+ * consumes.
+ *
+ * Layout (all arrays row-major, x fastest, no padding):
+ *   cells   (i,j)  i = 0..nx-1, j = 0..ny-1   index j*nx + i
+ *   x-faces (i,j)  i = 0..nx,   j = 0..ny-1   index j*(nx+1) + i   (u, Fx, beta_x)
+ *   y-faces (i,j)  i = 0..nx-1, j = 0..ny     index j*nx + i       (v, Fy, beta_y)
+ *   cell (i,j) has centre (x0 + (i+1/2)h, y0 + (j+1/2)h); cells are square.
+ *   Wall faces (i = 0, nx of u; j = 0, ny of v) are no-slip walls: u, v,
+ *   beta and F there are zero on output and ignored on input.
+ *   Markers: ndrops closed counter-clockwise polylines; drop d owns markers
+ *   drop_start[d] .. drop_start[d+1]-1, the last joined to the first.
+ *
+ * Pointers: "device" arrays are caller-owned CUDA device memory (borrowed for
+ * the duration of the call, never freed or retained); "host" arrays are plain
+ * host memory.  Every call is ordered on the stream given to ib_init (or
+ * passed explicitly); calls that return results to the host synchronise
+ * that stream.  No call aborts, traps or prints: each returns an ib_status
+ * and, for context calls, ib_last_error() gives a one-line message.
+ * Numbers are IEEE binary64 unless stated.
+ */
+#ifndef IB_H
+#define IB_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IB_OK = 0,
+    IB_EINVAL = 1,   /* bad argument: sizes, null pointer, unsupported grid */
+    IB_ENOMEM = 2,   /* device allocation failed */
+    IB_ENOTCONV = 3, /* pressure solve hit max_cycles above tol (result kept) */
+    IB_ENAN = 4,     /* non-finite residual */
+    IB_EMARKER = 5,  /* marker outside the domain, closer than 3 cells to a
+                        wall, or a drop not counter-clockwise */
+    IB_ECUDA = 6     /* a CUDA runtime call failed */
+} ib_status;
+
+typedef struct ib_config {
+    int32_t nx, ny;           /* cells; multigrid halves both while even and >= 8 */
+    double h, x0, y0;         /* cell size and lower-left corner */
+    double rho_g, rho_l;      /* ambient (H = 0) and drop (H = 1) density */
+    double mu_g, mu_l;        /* ambient and drop dynamic viscosity */
+    double sigma;             /* surface tension coefficient */
+    double gx, gy;            /* uniform body acceleration */
+    int32_t kernel;           /* 0: cosine kernel, Sec. 2.2 Eq. (cherby); 1: Peskin 4-point */
+    int32_t spread;           /* 0: conventional, Sec. 3.1 Eq. (delta_vec);
+                                 1: irrotational, Sec. 3.2 Eq. (delta_hea_xy) */
+    int32_t precision;        /* 0: FP64 multigrid; 1: FP32 V-cycles inside FP64
+                                 defect correction (residual, coarsest solve FP64) */
+    double tol;               /* relative residual ||b - A p||_2 / ||b||_2 */
+    int32_t max_cycles;       /* V-cycles (or outer iterations) per solve */
+    int32_t nu1, nu2;         /* pre/post red-black Gauss-Seidel sweeps */
+    int32_t relocate_every;   /* B-spline relocation period in steps, 0 = never */
+} ib_config;
+
+typedef struct ib_ctx ib_ctx;
+
+/* ---------------------------------------------------------------------- */
+/* Context: owns every device buffer it allocates (fields, markers, cell
+ * lists, the multigrid hierarchy).  `stream` is a cudaStream_t (0 = legacy
+ * default stream).  X, Y, drop_start are HOST arrays of nmarkers and
+ * ndrops+1 entries, copied in.  Fields start at zero.
+ * Errors: IB_EINVAL (sizes, grid that cannot coarsen to <= 1024 coarsest
+ * cells, more than 2^20 markers), IB_EMARKER, IB_ENOMEM, IB_ECUDA; on error
+ * *out is NULL and nothing stays allocated.                                */
+ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X,
+                  const double *Y, const int32_t *drop_start, int32_t ndrops,
+                  void *stream);
+void ib_destroy(ib_ctx *ctx);
+const char *ib_last_error(const ib_ctx *ctx); /* never NULL */
+
+/* Replace / read the marker positions (nmarkers entries each).  where = 0:
+ * host pointers, 1: device pointers.  Set validates the positions
+ * (IB_EMARKER) and keeps the drop structure given to ib_init.             */
+ib_status ib_set_markers(ib_ctx *ctx, const double *X, const double *Y, int where);
+ib_status ib_get_markers(ib_ctx *ctx, double *X, double *Y, int where);
+int32_t ib_num_markers(const ib_ctx *ctx);
+
+/* Named fields of the context, copied to/from `dst`/`src` (where = 0 host,
+ * 1 device).  which: 0 u, 1 v, 2 p, 3 H, 4 rho, 5 beta_x, 6 beta_y, 7 Fx,
+ * 8 Fy, 9 rhs b, 10 mu, 11 u*, 12 v*.  Sizes follow the layout above.    */
+ib_status ib_get_field(ib_ctx *ctx, int which, double *dst, int where);
+ib_status ib_set_field(ib_ctx *ctx, int which, const double *src, int where);
+
+/* Section 4 Eq. (ten_f): signed discrete curvature at each marker (positive
+ * for a convex counter-clockwise drop), unit inward normal and arc weight
+ * ds_m = (|X_m - X_{m-1}| + |X_{m+1} - X_m|)/2.  Device outputs, nmarkers
+ * each; any may be NULL.                                                   */
+ib_status ib_marker_geometry(ib_ctx *ctx, double *kappa, double *nx,
+                             double *ny, double *ds);
+
+/* Marker-to-cell binning: key = floor((Y-y0)/h)*nx + floor((X-x0)/h) and the
+ * marker ids ordered by (key, id); device outputs (uint32, nmarkers each;
+ * either may be NULL) and cell_start (uint32, nx*ny+1, may be NULL).      */
+ib_status ib_marker_sort(ib_ctx *ctx, uint32_t *keys_sorted,
+                         uint32_t *ids_sorted, uint32_t *cell_start);
+
+/* Section 2.2 Eq. (jump_condu): U(X_m) = sum over faces u phi(rx) phi(ry)
+ * with the configured kernel; u, v device face arrays, U, V device
+ * marker arrays (nmarkers).                                                */
+ib_status ib_interp(ib_ctx *ctx, const double *u, const double *v, double *U,
+                    double *V);
+
+/* Surface-tension spreading onto faces.  mode 0: conventional, Sec. 3.1 Eq.
+ * (delta_vec), F = sum_m fmag_m n_m ds_m phi phi / h^2, a deterministic
+ * gather over markers sorted by cell.  mode 1: irrotational, Sec. 3.2 Eqs.
+ * (delta_hea), (delta_hea_xy): H from the five-strip polygons about every
+ * segment, F = f_face (H_ij - H_{i-1,j}) / h with f_face from the nearest
+ * segment.  fmag: device per-marker force magnitude, or NULL for sigma *
+ * kappa.  Fx, Fy device face arrays; H device cell array or NULL (mode 1
+ * only; mode 0 leaves H untouched).  Also stores Fx, Fy (and H) in the
+ * context.                                                                 */
+ib_status ib_spread(ib_ctx *ctx, int mode, const double *fmag, double *Fx,
+                    double *Fy, double *H);
+
+/* Section 3.2 polygon discrete Heaviside alone (device cell array).        */
+ib_status ib_heaviside(ib_ctx *ctx, double *H);
+
+/* Section 4 Eqs. (bspline), (bcurve), (bspline_ls): least-squares periodic
+ * cubic B-spline through each drop's markers (knot spacing ~1.5 h, chord
+ * length parameters) and re-placement of the same number of markers at equal
+ * arc length.  Updates the context's markers.  IB_EINVAL if a drop's normal
+ * equations are not positive definite.                                     */
+ib_status ib_relocate(ib_ctx *ctx);
+
+/* Section 2.1 Eq. (ps): load the face coefficients beta_x, beta_y (device
+ * face arrays) the solver will use and build the coarse hierarchy
+ * (coarse face = mean of its two fine faces, FP32 copies, inverse
+ * diagonals, dense LU of the coarsest level).                              */
+ib_status mg_setup(ib_ctx *ctx, const double *bx, const double *by);
+
+/* Solve div(beta grad p) = rhs - mean(rhs) with the coefficients of the last
+ * mg_setup (or ns_step) to ||b - A p||_2 <= tol ||b||_2 by V(nu1,nu2)
+ * cycles (precision 0) or FP64 defect correction around FP32 V-cycles
+ * (precision 1); p (device cell array) is the initial guess on entry and
+ * the mean-zero solution on exit; rhs (device) is not modified.  cycles_out,
+ * relres_out are host pointers (may be NULL).  Returns IB_ENOTCONV when the
+ * cap is reached (p holds the last iterate) and IB_ENAN on a non-finite
+ * residual.                                                                */
+ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
+                   double tol, int max_cycles, int *cycles_out,
+                   double *relres_out);
+
+/* One or more time steps of Section 2.1's fractional step with the force in
+ * the projection (Sec. 3.2 Eq. (ns2_new)): [B-spline relocation every
+ * relocate_every steps], curvature, Heaviside, rho/mu/beta (Eq.
+ * (indicator)), AB2 advection + explicit viscous predictor (Eqs. (ad_bf),
+ * (cr_ni)), spreading, rhs, pressure solve, correction, interpolation and
+ * marker advection X += dt U.  warm: 0 zero initial pressure, 1 previous
+ * step's pressure.  The last step's cycles and residual are returned by
+ * ib_last_solve.                                                           */
+ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
+ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
+
+/* Measurement hooks.  ib_launch_count: kernels launched by this library in
+ * this process so far.  ib_profile_begin(kind) starts CUDA-event timing, on
+ * the launching stream, of every launch of one kernel class (0: fine-level
+ * FP64 red-black sweep, 1: fine-level FP32 sweep, 2: fine-level FP64
+ * residual norm); ib_profile_end synchronises on the recorded events and
+ * returns their summed duration (ms) and count.  Timing is process-wide and
+ * not thread-safe; at most 16384 launches are recorded.                    */
+unsigned long long ib_launch_count(void);
+ib_status ib_profile_begin(int kind);
+ib_status ib_profile_end(double *total_ms, int *launches);
+
+/* Checkpoint: every field, the AB2 history, markers and the step counter,
+ * written to / read from a binary file at `path` (host I/O, synchronises).
+ * ib_load requires a context with the same nx, ny and marker count.       */
+ib_status ib_save(ib_ctx *ctx, const char *path);
+ib_status ib_load(ib_ctx *ctx, const char *path);
+
+/* ---------------------------------------------------------------------- */
+/* Context-free grid operators (device arrays, launched on `stream`, no
+ * allocation).  Each is one step of the path, exposed for verification.
+ * Errors: IB_EINVAL for bad sizes or NULL pointers, IB_ECUDA on launch
+ * failure.                                                                 */
+
+/* Section 2.2 Eq. (indicator) and Section 2.1: rho, mu from H; beta on
+ * faces = 1 / (two-cell average of rho), walls 0.                          */
+ib_status ib_op_coeffs(int32_t nx, int32_t ny, double rho_g, double rho_l,
+                       double mu_g, double mu_l, const double *H, double *rho,
+                       double *mu, double *bx, double *by, void *stream);
+/* Section 2.1 Eq. (ps): r = b - A p (A the 5-point flux-form operator).    */
+ib_status ib_op_residual(int32_t nx, int32_t ny, double h, const double *bx,
+                         const double *by, const double *b, const double *p,
+                         double *r, void *stream);
+/* nsweeps red-black Gauss-Seidel sweeps on A p = b (red = (i+j) even first). */
+ib_status ib_op_rbgs(int32_t nx, int32_t ny, double h, const double *bx,
+                     const double *by, const double *b, double *p,
+                     int32_t nsweeps, void *stream);
+/* rc = average of the four children of r - A p (nx, ny even).            */
+ib_status ib_op_restrict_residual(int32_t nx, int32_t ny, double h,
+                                  const double *bx, const double *by,
+                                  const double *b, const double *p, double *rc,
+                                  void *stream);
+/* ef += bilinear prolongation (9,3,3,1)/16 of ec (nxc x nyc).             */
+ib_status ib_op_prolong_add(int32_t nxc, int32_t nyc, const double *ec,
+                            double *ef, void *stream);
+/* Coarse faces = mean of the two fine faces (nx, ny even).                 */
+ib_status ib_op_coarsen_beta(int32_t nx, int32_t ny, const double *bx,
+                             const double *by, double *bxc, double *byc,
+                             void *stream);
+/* Section 2.1 Eq. (ps) and Sec. 3.2 Eq. (ns2_new):
+ * b = div(u*)/dt + div(beta F).                                            */
+ib_status ib_op_rhs(int32_t nx, int32_t ny, double h, double dt,
+                    const double *us, const double *vs, const double *Fx,
+                    const double *Fy, const double *bx, const double *by,
+                    double *b, void *stream);
+/* u = u* + dt beta (F - grad p) on interior faces, walls 0.               */
+ib_status ib_op_correct(int32_t nx, int32_t ny, double h, double dt,
+                        const double *us, const double *vs, const double *p,
+                        const double *Fx, const double *Fy, const double *bx,
+                        const double *by, double *u, double *v, void *stream);
+/* Section 2.1 Eqs. (ad_bf), (cr_ni): u* = u + dt((D - (3/2 A - 1/2 A_prev))
+ * / rho_face + g), Euler when have_prev = 0; au, av receive A (face
+ * arrays).                                                                 */
+ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt,
+                          const double *rho, const double *mu, const double *u,
+                          const double *v, const double *au_prev,
+                          const double *av_prev, int32_t have_prev, double gx,
+                          double gy, double *us, double *vs, double *au,
+                          double *av, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -75,6 +75,7 @@ def lib():
                                       _D, _D]),
             "or_curvature": (None, [_i, _D, _D, _i, _I32, _D, _D, _D, _D]),
             "or_inside": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D]),
+            "or_inside_cell": (_d, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32]),
             "or_heaviside": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D]),
             "or_heaviside_cell": (_d, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _d]),
             "or_spread_irrot": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D, _D,
@@ -272,6 +273,11 @@ def inside(X, Y, drop_start, nx, ny, h, x0=0.0, y0=0.0):
     lib().or_inside(nx, ny, h, x0, y0, len(X), _f64(X), _f64(Y), len(drop_start) - 1,
                     _ds(drop_start), chi)
     return chi
+
+
+def inside_cell(i, j, X, Y, drop_start, h, x0=0.0, y0=0.0):
+    return lib().or_inside_cell(int(i), int(j), h, x0, y0, len(X), _f64(X), _f64(Y),
+                                len(drop_start) - 1, _ds(drop_start))
 
 
 def heaviside(X, Y, drop_start, nx, ny, h, x0=0.0, y0=0.0):

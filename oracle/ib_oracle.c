@@ -691,13 +691,17 @@ void or_spread_conv(int kernel, int nx, int ny, double h, double x0,
 }
 
 /* ------------------------------------------------------------------------ */
-static void nbrs(int m, int ndrops, const int32_t *ds_, int *prev, int *next)
+/* Predecessor and successor of every marker along its closed polyline.     */
+static void links(int M, int ndrops, const int32_t *ds_, int *prev, int *next)
 {
-    int d = 0;
-    while (d + 1 < ndrops && m >= ds_[d + 1]) d++;
-    int s = ds_[d], e = ds_[d + 1];
-    *prev = (m == s) ? e - 1 : m - 1;
-    *next = (m == e - 1) ? s : m + 1;
+    for (int d = 0; d < ndrops; d++) {
+        int s = ds_[d], e = ds_[d + 1];
+        for (int m = s; m < e; m++) {
+            prev[m] = (m == s) ? e - 1 : m - 1;
+            next[m] = (m == e - 1) ? s : m + 1;
+        }
+    }
+    (void)M;
 }
 
 /* Section 4 Eq. (ten_f): curvature = change of the unit tangent over the
@@ -710,9 +714,10 @@ void or_curvature(int M, const double *X, const double *Y, int ndrops,
                   const int32_t *drop_start, double *kappa, double *nxm,
                   double *nym, double *ds)
 {
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    links(M, ndrops, drop_start, prv, nxt);
     for (int m = 0; m < M; m++) {
-        int pm, nm;
-        nbrs(m, ndrops, drop_start, &pm, &nm);
+        int pm = prv[m], nm = nxt[m];
         double ax = X[m] - X[pm], ay = Y[m] - Y[pm];
         double bx = X[nm] - X[m], by = Y[nm] - Y[m];
         double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
@@ -728,17 +733,17 @@ void or_curvature(int M, const double *X, const double *Y, int ndrops,
         nym[m] = ny_ / ln;
         ds[m] = dsm;
     }
+    free(prv); free(nxt);
 }
 
 /* ------------------------------------------------------------------------ */
 /* Crossing-number test of a point against every segment of every drop.      */
 static int inside_point(double px, double py, int M, const double *X,
-                        const double *Y, int ndrops, const int32_t *drop_start)
+                        const double *Y, const int *nxt)
 {
     int cnt = 0;
     for (int m = 0; m < M; m++) {
-        int pm, nm;
-        nbrs(m, ndrops, drop_start, &pm, &nm);
+        int nm = nxt[m];
         double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
         if ((ay > py) != (by > py)) {
             double xc = ax + (py - ay) * (bx - ax) / (by - ay);
@@ -748,15 +753,49 @@ static int inside_point(double px, double py, int M, const double *X,
     return cnt & 1;
 }
 
+double or_inside_cell(int i, int j, double h, double x0, double y0, int M,
+                      const double *X, const double *Y, int ndrops,
+                      const int32_t *drop_start)
+{
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    links(M, ndrops, drop_start, prv, nxt);
+    int r = inside_point(x0 + ((double)i + 0.5) * h, y0 + ((double)j + 0.5) * h, M, X, Y, nxt);
+    free(prv); free(nxt);
+    return r;
+}
+
+/* The same crossing-number test for every cell centre, row by row: the
+ * crossings of a row's centre line are computed once, and a cell is inside
+ * when an odd number of them lie strictly to the right of its centre.       */
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
 void or_inside(int nx, int ny, double h, double x0, double y0, int M,
                const double *X, const double *Y, int ndrops,
                const int32_t *drop_start, double *chi)
 {
-    for (int j = 0; j < ny; j++)
-        for (int i = 0; i < nx; i++)
-            chi[CC(i, j)] = inside_point(x0 + ((double)i + 0.5) * h,
-                                         y0 + ((double)j + 0.5) * h, M, X, Y,
-                                         ndrops, drop_start);
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    double *xs = (double *)malloc((size_t)(M + 1) * sizeof(double));
+    links(M, ndrops, drop_start, prv, nxt);
+    for (int j = 0; j < ny; j++) {
+        double py = y0 + ((double)j + 0.5) * h;
+        int nc = 0;
+        for (int m = 0; m < M; m++) {
+            double ax = X[m], ay = Y[m], bx = X[nxt[m]], by = Y[nxt[m]];
+            if ((ay > py) != (by > py)) xs[nc++] = ax + (py - ay) * (bx - ax) / (by - ay);
+        }
+        qsort(xs, (size_t)nc, sizeof(double), cmp_double);
+        int k = 0; /* crossings <= the current centre */
+        for (int i = 0; i < nx; i++) {
+            double px = x0 + ((double)i + 0.5) * h;
+            while (k < nc && !(xs[k] > px)) k++;
+            chi[CC(i, j)] = (double)((nc - k) & 1);
+        }
+    }
+    free(prv); free(nxt); free(xs);
 }
 
 /* Area of the part of polygon (px,py)[n] inside the unit square [0,1]^2, by
@@ -842,10 +881,11 @@ double or_heaviside_cell(int i, int j, double h, double x0, double y0, int M,
     double *nxm = (double *)malloc((size_t)M * sizeof(double));
     double *nym = (double *)malloc((size_t)M * sizeof(double));
     marker_normals(M, X, Y, ndrops, drop_start, nxm, nym);
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    links(M, ndrops, drop_start, prv, nxt);
     double acc = 0.0, cov = 0.0;
     for (int m = 0; m < M; m++) {
-        int pm, nm;
-        nbrs(m, ndrops, drop_start, &pm, &nm);
+        int nm = nxt[m];
         for (int k = 0; k < 5; k++) {
             double qx[4], qy[4];
             strip_quad(m, nm, k, X, Y, nxm, nym, x0, y0, h, qx, qy);
@@ -855,7 +895,7 @@ double or_heaviside_cell(int i, int j, double h, double x0, double y0, int M,
             cov += A;
         }
     }
-    free(nxm); free(nym);
+    free(nxm); free(nym); free(prv); free(nxt);
     double unc = 1.0 - cov;
     if (unc < 0.0) unc = 0.0;
     return acc + unc * chi;
@@ -873,9 +913,10 @@ void or_heaviside(int nx, int ny, double h, double x0, double y0, int M,
     double *nym = (double *)malloc((size_t)M * sizeof(double));
     or_inside(nx, ny, h, x0, y0, M, X, Y, ndrops, drop_start, chi);
     marker_normals(M, X, Y, ndrops, drop_start, nxm, nym);
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    links(M, ndrops, drop_start, prv, nxt);
     for (int m = 0; m < M; m++) {
-        int pm, nm;
-        nbrs(m, ndrops, drop_start, &pm, &nm);
+        int nm = nxt[m];
         for (int k = 0; k < 5; k++) {
             double qx[4], qy[4];
             strip_quad(m, nm, k, X, Y, nxm, nym, x0, y0, h, qx, qy);
@@ -908,7 +949,7 @@ void or_heaviside(int nx, int ny, double h, double x0, double y0, int M,
         if (unc < 0.0) unc = 0.0;
         H[c] = acc[c] + unc * chi[c];
     }
-    free(chi); free(acc); free(cov); free(nxm); free(nym);
+    free(chi); free(acc); free(cov); free(nxm); free(nym); free(prv); free(nxt);
 }
 
 /* Section 3.2 Eq. (delta_hea_xy), with the 1/h that turns the difference of
@@ -918,13 +959,12 @@ void or_heaviside(int nx, int ny, double h, double x0, double y0, int M,
  * interpolated between that segment's two markers.  Faces with a zero
  * difference carry no force; wall faces none.                                */
 static double face_fmag(double qx, double qy, int M, const double *X,
-                        const double *Y, int ndrops, const int32_t *drop_start,
-                        double x0, double y0, double h, const double *fmag)
+                        const double *Y, const int *nxt, double x0, double y0,
+                        double h, const double *fmag)
 {
     double best = INFINITY, fb = 0.0;
     for (int m = 0; m < M; m++) {
-        int pm, nm;
-        nbrs(m, ndrops, drop_start, &pm, &nm);
+        int nm = nxt[m];
         double ax = (X[m] - x0) / h, ay = (Y[m] - y0) / h;
         double bx = (X[nm] - x0) / h, by = (Y[nm] - y0) / h;
         double ex = bx - ax, ey = by - ay;
@@ -943,14 +983,16 @@ void or_spread_irrot(int nx, int ny, double h, double x0, double y0, int M,
                      const int32_t *drop_start, const double *fmag,
                      const double *H, double *Fx, double *Fy)
 {
+    int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
+    links(M, ndrops, drop_start, prv, nxt);
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++) {
             double F = 0.0;
             if (i > 0 && i < nx) {
                 double dH = H[CC(i, j)] - H[CC(i - 1, j)];
                 if (dH != 0.0)
-                    F = face_fmag((double)i, (double)j + 0.5, M, X, Y, ndrops,
-                                  drop_start, x0, y0, h, fmag) * dH / h;
+                    F = face_fmag((double)i, (double)j + 0.5, M, X, Y, nxt, x0, y0, h,
+                                  fmag) * dH / h;
             }
             Fx[XF(i, j)] = F;
         }
@@ -960,11 +1002,12 @@ void or_spread_irrot(int nx, int ny, double h, double x0, double y0, int M,
             if (j > 0 && j < ny) {
                 double dH = H[CC(i, j)] - H[CC(i, j - 1)];
                 if (dH != 0.0)
-                    F = face_fmag((double)i + 0.5, (double)j, M, X, Y, ndrops,
-                                  drop_start, x0, y0, h, fmag) * dH / h;
+                    F = face_fmag((double)i + 0.5, (double)j, M, X, Y, nxt, x0, y0, h,
+                                  fmag) * dH / h;
             }
             Fy[YF(i, j)] = F;
         }
+    free(prv); free(nxt);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1076,6 +1119,7 @@ int or_bspline_relocate(int M, const double *X, const double *Y, int ndrops,
         int g = (int)floor(L / (1.5 * h) + 0.5);
         if (g < 4) g = 4;
         if (g > n) g = n;
+        if (g < 1) g = 1;
         double tau = L / g;
         double *G = (double *)calloc((size_t)g * g, sizeof(double));
         double *cx = (double *)calloc((size_t)g, sizeof(double));

@@ -89,6 +89,9 @@ void or_curvature(int M, const double *X, const double *Y, int ndrops,
 void or_inside(int nx, int ny, double h, double x0, double y0, int M,
                const double *X, const double *Y, int ndrops,
                const int32_t *drop_start, double *chi);
+double or_inside_cell(int i, int j, double h, double x0, double y0, int M,
+                      const double *X, const double *Y, int ndrops,
+                      const int32_t *drop_start);
 void or_heaviside(int nx, int ny, double h, double x0, double y0, int M,
                   const double *X, const double *Y, int ndrops,
                   const int32_t *drop_start, double *H);

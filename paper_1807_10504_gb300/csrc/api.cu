@@ -1,0 +1,557 @@
+// C ABI of the library (declared in include/ib.h): the context that owns the
+// fields, markers and multigrid hierarchy, the composed time step, and the
+// context-free verification entry points.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ib_internal.cuh"
+
+struct ib_ctx {
+    ib_config cfg;
+    cudaStream_t s = nullptr;
+    std::string err;
+    ibk::MG mg;
+    ibk::Markers mk;
+    double *u = nullptr, *v = nullptr, *us = nullptr, *vs = nullptr, *au = nullptr,
+           *av = nullptr, *p = nullptr, *H = nullptr, *rho = nullptr, *mu = nullptr,
+           *bx = nullptr, *by = nullptr, *Fx = nullptr, *Fy = nullptr, *b = nullptr;
+    void *fmem = nullptr;
+    int step = 0;
+    int have_prev = 0;
+    int last_cycles = 0;
+    double last_relres = 0.0;
+    bool mg_ready = false;
+    uint32_t *flags_host = nullptr;
+};
+
+namespace {
+
+using namespace ibk;
+
+ib_status fail(ib_ctx *c, ib_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+ib_status cuda_check(ib_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return IB_OK;
+    return fail(c, IB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+ib_status launch_check(ib_ctx *c, const char *what)
+{
+    return cuda_check(c, cudaGetLastError(), what);
+}
+
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Orientation and wall distance of host marker arrays.
+ib_status check_markers_host(ib_ctx *c, const ib_config &g, const double *X, const double *Y,
+                             const int32_t *ds, int nd)
+{
+    const double m3 = 3.0 * g.h;
+    for (int d = 0; d < nd; d++) {
+        int s = ds[d], e = ds[d + 1];
+        if (e - s < 3) return fail(c, IB_EINVAL, "a drop needs at least 3 markers");
+        double a = 0.0;
+        for (int m = s; m < e; m++) {
+            int n = (m + 1 == e) ? s : m + 1;
+            if (!(X[m] >= g.x0 + m3 && X[m] <= g.x0 + g.nx * g.h - m3 && Y[m] >= g.y0 + m3 &&
+                  Y[m] <= g.y0 + g.ny * g.h - m3))
+                return fail(c, IB_EMARKER, "marker outside the domain or within 3 cells of a wall");
+            a += X[m] * Y[n] - X[n] * Y[m];
+        }
+        if (!(a > 0.0)) return fail(c, IB_EMARKER, "drop markers are not counter-clockwise");
+    }
+    return IB_OK;
+}
+
+ib_status read_flags(ib_ctx *c)
+{
+    cudaError_t e = cudaMemcpyAsync(c->flags_host, c->mk.flags, 3 * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "flags");
+    ib_status st = IB_OK;
+    if (c->flags_host[0]) st = fail(c, IB_EMARKER, "a marker left the domain or came within 3 cells of a wall");
+    else if (c->flags_host[1]) st = fail(c, IB_EINVAL, "too many interface segments near a cell block or row");
+    else if (c->flags_host[2]) st = fail(c, IB_EINVAL, "B-spline normal equations not positive definite");
+    cudaMemsetAsync(c->mk.flags, 0, 3 * sizeof(uint32_t), c->s);
+    return st;
+}
+
+double *field_ptr(ib_ctx *c, int which, size_t *n)
+{
+    const size_t nc = (size_t)c->cfg.nx * c->cfg.ny, fx = (size_t)(c->cfg.nx + 1) * c->cfg.ny,
+                 fy = (size_t)c->cfg.nx * (c->cfg.ny + 1);
+    switch (which) {
+    case 0: *n = fx; return c->u;
+    case 1: *n = fy; return c->v;
+    case 2: *n = nc; return c->p;
+    case 3: *n = nc; return c->H;
+    case 4: *n = nc; return c->rho;
+    case 5: *n = fx; return c->bx;
+    case 6: *n = fy; return c->by;
+    case 7: *n = fx; return c->Fx;
+    case 8: *n = fy; return c->Fy;
+    case 9: *n = nc; return c->b;
+    case 10: *n = nc; return c->mu;
+    case 11: *n = fx; return c->us;
+    case 12: *n = fy; return c->vs;
+    default: *n = 0; return nullptr;
+    }
+}
+
+ib_status spread_into(ib_ctx *c, int mode, const double *fmag, double *Fx, double *Fy, double *H)
+{
+    Markers &mk = c->mk;
+    launch_geometry(mk, c->cfg.sigma, c->s);
+    launch_sort(mk, c->s);
+    const double *f = fmag ? fmag : mk.fmag;
+    if (mode == 0) {
+        launch_spread_conv(mk, c->cfg.kernel, f, Fx, Fy, c->s);
+    } else {
+        double *Hd = H ? H : c->H;
+        launch_heaviside(mk, Hd, c->s);
+        launch_spread_irrot(mk, f, Hd, Fx, Fy, c->s);
+    }
+    return launch_check(c, "spread");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ib_last_error(const ib_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+void ib_destroy(ib_ctx *c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    else cudaDeviceSynchronize();
+    mg_free(c->mg);
+    markers_free(c->mk);
+    if (c->fmem) cudaFree(c->fmem);
+    if (c->flags_host) cudaFreeHost(c->flags_host);
+    delete c;
+}
+
+ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const double *Y,
+                  const int32_t *drop_start, int32_t ndrops, void *stream)
+{
+    if (!out) return IB_EINVAL;
+    *out = nullptr;
+    if (!cfg || !X || !Y || !drop_start || ndrops < 1) return IB_EINVAL;
+    const ib_config &g = *cfg;
+    if (g.nx < 2 || g.ny < 2 || (long)g.nx * g.ny > (1L << 28) || !(g.h > 0) || g.nu1 < 0 ||
+        g.nu2 < 0 || g.max_cycles < 0 || !(g.tol >= 0) || g.kernel < 0 || g.kernel > 1 ||
+        g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 1)
+        return IB_EINVAL;
+    std::vector<int> nxs, nys;
+    if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
+    if (drop_start[0] != 0) return IB_EINVAL;
+    for (int d = 0; d < ndrops; d++)
+        if (drop_start[d + 1] - drop_start[d] < 3) return IB_EINVAL;
+    const int M = drop_start[ndrops];
+    if (M > (1 << 20)) return IB_EINVAL;
+    ib_ctx *c = new ib_ctx();
+    c->cfg = g;
+    c->s = (cudaStream_t)stream;
+    ib_status st = check_markers_host(c, g, X, Y, drop_start, ndrops);
+    if (st != IB_OK) { delete c; return st; }
+    const size_t nc = (size_t)g.nx * g.ny, fx = (size_t)(g.nx + 1) * g.ny, fy = (size_t)g.nx * (g.ny + 1);
+    size_t bytes = al(fx * 8) * 6 + al(fy * 8) * 6 + al(nc * 8) * 5;
+    if (cudaMalloc(&c->fmem, bytes) != cudaSuccess) { c->fmem = nullptr; ib_destroy(c); return IB_ENOMEM; }
+    char *q = (char *)c->fmem;
+    auto take = [&](size_t b) { char *r = q; q += al(b); return (double *)r; };
+    c->u = take(fx * 8); c->us = take(fx * 8); c->au = take(fx * 8);
+    c->bx = take(fx * 8); c->Fx = take(fx * 8);
+    double *spare_x = take(fx * 8); (void)spare_x;
+    c->v = take(fy * 8); c->vs = take(fy * 8); c->av = take(fy * 8);
+    c->by = take(fy * 8); c->Fy = take(fy * 8);
+    double *spare_y = take(fy * 8); (void)spare_y;
+    c->p = take(nc * 8); c->H = take(nc * 8); c->rho = take(nc * 8); c->mu = take(nc * 8);
+    c->b = take(nc * 8);
+    cudaError_t e = cudaMemset(c->fmem, 0, bytes);
+    if (e == cudaSuccess) e = mg_alloc(c->mg, g.nx, g.ny, g.h);
+    if (e == cudaSuccess) e = markers_alloc(c->mk, M, ndrops, g.nx, g.ny, g.h, g.x0, g.y0, drop_start);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->flags_host, 64);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mk.X, X, (size_t)M * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mk.Y, Y, (size_t)M * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        ib_status r = (e == cudaErrorMemoryAllocation) ? IB_ENOMEM : IB_ECUDA;
+        ib_destroy(c);
+        return r;
+    }
+    *out = c;
+    return IB_OK;
+}
+
+int32_t ib_num_markers(const ib_ctx *c) { return c ? c->mk.M : 0; }
+
+ib_status ib_set_markers(ib_ctx *c, const double *X, const double *Y, int where)
+{
+    if (!c || !X || !Y) return IB_EINVAL;
+    const int M = c->mk.M;
+    if (where == 0) {
+        ib_status st = check_markers_host(c, c->cfg, X, Y, c->mk.drop_start_h.data(), c->mk.ndrops);
+        if (st != IB_OK) return st;
+    }
+    cudaMemcpyKind k = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(c->mk.X, X, (size_t)M * 8, k, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->mk.Y, Y, (size_t)M * 8, k, c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "set markers");
+    if (where) {
+        launch_validate(c->mk, c->s);
+        return read_flags(c);
+    }
+    return IB_OK;
+}
+
+ib_status ib_get_markers(ib_ctx *c, double *X, double *Y, int where)
+{
+    if (!c || !X || !Y) return IB_EINVAL;
+    cudaMemcpyKind k = where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(X, c->mk.X, (size_t)c->mk.M * 8, k, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Y, c->mk.Y, (size_t)c->mk.M * 8, k, c->s);
+    if (e == cudaSuccess && !where) e = cudaStreamSynchronize(c->s);
+    return cuda_check(c, e, "get markers");
+}
+
+ib_status ib_get_field(ib_ctx *c, int which, double *dst, int where)
+{
+    if (!c || !dst) return IB_EINVAL;
+    size_t n;
+    double *f = field_ptr(c, which, &n);
+    if (!f) return fail(c, IB_EINVAL, "unknown field");
+    cudaError_t e = cudaMemcpyAsync(dst, f, n * 8, where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess && !where) e = cudaStreamSynchronize(c->s);
+    return cuda_check(c, e, "get field");
+}
+
+ib_status ib_set_field(ib_ctx *c, int which, const double *src, int where)
+{
+    if (!c || !src) return IB_EINVAL;
+    size_t n;
+    double *f = field_ptr(c, which, &n);
+    if (!f) return fail(c, IB_EINVAL, "unknown field");
+    cudaError_t e = cudaMemcpyAsync(f, src, n * 8, where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s);
+    if (which == 5 || which == 6) c->mg_ready = false;
+    return cuda_check(c, e, "set field");
+}
+
+ib_status ib_marker_geometry(ib_ctx *c, double *kappa, double *nx, double *ny, double *ds)
+{
+    if (!c) return IB_EINVAL;
+    launch_geometry(c->mk, c->cfg.sigma, c->s);
+    const size_t b = (size_t)c->mk.M * 8;
+    cudaError_t e = cudaSuccess;
+    if (kappa && e == cudaSuccess) e = cudaMemcpyAsync(kappa, c->mk.kappa, b, cudaMemcpyDeviceToDevice, c->s);
+    if (nx && e == cudaSuccess) e = cudaMemcpyAsync(nx, c->mk.nxm, b, cudaMemcpyDeviceToDevice, c->s);
+    if (ny && e == cudaSuccess) e = cudaMemcpyAsync(ny, c->mk.nym, b, cudaMemcpyDeviceToDevice, c->s);
+    if (ds && e == cudaSuccess) e = cudaMemcpyAsync(ds, c->mk.ds, b, cudaMemcpyDeviceToDevice, c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "geometry");
+    return launch_check(c, "geometry");
+}
+
+__global__ void k_gather_keys(int M, const uint32_t *key, const uint32_t *ids, uint32_t *out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M) out[k] = key[ids[k]];
+}
+
+ib_status ib_marker_sort(ib_ctx *c, uint32_t *keys_sorted, uint32_t *ids_sorted, uint32_t *cell_start)
+{
+    if (!c) return IB_EINVAL;
+    Markers &mk = c->mk;
+    launch_sort(mk, c->s);
+    if (keys_sorted) { note_launch(); k_gather_keys<<<cdiv(mk.M, 256), 256, 0, c->s>>>(mk.M, mk.key, mk.ids, keys_sorted);
+    }
+    cudaError_t e = cudaSuccess;
+    if (ids_sorted) e = cudaMemcpyAsync(ids_sorted, mk.ids, (size_t)mk.M * 4, cudaMemcpyDeviceToDevice, c->s);
+    if (cell_start && e == cudaSuccess)
+        e = cudaMemcpyAsync(cell_start, mk.cell_start, ((size_t)mk.nx * mk.ny + 1) * 4,
+                            cudaMemcpyDeviceToDevice, c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "sort");
+    return launch_check(c, "sort");
+}
+
+ib_status ib_interp(ib_ctx *c, const double *u, const double *v, double *U, double *V)
+{
+    if (!c || !u || !v || !U || !V) return IB_EINVAL;
+    launch_interp(c->mk, c->cfg.kernel, u, v, U, V, 0.0, c->s);
+    return launch_check(c, "interp");
+}
+
+ib_status ib_spread(ib_ctx *c, int mode, const double *fmag, double *Fx, double *Fy, double *H)
+{
+    if (!c || !Fx || !Fy || mode < 0 || mode > 1) return IB_EINVAL;
+    ib_status st = spread_into(c, mode, fmag, c->Fx, c->Fy, H ? H : nullptr);
+    if (st != IB_OK) return st;
+    st = read_flags(c);
+    if (st != IB_OK) return st;
+    const size_t fx = (size_t)(c->cfg.nx + 1) * c->cfg.ny, fy = (size_t)c->cfg.nx * (c->cfg.ny + 1);
+    cudaError_t e = cudaMemcpyAsync(Fx, c->Fx, fx * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Fy, c->Fy, fy * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess && H && mode == 1)
+        e = cudaMemcpyAsync(c->H, H, (size_t)c->cfg.nx * c->cfg.ny * 8, cudaMemcpyDeviceToDevice, c->s);
+    return cuda_check(c, e, "spread copy");
+}
+
+ib_status ib_heaviside(ib_ctx *c, double *H)
+{
+    if (!c || !H) return IB_EINVAL;
+    launch_geometry(c->mk, c->cfg.sigma, c->s);
+    launch_sort(c->mk, c->s);
+    launch_heaviside(c->mk, H, c->s);
+    ib_status st = launch_check(c, "heaviside");
+    if (st != IB_OK) return st;
+    return read_flags(c);
+}
+
+ib_status ib_relocate(ib_ctx *c)
+{
+    if (!c) return IB_EINVAL;
+    launch_relocate(c->mk, c->s);
+    ib_status st = launch_check(c, "relocate");
+    if (st != IB_OK) return st;
+    return read_flags(c);
+}
+
+ib_status mg_setup(ib_ctx *c, const double *bx, const double *by)
+{
+    if (!c || !bx || !by) return IB_EINVAL;
+    mg_build(c->mg, bx, by, c->s);
+    c->mg_ready = true;
+    return launch_check(c, "mg_setup");
+}
+
+ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, double tol,
+                   int max_cycles, int *cycles_out, double *relres_out)
+{
+    if (!c || !rhs || !p || precision < 0 || precision > 1 || max_cycles < 0 || !(tol >= 0))
+        return IB_EINVAL;
+    if (!c->mg_ready) return fail(c, IB_EINVAL, "mg_setup (or ns_step) has not loaded coefficients");
+    int cyc = 0;
+    double rr = 0.0;
+    ib_status st = mg_run(c->mg, rhs, p, precision, tol, max_cycles, c->cfg.nu1, c->cfg.nu2,
+                          &cyc, &rr, c->s, c->err);
+    if (cycles_out) *cycles_out = cyc;
+    if (relres_out) *relres_out = rr;
+    return st;
+}
+
+ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
+{
+    if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 1) return IB_EINVAL;
+    const ib_config &g = c->cfg;
+    Markers &mk = c->mk;
+    for (int it = 0; it < nsteps; it++) {
+        if (g.relocate_every > 0 && c->step % g.relocate_every == 0) launch_relocate(mk, c->s);
+        launch_geometry(mk, g.sigma, c->s);
+        launch_sort(mk, c->s);
+        launch_heaviside(mk, c->H, c->s);
+        launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, c->H, c->rho, c->mu, c->bx,
+                      c->by, c->s);
+        mg_build(c->mg, c->bx, c->by, c->s);
+        c->mg_ready = true;
+        launch_predictor(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
+                         c->have_prev, g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
+        if (g.spread == 0) launch_spread_conv(mk, g.kernel, mk.fmag, c->Fx, c->Fy, c->s);
+        else launch_spread_irrot(mk, mk.fmag, c->H, c->Fx, c->Fy, c->s);
+        launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
+        ib_status st = launch_check(c, "step");
+        if (st != IB_OK) return st;
+        if (!warm) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
+        st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
+                    &c->last_cycles, &c->last_relres, c->s, c->err);
+        if (st != IB_OK && st != IB_ENOTCONV) return st;
+        launch_correct(g.nx, g.ny, g.h, dt, c->us, c->vs, c->p, c->Fx, c->Fy, c->bx, c->by, c->u,
+                       c->v, c->s);
+        launch_interp(mk, g.kernel, c->u, c->v, mk.U, mk.V, dt, c->s);
+        launch_validate(mk, c->s);
+        c->have_prev = 1;
+        c->step++;
+        ib_status fs = read_flags(c);
+        if (fs != IB_OK) return fs;
+        if (st != IB_OK) return st;
+    }
+    return launch_check(c, "step");
+}
+
+unsigned long long ib_launch_count(void) { return launch_count(); }
+
+ib_status ib_profile_begin(int kind)
+{
+    if (kind < 0 || kind > 2) return IB_EINVAL;
+    return prof_begin(kind) ? IB_OK : IB_ECUDA;
+}
+
+ib_status ib_profile_end(double *total_ms, int *launches)
+{
+    return prof_end(total_ms, launches) ? IB_OK : IB_ECUDA;
+}
+
+ib_status ib_last_solve(const ib_ctx *c, int *cycles, double *relres)
+{
+    if (!c) return IB_EINVAL;
+    if (cycles) *cycles = c->last_cycles;
+    if (relres) *relres = c->last_relres;
+    return IB_OK;
+}
+
+// ------------------------------------------------------------- checkpoint
+static const uint64_t kMagic = 0x31303531304249ULL;  // "IB01501"
+
+ib_status ib_save(ib_ctx *c, const char *path)
+{
+    if (!c || !path) return IB_EINVAL;
+    const size_t nc = (size_t)c->cfg.nx * c->cfg.ny, fx = (size_t)(c->cfg.nx + 1) * c->cfg.ny,
+                 fy = (size_t)c->cfg.nx * (c->cfg.ny + 1), M = c->mk.M;
+    std::vector<double> buf(3 * fx + 3 * fy + nc + 2 * M);
+    double *q = buf.data();
+    struct { double *d; size_t n; } parts[] = {{c->u, fx}, {c->au, fx}, {c->us, fx}, {c->v, fy},
+                                               {c->av, fy}, {c->vs, fy}, {c->p, nc},
+                                               {c->mk.X, M}, {c->mk.Y, M}};
+    for (auto &pt : parts) {
+        cudaError_t e = cudaMemcpyAsync(q, pt.d, pt.n * 8, cudaMemcpyDeviceToHost, c->s);
+        if (e != cudaSuccess) return cuda_check(c, e, "save");
+        q += pt.n;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "save");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(c, IB_EINVAL, "cannot open checkpoint for writing");
+    int64_t hdr[6] = {(int64_t)kMagic, c->cfg.nx, c->cfg.ny, (int64_t)M, c->step, c->have_prev};
+    bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1 && fwrite(buf.data(), 8, buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? IB_OK : fail(c, IB_EINVAL, "checkpoint write failed");
+}
+
+ib_status ib_load(ib_ctx *c, const char *path)
+{
+    if (!c || !path) return IB_EINVAL;
+    const size_t nc = (size_t)c->cfg.nx * c->cfg.ny, fx = (size_t)(c->cfg.nx + 1) * c->cfg.ny,
+                 fy = (size_t)c->cfg.nx * (c->cfg.ny + 1), M = c->mk.M;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(c, IB_EINVAL, "cannot open checkpoint");
+    int64_t hdr[6];
+    std::vector<double> buf(3 * fx + 3 * fy + nc + 2 * M);
+    bool ok = fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int64_t)kMagic &&
+              hdr[1] == c->cfg.nx && hdr[2] == c->cfg.ny && hdr[3] == (int64_t)M &&
+              fread(buf.data(), 8, buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return fail(c, IB_EINVAL, "checkpoint does not match this context");
+    const double *q = buf.data();
+    struct { double *d; size_t n; } parts[] = {{c->u, fx}, {c->au, fx}, {c->us, fx}, {c->v, fy},
+                                               {c->av, fy}, {c->vs, fy}, {c->p, nc},
+                                               {c->mk.X, M}, {c->mk.Y, M}};
+    for (auto &pt : parts) {
+        cudaError_t e = cudaMemcpyAsync(pt.d, q, pt.n * 8, cudaMemcpyHostToDevice, c->s);
+        if (e != cudaSuccess) return cuda_check(c, e, "load");
+        q += pt.n;
+    }
+    c->step = (int)hdr[4];
+    c->have_prev = (int)hdr[5];
+    return cuda_check(c, cudaStreamSynchronize(c->s), "load");
+}
+
+// ------------------------------------------------------------- context-free ops
+#define OPCHK(cond) do { if (!(cond)) return IB_EINVAL; } while (0)
+static ib_status op_done()
+{
+    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status ib_op_coeffs(int32_t nx, int32_t ny, double rho_g, double rho_l, double mu_g,
+                       double mu_l, const double *H, double *rho, double *mu, double *bx,
+                       double *by, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && H && rho && mu && bx && by);
+    launch_coeffs(nx, ny, rho_g, rho_l, mu_g, mu_l, H, rho, mu, bx, by, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_residual(int32_t nx, int32_t ny, double h, const double *bx, const double *by,
+                         const double *b, const double *p, double *r, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && bx && by && b && p && r);
+    launch_residual(nx, ny, h, bx, by, b, p, r, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_rbgs(int32_t nx, int32_t ny, double h, const double *bx, const double *by,
+                     const double *b, double *p, int32_t nsweeps, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && bx && by && b && p && nsweeps >= 0);
+    for (int k = 0; k < nsweeps; k++)
+        launch_rbgs(nx, ny, h, bx, by, nullptr, b, p, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_restrict_residual(int32_t nx, int32_t ny, double h, const double *bx,
+                                  const double *by, const double *b, const double *p,
+                                  double *rc, void *stream)
+{
+    OPCHK(nx > 1 && ny > 1 && nx % 2 == 0 && ny % 2 == 0 && h > 0 && bx && by && b && p && rc);
+    launch_restrict_residual(nx, ny, h, bx, by, b, p, rc, nullptr, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_prolong_add(int32_t nxc, int32_t nyc, const double *ec, double *ef, void *stream)
+{
+    OPCHK(nxc > 0 && nyc > 0 && ec && ef);
+    launch_prolong_add(nxc, nyc, ec, ef, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_coarsen_beta(int32_t nx, int32_t ny, const double *bx, const double *by,
+                             double *bxc, double *byc, void *stream)
+{
+    OPCHK(nx > 1 && ny > 1 && nx % 2 == 0 && ny % 2 == 0 && bx && by && bxc && byc);
+    launch_coarsen_beta(nx, ny, bx, by, bxc, byc, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_rhs(int32_t nx, int32_t ny, double h, double dt, const double *us,
+                    const double *vs, const double *Fx, const double *Fy, const double *bx,
+                    const double *by, double *b, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && dt > 0 && us && vs && Fx && Fy && bx && by && b);
+    launch_rhs(nx, ny, h, dt, us, vs, Fx, Fy, bx, by, b, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_correct(int32_t nx, int32_t ny, double h, double dt, const double *us,
+                        const double *vs, const double *p, const double *Fx, const double *Fy,
+                        const double *bx, const double *by, double *u, double *v, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && us && vs && p && Fx && Fy && bx && by && u && v);
+    launch_correct(nx, ny, h, dt, us, vs, p, Fx, Fy, bx, by, u, v, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt, const double *rho,
+                          const double *mu, const double *u, const double *v,
+                          const double *au_prev, const double *av_prev, int32_t have_prev,
+                          double gx, double gy, double *us, double *vs, double *au, double *av,
+                          void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && rho && mu && u && v && us && vs && au && av);
+    OPCHK(!have_prev || (au_prev && av_prev));
+    launch_predictor(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx, gy, us, vs,
+                     au, av, (cudaStream_t)stream);
+    return op_done();
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ib.h"
+
+namespace ibk {
+
+constexpr int kTailCells = 1024;     // levels with at most this many cells run in one CTA
+constexpr int kMaxCoarsest = 1024;   // dense LU limit of the coarsest level
+constexpr int kBlk = 8;              // marker-activity block edge (cells)
+constexpr int kSearch = 7;           // marker search radius (cells) around a cell or face
+constexpr int kMaxCand = 2048;       // candidate segments per activity block
+constexpr int kMaxCross = 2048;      // interface crossings per grid row
+
+inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+// Process-wide count of kernel launches issued by this library.
+void note_launch(int n = 1);
+unsigned long long launch_count();
+
+// Optional CUDA-event timing of one kernel class, on the stream it runs on.
+enum ProfKind { kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2 };
+bool prof_on(int kind);
+void prof_mark(cudaStream_t s, bool start);
+bool prof_begin(int kind);
+bool prof_end(double *total_ms, int *launches);
+
+// ---------------------------------------------------------------- grid ops
+void launch_coeffs(int nx, int ny, double rho_g, double rho_l, double mu_g,
+                   double mu_l, const double *H, double *rho, double *mu,
+                   double *bx, double *by, cudaStream_t s);
+void launch_rhs(int nx, int ny, double h, double dt, const double *us,
+                const double *vs, const double *Fx, const double *Fy,
+                const double *bx, const double *by, double *b, cudaStream_t s);
+void launch_correct(int nx, int ny, double h, double dt, const double *us,
+                    const double *vs, const double *p, const double *Fx,
+                    const double *Fy, const double *bx, const double *by,
+                    double *u, double *v, cudaStream_t s);
+void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
+                      const double *mu, const double *u, const double *v,
+                      const double *au_prev, const double *av_prev,
+                      int have_prev, double gx, double gy, double *us,
+                      double *vs, double *au, double *av, cudaStream_t s);
+
+// ---------------------------------------------------------------- multigrid
+template <typename T>
+struct LevelT {
+    T *e = nullptr, *r = nullptr, *bx = nullptr, *by = nullptr, *invd = nullptr;
+};
+
+struct Level {
+    int nx = 0, ny = 0;
+    double h = 0;
+    LevelT<double> d;
+    LevelT<float> f;
+};
+
+struct MG {
+    std::vector<Level> lv;
+    int tail = 0;                 // first level handled by the single-CTA tail kernel
+    double *lu = nullptr;         // coarsest dense LU (n x n), FP64
+    int *piv = nullptr;           // coarsest row permutation
+    double *red = nullptr;        // reduction partials + results (device)
+    unsigned *red_count = nullptr;
+    double *red_host = nullptr;   // pinned mirror of the results
+    int red_blocks = 0;
+    void *mem = nullptr;          // one allocation for all of the above
+    size_t bytes = 0;
+};
+
+bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys);
+cudaError_t mg_alloc(MG &mg, int nx, int ny, double h);
+void mg_free(MG &mg);
+// Copy level-0 coefficients (walls forced to 0) and build the hierarchy.
+void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s);
+// Runs the solve on level-0 arrays of the hierarchy; p is read/written in place.
+ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
+                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                 cudaStream_t s, std::string &err);
+
+void launch_rbgs(int nx, int ny, double h, const double *bx, const double *by,
+                 const double *invd, const double *b, double *p, cudaStream_t s);
+void launch_invdiag(int nx, int ny, const double *bx, const double *by,
+                    double *invd, cudaStream_t s);
+void launch_restrict_residual(int nx, int ny, double h, const double *bx,
+                              const double *by, const double *b, const double *p,
+                              double *rc, double *ec, cudaStream_t s);
+void launch_prolong_add(int nxc, int nyc, const double *ec, double *ef,
+                        cudaStream_t s);
+void launch_coarsen_beta(int nx, int ny, const double *bx, const double *by,
+                         double *bxc, double *byc, cudaStream_t s);
+void launch_residual(int nx, int ny, double h, const double *bx,
+                     const double *by, const double *b, const double *p,
+                     double *r, cudaStream_t s);
+
+// ---------------------------------------------------------------- markers
+struct Markers {
+    int M = 0, ndrops = 0, nx = 0, ny = 0, bnx = 0, bny = 0;
+    double h = 0, x0 = 0, y0 = 0;
+    double *X = nullptr, *Y = nullptr, *kappa = nullptr, *nxm = nullptr,
+           *nym = nullptr, *ds = nullptr, *fmag = nullptr, *U = nullptr,
+           *V = nullptr, *Xn = nullptr, *Yn = nullptr;
+    int32_t *drop_start = nullptr, *drop_of = nullptr;
+    uint32_t *key = nullptr, *tmp_ids = nullptr, *ids = nullptr,
+             *cell_count = nullptr, *cell_start = nullptr, *scan_part = nullptr,
+             *bcount = nullptr, *bactive = nullptr, *flags = nullptr;
+    std::vector<int32_t> drop_start_h;
+    int max_drop = 0;
+    void *mem = nullptr;
+};
+
+cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny,
+                          double h, double x0, double y0,
+                          const int32_t *drop_start_host);
+void markers_free(Markers &mk);
+// flags[0]: bad marker (outside / too near a wall); flags[1]: candidate or
+// crossing list overflow; flags[2]: B-spline system not positive definite.
+void launch_validate(Markers &mk, cudaStream_t s);
+void launch_geometry(Markers &mk, double sigma, cudaStream_t s);
+void launch_sort(Markers &mk, cudaStream_t s);
+void launch_interp(const Markers &mk, int kernel, const double *u,
+                   const double *v, double *U, double *V, double dt_move,
+                   cudaStream_t s);
+void launch_spread_conv(const Markers &mk, int kernel, const double *fmag,
+                        double *Fx, double *Fy, cudaStream_t s);
+void launch_heaviside(const Markers &mk, double *H, cudaStream_t s);
+void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
+                         double *Fx, double *Fy, cudaStream_t s);
+void launch_relocate(Markers &mk, cudaStream_t s);
+
+}  // namespace ibk

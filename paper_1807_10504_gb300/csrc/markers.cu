@@ -1,0 +1,942 @@
+// Lagrangian marker kernels of the method (Sections 2.2, 3 and 4):
+//   binning + deterministic (key, id) order, velocity interpolation
+//   (Eq. (jump_condu)), conventional spreading (Eq. (delta_vec)) as a gather
+//   over markers sorted by cell, the polygon discrete Heaviside and the
+//   irrotational face force (Eqs. (delta_hea), (delta_hea_xy)), discrete
+//   curvature (Eq. (ten_f)) and least-squares B-spline relocation
+//   (Eqs. (bspline), (bcurve), (bspline_ls)).
+//
+// This translation unit is compiled without multiply-add contraction so that
+// integer decisions taken from floating point (cell keys, inside/outside
+// crossings, nearest segment) follow the same IEEE operations as a plain
+// reading of the definitions.  No floating-point atomics: every sum has a
+// fixed order.  All marker work is O(markers x stencil) and small next to the
+// pressure solve; the band kernels touch only 8x8-cell blocks that have a
+// marker within kSearch cells.
+#include <math.h>
+
+#include "ib_internal.cuh"
+
+namespace ibk {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double phi(int kernel, double r)
+{
+    double a = fabs(r);
+    if (a >= 2.0) return 0.0;
+    if (kernel == 0) return 0.25 * (1.0 + cospi(0.5 * r));
+    if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+}
+
+__device__ __forceinline__ void nbrs(int m, const int32_t *drop_of,
+                                     const int32_t *drop_start, int *pm, int *nm)
+{
+    int d = drop_of[m], s = drop_start[d], e = drop_start[d + 1];
+    *pm = (m == s) ? e - 1 : m - 1;
+    *nm = (m == e - 1) ? s : m + 1;
+}
+
+// ------------------------------------------------------------ validation
+__global__ void k_validate(int M, const double *__restrict__ X, const double *__restrict__ Y,
+                           double xlo, double xhi, double ylo, double yhi,
+                           uint32_t *__restrict__ flags)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double x = X[m], y = Y[m];
+    if (!(x >= xlo && x <= xhi && y >= ylo && y <= yhi)) atomicOr(&flags[0], 1u);
+}
+
+// ------------------------------------------------------------ geometry
+__global__ void k_geometry(int M, const double *__restrict__ X, const double *__restrict__ Y,
+                           const int32_t *__restrict__ drop_of,
+                           const int32_t *__restrict__ drop_start, double sigma,
+                           double *__restrict__ kappa, double *__restrict__ nxm,
+                           double *__restrict__ nym, double *__restrict__ ds,
+                           double *__restrict__ fmag)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int pm, nm;
+    nbrs(m, drop_of, drop_start, &pm, &nm);
+    double ax = X[m] - X[pm], ay = Y[m] - Y[pm];
+    double bx = X[nm] - X[m], by = Y[nm] - Y[m];
+    double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
+    double tax = ax / la, tay = ay / la, tbx = bx / lb, tby = by / lb;
+    double dsm = 0.5 * (la + lb);
+    double dx = tbx - tax, dy = tby - tay;
+    double cr = tax * tby - tay * tbx;
+    double k = sqrt(dx * dx + dy * dy) / dsm;
+    k = cr >= 0.0 ? k : -k;
+    double nx_ = -tay - tby, ny_ = tax + tbx;
+    double ln = sqrt(nx_ * nx_ + ny_ * ny_);
+    kappa[m] = k;
+    nxm[m] = nx_ / ln;
+    nym[m] = ny_ / ln;
+    ds[m] = dsm;
+    fmag[m] = sigma * k;
+}
+
+// ------------------------------------------------------------ binning
+__global__ void k_keys(int M, const double *__restrict__ X, const double *__restrict__ Y,
+                       double x0, double y0, double h, int nx, int ny, int bnx,
+                       uint32_t *__restrict__ key, uint32_t *__restrict__ count,
+                       uint32_t *__restrict__ bcount)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int kx = (int)floor((X[m] - x0) / h), ky = (int)floor((Y[m] - y0) / h);
+    kx = min(max(kx, 0), nx - 1);
+    ky = min(max(ky, 0), ny - 1);
+    uint32_t k = (uint32_t)ky * (uint32_t)nx + (uint32_t)kx;
+    key[m] = k;
+    atomicAdd(&count[k], 1u);
+    atomicAdd(&bcount[(ky / kBlk) * bnx + kx / kBlk], 1u);
+}
+
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kT * kScanItems;
+
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t sh[kT];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kT; o <<= 1) {
+        uint32_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t incl = sh[threadIdx.x];
+    if (total) *total = sh[kT - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+__global__ void k_scan_partial(long n, const uint32_t *__restrict__ a, uint32_t *__restrict__ part)
+{
+    long base = (long)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        long q = base + (long)threadIdx.x * kScanItems + k;
+        if (q < n) s += a[q];
+    }
+    uint32_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_parts(int nparts, uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nparts; base += kT) {
+        int q = base + threadIdx.x;
+        uint32_t v = q < nparts ? part[q] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_excl_scan(v, &tot);
+        if (q < nparts) part[q] = ex + carry;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_final(long n, const uint32_t *__restrict__ a,
+                             const uint32_t *__restrict__ part, uint32_t *__restrict__ out,
+                             uint32_t total_M)
+{
+    long base = (long)blockIdx.x * kScanChunk + (long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        long q = base + k;
+        v[k] = q < n ? a[q] : 0u;
+        s += v[k];
+    }
+    uint32_t ex = block_excl_scan(s, nullptr) + part[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        long q = base + k;
+        if (q < n) out[q] = ex;
+        ex += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = total_M;
+}
+
+__global__ void k_place(int M, const uint32_t *__restrict__ key,
+                        const uint32_t *__restrict__ cell_start, uint32_t *__restrict__ count,
+                        uint32_t *__restrict__ tmp_ids)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    uint32_t k = key[m];
+    uint32_t slot = cell_start[k] + atomicSub(&count[k], 1u) - 1u;
+    tmp_ids[slot] = (uint32_t)m;
+}
+
+// Deterministic rank inside the cell: ids ascending.
+__global__ void k_rerank(int M, const uint32_t *__restrict__ key,
+                         const uint32_t *__restrict__ cell_start,
+                         const uint32_t *__restrict__ tmp_ids, uint32_t *__restrict__ ids)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    uint32_t k = key[m], s = cell_start[k], e = cell_start[k + 1], r = 0;
+    for (uint32_t t = s; t < e; t++) r += tmp_ids[t] < (uint32_t)m ? 1u : 0u;
+    ids[s + r] = (uint32_t)m;
+}
+
+__global__ void k_block_active(int bnx, int bny, const uint32_t *__restrict__ bcount,
+                               uint32_t *__restrict__ active)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= bnx * bny) return;
+    int bi = b % bnx, bj = b / bnx;
+    uint32_t any = 0;
+    for (int dj = -1; dj <= 1; dj++)
+        for (int di = -1; di <= 1; di++) {
+            int ii = bi + di, jj = bj + dj;
+            if (ii >= 0 && ii < bnx && jj >= 0 && jj < bny) any |= bcount[jj * bnx + ii];
+        }
+    active[b] = any ? 1u : 0u;
+}
+
+// ------------------------------------------------------------ interpolation
+__global__ void k_interp(int M, int kernel, int nx, int ny, double h, double x0, double y0,
+                         const double *__restrict__ u, const double *__restrict__ v,
+                         double *__restrict__ X, double *__restrict__ Y,
+                         double *__restrict__ U, double *__restrict__ V, double dt_move)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double Xm = X[m], Ym = Y[m];
+    double sx = (Xm - x0) / h, sy = (Ym - y0) / h - 0.5;
+    int i0 = (int)floor(sx) - 1, j0 = (int)floor(sy) - 1;
+    double acc = 0.0;
+    for (int b = 0; b < 4; b++)
+        for (int a = 0; a < 4; a++) {
+            int i = i0 + a, j = j0 + b;
+            if (i < 0 || i > nx || j < 0 || j > ny - 1) continue;
+            acc += u[(long)j * (nx + 1) + i] * (phi(kernel, (double)i - sx) * phi(kernel, (double)j - sy));
+        }
+    double Um = acc;
+    sx = (Xm - x0) / h - 0.5;
+    sy = (Ym - y0) / h;
+    i0 = (int)floor(sx) - 1;
+    j0 = (int)floor(sy) - 1;
+    acc = 0.0;
+    for (int b = 0; b < 4; b++)
+        for (int a = 0; a < 4; a++) {
+            int i = i0 + a, j = j0 + b;
+            if (i < 0 || i > nx - 1 || j < 0 || j > ny) continue;
+            acc += v[(long)j * nx + i] * (phi(kernel, (double)i - sx) * phi(kernel, (double)j - sy));
+        }
+    double Vm = acc;
+    if (U) U[m] = Um;
+    if (V) V[m] = Vm;
+    if (dt_move != 0.0) {
+        X[m] = Xm + dt_move * Um;
+        Y[m] = Ym + dt_move * Vm;
+    }
+}
+
+// ------------------------------------------------------------ conventional spread
+// One thread per face; markers of the 4 x 5 (x-faces) or 5 x 4 (y-faces)
+// cells that can reach the face, visited row by row in (cell, id) order.
+__global__ void k_spread_conv(int kernel, int nx, int ny, double h, double x0, double y0,
+                              int bnx, const uint32_t *__restrict__ bactive,
+                              const uint32_t *__restrict__ cell_start,
+                              const uint32_t *__restrict__ ids, const double *__restrict__ X,
+                              const double *__restrict__ Y, const double *__restrict__ fmag,
+                              const double *__restrict__ nxm, const double *__restrict__ nym,
+                              const double *__restrict__ ds, double *__restrict__ Fx,
+                              double *__restrict__ Fy)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nxf = (long)(nx + 1) * ny;
+    const double ih2 = 1.0 / (h * h);
+    bool isx = k < nxf;
+    int i, j;
+    if (isx) {
+        j = (int)(k / (nx + 1));
+        i = (int)(k - (long)j * (nx + 1));
+        if (i == 0 || i == nx) return;
+    } else {
+        k -= nxf;
+        if (k >= (long)nx * (ny + 1)) return;
+        j = (int)(k / nx);
+        i = (int)(k - (long)j * nx);
+        if (j == 0 || j == ny) return;
+    }
+    int ci = min(i, nx - 1), cj = min(j, ny - 1);
+    if (!bactive[(cj / kBlk) * bnx + ci / kBlk]) return;
+    int ia = isx ? i - 2 : i - 2, ib = isx ? i + 1 : i + 2;
+    int ja = isx ? j - 2 : j - 2, jb = isx ? j + 2 : j + 1;
+    ia = max(ia, 0); ib = min(ib, nx - 1); ja = max(ja, 0); jb = min(jb, ny - 1);
+    double acc = 0.0;
+    for (int jj = ja; jj <= jb; jj++) {
+        uint32_t s = cell_start[(long)jj * nx + ia], e = cell_start[(long)jj * nx + ib + 1];
+        for (uint32_t t = s; t < e; t++) {
+            int m = (int)ids[t];
+            double sx, sy, c;
+            if (isx) {
+                sx = (X[m] - x0) / h; sy = (Y[m] - y0) / h - 0.5;
+                c = fmag[m] * nxm[m] * ds[m] * ih2;
+            } else {
+                sx = (X[m] - x0) / h - 0.5; sy = (Y[m] - y0) / h;
+                c = fmag[m] * nym[m] * ds[m] * ih2;
+            }
+            double rx = (double)i - sx, ry = (double)j - sy;
+            if (fabs(rx) >= 2.0 || fabs(ry) >= 2.0) continue;
+            acc += c * (phi(kernel, rx) * phi(kernel, ry));
+        }
+    }
+    if (isx) Fx[k] = acc; else Fy[k] = acc;
+}
+
+// ------------------------------------------------------------ inside / outside
+// One CTA per row: crossings of the row's centre line with every segment,
+// sorted, then a crossing count per cell centre.  Writes H = chi.
+__global__ void __launch_bounds__(kT)
+k_rows_inside(int M, int nx, double h, double x0, double y0, const double *__restrict__ X,
+              const double *__restrict__ Y, const int32_t *__restrict__ drop_of,
+              const int32_t *__restrict__ drop_start, double *__restrict__ H,
+              uint32_t *__restrict__ flags)
+{
+    __shared__ double xs[kMaxCross], srt[kMaxCross];
+    __shared__ int nc;
+    const int j = blockIdx.x;
+    const double py = y0 + ((double)j + 0.5) * h;
+    if (threadIdx.x == 0) nc = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += kT) {
+        int pm, nm;
+        nbrs(m, drop_of, drop_start, &pm, &nm);
+        double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
+        if ((ay > py) != (by > py)) {
+            double xc = ax + (py - ay) * (bx - ax) / (by - ay);
+            int q = atomicAdd(&nc, 1);
+            if (q < kMaxCross) xs[q] = xc;
+        }
+    }
+    __syncthreads();
+    int n = nc;
+    if (n > kMaxCross) {
+        if (threadIdx.x == 0) atomicOr(&flags[1], 1u);
+        n = kMaxCross;
+    }
+    for (int q = threadIdx.x; q < n; q += kT) {
+        double v = xs[q];
+        int r = 0;
+        for (int t = 0; t < n; t++) r += (xs[t] < v || (xs[t] == v && t < q)) ? 1 : 0;
+        srt[r] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx; i += kT) {
+        double px = x0 + ((double)i + 0.5) * h;
+        int lo = 0, hi = n;  // first index with srt > px
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (srt[mid] > px) hi = mid; else lo = mid + 1;
+        }
+        H[(long)j * nx + i] = (double)((n - lo) & 1);
+    }
+}
+
+// ------------------------------------------------------------ band candidates
+// Segments (start-marker ids) whose start marker lies within kSearch cells of
+// an 8x8 block, gathered row by row and sorted ascending.
+__device__ int gather_candidates(int bi, int bj, int nx, int ny,
+                                 const uint32_t *__restrict__ cell_start,
+                                 const uint32_t *__restrict__ ids, uint32_t *cand,
+                                 uint32_t *tmp, uint32_t *flags)
+{
+    __shared__ uint32_t rowoff[kBlk + 2 * kSearch + 1];
+    __shared__ int total;
+    const int ia = max(bi * kBlk - kSearch, 0), ib = min(bi * kBlk + kBlk - 1 + kSearch, nx - 1);
+    const int ja = max(bj * kBlk - kSearch, 0), jb = min(bj * kBlk + kBlk - 1 + kSearch, ny - 1);
+    const int nrows = jb - ja + 1;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int r = 0; r < nrows; r++) {
+            rowoff[r] = acc;
+            long base = (long)(ja + r) * nx;
+            acc += cell_start[base + ib + 1] - cell_start[base + ia];
+        }
+        rowoff[nrows] = acc;
+        total = (int)acc;
+    }
+    __syncthreads();
+    int n = total;
+    if (n > kMaxCand) {
+        if (threadIdx.x == 0) atomicOr(&flags[1], 1u);
+        n = kMaxCand;
+    }
+    for (int r = 0; r < nrows; r++) {
+        long base = (long)(ja + r) * nx;
+        uint32_t s = cell_start[base + ia], cnt = rowoff[r + 1] - rowoff[r];
+        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            uint32_t q = rowoff[r] + t;
+            if ((int)q < n) tmp[q] = ids[s + t];
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        uint32_t v = tmp[q];
+        int r = 0;
+        for (int t = 0; t < n; t++) r += tmp[t] < v ? 1 : 0;
+        cand[r] = v;
+    }
+    __syncthreads();
+    return n;
+}
+
+// Area of the part of a polygon inside the unit square (Sutherland-Hodgman
+// against x >= 0, x <= 1, y >= 0, y <= 1, then the shoelace formula).
+__device__ double clip_area_unit(const double *px, const double *py)
+{
+    double ax[12], ay[12], bx[12], by[12];
+    int na = 4;
+    for (int k = 0; k < 4; k++) { ax[k] = px[k]; ay[k] = py[k]; }
+    for (int side = 0; side < 4; side++) {
+        int nb = 0;
+        for (int k = 0; k < na; k++) {
+            int k1 = (k + 1 == na) ? 0 : k + 1;
+            double sx = ax[k], sy = ay[k], ex = ax[k1], ey = ay[k1];
+            double ds_, de;
+            if (side == 0) { ds_ = sx; de = ex; }
+            else if (side == 1) { ds_ = 1.0 - sx; de = 1.0 - ex; }
+            else if (side == 2) { ds_ = sy; de = ey; }
+            else { ds_ = 1.0 - sy; de = 1.0 - ey; }
+            bool sin_ = ds_ >= 0.0, ein = de >= 0.0;
+            if (sin_ && ein) { bx[nb] = ex; by[nb] = ey; nb++; }
+            else if (sin_ && !ein) {
+                double t = ds_ / (ds_ - de);
+                bx[nb] = sx + t * (ex - sx); by[nb] = sy + t * (ey - sy); nb++;
+            } else if (!sin_ && ein) {
+                double t = ds_ / (ds_ - de);
+                bx[nb] = sx + t * (ex - sx); by[nb] = sy + t * (ey - sy); nb++;
+                bx[nb] = ex; by[nb] = ey; nb++;
+            }
+        }
+        na = nb;
+        for (int k = 0; k < na; k++) { ax[k] = bx[k]; ay[k] = by[k]; }
+        if (na == 0) return 0.0;
+    }
+    double a = 0.0;
+    for (int k = 0; k < na; k++) {
+        int k1 = (k + 1 == na) ? 0 : k + 1;
+        a += ax[k] * ay[k1] - ax[k1] * ay[k];
+    }
+    return 0.5 * a;
+}
+
+__device__ __forceinline__ double strip_value(int k)
+{
+    // integral of the cosine kernel from -2 to the strip centre r = k - 2
+    double r = (double)k - 2.0;
+    if (r <= -2.0) return 0.0;
+    if (r >= 2.0) return 1.0;
+    return 0.5 + r / 4.0 + sin(M_PI * r / 2.0) / (2.0 * M_PI);
+}
+
+constexpr int kBT = kBlk * kBlk;  // one thread per cell of the block
+
+__global__ void __launch_bounds__(kBT)
+k_band_heaviside(int nx, int ny, double h, double x0, double y0, int bnx,
+                 const uint32_t *__restrict__ bactive, const uint32_t *__restrict__ cell_start,
+                 const uint32_t *__restrict__ ids, const double *__restrict__ X,
+                 const double *__restrict__ Y, const double *__restrict__ nxm,
+                 const double *__restrict__ nym, const int32_t *__restrict__ drop_of,
+                 const int32_t *__restrict__ drop_start, double *__restrict__ H,
+                 uint32_t *__restrict__ flags)
+{
+    __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (!bactive[bj * bnx + bi]) return;
+    const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
+    const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
+    if (i >= nx || j >= ny) return;
+    double Hk[5];
+    for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
+    double acc = 0.0, cov = 0.0;
+    for (int q = 0; q < n; q++) {
+        int m = (int)cand[q], pm, nm;
+        nbrs(m, drop_of, drop_start, &pm, &nm);
+        double gxa = (X[m] - x0) / h, gya = (Y[m] - y0) / h;
+        double gxb = (X[nm] - x0) / h, gyb = (Y[nm] - y0) / h;
+        double na_x = nxm[m], na_y = nym[m], nb_x = nxm[nm], nb_y = nym[nm];
+        // whole slab bounding box (offsets -2.5 .. 2.5) against the cell
+        double sx0 = fmin(fmin(gxa - 2.5 * fabs(na_x), gxb - 2.5 * fabs(nb_x)), 1e300);
+        double sx1 = fmax(gxa + 2.5 * fabs(na_x), gxb + 2.5 * fabs(nb_x));
+        double sy0 = fmin(gya - 2.5 * fabs(na_y), gyb - 2.5 * fabs(nb_y));
+        double sy1 = fmax(gya + 2.5 * fabs(na_y), gyb + 2.5 * fabs(nb_y));
+        if (sx1 < (double)i || sx0 > (double)(i + 1) || sy1 < (double)j || sy0 > (double)(j + 1))
+            continue;
+        for (int k = 0; k < 5; k++) {
+            double a = (double)k - 2.5, b = (double)k - 1.5;
+            double qx[4], qy[4];
+            qx[0] = gxa + a * na_x; qy[0] = gya + a * na_y;
+            qx[1] = gxb + a * nb_x; qy[1] = gyb + a * nb_y;
+            qx[2] = gxb + b * nb_x; qy[2] = gyb + b * nb_y;
+            qx[3] = gxa + b * na_x; qy[3] = gya + b * na_y;
+            for (int t = 0; t < 4; t++) { qx[t] -= (double)i; qy[t] -= (double)j; }
+            double mnx = fmin(fmin(qx[0], qx[1]), fmin(qx[2], qx[3]));
+            double mxx = fmax(fmax(qx[0], qx[1]), fmax(qx[2], qx[3]));
+            double mny = fmin(fmin(qy[0], qy[1]), fmin(qy[2], qy[3]));
+            double mxy = fmax(fmax(qy[0], qy[1]), fmax(qy[2], qy[3]));
+            if (mxx < 0.0 || mnx > 1.0 || mxy < 0.0 || mny > 1.0) continue;
+            double A = clip_area_unit(qx, qy);
+            acc += A * Hk[k];
+            cov += A;
+        }
+    }
+    long c = (long)j * nx + i;
+    double unc = 1.0 - cov;
+    if (unc < 0.0) unc = 0.0;
+    H[c] = acc + unc * H[c];
+}
+
+// Irrotational face force F = f_face (H_ij - H_nb) / h on the x-face left of
+// and the y-face below every cell of an active block; f_face from the nearest
+// segment (closest point clamped to the segment, ties to the lower id),
+// linear in the segment parameter between its two markers.
+__global__ void __launch_bounds__(kBT)
+k_spread_irrot(int nx, int ny, double h, double x0, double y0, int bnx,
+               const uint32_t *__restrict__ bactive, const uint32_t *__restrict__ cell_start,
+               const uint32_t *__restrict__ ids, const double *__restrict__ X,
+               const double *__restrict__ Y, const double *__restrict__ fmag,
+               const int32_t *__restrict__ drop_of, const int32_t *__restrict__ drop_start,
+               const double *__restrict__ H, double *__restrict__ Fx, double *__restrict__ Fy,
+               uint32_t *__restrict__ flags)
+{
+    __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (!bactive[bj * bnx + bi]) return;
+    const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
+    const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
+    if (i >= nx || j >= ny) return;
+    for (int dir = 0; dir < 2; dir++) {
+        double dH;
+        double qx, qy;
+        if (dir == 0) {
+            if (i == 0) continue;
+            dH = H[(long)j * nx + i] - H[(long)j * nx + i - 1];
+            qx = (double)i; qy = (double)j + 0.5;
+        } else {
+            if (j == 0) continue;
+            dH = H[(long)j * nx + i] - H[(long)(j - 1) * nx + i];
+            qx = (double)i + 0.5; qy = (double)j;
+        }
+        double F = 0.0;
+        if (dH != 0.0) {
+            double best = INFINITY, fb = 0.0;
+            for (int q = 0; q < n; q++) {
+                int m = (int)cand[q], pm, nm;
+                nbrs(m, drop_of, drop_start, &pm, &nm);
+                double ax = (X[m] - x0) / h, ay = (Y[m] - y0) / h;
+                double bx = (X[nm] - x0) / h, by = (Y[nm] - y0) / h;
+                double ex = bx - ax, ey = by - ay;
+                double t = ((qx - ax) * ex + (qy - ay) * ey) / (ex * ex + ey * ey);
+                if (t < 0.0) t = 0.0;
+                if (t > 1.0) t = 1.0;
+                double dx = ax + t * ex - qx, dy = ay + t * ey - qy;
+                double d2 = dx * dx + dy * dy;
+                if (d2 < best) { best = d2; fb = (1.0 - t) * fmag[m] + t * fmag[nm]; }
+            }
+            F = fb * dH / h;
+        }
+        if (dir == 0) Fx[(long)j * (nx + 1) + i] = F;
+        else Fy[(long)j * nx + i] = F;
+    }
+}
+
+// ------------------------------------------------------------ B-spline
+// One CTA per drop.  Same steps as the definition: chord-length parameters,
+// g = round(L / 1.5h) spans (4 <= g <= n), periodic cubic basis by the
+// Cox-de Boor recursion, normal equations accumulated in ascending marker
+// order, Cholesky in the matrix's envelope (band of 3 plus the last three
+// rows, which is where the cyclic wrap fills in), arc length by 8-point
+// Gauss-Legendre per span, 12 Newton steps per new marker.
+__device__ void bspl_basis(double s, double tau, int g, int *idx, double *w, double *dw)
+{
+    int q = (int)floor(s / tau);
+    if (q > g - 1) q = g - 1;
+    if (q < 0) q = 0;
+    double N[4][4];
+    N[0][0] = 1.0;
+    for (int d = 1; d <= 3; d++)
+        for (int r = 0; r <= d; r++) {
+            int k = q - d + r;
+            double tk = k * tau, tkd = (k + d) * tau, tk1 = (k + 1) * tau, tkd1 = (k + d + 1) * tau;
+            double left = (r >= 1) ? (s - tk) / (tkd - tk) * N[d - 1][r - 1] : 0.0;
+            double right = (r <= d - 1) ? (tkd1 - s) / (tkd1 - tk1) * N[d - 1][r] : 0.0;
+            N[d][r] = left + right;
+        }
+    for (int r = 0; r <= 3; r++) {
+        int k = q - 3 + r;
+        idx[r] = ((k % g) + g) % g;
+        w[r] = N[3][r];
+        double a = (r >= 1) ? N[2][r - 1] : 0.0;
+        double b = (r <= 2) ? N[2][r] : 0.0;
+        dw[r] = 3.0 / (3.0 * tau) * a - 3.0 / (3.0 * tau) * b;
+    }
+}
+
+__constant__ double cGLX[8] = {-0.9602898564975363, -0.7966664774136267,
+                               -0.5255324099163290, -0.1834346424956498,
+                               0.1834346424956498,  0.5255324099163290,
+                               0.7966664774136267,  0.9602898564975363};
+__constant__ double cGLW[8] = {0.1012285362903763, 0.2223810344533745,
+                               0.3137066458778873, 0.3626837833783620,
+                               0.3626837833783620, 0.3137066458778873,
+                               0.2223810344533745, 0.1012285362903763};
+
+__device__ double bspl_speed(double s, double tau, int g, const double *cx, const double *cy)
+{
+    int idx[4];
+    double w[4], dw[4], dx = 0.0, dy = 0.0;
+    bspl_basis(s, tau, g, idx, w, dw);
+    for (int r = 0; r < 4; r++) { dx += cx[idx[r]] * dw[r]; dy += cy[idx[r]] * dw[r]; }
+    return sqrt(dx * dx + dy * dy);
+}
+
+__device__ double gl_len(double a, double b, double tau, int g, const double *cx, const double *cy)
+{
+    double mid = 0.5 * (a + b), half = 0.5 * (b - a), s = 0.0;
+    for (int k = 0; k < 8; k++) s += cGLW[k] * bspl_speed(mid + half * cGLX[k], tau, g, cx, cy);
+    return s * half;
+}
+
+struct Env {
+    // L (lower Cholesky factor) in its envelope: band rows r in [3, g-3) keep
+    // columns r-3..r, the other rows are dense.
+    int g;
+    double *band, *dense;
+    __device__ bool is_band(int r) const { return r >= 3 && r < g - 3; }
+    __device__ int dense_row(int r) const { return r < 3 ? r : 3 + (r - (g - 3)); }
+    __device__ int first(int r) const { return is_band(r) ? r - 3 : 0; }
+    __device__ double get(int r, int c) const {
+        if (is_band(r)) return (c >= r - 3 && c <= r) ? band[r * 4 + (c - r + 3)] : 0.0;
+        return dense[(long)dense_row(r) * g + c];
+    }
+    __device__ void set(int r, int c, double v) {
+        if (is_band(r)) band[r * 4 + (c - r + 3)] = v;
+        else dense[(long)dense_row(r) * g + c] = v;
+    }
+};
+
+// G[r][c] of the cyclic band matrix stored as Gc[i*4 + d] = G[i][(i+d) mod g].
+__device__ double gval(const double *Gc, int g, int r, int c)
+{
+    int d1 = ((c - r) % g + g) % g, d2 = ((r - c) % g + g) % g;
+    if (d1 <= 3) return Gc[r * 4 + d1];
+    if (d2 <= 3) return Gc[c * 4 + d2];
+    return 0.0;
+}
+
+__device__ int env_solve(Env &L, const double *Gc, int g, double *b)
+{
+    // factorisation (sequential, ascending sums as in a dense Cholesky)
+    for (int c = 0; c < g; c++) {
+        double s = gval(Gc, g, c, c);
+        for (int k = L.first(c); k < c; k++) { double v = L.get(c, k); s -= v * v; }
+        if (!(s > 0.0)) return -1;
+        double d = sqrt(s);
+        L.set(c, c, d);
+        for (int r = c + 1; r < g; r++) {
+            if (L.is_band(r) && r - 3 > c) continue;  // outside the envelope
+            double t = gval(Gc, g, r, c);
+            for (int k = max(L.first(r), L.first(c)); k < c; k++) t -= L.get(r, k) * L.get(c, k);
+            L.set(r, c, t / d);
+        }
+    }
+    for (int r = 0; r < g; r++) {
+        double s = b[r];
+        for (int k = L.first(r); k < r; k++) s -= L.get(r, k) * b[k];
+        b[r] = s / L.get(r, r);
+    }
+    for (int r = g - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int k = r + 1; k < g; k++) {
+            if (L.is_band(k) && k - 3 > r) continue;
+            s -= L.get(k, r) * b[k];
+        }
+        b[r] = s / L.get(r, r);
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(kT)
+k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
+           const int32_t *__restrict__ drop_start, double h, int maxn,
+           double *__restrict__ Xo, double *__restrict__ Yo, uint32_t *__restrict__ flags)
+{
+    extern __shared__ double sm[];
+    const int d = blockIdx.x, s0 = drop_start[d], n = drop_start[d + 1] - s0;
+    // shared layout: sp[n+1], qs[maxg+1] (as double), Gc[4g], cx[g], cy[g],
+    // band[4g], dense[6g], cum[g+1]
+    const int maxg = maxn;
+    double *sp = sm;
+    int *qs = (int *)(sp + maxn + 1);
+    double *Gc = (double *)(qs + 2 * (maxg + 1));
+    double *cx = Gc + 4 * maxg, *cy = cx + maxg, *band = cy + maxg, *dense = band + 4 * maxg;
+    double *cum = dense + 6 * maxg;
+    __shared__ int g_s, bad;
+    __shared__ double tau_s;
+    if (threadIdx.x == 0) {
+        double L = 0.0;
+        for (int m = 0; m < n; m++) {
+            int a = s0 + m, b = s0 + (m + 1) % n;
+            sp[m] = L;
+            double dx = X[b] - X[a], dy = Y[b] - Y[a];
+            L += sqrt(dx * dx + dy * dy);
+        }
+        int g = (int)floor(L / (1.5 * h) + 0.5);
+        if (g < 4) g = 4;
+        if (g > n) g = n;
+        g_s = g;
+        tau_s = L / g;
+        bad = 0;
+        // first marker of every span (parameters ascend with m)
+        int q = 0;
+        for (int k = 0; k <= g; k++) qs[k] = n;
+        for (int m = 0; m < n; m++) {
+            int qq = (int)floor(sp[m] / tau_s);
+            if (qq > g - 1) qq = g - 1;
+            while (q <= qq) { qs[q] = m; q++; }
+        }
+        while (q <= g) { qs[q] = n; q++; }
+    }
+    __syncthreads();
+    const int g = g_s;
+    const double tau = tau_s;
+    // normal equations: entry (i, i+d) and rhs i, markers of spans i..i+3 in
+    // ascending marker order
+    for (int e = threadIdx.x; e < 5 * g; e += kT) {
+        int i = e / 5, dd = e % 5;  // dd 0..3: G[i][(i+dd)%g]; dd 4: rhs row i
+        int sp4[4];
+        for (int t = 0; t < 4; t++) sp4[t] = (i + t) % g;
+        for (int a = 1; a < 4; a++)
+            for (int b = a; b > 0 && sp4[b] < sp4[b - 1]; b--) { int tt = sp4[b]; sp4[b] = sp4[b - 1]; sp4[b - 1] = tt; }
+        int jcol = (i + (dd < 4 ? dd : 0)) % g;
+        double acc = 0.0, accy = 0.0;
+        for (int t = 0; t < 4; t++) {
+            if (t > 0 && sp4[t] == sp4[t - 1]) continue;
+            for (int m = qs[sp4[t]]; m < qs[sp4[t] + 1]; m++) {
+                int idx[4];
+                double w[4], dw[4];
+                bspl_basis(sp[m], tau, g, idx, w, dw);
+                int a = -1, b = -1;
+                for (int r = 0; r < 4; r++) { if (idx[r] == i) a = r; if (idx[r] == jcol) b = r; }
+                if (a < 0) continue;
+                if (dd < 4) { if (b >= 0) acc += w[a] * w[b]; }
+                else { acc += w[a] * X[s0 + m]; accy += w[a] * Y[s0 + m]; }
+            }
+        }
+        if (dd < 4) Gc[i * 4 + dd] = acc;
+        else { cx[i] = acc; cy[i] = accy; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Env L{g, band, dense};
+        if (env_solve(L, Gc, g, cx) != 0 || env_solve(L, Gc, g, cy) != 0) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) atomicOr(&flags[2], 1u);
+        for (int m = threadIdx.x; m < n; m += kT) { Xo[s0 + m] = X[s0 + m]; Yo[s0 + m] = Y[s0 + m]; }
+        return;
+    }
+    for (int q = threadIdx.x; q < g; q += kT) cum[q + 1] = gl_len(q * tau, (q + 1) * tau, tau, g, cx, cy);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cum[0] = 0.0;
+        for (int q = 0; q < g; q++) cum[q + 1] = cum[q] + cum[q + 1];
+    }
+    __syncthreads();
+    const double Lp = cum[g];
+    for (int m = threadIdx.x; m < n; m += kT) {
+        double target = Lp * (double)m / (double)n;
+        int lo = 0, hi = g - 1;  // largest q <= g-1 with cum[q] <= target
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (cum[mid] <= target) lo = mid; else hi = mid - 1;
+        }
+        int q = lo;
+        double a = q * tau, b = (q + 1) * tau;
+        double seg = cum[q + 1] - cum[q];
+        double s = a + tau * (target - cum[q]) / seg;
+        for (int it = 0; it < 12; it++) {
+            double f = cum[q] + gl_len(a, s, tau, g, cx, cy) - target;
+            double sp_ = bspl_speed(s, tau, g, cx, cy);
+            s -= f / sp_;
+            if (s < a) s = a;
+            if (s > b) s = b;
+        }
+        int idx[4];
+        double w[4], dw[4], px = 0.0, py = 0.0;
+        bspl_basis(s, tau, g, idx, w, dw);
+        for (int r = 0; r < 4; r++) { px += cx[idx[r]] * w[r]; py += cy[idx[r]] * w[r]; }
+        Xo[s0 + m] = px;
+        Yo[s0 + m] = py;
+    }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- host
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double h,
+                          double x0, double y0, const int32_t *drop_start_host)
+{
+    mk.M = M; mk.ndrops = ndrops; mk.nx = nx; mk.ny = ny; mk.h = h; mk.x0 = x0; mk.y0 = y0;
+    mk.bnx = (nx + kBlk - 1) / kBlk;
+    mk.bny = (ny + kBlk - 1) / kBlk;
+    mk.drop_start_h.assign(drop_start_host, drop_start_host + ndrops + 1);
+    mk.max_drop = 0;
+    for (int d = 0; d < ndrops; d++)
+        mk.max_drop = std::max(mk.max_drop, drop_start_host[d + 1] - drop_start_host[d]);
+    size_t ncell = (size_t)nx * ny, nb = (size_t)mk.bnx * mk.bny;
+    size_t nparts = (ncell + kScanChunk - 1) / kScanChunk;
+    size_t bytes = al(M * 8) * 11 + al((ndrops + 1) * 4) + al(M * 4) * 4 + al(ncell * 4) +
+                   al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
+    cudaError_t e = cudaMalloc(&mk.mem, bytes);
+    if (e != cudaSuccess) { mk.mem = nullptr; return e; }
+    char *q = (char *)mk.mem;
+    auto take = [&](size_t b) { char *r = q; q += al(b); return (void *)r; };
+    mk.X = (double *)take(M * 8); mk.Y = (double *)take(M * 8);
+    mk.kappa = (double *)take(M * 8); mk.nxm = (double *)take(M * 8); mk.nym = (double *)take(M * 8);
+    mk.ds = (double *)take(M * 8); mk.fmag = (double *)take(M * 8);
+    mk.U = (double *)take(M * 8); mk.V = (double *)take(M * 8);
+    mk.Xn = (double *)take(M * 8); mk.Yn = (double *)take(M * 8);
+    mk.drop_start = (int32_t *)take((ndrops + 1) * 4);
+    mk.drop_of = (int32_t *)take(M * 4);
+    mk.key = (uint32_t *)take(M * 4); mk.tmp_ids = (uint32_t *)take(M * 4); mk.ids = (uint32_t *)take(M * 4);
+    mk.cell_count = (uint32_t *)take(ncell * 4);
+    mk.cell_start = (uint32_t *)take((ncell + 1) * 4);
+    mk.scan_part = (uint32_t *)take(nparts * 4);
+    mk.bcount = (uint32_t *)take(nb * 4); mk.bactive = (uint32_t *)take(nb * 4);
+    mk.flags = (uint32_t *)take(64);
+    std::vector<int32_t> dof(M);
+    for (int d = 0; d < ndrops; d++)
+        for (int m = drop_start_host[d]; m < drop_start_host[d + 1]; m++) dof[m] = d;
+    e = cudaMemset(mk.mem, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(mk.drop_start, drop_start_host, (ndrops + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && M > 0) e = cudaMemcpy(mk.drop_of, dof.data(), M * 4, cudaMemcpyHostToDevice);
+    return e;
+}
+
+void markers_free(Markers &mk)
+{
+    if (mk.mem) cudaFree(mk.mem);
+    mk.mem = nullptr;
+}
+
+void launch_validate(Markers &mk, cudaStream_t s)
+{
+    double m3 = 3.0 * mk.h;
+    note_launch();
+    k_validate<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.X, mk.Y, mk.x0 + m3, mk.x0 + mk.nx * mk.h - m3,
+                                            mk.y0 + m3, mk.y0 + mk.ny * mk.h - m3, mk.flags);
+}
+
+void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
+{
+    note_launch();
+    k_geometry<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.X, mk.Y, mk.drop_of, mk.drop_start, sigma,
+                                            mk.kappa, mk.nxm, mk.nym, mk.ds, mk.fmag);
+}
+
+void launch_sort(Markers &mk, cudaStream_t s)
+{
+    long ncell = (long)mk.nx * mk.ny;
+    cudaMemsetAsync(mk.cell_count, 0, ncell * 4, s);
+    cudaMemsetAsync(mk.bcount, 0, (size_t)mk.bnx * mk.bny * 4, s);
+    note_launch();
+    k_keys<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.X, mk.Y, mk.x0, mk.y0, mk.h, mk.nx, mk.ny,
+                                        mk.bnx, mk.key, mk.cell_count, mk.bcount);
+    int nparts = (int)cdiv(ncell, kScanChunk);
+    note_launch();
+    k_scan_partial<<<nparts, kT, 0, s>>>(ncell, mk.cell_count, mk.scan_part);
+    note_launch();
+    k_scan_parts<<<1, kT, 0, s>>>(nparts, mk.scan_part);
+    note_launch();
+    k_scan_final<<<nparts, kT, 0, s>>>(ncell, mk.cell_count, mk.scan_part, mk.cell_start,
+                                       (uint32_t)mk.M);
+    note_launch();
+    k_place<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.key, mk.cell_start, mk.cell_count, mk.tmp_ids);
+    note_launch();
+    k_rerank<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.key, mk.cell_start, mk.tmp_ids, mk.ids);
+    int nb = mk.bnx * mk.bny;
+    note_launch();
+    k_block_active<<<cdiv(nb, kT), kT, 0, s>>>(mk.bnx, mk.bny, mk.bcount, mk.bactive);
+}
+
+void launch_interp(const Markers &mk, int kernel, const double *u, const double *v,
+                   double *U, double *V, double dt_move, cudaStream_t s)
+{
+    note_launch();
+    k_interp<<<cdiv(mk.M, 128), 128, 0, s>>>(mk.M, kernel, mk.nx, mk.ny, mk.h, mk.x0, mk.y0, u, v,
+                                            mk.X, mk.Y, U, V, dt_move);
+}
+
+void launch_spread_conv(const Markers &mk, int kernel, const double *fmag, double *Fx,
+                        double *Fy, cudaStream_t s)
+{
+    long nf = (long)(mk.nx + 1) * mk.ny + (long)mk.nx * (mk.ny + 1);
+    cudaMemsetAsync(Fx, 0, (size_t)(mk.nx + 1) * mk.ny * 8, s);
+    cudaMemsetAsync(Fy, 0, (size_t)mk.nx * (mk.ny + 1) * 8, s);
+    note_launch();
+    k_spread_conv<<<cdiv(nf, kT), kT, 0, s>>>(kernel, mk.nx, mk.ny, mk.h, mk.x0, mk.y0, mk.bnx,
+                                             mk.bactive, mk.cell_start, mk.ids, mk.X, mk.Y,
+                                             fmag, mk.nxm, mk.nym, mk.ds, Fx, Fy);
+}
+
+void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
+{
+    note_launch();
+    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.M, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.drop_of,
+                                       mk.drop_start, H, mk.flags);
+    dim3 g(mk.bnx, mk.bny);
+    note_launch();
+    k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.x0, mk.y0, mk.bnx, mk.bactive,
+                                       mk.cell_start, mk.ids, mk.X, mk.Y, mk.nxm, mk.nym,
+                                       mk.drop_of, mk.drop_start, H, mk.flags);
+}
+
+void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H, double *Fx,
+                         double *Fy, cudaStream_t s)
+{
+    cudaMemsetAsync(Fx, 0, (size_t)(mk.nx + 1) * mk.ny * 8, s);
+    cudaMemsetAsync(Fy, 0, (size_t)mk.nx * (mk.ny + 1) * 8, s);
+    dim3 g(mk.bnx, mk.bny);
+    note_launch();
+    k_spread_irrot<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.x0, mk.y0, mk.bnx, mk.bactive,
+                                     mk.cell_start, mk.ids, mk.X, mk.Y, fmag, mk.drop_of,
+                                     mk.drop_start, H, Fx, Fy, mk.flags);
+}
+
+size_t relocate_smem(int maxn)
+{
+    return (size_t)(maxn + 1) * 8 + (size_t)2 * (maxn + 1) * 4 + (size_t)4 * maxn * 8 +
+           (size_t)2 * maxn * 8 + (size_t)4 * maxn * 8 + (size_t)6 * maxn * 8 + (size_t)(maxn + 1) * 8 + 64;
+}
+
+void launch_relocate(Markers &mk, cudaStream_t s)
+{
+    size_t sm = relocate_smem(mk.max_drop);
+    cudaFuncSetAttribute(k_relocate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    note_launch();
+    k_relocate<<<mk.ndrops, kT, sm, s>>>(mk.X, mk.Y, mk.drop_start, mk.h, mk.max_drop, mk.Xn,
+                                         mk.Yn, mk.flags);
+    cudaMemcpyAsync(mk.X, mk.Xn, (size_t)mk.M * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(mk.Y, mk.Yn, (size_t)mk.M * 8, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace ibk

@@ -1,0 +1,797 @@
+// Multigrid for the variable-coefficient pressure equation of Section 2.1
+// Eq. (ps), div(beta grad p) = b, on the cell-centred MAC grid.  The paper
+// names multigrid and nothing more; this is the V(nu1, nu2) cycle with a
+// red-black Gauss-Seidel smoother, residual + four-child averaging
+// restriction, bilinear (9,3,3,1)/16 prolongation, coarse face coefficients
+// = mean of the two fine faces, and a dense LU solve of the coarsest level
+// with the constant null space removed by A + s 1 1^T (s = A_00).
+//
+// GB300 mapping:
+//  * one red+black sweep = one launch: a 64x16 tile of p (+2-cell halo) is
+//    staged in shared memory, red cells of the tile and its 1-cell ring are
+//    updated there, then the black cells of the tile, and the tile is stored;
+//    HBM traffic is one read of p, b, beta_x, beta_y, 1/diag and one write of
+//    p per sweep (40 B/cell in FP64 plus the 1/diag stream).
+//  * levels with <= 1024 cells run as one single-CTA kernel (the whole lower
+//    V-cycle and the coarsest solve), since launches dominate there.
+//  * norms are deterministic two-stage reductions (fixed per-thread order,
+//    fixed tree, last-block fold) with no floating-point atomics.
+//  * the FP32 instantiations of the same kernels form the inner cycle of the
+//    defect-correction solve; the residual, the update and the coarsest
+//    solve stay FP64.
+#include <math.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "ib_internal.cuh"
+
+namespace ibk {
+namespace {
+
+constexpr int TW = 64, TH = 16, TT = 256;
+constexpr int kRedT = 256;
+
+// ------------------------------------------------------------------ sweeps
+template <typename T>
+__global__ void __launch_bounds__(TT)
+k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict__ by,
+             const T *__restrict__ invd, const T *__restrict__ b, T *__restrict__ p)
+{
+    __shared__ T ps[TH + 4][TW + 4];
+    const int gi0 = blockIdx.x * TW - 2, gj0 = blockIdx.y * TH - 2;
+    const long nxf = nx + 1;
+    for (int k = threadIdx.x; k < (TH + 4) * (TW + 4); k += TT) {
+        int r = k / (TW + 4), c = k - r * (TW + 4);
+        int gi = gi0 + c, gj = gj0 + r;
+        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? p[(long)gj * nx + gi] : T(0);
+    }
+    __syncthreads();
+    // red cells ((i+j) even) of the tile and its one-cell ring
+    constexpr int RW = (TW + 2) / 2;
+    for (int k = threadIdx.x; k < (TH + 2) * RW; k += TT) {
+        int r = 1 + k / RW, cc = k - (r - 1) * RW;
+        int gj = gj0 + r;
+        int c = 1 + 2 * cc + ((gi0 + 1 + gj) & 1);
+        int gi = gi0 + c;
+        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
+        long kc = (long)gj * nx + gi, kx = (long)gj * nxf + gi;
+        T s = bx[kx + 1] * ps[r][c + 1];
+        s = fma(bx[kx], ps[r][c - 1], s);
+        s = fma(by[kc + nx], ps[r + 1][c], s);
+        s = fma(by[kc], ps[r - 1][c], s);
+        T id = invd ? invd[kc]
+                    : T(1) / ((gi + 1 < nx ? bx[kx + 1] : T(0)) + (gi > 0 ? bx[kx] : T(0)) +
+                              (gj + 1 < ny ? by[kc + nx] : T(0)) + (gj > 0 ? by[kc] : T(0)));
+        ps[r][c] = (s - h2 * b[kc]) * id;
+    }
+    __syncthreads();
+    constexpr int BW = TW / 2;
+    for (int k = threadIdx.x; k < TH * BW; k += TT) {
+        int r = 2 + k / BW, cc = k - (r - 2) * BW;
+        int gj = gj0 + r;
+        int c = 2 + 2 * cc + ((gi0 + gj + 1) & 1);
+        int gi = gi0 + c;
+        if (gi >= nx || gj >= ny) continue;
+        long kc = (long)gj * nx + gi, kx = (long)gj * nxf + gi;
+        T s = bx[kx + 1] * ps[r][c + 1];
+        s = fma(bx[kx], ps[r][c - 1], s);
+        s = fma(by[kc + nx], ps[r + 1][c], s);
+        s = fma(by[kc], ps[r - 1][c], s);
+        T id = invd ? invd[kc]
+                    : T(1) / ((gi + 1 < nx ? bx[kx + 1] : T(0)) + (gi > 0 ? bx[kx] : T(0)) +
+                              (gj + 1 < ny ? by[kc + nx] : T(0)) + (gj > 0 ? by[kc] : T(0)));
+        ps[r][c] = (s - h2 * b[kc]) * id;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < TH * TW; k += TT) {
+        int r = 2 + k / TW, c = 2 + (k - (r - 2) * TW);
+        int gi = gi0 + c, gj = gj0 + r;
+        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
+                                      const T *by, const T *p)
+{
+    // sum_f beta_f (p_nb - p_c) in the order E, W, N, S; wall faces have beta = 0
+    long kc = (long)j * nx + i, kx = (long)j * (nx + 1) + i;
+    T c = p[kc];
+    T pE = (i + 1 < nx) ? p[kc + 1] : c, pW = (i > 0) ? p[kc - 1] : c;
+    T pN = (j + 1 < ny) ? p[kc + nx] : c, pS = (j > 0) ? p[kc - nx] : c;
+    T s = bx[kx + 1] * (pE - c);
+    s -= bx[kx] * (c - pW);
+    s += by[kc + nx] * (pN - c);
+    s -= by[kc] * (c - pS);
+    return s;
+}
+
+// Coarse residual = average of the four children's b - A p; zeroes the coarse
+// correction.
+template <typename T>
+__global__ void k_restrict_residual(int nx, int ny, T ih2, const T *__restrict__ bx,
+                                    const T *__restrict__ by, const T *__restrict__ b,
+                                    const T *__restrict__ p, T *__restrict__ rc,
+                                    T *__restrict__ ec)
+{
+    int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
+    int nxc = nx / 2;
+    if (I >= nxc) return;
+    int i = 2 * I, j = 2 * J;
+    T r00 = b[(long)j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+    T r10 = b[(long)j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * ih2;
+    T r01 = b[(long)(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * ih2;
+    T r11 = b[(long)(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * ih2;
+    long kc = (long)J * nxc + I;
+    rc[kc] = T(0.25) * (r00 + r10 + r01 + r11);
+    if (ec) ec[kc] = T(0);
+}
+
+template <typename T>
+__global__ void k_prolong_add(int nxc, int nyc, const T *__restrict__ ec, T *__restrict__ ef)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    int nx = 2 * nxc;
+    if (i >= nx) return;
+    int I = i >> 1, J = j >> 1;
+    int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
+    int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
+    T c00 = ec[(long)J * nxc + I], c10 = ec[(long)J * nxc + I2];
+    T c01 = ec[(long)J2 * nxc + I], c11 = ec[(long)J2 * nxc + I2];
+    ef[(long)j * nx + i] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
+}
+
+template <typename T>
+__global__ void k_residual(int nx, int ny, T ih2, const T *__restrict__ bx,
+                           const T *__restrict__ by, const T *__restrict__ b,
+                           const T *__restrict__ p, T *__restrict__ r)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    r[(long)j * nx + i] = b[(long)j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+}
+
+template <typename T>
+__global__ void k_invdiag(int nx, int ny, const double *__restrict__ bx,
+                          const double *__restrict__ by, T *__restrict__ invd)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    long kc = (long)j * nx + i, kx = (long)j * (nx + 1) + i;
+    double d = bx[kx + 1] + bx[kx] + by[kc + nx] + by[kc];
+    invd[kc] = (T)(d > 0.0 ? 1.0 / d : 0.0);
+}
+
+__global__ void k_coarsen_beta(int nx, int ny, const double *__restrict__ bx,
+                               const double *__restrict__ by, double *__restrict__ bxc,
+                               double *__restrict__ byc)
+{
+    int nxc = nx / 2, nyc = ny / 2;
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nxfc = (long)(nxc + 1) * nyc;
+    if (k < nxfc) {
+        int J = (int)(k / (nxc + 1)), I = (int)(k - (long)J * (nxc + 1));
+        bxc[k] = 0.5 * (bx[(long)(2 * J) * (nx + 1) + 2 * I] + bx[(long)(2 * J + 1) * (nx + 1) + 2 * I]);
+        return;
+    }
+    k -= nxfc;
+    if (k >= (long)nxc * (nyc + 1)) return;
+    int J = (int)(k / nxc), I = (int)(k - (long)J * nxc);
+    byc[k] = 0.5 * (by[(long)(2 * J) * nx + 2 * I] + by[(long)(2 * J) * nx + 2 * I + 1]);
+}
+
+// Level-0 coefficients with the wall faces forced to zero.
+__global__ void k_copy_beta(int nx, int ny, const double *__restrict__ bx,
+                            const double *__restrict__ by, double *__restrict__ ox,
+                            double *__restrict__ oy)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nxf = (long)(nx + 1) * ny;
+    if (k < nxf) {
+        int j = (int)(k / (nx + 1)), i = (int)(k - (long)j * (nx + 1));
+        ox[k] = (i == 0 || i == nx) ? 0.0 : bx[k];
+        return;
+    }
+    k -= nxf;
+    if (k >= (long)nx * (ny + 1)) return;
+    int j = (int)(k / nx);
+    oy[k] = (j == 0 || j == ny) ? 0.0 : by[k];
+}
+
+__global__ void k_to_float(long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) b[k] = (float)a[k];
+}
+
+// ------------------------------------------------------------ coarsest LU
+// Dense A' = A + s 1 1^T (s = A_00), then LU with partial pivoting (first
+// maximal |pivot|), one CTA.
+__global__ void __launch_bounds__(1024)
+k_coarse_lu(int nx, int ny, double h, const double *__restrict__ bx,
+            const double *__restrict__ by, double *__restrict__ A, int *__restrict__ piv)
+{
+    const int n = nx * ny;
+    const double hh = h * h;
+    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] = 0.0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        int i = c % nx, j = c / nx;
+        long kx = (long)j * (nx + 1) + i, kc = c;
+        double d = 0.0;
+        if (i + 1 < nx) { d += bx[kx + 1] * (0.0 - 1.0); A[(long)(c + 1) * n + c] = bx[kx + 1] * (1.0 - 0.0) / hh; }
+        if (i > 0) { d -= bx[kx] * (1.0 - 0.0); A[(long)(c - 1) * n + c] = -bx[kx] * (0.0 - 1.0) / hh; }
+        if (j + 1 < ny) { d += by[kc + nx] * (0.0 - 1.0); A[(long)(c + nx) * n + c] = by[kc + nx] * (1.0 - 0.0) / hh; }
+        if (j > 0) { d -= by[kc] * (1.0 - 0.0); A[(long)(c - nx) * n + c] = -by[kc] * (0.0 - 1.0) / hh; }
+        A[(long)c * n + c] = d / hh;
+    }
+    __syncthreads();
+    __shared__ double s0;
+    if (threadIdx.x == 0) s0 = A[0];
+    __syncthreads();
+    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] += s0;
+    __syncthreads();
+    __shared__ int pr;
+    for (int c = 0; c < n; c++) {
+        if (threadIdx.x == 0) {
+            int best = c;
+            for (int r = c + 1; r < n; r++)
+                if (fabs(A[(long)r * n + c]) > fabs(A[(long)best * n + c])) best = r;
+            pr = best;
+            piv[c] = best;
+        }
+        __syncthreads();
+        if (pr != c)
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                double t = A[(long)c * n + k];
+                A[(long)c * n + k] = A[(long)pr * n + k];
+                A[(long)pr * n + k] = t;
+            }
+        __syncthreads();
+        double d = A[(long)c * n + c];
+        for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) A[(long)r * n + c] /= d;
+        __syncthreads();
+        int w = n - c - 1;
+        for (long k = threadIdx.x; k < (long)w * w; k += blockDim.x) {
+            int r = c + 1 + (int)(k / w), q = c + 1 + (int)(k % w);
+            A[(long)r * n + q] -= A[(long)r * n + c] * A[(long)c * n + q];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ tail kernel
+constexpr int kMaxLv = 16;
+template <typename T>
+struct TailArgs {
+    int lt, nl;
+    int nx[kMaxLv], ny[kMaxLv];
+    T h2[kMaxLv], ih2[kMaxLv];
+    T *e[kMaxLv], *r[kMaxLv];
+    const T *bx[kMaxLv], *by[kMaxLv], *invd[kMaxLv];
+    const double *lu;
+    const int *piv;
+    int nu1, nu2;
+};
+
+template <typename T>
+__device__ void tail_smooth(const TailArgs<T> &a, int l, int nsw)
+{
+    const int nx = a.nx[l], ny = a.ny[l], n = nx * ny;
+    const T *bx = a.bx[l], *by = a.by[l], *invd = a.invd[l], *r = a.r[l];
+    T *e = a.e[l];
+    const T h2 = a.h2[l];
+    for (int s = 0; s < nsw; s++)
+        for (int color = 0; color < 2; color++) {
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                int j = k / nx, i = k - j * nx;
+                if (((i + j) & 1) != color) continue;
+                long kx = (long)j * (nx + 1) + i;
+                T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
+                T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
+                T sm = bx[kx + 1] * pE;
+                sm = fma(bx[kx], pW, sm);
+                sm = fma(by[k + nx], pN, sm);
+                sm = fma(by[k], pS, sm);
+                e[k] = (sm - h2 * r[k]) * invd[k];
+            }
+            __syncthreads();
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tail(TailArgs<T> a)
+{
+    __shared__ double xs[kMaxCoarsest];
+    const int L = a.nl;
+    for (int l = a.lt; l < L - 1; l++) {
+        tail_smooth(a, l, a.nu1);
+        const int nx = a.nx[l], ny = a.ny[l], nxc = nx / 2, nc = nxc * (ny / 2);
+        const T *bx = a.bx[l], *by = a.by[l], *b = a.r[l], *p = a.e[l];
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+            int J = k / nxc, I = k - J * nxc, i = 2 * I, j = 2 * J;
+            T r00 = b[(long)j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * a.ih2[l];
+            T r10 = b[(long)j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * a.ih2[l];
+            T r01 = b[(long)(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * a.ih2[l];
+            T r11 = b[(long)(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * a.ih2[l];
+            a.r[l + 1][k] = T(0.25) * (r00 + r10 + r01 + r11);
+            a.e[l + 1][k] = T(0);
+        }
+        __syncthreads();
+    }
+    // coarsest: x = A'^{-1} r by the stored LU (row swaps, unit lower, upper)
+    {
+        const int lc = L - 1, n = a.nx[lc] * a.ny[lc];
+        for (int k = threadIdx.x; k < n; k += blockDim.x) xs[k] = (double)a.r[lc][k];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane == 0)
+                for (int c = 0; c < n; c++) {
+                    int pr = a.piv[c];
+                    if (pr != c) { double t = xs[c]; xs[c] = xs[pr]; xs[pr] = t; }
+                }
+            __syncwarp();
+            for (int rr = 0; rr < n; rr++) {
+                double s = 0.0;
+                for (int k = lane; k < rr; k += 32) s += a.lu[(long)rr * n + k] * xs[k];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) xs[rr] -= s;
+                __syncwarp();
+            }
+            for (int rr = n - 1; rr >= 0; rr--) {
+                double s = 0.0;
+                for (int k = rr + 1 + lane; k < n; k += 32) s += a.lu[(long)rr * n + k] * xs[k];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) xs[rr] = (xs[rr] - s) / a.lu[(long)rr * n + rr];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) a.e[lc][k] = (T)xs[k];
+        __syncthreads();
+    }
+    for (int l = L - 2; l >= a.lt; l--) {
+        const int nx = a.nx[l], ny = a.ny[l], nxc = nx / 2, nyc = ny / 2;
+        const T *ec = a.e[l + 1];
+        T *ef = a.e[l];
+        for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
+            int j = k / nx, i = k - j * nx;
+            int I = i >> 1, J = j >> 1;
+            int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
+            int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
+            T c00 = ec[J * nxc + I], c10 = ec[J * nxc + I2];
+            T c01 = ec[J2 * nxc + I], c11 = ec[J2 * nxc + I2];
+            ef[k] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
+        }
+        __syncthreads();
+        tail_smooth(a, l, a.nu2);
+    }
+}
+
+// --------------------------------------------------------------- reductions
+// Deterministic sum: each block folds a fixed strided slice in a fixed order
+// and a fixed tree; the last block to finish folds the block partials.
+template <typename F>
+__device__ void block_fold_and_finish(double v, double *part, unsigned *count,
+                                      double *out)
+{
+    __shared__ double sh[kRedT];
+    __shared__ bool last;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sh[0];
+        __threadfence();
+        unsigned t = atomicAdd(count, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kRedT) s += ((volatile double *)part)[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kRedT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out = sh[0];
+        *count = 0u;
+    }
+}
+
+struct NoOp {};
+
+__global__ void __launch_bounds__(kRedT)
+k_sum(long n, const double *__restrict__ a, double *part, unsigned *count, double *out)
+{
+    double s = 0.0;
+    for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT)
+        s += a[k];
+    block_fold_and_finish<NoOp>(s, part, count, out);
+}
+
+// r0 = b - sum/n; accumulates sum r0^2.
+__global__ void __launch_bounds__(kRedT)
+k_sub_mean(long n, const double *__restrict__ b, const double *__restrict__ sum,
+           double *__restrict__ r0, double *part, unsigned *count, double *out)
+{
+    const double m = *sum / (double)n;
+    double s = 0.0;
+    for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT) {
+        double v = b[k] - m;
+        r0[k] = v;
+        s += v * v;
+    }
+    block_fold_and_finish<NoOp>(s, part, count, out);
+}
+
+__global__ void k_apply_mean(long n, double *__restrict__ p, const double *__restrict__ sum,
+                             double *__restrict__ dst)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = p[k] - *sum / (double)n;
+}
+
+// sum (b0 - A p)^2 over the fine grid, FP64.  With rf != NULL also writes the
+// FP32 residual and zeroes the FP32 correction for the inner cycle.
+__global__ void __launch_bounds__(kRedT)
+k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
+          const double *__restrict__ by, const double *__restrict__ b0,
+          const double *__restrict__ p, float *__restrict__ rf, float *__restrict__ ef,
+          double *part, unsigned *count, double *out)
+{
+    const long n = (long)nx * ny;
+    double s = 0.0;
+    for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT) {
+        int j = (int)(k / nx), i = (int)(k - (long)j * nx);
+        double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+        s += r * r;
+        if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
+    }
+    block_fold_and_finish<NoOp>(s, part, count, out);
+}
+
+__global__ void k_add_f32(long n, const float *__restrict__ e, double *__restrict__ p)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] += (double)e[k];
+}
+
+template <typename T>
+void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
+{
+    auto lvT = [&](int l) -> LevelT<T> & {
+        if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
+    };
+    const int L = (int)mg.lv.size(), lt = mg.tail;
+    for (int l = 0; l < lt; l++) {
+        Level &v = mg.lv[l];
+        LevelT<T> &a = lvT(l), &c = lvT(l + 1);
+        dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
+        T h2 = (T)(v.h * v.h);
+        for (int k = 0; k < nu1; k++) {
+            const bool pr = l == 0 && prof_on(sizeof(T) == 8 ? kProfSweep64 : kProfSweep32);
+            if (pr) prof_mark(s, true);
+            note_launch();
+            k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+            if (pr) prof_mark(s, false);
+        }
+        dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
+        note_launch();
+        k_restrict_residual<T><<<gr, 128, 0, s>>>(v.nx, v.ny, (T)(1.0 / (v.h * v.h)), a.bx,
+                                                  a.by, a.r, a.e, c.r, c.e);
+    }
+    TailArgs<T> ta;
+    ta.lt = lt;
+    ta.nl = L;
+    for (int l = lt; l < L; l++) {
+        Level &v = mg.lv[l];
+        LevelT<T> &a = lvT(l);
+        ta.nx[l] = v.nx; ta.ny[l] = v.ny;
+        ta.h2[l] = (T)(v.h * v.h); ta.ih2[l] = (T)(1.0 / (v.h * v.h));
+        ta.e[l] = a.e; ta.r[l] = a.r; ta.bx[l] = a.bx; ta.by[l] = a.by; ta.invd[l] = a.invd;
+    }
+    ta.lu = mg.lu;
+    ta.piv = mg.piv;
+    ta.nu1 = nu1;
+    ta.nu2 = nu2;
+    note_launch();
+    k_tail<T><<<1, 1024, 0, s>>>(ta);
+    for (int l = lt - 1; l >= 0; l--) {
+        Level &v = mg.lv[l];
+        LevelT<T> &a = lvT(l), &c = lvT(l + 1);
+        dim3 gp(cdiv(v.nx, 128), v.ny);
+        note_launch();
+        k_prolong_add<T><<<gp, 128, 0, s>>>(v.nx / 2, v.ny / 2, c.e, a.e);
+        dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
+        T h2 = (T)(v.h * v.h);
+        for (int k = 0; k < nu2; k++) {
+            const bool pr = l == 0 && prof_on(sizeof(T) == 8 ? kProfSweep64 : kProfSweep32);
+            if (pr) prof_mark(s, true);
+            note_launch();
+            k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+            if (pr) prof_mark(s, false);
+        }
+    }
+}
+
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ------------------------------------------------------------------- host
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+constexpr int kProfMax = 16384;
+struct Prof {
+    int kind = -1;
+    int n = 0;
+    bool open = false;
+    std::vector<cudaEvent_t> ev;
+} g_prof;
+}  // namespace
+
+void note_launch(int n) { g_launches += (unsigned long long)n; }
+unsigned long long launch_count() { return g_launches.load(); }
+bool prof_on(int kind) { return g_prof.kind == kind && g_prof.n < kProfMax; }
+void prof_mark(cudaStream_t s, bool start)
+{
+    if (start) {
+        cudaEventRecord(g_prof.ev[2 * g_prof.n], s);
+        g_prof.open = true;
+    } else if (g_prof.open) {
+        cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], s);
+        g_prof.n++;
+        g_prof.open = false;
+    }
+}
+
+bool prof_begin(int kind)
+{
+    if (g_prof.ev.empty()) {
+        g_prof.ev.resize(2 * kProfMax);
+        for (auto &e : g_prof.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return false;
+    }
+    g_prof.kind = kind;
+    g_prof.n = 0;
+    g_prof.open = false;
+    return true;
+}
+
+bool prof_end(double *total_ms, int *launches)
+{
+    double t = 0.0;
+    for (int k = 0; k < g_prof.n; k++) {
+        if (cudaEventSynchronize(g_prof.ev[2 * k + 1]) != cudaSuccess) return false;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g_prof.ev[2 * k], g_prof.ev[2 * k + 1]) != cudaSuccess)
+            return false;
+        t += ms;
+    }
+    if (total_ms) *total_ms = t;
+    if (launches) *launches = g_prof.n;
+    g_prof.kind = -1;
+    g_prof.n = 0;
+    return true;
+}
+
+bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys)
+{
+    nxs.assign(1, nx);
+    nys.assign(1, ny);
+    while ((int)nxs.size() < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && nx >= 8 && ny >= 8) {
+        nx /= 2; ny /= 2;
+        nxs.push_back(nx); nys.push_back(ny);
+    }
+    return (long)nx * ny <= kMaxCoarsest;
+}
+
+cudaError_t mg_alloc(MG &mg, int nx, int ny, double h)
+{
+    std::vector<int> nxs, nys;
+    mg_levels(nx, ny, nxs, nys);
+    const int L = (int)nxs.size();
+    mg.lv.assign(L, Level());
+    size_t bytes = 0;
+    for (int l = 0; l < L; l++) {
+        size_t n = (size_t)nxs[l] * nys[l], fx = (size_t)(nxs[l] + 1) * nys[l],
+               fy = (size_t)nxs[l] * (nys[l] + 1);
+        bytes += al(n * 8) * 3 + al(fx * 8) + al(fy * 8) + al(n * 4) * 3 + al(fx * 4) + al(fy * 4);
+    }
+    const long nc = (long)nxs[L - 1] * nys[L - 1];
+    mg.red_blocks = 2 * 152;
+    bytes += al((size_t)nc * nc * 8) + al((size_t)nc * 4) + al((size_t)(mg.red_blocks + 16) * 8) + al(64);
+    cudaError_t e = cudaMalloc(&mg.mem, bytes);
+    if (e != cudaSuccess) { mg.mem = nullptr; return e; }
+    e = cudaMallocHost((void **)&mg.red_host, 16 * sizeof(double));
+    if (e != cudaSuccess) { cudaFree(mg.mem); mg.mem = nullptr; mg.red_host = nullptr; return e; }
+    mg.bytes = bytes;
+    char *q = (char *)mg.mem;
+    auto take = [&](size_t b) { char *r = q; q += al(b); return (void *)r; };
+    for (int l = 0; l < L; l++) {
+        Level &v = mg.lv[l];
+        v.nx = nxs[l]; v.ny = nys[l]; v.h = h * (double)(1 << l);
+        size_t n = (size_t)v.nx * v.ny, fx = (size_t)(v.nx + 1) * v.ny, fy = (size_t)v.nx * (v.ny + 1);
+        v.d.e = (double *)take(n * 8); v.d.r = (double *)take(n * 8); v.d.invd = (double *)take(n * 8);
+        v.d.bx = (double *)take(fx * 8); v.d.by = (double *)take(fy * 8);
+        v.f.e = (float *)take(n * 4); v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
+        v.f.bx = (float *)take(fx * 4); v.f.by = (float *)take(fy * 4);
+    }
+    mg.lu = (double *)take((size_t)nc * nc * 8);
+    mg.piv = (int *)take((size_t)nc * 4);
+    mg.red = (double *)take((size_t)(mg.red_blocks + 16) * 8);
+    mg.red_count = (unsigned *)take(64);
+    int t = 0;
+    while (t < L && (long)nxs[t] * nys[t] > kTailCells) t++;
+    mg.tail = std::min(t, L - 1);
+    e = cudaMemset(mg.mem, 0, bytes);
+    return e;
+}
+
+void mg_free(MG &mg)
+{
+    if (mg.mem) cudaFree(mg.mem);
+    if (mg.red_host) cudaFreeHost(mg.red_host);
+    mg.mem = nullptr;
+    mg.red_host = nullptr;
+    mg.lv.clear();
+}
+
+void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
+{
+    const int L = (int)mg.lv.size();
+    Level &v0 = mg.lv[0];
+    long nf0 = (long)(v0.nx + 1) * v0.ny + (long)v0.nx * (v0.ny + 1);
+    note_launch();
+    k_copy_beta<<<cdiv(nf0, 256), 256, 0, s>>>(v0.nx, v0.ny, bx, by, v0.d.bx, v0.d.by);
+    for (int l = 0; l < L; l++) {
+        Level &v = mg.lv[l];
+        if (l > 0) {
+            Level &f = mg.lv[l - 1];
+            long nfc = (long)(v.nx + 1) * v.ny + (long)v.nx * (v.ny + 1);
+            note_launch();
+            k_coarsen_beta<<<cdiv(nfc, 256), 256, 0, s>>>(f.nx, f.ny, f.d.bx, f.d.by, v.d.bx, v.d.by);
+        }
+        dim3 g(cdiv(v.nx, 128), v.ny);
+        note_launch();
+        k_invdiag<double><<<g, 128, 0, s>>>(v.nx, v.ny, v.d.bx, v.d.by, v.d.invd);
+        note_launch();
+        k_invdiag<float><<<g, 128, 0, s>>>(v.nx, v.ny, v.d.bx, v.d.by, v.f.invd);
+        long fx = (long)(v.nx + 1) * v.ny, fy = (long)v.nx * (v.ny + 1);
+        note_launch();
+        k_to_float<<<cdiv(fx, 256), 256, 0, s>>>(fx, v.d.bx, v.f.bx);
+        note_launch();
+        k_to_float<<<cdiv(fy, 256), 256, 0, s>>>(fy, v.d.by, v.f.by);
+    }
+    Level &vc = mg.lv[L - 1];
+    note_launch();
+    k_coarse_lu<<<1, 1024, 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu, mg.piv);
+}
+
+ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
+                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                 cudaStream_t s, std::string &err)
+{
+    Level &v0 = mg.lv[0];
+    const long n = (long)v0.nx * v0.ny;
+    const int RB = mg.red_blocks;
+    double *part = mg.red + 8;
+    double *res = mg.red;  // res[0] sum b, res[1] |b0|^2, res[2] |r|^2, res[3] sum p
+    double *e0 = v0.d.e, *b0 = v0.d.r;
+    const double ih2 = 1.0 / (v0.h * v0.h);
+    cudaMemcpyAsync(e0, p, n * 8, cudaMemcpyDeviceToDevice, s);
+    note_launch();
+    k_sum<<<RB, kRedT, 0, s>>>(n, rhs, part, mg.red_count, res + 0);
+    note_launch();
+    k_sub_mean<<<RB, kRedT, 0, s>>>(n, rhs, res + 0, b0, part, mg.red_count, res + 1);
+    auto resnorm = [&]() {
+        const bool pr = prof_on(kProfResnorm);
+        if (pr) prof_mark(s, true);
+        note_launch();
+        k_resnorm<<<RB, kRedT, 0, s>>>(v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
+                                       precision ? v0.f.r : nullptr,
+                                       precision ? v0.f.e : nullptr, part, mg.red_count,
+                                       res + 2);
+        if (pr) prof_mark(s, false);
+        cudaMemcpyAsync(mg.red_host, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        return cudaStreamSynchronize(s);
+    };
+    cudaError_t ce = resnorm();
+    if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
+    double nb = sqrt(mg.red_host[1]);
+    int c = 0;
+    double rr = 0.0;
+    ib_status st = IB_OK;
+    if (nb == 0.0) {
+        cudaMemsetAsync(p, 0, n * 8, s);
+        ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
+    } else {
+        rr = sqrt(mg.red_host[2]) / nb;
+        while (rr > tol && c < max_cycles && isfinite(rr)) {
+            if (precision == 0) {
+                vcycle<double>(mg, nu1, nu2, s);
+            } else {
+                vcycle<float>(mg, nu1, nu2, s);
+                note_launch();
+                k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
+            }
+            c++;
+            ce = resnorm();
+            if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
+            rr = sqrt(mg.red_host[2]) / nb;
+        }
+        note_launch();
+        k_sum<<<RB, kRedT, 0, s>>>(n, e0, part, mg.red_count, res + 3);
+        note_launch();
+        k_apply_mean<<<cdiv(n, 256), 256, 0, s>>>(n, e0, res + 3, p);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
+        if (!isfinite(rr)) { st = IB_ENAN; err = "non-finite residual"; }
+        else if (rr > tol) { st = IB_ENOTCONV; err = "cycle cap reached above tolerance"; }
+    }
+    if (cycles) *cycles = c;
+    if (relres) *relres = rr;
+    return st;
+}
+
+// Context-free launches used by the verification entry points.
+void launch_rbgs(int nx, int ny, double h, const double *bx, const double *by,
+                 const double *invd, const double *b, double *p, cudaStream_t s)
+{
+    dim3 g(cdiv(nx, TW), cdiv(ny, TH));
+    note_launch();
+    k_rbgs_sweep<double><<<g, TT, 0, s>>>(nx, ny, h * h, bx, by, invd, b, p);
+}
+
+void launch_invdiag(int nx, int ny, const double *bx, const double *by,
+                    double *invd, cudaStream_t s)
+{
+    dim3 g(cdiv(nx, 128), ny);
+    note_launch();
+    k_invdiag<double><<<g, 128, 0, s>>>(nx, ny, bx, by, invd);
+}
+
+void launch_restrict_residual(int nx, int ny, double h, const double *bx,
+                              const double *by, const double *b, const double *p,
+                              double *rc, double *ec, cudaStream_t s)
+{
+    dim3 gr(cdiv(nx / 2, 128), ny / 2);
+    note_launch();
+    k_restrict_residual<double><<<gr, 128, 0, s>>>(nx, ny, 1.0 / (h * h), bx, by, b, p, rc, ec);
+}
+
+void launch_prolong_add(int nxc, int nyc, const double *ec, double *ef, cudaStream_t s)
+{
+    dim3 gp(cdiv(2 * nxc, 128), 2 * nyc);
+    note_launch();
+    k_prolong_add<double><<<gp, 128, 0, s>>>(nxc, nyc, ec, ef);
+}
+
+void launch_coarsen_beta(int nx, int ny, const double *bx, const double *by,
+                         double *bxc, double *byc, cudaStream_t s)
+{
+    long nfc = (long)(nx / 2 + 1) * (ny / 2) + (long)(nx / 2) * (ny / 2 + 1);
+    note_launch();
+    k_coarsen_beta<<<cdiv(nfc, 256), 256, 0, s>>>(nx, ny, bx, by, bxc, byc);
+}
+
+void launch_residual(int nx, int ny, double h, const double *bx, const double *by,
+                     const double *b, const double *p, double *r, cudaStream_t s)
+{
+    dim3 g(cdiv(nx, 128), ny);
+    note_launch();
+    k_residual<double><<<g, 128, 0, s>>>(nx, ny, 1.0 / (h * h), bx, by, b, p, r);
+}
+
+}  // namespace ibk

@@ -1,0 +1,105 @@
+"""GPU parity of the composed time step (ns_step through the C ABI) against
+the oracle's step on the static-drop (64^2) and oscillating-drop (256^2)
+workloads, checkpoint/resume bit-identity and run-to-run determinism."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ib():
+    import paper_1807_10504_gb300 as ib
+    ib.lib()
+    return ib
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def run_pair(ib, O, n, mk, steps, tol=1e-12, **kw):
+    h = 1.0 / n
+    cfg = ib.Config(nx=n, ny=n, h=h, tol=tol, max_cycles=200, **kw)
+    ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    ocfg = O.Config(nx=n, ny=n, h=h, tol=tol, max_cycles=200,
+                    **{k: v for k, v in kw.items() if k != "precision"})
+    st = O.init_state(ocfg, mk.X, mk.Y, mk.drop_start)
+    dt = W.capillary_dt(h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    for _ in range(steps):
+        ctx.ns_step(dt, 1, 1)
+        O.ns_step(ocfg, st, dt)
+    return ctx, st
+
+
+@pytest.mark.parametrize("spread", [0, 1])
+def test_static_drop_steps_match_oracle(T, ib, O, spread):
+    mk = W.static_drop(64, 0.25, 128)
+    ctx, st = run_pair(ib, O, 64, mk, 3, spread=spread, relocate_every=10)
+    for name, ref in (("u", st.u), ("v", st.v), ("p", st.p)):
+        assert rel(ctx.get_host(name), ref) <= 1e-9, name
+    X, Y = ctx.markers()
+    assert np.abs(X.cpu().numpy() - st.X).max() <= 1e-12
+    assert np.abs(Y.cpu().numpy() - st.Y).max() <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_oscillating_drop_steps_match_oracle(T, ib, O, precision):
+    mk = W.oscillating_drop()
+    ctx, st = run_pair(ib, O, 256, mk, 2, tol=1e-10 if precision else 1e-12, spread=1,
+                       relocate_every=10, precision=precision)
+    bound = 1e-6 if precision else 1e-9
+    for name, ref in (("u", st.u), ("v", st.v), ("p", st.p)):
+        assert rel(ctx.get_host(name), ref) <= bound, name
+    for name, ref in (("H", st.last["H"]), ("Fx", st.last["Fx"]), ("Fy", st.last["Fy"])):
+        assert rel(ctx.get_host(name), ref) <= 1e-11, name
+
+
+def test_checkpoint_resume_and_determinism(T, ib, tmp_path):
+    mk = W.oscillating_drop(200, seed=5)
+    n = 96
+    cfg = ib.Config(nx=n, ny=n, h=1.0 / n, relocate_every=3)
+    dt = W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    a = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    a.ns_step(dt, 2, 1)
+    path = os.path.join(tmp_path, "ck.bin")
+    a.save(path)
+    a.ns_step(dt, 3, 1)
+    b = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    b.load(path)
+    b.ns_step(dt, 3, 1)
+    c = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    c.ns_step(dt, 5, 1)
+    for name in ("u", "v", "p"):
+        ua, ub, uc = a.get_host(name), b.get_host(name), c.get_host(name)
+        assert np.array_equal(ua, ub) and np.array_equal(ua, uc), name
+    assert T.equal(a.markers()[0], b.markers()[0])
+
+
+def test_step_errors(T, ib):
+    mk = W.static_drop(32, 0.25, 64)
+    cfg = ib.Config(nx=32, ny=32, h=1 / 32)
+    ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    with pytest.raises(ib.IBError) as e:
+        ctx.ns_step(-1.0)
+    assert e.value.status == ib.IB_EINVAL
+    # a huge time step throws markers out of the domain: reported, no fault
+    u = T.full((32, 33), 50.0, dtype=T.float64, device="cuda")
+    u[:, 0] = 0
+    u[:, -1] = 0
+    ctx.set("u", u)
+    with pytest.raises(ib.IBError) as e:
+        ctx.ns_step(0.05, 1, 1)
+    assert e.value.status == ib.IB_EMARKER

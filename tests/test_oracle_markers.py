@@ -277,3 +277,12 @@ def test_bspline_relocation_circle_and_equivariance(O):
     assert d.std() / d.mean() < 1e-6
     Xs, Ys = O.bspline_relocate(mk.X + 0.125, mk.Y - 0.25, mk.drop_start, h)
     assert np.abs(Xs - 0.125 - Xo).max() < 1e-12 and np.abs(Ys + 0.25 - Yo).max() < 1e-12
+
+
+def test_row_inside_equals_pointwise_crossing_number(O):
+    n, h = 80, 1 / 80
+    mk = W.multidrop(80, ndrops=5, rmin=0.06, rmax=0.12, n_per_drop=70, seed=9, gap_cells=6)
+    chi = O.inside(mk.X, mk.Y, mk.drop_start, n, n, h)
+    for j in range(0, n, 3):
+        for i in range(n):
+            assert chi[j, i] == O.inside_cell(i, j, mk.X, mk.Y, mk.drop_start, h)
