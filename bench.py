@@ -48,6 +48,19 @@ def make_markers(name, seed_offset=0):
     return W.static_drop(wl["n"], 0.25, 128)
 
 
+def max_over_ranks(x: float) -> float:
+    """Max of a host float over the ranks of the default process group (the
+    identity when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,6 +191,15 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.ncu:
+        torch.cuda.profiler.start()
+        for k in range(args.steps):
+            ctx.ns_step(dt, 1, 1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        ctx.close()
+        return 0
+
     sweep_kind = ib.PROF_SWEEP32 if args.precision == 1 else ib.PROF_SWEEP64
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -196,12 +218,7 @@ def run_ours(args):
     launches = ib.launch_count() - l0
     sweep_ms, sweep_n = ib.profile_end()
     clocks = clk.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
     value = ws * args.steps / (t_ms / 1e3)
 
     # pressure solve alone, cold start, on this state's system: FP64 vs mixed
@@ -248,7 +265,7 @@ def run_ours(args):
         ctx.get_host("p", ph)
         ctx.get_markers_host(Xh, Yh)
     barrier()
-    e2e_t = time.perf_counter() - t0
+    e2e_t = max_over_ranks(time.perf_counter() - t0)
 
     avg_sweep = sweep_ms / max(sweep_n, 1)
     bpc = 20.0 if sweep_kind == ib.PROF_SWEEP32 else 40.0
@@ -301,6 +318,9 @@ def main():
     ap.add_argument("--workload", default="multidrop1024", choices=list(WORKLOADS))
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true",
+                    help="only warm-up + timed steps, the timed steps inside a CUDA profiler "
+                         "range (for ncu --profile-from-start off); prints no JSON")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

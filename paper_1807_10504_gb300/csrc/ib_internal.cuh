@@ -14,7 +14,7 @@ constexpr int kTailCells = 1024;     // levels with at most this many cells run 
 constexpr int kMaxCoarsest = 1024;   // dense LU limit of the coarsest level
 constexpr int kBlk = 8;              // marker-activity block edge (cells)
 constexpr int kSearch = 7;           // marker search radius (cells) around a cell or face
-constexpr int kMaxCand = 2048;       // candidate segments per activity block
+constexpr int kMaxCand = 1024;       // candidate segments per activity block
 constexpr int kMaxCross = 2048;      // interface crossings per grid row
 
 inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
@@ -60,8 +60,30 @@ struct Level {
     LevelT<float> f;
 };
 
+struct SolveCtl {
+    double tol;
+    int max_cycles;
+    int cycles;
+    double rr;
+    int zero_p;
+    int pad;
+};
+
+struct SolveGraph {
+    const double *rhs = nullptr;
+    double *p = nullptr;
+    int precision = 0, nu1 = 0, nu2 = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long outer_kernels = 0, body_kernels = 0;
+};
+
 struct MG {
-    std::vector<Level> lv;
+    Level lv[16];
+    int L = 0;                    // number of levels in lv
+    std::vector<SolveGraph> graphs;  // instantiated solves, keyed by pointers and settings
+    cudaStream_t cap = nullptr, cap_body = nullptr;
+    SolveCtl *ctl = nullptr, *ctl_host = nullptr;
+    bool use_graphs = true;
     int tail = 0;                 // first level handled by the single-CTA tail kernel
     double *lu = nullptr;         // coarsest dense LU (n x n), FP64
     int *piv = nullptr;           // coarsest row permutation
@@ -74,6 +96,10 @@ struct MG {
 };
 
 bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys);
+// Places the hierarchy (levels, coarsest LU, reduction partials, control
+// block) at `base` (or only measures it when base is NULL); returns its bytes.
+// Allocates nothing.
+size_t mg_layout(MG &mg, int nx, int ny, double h, char *base);
 cudaError_t mg_alloc(MG &mg, int nx, int ny, double h);
 void mg_free(MG &mg);
 // Copy level-0 coefficients (walls forced to 0) and build the hierarchy.
@@ -105,7 +131,11 @@ struct Markers {
     double *X = nullptr, *Y = nullptr, *kappa = nullptr, *nxm = nullptr,
            *nym = nullptr, *ds = nullptr, *fmag = nullptr, *U = nullptr,
            *V = nullptr, *Xn = nullptr, *Yn = nullptr;
-    int32_t *drop_start = nullptr, *drop_of = nullptr;
+    double *gx = nullptr, *gy = nullptr;   // marker positions in grid units
+    float *gxf = nullptr, *gyf = nullptr;  // the same rounded to FP32 (screening only)
+    float4 *sbox = nullptr;                // slab box of segment (m, next m), grid units
+    double2 *dyr = nullptr;                // per-drop [min Y, max Y]
+    int32_t *drop_start = nullptr, *drop_of = nullptr, *next = nullptr;
     uint32_t *key = nullptr, *tmp_ids = nullptr, *ids = nullptr,
              *cell_count = nullptr, *cell_start = nullptr, *scan_part = nullptr,
              *bcount = nullptr, *bactive = nullptr, *flags = nullptr;

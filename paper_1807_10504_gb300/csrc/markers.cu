@@ -53,13 +53,20 @@ __global__ void k_validate(int M, const double *__restrict__ X, const double *__
 // ------------------------------------------------------------ geometry
 __global__ void k_geometry(int M, const double *__restrict__ X, const double *__restrict__ Y,
                            const int32_t *__restrict__ drop_of,
-                           const int32_t *__restrict__ drop_start, double sigma,
-                           double *__restrict__ kappa, double *__restrict__ nxm,
-                           double *__restrict__ nym, double *__restrict__ ds,
-                           double *__restrict__ fmag)
+                           const int32_t *__restrict__ drop_start, double sigma, double x0,
+                           double y0, double h, double *__restrict__ kappa,
+                           double *__restrict__ nxm, double *__restrict__ nym,
+                           double *__restrict__ ds, double *__restrict__ fmag,
+                           double *__restrict__ gx, double *__restrict__ gy,
+                           float *__restrict__ gxf, float *__restrict__ gyf)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
+    {
+        double a = (X[m] - x0) / h, b = (Y[m] - y0) / h;
+        gx[m] = a; gy[m] = b;
+        gxf[m] = (float)a; gyf[m] = (float)b;
+    }
     int pm, nm;
     nbrs(m, drop_of, drop_start, &pm, &nm);
     double ax = X[m] - X[pm], ay = Y[m] - Y[pm];
@@ -78,6 +85,46 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
     nym[m] = ny_ / ln;
     ds[m] = dsm;
     fmag[m] = sigma * k;
+}
+
+// Slab box of segment (m, next m): the four corners at offsets -2.5 and +2.5
+// cells along both marker normals, in grid units, rounded outward to FP32 so
+// that an FP32 test against a cell never rejects a strip that touches it.
+__global__ void k_segments(int M, const int32_t *__restrict__ next, const double *__restrict__ gx,
+                           const double *__restrict__ gy, const double *__restrict__ nxm,
+                           const double *__restrict__ nym, float4 *__restrict__ sbox)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int nm = next[m];
+    double xs[4] = {gx[m] - 2.5 * nxm[m], gx[m] + 2.5 * nxm[m], gx[nm] - 2.5 * nxm[nm],
+                    gx[nm] + 2.5 * nxm[nm]};
+    double ys[4] = {gy[m] - 2.5 * nym[m], gy[m] + 2.5 * nym[m], gy[nm] - 2.5 * nym[nm],
+                    gy[nm] + 2.5 * nym[nm]};
+    double x0 = fmin(fmin(xs[0], xs[1]), fmin(xs[2], xs[3]));
+    double x1 = fmax(fmax(xs[0], xs[1]), fmax(xs[2], xs[3]));
+    double y0 = fmin(fmin(ys[0], ys[1]), fmin(ys[2], ys[3]));
+    double y1 = fmax(fmax(ys[0], ys[1]), fmax(ys[2], ys[3]));
+    sbox[m] = make_float4(__double2float_rd(x0) - 1e-3f, __double2float_ru(x1) + 1e-3f,
+                          __double2float_rd(y0) - 1e-3f, __double2float_ru(y1) + 1e-3f);
+}
+
+// One warp per drop: the range of its marker Y.
+__global__ void k_drop_yrange(int ndrops, const int32_t *__restrict__ drop_start,
+                              const double *__restrict__ Y, double2 *__restrict__ dyr)
+{
+    int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (d >= ndrops) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int m = drop_start[d] + lane; m < drop_start[d + 1]; m += 32) {
+        lo = fmin(lo, Y[m]);
+        hi = fmax(hi, Y[m]);
+    }
+    for (int o = 16; o; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) dyr[d] = make_double2(lo, hi);
 }
 
 // ------------------------------------------------------------ binning
@@ -302,10 +349,10 @@ __global__ void k_spread_conv(int kernel, int nx, int ny, double h, double x0, d
 // One CTA per row: crossings of the row's centre line with every segment,
 // sorted, then a crossing count per cell centre.  Writes H = chi.
 __global__ void __launch_bounds__(kT)
-k_rows_inside(int M, int nx, double h, double x0, double y0, const double *__restrict__ X,
-              const double *__restrict__ Y, const int32_t *__restrict__ drop_of,
-              const int32_t *__restrict__ drop_start, double *__restrict__ H,
-              uint32_t *__restrict__ flags)
+k_rows_inside(int ndrops, int nx, double h, double x0, double y0, const double *__restrict__ X,
+              const double *__restrict__ Y, const int32_t *__restrict__ next,
+              const int32_t *__restrict__ drop_start, const double2 *__restrict__ dyr,
+              double *__restrict__ H, uint32_t *__restrict__ flags)
 {
     __shared__ double xs[kMaxCross], srt[kMaxCross];
     __shared__ int nc;
@@ -313,14 +360,19 @@ k_rows_inside(int M, int nx, double h, double x0, double y0, const double *__res
     const double py = y0 + ((double)j + 0.5) * h;
     if (threadIdx.x == 0) nc = 0;
     __syncthreads();
-    for (int m = threadIdx.x; m < M; m += kT) {
-        int pm, nm;
-        nbrs(m, drop_of, drop_start, &pm, &nm);
-        double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
-        if ((ay > py) != (by > py)) {
-            double xc = ax + (py - ay) * (bx - ax) / (by - ay);
-            int q = atomicAdd(&nc, 1);
-            if (q < kMaxCross) xs[q] = xc;
+    // a drop entirely above (py < min Y) or not above (py >= max Y) the line
+    // has no segment with one end above it and the other not
+    for (int d = 0; d < ndrops; d++) {
+        double2 r = dyr[d];
+        if (py < r.x || py >= r.y) continue;
+        for (int m = drop_start[d] + threadIdx.x; m < drop_start[d + 1]; m += kT) {
+            int nm = next[m];
+            double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
+            if ((ay > py) != (by > py)) {
+                double xc = ax + (py - ay) * (bx - ax) / (by - ay);
+                int q = atomicAdd(&nc, 1);
+                if (q < kMaxCross) xs[q] = xc;
+            }
         }
     }
     __syncthreads();
@@ -447,13 +499,12 @@ __device__ __forceinline__ double strip_value(int k)
 constexpr int kBT = kBlk * kBlk;  // one thread per cell of the block
 
 __global__ void __launch_bounds__(kBT)
-k_band_heaviside(int nx, int ny, double h, double x0, double y0, int bnx,
-                 const uint32_t *__restrict__ bactive, const uint32_t *__restrict__ cell_start,
-                 const uint32_t *__restrict__ ids, const double *__restrict__ X,
-                 const double *__restrict__ Y, const double *__restrict__ nxm,
-                 const double *__restrict__ nym, const int32_t *__restrict__ drop_of,
-                 const int32_t *__restrict__ drop_start, double *__restrict__ H,
-                 uint32_t *__restrict__ flags)
+k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
+                 const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
+                 const int32_t *__restrict__ next, const double *__restrict__ gx,
+                 const double *__restrict__ gy, const double *__restrict__ nxm,
+                 const double *__restrict__ nym, const float4 *__restrict__ sbox,
+                 double *__restrict__ H, uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
     const int bi = blockIdx.x, bj = blockIdx.y;
@@ -461,29 +512,24 @@ k_band_heaviside(int nx, int ny, double h, double x0, double y0, int bnx,
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
     const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
     if (i >= nx || j >= ny) return;
+    const float fi = (float)i, fj = (float)j;
     double Hk[5];
     for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
     double acc = 0.0, cov = 0.0;
     for (int q = 0; q < n; q++) {
-        int m = (int)cand[q], pm, nm;
-        nbrs(m, drop_of, drop_start, &pm, &nm);
-        double gxa = (X[m] - x0) / h, gya = (Y[m] - y0) / h;
-        double gxb = (X[nm] - x0) / h, gyb = (Y[nm] - y0) / h;
-        double na_x = nxm[m], na_y = nym[m], nb_x = nxm[nm], nb_y = nym[nm];
-        // whole slab bounding box (offsets -2.5 .. 2.5) against the cell
-        double sx0 = fmin(fmin(gxa - 2.5 * fabs(na_x), gxb - 2.5 * fabs(nb_x)), 1e300);
-        double sx1 = fmax(gxa + 2.5 * fabs(na_x), gxb + 2.5 * fabs(nb_x));
-        double sy0 = fmin(gya - 2.5 * fabs(na_y), gyb - 2.5 * fabs(nb_y));
-        double sy1 = fmax(gya + 2.5 * fabs(na_y), gyb + 2.5 * fabs(nb_y));
-        if (sx1 < (double)i || sx0 > (double)(i + 1) || sy1 < (double)j || sy0 > (double)(j + 1))
-            continue;
+        const int m = (int)cand[q];
+        const float4 b = sbox[m];
+        if (b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj) continue;
+        const int nm = next[m];
+        const double gxa = gx[m], gya = gy[m], gxb = gx[nm], gyb = gy[nm];
+        const double na_x = nxm[m], na_y = nym[m], nb_x = nxm[nm], nb_y = nym[nm];
         for (int k = 0; k < 5; k++) {
-            double a = (double)k - 2.5, b = (double)k - 1.5;
+            double a = (double)k - 2.5, bb = (double)k - 1.5;
             double qx[4], qy[4];
             qx[0] = gxa + a * na_x; qy[0] = gya + a * na_y;
             qx[1] = gxb + a * nb_x; qy[1] = gyb + a * nb_y;
-            qx[2] = gxb + b * nb_x; qy[2] = gyb + b * nb_y;
-            qx[3] = gxa + b * na_x; qy[3] = gya + b * na_y;
+            qx[2] = gxb + bb * nb_x; qy[2] = gyb + bb * nb_y;
+            qx[3] = gxa + bb * na_x; qy[3] = gya + bb * na_y;
             for (int t = 0; t < 4; t++) { qx[t] -= (double)i; qy[t] -= (double)j; }
             double mnx = fmin(fmin(qx[0], qx[1]), fmin(qx[2], qx[3]));
             double mxx = fmax(fmax(qx[0], qx[1]), fmax(qx[2], qx[3]));
@@ -506,11 +552,11 @@ k_band_heaviside(int nx, int ny, double h, double x0, double y0, int bnx,
 // segment (closest point clamped to the segment, ties to the lower id),
 // linear in the segment parameter between its two markers.
 __global__ void __launch_bounds__(kBT)
-k_spread_irrot(int nx, int ny, double h, double x0, double y0, int bnx,
-               const uint32_t *__restrict__ bactive, const uint32_t *__restrict__ cell_start,
-               const uint32_t *__restrict__ ids, const double *__restrict__ X,
-               const double *__restrict__ Y, const double *__restrict__ fmag,
-               const int32_t *__restrict__ drop_of, const int32_t *__restrict__ drop_start,
+k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ bactive,
+               const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
+               const int32_t *__restrict__ next, const double *__restrict__ gx,
+               const double *__restrict__ gy, const float *__restrict__ gxf,
+               const float *__restrict__ gyf, const double *__restrict__ fmag,
                const double *__restrict__ H, double *__restrict__ Fx, double *__restrict__ Fy,
                uint32_t *__restrict__ flags)
 {
@@ -534,12 +580,32 @@ k_spread_irrot(int nx, int ny, double h, double x0, double y0, int bnx,
         }
         double F = 0.0;
         if (dH != 0.0) {
+            // FP32 screen: squared distances carry an error far below 0.05
+            // (grid units, coordinates < 2^15), so the exact nearest segment is
+            // among those within best + 0.05 of the FP32 minimum.
+            const float fqx = (float)qx, fqy = (float)qy;
+            float best32 = INFINITY;
+            for (int q = 0; q < n; q++) {
+                int m = (int)cand[q], nm = next[m];
+                float ax = gxf[m], ay = gyf[m], ex = gxf[nm] - ax, ey = gyf[nm] - ay;
+                float t = ((fqx - ax) * ex + (fqy - ay) * ey) / (ex * ex + ey * ey);
+                t = fminf(fmaxf(t, 0.0f), 1.0f);
+                float dx = ax + t * ex - fqx, dy = ay + t * ey - fqy;
+                best32 = fminf(best32, dx * dx + dy * dy);
+            }
+            const float lim = best32 + 0.05f;
             double best = INFINITY, fb = 0.0;
             for (int q = 0; q < n; q++) {
-                int m = (int)cand[q], pm, nm;
-                nbrs(m, drop_of, drop_start, &pm, &nm);
-                double ax = (X[m] - x0) / h, ay = (Y[m] - y0) / h;
-                double bx = (X[nm] - x0) / h, by = (Y[nm] - y0) / h;
+                int m = (int)cand[q], nm = next[m];
+                {
+                    float ax = gxf[m], ay = gyf[m], ex = gxf[nm] - ax, ey = gyf[nm] - ay;
+                    float t = ((fqx - ax) * ex + (fqy - ay) * ey) / (ex * ex + ey * ey);
+                    t = fminf(fmaxf(t, 0.0f), 1.0f);
+                    float dx = ax + t * ex - fqx, dy = ay + t * ey - fqy;
+                    if (dx * dx + dy * dy > lim) continue;
+                }
+                double ax = gx[m], ay = gy[m];
+                double bx = gx[nm], by = gy[nm];
                 double ex = bx - ax, ey = by - ay;
                 double t = ((qx - ax) * ex + (qy - ay) * ey) / (ex * ex + ey * ey);
                 if (t < 0.0) t = 0.0;
@@ -804,7 +870,8 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
         mk.max_drop = std::max(mk.max_drop, drop_start_host[d + 1] - drop_start_host[d]);
     size_t ncell = (size_t)nx * ny, nb = (size_t)mk.bnx * mk.bny;
     size_t nparts = (ncell + kScanChunk - 1) / kScanChunk;
-    size_t bytes = al(M * 8) * 11 + al((ndrops + 1) * 4) + al(M * 4) * 4 + al(ncell * 4) +
+    size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) +
+                   al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
     if (e != cudaSuccess) { mk.mem = nullptr; return e; }
@@ -815,20 +882,29 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.ds = (double *)take(M * 8); mk.fmag = (double *)take(M * 8);
     mk.U = (double *)take(M * 8); mk.V = (double *)take(M * 8);
     mk.Xn = (double *)take(M * 8); mk.Yn = (double *)take(M * 8);
+    mk.gx = (double *)take(M * 8); mk.gy = (double *)take(M * 8);
+    mk.gxf = (float *)take(M * 4); mk.gyf = (float *)take(M * 4);
+    mk.sbox = (float4 *)take(M * 16);
+    mk.dyr = (double2 *)take(ndrops * 16);
     mk.drop_start = (int32_t *)take((ndrops + 1) * 4);
     mk.drop_of = (int32_t *)take(M * 4);
+    mk.next = (int32_t *)take(M * 4);
     mk.key = (uint32_t *)take(M * 4); mk.tmp_ids = (uint32_t *)take(M * 4); mk.ids = (uint32_t *)take(M * 4);
     mk.cell_count = (uint32_t *)take(ncell * 4);
     mk.cell_start = (uint32_t *)take((ncell + 1) * 4);
     mk.scan_part = (uint32_t *)take(nparts * 4);
     mk.bcount = (uint32_t *)take(nb * 4); mk.bactive = (uint32_t *)take(nb * 4);
     mk.flags = (uint32_t *)take(64);
-    std::vector<int32_t> dof(M);
+    std::vector<int32_t> dof(M), nxt(M);
     for (int d = 0; d < ndrops; d++)
-        for (int m = drop_start_host[d]; m < drop_start_host[d + 1]; m++) dof[m] = d;
+        for (int m = drop_start_host[d]; m < drop_start_host[d + 1]; m++) {
+            dof[m] = d;
+            nxt[m] = (m + 1 == drop_start_host[d + 1]) ? drop_start_host[d] : m + 1;
+        }
     e = cudaMemset(mk.mem, 0, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(mk.drop_start, drop_start_host, (ndrops + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(mk.drop_of, dof.data(), M * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && M > 0) e = cudaMemcpy(mk.next, nxt.data(), M * 4, cudaMemcpyHostToDevice);
     return e;
 }
 
@@ -850,7 +926,13 @@ void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
 {
     note_launch();
     k_geometry<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.X, mk.Y, mk.drop_of, mk.drop_start, sigma,
-                                            mk.kappa, mk.nxm, mk.nym, mk.ds, mk.fmag);
+                                            mk.x0, mk.y0, mk.h, mk.kappa, mk.nxm, mk.nym, mk.ds,
+                                            mk.fmag, mk.gx, mk.gy, mk.gxf, mk.gyf);
+    note_launch();
+    k_segments<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox);
+    note_launch();
+    k_drop_yrange<<<cdiv((long)mk.ndrops * 32, kT), kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.Y,
+                                                               mk.dyr);
 }
 
 void launch_sort(Markers &mk, cudaStream_t s)
@@ -901,13 +983,13 @@ void launch_spread_conv(const Markers &mk, int kernel, const double *fmag, doubl
 void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
 {
     note_launch();
-    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.M, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.drop_of,
-                                       mk.drop_start, H, mk.flags);
+    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.next,
+                                       mk.drop_start, mk.dyr, H, mk.flags);
     dim3 g(mk.bnx, mk.bny);
     note_launch();
-    k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.x0, mk.y0, mk.bnx, mk.bactive,
-                                       mk.cell_start, mk.ids, mk.X, mk.Y, mk.nxm, mk.nym,
-                                       mk.drop_of, mk.drop_start, H, mk.flags);
+    k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids,
+                                       mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox, H,
+                                       mk.flags);
 }
 
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H, double *Fx,
@@ -917,9 +999,9 @@ void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
     cudaMemsetAsync(Fy, 0, (size_t)mk.nx * (mk.ny + 1) * 8, s);
     dim3 g(mk.bnx, mk.bny);
     note_launch();
-    k_spread_irrot<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.x0, mk.y0, mk.bnx, mk.bactive,
-                                     mk.cell_start, mk.ids, mk.X, mk.Y, fmag, mk.drop_of,
-                                     mk.drop_start, H, Fx, Fy, mk.flags);
+    k_spread_irrot<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.bnx, mk.bactive, mk.cell_start,
+                                     mk.ids, mk.next, mk.gx, mk.gy, mk.gxf, mk.gyf, fmag, H, Fx,
+                                     Fy, mk.flags);
 }
 
 size_t relocate_smem(int maxn)

@@ -91,6 +91,70 @@ k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict
     }
 }
 
+// Two red-black sweeps in one launch (FP32 inner cycle): the tile of p with a
+// 4-cell halo and b, beta_x, beta_y, 1/diag with a 3-cell halo are staged in
+// shared memory with all loads issued up front; the sweeps then run from
+// shared memory on shrinking rings (red on ring 3, black on ring 2, red on
+// ring 1, black on the tile) so the tile's result equals two global sweeps.
+constexpr int FW = 64, FH = 16, FT = 256;
+__global__ void __launch_bounds__(FT)
+k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float *__restrict__ by,
+            const float *__restrict__ invd, const float *__restrict__ b, float *__restrict__ p)
+{
+    constexpr int PW = FW + 8, PH = FH + 8;      // p with halo 4
+    constexpr int CW = FW + 6, CH = FH + 6;      // cell data with halo 3
+    __shared__ float ps[PH][PW];
+    __shared__ float bs[CH][CW], ds[CH][CW], xs[CH][CW + 1], ys[CH + 1][CW];
+    const int gi0 = blockIdx.x * FW - 4, gj0 = blockIdx.y * FH - 4;
+    const long nxf = nx + 1;
+    for (int k = threadIdx.x; k < PH * PW; k += FT) {
+        int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
+        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? p[(long)gj * nx + gi] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < CH * CW; k += FT) {
+        int r = k / CW, c = k - r * CW, gi = gi0 + 1 + c, gj = gj0 + 1 + r;
+        bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        long kc = (long)gj * nx + gi;
+        bs[r][c] = in ? b[kc] : 0.0f;
+        ds[r][c] = in ? invd[kc] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < CH * (CW + 1); k += FT) {
+        int r = k / (CW + 1), c = k - r * (CW + 1), gi = gi0 + 1 + c, gj = gj0 + 1 + r;
+        xs[r][c] = (gi >= 0 && gi <= nx && gj >= 0 && gj < ny) ? bx[(long)gj * nxf + gi] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < (CH + 1) * CW; k += FT) {
+        int r = k / CW, c = k - r * CW, gi = gi0 + 1 + c, gj = gj0 + 1 + r;
+        ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[(long)gj * nx + gi] : 0.0f;
+    }
+    __syncthreads();
+    // ring q: local p rows/cols [4-q, 4+F+q); colour: 0 red, 1 black
+#pragma unroll
+    for (int ph = 0; ph < 4; ph++) {
+        const int q = 3 - ph, color = ph & 1;
+        const int w = FW + 2 * q, hgt = FH + 2 * q, hw = w / 2;
+        for (int k = threadIdx.x; k < hgt * hw; k += FT) {
+            int rr = k / hw, cc = k - rr * hw;
+            int r = 4 - q + rr;                       // local p row
+            int gj = gj0 + r;
+            int c = 4 - q + 2 * cc + ((gi0 + 4 - q + gj + color) & 1);
+            int gi = gi0 + c;
+            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
+            int r1 = r - 1, c1 = c - 1;               // local cell-data indices
+            float sm = xs[r1][c1 + 1] * ps[r][c + 1];
+            sm = fmaf(xs[r1][c1], ps[r][c - 1], sm);
+            sm = fmaf(ys[r1 + 1][c1], ps[r + 1][c], sm);
+            sm = fmaf(ys[r1][c1], ps[r - 1][c], sm);
+            ps[r][c] = (sm - h2 * bs[r1][c1]) * ds[r1][c1];
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < FH * FW; k += FT) {
+        int r = 4 + k / FW, c = 4 + (k - (k / FW) * FW);
+        int gi = gi0 + c, gj = gj0 + r;
+        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
                                       const T *by, const T *p)
@@ -301,9 +365,40 @@ __device__ void tail_smooth(const TailArgs<T> &a, int l, int nsw)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_tail(TailArgs<T> a)
+__host__ __device__ size_t tail_smem_elems(const TailArgs<T> &a)
 {
+    size_t n = 0;
+    for (int l = a.lt; l < a.nl; l++) {
+        size_t c = (size_t)a.nx[l] * a.ny[l];
+        n += 3 * c + (size_t)(a.nx[l] + 1) * a.ny[l] + (size_t)a.nx[l] * (a.ny[l] + 1);
+    }
+    return n;
+}
+
+// The lower V-cycle (levels lt..L-1, each at most 1024 cells) in one CTA: the
+// coefficients and the level-lt iterate and right-hand side are copied into
+// shared memory, the cycle runs there, and the level-lt iterate is copied
+// back.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
+{
+    extern __shared__ __align__(16) unsigned char tail_sm[];
     __shared__ double xs[kMaxCoarsest];
+    TailArgs<T> a = g;
+    T *q = (T *)tail_sm;
+    for (int l = g.lt; l < g.nl; l++) {
+        const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
+        T *e = q, *r = q + c, *iv = q + 2 * c, *bxs = q + 3 * c, *bys = q + 3 * c + fx;
+        q += 3 * c + fx + fy;
+        for (int k = threadIdx.x; k < c; k += blockDim.x) {
+            iv[k] = g.invd[l][k];
+            if (l == g.lt) { e[k] = g.e[l][k]; r[k] = g.r[l][k]; }
+        }
+        for (int k = threadIdx.x; k < fx; k += blockDim.x) bxs[k] = g.bx[l][k];
+        for (int k = threadIdx.x; k < fy; k += blockDim.x) bys[k] = g.by[l][k];
+        a.e[l] = e; a.r[l] = r; a.invd[l] = iv; a.bx[l] = bxs; a.by[l] = bys;
+    }
+    __syncthreads();
     const int L = a.nl;
     for (int l = a.lt; l < L - 1; l++) {
         tail_smooth(a, l, a.nu1);
@@ -368,6 +463,7 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs<T> a)
         __syncthreads();
         tail_smooth(a, l, a.nu2);
     }
+    for (int k = threadIdx.x; k < a.nx[a.lt] * a.ny[a.lt]; k += blockDim.x) g.e[a.lt][k] = a.e[a.lt][k];
 }
 
 // --------------------------------------------------------------- reductions
@@ -466,25 +562,66 @@ __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restric
     if (k < n) p[k] += (double)e[k];
 }
 
+// Convergence test of the device-side solve loop (one thread): updates the
+// cycle count and relative residual and sets the WHILE condition.
+__global__ void k_check(SolveCtl *ctl, const double *res, cudaGraphConditionalHandle hnd, int first)
+{
+    const double nb = sqrt(res[1]);
+    if (first) { ctl->cycles = 0; ctl->zero_p = nb == 0.0 ? 1 : 0; }
+    else ctl->cycles += 1;
+    const double rr = nb == 0.0 ? 0.0 : sqrt(res[2]) / nb;
+    ctl->rr = rr;
+    const unsigned go = (nb != 0.0 && rr > ctl->tol && ctl->cycles < ctl->max_cycles && isfinite(rr)) ? 1u : 0u;
+    cudaGraphSetConditional(hnd, go);
+}
+
+__global__ void k_finalize(long n, const double *__restrict__ e0, const double *__restrict__ sum,
+                           const SolveCtl *__restrict__ ctl, double *__restrict__ p)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = ctl->zero_p ? 0.0 : e0[k] - *sum / (double)n;
+}
+
+// nsw sweeps on one level: FP32 in fused pairs, FP64 one sweep per launch
+// (the FP64 sweep is bound by the FP64 pipe, where fusing only adds halo work).
+template <typename T>
+void smooth(const Level &v, LevelT<T> &a, int nsw, bool fine, cudaStream_t s)
+{
+    const T h2 = (T)(v.h * v.h);
+    int k = 0;
+    if constexpr (sizeof(T) == 4) {
+        dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
+        for (; k + 2 <= nsw; k += 2) {
+            const bool pr = fine && prof_on(kProfSweep32);
+            if (pr) prof_mark(s, true);
+            note_launch();
+            k_rbgs2_f32<<<g2, FT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+            if (pr) prof_mark(s, false);
+        }
+    }
+    dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
+    for (; k < nsw; k++) {
+        const bool pr = fine && sizeof(T) == 8 && prof_on(kProfSweep64);
+        if (pr) prof_mark(s, true);
+        note_launch();
+        k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+        if (pr) prof_mark(s, false);
+    }
+}
+
 template <typename T>
 void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
 {
     auto lvT = [&](int l) -> LevelT<T> & {
         if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
     };
-    const int L = (int)mg.lv.size(), lt = mg.tail;
+    const int L = mg.L, lt = mg.tail;
     for (int l = 0; l < lt; l++) {
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l), &c = lvT(l + 1);
         dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
         T h2 = (T)(v.h * v.h);
-        for (int k = 0; k < nu1; k++) {
-            const bool pr = l == 0 && prof_on(sizeof(T) == 8 ? kProfSweep64 : kProfSweep32);
-            if (pr) prof_mark(s, true);
-            note_launch();
-            k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
-            if (pr) prof_mark(s, false);
-        }
+        smooth<T>(v, a, nu1, l == 0, s);
         dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
         note_launch();
         k_restrict_residual<T><<<gr, 128, 0, s>>>(v.nx, v.ny, (T)(1.0 / (v.h * v.h)), a.bx,
@@ -505,7 +642,8 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
     ta.nu1 = nu1;
     ta.nu2 = nu2;
     note_launch();
-    k_tail<T><<<1, 1024, 0, s>>>(ta);
+    const size_t smem = tail_smem_elems(ta) * sizeof(T);
+    k_tail<T><<<1, 1024, smem, s>>>(ta);
     for (int l = lt - 1; l >= 0; l--) {
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l), &c = lvT(l + 1);
@@ -514,13 +652,7 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
         k_prolong_add<T><<<gp, 128, 0, s>>>(v.nx / 2, v.ny / 2, c.e, a.e);
         dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
         T h2 = (T)(v.h * v.h);
-        for (int k = 0; k < nu2; k++) {
-            const bool pr = l == 0 && prof_on(sizeof(T) == 8 ? kProfSweep64 : kProfSweep32);
-            if (pr) prof_mark(s, true);
-            note_launch();
-            k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
-            if (pr) prof_mark(s, false);
-        }
+        smooth<T>(v, a, nu2, l == 0, s);
     }
 }
 
@@ -540,9 +672,10 @@ struct Prof {
 } g_prof;
 }  // namespace
 
-void note_launch(int n) { g_launches += (unsigned long long)n; }
+void note_launch(int n) { g_launches += (unsigned long long)(long long)n; }
 unsigned long long launch_count() { return g_launches.load(); }
 bool prof_on(int kind) { return g_prof.kind == kind && g_prof.n < kProfMax; }
+static bool prof_active() { return g_prof.kind >= 0; }
 void prof_mark(cudaStream_t s, bool start)
 {
     if (start) {
@@ -596,28 +729,24 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys)
     return (long)nx * ny <= kMaxCoarsest;
 }
 
-cudaError_t mg_alloc(MG &mg, int nx, int ny, double h)
+size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
 {
-    std::vector<int> nxs, nys;
-    mg_levels(nx, ny, nxs, nys);
-    const int L = (int)nxs.size();
-    mg.lv.assign(L, Level());
-    size_t bytes = 0;
-    for (int l = 0; l < L; l++) {
-        size_t n = (size_t)nxs[l] * nys[l], fx = (size_t)(nxs[l] + 1) * nys[l],
-               fy = (size_t)nxs[l] * (nys[l] + 1);
-        bytes += al(n * 8) * 3 + al(fx * 8) + al(fy * 8) + al(n * 4) * 3 + al(fx * 4) + al(fy * 4);
+    int nxs[16], nys[16], L = 0;
+    nxs[0] = nx; nys[0] = ny; L = 1;
+    while (L < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && nx >= 8 && ny >= 8) {
+        nx /= 2; ny /= 2;
+        nxs[L] = nx; nys[L] = ny; L++;
     }
     const long nc = (long)nxs[L - 1] * nys[L - 1];
     mg.red_blocks = 2 * 152;
-    bytes += al((size_t)nc * nc * 8) + al((size_t)nc * 4) + al((size_t)(mg.red_blocks + 16) * 8) + al(64);
-    cudaError_t e = cudaMalloc(&mg.mem, bytes);
-    if (e != cudaSuccess) { mg.mem = nullptr; return e; }
-    e = cudaMallocHost((void **)&mg.red_host, 16 * sizeof(double));
-    if (e != cudaSuccess) { cudaFree(mg.mem); mg.mem = nullptr; mg.red_host = nullptr; return e; }
-    mg.bytes = bytes;
-    char *q = (char *)mg.mem;
-    auto take = [&](size_t b) { char *r = q; q += al(b); return (void *)r; };
+    char *q = base;
+    size_t off = 0;
+    auto take = [&](size_t b) -> void * {
+        void *r = base ? (void *)(q + off) : nullptr;
+        off += al(b);
+        return r;
+    };
+    mg.L = L;
     for (int l = 0; l < L; l++) {
         Level &v = mg.lv[l];
         v.nx = nxs[l]; v.ny = nys[l]; v.h = h * (double)(1 << l);
@@ -631,25 +760,48 @@ cudaError_t mg_alloc(MG &mg, int nx, int ny, double h)
     mg.piv = (int *)take((size_t)nc * 4);
     mg.red = (double *)take((size_t)(mg.red_blocks + 16) * 8);
     mg.red_count = (unsigned *)take(64);
+    mg.ctl = (SolveCtl *)take(sizeof(SolveCtl));
     int t = 0;
     while (t < L && (long)nxs[t] * nys[t] > kTailCells) t++;
     mg.tail = std::min(t, L - 1);
-    e = cudaMemset(mg.mem, 0, bytes);
+    return off;
+}
+
+cudaError_t mg_alloc(MG &mg, int nx, int ny, double h)
+{
+    const size_t bytes = mg_layout(mg, nx, ny, h, nullptr);
+    cudaError_t e = cudaMalloc(&mg.mem, bytes);
+    if (e != cudaSuccess) { mg.mem = nullptr; return e; }
+    mg_layout(mg, nx, ny, h, (char *)mg.mem);
+    mg.bytes = bytes;
+    e = cudaMallocHost((void **)&mg.red_host, 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&mg.ctl_host, sizeof(SolveCtl));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.cap_body, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(mg.mem, 0, bytes);
     return e;
 }
 
 void mg_free(MG &mg)
 {
+    for (auto &g : mg.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    mg.graphs.clear();
+    if (mg.cap) cudaStreamDestroy(mg.cap);
+    if (mg.cap_body) cudaStreamDestroy(mg.cap_body);
+    mg.cap = mg.cap_body = nullptr;
+    if (mg.ctl_host) cudaFreeHost(mg.ctl_host);
+    mg.ctl_host = nullptr;
     if (mg.mem) cudaFree(mg.mem);
     if (mg.red_host) cudaFreeHost(mg.red_host);
     mg.mem = nullptr;
     mg.red_host = nullptr;
-    mg.lv.clear();
+    mg.L = 0;
 }
 
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 {
-    const int L = (int)mg.lv.size();
+    const int L = mg.L;
     Level &v0 = mg.lv[0];
     long nf0 = (long)(v0.nx + 1) * v0.ny + (long)v0.nx * (v0.ny + 1);
     note_launch();
@@ -673,14 +825,28 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         note_launch();
         k_to_float<<<cdiv(fy, 256), 256, 0, s>>>(fy, v.d.by, v.f.by);
     }
+    {
+        // shared memory of the single-CTA tail (set here, outside any capture)
+        size_t e = 0;
+        for (int l = mg.tail; l < L; l++) {
+            size_t c = (size_t)mg.lv[l].nx * mg.lv[l].ny;
+            e += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
+        }
+        cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(e * 8));
+        cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(e * 4));
+    }
     Level &vc = mg.lv[L - 1];
     note_launch();
     k_coarse_lu<<<1, 1024, 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu, mg.piv);
 }
 
-ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
-                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
-                 cudaStream_t s, std::string &err)
+// Host-driven solve: one launch per kernel and a host read of the residual
+// after every cycle.  Used when per-kernel event timing is active (events
+// cannot time kernels inside a graph) and as the reference for the graph
+// solve below.
+static ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, double tol,
+                               int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                               cudaStream_t s, std::string &err)
 {
     Level &v0 = mg.lv[0];
     const long n = (long)v0.nx * v0.ny;
@@ -743,6 +909,146 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
     if (cycles) *cycles = c;
     if (relres) *relres = rr;
     return st;
+}
+
+// The same solve as one CUDA graph: prologue (copy-in, mean removal, initial
+// residual, convergence test), a device-side WHILE node whose body is one
+// cycle + FP64 residual + convergence test, and an epilogue (mean removal,
+// control block to the host).  One graph launch and one host synchronisation
+// per solve; the loop is bounded by max_cycles on the device.
+static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
+{
+    Level &v0 = mg.lv[0];
+    const long n = (long)v0.nx * v0.ny;
+    const int RB = mg.red_blocks;
+    double *part = mg.red + 8, *res = mg.red;
+    double *e0 = v0.d.e, *b0 = v0.d.r;
+    const double ih2 = 1.0 / (v0.h * v0.h);
+    cudaStream_t c = mg.cap, cb = mg.cap_body;
+    const unsigned long long k0 = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    if (sg.p != e0) cudaMemcpyAsync(e0, sg.p, n * 8, cudaMemcpyDeviceToDevice, c);
+    note_launch();
+    k_sum<<<RB, kRedT, 0, c>>>(n, sg.rhs, part, mg.red_count, res + 0);
+    note_launch();
+    k_sub_mean<<<RB, kRedT, 0, c>>>(n, sg.rhs, res + 0, b0, part, mg.red_count, res + 1);
+    auto resnorm = [&](cudaStream_t st) {
+        note_launch();
+        k_resnorm<<<RB, kRedT, 0, st>>>(v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
+                                        sg.precision ? v0.f.r : nullptr,
+                                        sg.precision ? v0.f.e : nullptr, part, mg.red_count,
+                                        res + 2);
+    };
+    resnorm(c);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps;
+    const cudaGraphEdgeData *ed;
+    size_t nd;
+    cudaGraphConditionalHandle hnd;
+    unsigned long long kb0 = 0, kb1 = 0;
+    e = cudaStreamGetCaptureInfo(c, &cs, nullptr, &g, &deps, &ed, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        note_launch();
+        k_check<<<1, 1, 0, c>>>(mg.ctl, res, hnd, 1);
+        e = cudaStreamGetCaptureInfo(c, &cs, nullptr, &g, &deps, &ed, &nd);
+    }
+    cudaGraphNode_t wnode;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, g, deps, ed, nd, &cp);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(c, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        kb0 = launch_count();
+        e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            if (sg.precision == 0) {
+                vcycle<double>(mg, sg.nu1, sg.nu2, cb);
+            } else {
+                vcycle<float>(mg, sg.nu1, sg.nu2, cb);
+                note_launch();
+                k_add_f32<<<cdiv(n, 256), 256, 0, cb>>>(n, v0.f.e, e0);
+            }
+            resnorm(cb);
+            note_launch();
+            k_check<<<1, 1, 0, cb>>>(mg.ctl, res, hnd, 0);
+            e = cudaStreamEndCapture(cb, &body);
+        }
+        kb1 = launch_count();
+    }
+    if (e == cudaSuccess) {
+        note_launch();
+        k_sum<<<RB, kRedT, 0, c>>>(n, e0, part, mg.red_count, res + 3);
+        note_launch();
+        k_finalize<<<cdiv(n, 256), 256, 0, c>>>(n, e0, res + 3, mg.ctl, sg.p);
+        cudaMemcpyAsync(mg.ctl_host, mg.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, c);
+    }
+    cudaGraph_t full = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c, &full);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, full, 0);
+    if (full) cudaGraphDestroy(full);
+    const unsigned long long kall = launch_count() - k0;
+    sg.body_kernels = kb1 - kb0;
+    sg.outer_kernels = kall - sg.body_kernels;
+    note_launch(-(int)kall);  // capture issues no kernel; executions are counted per launch
+    cudaGetLastError();
+    return e;
+}
+
+static bool prof_active();
+
+ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
+                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                 cudaStream_t s, std::string &err)
+{
+    if (!mg.use_graphs || prof_active())
+        return mg_run_direct(mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles, relres, s, err);
+    SolveGraph *sg = nullptr;
+    for (auto &g : mg.graphs)
+        if (g.rhs == rhs && g.p == p && g.precision == precision && g.nu1 == nu1 && g.nu2 == nu2)
+            sg = &g;
+    if (!sg) {
+        if (mg.graphs.size() >= 8) {
+            cudaGraphExecDestroy(mg.graphs.front().exec);
+            mg.graphs.erase(mg.graphs.begin());
+        }
+        SolveGraph ng;
+        ng.rhs = rhs; ng.p = p; ng.precision = precision; ng.nu1 = nu1; ng.nu2 = nu2;
+        cudaError_t e = build_solve_graph(mg, ng);
+        if (e != cudaSuccess) {
+            if (ng.exec) cudaGraphExecDestroy(ng.exec);
+            // graphs unavailable: keep solving with direct launches
+            mg.use_graphs = false;
+            return mg_run_direct(mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles, relres, s, err);
+        }
+        mg.graphs.push_back(ng);
+        sg = &mg.graphs.back();
+    }
+    mg.ctl_host->tol = tol;
+    mg.ctl_host->max_cycles = max_cycles;
+    cudaError_t e = cudaMemcpyAsync(mg.ctl, mg.ctl_host, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { err = cudaGetErrorString(e); return IB_ECUDA; }
+    const int c = mg.ctl_host->cycles;
+    const double rr = mg.ctl_host->rr;
+    note_launch((int)(sg->outer_kernels + (unsigned long long)c * sg->body_kernels));
+    if (cycles) *cycles = c;
+    if (relres) *relres = rr;
+    if (mg.ctl_host->zero_p) return IB_OK;
+    if (!isfinite(rr)) { err = "non-finite residual"; return IB_ENAN; }
+    if (rr > tol) { err = "cycle cap reached above tolerance"; return IB_ENOTCONV; }
+    return IB_OK;
 }
 
 // Context-free launches used by the verification entry points.

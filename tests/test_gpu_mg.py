@@ -29,7 +29,8 @@ def ib():
 def ctx_for(ib, nx, ny):
     # a context only to own the solver; one small drop well inside
     n = min(nx, ny)
-    X, Y = W.circle(0.5 * nx / n, 0.5 * ny / n, 0.2, 16)
+    R = min(0.2, 0.45 - 3.0 / n)  # at least 3 cells from the walls
+    X, Y = W.circle(0.5 * nx / n, 0.5 * ny / n, R, 16)
     cfg = ib.Config(nx=nx, ny=ny, h=1.0 / n)
     return ib.Context(cfg, X, Y, [0, 16])
 
@@ -39,10 +40,8 @@ def coeffs(O, nx, ny, seed, poly=False):
         mk = W.multidrop(nx, ndrops=6, rmin=0.05, rmax=0.12, n_per_drop=200, seed=seed,
                          gap_cells=12)
         H = O.heaviside(mk.X, mk.Y, mk.drop_start, nx, ny, 1.0 / nx)
-    elif nx == ny:
-        H = W.random_H(nx, ny, seed)
     else:
-        H = np.clip(W.random_cells(nx, ny, seed) + 0.5, 0, 1)
+        H = W.random_H(nx, ny, seed)
     return O.coeffs(H, 1e-3, 1.0, 1e-4, 1e-2)
 
 

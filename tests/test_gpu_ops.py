@@ -35,8 +35,7 @@ def rel(a, b):
 
 
 def setup(O, nx, ny, seed):
-    H = W.random_H(nx, ny, seed) if nx == ny else np.clip(
-        W.random_cells(nx, ny, seed) * 2, 0, 1)
+    H = W.random_H(nx, ny, seed)
     rho, mu, bx, by = O.coeffs(H, 1e-3, 1.0, 1e-4, 1e-2)
     return H, rho, mu, bx, by
 
