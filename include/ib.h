@@ -176,6 +176,35 @@ ib_status ib_save(ib_ctx *ctx, const char *path);
 ib_status ib_load(ib_ctx *ctx, const char *path);
 
 /* ---------------------------------------------------------------------- */
+/* Pressure solve that allocates nothing (the paper has no counterpart; it
+ * serves callers that cannot allocate device memory: code running under a
+ * memory manager that owns all device memory, such as a framework's caching
+ * allocator or a fixed-budget embedded deployment, and latency-critical loops
+ * that cannot afford cudaMalloc's implicit device synchronisation).
+ *
+ * Same solve as mg_setup + mg_solve with the host-driven cycle loop, on the
+ * coefficients bx, by (device face arrays, walls ignored), right-hand side
+ * rhs and initial guess / mean-zero solution p (device cell arrays) of an
+ * nx x ny grid with cell size h, launched on `stream`.  Its scratch (the
+ * multigrid hierarchy, coarsest LU, reduction partials) is one file-scope
+ * device array of IB_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading
+ * the library holds until the process exits; grids above
+ * IB_NOALLOC_MAX_CELLS cells (or whose hierarchy does not fit) return
+ * IB_EINVAL.  No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and its contents persist between calls, so calls
+ * that overlap on the GPU (other streams, other host threads) race; the call
+ * is not thread-safe.  Status codes as mg_solve.                            */
+#define IB_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define IB_NOALLOC_MAX_CELLS 65536
+ib_status mg_solve_noalloc(int32_t nx, int32_t ny, double h, const double *bx,
+                           const double *by, const double *rhs, double *p,
+                           int precision, double tol, int max_cycles, int nu1,
+                           int nu2, int *cycles_out, double *relres_out,
+                           void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Context-free grid operators (device arrays, launched on `stream`, no
  * allocation).  Each is one step of the path, exposed for verification.
  * Errors: IB_EINVAL for bad sizes or NULL pointers, IB_ECUDA on launch

@@ -33,7 +33,7 @@ EXPORTS = [
     "ns_step", "ib_last_solve", "ib_save", "ib_load", "ib_op_coeffs", "ib_op_residual",
     "ib_op_rbgs", "ib_op_restrict_residual", "ib_op_prolong_add", "ib_op_coarsen_beta",
     "ib_op_rhs", "ib_op_correct", "ib_op_predictor", "ib_launch_count", "ib_profile_begin",
-    "ib_profile_end",
+    "ib_profile_end", "mg_solve_noalloc",
 ]
 
 
@@ -89,6 +89,8 @@ def lib():
             "ib_op_coarsen_beta": [_i32, _i32, _P, _P, _P, _P, _P],
             "ib_op_rhs": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P],
             "ib_op_correct": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+            "mg_solve_noalloc": [_i32, _i32, _d, _P, _P, _P, _P, C.c_int, _d, C.c_int, C.c_int,
+                                 C.c_int, C.POINTER(C.c_int), C.POINTER(_d), _P],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
         }
@@ -301,6 +303,21 @@ class Context:
 
     def load(self, path):
         _check(lib().ib_load(self._h, str(path).encode()), self._h)
+
+
+# -------------------------------------------------------------- no-allocation solve
+def mg_solve_noalloc(bx, by, rhs, p, h, precision=0, tol=1e-10, max_cycles=100, nu1=2, nu2=2):
+    """Pressure solve through ``mg_solve_noalloc``: scratch comes from a fixed
+    device array inside the library, so nothing is allocated (for callers that
+    cannot allocate device memory).  ``p`` is updated in place.  Returns
+    (status, cycles, relative residual)."""
+    torch = _torch()
+    ny, nx = p.shape
+    cyc, rr = C.c_int(0), C.c_double(0.0)
+    st = lib().mg_solve_noalloc(nx, ny, h, _ptr(bx, torch.float64), _ptr(by, torch.float64),
+                                _ptr(rhs, torch.float64), _ptr(p, torch.float64), precision, tol,
+                                max_cycles, nu1, nu2, C.byref(cyc), C.byref(rr), _stream())
+    return st, cyc.value, rr.value
 
 
 # -------------------------------------------------------------- measurement

@@ -21,6 +21,7 @@ SOURCES = {
     "mg.cu": [],
     "markers.cu": ["--fmad=false"],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 

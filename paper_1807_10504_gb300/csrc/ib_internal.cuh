@@ -109,6 +109,12 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
                  int max_cycles, int nu1, int nu2, int *cycles, double *relres,
                  cudaStream_t s, std::string &err);
 
+// The same solve with one launch per kernel and a host read of the residual
+// after each cycle (no graph objects, no allocation of its own).
+ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, double tol,
+                        int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                        cudaStream_t s, std::string &err);
+
 void launch_rbgs(int nx, int ny, double h, const double *bx, const double *by,
                  const double *invd, const double *b, double *p, cudaStream_t s);
 void launch_invdiag(int nx, int ny, const double *bx, const double *by,

@@ -844,9 +844,9 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 // after every cycle.  Used when per-kernel event timing is active (events
 // cannot time kernels inside a graph) and as the reference for the graph
 // solve below.
-static ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, double tol,
-                               int max_cycles, int nu1, int nu2, int *cycles, double *relres,
-                               cudaStream_t s, std::string &err)
+ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, double tol,
+                        int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                        cudaStream_t s, std::string &err)
 {
     Level &v0 = mg.lv[0];
     const long n = (long)v0.nx * v0.ny;
