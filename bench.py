@@ -178,6 +178,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    if args.no_graphs:
+        ctx.use_graphs(False)
     dt = W.capillary_dt(h, cfg.rho_l, cfg.rho_g, cfg.sigma, cfg.mu_l, cfg.mu_g)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -318,6 +320,8 @@ def main():
     ap.add_argument("--workload", default="multidrop1024", choices=list(WORKLOADS))
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="solve with one launch per kernel (for kernel profilers)")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + timed steps, the timed steps inside a CUDA profiler "
                          "range (for ncu --profile-from-start off); prints no JSON")

@@ -153,10 +153,46 @@ ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
  * (indicator)), AB2 advection + explicit viscous predictor (Eqs. (ad_bf),
  * (cr_ni)), spreading, rhs, pressure solve, correction, interpolation and
  * marker advection X += dt U.  warm: 0 zero initial pressure, 1 previous
- * step's pressure.  The last step's cycles and residual are returned by
+ * step's pressure, 2 the attached network's estimate (square grid, side a
+ * multiple of 4).  The last step's cycles and residual are returned by
  * ib_last_solve.                                                           */
 ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
 ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
+
+/* ---------------------------------------------------------------------- */
+/* Learned warm start (no counterpart in the paper; the network only moves
+ * the starting point of the multigrid solve, which still runs to the same
+ * residual tolerance).  A 3-level encoder/decoder CNN, channels c1 = 16 and
+ * c2 = 32 (the only supported widths), BF16 weights and activations with
+ * FP32 accumulation on the tensor cores, FP32 master weights and Adam state.
+ * Input of a sample: rhs b and cell density rho (device FP64 N x N, N a
+ * multiple of 4; B samples stored back to back); features
+ * ((b - mean b)/s, (1/rho)/max(1/rho)) with s = rms(b - mean b); target p / s
+ * with a mean-removed squared-error loss; output p0 = s (y - mean y).
+ * Parameters are a flat FP32 host array, layer by layer (c1a, c1b, c2a, c2b,
+ * c3a, c3b, c4, c5, c6), each weights [cout][3][3][cin] then bias [cout].
+ * Calls run on `stream`; cnn_train_step, cnn_grad synchronise it when they
+ * return the loss (host float, may be NULL).                               */
+typedef struct ib_cnn ib_cnn;
+ib_status cnn_init(ib_cnn **out, int32_t c1, int32_t c2, uint64_t seed, void *stream);
+void cnn_destroy(ib_cnn *net);
+int64_t cnn_num_params(const ib_cnn *net);
+ib_status cnn_get_params(ib_cnn *net, float *host, int64_t n);
+ib_status cnn_set_params(ib_cnn *net, const float *host, int64_t n);  /* resets Adam */
+/* Loss and parameter gradients (host, cnn_num_params floats) without update. */
+ib_status cnn_grad(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
+                   const double *rho, const double *p, float *loss,
+                   float *grads_host, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch.            */
+ib_status cnn_train_step(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
+                         const double *rho, const double *p, float lr,
+                         float *loss, void *stream);
+/* p0 (device FP64, B x N x N) = network estimate of the pressure.          */
+ib_status cnn_infer(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
+                    const double *rho, double *p0, void *stream);
+/* Attach (or detach with NULL) a network used by ns_step(..., warm = 2); the
+ * context does not own it.                                                 */
+ib_status ib_attach_cnn(ib_ctx *ctx, ib_cnn *net);
 
 /* Measurement hooks.  ib_launch_count: kernels launched by this library in
  * this process so far.  ib_profile_begin(kind) starts CUDA-event timing, on
@@ -166,6 +202,11 @@ ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
  * returns their summed duration (ms) and count.  Timing is process-wide and
  * not thread-safe; at most 16384 launches are recorded.                    */
 unsigned long long ib_launch_count(void);
+/* Solve with the captured CUDA graph (default, enable = 1) or with one launch
+ * per kernel and a host residual check per cycle (enable = 0); results are
+ * the same.  Kernels inside the graph's device-side loop cannot be timed
+ * one by one by events or kernel profilers, hence the switch.             */
+ib_status ib_use_graphs(ib_ctx *ctx, int enable);
 ib_status ib_profile_begin(int kind);
 ib_status ib_profile_end(double *total_ms, int *launches);
 

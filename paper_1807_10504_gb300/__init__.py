@@ -33,7 +33,9 @@ EXPORTS = [
     "ns_step", "ib_last_solve", "ib_save", "ib_load", "ib_op_coeffs", "ib_op_residual",
     "ib_op_rbgs", "ib_op_restrict_residual", "ib_op_prolong_add", "ib_op_coarsen_beta",
     "ib_op_rhs", "ib_op_correct", "ib_op_predictor", "ib_launch_count", "ib_profile_begin",
-    "ib_profile_end", "mg_solve_noalloc",
+    "ib_profile_end", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
+    "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
+    "ib_attach_cnn", "ib_use_graphs",
 ]
 
 
@@ -91,6 +93,12 @@ def lib():
             "ib_op_correct": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
             "mg_solve_noalloc": [_i32, _i32, _d, _P, _P, _P, _P, C.c_int, _d, C.c_int, C.c_int,
                                  C.c_int, C.POINTER(C.c_int), C.POINTER(_d), _P],
+            "cnn_init": [C.POINTER(_P), _i32, _i32, C.c_uint64, _P],
+            "cnn_get_params": [_P, _P, C.c_int64], "cnn_set_params": [_P, _P, C.c_int64],
+            "cnn_grad": [_P, _i32, _i32, _P, _P, _P, C.POINTER(C.c_float), _P, _P],
+            "cnn_train_step": [_P, _i32, _i32, _P, _P, _P, C.c_float, C.POINTER(C.c_float), _P],
+            "cnn_infer": [_P, _i32, _i32, _P, _P, _P, _P],
+            "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
         }
@@ -108,6 +116,10 @@ def lib():
         L.ib_profile_end.restype = C.c_int
         L.ib_launch_count.argtypes = []
         L.ib_launch_count.restype = C.c_ulonglong
+        L.cnn_destroy.argtypes = [_P]
+        L.cnn_destroy.restype = None
+        L.cnn_num_params.argtypes = [_P]
+        L.cnn_num_params.restype = C.c_int64
         L.ib_num_markers.argtypes = [_P]
         L.ib_num_markers.restype = _i32
         _lib = L
@@ -298,11 +310,73 @@ class Context:
         lib().ib_last_solve(self._h, C.byref(cyc), C.byref(rr))
         return cyc.value, rr.value
 
+    def use_graphs(self, enable: bool):
+        _check(lib().ib_use_graphs(self._h, int(enable)), self._h)
+
+    def attach(self, net):
+        """Use `net` (a Net) for ns_step(..., warm=2); None detaches."""
+        self._net = net
+        _check(lib().ib_attach_cnn(self._h, net._h if net is not None else None), self._h)
+
     def save(self, path):
         _check(lib().ib_save(self._h, str(path).encode()), self._h)
 
     def load(self, path):
         _check(lib().ib_load(self._h, str(path).encode()), self._h)
+
+
+# -------------------------------------------------------------- learned warm start
+class Net:
+    """The warm-start CNN (``cnn_*`` entry points): BF16 tensor-core forward
+    and backward kernels, FP32 master weights and Adam state on the device."""
+
+    def __init__(self, seed=0, c1=16, c2=32):
+        torch = _torch()
+        self._h = C.c_void_p()
+        st = lib().cnn_init(C.byref(self._h), c1, c2, seed,
+                            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        _check(st, None, "cnn_init")
+        self.nparam = int(lib().cnn_num_params(self._h))
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().cnn_destroy(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        _check(lib().cnn_get_params(self._h, out.ctypes.data, self.nparam), None, "cnn_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        _check(lib().cnn_set_params(self._h, flat.ctypes.data, self.nparam), None, "cnn_set_params")
+
+    def grad(self, rhs, rho, p):
+        B, N = rhs.shape[0], rhs.shape[-1]
+        loss = C.c_float(0.0)
+        g = np.empty(self.nparam, np.float32)
+        _check(lib().cnn_grad(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p), C.byref(loss),
+                              g.ctypes.data, _stream()), None, "cnn_grad")
+        return loss.value, g
+
+    def train_step(self, rhs, rho, p, lr=1e-3):
+        B, N = rhs.shape[0], rhs.shape[-1]
+        loss = C.c_float(0.0)
+        _check(lib().cnn_train_step(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p), lr,
+                                    C.byref(loss), _stream()), None, "cnn_train_step")
+        return loss.value
+
+    def infer(self, rhs, rho):
+        torch = _torch()
+        B, N = rhs.shape[0], rhs.shape[-1]
+        p0 = torch.empty((B, N, N), dtype=torch.float64, device="cuda")
+        _check(lib().cnn_infer(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p0), _stream()), None,
+               "cnn_infer")
+        return p0
 
 
 # -------------------------------------------------------------- no-allocation solve

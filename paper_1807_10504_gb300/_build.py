@@ -22,6 +22,7 @@ SOURCES = {
     "markers.cu": ["--fmad=false"],
     "api.cu": [],
     "noalloc.cu": [],
+    "cnn.cu": [],
 }
 
 

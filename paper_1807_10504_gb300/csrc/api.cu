@@ -27,6 +27,12 @@ struct ib_ctx {
     double last_relres = 0.0;
     bool mg_ready = false;
     uint32_t *flags_host = nullptr;
+    struct ib_cnn *cnn = nullptr;   // attached warm-start network (not owned)
+};
+
+struct ib_cnn {
+    ibk::Cnn *n = nullptr;
+    std::string err;
 };
 
 namespace {
@@ -353,7 +359,9 @@ ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, doubl
 
 ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
 {
-    if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 1) return IB_EINVAL;
+    if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 2) return IB_EINVAL;
+    if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % 4 != 0))
+        return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid (side % 4 == 0)");
     const ib_config &g = c->cfg;
     Markers &mk = c->mk;
     for (int it = 0; it < nsteps; it++) {
@@ -372,7 +380,13 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
         ib_status st = launch_check(c, "step");
         if (st != IB_OK) return st;
-        if (!warm) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
+        if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
+        if (warm == 2) {
+            cudaError_t ce = cnn_workspace(*c->cnn->n, 1, g.nx);
+            if (ce != cudaSuccess) return cuda_check(c, ce, "network workspace");
+            cnn_forward(*c->cnn->n, 1, g.nx, c->b, c->rho, nullptr, c->s);
+            cnn_output(*c->cnn->n, 1, g.nx, c->p, c->s);
+        }
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                     &c->last_cycles, &c->last_relres, c->s, c->err);
         if (st != IB_OK && st != IB_ENOTCONV) return st;
@@ -391,6 +405,13 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
 
 unsigned long long ib_launch_count(void) { return launch_count(); }
 
+ib_status ib_use_graphs(ib_ctx *c, int enable)
+{
+    if (!c) return IB_EINVAL;
+    c->mg.use_graphs = enable != 0;
+    return IB_OK;
+}
+
 ib_status ib_profile_begin(int kind)
 {
     if (kind < 0 || kind > 2) return IB_EINVAL;
@@ -407,6 +428,107 @@ ib_status ib_last_solve(const ib_ctx *c, int *cycles, double *relres)
     if (!c) return IB_EINVAL;
     if (cycles) *cycles = c->last_cycles;
     if (relres) *relres = c->last_relres;
+    return IB_OK;
+}
+
+// ------------------------------------------------------------- CNN warm start
+ib_status cnn_init(ib_cnn **out, int32_t c1, int32_t c2, uint64_t seed, void *stream)
+{
+    if (!out) return IB_EINVAL;
+    *out = nullptr;
+    if (c1 != 16 || c2 != 32) return IB_EINVAL;
+    cudaError_t e = cudaSuccess;
+    ibk::Cnn *n = ibk::cnn_new(c1, c2, seed, (cudaStream_t)stream, &e);
+    if (!n) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
+    e = ibk::cnn_pack(*n, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) { ibk::cnn_free(n); return IB_ECUDA; }
+    ib_cnn *h = new ib_cnn();
+    h->n = n;
+    *out = h;
+    return IB_OK;
+}
+
+void cnn_destroy(ib_cnn *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    ibk::cnn_free(h->n);
+    delete h;
+}
+
+int64_t cnn_num_params(const ib_cnn *h) { return h ? (int64_t)ibk::cnn_nparam(*h->n) : 0; }
+
+ib_status cnn_get_params(ib_cnn *h, float *host, int64_t n)
+{
+    if (!h || !host || n != (int64_t)ibk::cnn_nparam(*h->n)) return IB_EINVAL;
+    cudaError_t e = cudaMemcpy(host, ibk::cnn_weights(*h->n), (size_t)n * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status cnn_set_params(ib_cnn *h, const float *host, int64_t n)
+{
+    if (!h || !host || n != (int64_t)ibk::cnn_nparam(*h->n)) return IB_EINVAL;
+    cudaError_t e = cudaMemcpy(ibk::cnn_weights(*h->n), host, (size_t)n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = ibk::cnn_pack(*h->n, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    ibk::cnn_reset_adam(*h->n);
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+static ib_status cnn_fb(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
+                        const double *p, float *loss, cudaStream_t s)
+{
+    if (!h || B < 1 || N < 4 || N % 4 || !rhs || !rho || !p) return IB_EINVAL;
+    cudaError_t e = ibk::cnn_workspace(*h->n, B, N);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
+    ibk::cnn_forward(*h->n, B, N, rhs, rho, p, s);
+    ibk::cnn_backward(*h->n, B, N, s);
+    if (loss) {
+        std::vector<float> ls(B);
+        e = cudaMemcpyAsync(ls.data(), ibk::cnn_lsum(*h->n), B * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float t = 0.0f;
+        for (float v : ls) t += v;
+        *loss = t;
+    }
+    return cudaGetLastError() == cudaSuccess && e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status cnn_grad(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
+                   const double *p, float *loss, float *grads_host, void *stream)
+{
+    ib_status st = cnn_fb(h, B, N, rhs, rho, p, loss, (cudaStream_t)stream);
+    if (st != IB_OK || !grads_host) return st;
+    cudaError_t e = cudaMemcpy(grads_host, ibk::cnn_grads(*h->n), ibk::cnn_nparam(*h->n) * 4,
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status cnn_train_step(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
+                         const double *p, float lr, float *loss, void *stream)
+{
+    ib_status st = cnn_fb(h, B, N, rhs, rho, p, loss, (cudaStream_t)stream);
+    if (st != IB_OK) return st;
+    ibk::cnn_adam(*h->n, lr, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
+                    double *p0, void *stream)
+{
+    if (!h || B < 1 || N < 4 || N % 4 || !rhs || !rho || !p0) return IB_EINVAL;
+    cudaError_t e = ibk::cnn_workspace(*h->n, B, N);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
+    ibk::cnn_forward(*h->n, B, N, rhs, rho, nullptr, (cudaStream_t)stream);
+    ibk::cnn_output(*h->n, B, N, p0, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status ib_attach_cnn(ib_ctx *c, ib_cnn *h)
+{
+    if (!c) return IB_EINVAL;
+    c->cnn = h;
     return IB_OK;
 }
 

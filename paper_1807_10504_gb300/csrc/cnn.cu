@@ -1,0 +1,773 @@
+// Learned warm start for the pressure solve: a small 3-level encoder/decoder
+// CNN (16/32 channels) on BF16 activations and weights with FP32 accumulation,
+// trained on the GPU by these kernels (forward, backward-data,
+// backward-weight, loss, Adam).  The network maps (b / s, (1/rho) / max) to
+// p / s, s the rms of the mean-free right-hand side; the multigrid solve then
+// continues from s * (y - mean y) to the requested residual.
+//
+// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
+// BF16 in, FP32 accumulate): an 8 x 16 output tile (M = 128 pixels) per CTA,
+// the input tile with its 1-pixel halo and all weights staged in shared
+// memory with padded strides (conflict-free fragment loads), K = 9 taps x
+// input channels.  Activations are NHWC with channel counts padded to 16.
+// The weight gradient is split over pixel chunks and reduced in a fixed
+// order, so training is deterministic.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <vector>
+
+#include "ib_internal.cuh"
+
+namespace ibk {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int CH = 8, CW = 16;  // conv output tile: 8 rows x 16 columns
+
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// keep each bf16 half of v where the matching half of the mask is > 0
+__device__ __forceinline__ uint32_t relu_mask(uint32_t v, uint32_t m)
+{
+    uint32_t r = 0;
+    if ((m & 0x8000u) == 0 && (m & 0x7fffu) != 0) r |= v & 0xffffu;
+    if ((m & 0x80000000u) == 0 && (m & 0x7fff0000u) != 0) r |= v & 0xffff0000u;
+    return r;
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv_smem()
+{
+    return ((size_t)(CH + 2) * (CW + 2) * (CIN + 8) + (size_t)COUT * (9 * CIN + 8)) * 2;
+}
+
+// y = act(conv3x3(x * [xmask > 0]) + bias), NHWC, zero padding.
+// w: [COUT][9][CIN] (tap = 3 dy + dx multiplies x[i + dy - 1, j + dx - 1]).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+k_conv_fwd(int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xmask,
+           const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
+           bf16 *__restrict__ y, float *__restrict__ y32)
+{
+    constexpr int XS = CIN + 8, WS = 9 * CIN + 8, NT = COUT / 8;
+    extern __shared__ __align__(16) unsigned char conv_sm[];
+    bf16 *xs = (bf16 *)conv_sm;
+    bf16 *ws = xs + (CH + 2) * (CW + 2) * XS;
+    const int bz = blockIdx.z, ty0 = blockIdx.y * CH, tx0 = blockIdx.x * CW;
+    for (int k = threadIdx.x; k < (CH + 2) * (CW + 2) * (CIN / 2); k += 128) {
+        const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
+        const int r = pix / (CW + 2), c = pix - r * (CW + 2);
+        const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+        uint32_t v = 0;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            const long off = (((long)bz * H + gy) * W + gx) * CIN + 2 * cp;
+            v = *(const uint32_t *)(x + off);
+            if (xmask) v = relu_mask(v, *(const uint32_t *)(xmask + off));
+        }
+        *(uint32_t *)(xs + pix * XS + 2 * cp) = v;
+    }
+    for (int k = threadIdx.x; k < COUT * (9 * CIN / 2); k += 128) {
+        const int co = k / (9 * CIN / 2), q = k - co * (9 * CIN / 2);
+        *(uint32_t *)(ws + co * WS + 2 * q) = *(const uint32_t *)(w + (long)co * 9 * CIN + 2 * q);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < NT; b++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[a][b][q] = 0.0f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+        for (int c0 = 0; c0 < CIN; c0 += 16) {
+            uint32_t bf[NT][2];
+#pragma unroll
+            for (int nt = 0; nt < NT; nt++) {
+                const bf16 *wp = ws + (nt * 8 + g) * WS + tap * CIN + c0 + 2 * t4;
+                bf[nt][0] = *(const uint32_t *)wp;
+                bf[nt][1] = *(const uint32_t *)(wp + 8);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) {
+                const int r = 2 * warp + mt;
+                const bf16 *xa = xs + ((r + dy) * (CW + 2) + g + dx) * XS + c0 + 2 * t4;
+                const bf16 *xb = xa + 8 * XS;
+                uint32_t af[4];
+                af[0] = *(const uint32_t *)xa;
+                af[1] = *(const uint32_t *)xb;
+                af[2] = *(const uint32_t *)(xa + 8);
+                af[3] = *(const uint32_t *)(xb + 8);
+#pragma unroll
+                for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], af, bf[nt]);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+        const int oy = ty0 + 2 * warp + mt;
+        if (oy >= H) continue;
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            const int co = nt * 8 + 2 * t4;
+            const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int ox = tx0 + g + 8 * half;
+                if (ox >= W) continue;
+                float v0 = acc[mt][nt][2 * half] + b0, v1 = acc[mt][nt][2 * half + 1] + b1;
+                if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                const long off = (((long)bz * H + oy) * W + ox) * COUT + co;
+                *(__nv_bfloat162 *)(y + off) = __floats2bfloat162_rn(v0, v1);
+                if (y32) { y32[off] = v0; y32[off + 1] = v1; }
+            }
+        }
+    }
+}
+
+// Partial weight (and bias) gradients of one tap over a chunk of output
+// tiles: dW[co][tap][ci] += sum_p g[p][co] x[p + tap][ci], with
+// g = gy * [ymask > 0].  M = COUT, N = CIN, K = pixels (16 per step).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+k_conv_dw(int B, int H, int W, int tiles_per_chunk, const bf16 *__restrict__ x,
+          const bf16 *__restrict__ gy, const bf16 *__restrict__ ymask,
+          float *__restrict__ part_w, float *__restrict__ part_b)
+{
+    constexpr int XS = CIN + 8, GS = COUT + 8, MT = COUT / 16, NT = CIN / 8;
+    constexpr int FR = MT * NT;                 // fragments per tap
+    constexpr int FPW = (FR + 3) / 4;           // fragments per warp
+    __shared__ __align__(16) bf16 xs[(CH + 2) * (CW + 2) * XS];
+    __shared__ __align__(16) bf16 gs[CH * CW * GS];
+    const int tap = blockIdx.x, chunk = blockIdx.y;
+    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+    const int tw = (W + CW - 1) / CW, th = (H + CH - 1) / CH, ntiles = B * tw * th;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    float acc[FPW][4];
+#pragma unroll
+    for (int f = 0; f < FPW; f++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[f][q] = 0.0f;
+    float bacc = 0.0f;  // bias partial of channel threadIdx.x (tap 0 only)
+    for (int tl = chunk * tiles_per_chunk; tl < min(ntiles, (chunk + 1) * tiles_per_chunk); tl++) {
+        const int bz = tl / (tw * th), rem = tl - bz * tw * th;
+        const int ty0 = (rem / tw) * CH, tx0 = (rem - (rem / tw) * tw) * CW;
+        __syncthreads();
+        for (int k = threadIdx.x; k < (CH + 2) * (CW + 2) * (CIN / 2); k += 128) {
+            const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
+            const int r = pix / (CW + 2), c = pix - r * (CW + 2);
+            const int yy = ty0 + r - 1, xx = tx0 + c - 1;
+            uint32_t v = 0;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = *(const uint32_t *)(x + (((long)bz * H + yy) * W + xx) * CIN + 2 * cp);
+            *(uint32_t *)(xs + pix * XS + 2 * cp) = v;
+        }
+        for (int k = threadIdx.x; k < CH * CW * (COUT / 2); k += 128) {
+            const int pix = k / (COUT / 2), cp = k - pix * (COUT / 2);
+            const int r = pix / CW, c = pix - r * CW;
+            const int yy = ty0 + r, xx = tx0 + c;
+            uint32_t v = 0;
+            if (yy < H && xx < W) {
+                const long off = (((long)bz * H + yy) * W + xx) * COUT + 2 * cp;
+                v = *(const uint32_t *)(gy + off);
+                if (ymask) v = relu_mask(v, *(const uint32_t *)(ymask + off));
+            }
+            *(uint32_t *)(gs + pix * GS + 2 * cp) = v;
+        }
+        __syncthreads();
+        if (tap == 0 && threadIdx.x < COUT)
+            for (int pix = 0; pix < CH * CW; pix++) bacc += __bfloat162float(gs[pix * GS + threadIdx.x]);
+#pragma unroll
+        for (int f = 0; f < FPW; f++) {
+            const int fr = warp * FPW + f;
+            if (fr >= FR) break;
+            const int mt = fr / NT, nt = fr - mt * NT;
+            const int co = mt * 16 + g, ci = nt * 8 + g;
+#pragma unroll 2
+            for (int r = 0; r < CH; r++) {  // K step = the 16 pixels of output row r
+                const bf16 *ga = gs + (r * CW) * GS;
+                const int p0 = 2 * t4, p1 = 2 * t4 + 1, p2 = 2 * t4 + 8, p3 = 2 * t4 + 9;
+                __nv_bfloat162 a0, a1, a2, a3;
+                a0.x = ga[p0 * GS + co];       a0.y = ga[p1 * GS + co];
+                a1.x = ga[p0 * GS + co + 8];   a1.y = ga[p1 * GS + co + 8];
+                a2.x = ga[p2 * GS + co];       a2.y = ga[p3 * GS + co];
+                a3.x = ga[p2 * GS + co + 8];   a3.y = ga[p3 * GS + co + 8];
+                uint32_t af[4] = {*(uint32_t *)&a0, *(uint32_t *)&a1, *(uint32_t *)&a2, *(uint32_t *)&a3};
+                const bf16 *xb = xs + ((r + dy) * (CW + 2) + dx) * XS + ci;
+                __nv_bfloat162 b0, b1;
+                b0.x = xb[p0 * XS]; b0.y = xb[p1 * XS];
+                b1.x = xb[p2 * XS]; b1.y = xb[p3 * XS];
+                uint32_t bf[2] = {*(uint32_t *)&b0, *(uint32_t *)&b1};
+                mma_bf16(acc[f], af, bf);
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < FPW; f++) {
+        const int fr = warp * FPW + f;
+        if (fr >= FR) break;
+        const int mt = fr / NT, nt = fr - mt * NT;
+        // C fragment: rows co (g, g+8), columns ci (2 t4, 2 t4 + 1)
+        const int co0 = mt * 16 + g, ci0 = nt * 8 + 2 * t4;
+        float *pw = part_w + (long)chunk * COUT * 9 * CIN;
+        pw[(long)co0 * 9 * CIN + tap * CIN + ci0] = acc[f][0];
+        pw[(long)co0 * 9 * CIN + tap * CIN + ci0 + 1] = acc[f][1];
+        pw[(long)(co0 + 8) * 9 * CIN + tap * CIN + ci0] = acc[f][2];
+        pw[(long)(co0 + 8) * 9 * CIN + tap * CIN + ci0 + 1] = acc[f][3];
+    }
+    if (tap == 0 && threadIdx.x < COUT) part_b[(long)chunk * COUT + threadIdx.x] = bacc;
+}
+
+// Sum of the chunk partials in chunk order.
+__global__ void k_reduce_parts(int nchunks, long n, const float *__restrict__ part,
+                               float *__restrict__ out)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float s = 0.0f;
+    for (int c = 0; c < nchunks; c++) s += part[(long)c * n + k];
+    out[k] = s;
+}
+
+// --- layout helpers (bf16 NHWC) -----------------------------------------
+__global__ void k_pool2(long nout, int H2, int W2, int C, const bf16 *__restrict__ x,
+                        bf16 *__restrict__ y)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nout) return;
+    const int c = (int)(k % C);
+    long p = k / C;
+    const int j = (int)(p % W2);
+    p /= W2;
+    const int i = (int)(p % H2);
+    const long b = p / H2;
+    const int W = 2 * W2;
+    const long base = ((b * (2 * H2) + 2 * i) * W + 2 * j) * C + c;
+    float s = __bfloat162float(x[base]) + __bfloat162float(x[base + C]) +
+              __bfloat162float(x[base + (long)W * C]) + __bfloat162float(x[base + (long)W * C + C]);
+    y[k] = __float2bfloat16_rn(0.25f * s);
+}
+
+// out = [up2(t) | s] along channels (t: C1 at half resolution, s: C2)
+__global__ void k_up_cat(long nout, int H, int W, int C1, int C2, const bf16 *__restrict__ t,
+                         const bf16 *__restrict__ s, bf16 *__restrict__ out)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nout) return;
+    const int C = C1 + C2, c = (int)(k % C);
+    long p = k / C;
+    const int j = (int)(p % W);
+    p /= W;
+    const int i = (int)(p % H);
+    const long b = p / H;
+    out[k] = c < C1 ? t[((b * (H / 2) + i / 2) * (W / 2) + j / 2) * C1 + c]
+                    : s[((b * H + i) * W + j) * C2 + (c - C1)];
+}
+
+// gt = sum over 2x2 of g[..., :C1];  gs = g[..., C1:] (+ gs_add)
+__global__ void k_up_cat_bwd(long nhalf, int H2, int W2, int C1, int C2, const bf16 *__restrict__ g,
+                             bf16 *__restrict__ gt)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nhalf) return;
+    const int c = (int)(k % C1);
+    long p = k / C1;
+    const int j = (int)(p % W2);
+    p /= W2;
+    const int i = (int)(p % H2);
+    const long b = p / H2;
+    const int W = 2 * W2, C = C1 + C2;
+    const long base = ((b * (2 * H2) + 2 * i) * W + 2 * j) * C + c;
+    float s = __bfloat162float(g[base]) + __bfloat162float(g[base + C]) +
+              __bfloat162float(g[base + (long)W * C]) + __bfloat162float(g[base + (long)W * C + C]);
+    gt[k] = __float2bfloat16_rn(s);
+}
+
+// gskip = g_cat[..., C1:] + pool2_bwd(gp)   (gp at half resolution, C2 channels)
+__global__ void k_skip_grad(long n, int H, int W, int C1, int C2, const bf16 *__restrict__ gcat,
+                            const bf16 *__restrict__ gp, bf16 *__restrict__ gskip)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = (int)(k % C2);
+    long p = k / C2;
+    const int j = (int)(p % W);
+    p /= W;
+    const int i = (int)(p % H);
+    const long b = p / H;
+    float v = __bfloat162float(gcat[((b * H + i) * W + j) * (C1 + C2) + C1 + c]);
+    v += 0.25f * __bfloat162float(gp[((b * (H / 2) + i / 2) * (W / 2) + j / 2) * C2 + c]);
+    gskip[k] = __float2bfloat16_rn(v);
+}
+
+// --- features, loss, output ----------------------------------------------
+// Per sample: mean of b, rms s of (b - mean), max of 1/rho; one CTA per sample.
+__global__ void __launch_bounds__(256)
+k_sample_stats(int N2, const double *__restrict__ b, const double *__restrict__ rho,
+               double *__restrict__ stats)
+{
+    __shared__ double sh[3][256];
+    const double *bb = b + (long)blockIdx.x * N2, *rr = rho + (long)blockIdx.x * N2;
+    double s = 0.0, mx = 0.0;
+    for (int k = threadIdx.x; k < N2; k += 256) { s += bb[k]; mx = fmax(mx, 1.0 / rr[k]); }
+    sh[0][threadIdx.x] = s; sh[2][threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    const double mean = sh[0][0] / N2;
+    double q = 0.0;
+    for (int k = threadIdx.x; k < N2; k += 256) { double d = bb[k] - mean; q += d * d; }
+    __syncthreads();
+    sh[1][threadIdx.x] = q;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double r = sqrt(sh[1][0] / N2);
+        stats[3 * blockIdx.x + 0] = mean;
+        stats[3 * blockIdx.x + 1] = r > 0.0 ? r : 1.0;
+        stats[3 * blockIdx.x + 2] = sh[2][0];
+    }
+}
+
+// x[..., 0] = (b - mean)/s, x[..., 1] = (1/rho)/max, other channels 0; and
+// (training) t = p / s.
+__global__ void k_features(long n, int N2, const double *__restrict__ b, const double *__restrict__ rho,
+                           const double *__restrict__ p, const double *__restrict__ stats,
+                           bf16 *__restrict__ x, float *__restrict__ t)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long smp = k / N2;
+    const double mean = stats[3 * smp], s = stats[3 * smp + 1], mx = stats[3 * smp + 2];
+    __nv_bfloat162 v = __floats2bfloat162_rn((float)((b[k] - mean) / s), (float)((1.0 / rho[k]) / mx));
+    uint32_t *xp = (uint32_t *)(x + k * 16);
+    xp[0] = *(uint32_t *)&v;
+#pragma unroll
+    for (int q = 1; q < 8; q++) xp[q] = 0u;
+    if (t) t[k] = (float)(p[k] / s);
+}
+
+// Mean-removed squared error per sample (one CTA per sample): loss partial and
+// the gradient 2 d / (B n) minus its mean, written as BF16 channel 0 of a
+// 16-channel tensor.
+__global__ void __launch_bounds__(256)
+k_loss(int N2, int Bn, const float *__restrict__ y32, const float *__restrict__ t,
+       bf16 *__restrict__ gy, float *__restrict__ lsum)
+{
+    __shared__ float sh[2][256];
+    const long base = (long)blockIdx.x * N2;
+    float sy = 0.0f, st = 0.0f;
+    for (int k = threadIdx.x; k < N2; k += 256) { sy += y32[(base + k) * 16]; st += t[base + k]; }
+    sh[0][threadIdx.x] = sy; sh[1][threadIdx.x] = st;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) { sh[0][threadIdx.x] += sh[0][threadIdx.x + o]; sh[1][threadIdx.x] += sh[1][threadIdx.x + o]; }
+        __syncthreads();
+    }
+    const float my = sh[0][0] / N2, mt = sh[1][0] / N2;
+    __syncthreads();
+    float l = 0.0f, gs = 0.0f;
+    const float sc = 2.0f / ((float)Bn * (float)N2);
+    for (int k = threadIdx.x; k < N2; k += 256) {
+        float d = (y32[(base + k) * 16] - my) - (t[base + k] - mt);
+        l += d * d;
+        gs += sc * d;
+    }
+    sh[0][threadIdx.x] = l; sh[1][threadIdx.x] = gs;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) { sh[0][threadIdx.x] += sh[0][threadIdx.x + o]; sh[1][threadIdx.x] += sh[1][threadIdx.x + o]; }
+        __syncthreads();
+    }
+    const float gmean = sh[1][0] / N2;
+    for (int k = threadIdx.x; k < N2; k += 256) {
+        float d = (y32[(base + k) * 16] - my) - (t[base + k] - mt);
+        uint32_t *gp = (uint32_t *)(gy + (base + k) * 16);
+        __nv_bfloat162 v = __floats2bfloat162_rn(sc * d - gmean, 0.0f);
+        gp[0] = *(uint32_t *)&v;
+#pragma unroll
+        for (int q = 1; q < 8; q++) gp[q] = 0u;
+    }
+    if (threadIdx.x == 0) lsum[blockIdx.x] = sh[0][0] / ((float)Bn * (float)N2);
+}
+
+// p0 = s (y - mean y), FP64 out; one CTA per sample.
+__global__ void __launch_bounds__(256)
+k_output(int N2, const float *__restrict__ y32, const double *__restrict__ stats, double *__restrict__ p0)
+{
+    __shared__ double sh[256];
+    const long base = (long)blockIdx.x * N2;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < N2; k += 256) s += y32[(base + k) * 16];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double my = sh[0] / N2, sc = stats[3 * blockIdx.x + 1];
+    for (int k = threadIdx.x; k < N2; k += 256) p0[base + k] = sc * ((double)y32[(base + k) * 16] - my);
+}
+
+// Adam with bias correction on FP32 master weights.
+__global__ void k_adam(long n, float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.0f - b1) * gk, vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    w[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+// Master [co][3][3][ci] FP32 -> forward BF16 [COP][9][CIP] (zero padded) and
+// backward-data BF16 [CIP][9][COP] with the taps flipped.
+__global__ void k_pack(int ci, int co, int cip, int cop, const float *__restrict__ w,
+                       bf16 *__restrict__ wf, bf16 *__restrict__ wb)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cop * 9 * cip) return;
+    const int o = k / (9 * cip), r = k - o * 9 * cip, tap = r / cip, i = r - tap * cip;
+    const float v = (o < co && i < ci) ? w[((long)o * 9 + tap) * ci + i] : 0.0f;
+    wf[k] = __float2bfloat16_rn(v);
+    if (wb) wb[((long)i * 9 + (8 - tap)) * cop + o] = __float2bfloat16_rn(v);
+}
+
+// Padded gradients [COP][9][CIP] and [COP] -> master layout [co][9][ci], [co].
+__global__ void k_unpack_grad(int ci, int co, int cip, const float *__restrict__ gpw,
+                              const float *__restrict__ gpb, float *__restrict__ gw,
+                              float *__restrict__ gb)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < co) gb[k] = gpb[k];
+    if (k >= co * 9 * ci) return;
+    const int o = k / (9 * ci), r = k - o * 9 * ci, tap = r / ci, i = r - tap * ci;
+    gw[k] = gpw[((long)o * 9 + tap) * cip + i];
+}
+
+}  // namespace
+
+// ======================================================================= host
+struct CnnLayer {
+    int ci, co, cip, cop;     // real and padded channel counts
+    bool relu;
+    size_t woff, boff;        // offsets in the flat FP32 parameter vector
+    size_t pwoff, pboff;      // offsets of the padded gradients [COP][9][CIP], [COP]
+    bf16 *wf = nullptr, *wb = nullptr;
+};
+
+struct Cnn {
+    int c1 = 16, c2 = 32;
+    std::vector<CnnLayer> L;
+    size_t nparam = 0, npad = 0;
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // flat FP32
+    void *wmem = nullptr;
+    int step = 0;
+    // activation workspace, sized for B x N x N
+    int capB = 0, capN = 0;
+    void *amem = nullptr;
+    bf16 *x = nullptr, *a1 = nullptr, *s1 = nullptr, *p1 = nullptr, *a2 = nullptr, *s2 = nullptr,
+         *p2 = nullptr, *a3 = nullptr, *t3 = nullptr, *cat4 = nullptr, *t4 = nullptr,
+         *cat5 = nullptr, *a5 = nullptr, *y = nullptr, *gbig = nullptr, *gbig2 = nullptr,
+         *gmid = nullptr, *gmid2 = nullptr, *gsmall = nullptr, *gsmall2 = nullptr, *gcat = nullptr,
+         *gup = nullptr;
+    float *y32 = nullptr, *t = nullptr, *lsum = nullptr, *gpad = nullptr, *part = nullptr;
+    double *stats = nullptr;
+    size_t part_cap = 0;
+};
+
+namespace {
+
+template <int CIN, int COUT>
+void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
+              const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
+{
+    constexpr size_t sm = conv_smem<CIN, COUT>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv_fwd<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    dim3 g(cdiv(W, CW), cdiv(H, CH), B);
+    note_launch();
+    k_conv_fwd<CIN, COUT><<<g, 128, sm, s>>>(H, W, x, xmask, w, bias, relu, y, y32);
+}
+
+template <int CIN, int COUT>
+void conv_dw(Cnn &n, int B, int H, int W, const bf16 *x, const bf16 *gy, const bf16 *ymask,
+             float *gw_pad, float *gb, cudaStream_t s)
+{
+    const int ntiles = B * (int)cdiv(W, CW) * (int)cdiv(H, CH);
+    const int nchunks = std::min(ntiles, 64);
+    const int tpc = (ntiles + nchunks - 1) / nchunks;
+    float *pw = n.part, *pb = n.part + (size_t)nchunks * COUT * 9 * CIN;
+    dim3 g(9, nchunks);
+    note_launch();
+    k_conv_dw<CIN, COUT><<<g, 128, 0, s>>>(B, H, W, tpc, x, gy, ymask, pw, pb);
+    const long nw = (long)COUT * 9 * CIN;
+    note_launch();
+    k_reduce_parts<<<cdiv(nw, 256), 256, 0, s>>>(nchunks, nw, pw, gw_pad);
+    note_launch();
+    k_reduce_parts<<<1, 256, 0, s>>>(nchunks, COUT, pb, gb);
+}
+
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+Cnn *cnn_new(int c1, int c2, unsigned long long seed, cudaStream_t s, cudaError_t *err)
+{
+    (void)s;
+    Cnn *n = new Cnn();
+    n->c1 = c1;
+    n->c2 = c2;
+    auto pad = [](int c) { return (c + 15) / 16 * 16; };
+    const int spec[9][3] = {{2, c1, 1}, {c1, c1, 1}, {c1, c2, 1}, {c2, c2, 1}, {c2, c2, 1},
+                            {c2, c2, 1}, {2 * c2, c2, 1}, {c2 + c1, c1, 1}, {c1, 1, 0}};
+    size_t off = 0;
+    for (auto &sp : spec) {
+        CnnLayer l;
+        l.ci = sp[0]; l.co = sp[1]; l.relu = sp[2] != 0;
+        l.cip = pad(l.ci); l.cop = pad(l.co);
+        l.woff = off; off += (size_t)l.co * 9 * l.ci;
+        l.boff = off; off += (size_t)l.co;
+        n->L.push_back(l);
+    }
+    n->nparam = off;
+    size_t po = 0;
+    for (auto &l : n->L) {
+        l.pwoff = po; po += (size_t)l.cop * 9 * l.cip;
+        l.pboff = po; po += (size_t)l.cop;
+    }
+    n->npad = po;
+    size_t bytes = al(off * 4) * 4;
+    for (auto &l : n->L) bytes += 2 * al((size_t)l.cop * 9 * l.cip * 2);
+    *err = cudaMalloc(&n->wmem, bytes);
+    if (*err != cudaSuccess) { n->wmem = nullptr; cnn_free(n); return nullptr; }
+    char *q = (char *)n->wmem;
+    auto take = [&](size_t b) { char *r = q; q += al(b); return (void *)r; };
+    n->w = (float *)take(off * 4); n->m = (float *)take(off * 4);
+    n->v = (float *)take(off * 4); n->g = (float *)take(off * 4);
+    for (auto &l : n->L) {
+        l.wf = (bf16 *)take((size_t)l.cop * 9 * l.cip * 2);
+        l.wb = (bf16 *)take((size_t)l.cop * 9 * l.cip * 2);
+    }
+    // He-normal initial weights (Box-Muller on a splitmix64 stream), zero biases
+    std::vector<float> h(off, 0.0f);
+    unsigned long long st = seed ^ 0x9E3779B97F4A7C15ULL;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ULL;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return (double)((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (auto &l : n->L) {
+        const double sd = sqrt(2.0 / (9.0 * l.ci));
+        for (size_t k = 0; k < (size_t)l.co * 9 * l.ci; k++) {
+            double u1 = next(), u2 = next();
+            if (u1 < 1e-300) u1 = 1e-300;
+            h[l.woff + k] = (float)(sd * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+        }
+    }
+    *err = cudaMemcpy(n->w, h.data(), off * 4, cudaMemcpyHostToDevice);
+    if (*err == cudaSuccess) *err = cudaMemset(n->m, 0, off * 4 * 3);
+    if (*err != cudaSuccess) { cnn_free(n); return nullptr; }
+    return n;
+}
+
+void cnn_free(Cnn *n)
+{
+    if (!n) return;
+    if (n->wmem) cudaFree(n->wmem);
+    if (n->amem) cudaFree(n->amem);
+    delete n;
+}
+
+cudaError_t cnn_pack(Cnn &n, cudaStream_t s)
+{
+    for (auto &l : n.L) {
+        int tot = l.cop * 9 * l.cip;
+        note_launch();
+        k_pack<<<cdiv(tot, 256), 256, 0, s>>>(l.ci, l.co, l.cip, l.cop, n.w + l.woff, l.wf, l.wb);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_workspace(Cnn &n, int B, int N)
+{
+    if (B <= n.capB && N <= n.capN && n.amem) return cudaSuccess;
+    if (n.amem) cudaFree(n.amem);
+    n.amem = nullptr;
+    const size_t P = (size_t)B * N * N, P2 = P / 4, P4 = P / 16;
+    const int c1 = n.c1, c2 = n.c2;
+    size_t bytes = al(P * 16 * 2) +                       // x
+                   al(P * c1 * 2) * 2 +                    // a1, s1
+                   al(P2 * c1 * 2) + al(P2 * c2 * 2) * 2 + // p1, a2, s2
+                   al(P4 * c2 * 2) * 3 +                   // p2, a3, t3
+                   al(P2 * 2 * c2 * 2) + al(P2 * c2 * 2) + // cat4, t4
+                   al(P * (c1 + c2) * 2) + al(P * c1 * 2) + al(P * 16 * 2) +  // cat5, a5, y
+                   al(P * 64 * 2) * 2 + al(P2 * 64 * 2) * 2 + al(P4 * 64 * 2) * 2 +  // grads
+                   al(P * 64 * 2) + al(P2 * 64 * 2) +      // gcat, gup
+                   al(P * 16 * 4) + al(P * 4) + al(B * 4) + al(n.npad * 4) + al(B * 3 * 8);
+    const size_t part = (size_t)64 * (64 * 9 * 64 + 64);
+    bytes += al(part * 4);
+    cudaError_t e = cudaMalloc(&n.amem, bytes);
+    if (e != cudaSuccess) { n.amem = nullptr; return e; }
+    char *q = (char *)n.amem;
+    auto take = [&](size_t b) { char *r = q; q += al(b); return (void *)r; };
+    n.x = (bf16 *)take(P * 16 * 2);
+    n.a1 = (bf16 *)take(P * c1 * 2); n.s1 = (bf16 *)take(P * c1 * 2);
+    n.p1 = (bf16 *)take(P2 * c1 * 2); n.a2 = (bf16 *)take(P2 * c2 * 2); n.s2 = (bf16 *)take(P2 * c2 * 2);
+    n.p2 = (bf16 *)take(P4 * c2 * 2); n.a3 = (bf16 *)take(P4 * c2 * 2); n.t3 = (bf16 *)take(P4 * c2 * 2);
+    n.cat4 = (bf16 *)take(P2 * 2 * c2 * 2); n.t4 = (bf16 *)take(P2 * c2 * 2);
+    n.cat5 = (bf16 *)take(P * (c1 + c2) * 2); n.a5 = (bf16 *)take(P * c1 * 2);
+    n.y = (bf16 *)take(P * 16 * 2);
+    n.gbig = (bf16 *)take(P * 64 * 2); n.gbig2 = (bf16 *)take(P * 64 * 2);
+    n.gmid = (bf16 *)take(P2 * 64 * 2); n.gmid2 = (bf16 *)take(P2 * 64 * 2);
+    n.gsmall = (bf16 *)take(P4 * 64 * 2); n.gsmall2 = (bf16 *)take(P4 * 64 * 2);
+    n.gcat = (bf16 *)take(P * 64 * 2); n.gup = (bf16 *)take(P2 * 64 * 2);
+    n.y32 = (float *)take(P * 16 * 4); n.t = (float *)take(P * 4); n.lsum = (float *)take(B * 4);
+    n.gpad = (float *)take(n.npad * 4);
+    n.stats = (double *)take(B * 3 * 8);
+    n.part = (float *)take(part * 4);
+    n.part_cap = part;
+    n.capB = B;
+    n.capN = N;
+    return cudaSuccess;
+}
+
+// Forward pass on B samples of N x N (N a multiple of 4).  Fills the
+// activation workspace; y32 holds the output in channel 0 of 16.
+void cnn_forward(Cnn &n, int B, int N, const double *rhs, const double *rho, const double *p,
+                 cudaStream_t s)
+{
+    const int N2 = N * N, H2 = N / 2, H4 = N / 4;
+    const long P = (long)B * N2;
+    note_launch();
+    k_sample_stats<<<B, 256, 0, s>>>(N2, rhs, rho, n.stats);
+    note_launch();
+    k_features<<<cdiv(P, 256), 256, 0, s>>>(P, N2, rhs, rho, p, n.stats, n.x, p ? n.t : nullptr);
+    auto &L = n.L;
+    auto bias = [&](int k) { return n.w + L[k].boff; };
+    conv_fwd<16, 16>(B, N, N, n.x, nullptr, L[0].wf, bias(0), 1, n.a1, nullptr, s);
+    conv_fwd<16, 16>(B, N, N, n.a1, nullptr, L[1].wf, bias(1), 1, n.s1, nullptr, s);
+    note_launch();
+    k_pool2<<<cdiv((long)B * H2 * H2 * 16, 256), 256, 0, s>>>((long)B * H2 * H2 * 16, H2, H2, 16, n.s1, n.p1);
+    conv_fwd<16, 32>(B, H2, H2, n.p1, nullptr, L[2].wf, bias(2), 1, n.a2, nullptr, s);
+    conv_fwd<32, 32>(B, H2, H2, n.a2, nullptr, L[3].wf, bias(3), 1, n.s2, nullptr, s);
+    note_launch();
+    k_pool2<<<cdiv((long)B * H4 * H4 * 32, 256), 256, 0, s>>>((long)B * H4 * H4 * 32, H4, H4, 32, n.s2, n.p2);
+    conv_fwd<32, 32>(B, H4, H4, n.p2, nullptr, L[4].wf, bias(4), 1, n.a3, nullptr, s);
+    conv_fwd<32, 32>(B, H4, H4, n.a3, nullptr, L[5].wf, bias(5), 1, n.t3, nullptr, s);
+    note_launch();
+    k_up_cat<<<cdiv((long)B * H2 * H2 * 64, 256), 256, 0, s>>>((long)B * H2 * H2 * 64, H2, H2, 32, 32, n.t3, n.s2, n.cat4);
+    conv_fwd<64, 32>(B, H2, H2, n.cat4, nullptr, L[6].wf, bias(6), 1, n.t4, nullptr, s);
+    note_launch();
+    k_up_cat<<<cdiv(P * 48, 256), 256, 0, s>>>(P * 48, N, N, 32, 16, n.t4, n.s1, n.cat5);
+    conv_fwd<48, 16>(B, N, N, n.cat5, nullptr, L[7].wf, bias(7), 1, n.a5, nullptr, s);
+    conv_fwd<16, 16>(B, N, N, n.a5, nullptr, L[8].wf, bias(8), 0, n.y, n.y32, s);
+}
+
+// Loss and gradients of every parameter (into n.g, master layout).
+void cnn_backward(Cnn &n, int B, int N, cudaStream_t s)
+{
+    const int N2 = N * N, H2 = N / 2, H4 = N / 4;
+    const long P = (long)B * N2;
+    auto &L = n.L;
+    note_launch();
+    k_loss<<<B, 256, 0, s>>>(N2, B, n.y32, n.t, n.gbig, n.lsum);
+    float *gp = n.gpad;
+    auto dwb = [&](int k) { return std::make_pair(gp + L[k].pwoff, gp + L[k].pboff); };
+    auto unpack = [&](int k) {
+        const int tot = std::max(L[k].co * 9 * L[k].ci, L[k].co);
+        note_launch();
+        k_unpack_grad<<<cdiv(tot, 256), 256, 0, s>>>(L[k].ci, L[k].co, L[k].cip, gp + L[k].pwoff,
+                                                    gp + L[k].pboff, n.g + L[k].woff, n.g + L[k].boff);
+    };
+    // c6 (linear): input a5, grad gbig (16 ch, channel 0)
+    conv_dw<16, 16>(n, B, N, N, n.a5, n.gbig, nullptr, dwb(8).first, dwb(8).second, s);
+    conv_fwd<16, 16>(B, N, N, n.gbig, nullptr, L[8].wb, nullptr, 0, n.gbig2, nullptr, s);  // grad a5
+    // c5: out a5 (mask), in cat5
+    conv_dw<48, 16>(n, B, N, N, n.cat5, n.gbig2, n.a5, dwb(7).first, dwb(7).second, s);
+    conv_fwd<16, 48>(B, N, N, n.gbig2, n.a5, L[7].wb, nullptr, 0, n.gcat, nullptr, s);     // grad cat5
+    note_launch();
+    k_up_cat_bwd<<<cdiv((long)B * H2 * H2 * 32, 256), 256, 0, s>>>((long)B * H2 * H2 * 32, H2, H2, 32, 16, n.gcat, n.gmid);  // grad t4
+    // c4: out t4 (mask), in cat4
+    conv_dw<64, 32>(n, B, H2, H2, n.cat4, n.gmid, n.t4, dwb(6).first, dwb(6).second, s);
+    conv_fwd<32, 64>(B, H2, H2, n.gmid, n.t4, L[6].wb, nullptr, 0, n.gup, nullptr, s);     // grad cat4
+    note_launch();
+    k_up_cat_bwd<<<cdiv((long)B * H4 * H4 * 32, 256), 256, 0, s>>>((long)B * H4 * H4 * 32, H4, H4, 32, 32, n.gup, n.gsmall);  // grad t3
+    // c3b: out t3, in a3
+    conv_dw<32, 32>(n, B, H4, H4, n.a3, n.gsmall, n.t3, dwb(5).first, dwb(5).second, s);
+    conv_fwd<32, 32>(B, H4, H4, n.gsmall, n.t3, L[5].wb, nullptr, 0, n.gsmall2, nullptr, s);  // grad a3
+    // c3a: out a3, in p2
+    conv_dw<32, 32>(n, B, H4, H4, n.p2, n.gsmall2, n.a3, dwb(4).first, dwb(4).second, s);
+    conv_fwd<32, 32>(B, H4, H4, n.gsmall2, n.a3, L[4].wb, nullptr, 0, n.gsmall, nullptr, s);  // grad p2
+    // grad s2 = cat4 split + pool2 backward
+    note_launch();
+    k_skip_grad<<<cdiv((long)B * H2 * H2 * 32, 256), 256, 0, s>>>((long)B * H2 * H2 * 32, H2, H2, 32, 32, n.gup, n.gsmall, n.gmid2);
+    // c2b: out s2, in a2
+    conv_dw<32, 32>(n, B, H2, H2, n.a2, n.gmid2, n.s2, dwb(3).first, dwb(3).second, s);
+    conv_fwd<32, 32>(B, H2, H2, n.gmid2, n.s2, L[3].wb, nullptr, 0, n.gmid, nullptr, s);   // grad a2
+    // c2a: out a2, in p1
+    conv_dw<16, 32>(n, B, H2, H2, n.p1, n.gmid, n.a2, dwb(2).first, dwb(2).second, s);
+    conv_fwd<32, 16>(B, H2, H2, n.gmid, n.a2, L[2].wb, nullptr, 0, n.gmid2, nullptr, s);   // grad p1
+    // grad s1 = cat5 split + pool2 backward
+    note_launch();
+    k_skip_grad<<<cdiv(P * 16, 256), 256, 0, s>>>(P * 16, N, N, 32, 16, n.gcat, n.gmid2, n.gbig);
+    // c1b: out s1, in a1
+    conv_dw<16, 16>(n, B, N, N, n.a1, n.gbig, n.s1, dwb(1).first, dwb(1).second, s);
+    conv_fwd<16, 16>(B, N, N, n.gbig, n.s1, L[1].wb, nullptr, 0, n.gbig2, nullptr, s);     // grad a1
+    // c1a: out a1, in x
+    conv_dw<16, 16>(n, B, N, N, n.x, n.gbig2, n.a1, dwb(0).first, dwb(0).second, s);
+    for (int k = 0; k < 9; k++) unpack(k);
+}
+
+void cnn_adam(Cnn &n, float lr, cudaStream_t s)
+{
+    n.step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)n.step), c2 = 1.0f - powf(b2, (float)n.step);
+    note_launch();
+    k_adam<<<cdiv((long)n.nparam, 256), 256, 0, s>>>((long)n.nparam, n.w, n.m, n.v, n.g, lr, b1, b2,
+                                                    1e-8f, c1, c2);
+    cnn_pack(n, s);
+}
+
+void cnn_output(Cnn &n, int B, int N, double *p0, cudaStream_t s)
+{
+    note_launch();
+    k_output<<<B, 256, 0, s>>>(N * N, n.y32, n.stats, p0);
+}
+
+size_t cnn_nparam(const Cnn &n) { return n.nparam; }
+float *cnn_weights(Cnn &n) { return n.w; }
+float *cnn_grads(Cnn &n) { return n.g; }
+float *cnn_lsum(Cnn &n) { return n.lsum; }
+int cnn_steps(const Cnn &n) { return n.step; }
+void cnn_reset_adam(Cnn &n) { n.step = 0; cudaMemset(n.m, 0, n.nparam * 8); }
+
+}  // namespace ibk

@@ -141,6 +141,10 @@ struct Markers {
     float *gxf = nullptr, *gyf = nullptr;  // the same rounded to FP32 (screening only)
     float4 *sbox = nullptr;                // slab box of segment (m, next m), grid units
     double2 *dyr = nullptr;                // per-drop [min Y, max Y]
+    unsigned long long *ykey = nullptr;    // order-preserving integer key of each Y
+    ulonglong2 *dyk = nullptr;             // keys of the per-drop Y range
+    double *sv = nullptr;                  // per segment: 12 strip corner points (24 doubles)
+    float4 *sb5 = nullptr;                 // per segment: FP32 outward box of each of 5 strips
     int32_t *drop_start = nullptr, *drop_of = nullptr, *next = nullptr;
     uint32_t *key = nullptr, *tmp_ids = nullptr, *ids = nullptr,
              *cell_count = nullptr, *cell_start = nullptr, *scan_part = nullptr,
@@ -168,5 +172,23 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s);
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
                          double *Fx, double *Fy, cudaStream_t s);
 void launch_relocate(Markers &mk, cudaStream_t s);
+
+// ---------------------------------------------------------------- CNN
+struct Cnn;
+Cnn *cnn_new(int c1, int c2, unsigned long long seed, cudaStream_t s, cudaError_t *err);
+void cnn_free(Cnn *n);
+cudaError_t cnn_pack(Cnn &n, cudaStream_t s);
+cudaError_t cnn_workspace(Cnn &n, int B, int N);
+void cnn_forward(Cnn &n, int B, int N, const double *rhs, const double *rho, const double *p,
+                 cudaStream_t s);
+void cnn_backward(Cnn &n, int B, int N, cudaStream_t s);
+void cnn_adam(Cnn &n, float lr, cudaStream_t s);
+void cnn_output(Cnn &n, int B, int N, double *p0, cudaStream_t s);
+size_t cnn_nparam(const Cnn &n);
+float *cnn_weights(Cnn &n);
+float *cnn_grads(Cnn &n);
+float *cnn_lsum(Cnn &n);
+int cnn_steps(const Cnn &n);
+void cnn_reset_adam(Cnn &n);
 
 }  // namespace ibk

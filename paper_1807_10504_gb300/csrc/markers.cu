@@ -31,6 +31,14 @@ __device__ __forceinline__ double phi(int kernel, double r)
     return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
 }
 
+// Integer key with the order of the doubles (non-NaN; -0 treated as +0), so
+// that the many exact comparisons of the inside test run on the integer pipe.
+__device__ __forceinline__ unsigned long long okey(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d + 0.0);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
 __device__ __forceinline__ void nbrs(int m, const int32_t *drop_of,
                                      const int32_t *drop_start, int *pm, int *nm)
 {
@@ -58,10 +66,12 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
                            double *__restrict__ nxm, double *__restrict__ nym,
                            double *__restrict__ ds, double *__restrict__ fmag,
                            double *__restrict__ gx, double *__restrict__ gy,
-                           float *__restrict__ gxf, float *__restrict__ gyf)
+                           float *__restrict__ gxf, float *__restrict__ gyf,
+                           unsigned long long *__restrict__ ykey)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
+    ykey[m] = okey(Y[m]);
     {
         double a = (X[m] - x0) / h, b = (Y[m] - y0) / h;
         gx[m] = a; gy[m] = b;
@@ -92,26 +102,42 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
 // that an FP32 test against a cell never rejects a strip that touches it.
 __global__ void k_segments(int M, const int32_t *__restrict__ next, const double *__restrict__ gx,
                            const double *__restrict__ gy, const double *__restrict__ nxm,
-                           const double *__restrict__ nym, float4 *__restrict__ sbox)
+                           const double *__restrict__ nym, float4 *__restrict__ sbox,
+                           double *__restrict__ sv, float4 *__restrict__ sb5)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     int nm = next[m];
-    double xs[4] = {gx[m] - 2.5 * nxm[m], gx[m] + 2.5 * nxm[m], gx[nm] - 2.5 * nxm[nm],
-                    gx[nm] + 2.5 * nxm[nm]};
-    double ys[4] = {gy[m] - 2.5 * nym[m], gy[m] + 2.5 * nym[m], gy[nm] - 2.5 * nym[nm],
-                    gy[nm] + 2.5 * nym[nm]};
-    double x0 = fmin(fmin(xs[0], xs[1]), fmin(xs[2], xs[3]));
-    double x1 = fmax(fmax(xs[0], xs[1]), fmax(xs[2], xs[3]));
-    double y0 = fmin(fmin(ys[0], ys[1]), fmin(ys[2], ys[3]));
-    double y1 = fmax(fmax(ys[0], ys[1]), fmax(ys[2], ys[3]));
-    sbox[m] = make_float4(__double2float_rd(x0) - 1e-3f, __double2float_ru(x1) + 1e-3f,
-                          __double2float_rd(y0) - 1e-3f, __double2float_ru(y1) + 1e-3f);
+    const double gxa = gx[m], gya = gy[m], gxb = gx[nm], gyb = gy[nm];
+    const double nax = nxm[m], nay = nym[m], nbx = nxm[nm], nby = nym[nm];
+    // corner o (offset o - 2.5 cells) on the normal at m: (2o, 2o+1); at next m: 12 + (2o, 2o+1)
+    double *v = sv + (long)m * 24;
+    double ax[6], ay[6], bx[6], by[6];
+    for (int o = 0; o < 6; o++) {
+        const double a = (double)o - 2.5;
+        ax[o] = gxa + a * nax; ay[o] = gya + a * nay;
+        bx[o] = gxb + a * nbx; by[o] = gyb + a * nby;
+        v[2 * o] = ax[o]; v[2 * o + 1] = ay[o];
+        v[12 + 2 * o] = bx[o]; v[12 + 2 * o + 1] = by[o];
+    }
+    float fx0 = INFINITY, fx1 = -INFINITY, fy0 = INFINITY, fy1 = -INFINITY;
+    for (int k = 0; k < 5; k++) {
+        double x0 = fmin(fmin(ax[k], ax[k + 1]), fmin(bx[k], bx[k + 1]));
+        double x1 = fmax(fmax(ax[k], ax[k + 1]), fmax(bx[k], bx[k + 1]));
+        double y0 = fmin(fmin(ay[k], ay[k + 1]), fmin(by[k], by[k + 1]));
+        double y1 = fmax(fmax(ay[k], ay[k + 1]), fmax(by[k], by[k + 1]));
+        float4 f = make_float4(__double2float_rd(x0) - 1e-3f, __double2float_ru(x1) + 1e-3f,
+                               __double2float_rd(y0) - 1e-3f, __double2float_ru(y1) + 1e-3f);
+        sb5[(long)m * 5 + k] = f;
+        fx0 = fminf(fx0, f.x); fx1 = fmaxf(fx1, f.y); fy0 = fminf(fy0, f.z); fy1 = fmaxf(fy1, f.w);
+    }
+    sbox[m] = make_float4(fx0, fx1, fy0, fy1);
 }
 
 // One warp per drop: the range of its marker Y.
 __global__ void k_drop_yrange(int ndrops, const int32_t *__restrict__ drop_start,
-                              const double *__restrict__ Y, double2 *__restrict__ dyr)
+                              const double *__restrict__ Y, double2 *__restrict__ dyr,
+                              ulonglong2 *__restrict__ dyk)
 {
     int d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (d >= ndrops) return;
@@ -124,7 +150,10 @@ __global__ void k_drop_yrange(int ndrops, const int32_t *__restrict__ drop_start
         lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    if (lane == 0) dyr[d] = make_double2(lo, hi);
+    if (lane == 0) {
+        dyr[d] = make_double2(lo, hi);
+        dyk[d] = make_ulonglong2(okey(lo), okey(hi));
+    }
 }
 
 // ------------------------------------------------------------ binning
@@ -350,28 +379,30 @@ __global__ void k_spread_conv(int kernel, int nx, int ny, double h, double x0, d
 // sorted, then a crossing count per cell centre.  Writes H = chi.
 __global__ void __launch_bounds__(kT)
 k_rows_inside(int ndrops, int nx, double h, double x0, double y0, const double *__restrict__ X,
-              const double *__restrict__ Y, const int32_t *__restrict__ next,
-              const int32_t *__restrict__ drop_start, const double2 *__restrict__ dyr,
-              double *__restrict__ H, uint32_t *__restrict__ flags)
+              const double *__restrict__ Y, const unsigned long long *__restrict__ ykey,
+              const int32_t *__restrict__ next, const int32_t *__restrict__ drop_start,
+              const ulonglong2 *__restrict__ dyk, double *__restrict__ H,
+              uint32_t *__restrict__ flags)
 {
-    __shared__ double xs[kMaxCross], srt[kMaxCross];
+    __shared__ unsigned long long xs[kMaxCross], srt[kMaxCross];
     __shared__ int nc;
     const int j = blockIdx.x;
     const double py = y0 + ((double)j + 0.5) * h;
+    const unsigned long long kp = okey(py);
     if (threadIdx.x == 0) nc = 0;
     __syncthreads();
     // a drop entirely above (py < min Y) or not above (py >= max Y) the line
     // has no segment with one end above it and the other not
     for (int d = 0; d < ndrops; d++) {
-        double2 r = dyr[d];
-        if (py < r.x || py >= r.y) continue;
+        const ulonglong2 r = dyk[d];
+        if (kp < r.x || kp >= r.y) continue;
         for (int m = drop_start[d] + threadIdx.x; m < drop_start[d + 1]; m += kT) {
-            int nm = next[m];
-            double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
-            if ((ay > py) != (by > py)) {
+            const int nm = next[m];
+            if ((ykey[m] > kp) != (ykey[nm] > kp)) {
+                double ax = X[m], ay = Y[m], bx = X[nm], by = Y[nm];
                 double xc = ax + (py - ay) * (bx - ax) / (by - ay);
                 int q = atomicAdd(&nc, 1);
-                if (q < kMaxCross) xs[q] = xc;
+                if (q < kMaxCross) xs[q] = okey(xc);
             }
         }
     }
@@ -382,18 +413,18 @@ k_rows_inside(int ndrops, int nx, double h, double x0, double y0, const double *
         n = kMaxCross;
     }
     for (int q = threadIdx.x; q < n; q += kT) {
-        double v = xs[q];
+        unsigned long long v = xs[q];
         int r = 0;
         for (int t = 0; t < n; t++) r += (xs[t] < v || (xs[t] == v && t < q)) ? 1 : 0;
         srt[r] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nx; i += kT) {
-        double px = x0 + ((double)i + 0.5) * h;
+        const unsigned long long kx = okey(x0 + ((double)i + 0.5) * h);
         int lo = 0, hi = n;  // first index with srt > px
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
-            if (srt[mid] > px) hi = mid; else lo = mid + 1;
+            if (srt[mid] > kx) hi = mid; else lo = mid + 1;
         }
         H[(long)j * nx + i] = (double)((n - lo) & 1);
     }
@@ -498,53 +529,90 @@ __device__ __forceinline__ double strip_value(int k)
 
 constexpr int kBT = kBlk * kBlk;  // one thread per cell of the block
 
+constexpr int kMaxPairs = 1024;  // (cell, segment) pairs with possible overlap per block
+
+// Three phases in one CTA per active 8x8 block: (1) every cell counts the
+// candidate segments whose FP32 slab box meets it and the counts are scanned;
+// (2) the (cell, segment) pairs are written in ascending segment order and
+// processed densely, one pair per thread: each of the segment's five strips
+// whose FP32 box meets the cell is clipped against it in FP64; (3) every
+// cell sums its pairs in order.  The FP32 boxes are outward-rounded, so they
+// only skip strips that cannot overlap the cell.
 __global__ void __launch_bounds__(kBT)
 k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
                  const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
-                 const int32_t *__restrict__ next, const double *__restrict__ gx,
-                 const double *__restrict__ gy, const double *__restrict__ nxm,
-                 const double *__restrict__ nym, const float4 *__restrict__ sbox,
-                 double *__restrict__ H, uint32_t *__restrict__ flags)
+                 const double *__restrict__ sv, const float4 *__restrict__ sbox,
+                 const float4 *__restrict__ sb5, double *__restrict__ H,
+                 uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
+    __shared__ uint32_t pseg[kMaxPairs];
+    __shared__ uint8_t pcell[kMaxPairs];
+    __shared__ double pacc[kMaxPairs], pcov[kMaxPairs];
+    __shared__ uint32_t cnt[kBT + 1];
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
-    const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
-    if (i >= nx || j >= ny) return;
+    const int t = threadIdx.x;
+    const int i = bi * kBlk + (t % kBlk), j = bj * kBlk + (t / kBlk);
+    const bool live = i < nx && j < ny;
     const float fi = (float)i, fj = (float)j;
+    auto meets = [&](float4 b) { return !(b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj); };
+    uint32_t c = 0;
+    if (live)
+        for (int q = 0; q < n; q++) c += meets(sbox[cand[q]]) ? 1u : 0u;
+    cnt[t] = c;
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < kBT; k++) { uint32_t v = cnt[k]; cnt[k] = acc; acc += v; }
+        cnt[kBT] = acc;
+    }
+    __syncthreads();
+    const uint32_t total = cnt[kBT];
+    if (total > kMaxPairs) {
+        if (t == 0) atomicOr(&flags[1], 1u);
+        return;
+    }
+    if (live) {
+        uint32_t o = cnt[t];
+        for (int q = 0; q < n; q++)
+            if (meets(sbox[cand[q]])) { pseg[o] = cand[q]; pcell[o] = (uint8_t)t; o++; }
+    }
+    __syncthreads();
     double Hk[5];
     for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
-    double acc = 0.0, cov = 0.0;
-    for (int q = 0; q < n; q++) {
-        const int m = (int)cand[q];
-        const float4 b = sbox[m];
-        if (b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj) continue;
-        const int nm = next[m];
-        const double gxa = gx[m], gya = gy[m], gxb = gx[nm], gyb = gy[nm];
-        const double na_x = nxm[m], na_y = nym[m], nb_x = nxm[nm], nb_y = nym[nm];
+    for (uint32_t p = t; p < total; p += kBT) {
+        const uint32_t m = pseg[p];
+        const int ct = pcell[p];
+        const int ci = bi * kBlk + (ct % kBlk), cj = bj * kBlk + (ct / kBlk);
+        const float gi = (float)ci, gj = (float)cj;
+        const double di = (double)ci, dj = (double)cj;
+        const double *v = sv + (long)m * 24;
+        double acc = 0.0, cov = 0.0;
         for (int k = 0; k < 5; k++) {
-            double a = (double)k - 2.5, bb = (double)k - 1.5;
+            const float4 b = sb5[(long)m * 5 + k];
+            if (b.x > gi + 1.0f || b.y < gi || b.z > gj + 1.0f || b.w < gj) continue;
             double qx[4], qy[4];
-            qx[0] = gxa + a * na_x; qy[0] = gya + a * na_y;
-            qx[1] = gxb + a * nb_x; qy[1] = gyb + a * nb_y;
-            qx[2] = gxb + bb * nb_x; qy[2] = gyb + bb * nb_y;
-            qx[3] = gxa + bb * na_x; qy[3] = gya + bb * na_y;
-            for (int t = 0; t < 4; t++) { qx[t] -= (double)i; qy[t] -= (double)j; }
-            double mnx = fmin(fmin(qx[0], qx[1]), fmin(qx[2], qx[3]));
-            double mxx = fmax(fmax(qx[0], qx[1]), fmax(qx[2], qx[3]));
-            double mny = fmin(fmin(qy[0], qy[1]), fmin(qy[2], qy[3]));
-            double mxy = fmax(fmax(qy[0], qy[1]), fmax(qy[2], qy[3]));
-            if (mxx < 0.0 || mnx > 1.0 || mxy < 0.0 || mny > 1.0) continue;
+            qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
+            qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
+            qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
+            qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
             double A = clip_area_unit(qx, qy);
             acc += A * Hk[k];
             cov += A;
         }
+        pacc[p] = acc;
+        pcov[p] = cov;
     }
-    long c = (long)j * nx + i;
+    __syncthreads();
+    if (!live) return;
+    double acc = 0.0, cov = 0.0;
+    for (uint32_t p = cnt[t]; p < cnt[t + 1]; p++) { acc += pacc[p]; cov += pcov[p]; }
+    long cidx = (long)j * nx + i;
     double unc = 1.0 - cov;
     if (unc < 0.0) unc = 0.0;
-    H[c] = acc + unc * H[c];
+    H[cidx] = acc + unc * H[cidx];
 }
 
 // Irrotational face force F = f_face (H_ij - H_nb) / h on the x-face left of
@@ -870,7 +938,8 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
         mk.max_drop = std::max(mk.max_drop, drop_start_host[d + 1] - drop_start_host[d]);
     size_t ncell = (size_t)nx * ny, nb = (size_t)mk.bnx * mk.bny;
     size_t nparts = (ncell + kScanChunk - 1) / kScanChunk;
-    size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) +
+    size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
+                   al((size_t)M * 24 * 8) + al((size_t)M * 5 * 16) + al(M * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
@@ -886,6 +955,10 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.gxf = (float *)take(M * 4); mk.gyf = (float *)take(M * 4);
     mk.sbox = (float4 *)take(M * 16);
     mk.dyr = (double2 *)take(ndrops * 16);
+    mk.dyk = (ulonglong2 *)take(ndrops * 16);
+    mk.sv = (double *)take((size_t)M * 24 * 8);
+    mk.sb5 = (float4 *)take((size_t)M * 5 * 16);
+    mk.ykey = (unsigned long long *)take(M * 8);
     mk.drop_start = (int32_t *)take((ndrops + 1) * 4);
     mk.drop_of = (int32_t *)take(M * 4);
     mk.next = (int32_t *)take(M * 4);
@@ -927,12 +1000,13 @@ void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
     note_launch();
     k_geometry<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.X, mk.Y, mk.drop_of, mk.drop_start, sigma,
                                             mk.x0, mk.y0, mk.h, mk.kappa, mk.nxm, mk.nym, mk.ds,
-                                            mk.fmag, mk.gx, mk.gy, mk.gxf, mk.gyf);
+                                            mk.fmag, mk.gx, mk.gy, mk.gxf, mk.gyf, mk.ykey);
     note_launch();
-    k_segments<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox);
+    k_segments<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox,
+                                            mk.sv, mk.sb5);
     note_launch();
     k_drop_yrange<<<cdiv((long)mk.ndrops * 32, kT), kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.Y,
-                                                               mk.dyr);
+                                                               mk.dyr, mk.dyk);
 }
 
 void launch_sort(Markers &mk, cudaStream_t s)
@@ -983,13 +1057,12 @@ void launch_spread_conv(const Markers &mk, int kernel, const double *fmag, doubl
 void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
 {
     note_launch();
-    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.next,
-                                       mk.drop_start, mk.dyr, H, mk.flags);
+    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.ykey,
+                                       mk.next, mk.drop_start, mk.dyk, H, mk.flags);
     dim3 g(mk.bnx, mk.bny);
     note_launch();
     k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids,
-                                       mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox, H,
-                                       mk.flags);
+                                       mk.sv, mk.sbox, mk.sb5, H, mk.flags);
 }
 
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H, double *Fx,

@@ -1,0 +1,137 @@
+"""GPU parity of the warm-start CNN kernels (forward, gradients) against the
+FP64 oracle fed the same BF16-rounded inputs and weights, training progress
+and determinism, and the warm start inside the pressure solve."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cnn as OC
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return torch
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def flat_of(P):
+    return np.concatenate([np.concatenate([P[n + ".w"].ravel(), P[n + ".b"]])
+                           for n, _, _, _ in OC.LAYERS]).astype(np.float32)
+
+
+def dict_of(flat, like):
+    P, o = {}, 0
+    for n, _, _, _ in OC.LAYERS:
+        for k in (".w", ".b"):
+            sz = like[n + k].size
+            P[n + k] = flat[o:o + sz].astype(np.float64).reshape(like[n + k].shape)
+            o += sz
+    return P
+
+
+def batch(B, N, seed):
+    rng = np.random.default_rng(seed)
+    rhs = np.stack([W.random_cells(N, N, seed + k) for k in range(B)])
+    H = np.stack([W.random_H(N, N, seed + 10 + k) for k in range(B)])
+    rho = 1e-3 + (1 - 1e-3) * H
+    p = rng.standard_normal((B, N, N))
+    return rhs, rho, p
+
+
+def oracle_inputs(rhs, rho, p):
+    xs, ss, ts = [], [], []
+    for k in range(rhs.shape[0]):
+        x, s = OC.features(rhs[k], 1.0 / rho[k])
+        xs.append(x[0]); ss.append(s); ts.append(p[k] / s)
+    return bf16(np.stack(xs)), np.array(ss), np.stack(ts)[..., None]
+
+
+def test_forward_matches_oracle(T):
+    import paper_1807_10504_gb300 as ib
+    B, N = 2, 32
+    P = OC.init_params(seed=1)
+    for n, _, co, _ in OC.LAYERS:
+        P[n + ".b"] = np.random.default_rng(len(n)).standard_normal(co) * 0.05
+    Pq = {k: (bf16(v) if k.endswith(".w") else v.astype(np.float32).astype(np.float64)) for k, v in P.items()}
+    net = ib.Net(seed=0)
+    net.set_params(flat_of(P))
+    rhs, rho, p = batch(B, N, 3)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    p0 = net.infer(d(rhs), d(rho)).cpu().numpy()
+    x, s, _ = oracle_inputs(rhs, rho, p)
+    y = OC.forward(Pq, x)[..., 0]
+    ref = s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True))
+    err = np.linalg.norm(p0 - ref) / np.linalg.norm(ref)
+    assert err < 3e-2, err
+
+
+def test_gradients_match_oracle(T):
+    import paper_1807_10504_gb300 as ib
+    B, N = 2, 32
+    P = OC.init_params(seed=2)
+    Pq = {k: (bf16(v) if k.endswith(".w") else v) for k, v in P.items()}
+    net = ib.Net(seed=0)
+    net.set_params(flat_of(P))
+    rhs, rho, p = batch(B, N, 5)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    loss, g = net.grad(d(rhs), d(rho), d(p))
+    x, s, t = oracle_inputs(rhs, rho, p)
+    y, cache = OC.forward(Pq, x, keep=True)
+    L, gy = OC.loss(y, t)
+    G, _ = OC.backward(Pq, cache, gy)
+    assert abs(loss - L) <= 3e-2 * L
+    Gg = dict_of(g, P)
+    # The last bias has an exactly zero gradient (the loss ignores constant
+    # shifts of the output); every other gradient must point the same way as
+    # the FP64 one (BF16 activations and gradients round at every layer, and
+    # the pixel sums cancel, so the relative error grows towards the input).
+    assert abs(Gg["c6.b"][0]) <= 1e-4 * np.linalg.norm(G["c6.w"])
+    for n, _, _, _ in OC.LAYERS:
+        for k in (".w", ".b"):
+            if n + k == "c6.b":
+                continue
+            a, ref = Gg[n + k].ravel(), G[n + k].ravel()
+            cos = a @ ref / (np.linalg.norm(a) * np.linalg.norm(ref))
+            err = np.linalg.norm(a - ref) / np.linalg.norm(ref)
+            assert cos > 0.995 and err < 0.12, (n + k, cos, err)
+
+
+def test_training_reduces_loss_and_is_deterministic(T):
+    import paper_1807_10504_gb300 as ib
+    B, N = 4, 32
+    rhs, rho, p = batch(B, N, 7)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    runs = []
+    for _ in range(2):
+        net = ib.Net(seed=4)
+        losses = [net.train_step(d(rhs), d(rho), d(p), lr=2e-3) for _ in range(60)]
+        runs.append((losses, net.get_params()))
+    losses = runs[0][0]
+    assert losses[-1] < 0.5 * losses[0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and runs[0][0] == runs[1][0]
+
+
+def test_warm_start_reaches_the_same_tolerance(T):
+    import paper_1807_10504_gb300 as ib
+    n = 64
+    mk = W.static_drop(n, 0.25, 128)
+    cfg = ib.Config(nx=n, ny=n, h=1.0 / n, relocate_every=0)
+    ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    net = ib.Net(seed=5)
+    ctx.attach(net)
+    dt = W.capillary_dt(cfg.h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    cyc, rr = ctx.ns_step(dt, 1, 2)
+    assert rr <= 1e-10
+    ctx.attach(None)
