@@ -166,9 +166,11 @@ ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
  * c2 = 32 (the only supported widths), BF16 weights and activations with
  * FP32 accumulation on the tensor cores, FP32 master weights and Adam state.
  * Input of a sample: rhs b and cell density rho (device FP64 N x N, N a
- * multiple of 4; B samples stored back to back); features
- * ((b - mean b)/s, (1/rho)/max(1/rho)) with s = rms(b - mean b); target p / s
- * with a mean-removed squared-error loss; output p0 = s (y - mean y).
+ * multiple of 4, cell size h; B samples stored back to back); features
+ * ((b - mean b)/s, (1/rho)/max(1/rho)) with s = rms(b - mean b); target
+ * p / (s h^2 c) with a mean-removed squared-error loss; output
+ * p0 = s h^2 c (y - mean y).  c is the network's pressure scale
+ * (cnn_set_scale, default 1), set from the training data.
  * Parameters are a flat FP32 host array, layer by layer (c1a, c1b, c2a, c2b,
  * c3a, c3b, c4, c5, c6), each weights [cout][3][3][cin] then bias [cout].
  * Calls run on `stream`; cnn_train_step, cnn_grad synchronise it when they
@@ -180,16 +182,18 @@ int64_t cnn_num_params(const ib_cnn *net);
 ib_status cnn_get_params(ib_cnn *net, float *host, int64_t n);
 ib_status cnn_set_params(ib_cnn *net, const float *host, int64_t n);  /* resets Adam */
 /* Loss and parameter gradients (host, cnn_num_params floats) without update. */
-ib_status cnn_grad(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
+ib_status cnn_grad(ib_cnn *net, int32_t B, int32_t N, double h, const double *rhs,
                    const double *rho, const double *p, float *loss,
                    float *grads_host, void *stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch.            */
-ib_status cnn_train_step(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
-                         const double *rho, const double *p, float lr,
-                         float *loss, void *stream);
+ib_status cnn_train_step(ib_cnn *net, int32_t B, int32_t N, double h,
+                         const double *rhs, const double *rho, const double *p,
+                         float lr, float *loss, void *stream);
 /* p0 (device FP64, B x N x N) = network estimate of the pressure.          */
-ib_status cnn_infer(ib_cnn *net, int32_t B, int32_t N, const double *rhs,
+ib_status cnn_infer(ib_cnn *net, int32_t B, int32_t N, double h, const double *rhs,
                     const double *rho, double *p0, void *stream);
+ib_status cnn_set_scale(ib_cnn *net, double c);
+double cnn_get_scale(const ib_cnn *net);
 /* Attach (or detach with NULL) a network used by ns_step(..., warm = 2); the
  * context does not own it.                                                 */
 ib_status ib_attach_cnn(ib_ctx *ctx, ib_cnn *net);

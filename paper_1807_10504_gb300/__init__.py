@@ -35,7 +35,7 @@ EXPORTS = [
     "ib_op_rhs", "ib_op_correct", "ib_op_predictor", "ib_launch_count", "ib_profile_begin",
     "ib_profile_end", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
-    "ib_attach_cnn", "ib_use_graphs",
+    "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale",
 ]
 
 
@@ -95,9 +95,11 @@ def lib():
                                  C.c_int, C.POINTER(C.c_int), C.POINTER(_d), _P],
             "cnn_init": [C.POINTER(_P), _i32, _i32, C.c_uint64, _P],
             "cnn_get_params": [_P, _P, C.c_int64], "cnn_set_params": [_P, _P, C.c_int64],
-            "cnn_grad": [_P, _i32, _i32, _P, _P, _P, C.POINTER(C.c_float), _P, _P],
-            "cnn_train_step": [_P, _i32, _i32, _P, _P, _P, C.c_float, C.POINTER(C.c_float), _P],
-            "cnn_infer": [_P, _i32, _i32, _P, _P, _P, _P],
+            "cnn_grad": [_P, _i32, _i32, _d, _P, _P, _P, C.POINTER(C.c_float), _P, _P],
+            "cnn_train_step": [_P, _i32, _i32, _d, _P, _P, _P, C.c_float, C.POINTER(C.c_float),
+                               _P],
+            "cnn_infer": [_P, _i32, _i32, _d, _P, _P, _P, _P],
+            "cnn_set_scale": [_P, _d],
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
@@ -118,6 +120,8 @@ def lib():
         L.ib_launch_count.restype = C.c_ulonglong
         L.cnn_destroy.argtypes = [_P]
         L.cnn_destroy.restype = None
+        L.cnn_get_scale.argtypes = [_P]
+        L.cnn_get_scale.restype = _d
         L.cnn_num_params.argtypes = [_P]
         L.cnn_num_params.restype = C.c_int64
         L.ib_num_markers.argtypes = [_P]
@@ -355,27 +359,38 @@ class Net:
         flat = np.ascontiguousarray(flat, np.float32)
         _check(lib().cnn_set_params(self._h, flat.ctypes.data, self.nparam), None, "cnn_set_params")
 
-    def grad(self, rhs, rho, p):
+    @property
+    def scale(self) -> float:
+        return float(lib().cnn_get_scale(self._h))
+
+    @scale.setter
+    def scale(self, c: float):
+        _check(lib().cnn_set_scale(self._h, float(c)), None, "cnn_set_scale")
+
+    def grad(self, rhs, rho, p, h=None):
         B, N = rhs.shape[0], rhs.shape[-1]
+        h = 1.0 / N if h is None else h
         loss = C.c_float(0.0)
         g = np.empty(self.nparam, np.float32)
-        _check(lib().cnn_grad(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p), C.byref(loss),
+        _check(lib().cnn_grad(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p), C.byref(loss),
                               g.ctypes.data, _stream()), None, "cnn_grad")
         return loss.value, g
 
-    def train_step(self, rhs, rho, p, lr=1e-3):
+    def train_step(self, rhs, rho, p, lr=1e-3, h=None):
         B, N = rhs.shape[0], rhs.shape[-1]
+        h = 1.0 / N if h is None else h
         loss = C.c_float(0.0)
-        _check(lib().cnn_train_step(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p), lr,
+        _check(lib().cnn_train_step(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p), lr,
                                     C.byref(loss), _stream()), None, "cnn_train_step")
         return loss.value
 
-    def infer(self, rhs, rho):
+    def infer(self, rhs, rho, h=None):
         torch = _torch()
         B, N = rhs.shape[0], rhs.shape[-1]
+        h = 1.0 / N if h is None else h
         p0 = torch.empty((B, N, N), dtype=torch.float64, device="cuda")
-        _check(lib().cnn_infer(self._h, B, N, _ptr(rhs), _ptr(rho), _ptr(p0), _stream()), None,
-               "cnn_infer")
+        _check(lib().cnn_infer(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p0), _stream()),
+               None, "cnn_infer")
         return p0
 
 

@@ -384,8 +384,8 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (warm == 2) {
             cudaError_t ce = cnn_workspace(*c->cnn->n, 1, g.nx);
             if (ce != cudaSuccess) return cuda_check(c, ce, "network workspace");
-            cnn_forward(*c->cnn->n, 1, g.nx, c->b, c->rho, nullptr, c->s);
-            cnn_output(*c->cnn->n, 1, g.nx, c->p, c->s);
+            cnn_forward(*c->cnn->n, 1, g.nx, g.h, c->b, c->rho, nullptr, c->s);
+            cnn_output(*c->cnn->n, 1, g.nx, g.h, c->p, c->s);
         }
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                     &c->last_cycles, &c->last_relres, c->s, c->err);
@@ -476,13 +476,13 @@ ib_status cnn_set_params(ib_cnn *h, const float *host, int64_t n)
     return e == cudaSuccess ? IB_OK : IB_ECUDA;
 }
 
-static ib_status cnn_fb(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
-                        const double *p, float *loss, cudaStream_t s)
+static ib_status cnn_fb(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
+                        const double *rho, const double *p, float *loss, cudaStream_t s)
 {
-    if (!h || B < 1 || N < 4 || N % 4 || !rhs || !rho || !p) return IB_EINVAL;
+    if (!h || B < 1 || N < 4 || N % 4 || !(hs > 0) || !rhs || !rho || !p) return IB_EINVAL;
     cudaError_t e = ibk::cnn_workspace(*h->n, B, N);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
-    ibk::cnn_forward(*h->n, B, N, rhs, rho, p, s);
+    ibk::cnn_forward(*h->n, B, N, hs, rhs, rho, p, s);
     ibk::cnn_backward(*h->n, B, N, s);
     if (loss) {
         std::vector<float> ls(B);
@@ -495,35 +495,46 @@ static ib_status cnn_fb(ib_cnn *h, int32_t B, int32_t N, const double *rhs, cons
     return cudaGetLastError() == cudaSuccess && e == cudaSuccess ? IB_OK : IB_ECUDA;
 }
 
-ib_status cnn_grad(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
-                   const double *p, float *loss, float *grads_host, void *stream)
+ib_status cnn_grad(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
+                   const double *rho, const double *p, float *loss, float *grads_host,
+                   void *stream)
 {
-    ib_status st = cnn_fb(h, B, N, rhs, rho, p, loss, (cudaStream_t)stream);
+    ib_status st = cnn_fb(h, B, N, hs, rhs, rho, p, loss, (cudaStream_t)stream);
     if (st != IB_OK || !grads_host) return st;
     cudaError_t e = cudaMemcpy(grads_host, ibk::cnn_grads(*h->n), ibk::cnn_nparam(*h->n) * 4,
                                cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? IB_OK : IB_ECUDA;
 }
 
-ib_status cnn_train_step(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
-                         const double *p, float lr, float *loss, void *stream)
+ib_status cnn_train_step(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
+                         const double *rho, const double *p, float lr, float *loss,
+                         void *stream)
 {
-    ib_status st = cnn_fb(h, B, N, rhs, rho, p, loss, (cudaStream_t)stream);
+    ib_status st = cnn_fb(h, B, N, hs, rhs, rho, p, loss, (cudaStream_t)stream);
     if (st != IB_OK) return st;
     ibk::cnn_adam(*h->n, lr, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
 }
 
-ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, const double *rhs, const double *rho,
-                    double *p0, void *stream)
+ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
+                    const double *rho, double *p0, void *stream)
 {
-    if (!h || B < 1 || N < 4 || N % 4 || !rhs || !rho || !p0) return IB_EINVAL;
+    if (!h || B < 1 || N < 4 || N % 4 || !(hs > 0) || !rhs || !rho || !p0) return IB_EINVAL;
     cudaError_t e = ibk::cnn_workspace(*h->n, B, N);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
-    ibk::cnn_forward(*h->n, B, N, rhs, rho, nullptr, (cudaStream_t)stream);
-    ibk::cnn_output(*h->n, B, N, p0, (cudaStream_t)stream);
+    ibk::cnn_forward(*h->n, B, N, hs, rhs, rho, nullptr, (cudaStream_t)stream);
+    ibk::cnn_output(*h->n, B, N, hs, p0, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
 }
+
+ib_status cnn_set_scale(ib_cnn *h, double c)
+{
+    if (!h || !(c > 0)) return IB_EINVAL;
+    ibk::cnn_set_scale(*h->n, c);
+    return IB_OK;
+}
+
+double cnn_get_scale(const ib_cnn *h) { return h ? ibk::cnn_get_scale(*h->n) : 0.0; }
 
 ib_status ib_attach_cnn(ib_ctx *c, ib_cnn *h)
 {

@@ -43,96 +43,133 @@ __device__ __forceinline__ uint32_t relu_mask(uint32_t v, uint32_t m)
     return r;
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool MASK>
 constexpr size_t conv_smem()
 {
-    return ((size_t)(CH + 2) * (CW + 2) * (CIN + 8) + (size_t)COUT * (9 * CIN + 8)) * 2;
+    return ((size_t)(MASK ? 4 : 2) * (CH + 2) * (CW + 2) * (CIN + 8) + (size_t)COUT * (9 * CIN + 8)) * 2;
 }
+
+// 4-byte asynchronous global -> shared copy; src-size 0 writes zeros.
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    const int sz = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // y = act(conv3x3(x * [xmask > 0]) + bias), NHWC, zero padding.
 // w: [COUT][9][CIN] (tap = 3 dy + dx multiplies x[i + dy - 1, j + dx - 1]).
-template <int CIN, int COUT>
+// Persistent: each CTA stages all weights once, then walks output tiles of
+// 8 x 16 pixels; the next tile (and its mask) is copied into the other
+// shared buffer with cp.async while the current one is on the tensor cores.
+template <int CIN, int COUT, bool MASK>
 __global__ void __launch_bounds__(128)
-k_conv_fwd(int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xmask,
+k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xmask,
            const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
            bf16 *__restrict__ y, float *__restrict__ y32)
 {
     constexpr int XS = CIN + 8, WS = 9 * CIN + 8, NT = COUT / 8;
+    constexpr int TP = (CH + 2) * (CW + 2);       // pixels of a haloed tile
     extern __shared__ __align__(16) unsigned char conv_sm[];
-    bf16 *xs = (bf16 *)conv_sm;
-    bf16 *ws = xs + (CH + 2) * (CW + 2) * XS;
-    const int bz = blockIdx.z, ty0 = blockIdx.y * CH, tx0 = blockIdx.x * CW;
-    for (int k = threadIdx.x; k < (CH + 2) * (CW + 2) * (CIN / 2); k += 128) {
-        const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
-        const int r = pix / (CW + 2), c = pix - r * (CW + 2);
-        const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-        uint32_t v = 0;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const long off = (((long)bz * H + gy) * W + gx) * CIN + 2 * cp;
-            v = *(const uint32_t *)(x + off);
-            if (xmask) v = relu_mask(v, *(const uint32_t *)(xmask + off));
-        }
-        *(uint32_t *)(xs + pix * XS + 2 * cp) = v;
-    }
+    bf16 *ws = (bf16 *)conv_sm;
+    bf16 *xs0 = ws + COUT * WS;                    // 2 input buffers, then 2 mask buffers
+    const int tw = (W + CW - 1) / CW, th = (H + CH - 1) / CH, ntiles = B * tw * th;
     for (int k = threadIdx.x; k < COUT * (9 * CIN / 2); k += 128) {
         const int co = k / (9 * CIN / 2), q = k - co * (9 * CIN / 2);
         *(uint32_t *)(ws + co * WS + 2 * q) = *(const uint32_t *)(w + (long)co * 9 * CIN + 2 * q);
     }
-    __syncthreads();
+    auto issue = [&](int tl, int buf) {
+        const int bz = tl / (tw * th), rem = tl - bz * tw * th;
+        const int ty0 = (rem / tw) * CH, tx0 = (rem - (rem / tw) * tw) * CW;
+        bf16 *xs = xs0 + buf * TP * XS;
+        bf16 *ms = xs0 + (2 + buf) * TP * XS;
+        for (int k = threadIdx.x; k < TP * (CIN / 2); k += 128) {
+            const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
+            const int r = pix / (CW + 2), c = pix - r * (CW + 2);
+            const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const long off = in ? (((long)bz * H + gy) * W + gx) * CIN + 2 * cp : 0;
+            cp_async4(xs + pix * XS + 2 * cp, x + off, in);
+            if (MASK) cp_async4(ms + pix * XS + 2 * cp, xmask + off, in);
+        }
+        cp_async_commit();
+    };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    float acc[2][NT][4];
+    int buf = 0;
+    if (blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    for (int tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int tn = tl + gridDim.x;
+        if (tn < ntiles) { issue(tn, buf ^ 1); cp_async_wait<1>(); }
+        else cp_async_wait<0>();
+        __syncthreads();
+        const bf16 *xs = xs0 + buf * TP * XS;
+        const bf16 *ms = xs0 + (2 + buf) * TP * XS;
+        float acc[2][NT][4];
 #pragma unroll
-    for (int a = 0; a < 2; a++)
+        for (int a = 0; a < 2; a++)
 #pragma unroll
-        for (int b = 0; b < NT; b++)
+            for (int b = 0; b < NT; b++)
 #pragma unroll
-            for (int q = 0; q < 4; q++) acc[a][b][q] = 0.0f;
+                for (int q = 0; q < 4; q++) acc[a][b][q] = 0.0f;
 #pragma unroll 1
-    for (int tap = 0; tap < 9; tap++) {
-        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+        for (int tap = 0; tap < 9; tap++) {
+            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
 #pragma unroll
-        for (int c0 = 0; c0 < CIN; c0 += 16) {
-            uint32_t bf[NT][2];
+            for (int c0 = 0; c0 < CIN; c0 += 16) {
+                uint32_t bf[NT][2];
+#pragma unroll
+                for (int nt = 0; nt < NT; nt++) {
+                    const bf16 *wp = ws + (nt * 8 + g) * WS + tap * CIN + c0 + 2 * t4;
+                    bf[nt][0] = *(const uint32_t *)wp;
+                    bf[nt][1] = *(const uint32_t *)(wp + 8);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; mt++) {
+                    const int r = 2 * warp + mt;
+                    const int o0 = ((r + dy) * (CW + 2) + g + dx) * XS + c0 + 2 * t4, o1 = o0 + 8 * XS;
+                    uint32_t af[4];
+                    af[0] = *(const uint32_t *)(xs + o0);
+                    af[1] = *(const uint32_t *)(xs + o1);
+                    af[2] = *(const uint32_t *)(xs + o0 + 8);
+                    af[3] = *(const uint32_t *)(xs + o1 + 8);
+                    if (MASK) {
+                        af[0] = relu_mask(af[0], *(const uint32_t *)(ms + o0));
+                        af[1] = relu_mask(af[1], *(const uint32_t *)(ms + o1));
+                        af[2] = relu_mask(af[2], *(const uint32_t *)(ms + o0 + 8));
+                        af[3] = relu_mask(af[3], *(const uint32_t *)(ms + o1 + 8));
+                    }
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], af, bf[nt]);
+                }
+            }
+        }
+        const int bz = tl / (tw * th), rem = tl - bz * tw * th;
+        const int ty0 = (rem / tw) * CH, tx0 = (rem - (rem / tw) * tw) * CW;
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            const int oy = ty0 + 2 * warp + mt;
+            if (oy >= H) continue;
 #pragma unroll
             for (int nt = 0; nt < NT; nt++) {
-                const bf16 *wp = ws + (nt * 8 + g) * WS + tap * CIN + c0 + 2 * t4;
-                bf[nt][0] = *(const uint32_t *)wp;
-                bf[nt][1] = *(const uint32_t *)(wp + 8);
-            }
+                const int co = nt * 8 + 2 * t4;
+                const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++) {
-                const int r = 2 * warp + mt;
-                const bf16 *xa = xs + ((r + dy) * (CW + 2) + g + dx) * XS + c0 + 2 * t4;
-                const bf16 *xb = xa + 8 * XS;
-                uint32_t af[4];
-                af[0] = *(const uint32_t *)xa;
-                af[1] = *(const uint32_t *)xb;
-                af[2] = *(const uint32_t *)(xa + 8);
-                af[3] = *(const uint32_t *)(xb + 8);
-#pragma unroll
-                for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], af, bf[nt]);
+                for (int half = 0; half < 2; half++) {
+                    const int ox = tx0 + g + 8 * half;
+                    if (ox >= W) continue;
+                    float v0 = acc[mt][nt][2 * half] + b0, v1 = acc[mt][nt][2 * half + 1] + b1;
+                    if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                    const long off = (((long)bz * H + oy) * W + ox) * COUT + co;
+                    *(__nv_bfloat162 *)(y + off) = __floats2bfloat162_rn(v0, v1);
+                    if (y32 && co == 0) y32[off / COUT] = v0;  // channel 0 only
+                }
             }
         }
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++) {
-        const int oy = ty0 + 2 * warp + mt;
-        if (oy >= H) continue;
-#pragma unroll
-        for (int nt = 0; nt < NT; nt++) {
-            const int co = nt * 8 + 2 * t4;
-            const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
-#pragma unroll
-            for (int half = 0; half < 2; half++) {
-                const int ox = tx0 + g + 8 * half;
-                if (ox >= W) continue;
-                float v0 = acc[mt][nt][2 * half] + b0, v1 = acc[mt][nt][2 * half + 1] + b1;
-                if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-                const long off = (((long)bz * H + oy) * W + ox) * COUT + co;
-                *(__nv_bfloat162 *)(y + off) = __floats2bfloat162_rn(v0, v1);
-                if (y32) { y32[off] = v0; y32[off + 1] = v1; }
-            }
-        }
+        __syncthreads();  // the buffer just read is refilled by the next issue
+        buf ^= 1;
     }
 }
 
@@ -312,58 +349,116 @@ __global__ void k_skip_grad(long n, int H, int W, int C1, int C2, const bf16 *__
 }
 
 // --- features, loss, output ----------------------------------------------
-// Per sample: mean of b, rms s of (b - mean), max of 1/rho; one CTA per sample.
-__global__ void __launch_bounds__(256)
-k_sample_stats(int N2, const double *__restrict__ b, const double *__restrict__ rho,
-               double *__restrict__ stats)
+// Per-sample statistics of the network input, in two launches: partial sums
+// over kRedBlocks CTAs per sample, then a fixed-order fold.  One pass gives
+// sum (b - b0) and sum (b - b0)^2 with b0 the sample's first value (a shift
+// that keeps the variance free of cancellation), and min rho (max(1/rho) is
+// 1/min(rho) exactly, IEEE division being monotone).
+// stats[kStat * smp + ...]: 0 mean b, 1 s = rms(b - mean) (1 if zero),
+// 2 1/s, 3 min rho, 4 1/(s pscale), 5 mean of the network output.
+constexpr int kRedBlocks = 64, kStat = 8;
+
+__device__ __forceinline__ void block_fold3(double (*sh)[256], double &a, double &b, double &c, bool cmin)
 {
-    __shared__ double sh[3][256];
-    const double *bb = b + (long)blockIdx.x * N2, *rr = rho + (long)blockIdx.x * N2;
-    double s = 0.0, mx = 0.0;
-    for (int k = threadIdx.x; k < N2; k += 256) { s += bb[k]; mx = fmax(mx, 1.0 / rr[k]); }
-    sh[0][threadIdx.x] = s; sh[2][threadIdx.x] = mx;
+    sh[0][threadIdx.x] = a; sh[1][threadIdx.x] = b; sh[2][threadIdx.x] = c;
     __syncthreads();
     for (int o = 128; o; o >>= 1) {
         if (threadIdx.x < o) {
             sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+            sh[2][threadIdx.x] = cmin ? fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + o])
+                                      : sh[2][threadIdx.x] + sh[2][threadIdx.x + o];
         }
         __syncthreads();
     }
-    const double mean = sh[0][0] / N2;
-    double q = 0.0;
-    for (int k = threadIdx.x; k < N2; k += 256) { double d = bb[k] - mean; q += d * d; }
-    __syncthreads();
-    sh[1][threadIdx.x] = q;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o) sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
-        __syncthreads();
+    a = sh[0][0]; b = sh[1][0]; c = sh[2][0];
+}
+
+__global__ void __launch_bounds__(256)
+k_stats_part(int N2, const double *__restrict__ b, const double *__restrict__ rho,
+             double *__restrict__ part)
+{
+    __shared__ double sh[3][256];
+    const int smp = blockIdx.y;
+    const double *bb = b + (long)smp * N2, *rr = rho + (long)smp * N2;
+    const double b0 = bb[0];
+    double sd = 0.0, sq = 0.0, mn = INFINITY;
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < N2; k += 256 * kRedBlocks) {
+        const double d = bb[k] - b0;
+        sd += d; sq += d * d; mn = fmin(mn, rr[k]);
     }
+    block_fold3(sh, sd, sq, mn, true);
     if (threadIdx.x == 0) {
-        double r = sqrt(sh[1][0] / N2);
-        stats[3 * blockIdx.x + 0] = mean;
-        stats[3 * blockIdx.x + 1] = r > 0.0 ? r : 1.0;
-        stats[3 * blockIdx.x + 2] = sh[2][0];
+        double *o = part + ((long)smp * kRedBlocks + blockIdx.x) * 3;
+        o[0] = sd; o[1] = sq; o[2] = mn;
     }
 }
 
-// x[..., 0] = (b - mean)/s, x[..., 1] = (1/rho)/max, other channels 0; and
-// (training) t = p / s.
+__global__ void __launch_bounds__(256)
+k_stats_final(int N2, const double *__restrict__ b, const double *__restrict__ part, double pscale,
+              double *__restrict__ stats)
+{
+    __shared__ double sh[3][256];
+    const int smp = blockIdx.x;
+    double sd = 0.0, sq = 0.0, mn = INFINITY;
+    if (threadIdx.x < kRedBlocks) {
+        const double *o = part + ((long)smp * kRedBlocks + threadIdx.x) * 3;
+        sd = o[0]; sq = o[1]; mn = o[2];
+    }
+    block_fold3(sh, sd, sq, mn, true);
+    if (threadIdx.x == 0) {
+        const double md = sd / N2, var = fmax(sq / N2 - md * md, 0.0), r = sqrt(var);
+        const double sc = r > 0.0 ? r : 1.0;
+        double *st = stats + kStat * smp;
+        st[0] = b[(long)smp * N2] + md;
+        st[1] = sc;
+        st[2] = 1.0 / sc;
+        st[3] = mn;
+        st[4] = 1.0 / (sc * pscale);
+    }
+}
+
+// Mean of the network output per sample (partials, then the fold into stats[5]).
+__global__ void __launch_bounds__(256)
+k_ysum_part(int N2, const float *__restrict__ y32, double *__restrict__ part)
+{
+    __shared__ double sh[3][256];
+    const int smp = blockIdx.y;
+    const float *yy = y32 + (long)smp * N2;
+    double s = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < N2; k += 256 * kRedBlocks) s += (double)yy[k];
+    block_fold3(sh, s, z0, z1, false);
+    if (threadIdx.x == 0) part[(long)smp * kRedBlocks + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256)
+k_ymean_final(int N2, const double *__restrict__ part, double *__restrict__ stats)
+{
+    __shared__ double sh[3][256];
+    double s = threadIdx.x < kRedBlocks ? part[(long)blockIdx.x * kRedBlocks + threadIdx.x] : 0.0;
+    double z0 = 0.0, z1 = 0.0;
+    block_fold3(sh, s, z0, z1, false);
+    if (threadIdx.x == 0) stats[kStat * blockIdx.x + 5] = s / N2;
+}
+
+// x[..., 0] = (b - mean)/s, x[..., 1] = (1/rho)/max(1/rho) = min(rho)/rho,
+// other channels 0 (BF16, rounded from FP32); and (training)
+// t = p / (s pscale), pscale = h^2 c.
 __global__ void k_features(long n, int N2, const double *__restrict__ b, const double *__restrict__ rho,
                            const double *__restrict__ p, const double *__restrict__ stats,
                            bf16 *__restrict__ x, float *__restrict__ t)
 {
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const long smp = k / N2;
-    const double mean = stats[3 * smp], s = stats[3 * smp + 1], mx = stats[3 * smp + 2];
-    __nv_bfloat162 v = __floats2bfloat162_rn((float)((b[k] - mean) / s), (float)((1.0 / rho[k]) / mx));
+    const double *st = stats + kStat * (k / N2);
+    const float f0 = (float)((b[k] - st[0]) * st[2]);
+    const float f1 = (float)st[3] / (float)rho[k];
+    __nv_bfloat162 v = __floats2bfloat162_rn(f0, f1);
     uint32_t *xp = (uint32_t *)(x + k * 16);
     xp[0] = *(uint32_t *)&v;
 #pragma unroll
     for (int q = 1; q < 8; q++) xp[q] = 0u;
-    if (t) t[k] = (float)(p[k] / s);
+    if (t) t[k] = (float)(p[k] * st[4]);
 }
 
 // Mean-removed squared error per sample (one CTA per sample): loss partial and
@@ -376,7 +471,7 @@ k_loss(int N2, int Bn, const float *__restrict__ y32, const float *__restrict__ 
     __shared__ float sh[2][256];
     const long base = (long)blockIdx.x * N2;
     float sy = 0.0f, st = 0.0f;
-    for (int k = threadIdx.x; k < N2; k += 256) { sy += y32[(base + k) * 16]; st += t[base + k]; }
+    for (int k = threadIdx.x; k < N2; k += 256) { sy += y32[base + k]; st += t[base + k]; }
     sh[0][threadIdx.x] = sy; sh[1][threadIdx.x] = st;
     __syncthreads();
     for (int o = 128; o; o >>= 1) {
@@ -388,7 +483,7 @@ k_loss(int N2, int Bn, const float *__restrict__ y32, const float *__restrict__ 
     float l = 0.0f, gs = 0.0f;
     const float sc = 2.0f / ((float)Bn * (float)N2);
     for (int k = threadIdx.x; k < N2; k += 256) {
-        float d = (y32[(base + k) * 16] - my) - (t[base + k] - mt);
+        float d = (y32[base + k] - my) - (t[base + k] - mt);
         l += d * d;
         gs += sc * d;
     }
@@ -400,7 +495,7 @@ k_loss(int N2, int Bn, const float *__restrict__ y32, const float *__restrict__ 
     }
     const float gmean = sh[1][0] / N2;
     for (int k = threadIdx.x; k < N2; k += 256) {
-        float d = (y32[(base + k) * 16] - my) - (t[base + k] - mt);
+        float d = (y32[base + k] - my) - (t[base + k] - mt);
         uint32_t *gp = (uint32_t *)(gy + (base + k) * 16);
         __nv_bfloat162 v = __floats2bfloat162_rn(sc * d - gmean, 0.0f);
         gp[0] = *(uint32_t *)&v;
@@ -410,22 +505,14 @@ k_loss(int N2, int Bn, const float *__restrict__ y32, const float *__restrict__ 
     if (threadIdx.x == 0) lsum[blockIdx.x] = sh[0][0] / ((float)Bn * (float)N2);
 }
 
-// p0 = s (y - mean y), FP64 out; one CTA per sample.
-__global__ void __launch_bounds__(256)
-k_output(int N2, const float *__restrict__ y32, const double *__restrict__ stats, double *__restrict__ p0)
+// p0 = s pscale (y - mean y), FP64 out.
+__global__ void k_output(long n, int N2, const float *__restrict__ y32, const double *__restrict__ stats,
+                         double pscale, double *__restrict__ p0)
 {
-    __shared__ double sh[256];
-    const long base = (long)blockIdx.x * N2;
-    double s = 0.0;
-    for (int k = threadIdx.x; k < N2; k += 256) s += y32[(base + k) * 16];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double my = sh[0] / N2, sc = stats[3 * blockIdx.x + 1];
-    for (int k = threadIdx.x; k < N2; k += 256) p0[base + k] = sc * ((double)y32[(base + k) * 16] - my);
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double *st = stats + kStat * (k / N2);
+    p0[k] = st[1] * pscale * ((double)y32[k] - st[5]);
 }
 
 // Adam with bias correction on FP32 master weights.
@@ -485,6 +572,7 @@ struct Cnn {
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // flat FP32
     void *wmem = nullptr;
     int step = 0;
+    double out_scale = 1.0;   // c in the pressure scale s h^2 c
     // activation workspace, sized for B x N x N
     int capB = 0, capN = 0;
     void *amem = nullptr;
@@ -494,25 +582,43 @@ struct Cnn {
          *gmid = nullptr, *gmid2 = nullptr, *gsmall = nullptr, *gsmall2 = nullptr, *gcat = nullptr,
          *gup = nullptr;
     float *y32 = nullptr, *t = nullptr, *lsum = nullptr, *gpad = nullptr, *part = nullptr;
-    double *stats = nullptr;
+    double *stats = nullptr, *rpart = nullptr;
     size_t part_cap = 0;
 };
 
 namespace {
 
+int g_sms = 0;
+
+template <int CIN, int COUT, bool MASK>
+void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
+                 const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
+{
+    constexpr size_t sm = conv_smem<CIN, COUT, MASK>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 152;
+    }
+    const int ntiles = B * (int)cdiv(W, CW) * (int)cdiv(H, CH);
+    const int per_sm = sm <= 56 * 1024 ? 4 : (sm <= 75 * 1024 ? 3 : 2);
+    const int grid = std::min(ntiles, g_sms * per_sm);
+    note_launch();
+    k_conv_fwd<CIN, COUT, MASK><<<grid, 128, sm, s>>>(B, H, W, x, xmask, w, bias, relu, y, y32);
+}
+
 template <int CIN, int COUT>
 void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
               const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
 {
-    constexpr size_t sm = conv_smem<CIN, COUT>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conv_fwd<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
-    dim3 g(cdiv(W, CW), cdiv(H, CH), B);
-    note_launch();
-    k_conv_fwd<CIN, COUT><<<g, 128, sm, s>>>(H, W, x, xmask, w, bias, relu, y, y32);
+    if (xmask) conv_launch<CIN, COUT, true>(B, H, W, x, xmask, w, bias, relu, y, y32, s);
+    else conv_launch<CIN, COUT, false>(B, H, W, x, xmask, w, bias, relu, y, y32, s);
 }
 
 template <int CIN, int COUT>
@@ -631,7 +737,8 @@ cudaError_t cnn_workspace(Cnn &n, int B, int N)
                    al(P * (c1 + c2) * 2) + al(P * c1 * 2) + al(P * 16 * 2) +  // cat5, a5, y
                    al(P * 64 * 2) * 2 + al(P2 * 64 * 2) * 2 + al(P4 * 64 * 2) * 2 +  // grads
                    al(P * 64 * 2) + al(P2 * 64 * 2) +      // gcat, gup
-                   al(P * 16 * 4) + al(P * 4) + al(B * 4) + al(n.npad * 4) + al(B * 3 * 8);
+                   al(P * 4) + al(P * 4) + al(B * 4) + al(n.npad * 4) + al(B * kStat * 8) +
+                   al(B * kRedBlocks * 3 * 8);
     const size_t part = (size_t)64 * (64 * 9 * 64 + 64);
     bytes += al(part * 4);
     cudaError_t e = cudaMalloc(&n.amem, bytes);
@@ -649,9 +756,10 @@ cudaError_t cnn_workspace(Cnn &n, int B, int N)
     n.gmid = (bf16 *)take(P2 * 64 * 2); n.gmid2 = (bf16 *)take(P2 * 64 * 2);
     n.gsmall = (bf16 *)take(P4 * 64 * 2); n.gsmall2 = (bf16 *)take(P4 * 64 * 2);
     n.gcat = (bf16 *)take(P * 64 * 2); n.gup = (bf16 *)take(P2 * 64 * 2);
-    n.y32 = (float *)take(P * 16 * 4); n.t = (float *)take(P * 4); n.lsum = (float *)take(B * 4);
+    n.y32 = (float *)take(P * 4); n.t = (float *)take(P * 4); n.lsum = (float *)take(B * 4);
     n.gpad = (float *)take(n.npad * 4);
-    n.stats = (double *)take(B * 3 * 8);
+    n.stats = (double *)take(B * kStat * 8);
+    n.rpart = (double *)take(B * kRedBlocks * 3 * 8);
     n.part = (float *)take(part * 4);
     n.part_cap = part;
     n.capB = B;
@@ -660,14 +768,16 @@ cudaError_t cnn_workspace(Cnn &n, int B, int N)
 }
 
 // Forward pass on B samples of N x N (N a multiple of 4).  Fills the
-// activation workspace; y32 holds the output in channel 0 of 16.
-void cnn_forward(Cnn &n, int B, int N, const double *rhs, const double *rho, const double *p,
-                 cudaStream_t s)
+// activation workspace; y32 holds the FP32 output (one channel).
+void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
+                 const double *p, cudaStream_t s)
 {
     const int N2 = N * N, H2 = N / 2, H4 = N / 4;
     const long P = (long)B * N2;
     note_launch();
-    k_sample_stats<<<B, 256, 0, s>>>(N2, rhs, rho, n.stats);
+    k_stats_part<<<dim3(kRedBlocks, B), 256, 0, s>>>(N2, rhs, rho, n.rpart);
+    note_launch();
+    k_stats_final<<<B, 256, 0, s>>>(N2, rhs, n.rpart, h * h * n.out_scale, n.stats);
     note_launch();
     k_features<<<cdiv(P, 256), 256, 0, s>>>(P, N2, rhs, rho, p, n.stats, n.x, p ? n.t : nullptr);
     auto &L = n.L;
@@ -757,11 +867,20 @@ void cnn_adam(Cnn &n, float lr, cudaStream_t s)
     cnn_pack(n, s);
 }
 
-void cnn_output(Cnn &n, int B, int N, double *p0, cudaStream_t s)
+void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s)
 {
+    const int N2 = N * N;
+    const long P = (long)B * N2;
     note_launch();
-    k_output<<<B, 256, 0, s>>>(N * N, n.y32, n.stats, p0);
+    k_ysum_part<<<dim3(kRedBlocks, B), 256, 0, s>>>(N2, n.y32, n.rpart);
+    note_launch();
+    k_ymean_final<<<B, 256, 0, s>>>(N2, n.rpart, n.stats);
+    note_launch();
+    k_output<<<cdiv(P, 256), 256, 0, s>>>(P, N2, n.y32, n.stats, h * h * n.out_scale, p0);
 }
+
+void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }
+double cnn_get_scale(const Cnn &n) { return n.out_scale; }
 
 size_t cnn_nparam(const Cnn &n) { return n.nparam; }
 float *cnn_weights(Cnn &n) { return n.w; }

@@ -144,6 +144,9 @@ struct Markers {
     unsigned long long *ykey = nullptr;    // order-preserving integer key of each Y
     ulonglong2 *dyk = nullptr;             // keys of the per-drop Y range
     double *sv = nullptr;                  // per segment: 12 strip corner points (24 doubles)
+    double *sl = nullptr;                  // per segment: 8 half-planes (nx, ny, c) FP64
+    float4 *slf = nullptr;                 // the same in FP32 (nx, ny, c, |n|)
+    uint8_t *scvx = nullptr;               // per segment: 1 if all five strips are convex
     float4 *sb5 = nullptr;                 // per segment: FP32 outward box of each of 5 strips
     int32_t *drop_start = nullptr, *drop_of = nullptr, *next = nullptr;
     uint32_t *key = nullptr, *tmp_ids = nullptr, *ids = nullptr,
@@ -179,11 +182,13 @@ Cnn *cnn_new(int c1, int c2, unsigned long long seed, cudaStream_t s, cudaError_
 void cnn_free(Cnn *n);
 cudaError_t cnn_pack(Cnn &n, cudaStream_t s);
 cudaError_t cnn_workspace(Cnn &n, int B, int N);
-void cnn_forward(Cnn &n, int B, int N, const double *rhs, const double *rho, const double *p,
-                 cudaStream_t s);
+void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
+                 const double *p, cudaStream_t s);
 void cnn_backward(Cnn &n, int B, int N, cudaStream_t s);
 void cnn_adam(Cnn &n, float lr, cudaStream_t s);
-void cnn_output(Cnn &n, int B, int N, double *p0, cudaStream_t s);
+void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s);
+void cnn_set_scale(Cnn &n, double c);
+double cnn_get_scale(const Cnn &n);
 size_t cnn_nparam(const Cnn &n);
 float *cnn_weights(Cnn &n);
 float *cnn_grads(Cnn &n);

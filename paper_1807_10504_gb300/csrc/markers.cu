@@ -100,10 +100,19 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
 // Slab box of segment (m, next m): the four corners at offsets -2.5 and +2.5
 // cells along both marker normals, in grid units, rounded outward to FP32 so
 // that an FP32 test against a cell never rejects a strip that touches it.
+// Half-plane {x : n.x - c >= 0} on the left of the directed line P -> Q.
+__device__ __forceinline__ void left_of(double px, double py, double qx, double qy, double *l)
+{
+    const double nx_ = -(qy - py), ny_ = qx - px;
+    l[0] = nx_; l[1] = ny_; l[2] = nx_ * px + ny_ * py;
+}
+
 __global__ void k_segments(int M, const int32_t *__restrict__ next, const double *__restrict__ gx,
                            const double *__restrict__ gy, const double *__restrict__ nxm,
                            const double *__restrict__ nym, float4 *__restrict__ sbox,
-                           double *__restrict__ sv, float4 *__restrict__ sb5)
+                           double *__restrict__ sv, float4 *__restrict__ sb5,
+                           double *__restrict__ sl, float4 *__restrict__ slf,
+                           uint8_t *__restrict__ scvx)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -132,6 +141,32 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
         fx0 = fminf(fx0, f.x); fx1 = fmaxf(fx1, f.y); fy0 = fminf(fy0, f.z); fy1 = fmaxf(fy1, f.w);
     }
     sbox[m] = make_float4(fx0, fx1, fy0, fy1);
+    // half-planes of the slab (the quadrilaterals are counter-clockwise):
+    // 0: normal edge at m (A5 -> A0), 1: normal edge at next m (B0 -> B5),
+    // 2 + o: offset line o (A_o -> B_o), inside = larger offsets
+    double L[8][3];
+    left_of(ax[5], ay[5], ax[0], ay[0], L[0]);
+    left_of(bx[0], by[0], bx[5], by[5], L[1]);
+    for (int o = 0; o < 6; o++) left_of(ax[o], ay[o], bx[o], by[o], L[2 + o]);
+    for (int q = 0; q < 8; q++) {
+        double *d = sl + ((long)m * 8 + q) * 3;
+        d[0] = L[q][0]; d[1] = L[q][1]; d[2] = L[q][2];
+        slf[(long)m * 8 + q] = make_float4((float)L[q][0], (float)L[q][1], (float)L[q][2],
+                                           (float)sqrt(L[q][0] * L[q][0] + L[q][1] * L[q][1]));
+    }
+    // The strips are the intersections of those half-planes only when every
+    // strip quadrilateral (A_k, B_k, B_k+1, A_k+1) is strictly convex; a
+    // radius of curvature below about 2.5 cells folds the inner strips.
+    bool cvx = true;
+    for (int k = 0; k < 5; k++) {
+        const double qx[4] = {ax[k], bx[k], bx[k + 1], ax[k + 1]}, qy[4] = {ay[k], by[k], by[k + 1], ay[k + 1]};
+        for (int c = 0; c < 4; c++) {
+            const int c1 = (c + 1) & 3, c2 = (c + 2) & 3;
+            const double cr = (qx[c1] - qx[c]) * (qy[c2] - qy[c1]) - (qy[c1] - qy[c]) * (qx[c2] - qx[c1]);
+            cvx = cvx && cr > 1e-6;
+        }
+    }
+    scvx[m] = cvx ? 1 : 0;
 }
 
 // One warp per drop: the range of its marker Y.
@@ -531,19 +566,66 @@ constexpr int kBT = kBlk * kBlk;  // one thread per cell of the block
 
 constexpr int kMaxPairs = 1024;  // (cell, segment) pairs with possible overlap per block
 
+// Position of the unit cell [i, i+1] x [j, j+1] against a half-plane
+// n.x - c >= 0 evaluated in FP32 with a margin far above the FP32 error:
+// -1 entirely outside, +1 entirely inside, 0 cut (or too close to tell).
+__device__ __forceinline__ int cell_side(float4 l, float fi, float fj)
+{
+    const float base = l.x * fi + l.y * fj - l.z;
+    const float hi = base + fmaxf(l.x, 0.0f) + fmaxf(l.y, 0.0f);
+    const float lo = base + fminf(l.x, 0.0f) + fminf(l.y, 0.0f);
+    const float m = 1e-2f * l.w;
+    return hi < -m ? -1 : (lo > m ? 1 : 0);
+}
+
+// Clip the convex polygon (x, y)[n] (cell-local coordinates) by the
+// half-plane a x + b y - c >= 0; returns the new vertex count.
+__device__ __forceinline__ int clip_half(double *x, double *y, int n, double a, double b, double c)
+{
+    double ox[10], oy[10];
+    int m = 0;
+    for (int k = 0; k < n; k++) {
+        const int k1 = (k + 1 == n) ? 0 : k + 1;
+        const double fs = a * x[k] + b * y[k] - c, fe = a * x[k1] + b * y[k1] - c;
+        const bool si = fs >= 0.0, ei = fe >= 0.0;
+        if (si && ei) { ox[m] = x[k1]; oy[m] = y[k1]; m++; }
+        else if (si != ei) {
+            const double t = fs / (fs - fe);
+            ox[m] = x[k] + t * (x[k1] - x[k]); oy[m] = y[k] + t * (y[k1] - y[k]); m++;
+            if (ei) { ox[m] = x[k1]; oy[m] = y[k1]; m++; }
+        }
+    }
+    for (int k = 0; k < m; k++) { x[k] = ox[k]; y[k] = oy[k]; }
+    return m;
+}
+
+__device__ __forceinline__ double poly_area(const double *x, const double *y, int n)
+{
+    double a = 0.0;
+    for (int k = 0; k < n; k++) {
+        const int k1 = (k + 1 == n) ? 0 : k + 1;
+        a += x[k] * y[k1] - x[k1] * y[k];
+    }
+    return 0.5 * a;
+}
+
 // Three phases in one CTA per active 8x8 block: (1) every cell counts the
-// candidate segments whose FP32 slab box meets it and the counts are scanned;
-// (2) the (cell, segment) pairs are written in ascending segment order and
-// processed densely, one pair per thread: each of the segment's five strips
-// whose FP32 box meets the cell is clipped against it in FP64; (3) every
-// cell sums its pairs in order.  The FP32 boxes are outward-rounded, so they
-// only skip strips that cannot overlap the cell.
+// candidate segments whose slab (the four outer half-planes) may meet it,
+// tested in FP32, and the counts are scanned; (2) the (cell, segment) pairs
+// are written in ascending segment order and processed densely, one pair per
+// thread: the cell square is clipped in FP64 by the half-planes of the slab
+// and of each strip that cut it (a half-plane containing the whole cell is
+// skipped, one excluding it ends the strip), so that the area of cell and
+// strip needs one or two half-plane clips; (3) every cell sums its pairs in
+// order.  Equal, up to rounding, to clipping each strip quadrilateral against
+// the cell, which is what a segment with a folded (non-convex) strip does.
 __global__ void __launch_bounds__(kBT)
 k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
                  const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
-                 const double *__restrict__ sv, const float4 *__restrict__ sbox,
-                 const float4 *__restrict__ sb5, double *__restrict__ H,
-                 uint32_t *__restrict__ flags)
+                 const double *__restrict__ sl, const float4 *__restrict__ slf,
+                 const uint8_t *__restrict__ scvx, const double *__restrict__ sv,
+                 const float4 *__restrict__ sb5, const float4 *__restrict__ sbox,
+                 double *__restrict__ H, uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
     __shared__ uint32_t pseg[kMaxPairs];
@@ -557,10 +639,17 @@ k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
     const int i = bi * kBlk + (t % kBlk), j = bj * kBlk + (t / kBlk);
     const bool live = i < nx && j < ny;
     const float fi = (float)i, fj = (float)j;
-    auto meets = [&](float4 b) { return !(b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj); };
+    auto meets = [&](uint32_t m) {
+        const float4 b = sbox[m];
+        if (b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj) return false;
+        if (!scvx[m]) return true;
+        const float4 *L = slf + (long)m * 8;
+        return cell_side(L[0], fi, fj) >= 0 && cell_side(L[1], fi, fj) >= 0 &&
+               cell_side(L[2], fi, fj) >= 0 && cell_side(L[7], fi, fj) <= 0;
+    };
     uint32_t c = 0;
     if (live)
-        for (int q = 0; q < n; q++) c += meets(sbox[cand[q]]) ? 1u : 0u;
+        for (int q = 0; q < n; q++) c += meets(cand[q]) ? 1u : 0u;
     cnt[t] = c;
     __syncthreads();
     if (t == 0) {
@@ -577,7 +666,7 @@ k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
     if (live) {
         uint32_t o = cnt[t];
         for (int q = 0; q < n; q++)
-            if (meets(sbox[cand[q]])) { pseg[o] = cand[q]; pcell[o] = (uint8_t)t; o++; }
+            if (meets(cand[q])) { pseg[o] = cand[q]; pcell[o] = (uint8_t)t; o++; }
     }
     __syncthreads();
     double Hk[5];
@@ -588,19 +677,61 @@ k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
         const int ci = bi * kBlk + (ct % kBlk), cj = bj * kBlk + (ct / kBlk);
         const float gi = (float)ci, gj = (float)cj;
         const double di = (double)ci, dj = (double)cj;
-        const double *v = sv + (long)m * 24;
+        if (!scvx[m]) {  // folded strips: clip each quadrilateral against the cell
+            const double *v = sv + (long)m * 24;
+            double acc = 0.0, cov = 0.0;
+            for (int k = 0; k < 5; k++) {
+                const float4 b = sb5[(long)m * 5 + k];
+                if (b.x > gi + 1.0f || b.y < gi || b.z > gj + 1.0f || b.w < gj) continue;
+                double qx[4], qy[4];
+                qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
+                qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
+                qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
+                qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
+                const double A = clip_area_unit(qx, qy);
+                acc += A * Hk[k];
+                cov += A;
+            }
+            pacc[p] = acc;
+            pcov[p] = cov;
+            continue;
+        }
+        const float4 *Lf = slf + (long)m * 8;
+        const double *Ld = sl + (long)m * 24;
+        int side[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) side[q] = cell_side(Lf[q], gi, gj);
+        // the cell square clipped by the slab's normal edges that cut it
+        double px[10] = {0.0, 1.0, 1.0, 0.0}, py[10] = {0.0, 0.0, 1.0, 1.0};
+        int np = 4;
+        for (int q = 0; q < 2 && np > 0; q++)
+            if (side[q] == 0)
+                np = clip_half(px, py, np, Ld[3 * q], Ld[3 * q + 1],
+                               Ld[3 * q + 2] - Ld[3 * q] * di - Ld[3 * q + 1] * dj);
         double acc = 0.0, cov = 0.0;
-        for (int k = 0; k < 5; k++) {
-            const float4 b = sb5[(long)m * 5 + k];
-            if (b.x > gi + 1.0f || b.y < gi || b.z > gj + 1.0f || b.w < gj) continue;
-            double qx[4], qy[4];
-            qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
-            qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
-            qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
-            qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
-            double A = clip_area_unit(qx, qy);
-            acc += A * Hk[k];
-            cov += A;
+        if (np > 0) {
+            const double a0 = poly_area(px, py, np);
+            for (int k = 0; k < 5; k++) {
+                const int lo = 2 + k, hi = 3 + k;  // inside offset k, outside offset k + 1
+                if (side[lo] < 0 || side[hi] > 0) continue;
+                double A;
+                if (side[lo] > 0 && side[hi] < 0) {
+                    A = a0;
+                } else {
+                    double qx[10], qy[10];
+                    for (int v = 0; v < np; v++) { qx[v] = px[v]; qy[v] = py[v]; }
+                    int nq = np;
+                    if (side[lo] == 0)
+                        nq = clip_half(qx, qy, nq, Ld[3 * lo], Ld[3 * lo + 1],
+                                       Ld[3 * lo + 2] - Ld[3 * lo] * di - Ld[3 * lo + 1] * dj);
+                    if (nq > 0 && side[hi] == 0)
+                        nq = clip_half(qx, qy, nq, -Ld[3 * hi], -Ld[3 * hi + 1],
+                                       -(Ld[3 * hi + 2] - Ld[3 * hi] * di - Ld[3 * hi + 1] * dj));
+                    A = nq > 0 ? poly_area(qx, qy, nq) : 0.0;
+                }
+                acc += A * Hk[k];
+                cov += A;
+            }
         }
         pacc[p] = acc;
         pcov[p] = cov;
@@ -939,7 +1070,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     size_t ncell = (size_t)nx * ny, nb = (size_t)mk.bnx * mk.bny;
     size_t nparts = (ncell + kScanChunk - 1) / kScanChunk;
     size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
-                   al((size_t)M * 24 * 8) + al((size_t)M * 5 * 16) + al(M * 8) +
+                   al((size_t)M * 24 * 8) * 2 + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
@@ -957,7 +1088,10 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.dyr = (double2 *)take(ndrops * 16);
     mk.dyk = (ulonglong2 *)take(ndrops * 16);
     mk.sv = (double *)take((size_t)M * 24 * 8);
+    mk.sl = (double *)take((size_t)M * 24 * 8);
+    mk.slf = (float4 *)take((size_t)M * 8 * 16);
     mk.sb5 = (float4 *)take((size_t)M * 5 * 16);
+    mk.scvx = (uint8_t *)take(M);
     mk.ykey = (unsigned long long *)take(M * 8);
     mk.drop_start = (int32_t *)take((ndrops + 1) * 4);
     mk.drop_of = (int32_t *)take(M * 4);
@@ -1003,7 +1137,7 @@ void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
                                             mk.fmag, mk.gx, mk.gy, mk.gxf, mk.gyf, mk.ykey);
     note_launch();
     k_segments<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox,
-                                            mk.sv, mk.sb5);
+                                            mk.sv, mk.sb5, mk.sl, mk.slf, mk.scvx);
     note_launch();
     k_drop_yrange<<<cdiv((long)mk.ndrops * 32, kT), kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.Y,
                                                                mk.dyr, mk.dyk);
@@ -1062,7 +1196,8 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
     dim3 g(mk.bnx, mk.bny);
     note_launch();
     k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids,
-                                       mk.sv, mk.sbox, mk.sb5, H, mk.flags);
+                                       mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5,
+                                       mk.sbox, H, mk.flags);
 }
 
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H, double *Fx,

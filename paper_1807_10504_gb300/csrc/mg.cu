@@ -101,56 +101,79 @@ __global__ void __launch_bounds__(FT)
 k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float *__restrict__ by,
             const float *__restrict__ invd, const float *__restrict__ b, float *__restrict__ p)
 {
-    constexpr int PW = FW + 8, PH = FH + 8;      // p with halo 4
-    constexpr int CW = FW + 6, CH = FH + 6;      // cell data with halo 3
-    __shared__ float ps[PH][PW];
-    __shared__ float bs[CH][CW], ds[CH][CW], xs[CH][CW + 1], ys[CH + 1][CW];
+    // every array staged on the same haloed window: rows gj0 .. gj0 + PH - 1,
+    // columns gi0 .. gi0 + PW - 1 (halo 4), y-faces one row more, x-faces one
+    // column more; rows of cell and y-face arrays are read as float4 when the
+    // window start is 16-byte aligned (nx % 4 == 0), the rest element-wise.
+    constexpr int PW = FW + 8, PH = FH + 8;
+    __shared__ __align__(16) float ps[PH][PW];
+    __shared__ __align__(16) float bs[PH][PW];
+    __shared__ __align__(16) float ds[PH][PW];
+    __shared__ __align__(16) float ys[PH + 1][PW];
+    __shared__ float xs[PH][PW + 1];
     const int gi0 = blockIdx.x * FW - 4, gj0 = blockIdx.y * FH - 4;
     const long nxf = nx + 1;
-    for (int k = threadIdx.x; k < PH * PW; k += FT) {
-        int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
-        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? p[(long)gj * nx + gi] : 0.0f;
+    const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
+    if (vec) {
+        constexpr int V = PW / 4;  // float4 per row
+        for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
+            const int r = k / V, c4 = k - r * V, gj = gj0 + r;
+            const long o = (long)gj * nx + gi0 + 4 * c4;
+            if (r < PH) {
+                float4 vp = make_float4(0.f, 0.f, 0.f, 0.f), vb = vp, vd = vp;
+                if (gj >= 0 && gj < ny) {
+                    vp = *(const float4 *)(p + o);
+                    vb = *(const float4 *)(b + o);
+                    vd = *(const float4 *)(invd + o);
+                }
+                *(float4 *)&ps[r][4 * c4] = vp;
+                *(float4 *)&bs[r][4 * c4] = vb;
+                *(float4 *)&ds[r][4 * c4] = vd;
+            }
+            float4 vy = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gj >= 0 && gj <= ny) vy = *(const float4 *)(by + o);
+            *(float4 *)&ys[r][4 * c4] = vy;
+        }
+    } else {
+        for (int k = threadIdx.x; k < (PH + 1) * PW; k += FT) {
+            const int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
+            const long o = (long)gj * nx + gi;
+            if (r < PH) {
+                const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+                ps[r][c] = in ? p[o] : 0.0f;
+                bs[r][c] = in ? b[o] : 0.0f;
+                ds[r][c] = in ? invd[o] : 0.0f;
+            }
+            ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[o] : 0.0f;
+        }
     }
-    for (int k = threadIdx.x; k < CH * CW; k += FT) {
-        int r = k / CW, c = k - r * CW, gi = gi0 + 1 + c, gj = gj0 + 1 + r;
-        bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-        long kc = (long)gj * nx + gi;
-        bs[r][c] = in ? b[kc] : 0.0f;
-        ds[r][c] = in ? invd[kc] : 0.0f;
-    }
-    for (int k = threadIdx.x; k < CH * (CW + 1); k += FT) {
-        int r = k / (CW + 1), c = k - r * (CW + 1), gi = gi0 + 1 + c, gj = gj0 + 1 + r;
+    for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
+        const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
         xs[r][c] = (gi >= 0 && gi <= nx && gj >= 0 && gj < ny) ? bx[(long)gj * nxf + gi] : 0.0f;
     }
-    for (int k = threadIdx.x; k < (CH + 1) * CW; k += FT) {
-        int r = k / CW, c = k - r * CW, gi = gi0 + 1 + c, gj = gj0 + 1 + r;
-        ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[(long)gj * nx + gi] : 0.0f;
-    }
     __syncthreads();
-    // ring q: local p rows/cols [4-q, 4+F+q); colour: 0 red, 1 black
+    // ring q: local rows/cols [4-q, 4+F+q); colour: 0 red, 1 black
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = 3 - ph, color = ph & 1;
         const int w = FW + 2 * q, hgt = FH + 2 * q, hw = w / 2;
         for (int k = threadIdx.x; k < hgt * hw; k += FT) {
-            int rr = k / hw, cc = k - rr * hw;
-            int r = 4 - q + rr;                       // local p row
-            int gj = gj0 + r;
-            int c = 4 - q + 2 * cc + ((gi0 + 4 - q + gj + color) & 1);
-            int gi = gi0 + c;
+            const int rr = k / hw, cc = k - rr * hw;
+            const int r = 4 - q + rr, gj = gj0 + r;
+            const int c = 4 - q + 2 * cc + ((gi0 + 4 - q + gj + color) & 1);
+            const int gi = gi0 + c;
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
-            int r1 = r - 1, c1 = c - 1;               // local cell-data indices
-            float sm = xs[r1][c1 + 1] * ps[r][c + 1];
-            sm = fmaf(xs[r1][c1], ps[r][c - 1], sm);
-            sm = fmaf(ys[r1 + 1][c1], ps[r + 1][c], sm);
-            sm = fmaf(ys[r1][c1], ps[r - 1][c], sm);
-            ps[r][c] = (sm - h2 * bs[r1][c1]) * ds[r1][c1];
+            float sm = xs[r][c + 1] * ps[r][c + 1];
+            sm = fmaf(xs[r][c], ps[r][c - 1], sm);
+            sm = fmaf(ys[r + 1][c], ps[r + 1][c], sm);
+            sm = fmaf(ys[r][c], ps[r - 1][c], sm);
+            ps[r][c] = (sm - h2 * bs[r][c]) * ds[r][c];
         }
         __syncthreads();
     }
     for (int k = threadIdx.x; k < FH * FW; k += FT) {
-        int r = 4 + k / FW, c = 4 + (k - (k / FW) * FW);
-        int gi = gi0 + c, gj = gj0 + r;
+        const int r = 4 + k / FW, c = 4 + (k - (k / FW) * FW);
+        const int gi = gi0 + c, gj = gj0 + r;
         if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
     }
 }
@@ -245,40 +268,59 @@ __global__ void k_coarsen_beta(int nx, int ny, const double *__restrict__ bx,
     byc[k] = 0.5 * (by[(long)(2 * J) * nx + 2 * I] + by[(long)(2 * J) * nx + 2 * I + 1]);
 }
 
-// Level-0 coefficients with the wall faces forced to zero.
-__global__ void k_copy_beta(int nx, int ny, const double *__restrict__ bx,
-                            const double *__restrict__ by, double *__restrict__ ox,
-                            double *__restrict__ oy)
+// Coefficients of one level in one pass, one thread per cell: the cell's
+// west and south faces (and the east / north wall faces of the last column /
+// row) from the finer level (mean of the two fine faces; at level 0 the
+// caller's faces with the walls set to zero), their FP32 copies, and the FP64
+// and FP32 inverse diagonals (the cell's four faces, recomputed locally).
+__global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
+                               const double *__restrict__ fby, double *__restrict__ bx,
+                               double *__restrict__ by, float *__restrict__ bxf,
+                               float *__restrict__ byf, double *__restrict__ invd,
+                               float *__restrict__ invdf)
 {
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long nxf = (long)(nx + 1) * ny;
-    if (k < nxf) {
-        int j = (int)(k / (nx + 1)), i = (int)(k - (long)j * (nx + 1));
-        ox[k] = (i == 0 || i == nx) ? 0.0 : bx[k];
-        return;
-    }
-    k -= nxf;
-    if (k >= (long)nx * (ny + 1)) return;
-    int j = (int)(k / nx);
-    oy[k] = (j == 0 || j == ny) ? 0.0 : by[k];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const int fnx = 2 * nx;  // finer level width (unused at level 0)
+    auto xface = [&](int I, int J) -> double {   // coefficient of x-face (I, J)
+        if (I == 0 || I == nx) return 0.0;
+        if (level0) return fbx[(long)J * (nx + 1) + I];
+        return 0.5 * (fbx[(long)(2 * J) * (fnx + 1) + 2 * I] + fbx[(long)(2 * J + 1) * (fnx + 1) + 2 * I]);
+    };
+    auto yface = [&](int I, int J) -> double {
+        if (J == 0 || J == ny) return 0.0;
+        if (level0) return fby[(long)J * nx + I];
+        return 0.5 * (fby[(long)(2 * J) * fnx + 2 * I] + fby[(long)(2 * J) * fnx + 2 * I + 1]);
+    };
+    const double w = xface(i, j), e = xface(i + 1, j), s = yface(i, j), n = yface(i, j + 1);
+    const long kx = (long)j * (nx + 1) + i, kc = (long)j * nx + i;
+    bx[kx] = w; bxf[kx] = (float)w;
+    by[kc] = s; byf[kc] = (float)s;
+    if (i == nx - 1) { bx[kx + 1] = e; bxf[kx + 1] = (float)e; }
+    if (j == ny - 1) { by[kc + nx] = n; byf[kc + nx] = (float)n; }
+    const double d = e + w + n + s;
+    const double id = d > 0.0 ? 1.0 / d : 0.0;
+    invd[kc] = id;
+    invdf[kc] = (float)id;
 }
 
-__global__ void k_to_float(long n, const double *__restrict__ a, float *__restrict__ b)
-{
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) b[k] = (float)a[k];
-}
-
-// ------------------------------------------------------------ coarsest LU
-// Dense A' = A + s 1 1^T (s = A_00), then LU with partial pivoting (first
-// maximal |pivot|), one CTA.
+// ------------------------------------------------------------ coarsest solve
+// Dense A' = A + s 1 1^T (s = A_00, removes the constant null space), then its
+// inverse by Gauss-Jordan elimination with partial pivoting (first maximal
+// |pivot|), stored transposed (Ainv^T) so that the per-cycle solve x = A'^-1 r
+// is one coalesced matrix-vector product.  One CTA; A and the inverse live in
+// the scratch `A` (2 n^2).
 __global__ void __launch_bounds__(1024)
-k_coarse_lu(int nx, int ny, double h, const double *__restrict__ bx,
-            const double *__restrict__ by, double *__restrict__ A, int *__restrict__ piv)
+k_coarse_inv(int nx, int ny, double h, const double *__restrict__ bx,
+             const double *__restrict__ by, double *__restrict__ A, double *__restrict__ AinvT)
 {
     const int n = nx * ny;
     const double hh = h * h;
-    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] = 0.0;
+    double *X = AinvT;  // identity, then the inverse (row-major), transposed at the end
+    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
+        A[k] = 0.0;
+        X[k] = (k / n == k % n) ? 1.0 : 0.0;
+    }
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         int i = c % nx, j = c / nx;
@@ -303,25 +345,38 @@ k_coarse_lu(int nx, int ny, double h, const double *__restrict__ bx,
             for (int r = c + 1; r < n; r++)
                 if (fabs(A[(long)r * n + c]) > fabs(A[(long)best * n + c])) best = r;
             pr = best;
-            piv[c] = best;
         }
         __syncthreads();
         if (pr != c)
             for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double t = A[(long)c * n + k];
-                A[(long)c * n + k] = A[(long)pr * n + k];
-                A[(long)pr * n + k] = t;
+                double t = A[(long)c * n + k]; A[(long)c * n + k] = A[(long)pr * n + k]; A[(long)pr * n + k] = t;
+                t = X[(long)c * n + k]; X[(long)c * n + k] = X[(long)pr * n + k]; X[(long)pr * n + k] = t;
             }
         __syncthreads();
-        double d = A[(long)c * n + c];
-        for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) A[(long)r * n + c] /= d;
+        __shared__ double dpiv;
+        if (threadIdx.x == 0) dpiv = A[(long)c * n + c];
         __syncthreads();
-        int w = n - c - 1;
-        for (long k = threadIdx.x; k < (long)w * w; k += blockDim.x) {
-            int r = c + 1 + (int)(k / w), q = c + 1 + (int)(k % w);
-            A[(long)r * n + q] -= A[(long)r * n + c] * A[(long)c * n + q];
+        const double d = dpiv;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) { A[(long)c * n + k] /= d; X[(long)c * n + k] /= d; }
+        __syncthreads();
+        for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
+            const int r = (int)(k / n), q = (int)(k % n);
+            if (r == c) continue;
+            const double f = A[(long)r * n + c];
+            if (q != c) A[(long)r * n + q] -= f * A[(long)c * n + q];
+            X[(long)r * n + q] -= f * X[(long)c * n + q];
         }
         __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x)
+            if (r != c) A[(long)r * n + c] = 0.0;
+        __syncthreads();
+    }
+    // transpose X in place through A (A is no longer needed)
+    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] = X[k];
+    __syncthreads();
+    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
+        const int r = (int)(k / n), q = (int)(k % n);
+        AinvT[(long)q * n + r] = A[k];
     }
 }
 
@@ -334,35 +389,9 @@ struct TailArgs {
     T h2[kMaxLv], ih2[kMaxLv];
     T *e[kMaxLv], *r[kMaxLv];
     const T *bx[kMaxLv], *by[kMaxLv], *invd[kMaxLv];
-    const double *lu;
-    const int *piv;
+    const double *ainvT;   // coarsest inverse, transposed
     int nu1, nu2;
 };
-
-template <typename T>
-__device__ void tail_smooth(const TailArgs<T> &a, int l, int nsw)
-{
-    const int nx = a.nx[l], ny = a.ny[l], n = nx * ny;
-    const T *bx = a.bx[l], *by = a.by[l], *invd = a.invd[l], *r = a.r[l];
-    T *e = a.e[l];
-    const T h2 = a.h2[l];
-    for (int s = 0; s < nsw; s++)
-        for (int color = 0; color < 2; color++) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                int j = k / nx, i = k - j * nx;
-                if (((i + j) & 1) != color) continue;
-                long kx = (long)j * (nx + 1) + i;
-                T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
-                T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
-                T sm = bx[kx + 1] * pE;
-                sm = fma(bx[kx], pW, sm);
-                sm = fma(by[k + nx], pN, sm);
-                sm = fma(by[k], pS, sm);
-                e[k] = (sm - h2 * r[k]) * invd[k];
-            }
-            __syncthreads();
-        }
-}
 
 template <typename T>
 __host__ __device__ size_t tail_smem_elems(const TailArgs<T> &a)
@@ -375,95 +404,147 @@ __host__ __device__ size_t tail_smem_elems(const TailArgs<T> &a)
     return n;
 }
 
+// Shared-memory view of the tail levels (one copy per block).
+template <typename T>
+struct TailView {
+    T *e[kMaxLv], *r[kMaxLv], *bx[kMaxLv], *by[kMaxLv], *iv[kMaxLv];
+};
+
+// Work of one level by a group of `nt` threads (thread index t): the whole
+// block, or one warp for the small levels, where block barriers would cost
+// more than the work.
+template <typename T, bool WARP>
+__device__ __forceinline__ void tsync()
+{
+    if (WARP) __syncwarp(); else __syncthreads();
+}
+
+template <typename T, bool WARP>
+__device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, int nsw, int t, int nt)
+{
+    const int nx = g.nx[l], ny = g.ny[l], n = nx * ny;
+    const T *bx = v.bx[l], *by = v.by[l], *invd = v.iv[l], *r = v.r[l];
+    T *e = v.e[l];
+    const T h2 = g.h2[l];
+    for (int s = 0; s < nsw; s++)
+        for (int color = 0; color < 2; color++) {
+            for (int k = t; k < n; k += nt) {
+                const int j = k / nx, i = k - j * nx;
+                if (((i + j) & 1) != color) continue;
+                const int kx = j * (nx + 1) + i;
+                const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
+                const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
+                T sm = bx[kx + 1] * pE;
+                sm = fma(bx[kx], pW, sm);
+                sm = fma(by[k + nx], pN, sm);
+                sm = fma(by[k], pS, sm);
+                e[k] = (sm - h2 * r[k]) * invd[k];
+            }
+            tsync<T, WARP>();
+        }
+}
+
+template <typename T, bool WARP>
+__device__ void tail_restrict(const TailArgs<T> &g, const TailView<T> &v, int l, int t, int nt)
+{
+    const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nc = nxc * (ny / 2);
+    const T *bx = v.bx[l], *by = v.by[l], *b = v.r[l], *p = v.e[l];
+    const T ih2 = g.ih2[l];
+    for (int k = t; k < nc; k += nt) {
+        const int J = k / nxc, I = k - J * nxc, i = 2 * I, j = 2 * J;
+        T r00 = b[j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+        T r10 = b[j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * ih2;
+        T r01 = b[(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * ih2;
+        T r11 = b[(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * ih2;
+        v.r[l + 1][k] = T(0.25) * (r00 + r10 + r01 + r11);
+        v.e[l + 1][k] = T(0);
+    }
+    tsync<T, WARP>();
+}
+
+template <typename T, bool WARP>
+__device__ void tail_prolong(const TailArgs<T> &g, const TailView<T> &v, int l, int t, int nt)
+{
+    const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nyc = ny / 2;
+    const T *ec = v.e[l + 1];
+    T *ef = v.e[l];
+    for (int k = t; k < nx * ny; k += nt) {
+        const int j = k / nx, i = k - j * nx;
+        const int I = i >> 1, J = j >> 1;
+        const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
+        const int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
+        const T c00 = ec[J * nxc + I], c10 = ec[J * nxc + I2];
+        const T c01 = ec[J2 * nxc + I], c11 = ec[J2 * nxc + I2];
+        ef[k] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
+    }
+    tsync<T, WARP>();
+}
+
 // The lower V-cycle (levels lt..L-1, each at most 1024 cells) in one CTA: the
 // coefficients and the level-lt iterate and right-hand side are copied into
 // shared memory, the cycle runs there, and the level-lt iterate is copied
-// back.
+// back.  Levels of at least 512 cells use the whole block; the smaller ones
+// and the coarsest LU solve run in warp 0 alone with warp barriers.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
 {
     extern __shared__ __align__(16) unsigned char tail_sm[];
     __shared__ double xs[kMaxCoarsest];
-    TailArgs<T> a = g;
-    T *q = (T *)tail_sm;
-    for (int l = g.lt; l < g.nl; l++) {
-        const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
-        T *e = q, *r = q + c, *iv = q + 2 * c, *bxs = q + 3 * c, *bys = q + 3 * c + fx;
-        q += 3 * c + fx + fy;
-        for (int k = threadIdx.x; k < c; k += blockDim.x) {
-            iv[k] = g.invd[l][k];
-            if (l == g.lt) { e[k] = g.e[l][k]; r[k] = g.r[l][k]; }
+    __shared__ TailView<T> v;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) {
+        T *q = (T *)tail_sm;
+        for (int l = g.lt; l < g.nl; l++) {
+            const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
+            v.e[l] = q; v.r[l] = q + c; v.iv[l] = q + 2 * c; v.bx[l] = q + 3 * c; v.by[l] = q + 3 * c + fx;
+            q += 3 * c + fx + fy;
         }
-        for (int k = threadIdx.x; k < fx; k += blockDim.x) bxs[k] = g.bx[l][k];
-        for (int k = threadIdx.x; k < fy; k += blockDim.x) bys[k] = g.by[l][k];
-        a.e[l] = e; a.r[l] = r; a.invd[l] = iv; a.bx[l] = bxs; a.by[l] = bys;
     }
     __syncthreads();
-    const int L = a.nl;
-    for (int l = a.lt; l < L - 1; l++) {
-        tail_smooth(a, l, a.nu1);
-        const int nx = a.nx[l], ny = a.ny[l], nxc = nx / 2, nc = nxc * (ny / 2);
-        const T *bx = a.bx[l], *by = a.by[l], *b = a.r[l], *p = a.e[l];
-        for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-            int J = k / nxc, I = k - J * nxc, i = 2 * I, j = 2 * J;
-            T r00 = b[(long)j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * a.ih2[l];
-            T r10 = b[(long)j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * a.ih2[l];
-            T r01 = b[(long)(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * a.ih2[l];
-            T r11 = b[(long)(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * a.ih2[l];
-            a.r[l + 1][k] = T(0.25) * (r00 + r10 + r01 + r11);
-            a.e[l + 1][k] = T(0);
+    for (int l = g.lt; l < g.nl; l++) {
+        const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
+        for (int k = tid; k < c; k += nthr) {
+            v.iv[l][k] = g.invd[l][k];
+            if (l == g.lt) { v.e[l][k] = g.e[l][k]; v.r[l][k] = g.r[l][k]; }
         }
-        __syncthreads();
+        for (int k = tid; k < fx; k += nthr) v.bx[l][k] = g.bx[l][k];
+        for (int k = tid; k < fy; k += nthr) v.by[l][k] = g.by[l][k];
     }
-    // coarsest: x = A'^{-1} r by the stored LU (row swaps, unit lower, upper)
-    {
-        const int lc = L - 1, n = a.nx[lc] * a.ny[lc];
-        for (int k = threadIdx.x; k < n; k += blockDim.x) xs[k] = (double)a.r[lc][k];
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            if (lane == 0)
-                for (int c = 0; c < n; c++) {
-                    int pr = a.piv[c];
-                    if (pr != c) { double t = xs[c]; xs[c] = xs[pr]; xs[pr] = t; }
-                }
-            __syncwarp();
-            for (int rr = 0; rr < n; rr++) {
-                double s = 0.0;
-                for (int k = lane; k < rr; k += 32) s += a.lu[(long)rr * n + k] * xs[k];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) xs[rr] -= s;
-                __syncwarp();
-            }
-            for (int rr = n - 1; rr >= 0; rr--) {
-                double s = 0.0;
-                for (int k = rr + 1 + lane; k < n; k += 32) s += a.lu[(long)rr * n + k] * xs[k];
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) xs[rr] = (xs[rr] - s) / a.lu[(long)rr * n + rr];
-                __syncwarp();
-            }
+    __syncthreads();
+    const int L = g.nl;
+    int lb = g.lt;  // first level handled by warp 0 alone
+    while (lb < L - 1 && g.nx[lb] * g.ny[lb] >= 512) lb++;
+    for (int l = g.lt; l < lb; l++) {
+        tail_smooth<T, false>(g, v, l, g.nu1, tid, nthr);
+        tail_restrict<T, false>(g, v, l, tid, nthr);
+    }
+    if (tid < 32) {
+        const int lane = tid;
+        for (int l = lb; l < L - 1; l++) {
+            tail_smooth<T, true>(g, v, l, g.nu1, lane, 32);
+            tail_restrict<T, true>(g, v, l, lane, 32);
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) a.e[lc][k] = (T)xs[k];
-        __syncthreads();
-    }
-    for (int l = L - 2; l >= a.lt; l--) {
-        const int nx = a.nx[l], ny = a.ny[l], nxc = nx / 2, nyc = ny / 2;
-        const T *ec = a.e[l + 1];
-        T *ef = a.e[l];
-        for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
-            int j = k / nx, i = k - j * nx;
-            int I = i >> 1, J = j >> 1;
-            int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
-            int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
-            T c00 = ec[J * nxc + I], c10 = ec[J * nxc + I2];
-            T c01 = ec[J2 * nxc + I], c11 = ec[J2 * nxc + I2];
-            ef[k] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
+        // coarsest: x = A'^{-1} r, one row of the inverse per lane
+        const int lc = L - 1, n = g.nx[lc] * g.ny[lc];
+        for (int k = lane; k < n; k += 32) xs[k] = (double)v.r[lc][k];
+        __syncwarp();
+        for (int k = lane; k < n; k += 32) {
+            double acc = 0.0;
+            for (int q = 0; q < n; q++) acc += g.ainvT[(long)q * n + k] * xs[q];
+            v.e[lc][k] = (T)acc;
         }
-        __syncthreads();
-        tail_smooth(a, l, a.nu2);
+        __syncwarp();
+        for (int l = L - 2; l >= lb; l--) {
+            tail_prolong<T, true>(g, v, l, lane, 32);
+            tail_smooth<T, true>(g, v, l, g.nu2, lane, 32);
+        }
     }
-    for (int k = threadIdx.x; k < a.nx[a.lt] * a.ny[a.lt]; k += blockDim.x) g.e[a.lt][k] = a.e[a.lt][k];
+    __syncthreads();
+    for (int l = lb - 1; l >= g.lt; l--) {
+        tail_prolong<T, false>(g, v, l, tid, nthr);
+        tail_smooth<T, false>(g, v, l, g.nu2, tid, nthr);
+    }
+    for (int k = tid; k < g.nx[g.lt] * g.ny[g.lt]; k += nthr) g.e[g.lt][k] = v.e[g.lt][k];
 }
 
 // --------------------------------------------------------------- reductions
@@ -545,14 +626,14 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
           const double *__restrict__ p, float *__restrict__ rf, float *__restrict__ ef,
           double *part, unsigned *count, double *out)
 {
-    const long n = (long)nx * ny;
     double s = 0.0;
-    for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT) {
-        int j = (int)(k / nx), i = (int)(k - (long)j * nx);
-        double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
-        s += r * r;
-        if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
-    }
+    for (int j = blockIdx.x; j < ny; j += gridDim.x)
+        for (int i = threadIdx.x; i < nx; i += kRedT) {
+            const long k = (long)j * nx + i;
+            const double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+            s += r * r;
+            if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
+        }
     block_fold_and_finish<NoOp>(s, part, count, out);
 }
 
@@ -637,8 +718,7 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
         ta.h2[l] = (T)(v.h * v.h); ta.ih2[l] = (T)(1.0 / (v.h * v.h));
         ta.e[l] = a.e; ta.r[l] = a.r; ta.bx[l] = a.bx; ta.by[l] = a.by; ta.invd[l] = a.invd;
     }
-    ta.lu = mg.lu;
-    ta.piv = mg.piv;
+    ta.ainvT = mg.lu + (size_t)mg.lv[mg.L - 1].nx * mg.lv[mg.L - 1].ny * mg.lv[mg.L - 1].nx * mg.lv[mg.L - 1].ny;
     ta.nu1 = nu1;
     ta.nu2 = nu2;
     note_launch();
@@ -756,7 +836,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         v.f.e = (float *)take(n * 4); v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
         v.f.bx = (float *)take(fx * 4); v.f.by = (float *)take(fy * 4);
     }
-    mg.lu = (double *)take((size_t)nc * nc * 8);
+    mg.lu = (double *)take((size_t)nc * nc * 8 * 2);  // A' and its transposed inverse
     mg.piv = (int *)take((size_t)nc * 4);
     mg.red = (double *)take((size_t)(mg.red_blocks + 16) * 8);
     mg.red_count = (unsigned *)take(64);
@@ -802,28 +882,13 @@ void mg_free(MG &mg)
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 {
     const int L = mg.L;
-    Level &v0 = mg.lv[0];
-    long nf0 = (long)(v0.nx + 1) * v0.ny + (long)v0.nx * (v0.ny + 1);
-    note_launch();
-    k_copy_beta<<<cdiv(nf0, 256), 256, 0, s>>>(v0.nx, v0.ny, bx, by, v0.d.bx, v0.d.by);
     for (int l = 0; l < L; l++) {
         Level &v = mg.lv[l];
-        if (l > 0) {
-            Level &f = mg.lv[l - 1];
-            long nfc = (long)(v.nx + 1) * v.ny + (long)v.nx * (v.ny + 1);
-            note_launch();
-            k_coarsen_beta<<<cdiv(nfc, 256), 256, 0, s>>>(f.nx, f.ny, f.d.bx, f.d.by, v.d.bx, v.d.by);
-        }
+        const double *fbx = l == 0 ? bx : mg.lv[l - 1].d.bx, *fby = l == 0 ? by : mg.lv[l - 1].d.by;
         dim3 g(cdiv(v.nx, 128), v.ny);
         note_launch();
-        k_invdiag<double><<<g, 128, 0, s>>>(v.nx, v.ny, v.d.bx, v.d.by, v.d.invd);
-        note_launch();
-        k_invdiag<float><<<g, 128, 0, s>>>(v.nx, v.ny, v.d.bx, v.d.by, v.f.invd);
-        long fx = (long)(v.nx + 1) * v.ny, fy = (long)v.nx * (v.ny + 1);
-        note_launch();
-        k_to_float<<<cdiv(fx, 256), 256, 0, s>>>(fx, v.d.bx, v.f.bx);
-        note_launch();
-        k_to_float<<<cdiv(fy, 256), 256, 0, s>>>(fy, v.d.by, v.f.by);
+        k_level_coeffs<<<g, 128, 0, s>>>(v.nx, v.ny, l == 0, fbx, fby, v.d.bx, v.d.by, v.f.bx, v.f.by,
+                                         v.d.invd, v.f.invd);
     }
     {
         // shared memory of the single-CTA tail (set here, outside any capture)
@@ -837,7 +902,8 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     }
     Level &vc = mg.lv[L - 1];
     note_launch();
-    k_coarse_lu<<<1, 1024, 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu, mg.piv);
+    const size_t nc2 = (size_t)vc.nx * vc.ny * vc.nx * vc.ny;
+    k_coarse_inv<<<1, 1024, 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu, mg.lu + nc2);
 }
 
 // Host-driven solve: one launch per kernel and a host read of the residual

@@ -67,10 +67,24 @@ def generate(n_samples, n_cells=128, seed=0, every=5, steps_per_run=40, precisio
     return B, R, P
 
 
+def pressure_scale(data):
+    """The constant c of the network's pressure scale s h^2 c: the median over
+    the samples of rms(p - mean p) / (rms(b - mean b) h^2), h = 1/N."""
+    B, R, P = data
+    N = B.shape[-1]
+    b0 = B - B.mean(dim=(1, 2), keepdim=True)
+    p0 = P - P.mean(dim=(1, 2), keepdim=True)
+    sb = b0.pow(2).mean(dim=(1, 2)).sqrt()
+    sp = p0.pow(2).mean(dim=(1, 2)).sqrt()
+    return float((sp / (sb / N ** 2)).median())
+
+
 def train(net: Net, data, steps=1000, batch=16, lr=2e-3, seed=0, time_budget=None):
-    """Adam on random mini-batches; returns the list of batch losses."""
+    """Adam on random mini-batches; returns the list of batch losses.  Sets
+    the network's pressure scale from the data first."""
     torch = _torch()
     B, R, P = data
+    net.scale = pressure_scale(data)
     gen = torch.Generator(device="cpu").manual_seed(seed)
     losses = []
     t0 = time.perf_counter()

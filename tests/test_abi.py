@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "ib.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(?:ib_status|void|const char|int32_t|int64_t|unsigned long long)\s*\**\s*(\w+)\s*\(", src)
+    names = re.findall(r"\b(?:ib_status|void|const char|int32_t|int64_t|double|unsigned long long)\s*\**\s*(\w+)\s*\(", src)
     return sorted(set(names))
 
 

@@ -50,12 +50,23 @@ def batch(B, N, seed):
     return rhs, rho, p
 
 
-def oracle_inputs(rhs, rho, p):
+def oracle_inputs(rhs, rho, p, c=1.0):
+    # pressure scale s h^2 c with h = 1/N
+    h2c = c / rhs.shape[-1] ** 2
     xs, ss, ts = [], [], []
     for k in range(rhs.shape[0]):
         x, s = OC.features(rhs[k], 1.0 / rho[k])
-        xs.append(x[0]); ss.append(s); ts.append(p[k] / s)
+        xs.append(x[0]); ss.append(s * h2c); ts.append(p[k] / (s * h2c))
     return bf16(np.stack(xs)), np.array(ss), np.stack(ts)[..., None]
+
+
+def fitted_scale(rhs, p):
+    # the median over samples of rms(p - mean p) / (rms(b - mean b) h^2)
+    N = rhs.shape[-1]
+    b0 = rhs - rhs.mean(axis=(1, 2), keepdims=True)
+    p0 = p - p.mean(axis=(1, 2), keepdims=True)
+    return float(np.median(np.sqrt((p0 ** 2).mean(axis=(1, 2))) /
+                           (np.sqrt((b0 ** 2).mean(axis=(1, 2))) / N ** 2)))
 
 
 def test_forward_matches_oracle(T):
@@ -85,9 +96,11 @@ def test_gradients_match_oracle(T):
     net = ib.Net(seed=0)
     net.set_params(flat_of(P))
     rhs, rho, p = batch(B, N, 5)
+    c = fitted_scale(rhs, p)
+    net.scale = c
     d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
     loss, g = net.grad(d(rhs), d(rho), d(p))
-    x, s, t = oracle_inputs(rhs, rho, p)
+    x, s, t = oracle_inputs(rhs, rho, p, c)
     y, cache = OC.forward(Pq, x, keep=True)
     L, gy = OC.loss(y, t)
     G, _ = OC.backward(Pq, cache, gy)
@@ -97,7 +110,7 @@ def test_gradients_match_oracle(T):
     # shifts of the output); every other gradient must point the same way as
     # the FP64 one (BF16 activations and gradients round at every layer, and
     # the pixel sums cancel, so the relative error grows towards the input).
-    assert abs(Gg["c6.b"][0]) <= 1e-4 * np.linalg.norm(G["c6.w"])
+    assert abs(Gg["c6.b"][0]) <= 2e-3 * np.linalg.norm(G["c6.w"])
     for n, _, _, _ in OC.LAYERS:
         for k in (".w", ".b"):
             if n + k == "c6.b":
@@ -105,7 +118,7 @@ def test_gradients_match_oracle(T):
             a, ref = Gg[n + k].ravel(), G[n + k].ravel()
             cos = a @ ref / (np.linalg.norm(a) * np.linalg.norm(ref))
             err = np.linalg.norm(a - ref) / np.linalg.norm(ref)
-            assert cos > 0.995 and err < 0.12, (n + k, cos, err)
+            assert cos > 0.99 and err < 0.15, (n + k, cos, err)
 
 
 def test_training_reduces_loss_and_is_deterministic(T):
@@ -116,6 +129,7 @@ def test_training_reduces_loss_and_is_deterministic(T):
     runs = []
     for _ in range(2):
         net = ib.Net(seed=4)
+        net.scale = fitted_scale(rhs, p)
         losses = [net.train_step(d(rhs), d(rho), d(p), lr=2e-3) for _ in range(60)]
         runs.append((losses, net.get_params()))
     losses = runs[0][0]
