@@ -49,30 +49,47 @@ constexpr size_t conv_smem()
     return ((size_t)(MASK ? 4 : 2) * (CH + 2) * (CW + 2) * (CIN + 8) + (size_t)COUT * (9 * CIN + 8)) * 2;
 }
 
-// 4-byte asynchronous global -> shared copy; src-size 0 writes zeros.
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc, bool valid)
+// 16-byte asynchronous copy (both addresses 16-byte aligned); src-size 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc, bool valid)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    const int sz = valid ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(sz));
+    const int sz = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(sz));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Address of channels [8q, 8q + 8) of the convolution input at pixel
+// (bz, gy, gx) (inside the image).  With CUP > 0 the input is the channel
+// concatenation up2(xu) ++ x: channels below CUP come from the half-resolution
+// tensor xu (nearest upsampling, CUP channels), the rest from x (CIN - CUP
+// channels); the concatenated tensor is never stored.
+template <int CIN, int CUP>
+__device__ __forceinline__ const bf16 *in_chunk(const bf16 *x, const bf16 *xu, int bz, int H, int W,
+                                                int gy, int gx, int q)
+{
+    if (CUP > 0 && q < CUP / 8)
+        return xu + (((long)bz * (H / 2) + gy / 2) * (W / 2) + gx / 2) * CUP + 8 * q;
+    return x + (((long)bz * H + gy) * W + gx) * (CIN - CUP) + 8 * q - CUP;
+}
 
 // y = act(conv3x3(x * [xmask > 0]) + bias), NHWC, zero padding.
 // w: [COUT][9][CIN] (tap = 3 dy + dx multiplies x[i + dy - 1, j + dx - 1]).
 // Persistent: each CTA stages all weights once, then walks output tiles of
 // 8 x 16 pixels; the next tile (and its mask) is copied into the other
 // shared buffer with cp.async while the current one is on the tensor cores.
-template <int CIN, int COUT, bool MASK>
+// CUP > 0: the input is up2(xu) ++ x (see in_chunk).
+template <int CIN, int COUT, int CUP, bool MASK>
 __global__ void __launch_bounds__(128)
-k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xmask,
+k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xu,
+           const bf16 *__restrict__ xmask,
            const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
            bf16 *__restrict__ y, float *__restrict__ y32)
 {
     constexpr int XS = CIN + 8, WS = 9 * CIN + 8, NT = COUT / 8;
     constexpr int TP = (CH + 2) * (CW + 2);       // pixels of a haloed tile
+    static_assert(CIN % 16 == 0 && CUP % 8 == 0 && (CUP == 0 || !MASK), "channel layout");
     extern __shared__ __align__(16) unsigned char conv_sm[];
     bf16 *ws = (bf16 *)conv_sm;
     bf16 *xs0 = ws + COUT * WS;                    // 2 input buffers, then 2 mask buffers
@@ -86,14 +103,15 @@ k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restri
         const int ty0 = (rem / tw) * CH, tx0 = (rem - (rem / tw) * tw) * CW;
         bf16 *xs = xs0 + buf * TP * XS;
         bf16 *ms = xs0 + (2 + buf) * TP * XS;
-        for (int k = threadIdx.x; k < TP * (CIN / 2); k += 128) {
-            const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
+        for (int k = threadIdx.x; k < TP * (CIN / 8); k += 128) {
+            const int pix = k / (CIN / 8), q = k - pix * (CIN / 8);
             const int r = pix / (CW + 2), c = pix - r * (CW + 2);
             const int gy = ty0 + r - 1, gx = tx0 + c - 1;
             const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            const long off = in ? (((long)bz * H + gy) * W + gx) * CIN + 2 * cp : 0;
-            cp_async4(xs + pix * XS + 2 * cp, x + off, in);
-            if (MASK) cp_async4(ms + pix * XS + 2 * cp, xmask + off, in);
+            cp_async16(xs + pix * XS + 8 * q, in ? in_chunk<CIN, CUP>(x, xu, bz, H, W, gy, gx, q) : x, in);
+            if (MASK)
+                cp_async16(ms + pix * XS + 8 * q,
+                           xmask + (in ? (((long)bz * H + gy) * W + gx) * CIN + 8 * q : 0), in);
         }
         cp_async_commit();
     };
@@ -176,10 +194,10 @@ k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restri
 // Partial weight (and bias) gradients of one tap over a chunk of output
 // tiles: dW[co][tap][ci] += sum_p g[p][co] x[p + tap][ci], with
 // g = gy * [ymask > 0].  M = COUT, N = CIN, K = pixels (16 per step).
-template <int CIN, int COUT>
+template <int CIN, int COUT, int CUP>
 __global__ void __launch_bounds__(128)
 k_conv_dw(int B, int H, int W, int tiles_per_chunk, const bf16 *__restrict__ x,
-          const bf16 *__restrict__ gy, const bf16 *__restrict__ ymask,
+          const bf16 *__restrict__ xu, const bf16 *__restrict__ gy, const bf16 *__restrict__ ymask,
           float *__restrict__ part_w, float *__restrict__ part_b)
 {
     constexpr int XS = CIN + 8, GS = COUT + 8, MT = COUT / 16, NT = CIN / 8;
@@ -201,14 +219,14 @@ k_conv_dw(int B, int H, int W, int tiles_per_chunk, const bf16 *__restrict__ x,
         const int bz = tl / (tw * th), rem = tl - bz * tw * th;
         const int ty0 = (rem / tw) * CH, tx0 = (rem - (rem / tw) * tw) * CW;
         __syncthreads();
-        for (int k = threadIdx.x; k < (CH + 2) * (CW + 2) * (CIN / 2); k += 128) {
-            const int pix = k / (CIN / 2), cp = k - pix * (CIN / 2);
+        for (int k = threadIdx.x; k < (CH + 2) * (CW + 2) * (CIN / 8); k += 128) {
+            const int pix = k / (CIN / 8), q = k - pix * (CIN / 8);
             const int r = pix / (CW + 2), c = pix - r * (CW + 2);
             const int yy = ty0 + r - 1, xx = tx0 + c - 1;
-            uint32_t v = 0;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                v = *(const uint32_t *)(x + (((long)bz * H + yy) * W + xx) * CIN + 2 * cp);
-            *(uint32_t *)(xs + pix * XS + 2 * cp) = v;
+                v = *(const uint4 *)in_chunk<CIN, CUP>(x, xu, bz, H, W, yy, xx, q);
+            *(uint4 *)(xs + pix * XS + 8 * q) = v;
         }
         for (int k = threadIdx.x; k < CH * CW * (COUT / 2); k += 128) {
             const int pix = k / (COUT / 2), cp = k - pix * (COUT / 2);
@@ -296,22 +314,6 @@ __global__ void k_pool2(long nout, int H2, int W2, int C, const bf16 *__restrict
     y[k] = __float2bfloat16_rn(0.25f * s);
 }
 
-// out = [up2(t) | s] along channels (t: C1 at half resolution, s: C2)
-__global__ void k_up_cat(long nout, int H, int W, int C1, int C2, const bf16 *__restrict__ t,
-                         const bf16 *__restrict__ s, bf16 *__restrict__ out)
-{
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nout) return;
-    const int C = C1 + C2, c = (int)(k % C);
-    long p = k / C;
-    const int j = (int)(p % W);
-    p /= W;
-    const int i = (int)(p % H);
-    const long b = p / H;
-    out[k] = c < C1 ? t[((b * (H / 2) + i / 2) * (W / 2) + j / 2) * C1 + c]
-                    : s[((b * H + i) * W + j) * C2 + (c - C1)];
-}
-
 // gt = sum over 2x2 of g[..., :C1];  gs = g[..., C1:] (+ gs_add)
 __global__ void k_up_cat_bwd(long nhalf, int H2, int W2, int C1, int C2, const bf16 *__restrict__ g,
                              bf16 *__restrict__ gt)
@@ -356,7 +358,7 @@ __global__ void k_skip_grad(long n, int H, int W, int C1, int C2, const bf16 *__
 // 1/min(rho) exactly, IEEE division being monotone).
 // stats[kStat * smp + ...]: 0 mean b, 1 s = rms(b - mean) (1 if zero),
 // 2 1/s, 3 min rho, 4 1/(s pscale), 5 mean of the network output.
-constexpr int kRedBlocks = 64, kStat = 8;
+constexpr int kRedBlocks = 256, kStat = 8;
 
 __device__ __forceinline__ void block_fold3(double (*sh)[256], double &a, double &b, double &c, bool cmin)
 {
@@ -577,8 +579,8 @@ struct Cnn {
     int capB = 0, capN = 0;
     void *amem = nullptr;
     bf16 *x = nullptr, *a1 = nullptr, *s1 = nullptr, *p1 = nullptr, *a2 = nullptr, *s2 = nullptr,
-         *p2 = nullptr, *a3 = nullptr, *t3 = nullptr, *cat4 = nullptr, *t4 = nullptr,
-         *cat5 = nullptr, *a5 = nullptr, *y = nullptr, *gbig = nullptr, *gbig2 = nullptr,
+         *p2 = nullptr, *a3 = nullptr, *t3 = nullptr, *t4 = nullptr,
+         *a5 = nullptr, *y = nullptr, *gbig = nullptr, *gbig2 = nullptr,
          *gmid = nullptr, *gmid2 = nullptr, *gsmall = nullptr, *gsmall2 = nullptr, *gcat = nullptr,
          *gup = nullptr;
     float *y32 = nullptr, *t = nullptr, *lsum = nullptr, *gpad = nullptr, *part = nullptr;
@@ -590,14 +592,14 @@ namespace {
 
 int g_sms = 0;
 
-template <int CIN, int COUT, bool MASK>
-void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
+template <int CIN, int COUT, int CUP, bool MASK>
+void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 *xmask, const bf16 *w,
                  const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
 {
     constexpr size_t sm = conv_smem<CIN, COUT, MASK>();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, CUP, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
     if (!g_sms) {
@@ -610,20 +612,28 @@ void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf
     const int per_sm = sm <= 56 * 1024 ? 4 : (sm <= 75 * 1024 ? 3 : 2);
     const int grid = std::min(ntiles, g_sms * per_sm);
     note_launch();
-    k_conv_fwd<CIN, COUT, MASK><<<grid, 128, sm, s>>>(B, H, W, x, xmask, w, bias, relu, y, y32);
+    k_conv_fwd<CIN, COUT, CUP, MASK><<<grid, 128, sm, s>>>(B, H, W, x, xu, xmask, w, bias, relu, y, y32);
 }
 
 template <int CIN, int COUT>
 void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
               const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
 {
-    if (xmask) conv_launch<CIN, COUT, true>(B, H, W, x, xmask, w, bias, relu, y, y32, s);
-    else conv_launch<CIN, COUT, false>(B, H, W, x, xmask, w, bias, relu, y, y32, s);
+    if (xmask) conv_launch<CIN, COUT, 0, true>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s);
+    else conv_launch<CIN, COUT, 0, false>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s);
 }
 
-template <int CIN, int COUT>
+// Convolution of the concatenation up2(xu) ++ x (CUP channels from xu).
+template <int CIN, int COUT, int CUP>
+void conv_fwd_cat(int B, int H, int W, const bf16 *xu, const bf16 *x, const bf16 *w,
+                  const float *bias, int relu, bf16 *y, cudaStream_t s)
+{
+    conv_launch<CIN, COUT, CUP, false>(B, H, W, x, xu, nullptr, w, bias, relu, y, nullptr, s);
+}
+
+template <int CIN, int COUT, int CUP = 0>
 void conv_dw(Cnn &n, int B, int H, int W, const bf16 *x, const bf16 *gy, const bf16 *ymask,
-             float *gw_pad, float *gb, cudaStream_t s)
+             float *gw_pad, float *gb, cudaStream_t s, const bf16 *xu = nullptr)
 {
     const int ntiles = B * (int)cdiv(W, CW) * (int)cdiv(H, CH);
     const int nchunks = std::min(ntiles, 64);
@@ -631,7 +641,7 @@ void conv_dw(Cnn &n, int B, int H, int W, const bf16 *x, const bf16 *gy, const b
     float *pw = n.part, *pb = n.part + (size_t)nchunks * COUT * 9 * CIN;
     dim3 g(9, nchunks);
     note_launch();
-    k_conv_dw<CIN, COUT><<<g, 128, 0, s>>>(B, H, W, tpc, x, gy, ymask, pw, pb);
+    k_conv_dw<CIN, COUT, CUP><<<g, 128, 0, s>>>(B, H, W, tpc, x, xu, gy, ymask, pw, pb);
     const long nw = (long)COUT * 9 * CIN;
     note_launch();
     k_reduce_parts<<<cdiv(nw, 256), 256, 0, s>>>(nchunks, nw, pw, gw_pad);
@@ -733,8 +743,8 @@ cudaError_t cnn_workspace(Cnn &n, int B, int N)
                    al(P * c1 * 2) * 2 +                    // a1, s1
                    al(P2 * c1 * 2) + al(P2 * c2 * 2) * 2 + // p1, a2, s2
                    al(P4 * c2 * 2) * 3 +                   // p2, a3, t3
-                   al(P2 * 2 * c2 * 2) + al(P2 * c2 * 2) + // cat4, t4
-                   al(P * (c1 + c2) * 2) + al(P * c1 * 2) + al(P * 16 * 2) +  // cat5, a5, y
+                   al(P2 * c2 * 2) +                       // t4
+                   al(P * c1 * 2) + al(P * 16 * 2) +       // a5, y
                    al(P * 64 * 2) * 2 + al(P2 * 64 * 2) * 2 + al(P4 * 64 * 2) * 2 +  // grads
                    al(P * 64 * 2) + al(P2 * 64 * 2) +      // gcat, gup
                    al(P * 4) + al(P * 4) + al(B * 4) + al(n.npad * 4) + al(B * kStat * 8) +
@@ -749,8 +759,8 @@ cudaError_t cnn_workspace(Cnn &n, int B, int N)
     n.a1 = (bf16 *)take(P * c1 * 2); n.s1 = (bf16 *)take(P * c1 * 2);
     n.p1 = (bf16 *)take(P2 * c1 * 2); n.a2 = (bf16 *)take(P2 * c2 * 2); n.s2 = (bf16 *)take(P2 * c2 * 2);
     n.p2 = (bf16 *)take(P4 * c2 * 2); n.a3 = (bf16 *)take(P4 * c2 * 2); n.t3 = (bf16 *)take(P4 * c2 * 2);
-    n.cat4 = (bf16 *)take(P2 * 2 * c2 * 2); n.t4 = (bf16 *)take(P2 * c2 * 2);
-    n.cat5 = (bf16 *)take(P * (c1 + c2) * 2); n.a5 = (bf16 *)take(P * c1 * 2);
+    n.t4 = (bf16 *)take(P2 * c2 * 2);
+    n.a5 = (bf16 *)take(P * c1 * 2);
     n.y = (bf16 *)take(P * 16 * 2);
     n.gbig = (bf16 *)take(P * 64 * 2); n.gbig2 = (bf16 *)take(P * 64 * 2);
     n.gmid = (bf16 *)take(P2 * 64 * 2); n.gmid2 = (bf16 *)take(P2 * 64 * 2);
@@ -792,12 +802,8 @@ void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double
     k_pool2<<<cdiv((long)B * H4 * H4 * 32, 256), 256, 0, s>>>((long)B * H4 * H4 * 32, H4, H4, 32, n.s2, n.p2);
     conv_fwd<32, 32>(B, H4, H4, n.p2, nullptr, L[4].wf, bias(4), 1, n.a3, nullptr, s);
     conv_fwd<32, 32>(B, H4, H4, n.a3, nullptr, L[5].wf, bias(5), 1, n.t3, nullptr, s);
-    note_launch();
-    k_up_cat<<<cdiv((long)B * H2 * H2 * 64, 256), 256, 0, s>>>((long)B * H2 * H2 * 64, H2, H2, 32, 32, n.t3, n.s2, n.cat4);
-    conv_fwd<64, 32>(B, H2, H2, n.cat4, nullptr, L[6].wf, bias(6), 1, n.t4, nullptr, s);
-    note_launch();
-    k_up_cat<<<cdiv(P * 48, 256), 256, 0, s>>>(P * 48, N, N, 32, 16, n.t4, n.s1, n.cat5);
-    conv_fwd<48, 16>(B, N, N, n.cat5, nullptr, L[7].wf, bias(7), 1, n.a5, nullptr, s);
+    conv_fwd_cat<64, 32, 32>(B, H2, H2, n.t3, n.s2, L[6].wf, bias(6), 1, n.t4, s);  // up2(t3) ++ s2
+    conv_fwd_cat<48, 16, 32>(B, N, N, n.t4, n.s1, L[7].wf, bias(7), 1, n.a5, s);     // up2(t4) ++ s1
     conv_fwd<16, 16>(B, N, N, n.a5, nullptr, L[8].wf, bias(8), 0, n.y, n.y32, s);
 }
 
@@ -820,14 +826,14 @@ void cnn_backward(Cnn &n, int B, int N, cudaStream_t s)
     // c6 (linear): input a5, grad gbig (16 ch, channel 0)
     conv_dw<16, 16>(n, B, N, N, n.a5, n.gbig, nullptr, dwb(8).first, dwb(8).second, s);
     conv_fwd<16, 16>(B, N, N, n.gbig, nullptr, L[8].wb, nullptr, 0, n.gbig2, nullptr, s);  // grad a5
-    // c5: out a5 (mask), in cat5
-    conv_dw<48, 16>(n, B, N, N, n.cat5, n.gbig2, n.a5, dwb(7).first, dwb(7).second, s);
-    conv_fwd<16, 48>(B, N, N, n.gbig2, n.a5, L[7].wb, nullptr, 0, n.gcat, nullptr, s);     // grad cat5
+    // c5: out a5 (mask), in up2(t4) ++ s1
+    conv_dw<48, 16, 32>(n, B, N, N, n.s1, n.gbig2, n.a5, dwb(7).first, dwb(7).second, s, n.t4);
+    conv_fwd<16, 48>(B, N, N, n.gbig2, n.a5, L[7].wb, nullptr, 0, n.gcat, nullptr, s);     // grad of up2(t4) ++ s1
     note_launch();
     k_up_cat_bwd<<<cdiv((long)B * H2 * H2 * 32, 256), 256, 0, s>>>((long)B * H2 * H2 * 32, H2, H2, 32, 16, n.gcat, n.gmid);  // grad t4
-    // c4: out t4 (mask), in cat4
-    conv_dw<64, 32>(n, B, H2, H2, n.cat4, n.gmid, n.t4, dwb(6).first, dwb(6).second, s);
-    conv_fwd<32, 64>(B, H2, H2, n.gmid, n.t4, L[6].wb, nullptr, 0, n.gup, nullptr, s);     // grad cat4
+    // c4: out t4 (mask), in up2(t3) ++ s2
+    conv_dw<64, 32, 32>(n, B, H2, H2, n.s2, n.gmid, n.t4, dwb(6).first, dwb(6).second, s, n.t3);
+    conv_fwd<32, 64>(B, H2, H2, n.gmid, n.t4, L[6].wb, nullptr, 0, n.gup, nullptr, s);     // grad of up2(t3) ++ s2
     note_launch();
     k_up_cat_bwd<<<cdiv((long)B * H4 * H4 * 32, 256), 256, 0, s>>>((long)B * H4 * H4 * 32, H4, H4, 32, 32, n.gup, n.gsmall);  // grad t3
     // c3b: out t3, in a3
@@ -836,7 +842,7 @@ void cnn_backward(Cnn &n, int B, int N, cudaStream_t s)
     // c3a: out a3, in p2
     conv_dw<32, 32>(n, B, H4, H4, n.p2, n.gsmall2, n.a3, dwb(4).first, dwb(4).second, s);
     conv_fwd<32, 32>(B, H4, H4, n.gsmall2, n.a3, L[4].wb, nullptr, 0, n.gsmall, nullptr, s);  // grad p2
-    // grad s2 = cat4 split + pool2 backward
+    // grad s2 = skip part of the c4 input grad + pool2 backward
     note_launch();
     k_skip_grad<<<cdiv((long)B * H2 * H2 * 32, 256), 256, 0, s>>>((long)B * H2 * H2 * 32, H2, H2, 32, 32, n.gup, n.gsmall, n.gmid2);
     // c2b: out s2, in a2
@@ -845,7 +851,7 @@ void cnn_backward(Cnn &n, int B, int N, cudaStream_t s)
     // c2a: out a2, in p1
     conv_dw<16, 32>(n, B, H2, H2, n.p1, n.gmid, n.a2, dwb(2).first, dwb(2).second, s);
     conv_fwd<32, 16>(B, H2, H2, n.gmid, n.a2, L[2].wb, nullptr, 0, n.gmid2, nullptr, s);   // grad p1
-    // grad s1 = cat5 split + pool2 backward
+    // grad s1 = skip part of the c5 input grad + pool2 backward
     note_launch();
     k_skip_grad<<<cdiv(P * 16, 256), 256, 0, s>>>(P * 16, N, N, 32, 16, n.gcat, n.gmid2, n.gbig);
     // c1b: out s1, in a1
