@@ -146,7 +146,12 @@ struct Markers {
     double *sv = nullptr;                  // per segment: 12 strip corner points (24 doubles)
     double *sl = nullptr;                  // per segment: 8 half-planes (nx, ny, c) FP64
     float4 *slf = nullptr;                 // the same in FP32 (nx, ny, c, |n|)
-    uint8_t *scvx = nullptr;               // per segment: 1 if all five strips are convex
+    uint8_t *scvx = nullptr;               // per segment: 1 = half-plane path (strips convex, lines well conditioned)
+    uint32_t pair_cap = 0;                 // capacity of the band (cell, segment) pair list
+    uint32_t *npairs = nullptr;            // pairs claimed by the last band pass
+    uint32_t *pseg = nullptr, *pcell = nullptr;  // pair list: segment, cell index
+    double *pacc = nullptr, *pcov = nullptr;     // per pair: sum A_k H_k, sum A_k
+    uint2 *crange = nullptr;               // per cell of an active block: (first pair, count)
     float4 *sb5 = nullptr;                 // per segment: FP32 outward box of each of 5 strips
     int32_t *drop_start = nullptr, *drop_of = nullptr, *next = nullptr;
     uint32_t *key = nullptr, *tmp_ids = nullptr, *ids = nullptr,
@@ -161,8 +166,8 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny,
                           double h, double x0, double y0,
                           const int32_t *drop_start_host);
 void markers_free(Markers &mk);
-// flags[0]: bad marker (outside / too near a wall); flags[1]: candidate or
-// crossing list overflow; flags[2]: B-spline system not positive definite.
+// flags[0]: bad marker (outside / too near a wall); flags[1]: candidate,
+// crossing or band pair list overflow; flags[2]: B-spline system not positive definite.
 void launch_validate(Markers &mk, cudaStream_t s);
 void launch_geometry(Markers &mk, double sigma, cudaStream_t s);
 void launch_sort(Markers &mk, cudaStream_t s);

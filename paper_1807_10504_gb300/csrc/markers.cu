@@ -97,15 +97,21 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
     fmag[m] = sigma * k;
 }
 
-// Slab box of segment (m, next m): the four corners at offsets -2.5 and +2.5
-// cells along both marker normals, in grid units, rounded outward to FP32 so
-// that an FP32 test against a cell never rejects a strip that touches it.
-// Half-plane {x : n.x - c >= 0} on the left of the directed line P -> Q.
+// Half-plane {x : n.x - c >= 0} on the left of the directed line P -> Q, with
+// n the unit left normal (a zero vector, which constrains nothing, if P = Q).
 __device__ __forceinline__ void left_of(double px, double py, double qx, double qy, double *l)
 {
-    const double nx_ = -(qy - py), ny_ = qx - px;
+    const double dx = qx - px, dy = qy - py, len = sqrt(dx * dx + dy * dy);
+    const double il = len > 0.0 ? 1.0 / len : 0.0;
+    const double nx_ = -dy * il, ny_ = dx * il;
     l[0] = nx_; l[1] = ny_; l[2] = nx_ * px + ny_ * py;
 }
+
+// Segment geometry of (m, next m): the strip corners at offsets -2.5 .. 2.5
+// cells along both marker normals (grid units), the strip and slab boxes
+// rounded outward to FP32 so that an FP32 test against a cell never rejects
+// a strip that touches it, the eight bounding half-planes and whether all
+// five strips are convex.
 
 __global__ void k_segments(int M, const int32_t *__restrict__ next, const double *__restrict__ gx,
                            const double *__restrict__ gy, const double *__restrict__ nxm,
@@ -157,6 +163,7 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     // The strips are the intersections of those half-planes only when every
     // strip quadrilateral (A_k, B_k, B_k+1, A_k+1) is strictly convex; a
     // radius of curvature below about 2.5 cells folds the inner strips.
+    // Segments that fail either test use quadrilateral clipping.
     bool cvx = true;
     for (int k = 0; k < 5; k++) {
         const double qx[4] = {ax[k], bx[k], bx[k + 1], ax[k + 1]}, qy[4] = {ay[k], by[k], by[k + 1], ay[k + 1]};
@@ -165,6 +172,15 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
             const double cr = (qx[c1] - qx[c]) * (qy[c2] - qy[c1]) - (qy[c1] - qy[c]) * (qx[c2] - qx[c1]);
             cvx = cvx && cr > 1e-6;
         }
+    }
+    // The half-plane path also wants every line at least 0.01 rad away from
+    // the grid axes (or exactly on one): a line nearly parallel to a cell edge
+    // meets it at an ill-conditioned point, which the area formula would use
+    // twice (once per boundary piece); quadrilateral clipping has no such
+    // sensitivity and takes those segments.
+    for (int q = 0; q < 8; q++) {
+        const double aa = fabs(L[q][0]), bb = fabs(L[q][1]);
+        cvx = cvx && (aa == 0.0 || aa >= 1e-2) && (bb == 0.0 || bb >= 1e-2);
     }
     scvx[m] = cvx ? 1 : 0;
 }
@@ -564,7 +580,6 @@ __device__ __forceinline__ double strip_value(int k)
 
 constexpr int kBT = kBlk * kBlk;  // one thread per cell of the block
 
-constexpr int kMaxPairs = 1024;  // (cell, segment) pairs with possible overlap per block
 
 // Position of the unit cell [i, i+1] x [j, j+1] against a half-plane
 // n.x - c >= 0 evaluated in FP32 with a margin far above the FP32 error:
@@ -578,60 +593,29 @@ __device__ __forceinline__ int cell_side(float4 l, float fi, float fj)
     return hi < -m ? -1 : (lo > m ? 1 : 0);
 }
 
-// Clip the convex polygon (x, y)[n] (cell-local coordinates) by the
-// half-plane a x + b y - c >= 0; returns the new vertex count.
-__device__ __forceinline__ int clip_half(double *x, double *y, int n, double a, double b, double c)
-{
-    double ox[10], oy[10];
-    int m = 0;
-    for (int k = 0; k < n; k++) {
-        const int k1 = (k + 1 == n) ? 0 : k + 1;
-        const double fs = a * x[k] + b * y[k] - c, fe = a * x[k1] + b * y[k1] - c;
-        const bool si = fs >= 0.0, ei = fe >= 0.0;
-        if (si && ei) { ox[m] = x[k1]; oy[m] = y[k1]; m++; }
-        else if (si != ei) {
-            const double t = fs / (fs - fe);
-            ox[m] = x[k] + t * (x[k1] - x[k]); oy[m] = y[k] + t * (y[k1] - y[k]); m++;
-            if (ei) { ox[m] = x[k1]; oy[m] = y[k1]; m++; }
-        }
-    }
-    for (int k = 0; k < m; k++) { x[k] = ox[k]; y[k] = oy[k]; }
-    return m;
-}
-
-__device__ __forceinline__ double poly_area(const double *x, const double *y, int n)
-{
-    double a = 0.0;
-    for (int k = 0; k < n; k++) {
-        const int k1 = (k + 1 == n) ? 0 : k + 1;
-        a += x[k] * y[k1] - x[k1] * y[k];
-    }
-    return 0.5 * a;
-}
-
-// Three phases in one CTA per active 8x8 block: (1) every cell counts the
-// candidate segments whose slab (the four outer half-planes) may meet it,
-// tested in FP32, and the counts are scanned; (2) the (cell, segment) pairs
-// are written in ascending segment order and processed densely, one pair per
-// thread: the cell square is clipped in FP64 by the half-planes of the slab
-// and of each strip that cut it (a half-plane containing the whole cell is
-// skipped, one excluding it ends the strip), so that the area of cell and
-// strip needs one or two half-plane clips; (3) every cell sums its pairs in
-// order.  Equal, up to rounding, to clipping each strip quadrilateral against
-// the cell, which is what a segment with a folded (non-convex) strip does.
+// The band Heaviside runs in three launches so that the FP64 clipping, whose
+// cost varies from cell to cell, is spread evenly over the GPU:
+//  k_band_pairs (one CTA per active 8x8 block): every cell counts the
+//    candidate segments whose slab (the four outer half-planes) may meet it,
+//    tested in FP32; the block takes a range of the global pair list and
+//    writes its (cell, segment) pairs, per cell in ascending segment order;
+//  k_band_area (flat over the pair list): the areas of cell and strips;
+//  k_band_sum (one CTA per active block): every cell sums its pairs in order,
+//    H = sum A_k H_k + max(0, 1 - sum A_k) chi.
+// Pair ranges are claimed with an atomic counter, so their place in the list
+// varies from run to run, but each cell's pairs and their order do not: H is
+// deterministic.
 __global__ void __launch_bounds__(kBT)
-k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
-                 const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
-                 const double *__restrict__ sl, const float4 *__restrict__ slf,
-                 const uint8_t *__restrict__ scvx, const double *__restrict__ sv,
-                 const float4 *__restrict__ sb5, const float4 *__restrict__ sbox,
-                 double *__restrict__ H, uint32_t *__restrict__ flags)
+k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
+             const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
+             const float4 *__restrict__ slf, const uint8_t *__restrict__ scvx,
+             const float4 *__restrict__ sbox, uint32_t cap, uint32_t *__restrict__ npairs,
+             uint32_t *__restrict__ pseg, uint32_t *__restrict__ pcell, uint2 *__restrict__ crange,
+             uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
-    __shared__ uint32_t pseg[kMaxPairs];
-    __shared__ uint8_t pcell[kMaxPairs];
-    __shared__ double pacc[kMaxPairs], pcov[kMaxPairs];
     __shared__ uint32_t cnt[kBT + 1];
+    __shared__ uint32_t base;
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
@@ -656,91 +640,206 @@ k_band_heaviside(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
         uint32_t acc = 0;
         for (int k = 0; k < kBT; k++) { uint32_t v = cnt[k]; cnt[k] = acc; acc += v; }
         cnt[kBT] = acc;
-    }
-    __syncthreads();
-    const uint32_t total = cnt[kBT];
-    if (total > kMaxPairs) {
-        if (t == 0) atomicOr(&flags[1], 1u);
-        return;
-    }
-    if (live) {
-        uint32_t o = cnt[t];
-        for (int q = 0; q < n; q++)
-            if (meets(cand[q])) { pseg[o] = cand[q]; pcell[o] = (uint8_t)t; o++; }
-    }
-    __syncthreads();
-    double Hk[5];
-    for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
-    for (uint32_t p = t; p < total; p += kBT) {
-        const uint32_t m = pseg[p];
-        const int ct = pcell[p];
-        const int ci = bi * kBlk + (ct % kBlk), cj = bj * kBlk + (ct / kBlk);
-        const float gi = (float)ci, gj = (float)cj;
-        const double di = (double)ci, dj = (double)cj;
-        if (!scvx[m]) {  // folded strips: clip each quadrilateral against the cell
-            const double *v = sv + (long)m * 24;
-            double acc = 0.0, cov = 0.0;
-            for (int k = 0; k < 5; k++) {
-                const float4 b = sb5[(long)m * 5 + k];
-                if (b.x > gi + 1.0f || b.y < gi || b.z > gj + 1.0f || b.w < gj) continue;
-                double qx[4], qy[4];
-                qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
-                qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
-                qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
-                qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
-                const double A = clip_area_unit(qx, qy);
-                acc += A * Hk[k];
-                cov += A;
-            }
-            pacc[p] = acc;
-            pcov[p] = cov;
-            continue;
+        const uint32_t b0 = atomicAdd(npairs, acc);
+        if (b0 > cap || acc > cap - b0) {
+            atomicOr(&flags[1], 1u);
+            base = 0xffffffffu;
+        } else {
+            base = b0;
         }
-        const float4 *Lf = slf + (long)m * 8;
-        const double *Ld = sl + (long)m * 24;
-        int side[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) side[q] = cell_side(Lf[q], gi, gj);
-        // the cell square clipped by the slab's normal edges that cut it
-        double px[10] = {0.0, 1.0, 1.0, 0.0}, py[10] = {0.0, 0.0, 1.0, 1.0};
-        int np = 4;
-        for (int q = 0; q < 2 && np > 0; q++)
-            if (side[q] == 0)
-                np = clip_half(px, py, np, Ld[3 * q], Ld[3 * q + 1],
-                               Ld[3 * q + 2] - Ld[3 * q] * di - Ld[3 * q + 1] * dj);
-        double acc = 0.0, cov = 0.0;
-        if (np > 0) {
-            const double a0 = poly_area(px, py, np);
-            for (int k = 0; k < 5; k++) {
-                const int lo = 2 + k, hi = 3 + k;  // inside offset k, outside offset k + 1
-                if (side[lo] < 0 || side[hi] > 0) continue;
-                double A;
-                if (side[lo] > 0 && side[hi] < 0) {
-                    A = a0;
-                } else {
-                    double qx[10], qy[10];
-                    for (int v = 0; v < np; v++) { qx[v] = px[v]; qy[v] = py[v]; }
-                    int nq = np;
-                    if (side[lo] == 0)
-                        nq = clip_half(qx, qy, nq, Ld[3 * lo], Ld[3 * lo + 1],
-                                       Ld[3 * lo + 2] - Ld[3 * lo] * di - Ld[3 * lo + 1] * dj);
-                    if (nq > 0 && side[hi] == 0)
-                        nq = clip_half(qx, qy, nq, -Ld[3 * hi], -Ld[3 * hi + 1],
-                                       -(Ld[3 * hi + 2] - Ld[3 * hi] * di - Ld[3 * hi + 1] * dj));
-                    A = nq > 0 ? poly_area(qx, qy, nq) : 0.0;
-                }
-                acc += A * Hk[k];
-                cov += A;
-            }
-        }
-        pacc[p] = acc;
-        pcov[p] = cov;
     }
     __syncthreads();
     if (!live) return;
+    const long cidx = (long)j * nx + i;
+    if (base == 0xffffffffu) {
+        crange[cidx] = make_uint2(0u, 0u);
+        return;
+    }
+    uint32_t o = base + cnt[t];
+    crange[cidx] = make_uint2(o, c);
+    for (int q = 0; q < n; q++)
+        if (meets(cand[q])) { pseg[o] = cand[q]; pcell[o] = (uint32_t)cidx; o++; }
+}
+
+// A bounding line of a strip in the cell's local frame (the cell is the unit
+// square [0,1]^2): f(x, y) = a x + b y - c >= 0 inside, (a, b) a unit vector,
+// with the reciprocals of a and b (0 where they vanish); on = false makes the
+// slot constrain nothing.
+struct CellLine {
+    double a, b, c, ra, rb;
+    bool on;
+};
+
+__device__ __forceinline__ double safe_rcp(double v) { return v != 0.0 ? 1.0 / v : 0.0; }
+
+__device__ __forceinline__ CellLine cell_line(const double *l, double di, double dj, bool on)
+{
+    CellLine L;
+    L.a = on ? l[0] : 0.0;
+    L.b = on ? l[1] : 0.0;
+    L.c = on ? l[2] - l[0] * di - l[1] * dj : -1.0;
+    L.ra = safe_rcp(L.a);
+    L.rb = safe_rcp(L.b);
+    L.on = on;
+    return L;
+}
+
+// Narrow [lo, hi] to the s with alpha + beta s >= 0 (rbeta = 1 / beta).
+__device__ __forceinline__ void narrow(double alpha, double beta, double rbeta, double &lo, double &hi)
+{
+    const double q = -alpha * rbeta;
+    if (beta > 0.0) lo = fmax(lo, q);
+    else if (beta < 0.0) hi = fmin(hi, q);
+    else if (alpha < 0.0) hi = -INFINITY;
+}
+
+// Area of the unit square cut by the half-planes L[0..n-1] (n = 2 or 3), by
+// Green's theorem: area = 1/2 of the boundary integral of x dy - y dx.  On the
+// square's bottom and left edges the integrand vanishes; the right edge
+// contributes the length of its part inside every half-plane, and so does the
+// top edge; a line, traversed with its inside on the left from P(s0) to
+// P(s1), P(s) = c (a, b) + s (b, -a), contributes (s1 - s0) cross(P(0), (b, -a))
+// = -(s1 - s0) c.  Each piece is an interval cut down by the other
+// constraints; r01, r02, r12 are the reciprocals of the pairwise
+// determinants a_i b_j - b_i a_j.  The result equals clipping the square by
+// the half-planes in turn and taking the shoelace area, up to rounding.
+template <int n>
+__device__ __forceinline__ double cut_area(const CellLine *L, double r01, double r02, double r12)
+{
+    double lo = 0.0, hi = 1.0, acc;
+#pragma unroll
+    for (int j = 0; j < n; j++) narrow(L[j].a - L[j].c, L[j].b, L[j].rb, lo, hi);  // x = 1
+    acc = fmax(hi - lo, 0.0);
+    lo = 0.0; hi = 1.0;
+#pragma unroll
+    for (int j = 0; j < n; j++) narrow(L[j].b - L[j].c, L[j].a, L[j].ra, lo, hi);  // y = 1
+    acc += fmax(hi - lo, 0.0);
+#pragma unroll
+    for (int j = 0; j < n; j++) {
+        const double a = L[j].a, b = L[j].b, c = L[j].c, px = c * a, py = c * b;
+        // a line lying on the top or right edge with the square on its inner
+        // side traces the same boundary as that edge: count it once
+        const bool on_edge = (a == 0.0 && b < 0.0 && b - c == 0.0) || (b == 0.0 && a < 0.0 && a - c == 0.0);
+        if (!L[j].on || on_edge) continue;
+        lo = -INFINITY; hi = INFINITY;
+        narrow(px, b, L[j].rb, lo, hi);             // x >= 0
+        narrow(1.0 - px, -b, -L[j].rb, lo, hi);     // x <= 1
+        narrow(py, -a, -L[j].ra, lo, hi);           // y >= 0
+        narrow(1.0 - py, a, L[j].ra, lo, hi);       // y <= 1
+#pragma unroll
+        for (int i = 0; i < n; i++) {
+            if (i == j || !L[i].on) continue;
+            const double beta = L[i].a * b - L[i].b * a;
+            // beta = D_ij; the reciprocals are of D_01, D_02, D_12 and D_ji = -D_ij
+            const double r = (i < j) ? ((i == 0) ? (j == 1 ? r01 : r02) : r12)
+                                     : -((j == 0) ? (i == 1 ? r01 : r02) : r12);
+            narrow(L[i].a * px + L[i].b * py - L[i].c, beta, r, lo, hi);
+        }
+        acc -= c * fmax(hi - lo, 0.0);
+    }
+    return 0.5 * acc;
+}
+
+// Area of cell (ci, cj) inside each of the five strips of segment m, weighted
+// sum and total.  Convex, well-conditioned strips: P is the cell square cut by the slab's normal
+// edges that cross it (area a0), S_o = area(P on the inner side of offset line
+// o) for o = 0..5 (a0 or 0 when the FP32 test finds the line clear of the
+// cell, else cut_area in FP64), and strip k has area S_k - S_k+1.  Other
+// segments (folded strips, lines within 0.01 rad of a grid axis): each
+// quadrilateral is clipped against the cell (Sutherland-Hodgman).
+__device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const double *__restrict__ sl,
+                                          const float4 *__restrict__ slf,
+                                          const uint8_t *__restrict__ scvx,
+                                          const double *__restrict__ sv,
+                                          const float4 *__restrict__ sb5, const double *Hk,
+                                          double &acc, double &cov)
+{
+    const float gi = (float)ci, gj = (float)cj;
+    const double di = (double)ci, dj = (double)cj;
+    acc = 0.0;
+    cov = 0.0;
+    if (!scvx[m]) {
+        const double *v = sv + (long)m * 24;
+        for (int k = 0; k < 5; k++) {
+            const float4 b = sb5[(long)m * 5 + k];
+            if (b.x > gi + 1.0f || b.y < gi || b.z > gj + 1.0f || b.w < gj) continue;
+            double qx[4], qy[4];
+            qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
+            qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
+            qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
+            qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
+            const double A = clip_area_unit(qx, qy);
+            acc += A * Hk[k];
+            cov += A;
+        }
+        return;
+    }
+    const float4 *Lf = slf + (long)m * 8;
+    const double *Ld = sl + (long)m * 24;
+    int side[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) side[q] = cell_side(Lf[q], gi, gj);
+    // slots 0, 1: the normal edges that cut the cell (others constrain nothing)
+    CellLine L[3];
+#pragma unroll
+    for (int q = 0; q < 2; q++) L[q] = cell_line(Ld + 3 * q, di, dj, side[q] == 0);
+    const double r01 = safe_rcp(L[0].a * L[1].b - L[0].b * L[1].a);
+    const double a0 = (side[0] == 0 || side[1] == 0) ? cut_area<2>(L, r01, 0.0, 0.0) : 1.0;
+    double S[6];
+#pragma unroll
+    for (int o = 0; o < 6; o++) {
+        const int q = 2 + o;
+        if (side[q] > 0) {
+            S[o] = a0;
+        } else if (side[q] < 0) {
+            S[o] = 0.0;
+        } else {
+            L[2] = cell_line(Ld + 3 * q, di, dj, true);
+            S[o] = cut_area<3>(L, r01, safe_rcp(L[0].a * L[2].b - L[0].b * L[2].a),
+                            safe_rcp(L[1].a * L[2].b - L[1].b * L[2].a));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const double A = S[k] - S[k + 1];
+        acc += A * Hk[k];
+        cov += A;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_band_area(int nx, const uint32_t *__restrict__ npairs, uint32_t cap,
+            const uint32_t *__restrict__ pseg, const uint32_t *__restrict__ pcell,
+            const double *__restrict__ sl, const float4 *__restrict__ slf,
+            const uint8_t *__restrict__ scvx, const double *__restrict__ sv,
+            const float4 *__restrict__ sb5, double *__restrict__ pacc, double *__restrict__ pcov)
+{
+    const uint32_t total = min(*npairs, cap);
+    double Hk[5];
+    for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+        const uint32_t cell = pcell[p];
+        const int cj = (int)(cell / (uint32_t)nx), ci = (int)(cell - (uint32_t)cj * (uint32_t)nx);
+        double acc, cov;
+        pair_area(pseg[p], ci, cj, sl, slf, scvx, sv, sb5, Hk, acc, cov);
+        pacc[p] = acc;
+        pcov[p] = cov;
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+k_band_sum(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
+           const uint2 *__restrict__ crange, const double *__restrict__ pacc,
+           const double *__restrict__ pcov, double *__restrict__ H)
+{
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (!bactive[bj * bnx + bi]) return;
+    const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
+    if (i >= nx || j >= ny) return;
+    const long cidx = (long)j * nx + i;
+    const uint2 r = crange[cidx];
     double acc = 0.0, cov = 0.0;
-    for (uint32_t p = cnt[t]; p < cnt[t + 1]; p++) { acc += pacc[p]; cov += pcov[p]; }
-    long cidx = (long)j * nx + i;
+    for (uint32_t p = r.x; p < r.x + r.y; p++) { acc += pacc[p]; cov += pcov[p]; }
     double unc = 1.0 - cov;
     if (unc < 0.0) unc = 0.0;
     H[cidx] = acc + unc * H[cidx];
@@ -760,11 +859,28 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
                uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
+    __shared__ float4 seg[kMaxCand];   // FP32 candidate segments: start, direction
+    __shared__ float seg_il[kMaxCand]; // 1 / |direction|^2
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int m = (int)cand[q], nm = next[m];
+        const float ax = gxf[m], ay = gyf[m], ex = gxf[nm] - ax, ey = gyf[nm] - ay;
+        seg[q] = make_float4(ax, ay, ex, ey);
+        seg_il[q] = 1.0f / (ex * ex + ey * ey);
+    }
+    __syncthreads();
     const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
     if (i >= nx || j >= ny) return;
+    // squared FP32 distance from (fqx, fqy) to candidate q
+    auto d2f = [&](int q, float fqx, float fqy) {
+        const float4 sg = seg[q];
+        float t = ((fqx - sg.x) * sg.z + (fqy - sg.y) * sg.w) * seg_il[q];
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        const float dx = sg.x + t * sg.z - fqx, dy = sg.y + t * sg.w - fqy;
+        return dx * dx + dy * dy;
+    };
     for (int dir = 0; dir < 2; dir++) {
         double dH;
         double qx, qy;
@@ -779,30 +895,18 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
         }
         double F = 0.0;
         if (dH != 0.0) {
-            // FP32 screen: squared distances carry an error far below 0.05
-            // (grid units, coordinates < 2^15), so the exact nearest segment is
-            // among those within best + 0.05 of the FP32 minimum.
+            // FP32 screen from the candidates staged in shared memory: squared
+            // distances carry an error far below 0.05 (grid units, coordinates
+            // < 2^15), so the exact nearest segment is among those within
+            // best + 0.05 of the FP32 minimum.
             const float fqx = (float)qx, fqy = (float)qy;
             float best32 = INFINITY;
-            for (int q = 0; q < n; q++) {
-                int m = (int)cand[q], nm = next[m];
-                float ax = gxf[m], ay = gyf[m], ex = gxf[nm] - ax, ey = gyf[nm] - ay;
-                float t = ((fqx - ax) * ex + (fqy - ay) * ey) / (ex * ex + ey * ey);
-                t = fminf(fmaxf(t, 0.0f), 1.0f);
-                float dx = ax + t * ex - fqx, dy = ay + t * ey - fqy;
-                best32 = fminf(best32, dx * dx + dy * dy);
-            }
+            for (int q = 0; q < n; q++) best32 = fminf(best32, d2f(q, fqx, fqy));
             const float lim = best32 + 0.05f;
             double best = INFINITY, fb = 0.0;
             for (int q = 0; q < n; q++) {
-                int m = (int)cand[q], nm = next[m];
-                {
-                    float ax = gxf[m], ay = gyf[m], ex = gxf[nm] - ax, ey = gyf[nm] - ay;
-                    float t = ((fqx - ax) * ex + (fqy - ay) * ey) / (ex * ex + ey * ey);
-                    t = fminf(fmaxf(t, 0.0f), 1.0f);
-                    float dx = ax + t * ex - fqx, dy = ay + t * ey - fqy;
-                    if (dx * dx + dy * dy > lim) continue;
-                }
+                if (d2f(q, fqx, fqy) > lim) continue;
+                const int m = (int)cand[q], nm = next[m];
                 double ax = gx[m], ay = gy[m];
                 double bx = gx[nm], by = gy[nm];
                 double ex = bx - ax, ey = by - ay;
@@ -1069,8 +1173,13 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
         mk.max_drop = std::max(mk.max_drop, drop_start_host[d + 1] - drop_start_host[d]);
     size_t ncell = (size_t)nx * ny, nb = (size_t)mk.bnx * mk.bny;
     size_t nparts = (ncell + kScanChunk - 1) / kScanChunk;
+    // (cell, segment) pairs of the band: about (5 + 1) x (segment length + 1)
+    // per segment; 64 per segment covers segments up to ~9 cells long.
+    const size_t pair_cap = (size_t)M * 64 + 4096;
+    mk.pair_cap = (uint32_t)pair_cap;
     size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
                    al((size_t)M * 24 * 8) * 2 + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) +
+                   al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
@@ -1092,6 +1201,10 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.slf = (float4 *)take((size_t)M * 8 * 16);
     mk.sb5 = (float4 *)take((size_t)M * 5 * 16);
     mk.scvx = (uint8_t *)take(M);
+    mk.npairs = (uint32_t *)take(64);
+    mk.pseg = (uint32_t *)take(pair_cap * 4); mk.pcell = (uint32_t *)take(pair_cap * 4);
+    mk.pacc = (double *)take(pair_cap * 8); mk.pcov = (double *)take(pair_cap * 8);
+    mk.crange = (uint2 *)take(ncell * 8);
     mk.ykey = (unsigned long long *)take(M * 8);
     mk.drop_start = (int32_t *)take((ndrops + 1) * 4);
     mk.drop_of = (int32_t *)take(M * 4);
@@ -1188,16 +1301,36 @@ void launch_spread_conv(const Markers &mk, int kernel, const double *fmag, doubl
                                              fmag, mk.nxm, mk.nym, mk.ds, Fx, Fy);
 }
 
+// Grid of the flat pair kernel: 8 CTAs of 256 threads per SM, grid-stride.
+int band_area_grid()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return 8 * sms;
+}
+
 void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
 {
     note_launch();
     k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.ykey,
                                        mk.next, mk.drop_start, mk.dyk, H, mk.flags);
     dim3 g(mk.bnx, mk.bny);
+    cudaMemsetAsync(mk.npairs, 0, sizeof(uint32_t), s);
     note_launch();
-    k_band_heaviside<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids,
-                                       mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5,
-                                       mk.sbox, H, mk.flags);
+    k_band_pairs<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids, mk.slf,
+                                   mk.scvx, mk.sbox, mk.pair_cap, mk.npairs, mk.pseg, mk.pcell,
+                                   mk.crange, mk.flags);
+    note_launch();
+    k_band_area<<<band_area_grid(), 256, 0, s>>>(mk.nx, mk.npairs, mk.pair_cap, mk.pseg, mk.pcell,
+                                                 mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5, mk.pacc,
+                                                 mk.pcov);
+    note_launch();
+    k_band_sum<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.crange, mk.pacc, mk.pcov, H);
 }
 
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H, double *Fx,

@@ -3,8 +3,10 @@
 // names multigrid and nothing more; this is the V(nu1, nu2) cycle with a
 // red-black Gauss-Seidel smoother, residual + four-child averaging
 // restriction, bilinear (9,3,3,1)/16 prolongation, coarse face coefficients
-// = mean of the two fine faces, and a dense LU solve of the coarsest level
-// with the constant null space removed by A + s 1 1^T (s = A_00).
+// = mean of the two fine faces, and an exact solve of the coarsest level
+// with the constant null space removed by A + s 1 1^T (s = A_00), applied as
+// a product with the inverse of that matrix (formed once per coefficient set
+// by Gauss-Jordan elimination in FP64).
 //
 // GB300 mapping:
 //  * one red+black sweep = one launch: a 64x16 tile of p (+2-cell halo) is
@@ -93,10 +95,23 @@ k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict
 
 // Two red-black sweeps in one launch (FP32 inner cycle): the tile of p with a
 // 4-cell halo and b, beta_x, beta_y, 1/diag with a 3-cell halo are staged in
-// shared memory with all loads issued up front; the sweeps then run from
+// shared memory by asynchronous copies, all issued before the first wait; the sweeps then run from
 // shared memory on shrinking rings (red on ring 3, black on ring 2, red on
 // ring 1, black on the tile) so the tile's result equals two global sweeps.
 constexpr int FW = 64, FH = 16, FT = 256;
+
+// Asynchronous global -> shared copies (both addresses aligned to the size);
+// src-size 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async16(void *d, const void *src, bool v)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)),
+                 "l"(src), "r"(v ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async4(void *d, const void *src, bool v)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)),
+                 "l"(src), "r"(v ? 4 : 0));
+}
 __global__ void __launch_bounds__(FT)
 k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float *__restrict__ by,
             const float *__restrict__ invd, const float *__restrict__ b, float *__restrict__ p)
@@ -114,25 +129,19 @@ k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float 
     const int gi0 = blockIdx.x * FW - 4, gj0 = blockIdx.y * FH - 4;
     const long nxf = nx + 1;
     const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
-    if (vec) {
+    if (vec) {  // 16-byte asynchronous copies, all in flight before the wait
         constexpr int V = PW / 4;  // float4 per row
         for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
             const int r = k / V, c4 = k - r * V, gj = gj0 + r;
             const long o = (long)gj * nx + gi0 + 4 * c4;
             if (r < PH) {
-                float4 vp = make_float4(0.f, 0.f, 0.f, 0.f), vb = vp, vd = vp;
-                if (gj >= 0 && gj < ny) {
-                    vp = *(const float4 *)(p + o);
-                    vb = *(const float4 *)(b + o);
-                    vd = *(const float4 *)(invd + o);
-                }
-                *(float4 *)&ps[r][4 * c4] = vp;
-                *(float4 *)&bs[r][4 * c4] = vb;
-                *(float4 *)&ds[r][4 * c4] = vd;
+                const bool in = gj >= 0 && gj < ny;
+                cp_async16(&ps[r][4 * c4], in ? p + o : p, in);
+                cp_async16(&bs[r][4 * c4], in ? b + o : b, in);
+                cp_async16(&ds[r][4 * c4], in ? invd + o : invd, in);
             }
-            float4 vy = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gj >= 0 && gj <= ny) vy = *(const float4 *)(by + o);
-            *(float4 *)&ys[r][4 * c4] = vy;
+            const bool iny = gj >= 0 && gj <= ny;
+            cp_async16(&ys[r][4 * c4], iny ? by + o : by, iny);
         }
     } else {
         for (int k = threadIdx.x; k < (PH + 1) * PW; k += FT) {
@@ -149,8 +158,10 @@ k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float 
     }
     for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
         const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
-        xs[r][c] = (gi >= 0 && gi <= nx && gj >= 0 && gj < ny) ? bx[(long)gj * nxf + gi] : 0.0f;
+        const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj < ny;
+        cp_async4(&xs[r][c], in ? bx + (long)gj * nxf + gi : bx, in);
     }
+    asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
     // ring q: local rows/cols [4-q, 4+F+q); colour: 0 red, 1 black
 #pragma unroll
