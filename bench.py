@@ -246,15 +246,13 @@ def run_ours(args):
     barrier()
     sweep_ms, sweep_n = ib.profile_end()
 
-    # pressure solve alone, cold start, on this state's system: FP64 vs mixed
+    # pressure solve alone, cold start, on this state's system: FP64 vs mixed,
+    # both through the solve graph
     b = ctx.get("b")
     solve = {}
     pk, pk_kind = peaks()
-    roof64 = None
     for prec, label in ((0, "fp64"), (1, "mixed")):
         times, cyc = [], None
-        if prec == 0:
-            ib.profile_begin(ib.PROF_SWEEP64)
         for rep in range(3 + 5):
             p = torch.zeros((n, n), dtype=torch.float64, device="cuda")
             flush.zero_()
@@ -265,16 +263,21 @@ def run_ours(args):
             torch.cuda.synchronize()
             if rep >= 3:
                 times.append(e0.elapsed_time(e1))
-        if prec == 0:
-            s64_ms, s64_n = ib.profile_end()
-            avg = s64_ms / max(s64_n, 1)
-            ach = 40.0 * n * n / (avg * 1e-3) / 1e9
-            roof64 = {"kernel": "k_rbgs_sweep<double> (fine level)", "bound": "hbm",
-                      "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                      "frac": ach / pk["hbm_gbs"], "traffic": None,
-                      "avg_launch_us": avg * 1e3, "launches": s64_n,
-                      "algorithmic_bytes_per_cell": 40}
         solve[label] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr}
+
+    # kernel durations on this step's data: back-to-back launches between two
+    # CUDA events on the context stream (ib_bench_kernel)
+    us32, cells = ctx.bench_kernel(0, 50)
+    us64, _ = ctx.bench_kernel(1, 50)
+    usb, pairs = ctx.bench_kernel(2, 10)
+    ach32 = 20.0 * cells / (us32 * 1e-6) / 1e9
+    ach64 = 40.0 * cells / (us64 * 1e-6) / 1e9
+    roof64 = {"kernel": "k_rbgs_sweep<double> (fine level, one red-black sweep)", "bound": "hbm",
+              "achieved": ach64, "peak": pk["hbm_gbs"], "unit": "GB/s",
+              "frac": ach64 / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
+              "avg_launch_us": us64, "algorithmic_bytes_per_cell": 40}
+    band = {"kernel": "k_band_area", "avg_launch_us": usb, "pairs": int(pairs),
+            "ns_per_pair": 1e3 * usb / max(pairs, 1)}
 
     # mixed precision from the learned warm start: a network trained here on
     # solver-generated 128^2 samples (its own kernels), inference inside the
@@ -287,6 +290,7 @@ def run_ours(args):
         losses = WS.train(net, data, steps=args.cnn_steps, batch=16, lr=2e-3)
         del data
         train_s = time.perf_counter() - t0
+        net.set_coarsen(args.cnn_coarsen)
         rho = ctx.get("rho")
         times, cyc = [], None
         for rep in range(3 + 5):
@@ -300,6 +304,7 @@ def run_ours(args):
             if rep >= 3:
                 times.append(e0.elapsed_time(e1))
         solve["mixed_cnn"] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr,
+                              "inference_grid": n >> args.cnn_coarsen,
                               "train": {"samples": args.cnn_samples, "steps": len(losses),
                                         "final_loss": losses[-1], "seconds": train_s}}
         del net
@@ -323,8 +328,6 @@ def run_ours(args):
     e2e_t = max_over_ranks(time.perf_counter() - t0)
 
     avg_sweep = sweep_ms / max(sweep_n, 1)
-    bpc = 20.0 if sweep_kind == ib.PROF_SWEEP32 else 40.0
-    ach = bpc * n * n / (avg_sweep * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -343,13 +346,21 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(2 * ctx.M * 8),
                 "d2h_bytes_per_step": int(n * n * 8 + 2 * ctx.M * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": ("k_rbgs_sweep<float> (fine level)" if sweep_kind == 1
-                                else "k_rbgs_sweep<double> (fine level)"),
-                     "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": ach / pk["hbm_gbs"], "traffic": None,
-                     "peak_source": pk_kind, "avg_launch_us": avg_sweep * 1e3,
-                     "launches": sweep_n, "algorithmic_bytes_per_cell": bpc},
+        "roofline": {"kernel": ("k_rbgs2_f32 (fine level, two fused FP32 red-black sweeps)"
+                                if args.precision == 1 else
+                                "k_rbgs_sweep<double> (fine level, one red-black sweep)"),
+                     "bound": "hbm", "achieved": ach32 if args.precision == 1 else ach64,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": (ach32 if args.precision == 1 else ach64) / pk["hbm_gbs"],
+                     "traffic": None, "peak_source": pk_kind,
+                     "avg_launch_us": us32 if args.precision == 1 else us64,
+                     "algorithmic_bytes_per_cell": 20.0 if args.precision == 1 else 40.0,
+                     "cells_per_launch": int(cells),
+                     "timing": "50 back-to-back launches on the step's fine-level data, "
+                               "CUDA events on the launching stream",
+                     "in_step_avg_launch_us": avg_sweep * 1e3, "in_step_launches": sweep_n},
         "roofline_fp64_sweep": roof64,
+        "band_strip_areas": band,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, t = cpu_baseline(name, 1)
@@ -376,6 +387,8 @@ def main():
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned warm start")
     ap.add_argument("--cnn-samples", type=int, default=800)
     ap.add_argument("--cnn-steps", type=int, default=800)
+    ap.add_argument("--cnn-coarsen", type=int, default=1,
+                    help="run the network on the grid coarsened by 2^k")
     ap.add_argument("--no-graphs", action="store_true",
                     help="solve with one launch per kernel (for kernel profilers)")
     ap.add_argument("--ncu", action="store_true",

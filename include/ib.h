@@ -189,9 +189,16 @@ ib_status cnn_grad(ib_cnn *net, int32_t B, int32_t N, double h, const double *rh
 ib_status cnn_train_step(ib_cnn *net, int32_t B, int32_t N, double h,
                          const double *rhs, const double *rho, const double *p,
                          float lr, float *loss, void *stream);
-/* p0 (device FP64, B x N x N) = network estimate of the pressure.          */
+/* p0 (device FP64, B x N x N) = network estimate of the pressure.  With
+ * cnn_set_coarsen(net, k), k > 0, rhs and rho are first averaged over
+ * 2^k x 2^k blocks, the network runs on that grid (cell size h 2^k) and its
+ * estimate is interpolated back to N x N (cell-centred bilinear, zero
+ * gradient at the walls, once per halving); N must then be a multiple of
+ * 4 * 2^k.  The same setting applies to ns_step(..., warm = 2).
+ * IB_EINVAL for bad sizes, IB_ENOMEM if the scratch cannot be allocated.  */
 ib_status cnn_infer(ib_cnn *net, int32_t B, int32_t N, double h, const double *rhs,
                     const double *rho, double *p0, void *stream);
+ib_status cnn_set_coarsen(ib_cnn *net, int32_t levels);   /* 0 .. 6 */
 ib_status cnn_set_scale(ib_cnn *net, double c);
 double cnn_get_scale(const ib_cnn *net);
 /* Attach (or detach with NULL) a network used by ns_step(..., warm = 2); the
@@ -213,6 +220,16 @@ unsigned long long ib_launch_count(void);
 ib_status ib_use_graphs(ib_ctx *ctx, int enable);
 ib_status ib_profile_begin(int kind);
 ib_status ib_profile_end(double *total_ms, int *launches);
+/* Kernel timing on the context's current data: `reps` back-to-back launches
+ * of one kernel between two CUDA events on the context stream (after one
+ * untimed launch); *us_per_launch = their mean duration, *units = the work
+ * units of one launch.  which = 0: fine-level FP32 smoother (two fused
+ * red-black sweeps; units = cells), 1: fine-level FP64 sweep (cells), 2: band
+ * strip areas of the last Heaviside pass (units = (cell, segment) pairs).
+ * The smoother launches overwrite the level-0 correction scratch, the
+ * strip-area launches recompute the same per-pair values: the context's
+ * state is unchanged.  Needs a prior solve (0, 1) / Heaviside pass (2).    */
+ib_status ib_bench_kernel(ib_ctx *ctx, int which, int reps, double *us_per_launch, double *units);
 
 /* Checkpoint: every field, the AB2 history, markers and the step counter,
  * written to / read from a binary file at `path` (host I/O, synchronises).

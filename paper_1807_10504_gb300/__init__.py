@@ -33,9 +33,9 @@ EXPORTS = [
     "ns_step", "ib_last_solve", "ib_save", "ib_load", "ib_op_coeffs", "ib_op_residual",
     "ib_op_rbgs", "ib_op_restrict_residual", "ib_op_prolong_add", "ib_op_coarsen_beta",
     "ib_op_rhs", "ib_op_correct", "ib_op_predictor", "ib_launch_count", "ib_profile_begin",
-    "ib_profile_end", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
+    "ib_profile_end", "ib_bench_kernel", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
-    "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale",
+    "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
 ]
 
 
@@ -99,7 +99,8 @@ def lib():
             "cnn_train_step": [_P, _i32, _i32, _d, _P, _P, _P, C.c_float, C.POINTER(C.c_float),
                                _P],
             "cnn_infer": [_P, _i32, _i32, _d, _P, _P, _P, _P],
-            "cnn_set_scale": [_P, _d],
+            "cnn_set_scale": [_P, _d], "cnn_set_coarsen": [_P, _i32],
+            "ib_bench_kernel": [_P, C.c_int, C.c_int, _P, _P],
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
@@ -314,6 +315,13 @@ class Context:
         lib().ib_last_solve(self._h, C.byref(cyc), C.byref(rr))
         return cyc.value, rr.value
 
+    def bench_kernel(self, which: int, reps: int = 50):
+        """(us per launch, work units per launch) of `reps` back-to-back
+        launches of one kernel on the current data (see ib_bench_kernel)."""
+        us, units = C.c_double(0.0), C.c_double(0.0)
+        _check(lib().ib_bench_kernel(self._h, which, reps, C.byref(us), C.byref(units)), self._h)
+        return us.value, units.value
+
     def use_graphs(self, enable: bool):
         _check(lib().ib_use_graphs(self._h, int(enable)), self._h)
 
@@ -383,6 +391,11 @@ class Net:
         _check(lib().cnn_train_step(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p), lr,
                                     C.byref(loss), _stream()), None, "cnn_train_step")
         return loss.value
+
+    def set_coarsen(self, levels: int):
+        """Run inference on the grid coarsened by 2^levels (inputs averaged,
+        estimate interpolated back); 0 = the solve grid itself."""
+        _check(lib().cnn_set_coarsen(self._h, int(levels)), None, "cnn_set_coarsen")
 
     def infer(self, rhs, rho, h=None):
         torch = _torch()

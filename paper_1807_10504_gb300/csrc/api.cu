@@ -32,6 +32,7 @@ struct ib_ctx {
 
 struct ib_cnn {
     ibk::Cnn *n = nullptr;
+    int coarsen = 0;   // inference grid = solve grid / 2^coarsen
     std::string err;
 };
 
@@ -360,8 +361,9 @@ ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, doubl
 ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
 {
     if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 2) return IB_EINVAL;
-    if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % 4 != 0))
-        return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid (side % 4 == 0)");
+    if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % (4 << c->cnn->coarsen) != 0))
+        return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid "
+                                  "(side a multiple of 4 * 2^coarsen)");
     const ib_config &g = c->cfg;
     Markers &mk = c->mk;
     for (int it = 0; it < nsteps; it++) {
@@ -382,10 +384,9 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (st != IB_OK) return st;
         if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
         if (warm == 2) {
-            cudaError_t ce = cnn_workspace(*c->cnn->n, 1, g.nx);
-            if (ce != cudaSuccess) return cuda_check(c, ce, "network workspace");
-            cnn_forward(*c->cnn->n, 1, g.nx, g.h, c->b, c->rho, nullptr, c->s);
-            cnn_output(*c->cnn->n, 1, g.nx, g.h, c->p, c->s);
+            cudaError_t ce = cnn_infer_levels(*c->cnn->n, 1, g.nx, g.h, c->b, c->rho, c->p,
+                                              c->cnn->coarsen, c->s);
+            if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
         }
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                     &c->last_cycles, &c->last_relres, c->s, c->err);
@@ -421,6 +422,43 @@ ib_status ib_profile_begin(int kind)
 ib_status ib_profile_end(double *total_ms, int *launches)
 {
     return prof_end(total_ms, launches) ? IB_OK : IB_ECUDA;
+}
+
+ib_status ib_bench_kernel(ib_ctx *c, int which, int reps, double *us_per_launch, double *units)
+{
+    if (!c || which < 0 || which > 2 || reps < 1 || !us_per_launch) return IB_EINVAL;
+    if (which < 2 && !c->mg_ready) return fail(c, IB_EINVAL, "no multigrid hierarchy yet");
+    double u = 0.0;
+    if (which < 2) {
+        u = (double)c->cfg.nx * c->cfg.ny;
+    } else {
+        uint32_t np = 0;
+        cudaError_t e = cudaMemcpyAsync(&np, c->mk.npairs, 4, cudaMemcpyDeviceToHost, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) return cuda_check(c, e, "pair count");
+        u = (double)std::min(np, c->mk.pair_cap);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto one = [&]() {
+        if (which == 0) mg_fine_smoother(c->mg, 1, c->s);
+        else if (which == 1) mg_fine_smoother(c->mg, 0, c->s);
+        else launch_band_area(c->mk, c->s);
+    };
+    one();  // warm-up
+    cudaEventRecord(e0, c->s);
+    for (int r = 0; r < reps; r++) one();
+    cudaEventRecord(e1, c->s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(c, e, "kernel timing");
+    *us_per_launch = 1e3 * ms / reps;
+    if (units) *units = u;
+    return IB_OK;
 }
 
 ib_status ib_last_solve(const ib_ctx *c, int *cycles, double *relres)
@@ -519,12 +557,18 @@ ib_status cnn_train_step(ib_cnn *h, int32_t B, int32_t N, double hs, const doubl
 ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
                     const double *rho, double *p0, void *stream)
 {
-    if (!h || B < 1 || N < 4 || N % 4 || !(hs > 0) || !rhs || !rho || !p0) return IB_EINVAL;
-    cudaError_t e = ibk::cnn_workspace(*h->n, B, N);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IB_ENOMEM : IB_ECUDA;
-    ibk::cnn_forward(*h->n, B, N, hs, rhs, rho, nullptr, (cudaStream_t)stream);
-    ibk::cnn_output(*h->n, B, N, hs, p0, (cudaStream_t)stream);
-    return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
+    if (!h || B < 1 || N < 4 || N % (4 << h->coarsen) || !(hs > 0) || !rhs || !rho || !p0)
+        return IB_EINVAL;
+    cudaError_t e = ibk::cnn_infer_levels(*h->n, B, N, hs, rhs, rho, p0, h->coarsen, (cudaStream_t)stream);
+    if (e == cudaErrorMemoryAllocation) return IB_ENOMEM;
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+ib_status cnn_set_coarsen(ib_cnn *h, int32_t levels)
+{
+    if (!h || levels < 0 || levels > 6) return IB_EINVAL;
+    h->coarsen = levels;
+    return IB_OK;
 }
 
 ib_status cnn_set_scale(ib_cnn *h, double c)
@@ -627,8 +671,22 @@ ib_status ib_op_rbgs(int32_t nx, int32_t ny, double h, const double *bx, const d
                      const double *b, double *p, int32_t nsweeps, void *stream)
 {
     OPCHK(nx > 0 && ny > 0 && h > 0 && bx && by && b && p && nsweeps >= 0);
-    for (int k = 0; k < nsweeps; k++)
-        launch_rbgs(nx, ny, h, bx, by, nullptr, b, p, (cudaStream_t)stream);
+    // sweeps alternate between p and a scratch copy (a sweep reads its
+    // neighbours' halo, so it must not write the buffer it reads)
+    double *tmp = nullptr;
+    const size_t bytes = (size_t)nx * ny * 8;
+    if (nsweeps > 0 && cudaMalloc(&tmp, bytes) != cudaSuccess) return IB_ENOMEM;
+    double *cur = p;
+    for (int k = 0; k < nsweeps; k++) {
+        double *nxt = cur == p ? tmp : p;
+        launch_rbgs(nx, ny, h, bx, by, nullptr, b, cur, nxt, (cudaStream_t)stream);
+        cur = nxt;
+    }
+    if (cur != p) cudaMemcpyAsync(p, cur, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (tmp) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaFree(tmp);
+    }
     return op_done();
 }
 

@@ -517,6 +517,34 @@ __global__ void k_output(long n, int N2, const float *__restrict__ y32, const do
     p0[k] = st[1] * pscale * ((double)y32[k] - st[5]);
 }
 
+// 2x2 mean of B samples of (2 Nc) x (2 Nc) into Nc x Nc.
+__global__ void k_restrict2(long nc, int Nc, const double *__restrict__ in, double *__restrict__ out)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const long N2c = (long)Nc * Nc, smp = k / N2c;
+    const int r = (int)(k - smp * N2c), J = r / Nc, I = r - J * Nc, N = 2 * Nc;
+    const double *a = in + smp * 4 * N2c + (long)(2 * J) * N + 2 * I;
+    out[k] = 0.25 * (a[0] + a[1] + a[N] + a[N + 1]);
+}
+
+// Cell-centred bilinear interpolation (9, 3, 3, 1)/16 of Nc x Nc samples to
+// (2 Nc) x (2 Nc), zero-gradient at the walls.
+__global__ void k_prolong2(long nf, int Nc, const double *__restrict__ ec, double *__restrict__ ef)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    const int N = 2 * Nc;
+    const long N2 = (long)N * N, smp = k / N2;
+    const int r = (int)(k - smp * N2), j = r / N, i = r - j * N;
+    const int I = i >> 1, J = j >> 1;
+    const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), Nc - 1);
+    const int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), Nc - 1);
+    const double *c = ec + smp * (long)Nc * Nc;
+    ef[k] = (9.0 * c[J * Nc + I] + 3.0 * c[J * Nc + I2] + 3.0 * c[J2 * Nc + I] + c[J2 * Nc + I2]) *
+            0.0625;
+}
+
 // Adam with bias correction on FP32 master weights.
 __global__ void k_adam(long n, float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                        const float *__restrict__ g, float lr, float b1, float b2, float eps,
@@ -586,6 +614,9 @@ struct Cnn {
     float *y32 = nullptr, *t = nullptr, *lsum = nullptr, *gpad = nullptr, *part = nullptr;
     double *stats = nullptr, *rpart = nullptr;
     size_t part_cap = 0;
+    // coarse-grid inference: restricted inputs and prolongated outputs
+    double *cbuf = nullptr;
+    size_t cbuf_cap = 0;
 };
 
 namespace {
@@ -719,6 +750,7 @@ void cnn_free(Cnn *n)
     if (!n) return;
     if (n->wmem) cudaFree(n->wmem);
     if (n->amem) cudaFree(n->amem);
+    if (n->cbuf) cudaFree(n->cbuf);
     delete n;
 }
 
@@ -883,6 +915,61 @@ void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s)
     k_ymean_final<<<B, 256, 0, s>>>(N2, n.rpart, n.stats);
     note_launch();
     k_output<<<cdiv(P, 256), 256, 0, s>>>(P, N2, n.y32, n.stats, h * h * n.out_scale, p0);
+}
+
+// Inference with the inputs averaged over 2^levels x 2^levels blocks, the
+// network run on the coarse grid (cell size h 2^levels) and its estimate
+// interpolated back (bilinear, once per level); levels = 0 is plain
+// inference.  N must be a multiple of 4 * 2^levels.
+cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
+                             double *p0, int levels, cudaStream_t s)
+{
+    const int Nc = N >> levels;
+    if (levels < 0 || levels > 6 || (Nc << levels) != N || Nc < 4 || Nc % 4) return cudaErrorInvalidValue;
+    cudaError_t e = cnn_workspace(n, B, Nc);
+    if (e != cudaSuccess) return e;
+    if (levels == 0) {
+        cnn_forward(n, B, N, h, rhs, rho, nullptr, s);
+        cnn_output(n, B, N, h, p0, s);
+        return cudaGetLastError();
+    }
+    // per level k = 1..levels: b_k, rho_k, p_k (B (N >> k)^2 each)
+    size_t need = 0;
+    for (int k = 1; k <= levels; k++) need += 3 * (size_t)B * (N >> k) * (N >> k);
+    if (need > n.cbuf_cap) {
+        if (n.cbuf) cudaFree(n.cbuf);
+        n.cbuf = nullptr;
+        n.cbuf_cap = 0;
+        e = cudaMalloc(&n.cbuf, need * 8);
+        if (e != cudaSuccess) return e;
+        n.cbuf_cap = need;
+    }
+    double *bk[8], *rk[8], *pk[8];
+    double *q = n.cbuf;
+    for (int k = 1; k <= levels; k++) {
+        const size_t m = (size_t)B * (N >> k) * (N >> k);
+        bk[k] = q; rk[k] = q + m; pk[k] = q + 2 * m;
+        q += 3 * m;
+    }
+    bk[0] = const_cast<double *>(rhs);
+    rk[0] = const_cast<double *>(rho);
+    pk[0] = p0;
+    for (int k = 1; k <= levels; k++) {
+        const long m = (long)B * (N >> k) * (N >> k);
+        note_launch();
+        k_restrict2<<<cdiv(m, 256), 256, 0, s>>>(m, N >> k, bk[k - 1], bk[k]);
+        note_launch();
+        k_restrict2<<<cdiv(m, 256), 256, 0, s>>>(m, N >> k, rk[k - 1], rk[k]);
+    }
+    const double hc = h * (double)(1 << levels);
+    cnn_forward(n, B, Nc, hc, bk[levels], rk[levels], nullptr, s);
+    cnn_output(n, B, Nc, hc, pk[levels], s);
+    for (int k = levels; k >= 1; k--) {
+        const long m = (long)B * (N >> (k - 1)) * (N >> (k - 1));
+        note_launch();
+        k_prolong2<<<cdiv(m, 256), 256, 0, s>>>(m, N >> k, pk[k], pk[k - 1]);
+    }
+    return cudaGetLastError();
 }
 
 void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }

@@ -84,94 +84,111 @@ __global__ void k_correct(int nx, int ny, double ih, double dt,
     v[k] = vs[k] + dt * (by[k] * (Fy[k] - gp));
 }
 
-// Predictor for u (x-faces) and v (y-faces) in one index space.  Node
-// averages use the four surrounding cells (two at a wall); no-slip walls by
-// the reflected ghost value.
-__global__ void k_predictor(int nx, int ny, double ih, double ih2, double dt,
-                            const double *__restrict__ rho, const double *__restrict__ mu,
-                            const double *__restrict__ u, const double *__restrict__ v,
-                            const double *__restrict__ aup, const double *__restrict__ avp,
-                            int have_prev, double gx, double gy, double *__restrict__ us,
-                            double *__restrict__ vs, double *__restrict__ au,
-                            double *__restrict__ av)
+// Tiled predictor: a 32 x 8 block of cells stages rho, mu, u and v with a
+// one-cell ring in shared memory, forms the node averages of rho and mu once
+// per node (four cells inside, the two wall cells on a wall), and each
+// thread then updates the x-face left of and the y-face below its cell (and
+// the wall face on the far side for the last column / row).
+constexpr int PX = 32, PY = 8;
+__global__ void __launch_bounds__(PX * PY)
+k_predictor(int nx, int ny, double ih, double ih2, double dt,
+            const double *__restrict__ rho, const double *__restrict__ mu,
+            const double *__restrict__ u, const double *__restrict__ v,
+            const double *__restrict__ aup, const double *__restrict__ avp,
+            int have_prev, double gx, double gy, double *__restrict__ us,
+            double *__restrict__ vs, double *__restrict__ au, double *__restrict__ av)
 {
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long nxf = (long)(nx + 1) * ny;
-#define RC(i, j) rho[(long)(j) * nx + (i)]
-#define MC(i, j) mu[(long)(j) * nx + (i)]
-#define UF(i, j) u[(long)(j) * (nx + 1) + (i)]
-#define VF(i, j) v[(long)(j) * nx + (i)]
-    if (k < nxf) {
-        int j = (int)(k / (nx + 1)), i = (int)(k - (long)j * (nx + 1));
-        if (i == 0 || i == nx) { us[k] = 0.0; au[k] = 0.0; return; }
-        double uc = u[k], uE = UF(i + 1, j), uW = UF(i - 1, j);
-        double uN = (j + 1 < ny) ? UF(i, j + 1) : -uc;
-        double uS = (j > 0) ? UF(i, j - 1) : -uc;
-        double aE = 0.5 * (uE + uc), aW = 0.5 * (uc + uW);
-        double fE = RC(i, j) * aE * aE, fW = RC(i - 1, j) * aW * aW;
-        double gN = 0.0, gS = 0.0, muN, muS;
-        if (j + 1 < ny) {
-            double rN = 0.25 * (RC(i - 1, j) + RC(i, j) + RC(i - 1, j + 1) + RC(i, j + 1));
-            double vN = 0.5 * (VF(i - 1, j + 1) + VF(i, j + 1));
-            gN = rN * vN * (0.5 * (uc + uN));
-            muN = 0.25 * (MC(i - 1, j) + MC(i, j) + MC(i - 1, j + 1) + MC(i, j + 1));
-        } else {
-            muN = 0.5 * (MC(i - 1, j) + MC(i, j));
+    constexpr int W = PX + 2, Hh = PY + 2;  // staged window: cells / faces i0-1 .. i0+PX
+    __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
+    __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
+    const int i0 = blockIdx.x * PX, j0 = blockIdx.y * PY;
+    const int t = threadIdx.y * PX + threadIdx.x;
+    const long nxf = nx + 1;
+    // staging; out-of-domain entries are never used by a face that is updated
+    for (int k = t; k < Hh * (W + 1); k += PX * PY) {
+        const int r = k / (W + 1), c = k - r * (W + 1), gi = i0 - 1 + c, gj = j0 - 1 + r;
+        const bool inj = gj >= 0 && gj < ny;
+        if (c < W) {
+            const bool in = inj && gi >= 0 && gi < nx;
+            const long o = (long)gj * nx + gi;
+            sr[r][c] = in ? rho[o] : 0.0;
+            sm[r][c] = in ? mu[o] : 0.0;
         }
-        if (j > 0) {
-            double rS = 0.25 * (RC(i - 1, j - 1) + RC(i, j - 1) + RC(i - 1, j) + RC(i, j));
-            double vS = 0.5 * (VF(i - 1, j) + VF(i, j));
-            gS = rS * vS * (0.5 * (uc + uS));
-            muS = 0.25 * (MC(i - 1, j - 1) + MC(i, j - 1) + MC(i - 1, j) + MC(i, j));
+        su[r][c] = (inj && gi >= 0 && gi <= nx) ? u[(long)gj * nxf + gi] : 0.0;
+    }
+    for (int k = t; k < (Hh + 1) * W; k += PX * PY) {
+        const int r = k / W, c = k - r * W, gi = i0 - 1 + c, gj = j0 - 1 + r;
+        sv[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? v[(long)gj * nx + gi] : 0.0;
+    }
+    __syncthreads();
+    // node (I, J) = corner of cells (I-1, J-1), (I, J-1), (I-1, J), (I, J);
+    // window index of cell (gi, gj) is (gj - j0 + 1, gi - i0 + 1)
+    for (int k = t; k < (PY + 1) * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double *r0 = &sr[r][c], *r1 = &sr[r + 1][c];  // rows J-1, J; columns I-1, I
+        const double *m0 = &sm[r][c], *m1 = &sm[r + 1][c];
+        const bool wx = I == 0 || I == nx, wy = J == 0 || J == ny;
+        nr[r][c] = 0.25 * (r0[0] + r0[1] + r1[0] + r1[1]);
+        if (!wx && !wy) nm[r][c] = 0.25 * (m0[0] + m0[1] + m1[0] + m1[1]);
+        else if (wy && !wx) nm[r][c] = J == 0 ? 0.5 * (m1[0] + m1[1]) : 0.5 * (m0[0] + m0[1]);
+        else if (wx && !wy) nm[r][c] = I == 0 ? 0.5 * (m0[1] + m1[1]) : 0.5 * (m0[0] + m1[0]);
+        else nm[r][c] = 0.0;  // corner: never used
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
+    if (i >= nx || j >= ny) return;
+    const int R = ty + 1, C = tx + 1;  // window index of cell (i, j)
+    // x-face (i, j), left of cell (i, j)
+    {
+        const long k = (long)j * nxf + i;
+        if (i == 0) {
+            us[k] = 0.0; au[k] = 0.0;
         } else {
-            muS = 0.5 * (MC(i - 1, j) + MC(i, j));
+            const double uc = su[R][C], uE = su[R][C + 1], uW = su[R][C - 1];
+            const double uN = (j + 1 < ny) ? su[R + 1][C] : -uc;
+            const double uS = (j > 0) ? su[R - 1][C] : -uc;
+            const double aE = 0.5 * (uE + uc), aW = 0.5 * (uc + uW);
+            const double fE = sr[R][C] * aE * aE, fW = sr[R][C - 1] * aW * aW;
+            double gN = 0.0, gS = 0.0;
+            if (j + 1 < ny) gN = nr[ty + 1][tx] * (0.5 * (sv[R + 1][C - 1] + sv[R + 1][C])) * (0.5 * (uc + uN));
+            if (j > 0) gS = nr[ty][tx] * (0.5 * (sv[R][C - 1] + sv[R][C])) * (0.5 * (uc + uS));
+            const double muN = nm[ty + 1][tx], muS = nm[ty][tx];
+            const double adv = (fE - fW) * ih + (gN - gS) * ih;
+            const double vis = (sm[R][C] * (uE - uc) - sm[R][C - 1] * (uc - uW) + muN * (uN - uc) -
+                                muS * (uc - uS)) * ih2;
+            const double rf = 0.5 * (sr[R][C - 1] + sr[R][C]);
+            const double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
+            us[k] = uc + dt * ((vis - ae) / rf + gx);
+            au[k] = adv;
         }
-        double adv = (fE - fW) * ih + (gN - gS) * ih;
-        double vis = (MC(i, j) * (uE - uc) - MC(i - 1, j) * (uc - uW) + muN * (uN - uc) -
-                      muS * (uc - uS)) * ih2;
-        double rf = 0.5 * (RC(i - 1, j) + RC(i, j));
-        double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
-        us[k] = uc + dt * ((vis - ae) / rf + gx);
-        au[k] = adv;
-        return;
+        if (i == nx - 1) { us[k + 1] = 0.0; au[k + 1] = 0.0; }  // right wall face
     }
-    k -= nxf;
-    if (k >= (long)nx * (ny + 1)) return;
-    int j = (int)(k / nx), i = (int)(k - (long)j * nx);
-    if (j == 0 || j == ny) { vs[k] = 0.0; av[k] = 0.0; return; }
-    double vc = v[k], vN = VF(i, j + 1), vS = VF(i, j - 1);
-    double vE = (i + 1 < nx) ? VF(i + 1, j) : -vc;
-    double vW = (i > 0) ? VF(i - 1, j) : -vc;
-    double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
-    double fN = RC(i, j) * aN * aN, fS = RC(i, j - 1) * aS * aS;
-    double gE = 0.0, gW = 0.0, muE, muW;
-    if (i + 1 < nx) {
-        double rE = 0.25 * (RC(i, j - 1) + RC(i + 1, j - 1) + RC(i, j) + RC(i + 1, j));
-        double uE = 0.5 * (UF(i + 1, j - 1) + UF(i + 1, j));
-        gE = rE * uE * (0.5 * (vc + vE));
-        muE = 0.25 * (MC(i, j - 1) + MC(i + 1, j - 1) + MC(i, j) + MC(i + 1, j));
-    } else {
-        muE = 0.5 * (MC(i, j - 1) + MC(i, j));
+    // y-face (i, j), below cell (i, j)
+    {
+        const long k = (long)j * nx + i;
+        if (j == 0) {
+            vs[k] = 0.0; av[k] = 0.0;
+        } else {
+            const double vc = sv[R][C], vN = sv[R + 1][C], vS = sv[R - 1][C];
+            const double vE = (i + 1 < nx) ? sv[R][C + 1] : -vc;
+            const double vW = (i > 0) ? sv[R][C - 1] : -vc;
+            const double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
+            const double fN = sr[R][C] * aN * aN, fS = sr[R - 1][C] * aS * aS;
+            double gE = 0.0, gW = 0.0;
+            if (i + 1 < nx) gE = nr[ty][tx + 1] * (0.5 * (su[R - 1][C + 1] + su[R][C + 1])) * (0.5 * (vc + vE));
+            if (i > 0) gW = nr[ty][tx] * (0.5 * (su[R - 1][C] + su[R][C])) * (0.5 * (vc + vW));
+            const double muE = nm[ty][tx + 1], muW = nm[ty][tx];
+            const double adv = (fN - fS) * ih + (gE - gW) * ih;
+            const double vis = (sm[R][C] * (vN - vc) - sm[R - 1][C] * (vc - vS) + muE * (vE - vc) -
+                                muW * (vc - vW)) * ih2;
+            const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
+            const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
+            vs[k] = vc + dt * ((vis - ae) / rf + gy);
+            av[k] = adv;
+        }
+        if (j == ny - 1) { vs[k + nx] = 0.0; av[k + nx] = 0.0; }  // top wall face
     }
-    if (i > 0) {
-        double rW = 0.25 * (RC(i - 1, j - 1) + RC(i, j - 1) + RC(i - 1, j) + RC(i, j));
-        double uW = 0.5 * (UF(i, j - 1) + UF(i, j));
-        gW = rW * uW * (0.5 * (vc + vW));
-        muW = 0.25 * (MC(i - 1, j - 1) + MC(i, j - 1) + MC(i - 1, j) + MC(i, j));
-    } else {
-        muW = 0.5 * (MC(i, j - 1) + MC(i, j));
-    }
-    double adv = (fN - fS) * ih + (gE - gW) * ih;
-    double vis = (MC(i, j) * (vN - vc) - MC(i, j - 1) * (vc - vS) + muE * (vE - vc) -
-                  muW * (vc - vW)) * ih2;
-    double rf = 0.5 * (RC(i, j - 1) + RC(i, j));
-    double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
-    vs[k] = vc + dt * ((vis - ae) / rf + gy);
-    av[k] = adv;
-#undef RC
-#undef MC
-#undef UF
-#undef VF
 }
 
 }  // namespace
@@ -215,11 +232,10 @@ void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       int have_prev, double gx, double gy, double *us,
                       double *vs, double *au, double *av, cudaStream_t s)
 {
-    long nf = (long)(nx + 1) * ny + (long)nx * (ny + 1);
+    dim3 g(cdiv(nx, PX), cdiv(ny, PY)), b(PX, PY);
     note_launch();
-    k_predictor<<<cdiv(nf, kT), kT, 0, s>>>(nx, ny, 1.0 / h, 1.0 / (h * h), dt, rho,
-                                            mu, u, v, au_prev, av_prev, have_prev,
-                                            gx, gy, us, vs, au, av);
+    k_predictor<<<g, b, 0, s>>>(nx, ny, 1.0 / h, 1.0 / (h * h), dt, rho, mu, u, v, au_prev,
+                                av_prev, have_prev, gx, gy, us, vs, au, av);
 }
 
 }  // namespace ibk

@@ -10,11 +10,13 @@
 
 namespace ibk {
 
-constexpr int kTailCells = 1024;     // levels with at most this many cells run in one CTA
+constexpr int kTailCells = 1024;     // levels with at most this many cells run in one CTA (FP64)
+constexpr int kTailCellsF32 = 4096;  // the same for the FP32 cycle (its levels fit shared memory)
 constexpr int kMaxCoarsest = 1024;   // dense LU limit of the coarsest level
 constexpr int kBlk = 8;              // marker-activity block edge (cells)
 constexpr int kSearch = 7;           // marker search radius (cells) around a cell or face
 constexpr int kMaxCand = 1024;       // candidate segments per activity block
+constexpr int kSegLine = 56;        // doubles per segment of the FP64 strip-line record
 constexpr int kMaxCross = 2048;      // interface crossings per grid row
 
 inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
@@ -51,6 +53,7 @@ void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
 template <typename T>
 struct LevelT {
     T *e = nullptr, *r = nullptr, *bx = nullptr, *by = nullptr, *invd = nullptr;
+    T *e2 = nullptr;  // second iterate buffer: sweeps read one and write the other
 };
 
 struct Level {
@@ -84,7 +87,8 @@ struct MG {
     cudaStream_t cap = nullptr, cap_body = nullptr;
     SolveCtl *ctl = nullptr, *ctl_host = nullptr;
     bool use_graphs = true;
-    int tail = 0;                 // first level handled by the single-CTA tail kernel
+    int tail = 0;                 // first level handled by the single-CTA tail kernel (FP64)
+    int tail_f = 0;               // the same for the FP32 cycle
     double *lu = nullptr;         // coarsest dense LU (n x n), FP64
     int *piv = nullptr;           // coarsest row permutation
     double *red = nullptr;        // reduction partials + results (device)
@@ -102,6 +106,9 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys);
 size_t mg_layout(MG &mg, int nx, int ny, double h, char *base);
 cudaError_t mg_alloc(MG &mg, int nx, int ny, double h);
 void mg_free(MG &mg);
+// One fine-level smoother launch on the current hierarchy data (precision 1:
+// two fused FP32 sweeps, 0: one FP64 sweep), for kernel timing.
+void mg_fine_smoother(MG &mg, int precision, cudaStream_t s);
 // Copy level-0 coefficients (walls forced to 0) and build the hierarchy.
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s);
 // Runs the solve on level-0 arrays of the hierarchy; p is read/written in place.
@@ -116,7 +123,8 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
                         cudaStream_t s, std::string &err);
 
 void launch_rbgs(int nx, int ny, double h, const double *bx, const double *by,
-                 const double *invd, const double *b, double *p, cudaStream_t s);
+                 const double *invd, const double *b, const double *pin, double *p,
+                 cudaStream_t s);
 void launch_invdiag(int nx, int ny, const double *bx, const double *by,
                     double *invd, cudaStream_t s);
 void launch_restrict_residual(int nx, int ny, double h, const double *bx,
@@ -144,7 +152,7 @@ struct Markers {
     unsigned long long *ykey = nullptr;    // order-preserving integer key of each Y
     ulonglong2 *dyk = nullptr;             // keys of the per-drop Y range
     double *sv = nullptr;                  // per segment: 12 strip corner points (24 doubles)
-    double *sl = nullptr;                  // per segment: 8 half-planes (nx, ny, c) FP64
+    double *sl = nullptr;                  // per segment: 8 half-planes (a, b, c, 1/a, 1/b) + determinant reciprocals, FP64
     float4 *slf = nullptr;                 // the same in FP32 (nx, ny, c, |n|)
     uint8_t *scvx = nullptr;               // per segment: 1 = half-plane path (strips convex, lines well conditioned)
     uint32_t pair_cap = 0;                 // capacity of the band (cell, segment) pair list
@@ -177,6 +185,7 @@ void launch_interp(const Markers &mk, int kernel, const double *u,
 void launch_spread_conv(const Markers &mk, int kernel, const double *fmag,
                         double *Fx, double *Fy, cudaStream_t s);
 void launch_heaviside(const Markers &mk, double *H, cudaStream_t s);
+void launch_band_area(const Markers &mk, cudaStream_t s);
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
                          double *Fx, double *Fy, cudaStream_t s);
 void launch_relocate(Markers &mk, cudaStream_t s);
@@ -192,6 +201,8 @@ void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double
 void cnn_backward(Cnn &n, int B, int N, cudaStream_t s);
 void cnn_adam(Cnn &n, float lr, cudaStream_t s);
 void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s);
+cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
+                             double *p0, int levels, cudaStream_t s);
 void cnn_set_scale(Cnn &n, double c);
 double cnn_get_scale(const Cnn &n);
 size_t cnn_nparam(const Cnn &n);

@@ -154,11 +154,23 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     left_of(ax[5], ay[5], ax[0], ay[0], L[0]);
     left_of(bx[0], by[0], bx[5], by[5], L[1]);
     for (int o = 0; o < 6; o++) left_of(ax[o], ay[o], bx[o], by[o], L[2 + o]);
+    // FP64 record (kSegLine doubles): per line a, b, c, 1/a, 1/b (0 where
+    // the component vanishes), then the reciprocals of the determinants
+    // a_i b_j - b_i a_j of the two normal edges and of each normal edge with
+    // each offset line, which the per-cell area formula would otherwise
+    // recompute for every cell the segment meets.
+    double *d = sl + (long)m * kSegLine;
+    auto rcp = [](double v) { return v != 0.0 ? 1.0 / v : 0.0; };
     for (int q = 0; q < 8; q++) {
-        double *d = sl + ((long)m * 8 + q) * 3;
-        d[0] = L[q][0]; d[1] = L[q][1]; d[2] = L[q][2];
+        d[5 * q + 0] = L[q][0]; d[5 * q + 1] = L[q][1]; d[5 * q + 2] = L[q][2];
+        d[5 * q + 3] = rcp(L[q][0]); d[5 * q + 4] = rcp(L[q][1]);
         slf[(long)m * 8 + q] = make_float4((float)L[q][0], (float)L[q][1], (float)L[q][2],
                                            (float)sqrt(L[q][0] * L[q][0] + L[q][1] * L[q][1]));
+    }
+    d[40] = rcp(L[0][0] * L[1][1] - L[0][1] * L[1][0]);
+    for (int o = 0; o < 6; o++) {
+        d[41 + 2 * o] = rcp(L[0][0] * L[2 + o][1] - L[0][1] * L[2 + o][0]);
+        d[42 + 2 * o] = rcp(L[1][0] * L[2 + o][1] - L[1][1] * L[2 + o][0]);
     }
     // The strips are the intersections of those half-planes only when every
     // strip quadrilateral (A_k, B_k, B_k+1, A_k+1) is strictly convex; a
@@ -173,14 +185,14 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
             cvx = cvx && cr > 1e-6;
         }
     }
-    // The half-plane path also wants every line at least 0.01 rad away from
+    // The half-plane path also wants every line at least 0.001 rad away from
     // the grid axes (or exactly on one): a line nearly parallel to a cell edge
     // meets it at an ill-conditioned point, which the area formula would use
     // twice (once per boundary piece); quadrilateral clipping has no such
     // sensitivity and takes those segments.
     for (int q = 0; q < 8; q++) {
         const double aa = fabs(L[q][0]), bb = fabs(L[q][1]);
-        cvx = cvx && (aa == 0.0 || aa >= 1e-2) && (bb == 0.0 || bb >= 1e-2);
+        cvx = cvx && (aa == 0.0 || aa >= 1e-3) && (bb == 0.0 || bb >= 1e-3);
     }
     scvx[m] = cvx ? 1 : 0;
 }
@@ -605,7 +617,9 @@ __device__ __forceinline__ int cell_side(float4 l, float fi, float fj)
 // Pair ranges are claimed with an atomic counter, so their place in the list
 // varies from run to run, but each cell's pairs and their order do not: H is
 // deterministic.
-__global__ void __launch_bounds__(kBT)
+constexpr int kPairT = 256, kPairSub = kPairT / kBT;  // 4 threads per cell
+constexpr int kStage = 256;  // candidates whose slab tests are staged in shared memory
+__global__ void __launch_bounds__(kPairT)
 k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
              const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
              const float4 *__restrict__ slf, const uint8_t *__restrict__ scvx,
@@ -614,32 +628,59 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
              uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
-    __shared__ uint32_t cnt[kBT + 1];
+    __shared__ float4 s_box[kStage], s_l[4][kStage];
+    __shared__ uint8_t s_cvx[kStage];
+    __shared__ uint32_t cnt[kPairT], wsum[kPairT / 32 + 1];
     __shared__ uint32_t base;
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
-    const int t = threadIdx.x;
-    const int i = bi * kBlk + (t % kBlk), j = bj * kBlk + (t / kBlk);
+    const int ns = min(n, kStage);
+    for (int q = threadIdx.x; q < ns; q += kPairT) {
+        const uint32_t m = cand[q];
+        s_box[q] = sbox[m];
+        s_l[0][q] = slf[(long)m * 8 + 0];
+        s_l[1][q] = slf[(long)m * 8 + 1];
+        s_l[2][q] = slf[(long)m * 8 + 2];
+        s_l[3][q] = slf[(long)m * 8 + 7];
+        s_cvx[q] = scvx[m];
+    }
+    __syncthreads();
+    const int t = threadIdx.x, cl = t / kPairSub, sub = t - cl * kPairSub;
+    const int i = bi * kBlk + (cl % kBlk), j = bj * kBlk + (cl / kBlk);
     const bool live = i < nx && j < ny;
     const float fi = (float)i, fj = (float)j;
-    auto meets = [&](uint32_t m) {
-        const float4 b = sbox[m];
+    auto meets = [&](int q) {
+        const uint32_t m = cand[q];
+        const bool st = q < kStage;
+        const float4 b = st ? s_box[q] : sbox[m];
         if (b.x > fi + 1.0f || b.y < fi || b.z > fj + 1.0f || b.w < fj) return false;
-        if (!scvx[m]) return true;
+        if (!(st ? s_cvx[q] : scvx[m])) return true;
         const float4 *L = slf + (long)m * 8;
-        return cell_side(L[0], fi, fj) >= 0 && cell_side(L[1], fi, fj) >= 0 &&
-               cell_side(L[2], fi, fj) >= 0 && cell_side(L[7], fi, fj) <= 0;
+        return cell_side(st ? s_l[0][q] : L[0], fi, fj) >= 0 &&
+               cell_side(st ? s_l[1][q] : L[1], fi, fj) >= 0 &&
+               cell_side(st ? s_l[2][q] : L[2], fi, fj) >= 0 &&
+               cell_side(st ? s_l[3][q] : L[7], fi, fj) <= 0;
     };
+    // this thread's contiguous share of the (ascending) candidate list
+    const int q0 = (n * sub) / kPairSub, q1 = (n * (sub + 1)) / kPairSub;
     uint32_t c = 0;
     if (live)
-        for (int q = 0; q < n; q++) c += meets(cand[q]) ? 1u : 0u;
-    cnt[t] = c;
+        for (int q = q0; q < q1; q++) c += meets(q) ? 1u : 0u;
+    // exclusive scan over threads (cell-major, then share): warp scans, then
+    // the warp totals
+    const int lane = t & 31, warp = t >> 5;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (t == 0) {
         uint32_t acc = 0;
-        for (int k = 0; k < kBT; k++) { uint32_t v = cnt[k]; cnt[k] = acc; acc += v; }
-        cnt[kBT] = acc;
+        for (int w = 0; w < kPairT / 32; w++) { const uint32_t v = wsum[w]; wsum[w] = acc; acc += v; }
+        wsum[kPairT / 32] = acc;
         const uint32_t b0 = atomicAdd(npairs, acc);
         if (b0 > cap || acc > cap - b0) {
             atomicOr(&flags[1], 1u);
@@ -649,16 +690,22 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
         }
     }
     __syncthreads();
+    const uint32_t excl = wsum[warp] + incl - c;
+    cnt[t] = excl;
+    __syncthreads();
     if (!live) return;
     const long cidx = (long)j * nx + i;
     if (base == 0xffffffffu) {
-        crange[cidx] = make_uint2(0u, 0u);
+        if (sub == 0) crange[cidx] = make_uint2(0u, 0u);
         return;
     }
-    uint32_t o = base + cnt[t];
-    crange[cidx] = make_uint2(o, c);
-    for (int q = 0; q < n; q++)
-        if (meets(cand[q])) { pseg[o] = cand[q]; pcell[o] = (uint32_t)cidx; o++; }
+    if (sub == 0) {
+        const uint32_t end = (cl + 1 < kBT) ? cnt[t + kPairSub] : wsum[kPairT / 32];
+        crange[cidx] = make_uint2(base + excl, end - excl);
+    }
+    uint32_t o = base + excl;
+    for (int q = q0; q < q1; q++)
+        if (meets(q)) { pseg[o] = cand[q]; pcell[o] = (uint32_t)cidx; o++; }
 }
 
 // A bounding line of a strip in the cell's local frame (the cell is the unit
@@ -670,16 +717,15 @@ struct CellLine {
     bool on;
 };
 
-__device__ __forceinline__ double safe_rcp(double v) { return v != 0.0 ? 1.0 / v : 0.0; }
-
+// l: a, b, c, 1/a, 1/b of the line in grid coordinates.
 __device__ __forceinline__ CellLine cell_line(const double *l, double di, double dj, bool on)
 {
     CellLine L;
     L.a = on ? l[0] : 0.0;
     L.b = on ? l[1] : 0.0;
     L.c = on ? l[2] - l[0] * di - l[1] * dj : -1.0;
-    L.ra = safe_rcp(L.a);
-    L.rb = safe_rcp(L.b);
+    L.ra = on ? l[3] : 0.0;
+    L.rb = on ? l[4] : 0.0;
     L.on = on;
     return L;
 }
@@ -745,7 +791,7 @@ __device__ __forceinline__ double cut_area(const CellLine *L, double r01, double
 // edges that cross it (area a0), S_o = area(P on the inner side of offset line
 // o) for o = 0..5 (a0 or 0 when the FP32 test finds the line clear of the
 // cell, else cut_area in FP64), and strip k has area S_k - S_k+1.  Other
-// segments (folded strips, lines within 0.01 rad of a grid axis): each
+// segments (folded strips, lines within 0.001 rad of a grid axis): each
 // quadrilateral is clipped against the cell (Sutherland-Hodgman).
 __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const double *__restrict__ sl,
                                           const float4 *__restrict__ slf,
@@ -775,15 +821,15 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
         return;
     }
     const float4 *Lf = slf + (long)m * 8;
-    const double *Ld = sl + (long)m * 24;
+    const double *Ld = sl + (long)m * kSegLine;
     int side[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) side[q] = cell_side(Lf[q], gi, gj);
     // slots 0, 1: the normal edges that cut the cell (others constrain nothing)
     CellLine L[3];
 #pragma unroll
-    for (int q = 0; q < 2; q++) L[q] = cell_line(Ld + 3 * q, di, dj, side[q] == 0);
-    const double r01 = safe_rcp(L[0].a * L[1].b - L[0].b * L[1].a);
+    for (int q = 0; q < 2; q++) L[q] = cell_line(Ld + 5 * q, di, dj, side[q] == 0);
+    const double r01 = Ld[40];
     const double a0 = (side[0] == 0 || side[1] == 0) ? cut_area<2>(L, r01, 0.0, 0.0) : 1.0;
     double S[6];
 #pragma unroll
@@ -794,9 +840,8 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
         } else if (side[q] < 0) {
             S[o] = 0.0;
         } else {
-            L[2] = cell_line(Ld + 3 * q, di, dj, true);
-            S[o] = cut_area<3>(L, r01, safe_rcp(L[0].a * L[2].b - L[0].b * L[2].a),
-                            safe_rcp(L[1].a * L[2].b - L[1].b * L[2].a));
+            L[2] = cell_line(Ld + 5 * q, di, dj, true);
+            S[o] = cut_area<3>(L, r01, Ld[41 + 2 * o], Ld[42 + 2 * o]);
         }
     }
 #pragma unroll
@@ -807,6 +852,7 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
     }
 }
 
+// One pair per thread.
 __global__ void __launch_bounds__(256)
 k_band_area(int nx, const uint32_t *__restrict__ npairs, uint32_t cap,
             const uint32_t *__restrict__ pseg, const uint32_t *__restrict__ pcell,
@@ -848,8 +894,13 @@ k_band_sum(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
 // Irrotational face force F = f_face (H_ij - H_nb) / h on the x-face left of
 // and the y-face below every cell of an active block; f_face from the nearest
 // segment (closest point clamped to the segment, ties to the lower id),
-// linear in the segment parameter between its two markers.
-__global__ void __launch_bounds__(kBT)
+// linear in the segment parameter between its two markers.  One thread per
+// face: the block's 128 faces are tested for dH != 0, the faces with work
+// are packed into a list (so the FP64 part runs on full warps), and each of
+// those screens the block's candidates (staged in shared memory in FP32)
+// before evaluating the survivors exactly in FP64, in ascending id.
+constexpr int kIrrT = 2 * kBT;  // one thread per face of the block
+__global__ void __launch_bounds__(kIrrT)
 k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ bactive,
                const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
                const int32_t *__restrict__ next, const double *__restrict__ gx,
@@ -861,6 +912,9 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
     __shared__ float4 seg[kMaxCand];   // FP32 candidate segments: start, direction
     __shared__ float seg_il[kMaxCand]; // 1 / |direction|^2
+    __shared__ uint8_t work[kIrrT];     // faces with dH != 0, packed
+    __shared__ double wdH[kIrrT];
+    __shared__ int nwork;
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
     const int n = gather_candidates(bi, bj, nx, ny, cell_start, ids, cand, tmp, flags);
@@ -870,58 +924,70 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
         seg[q] = make_float4(ax, ay, ex, ey);
         seg_il[q] = 1.0f / (ex * ex + ey * ey);
     }
+    if (threadIdx.x == 0) nwork = 0;
     __syncthreads();
-    const int i = bi * kBlk + (threadIdx.x % kBlk), j = bj * kBlk + (threadIdx.x / kBlk);
-    if (i >= nx || j >= ny) return;
-    // squared FP32 distance from (fqx, fqy) to candidate q
-    auto d2f = [&](int q, float fqx, float fqy) {
+    // face f: dir = f / 64 (0: x-face left of the cell, 1: y-face below), cell f % 64
+    auto face = [&](int f, int &dir, int &i, int &j) {
+        dir = f / kBT;
+        const int c = f - dir * kBT;
+        i = bi * kBlk + (c % kBlk);
+        j = bj * kBlk + (c / kBlk);
+    };
+    {
+        const int f = threadIdx.x;
+        int dir, i, j;
+        face(f, dir, i, j);
+        if (i < nx && j < ny && !(dir == 0 && i == 0) && !(dir == 1 && j == 0)) {
+            const double dH = dir == 0 ? H[(long)j * nx + i] - H[(long)j * nx + i - 1]
+                                       : H[(long)j * nx + i] - H[(long)(j - 1) * nx + i];
+            if (dH != 0.0) {
+                const int w = atomicAdd(&nwork, 1);
+                work[w] = (uint8_t)f;
+                wdH[w] = dH;
+            } else if (dir == 0) {
+                Fx[(long)j * (nx + 1) + i] = 0.0;
+            } else {
+                Fy[(long)j * nx + i] = 0.0;
+            }
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= nwork) return;
+    int dir, i, j;
+    face(work[threadIdx.x], dir, i, j);
+    const double dH = wdH[threadIdx.x];
+    const double qx = dir == 0 ? (double)i : (double)i + 0.5;
+    const double qy = dir == 0 ? (double)j + 0.5 : (double)j;
+    // FP32 screen: squared distances carry an error far below 0.05 (grid
+    // units, coordinates < 2^15), so the exact nearest segment is among those
+    // within best + 0.05 of the FP32 minimum.
+    const float fqx = (float)qx, fqy = (float)qy;
+    auto d2f = [&](int q) {
         const float4 sg = seg[q];
         float t = ((fqx - sg.x) * sg.z + (fqy - sg.y) * sg.w) * seg_il[q];
         t = fminf(fmaxf(t, 0.0f), 1.0f);
         const float dx = sg.x + t * sg.z - fqx, dy = sg.y + t * sg.w - fqy;
         return dx * dx + dy * dy;
     };
-    for (int dir = 0; dir < 2; dir++) {
-        double dH;
-        double qx, qy;
-        if (dir == 0) {
-            if (i == 0) continue;
-            dH = H[(long)j * nx + i] - H[(long)j * nx + i - 1];
-            qx = (double)i; qy = (double)j + 0.5;
-        } else {
-            if (j == 0) continue;
-            dH = H[(long)j * nx + i] - H[(long)(j - 1) * nx + i];
-            qx = (double)i + 0.5; qy = (double)j;
-        }
-        double F = 0.0;
-        if (dH != 0.0) {
-            // FP32 screen from the candidates staged in shared memory: squared
-            // distances carry an error far below 0.05 (grid units, coordinates
-            // < 2^15), so the exact nearest segment is among those within
-            // best + 0.05 of the FP32 minimum.
-            const float fqx = (float)qx, fqy = (float)qy;
-            float best32 = INFINITY;
-            for (int q = 0; q < n; q++) best32 = fminf(best32, d2f(q, fqx, fqy));
-            const float lim = best32 + 0.05f;
-            double best = INFINITY, fb = 0.0;
-            for (int q = 0; q < n; q++) {
-                if (d2f(q, fqx, fqy) > lim) continue;
-                const int m = (int)cand[q], nm = next[m];
-                double ax = gx[m], ay = gy[m];
-                double bx = gx[nm], by = gy[nm];
-                double ex = bx - ax, ey = by - ay;
-                double t = ((qx - ax) * ex + (qy - ay) * ey) / (ex * ex + ey * ey);
-                if (t < 0.0) t = 0.0;
-                if (t > 1.0) t = 1.0;
-                double dx = ax + t * ex - qx, dy = ay + t * ey - qy;
-                double d2 = dx * dx + dy * dy;
-                if (d2 < best) { best = d2; fb = (1.0 - t) * fmag[m] + t * fmag[nm]; }
-            }
-            F = fb * dH / h;
-        }
-        if (dir == 0) Fx[(long)j * (nx + 1) + i] = F;
-        else Fy[(long)j * nx + i] = F;
+    float best32 = INFINITY;
+    for (int q = 0; q < n; q++) best32 = fminf(best32, d2f(q));
+    const float lim = best32 + 0.05f;
+    double best = INFINITY, fb = 0.0;
+    for (int q = 0; q < n; q++) {
+        if (d2f(q) > lim) continue;
+        const int m = (int)cand[q], nm = next[m];
+        const double ax = gx[m], ay = gy[m];
+        const double ex = gx[nm] - ax, ey = gy[nm] - ay;
+        double t = ((qx - ax) * ex + (qy - ay) * ey) / (ex * ex + ey * ey);
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+        const double dx = ax + t * ex - qx, dy = ay + t * ey - qy;
+        const double d2 = dx * dx + dy * dy;
+        if (d2 < best) { best = d2; fb = (1.0 - t) * fmag[m] + t * fmag[nm]; }
     }
+    const double F = fb * dH / h;
+    if (dir == 0) Fx[(long)j * (nx + 1) + i] = F;
+    else Fy[(long)j * nx + i] = F;
 }
 
 // ------------------------------------------------------------ B-spline
@@ -1178,7 +1244,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     const size_t pair_cap = (size_t)M * 64 + 4096;
     mk.pair_cap = (uint32_t)pair_cap;
     size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
-                   al((size_t)M * 24 * 8) * 2 + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) +
+                   al((size_t)M * 24 * 8) + al((size_t)M * kSegLine * 8) + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) +
                    al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
@@ -1197,7 +1263,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.dyr = (double2 *)take(ndrops * 16);
     mk.dyk = (ulonglong2 *)take(ndrops * 16);
     mk.sv = (double *)take((size_t)M * 24 * 8);
-    mk.sl = (double *)take((size_t)M * 24 * 8);
+    mk.sl = (double *)take((size_t)M * kSegLine * 8);
     mk.slf = (float4 *)take((size_t)M * 8 * 16);
     mk.sb5 = (float4 *)take((size_t)M * 5 * 16);
     mk.scvx = (uint8_t *)take(M);
@@ -1249,7 +1315,8 @@ void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
                                             mk.x0, mk.y0, mk.h, mk.kappa, mk.nxm, mk.nym, mk.ds,
                                             mk.fmag, mk.gx, mk.gy, mk.gxf, mk.gyf, mk.ykey);
     note_launch();
-    k_segments<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox,
+    k_segments<<<cdiv(mk.M, 32), 32, 0, s>>>(  // FP64-heavy: spread over all SMs
+        mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox,
                                             mk.sv, mk.sb5, mk.sl, mk.slf, mk.scvx);
     note_launch();
     k_drop_yrange<<<cdiv((long)mk.ndrops * 32, kT), kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.Y,
@@ -1314,6 +1381,15 @@ int band_area_grid()
     return 8 * sms;
 }
 
+// Strip areas of the current band pair list (idempotent: pacc, pcov only).
+void launch_band_area(const Markers &mk, cudaStream_t s)
+{
+    note_launch();
+    k_band_area<<<band_area_grid(), 256, 0, s>>>(mk.nx, mk.npairs, mk.pair_cap, mk.pseg, mk.pcell,
+                                                 mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5, mk.pacc,
+                                                 mk.pcov);
+}
+
 void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
 {
     note_launch();
@@ -1322,13 +1398,10 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
     dim3 g(mk.bnx, mk.bny);
     cudaMemsetAsync(mk.npairs, 0, sizeof(uint32_t), s);
     note_launch();
-    k_band_pairs<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids, mk.slf,
+    k_band_pairs<<<g, kPairT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids, mk.slf,
                                    mk.scvx, mk.sbox, mk.pair_cap, mk.npairs, mk.pseg, mk.pcell,
                                    mk.crange, mk.flags);
-    note_launch();
-    k_band_area<<<band_area_grid(), 256, 0, s>>>(mk.nx, mk.npairs, mk.pair_cap, mk.pseg, mk.pcell,
-                                                 mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5, mk.pacc,
-                                                 mk.pcov);
+    launch_band_area(mk, s);
     note_launch();
     k_band_sum<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.crange, mk.pacc, mk.pcov, H);
 }
@@ -1340,7 +1413,7 @@ void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
     cudaMemsetAsync(Fy, 0, (size_t)mk.nx * (mk.ny + 1) * 8, s);
     dim3 g(mk.bnx, mk.bny);
     note_launch();
-    k_spread_irrot<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.bnx, mk.bactive, mk.cell_start,
+    k_spread_irrot<<<g, kIrrT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.bnx, mk.bactive, mk.cell_start,
                                      mk.ids, mk.next, mk.gx, mk.gy, mk.gxf, mk.gyf, fmag, H, Fx,
                                      Fy, mk.flags);
 }

@@ -9,13 +9,22 @@
 // by Gauss-Jordan elimination in FP64).
 //
 // GB300 mapping:
-//  * one red+black sweep = one launch: a 64x16 tile of p (+2-cell halo) is
-//    staged in shared memory, red cells of the tile and its 1-cell ring are
-//    updated there, then the black cells of the tile, and the tile is stored;
-//    HBM traffic is one read of p, b, beta_x, beta_y, 1/diag and one write of
-//    p per sweep (40 B/cell in FP64 plus the 1/diag stream).
-//  * levels with <= 1024 cells run as one single-CTA kernel (the whole lower
-//    V-cycle and the coarsest solve), since launches dominate there.
+//  * sweeps are tiled (FP64: one red+black sweep per launch on a 64x16 tile
+//    with a 2-cell halo; FP32: two sweeps per launch on shrinking rings of a
+//    4-cell halo) and out of place: a launch reads the iterate from one buffer
+//    and writes its tiles to the other, since blocks read their neighbours'
+//    tiles as halo.  HBM traffic is one read of p, b, beta_x, beta_y, 1/diag
+//    and one write of p per launch (40 B/cell FP64 per sweep, 20 B/cell FP32
+//    per two sweeps, plus the 1/diag stream).
+//  * the FP32 cycle fuses the residual and restriction into the pre-smoothing
+//    launch and the prolongation into the post-smoothing launch, so a level
+//    costs two launches.
+//  * kernels of the cycle use programmatic dependent launch: the next grid is
+//    scheduled while the previous one drains and waits (griddepcontrol) for
+//    its results.
+//  * levels with <= 1024 cells (FP64) / <= 4096 cells (FP32) run as one
+//    single-CTA kernel (the whole lower V-cycle and the coarsest solve) with
+//    its data in shared memory, since launches dominate there.
 //  * norms are deterministic two-stage reductions (fixed per-thread order,
 //    fixed tree, last-block fold) with no floating-point atomics.
 //  * the FP32 instantiations of the same kernels form the inner cycle of the
@@ -34,19 +43,49 @@ namespace {
 constexpr int TW = 64, TH = 16, TT = 256;
 constexpr int kRedT = 256;
 
+// Programmatic dependent launch: kernels of the V-cycle are launched with
+// programmatic stream serialisation, so the next grid is scheduled while the
+// previous one drains.  Each such kernel first waits until the grid before
+// it has completed and its writes are visible (griddepcontrol.wait), then
+// lets the next grid launch (griddepcontrol.launch_dependents); nothing is
+// read or written before the wait.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // ------------------------------------------------------------------ sweeps
 template <typename T>
 __global__ void __launch_bounds__(TT)
 k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict__ by,
-             const T *__restrict__ invd, const T *__restrict__ b, T *__restrict__ p)
+             const T *__restrict__ invd, const T *__restrict__ b, const T *__restrict__ pin,
+             T *__restrict__ p)
 {
+    pdl_enter();
     __shared__ T ps[TH + 4][TW + 4];
     const int gi0 = blockIdx.x * TW - 2, gj0 = blockIdx.y * TH - 2;
     const long nxf = nx + 1;
     for (int k = threadIdx.x; k < (TH + 4) * (TW + 4); k += TT) {
         int r = k / (TW + 4), c = k - r * (TW + 4);
         int gi = gi0 + c, gj = gj0 + r;
-        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? p[(long)gj * nx + gi] : T(0);
+        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? pin[(long)gj * nx + gi] : T(0);
     }
     __syncthreads();
     // red cells ((i+j) even) of the tile and its one-cell ring
@@ -93,11 +132,6 @@ k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict
     }
 }
 
-// Two red-black sweeps in one launch (FP32 inner cycle): the tile of p with a
-// 4-cell halo and b, beta_x, beta_y, 1/diag with a 3-cell halo are staged in
-// shared memory by asynchronous copies, all issued before the first wait; the sweeps then run from
-// shared memory on shrinking rings (red on ring 3, black on ring 2, red on
-// ring 1, black on the tile) so the tile's result equals two global sweeps.
 constexpr int FW = 64, FH = 16, FT = 256;
 
 // Asynchronous global -> shared copies (both addresses aligned to the size);
@@ -112,31 +146,61 @@ __device__ __forceinline__ void cp_async4(void *d, const void *src, bool v)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)),
                  "l"(src), "r"(v ? 4 : 0));
 }
+
+// Two red-black sweeps in one launch (FP32 inner cycle), staged in shared
+// memory by asynchronous copies issued before the first wait; the sweeps run
+// from shared memory on shrinking rings (red, black, red, black) so that the
+// tile's result equals two global sweeps.  MODE 0: the sweeps alone (halo 4).
+// MODE 1: the sweeps, then the residual b - A p of the tile's cells averaged
+// over 2x2 children into the coarse right-hand side (coarse correction set
+// to zero); the last black phase also covers the tile's one-cell ring so
+// that the residual sees final neighbours (halo 5).  MODE 2: p + P e_c (the
+// bilinear prolongation of the coarse correction) is formed while staging,
+// then the sweeps (halo 4).  Each mode equals the separate kernels in turn.
+// The iterate is read from pin and the tile written to p (a different
+// buffer): blocks read their neighbours' tiles as halo, so an in-place update
+// would let a block see values another block has already smoothed.
+template <int MODE>
 __global__ void __launch_bounds__(FT)
-k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float *__restrict__ by,
-            const float *__restrict__ invd, const float *__restrict__ b, float *__restrict__ p)
+k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
+              const float *__restrict__ by, const float *__restrict__ invd,
+              const float *__restrict__ b, const float *__restrict__ pin, float *__restrict__ p,
+              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp)
 {
-    // every array staged on the same haloed window: rows gj0 .. gj0 + PH - 1,
-    // columns gi0 .. gi0 + PW - 1 (halo 4), y-faces one row more, x-faces one
-    // column more; rows of cell and y-face arrays are read as float4 when the
-    // window start is 16-byte aligned (nx % 4 == 0), the rest element-wise.
-    constexpr int PW = FW + 8, PH = FH + 8;
+    pdl_enter();
+    constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
+    constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
+    constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA;
     __shared__ __align__(16) float ps[PH][PW];
     __shared__ __align__(16) float bs[PH][PW];
     __shared__ __align__(16) float ds[PH][PW];
     __shared__ __align__(16) float ys[PH + 1][PW];
     __shared__ float xs[PH][PW + 1];
-    const int gi0 = blockIdx.x * FW - 4, gj0 = blockIdx.y * FH - 4;
+    const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
     const long nxf = nx + 1;
+    const int nxc = nx / 2, nyc = ny / 2;
+    // p + P e_c at fine cell (gi, gj) (MODE 2)
+    auto pro = [&](int gi, int gj) {
+        const int I = gi >> 1, J = gj >> 1;
+        const int I2 = min(max(I + ((gi & 1) ? 1 : -1), 0), nxc - 1);
+        const int J2 = min(max(J + ((gj & 1) ? 1 : -1), 0), nyc - 1);
+        const float c00 = ecp[(long)J * nxc + I], c10 = ecp[(long)J * nxc + I2];
+        const float c01 = ecp[(long)J2 * nxc + I], c11 = ecp[(long)J2 * nxc + I2];
+        return pin[(long)gj * nx + gi] + (9.0f * c00 + 3.0f * c10 + 3.0f * c01 + c11) * 0.0625f;
+    };
     const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
-    if (vec) {  // 16-byte asynchronous copies, all in flight before the wait
+    if (vec) {
         constexpr int V = PW / 4;  // float4 per row
         for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
             const int r = k / V, c4 = k - r * V, gj = gj0 + r;
             const long o = (long)gj * nx + gi0 + 4 * c4;
             if (r < PH) {
                 const bool in = gj >= 0 && gj < ny;
-                cp_async16(&ps[r][4 * c4], in ? p + o : p, in);
+                if (MODE == 2) {
+                    for (int q = 0; q < 4; q++) ps[r][4 * c4 + q] = in ? pro(gi0 + 4 * c4 + q, gj) : 0.0f;
+                } else {
+                    cp_async16(&ps[r][4 * c4], in ? pin + o : pin, in);
+                }
                 cp_async16(&bs[r][4 * c4], in ? b + o : b, in);
                 cp_async16(&ds[r][4 * c4], in ? invd + o : invd, in);
             }
@@ -149,7 +213,7 @@ k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float 
             const long o = (long)gj * nx + gi;
             if (r < PH) {
                 const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-                ps[r][c] = in ? p[o] : 0.0f;
+                ps[r][c] = in ? (MODE == 2 ? pro(gi, gj) : pin[o]) : 0.0f;
                 bs[r][c] = in ? b[o] : 0.0f;
                 ds[r][c] = in ? invd[o] : 0.0f;
             }
@@ -163,15 +227,16 @@ k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float 
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
-    // ring q: local rows/cols [4-q, 4+F+q); colour: 0 red, 1 black
+    // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q)
+    constexpr int Q0 = HA - 1;  // outermost ring updated
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
-        const int q = 3 - ph, color = ph & 1;
+        const int q = Q0 - ph, color = ph & 1;
         const int w = FW + 2 * q, hgt = FH + 2 * q, hw = w / 2;
         for (int k = threadIdx.x; k < hgt * hw; k += FT) {
             const int rr = k / hw, cc = k - rr * hw;
-            const int r = 4 - q + rr, gj = gj0 + r;
-            const int c = 4 - q + 2 * cc + ((gi0 + 4 - q + gj + color) & 1);
+            const int r = HA - q + rr, gj = gj0 + r;
+            const int c = XO - q + 2 * cc + ((gi0 + XO - q + gj + color) & 1);
             const int gi = gi0 + c;
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
             float sm = xs[r][c + 1] * ps[r][c + 1];
@@ -182,8 +247,30 @@ k_rbgs2_f32(int nx, int ny, float h2, const float *__restrict__ bx, const float 
         }
         __syncthreads();
     }
+    if (MODE == 1) {
+        // one coarse cell per thread: FW/2 x FH/2 = 32 x 8
+        const int I = blockIdx.x * (FW / 2) + (threadIdx.x % (FW / 2));
+        const int J = blockIdx.y * (FH / 2) + (threadIdx.x / (FW / 2));
+        if (I < nxc && J < nyc) {
+            auto res = [&](int gi, int gj) {
+                const int r = gj - gj0, c = gi - gi0;
+                const float cc = ps[r][c];
+                const float pE = gi + 1 < nx ? ps[r][c + 1] : cc, pW = gi > 0 ? ps[r][c - 1] : cc;
+                const float pN = gj + 1 < ny ? ps[r + 1][c] : cc, pS = gj > 0 ? ps[r - 1][c] : cc;
+                float s = xs[r][c + 1] * (pE - cc);
+                s -= xs[r][c] * (cc - pW);
+                s += ys[r + 1][c] * (pN - cc);
+                s -= ys[r][c] * (cc - pS);
+                return bs[r][c] - s * ih2;
+            };
+            const int i = 2 * I, j = 2 * J;
+            const float r00 = res(i, j), r10 = res(i + 1, j), r01 = res(i, j + 1), r11 = res(i + 1, j + 1);
+            rc[(long)J * nxc + I] = 0.25f * (r00 + r10 + r01 + r11);
+            ecz[(long)J * nxc + I] = 0.0f;
+        }
+    }
     for (int k = threadIdx.x; k < FH * FW; k += FT) {
-        const int r = 4 + k / FW, c = 4 + (k - (k / FW) * FW);
+        const int r = HA + k / FW, c = XO + (k - (k / FW) * FW);
         const int gi = gi0 + c, gj = gj0 + r;
         if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
     }
@@ -213,6 +300,7 @@ __global__ void k_restrict_residual(int nx, int ny, T ih2, const T *__restrict__
                                     const T *__restrict__ p, T *__restrict__ rc,
                                     T *__restrict__ ec)
 {
+    pdl_enter();
     int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
     int nxc = nx / 2;
     if (I >= nxc) return;
@@ -229,6 +317,7 @@ __global__ void k_restrict_residual(int nx, int ny, T ih2, const T *__restrict__
 template <typename T>
 __global__ void k_prolong_add(int nxc, int nyc, const T *__restrict__ ec, T *__restrict__ ef)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     int nx = 2 * nxc;
     if (i >= nx) return;
@@ -415,33 +504,60 @@ __host__ __device__ size_t tail_smem_elems(const TailArgs<T> &a)
     return n;
 }
 
+// One element (4 or 8 bytes) global -> shared by an asynchronous copy.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *d, const T *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(d)),
+                 "l"(src), "n"(sizeof(T)));
+}
+
+// Copy n elements global -> shared: 16-byte copies while both addresses are
+// 16-byte aligned (the element count rounded down to whole 16-byte chunks),
+// single elements for the rest.
+template <typename T>
+__device__ __forceinline__ void stage_array(T *d, const T *src, int n, int tid, int nthr)
+{
+    constexpr int V = 16 / sizeof(T);
+    int done = 0;
+    if ((((uintptr_t)d | (uintptr_t)src) & 15) == 0) {
+        const int nv = n / V;
+        for (int k = tid; k < nv; k += nthr)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+                         ::"r"((unsigned)__cvta_generic_to_shared(d + V * k)), "l"(src + V * k));
+        done = nv * V;
+    }
+    for (int k = done + tid; k < n; k += nthr) cp_async_elem(d + k, src + k);
+}
+
 // Shared-memory view of the tail levels (one copy per block).
 template <typename T>
 struct TailView {
     T *e[kMaxLv], *r[kMaxLv], *bx[kMaxLv], *by[kMaxLv], *iv[kMaxLv];
 };
 
-// Work of one level by a group of `nt` threads (thread index t): the whole
-// block, or one warp for the small levels, where block barriers would cost
-// more than the work.
-template <typename T, bool WARP>
-__device__ __forceinline__ void tsync()
+// Work of one level by a group of NT threads (thread index t): the whole
+// block (NT = 1024), warps 0-3 (128, named barrier 1) or warp 0 (32), chosen
+// by the level's size so that barriers are not wider than the work.
+template <int NT>
+__device__ __forceinline__ void gsync()
 {
-    if (WARP) __syncwarp(); else __syncthreads();
+    if constexpr (NT == 1024) __syncthreads();
+    else if constexpr (NT == 128) asm volatile("bar.sync 1, 128;\n" ::: "memory");
+    else __syncwarp();
 }
 
-template <typename T, bool WARP>
-__device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, int nsw, int t, int nt)
+template <typename T, int NT>
+__device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, int nsw, int t)
 {
-    const int nx = g.nx[l], ny = g.ny[l], n = nx * ny;
+    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, nh = hx * ny;  // nx even: nx / 2 per colour and row
     const T *bx = v.bx[l], *by = v.by[l], *invd = v.iv[l], *r = v.r[l];
     T *e = v.e[l];
     const T h2 = g.h2[l];
     for (int s = 0; s < nsw; s++)
         for (int color = 0; color < 2; color++) {
-            for (int k = t; k < n; k += nt) {
-                const int j = k / nx, i = k - j * nx;
-                if (((i + j) & 1) != color) continue;
+            for (int q = t; q < nh; q += NT) {
+                const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1), k = j * nx + i;
                 const int kx = j * (nx + 1) + i;
                 const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
                 const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
@@ -451,17 +567,17 @@ __device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, i
                 sm = fma(by[k], pS, sm);
                 e[k] = (sm - h2 * r[k]) * invd[k];
             }
-            tsync<T, WARP>();
+            gsync<NT>();
         }
 }
 
-template <typename T, bool WARP>
-__device__ void tail_restrict(const TailArgs<T> &g, const TailView<T> &v, int l, int t, int nt)
+template <typename T, int NT>
+__device__ void tail_restrict(const TailArgs<T> &g, const TailView<T> &v, int l, int t)
 {
     const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nc = nxc * (ny / 2);
     const T *bx = v.bx[l], *by = v.by[l], *b = v.r[l], *p = v.e[l];
     const T ih2 = g.ih2[l];
-    for (int k = t; k < nc; k += nt) {
+    for (int k = t; k < nc; k += NT) {
         const int J = k / nxc, I = k - J * nxc, i = 2 * I, j = 2 * J;
         T r00 = b[j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
         T r10 = b[j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * ih2;
@@ -470,16 +586,16 @@ __device__ void tail_restrict(const TailArgs<T> &g, const TailView<T> &v, int l,
         v.r[l + 1][k] = T(0.25) * (r00 + r10 + r01 + r11);
         v.e[l + 1][k] = T(0);
     }
-    tsync<T, WARP>();
+    gsync<NT>();
 }
 
-template <typename T, bool WARP>
-__device__ void tail_prolong(const TailArgs<T> &g, const TailView<T> &v, int l, int t, int nt)
+template <typename T, int NT>
+__device__ void tail_prolong(const TailArgs<T> &g, const TailView<T> &v, int l, int t)
 {
     const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nyc = ny / 2;
     const T *ec = v.e[l + 1];
     T *ef = v.e[l];
-    for (int k = t; k < nx * ny; k += nt) {
+    for (int k = t; k < nx * ny; k += NT) {
         const int j = k / nx, i = k - j * nx;
         const int I = i >> 1, J = j >> 1;
         const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
@@ -488,21 +604,59 @@ __device__ void tail_prolong(const TailArgs<T> &g, const TailView<T> &v, int l, 
         const T c01 = ec[J2 * nxc + I], c11 = ec[J2 * nxc + I2];
         ef[k] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
     }
-    tsync<T, WARP>();
+    gsync<NT>();
 }
 
-// The lower V-cycle (levels lt..L-1, each at most 1024 cells) in one CTA: the
-// coefficients and the level-lt iterate and right-hand side are copied into
-// shared memory, the cycle runs there, and the level-lt iterate is copied
-// back.  Levels of at least 512 cells use the whole block; the smaller ones
-// and the coarsest LU solve run in warp 0 alone with warp barriers.
+template <typename T, int NT>
+__device__ void tail_down(const TailArgs<T> &g, const TailView<T> &v, int l0, int l1, int t)
+{
+    for (int l = l0; l < l1; l++) {
+        tail_smooth<T, NT>(g, v, l, g.nu1, t);
+        tail_restrict<T, NT>(g, v, l, t);
+    }
+}
+
+template <typename T, int NT>
+__device__ void tail_up(const TailArgs<T> &g, const TailView<T> &v, int l0, int l1, int t)
+{
+    for (int l = l1 - 1; l >= l0; l--) {
+        tail_prolong<T, NT>(g, v, l, t);
+        tail_smooth<T, NT>(g, v, l, g.nu2, t);
+    }
+}
+
+// Dynamic shared memory of the tail kernel: the levels' arrays, then the
+// coarsest level's inverse (FP64, 8-byte aligned) when it takes at most
+// 64 KB (else the solve reads it from global memory).
+constexpr size_t kTailInvMax = 64 * 1024;
+__host__ __device__ inline size_t tail_inv_bytes(int nco)
+{
+    const size_t b = (size_t)nco * nco * sizeof(double);
+    return b <= kTailInvMax ? b : 0;
+}
+
+template <typename T>
+__host__ __device__ size_t tail_smem_bytes(const TailArgs<T> &a)
+{
+    const size_t lv = tail_smem_elems(a) * sizeof(T);
+    return ((lv + 7) & ~(size_t)7) + tail_inv_bytes(a.nx[a.nl - 1] * a.ny[a.nl - 1]);
+}
+
+// The lower V-cycle (levels lt..L-1) in one CTA: the coefficients, the
+// level-lt iterate and right-hand side and the coarsest inverse are copied
+// into shared memory, the cycle runs there, and the level-lt iterate is
+// copied back.  Levels of at least 512 cells use the whole block, those of
+// at least 128 cells warps 0-3, the rest and the coarsest solve warp 0.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char tail_sm[];
     __shared__ double xs[kMaxCoarsest];
     __shared__ TailView<T> v;
+    __shared__ double *ainv;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const int L = g.nl, lc = L - 1, nco = g.nx[lc] * g.ny[lc];
     if (tid == 0) {
         T *q = (T *)tail_sm;
         for (int l = g.lt; l < g.nl; l++) {
@@ -510,51 +664,46 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
             v.e[l] = q; v.r[l] = q + c; v.iv[l] = q + 2 * c; v.bx[l] = q + 3 * c; v.by[l] = q + 3 * c + fx;
             q += 3 * c + fx + fy;
         }
+        ainv = tail_inv_bytes(nco) ? (double *)(tail_sm + ((tail_smem_elems(g) * sizeof(T) + 7) & ~(size_t)7))
+                                   : const_cast<double *>(g.ainvT);
     }
     __syncthreads();
+    // stage with asynchronous copies, all in flight before the wait
     for (int l = g.lt; l < g.nl; l++) {
         const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
-        for (int k = tid; k < c; k += nthr) {
-            v.iv[l][k] = g.invd[l][k];
-            if (l == g.lt) { v.e[l][k] = g.e[l][k]; v.r[l][k] = g.r[l][k]; }
+        stage_array(v.iv[l], g.invd[l], c, tid, nthr);
+        if (l == g.lt) { stage_array(v.e[l], g.e[l], c, tid, nthr); stage_array(v.r[l], g.r[l], c, tid, nthr); }
+        stage_array(v.bx[l], g.bx[l], fx, tid, nthr);
+        stage_array(v.by[l], g.by[l], fy, tid, nthr);
+    }
+    if (tail_inv_bytes(nco)) stage_array(ainv, g.ainvT, nco * nco, tid, nthr);
+    asm volatile("cp.async.wait_all;\n" ::);
+    __syncthreads();
+    int lb = g.lt;  // first level of warps 0-3
+    while (lb < lc && g.nx[lb] * g.ny[lb] >= 512) lb++;
+    int lw = lb;    // first level of warp 0
+    while (lw < lc && g.nx[lw] * g.ny[lw] >= 128) lw++;
+    tail_down<T, 1024>(g, v, g.lt, lb, tid);
+    if (tid < 128) {
+        tail_down<T, 128>(g, v, lb, lw, tid);
+        if (tid < 32) {
+            tail_down<T, 32>(g, v, lw, lc, tid);
+            // coarsest: x = A'^{-1} r, one row of the inverse per lane
+            for (int k = tid; k < nco; k += 32) xs[k] = (double)v.r[lc][k];
+            __syncwarp();
+            for (int k = tid; k < nco; k += 32) {
+                double acc = 0.0;
+                for (int q = 0; q < nco; q++) acc += ainv[q * nco + k] * xs[q];
+                v.e[lc][k] = (T)acc;
+            }
+            __syncwarp();
+            tail_up<T, 32>(g, v, lw, lc, tid);
         }
-        for (int k = tid; k < fx; k += nthr) v.bx[l][k] = g.bx[l][k];
-        for (int k = tid; k < fy; k += nthr) v.by[l][k] = g.by[l][k];
+        gsync<128>();
+        tail_up<T, 128>(g, v, lb, lw, tid);
     }
     __syncthreads();
-    const int L = g.nl;
-    int lb = g.lt;  // first level handled by warp 0 alone
-    while (lb < L - 1 && g.nx[lb] * g.ny[lb] >= 512) lb++;
-    for (int l = g.lt; l < lb; l++) {
-        tail_smooth<T, false>(g, v, l, g.nu1, tid, nthr);
-        tail_restrict<T, false>(g, v, l, tid, nthr);
-    }
-    if (tid < 32) {
-        const int lane = tid;
-        for (int l = lb; l < L - 1; l++) {
-            tail_smooth<T, true>(g, v, l, g.nu1, lane, 32);
-            tail_restrict<T, true>(g, v, l, lane, 32);
-        }
-        // coarsest: x = A'^{-1} r, one row of the inverse per lane
-        const int lc = L - 1, n = g.nx[lc] * g.ny[lc];
-        for (int k = lane; k < n; k += 32) xs[k] = (double)v.r[lc][k];
-        __syncwarp();
-        for (int k = lane; k < n; k += 32) {
-            double acc = 0.0;
-            for (int q = 0; q < n; q++) acc += g.ainvT[(long)q * n + k] * xs[q];
-            v.e[lc][k] = (T)acc;
-        }
-        __syncwarp();
-        for (int l = L - 2; l >= lb; l--) {
-            tail_prolong<T, true>(g, v, l, lane, 32);
-            tail_smooth<T, true>(g, v, l, g.nu2, lane, 32);
-        }
-    }
-    __syncthreads();
-    for (int l = lb - 1; l >= g.lt; l--) {
-        tail_prolong<T, false>(g, v, l, tid, nthr);
-        tail_smooth<T, false>(g, v, l, g.nu2, tid, nthr);
-    }
+    tail_up<T, 1024>(g, v, g.lt, lb, tid);
     for (int k = tid; k < g.nx[g.lt] * g.ny[g.lt]; k += nthr) g.e[g.lt][k] = v.e[g.lt][k];
 }
 
@@ -637,6 +786,7 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
           const double *__restrict__ p, float *__restrict__ rf, float *__restrict__ ef,
           double *part, unsigned *count, double *out)
 {
+    pdl_enter();
     double s = 0.0;
     for (int j = blockIdx.x; j < ny; j += gridDim.x)
         for (int i = threadIdx.x; i < nx; i += kRedT) {
@@ -650,6 +800,7 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
 
 __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restrict__ p)
 {
+    pdl_enter();
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) p[k] += (double)e[k];
 }
@@ -658,6 +809,7 @@ __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restric
 // cycle count and relative residual and sets the WHILE condition.
 __global__ void k_check(SolveCtl *ctl, const double *res, cudaGraphConditionalHandle hnd, int first)
 {
+    pdl_enter();
     const double nb = sqrt(res[1]);
     if (first) { ctl->cycles = 0; ctl->zero_p = nb == 0.0 ? 1 : 0; }
     else ctl->cycles += 1;
@@ -674,10 +826,15 @@ __global__ void k_finalize(long n, const double *__restrict__ e0, const double *
     if (k < n) p[k] = ctl->zero_p ? 0.0 : e0[k] - *sum / (double)n;
 }
 
-// nsw sweeps on one level: FP32 in fused pairs, FP64 one sweep per launch
-// (the FP64 sweep is bound by the FP64 pipe, where fusing only adds halo work).
+// The other buffer of a level's iterate (sweeps read one and write the other).
 template <typename T>
-void smooth(const Level &v, LevelT<T> &a, int nsw, bool fine, cudaStream_t s)
+T *other(LevelT<T> &a, T *cur) { return cur == a.e ? a.e2 : a.e; }
+
+// nsw sweeps on one level, reading the iterate from cur and leaving it in the
+// returned buffer: FP32 in fused pairs, FP64 one sweep per launch (the FP64
+// sweep is bound by the FP64 pipe, where fusing only adds halo work).
+template <typename T>
+T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t s)
 {
     const T h2 = (T)(v.h * v.h);
     int k = 0;
@@ -687,7 +844,11 @@ void smooth(const Level &v, LevelT<T> &a, int nsw, bool fine, cudaStream_t s)
             const bool pr = fine && prof_on(kProfSweep32);
             if (pr) prof_mark(s, true);
             note_launch();
-            k_rbgs2_f32<<<g2, FT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+            T *nxt = other(a, cur);
+            launch_pdl(k_smooth2_f32<0>, g2, FT, 0, s, v.nx, v.ny, h2, 0.0f, a.bx, a.by, a.invd, a.r,
+                       (const float *)cur, nxt, (float *)nullptr, (float *)nullptr,
+                       (const float *)nullptr);
+            cur = nxt;
             if (pr) prof_mark(s, false);
         }
     }
@@ -696,28 +857,56 @@ void smooth(const Level &v, LevelT<T> &a, int nsw, bool fine, cudaStream_t s)
         const bool pr = fine && sizeof(T) == 8 && prof_on(kProfSweep64);
         if (pr) prof_mark(s, true);
         note_launch();
-        k_rbgs_sweep<T><<<g, TT, 0, s>>>(v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r, a.e);
+        T *nxt = other(a, cur);
+        launch_pdl(k_rbgs_sweep<T>, g, TT, 0, s, v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r,
+                   (const T *)cur, nxt);
+        cur = nxt;
         if (pr) prof_mark(s, false);
     }
+    return cur;
 }
 
+// One V(nu1, nu2) cycle on the level-0 data of precision T.  Every level's
+// iterate moves between its two buffers (cur[l]); the coarse corrections
+// start in the canonical buffer, which the restriction zeroes, and level 0
+// ends in its canonical buffer (copied back when the sweep count is odd).
+// FP32 cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
+// restriction going down, prolongation + sweeps going up).
 template <typename T>
 void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
 {
     auto lvT = [&](int l) -> LevelT<T> & {
         if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
     };
-    const int L = mg.L, lt = mg.tail;
+    const int L = mg.L, lt = sizeof(T) == 8 ? mg.tail : mg.tail_f;
+    constexpr bool f32 = sizeof(T) == 4;
+    const bool fused = f32 && nu1 == 2 && nu2 == 2;
+    T *cur[kMaxLv];
+    for (int l = 0; l < L; l++) cur[l] = lvT(l).e;
     for (int l = 0; l < lt; l++) {
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l), &c = lvT(l + 1);
-        dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
-        T h2 = (T)(v.h * v.h);
-        smooth<T>(v, a, nu1, l == 0, s);
-        dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
-        note_launch();
-        k_restrict_residual<T><<<gr, 128, 0, s>>>(v.nx, v.ny, (T)(1.0 / (v.h * v.h)), a.bx,
-                                                  a.by, a.r, a.e, c.r, c.e);
+        if (fused) {
+            if constexpr (f32) {
+                dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
+                const bool pr = l == 0 && prof_on(kProfSweep32);
+                if (pr) prof_mark(s, true);
+                note_launch();
+                T *nxt = other(a, cur[l]);
+                launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
+                           (float)(1.0 / (v.h * v.h)), a.bx, a.by, a.invd, a.r,
+                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr);
+                if (pr) prof_mark(s, false);
+                cur[l] = nxt;
+            }
+        } else {
+            cur[l] = smooth<T>(v, a, cur[l], nu1, l == 0, s);
+            dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
+            note_launch();
+            launch_pdl(k_restrict_residual<T>, gr, 128, 0, s, v.nx, v.ny, (T)(1.0 / (v.h * v.h)),
+                       a.bx, a.by, a.r, (const T *)cur[l], c.r, c.e);
+        }
+        cur[l + 1] = c.e;
     }
     TailArgs<T> ta;
     ta.lt = lt;
@@ -729,22 +918,40 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
         ta.h2[l] = (T)(v.h * v.h); ta.ih2[l] = (T)(1.0 / (v.h * v.h));
         ta.e[l] = a.e; ta.r[l] = a.r; ta.bx[l] = a.bx; ta.by[l] = a.by; ta.invd[l] = a.invd;
     }
+    ta.e[lt] = cur[lt];
     ta.ainvT = mg.lu + (size_t)mg.lv[mg.L - 1].nx * mg.lv[mg.L - 1].ny * mg.lv[mg.L - 1].nx * mg.lv[mg.L - 1].ny;
     ta.nu1 = nu1;
     ta.nu2 = nu2;
     note_launch();
-    const size_t smem = tail_smem_elems(ta) * sizeof(T);
-    k_tail<T><<<1, 1024, smem, s>>>(ta);
+    const size_t smem = tail_smem_bytes(ta);
+    launch_pdl(k_tail<T>, 1, 1024, smem, s, ta);
     for (int l = lt - 1; l >= 0; l--) {
         Level &v = mg.lv[l];
-        LevelT<T> &a = lvT(l), &c = lvT(l + 1);
-        dim3 gp(cdiv(v.nx, 128), v.ny);
-        note_launch();
-        k_prolong_add<T><<<gp, 128, 0, s>>>(v.nx / 2, v.ny / 2, c.e, a.e);
-        dim3 g(cdiv(v.nx, TW), cdiv(v.ny, TH));
-        T h2 = (T)(v.h * v.h);
-        smooth<T>(v, a, nu2, l == 0, s);
+        LevelT<T> &a = lvT(l);
+        if (fused) {
+            if constexpr (f32) {
+                dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
+                const bool pr = l == 0 && prof_on(kProfSweep32);
+                if (pr) prof_mark(s, true);
+                note_launch();
+                T *nxt = other(a, cur[l]);
+                launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f,
+                           a.bx, a.by, a.invd, a.r, (const float *)cur[l], nxt, (float *)nullptr,
+                           (float *)nullptr, (const float *)cur[l + 1]);
+                if (pr) prof_mark(s, false);
+                cur[l] = nxt;
+            }
+        } else {
+            dim3 gp(cdiv(v.nx, 128), v.ny);
+            note_launch();
+            launch_pdl(k_prolong_add<T>, gp, 128, 0, s, v.nx / 2, v.ny / 2, (const T *)cur[l + 1],
+                       cur[l]);
+            cur[l] = smooth<T>(v, a, cur[l], nu2, l == 0, s);
+        }
     }
+    if (cur[0] != lvT(0).e)
+        cudaMemcpyAsync(lvT(0).e, cur[0], (size_t)mg.lv[0].nx * mg.lv[0].ny * sizeof(T),
+                        cudaMemcpyDeviceToDevice, s);
 }
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -842,9 +1049,11 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         Level &v = mg.lv[l];
         v.nx = nxs[l]; v.ny = nys[l]; v.h = h * (double)(1 << l);
         size_t n = (size_t)v.nx * v.ny, fx = (size_t)(v.nx + 1) * v.ny, fy = (size_t)v.nx * (v.ny + 1);
-        v.d.e = (double *)take(n * 8); v.d.r = (double *)take(n * 8); v.d.invd = (double *)take(n * 8);
+        v.d.e = (double *)take(n * 8); v.d.e2 = (double *)take(n * 8);
+        v.d.r = (double *)take(n * 8); v.d.invd = (double *)take(n * 8);
         v.d.bx = (double *)take(fx * 8); v.d.by = (double *)take(fy * 8);
-        v.f.e = (float *)take(n * 4); v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
+        v.f.e = (float *)take(n * 4); v.f.e2 = (float *)take(n * 4);
+        v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
         v.f.bx = (float *)take(fx * 4); v.f.by = (float *)take(fy * 4);
     }
     mg.lu = (double *)take((size_t)nc * nc * 8 * 2);  // A' and its transposed inverse
@@ -855,6 +1064,9 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
     int t = 0;
     while (t < L && (long)nxs[t] * nys[t] > kTailCells) t++;
     mg.tail = std::min(t, L - 1);
+    t = 0;
+    while (t < L && (long)nxs[t] * nys[t] > kTailCellsF32) t++;
+    mg.tail_f = std::min(t, L - 1);
     return off;
 }
 
@@ -890,6 +1102,12 @@ void mg_free(MG &mg)
     mg.L = 0;
 }
 
+void mg_fine_smoother(MG &mg, int precision, cudaStream_t s)
+{
+    if (precision) smooth<float>(mg.lv[0], mg.lv[0].f, mg.lv[0].f.e, 2, false, s);
+    else smooth<double>(mg.lv[0], mg.lv[0].d, mg.lv[0].d.e, 1, false, s);
+}
+
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 {
     const int L = mg.L;
@@ -904,12 +1122,20 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     {
         // shared memory of the single-CTA tail (set here, outside any capture)
         size_t e = 0;
+        size_t ef = 0;
         for (int l = mg.tail; l < L; l++) {
             size_t c = (size_t)mg.lv[l].nx * mg.lv[l].ny;
             e += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
         }
-        cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(e * 8));
-        cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(e * 4));
+        for (int l = mg.tail_f; l < L; l++) {
+            size_t c = (size_t)mg.lv[l].nx * mg.lv[l].ny;
+            ef += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
+        }
+        const size_t inv = tail_inv_bytes(mg.lv[L - 1].nx * mg.lv[L - 1].ny);
+        cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((e * 8 + 7) & ~(size_t)7) + inv));
+        cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((ef * 4 + 7) & ~(size_t)7) + inv));
     }
     Level &vc = mg.lv[L - 1];
     note_launch();
@@ -1012,10 +1238,9 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
     k_sub_mean<<<RB, kRedT, 0, c>>>(n, sg.rhs, res + 0, b0, part, mg.red_count, res + 1);
     auto resnorm = [&](cudaStream_t st) {
         note_launch();
-        k_resnorm<<<RB, kRedT, 0, st>>>(v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
-                                        sg.precision ? v0.f.r : nullptr,
-                                        sg.precision ? v0.f.e : nullptr, part, mg.red_count,
-                                        res + 2);
+        launch_pdl(k_resnorm, RB, kRedT, 0, st, v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
+                   sg.precision ? v0.f.r : nullptr, sg.precision ? v0.f.e : nullptr, part,
+                   mg.red_count, res + 2);
     };
     resnorm(c);
     cudaStreamCaptureStatus cs;
@@ -1053,11 +1278,11 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
             } else {
                 vcycle<float>(mg, sg.nu1, sg.nu2, cb);
                 note_launch();
-                k_add_f32<<<cdiv(n, 256), 256, 0, cb>>>(n, v0.f.e, e0);
+                launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
             }
             resnorm(cb);
             note_launch();
-            k_check<<<1, 1, 0, cb>>>(mg.ctl, res, hnd, 0);
+            launch_pdl(k_check, 1, 1, 0, cb, mg.ctl, res, hnd, 0);
             e = cudaStreamEndCapture(cb, &body);
         }
         kb1 = launch_count();
@@ -1130,11 +1355,12 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
 
 // Context-free launches used by the verification entry points.
 void launch_rbgs(int nx, int ny, double h, const double *bx, const double *by,
-                 const double *invd, const double *b, double *p, cudaStream_t s)
+                 const double *invd, const double *b, const double *pin, double *p,
+                 cudaStream_t s)
 {
     dim3 g(cdiv(nx, TW), cdiv(ny, TH));
     note_launch();
-    k_rbgs_sweep<double><<<g, TT, 0, s>>>(nx, ny, h * h, bx, by, invd, b, p);
+    k_rbgs_sweep<double><<<g, TT, 0, s>>>(nx, ny, h * h, bx, by, invd, b, pin, p);
 }
 
 void launch_invdiag(int nx, int ny, const double *bx, const double *by,

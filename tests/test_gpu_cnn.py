@@ -88,6 +88,43 @@ def test_forward_matches_oracle(T):
     assert err < 3e-2, err
 
 
+def prolong2(c):
+    """Cell-centred bilinear (9, 3, 3, 1)/16 interpolation to twice the
+    resolution, zero gradient at the walls (written out per fine cell)."""
+    B, n, _ = c.shape
+    f = np.empty((B, 2 * n, 2 * n))
+    for j in range(2 * n):
+        for i in range(2 * n):
+            I, J = i // 2, j // 2
+            I2 = min(max(I + (1 if i % 2 else -1), 0), n - 1)
+            J2 = min(max(J + (1 if j % 2 else -1), 0), n - 1)
+            f[:, j, i] = (9 * c[:, J, I] + 3 * c[:, J, I2] + 3 * c[:, J2, I] + c[:, J2, I2]) / 16
+    return f
+
+
+def test_coarse_grid_inference_matches_oracle(T):
+    import paper_1807_10504_gb300 as ib
+    B, N = 2, 64
+    P = OC.init_params(seed=2)
+    for n, _, co, _ in OC.LAYERS:
+        P[n + ".b"] = np.random.default_rng(len(n) + 7).standard_normal(co) * 0.05
+    Pq = {k: (bf16(v) if k.endswith(".w") else v.astype(np.float32).astype(np.float64)) for k, v in P.items()}
+    net = ib.Net(seed=0)
+    net.set_params(flat_of(P))
+    net.set_coarsen(1)
+    rhs, rho, p = batch(B, N, 5)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    p0 = net.infer(d(rhs), d(rho)).cpu().numpy()
+    mean2 = lambda a: a.reshape(B, N // 2, 2, N // 2, 2).mean(axis=(2, 4))
+    x, s, _ = oracle_inputs(mean2(rhs), mean2(rho), p[:, ::2, ::2])
+    y = OC.forward(Pq, x)[..., 0]
+    ref = prolong2(s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True)))
+    err = np.linalg.norm(p0 - ref) / np.linalg.norm(ref)
+    assert err < 3e-2, err
+    with pytest.raises(ib.IBError):  # 2^1 * 4 does not divide 36
+        net.infer(d(rhs[:, :36, :36]), d(rho[:, :36, :36]))
+
+
 def test_gradients_match_oracle(T):
     import paper_1807_10504_gb300 as ib
     B, N = 2, 32
@@ -146,6 +183,9 @@ def test_warm_start_reaches_the_same_tolerance(T):
     net = ib.Net(seed=5)
     ctx.attach(net)
     dt = W.capillary_dt(cfg.h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    cyc, rr = ctx.ns_step(dt, 1, 2)
+    assert rr <= 1e-10
+    net.set_coarsen(2)
     cyc, rr = ctx.ns_step(dt, 1, 2)
     assert rr <= 1e-10
     ctx.attach(None)

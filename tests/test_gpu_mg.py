@@ -160,3 +160,28 @@ def test_full_size_1024_density_ratio_1000(T, ib, O):
         assert abs(pn.mean()) <= 1e-12 * np.abs(pn).max()
         sols.append(pn)
     assert np.abs(sols[0] - sols[1]).max() <= 1e-6 * np.abs(sols[0]).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multiwave_grid_cycle_for_cycle_and_deterministic(T, ib, O, precision):
+    # 1024^2: the smoother grids span more than one wave of thread blocks, so
+    # a block can start after its neighbours have finished; every sweep reads
+    # one buffer and writes the other, so the iterate after k cycles is the
+    # oracle's and repeated solves are bitwise identical.
+    n = 1024
+    h = 1.0 / n
+    rho, mu, bx, by = coeffs(O, n, n, 21)
+    b = W.random_cells(n, n, 22)
+    ctx = ctx_for(ib, n, n)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx.mg_setup(d(bx), d(by))
+    runs = []
+    for _ in range(2):
+        p = T.zeros((n, n), dtype=T.float64, device="cuda")
+        st, cyc, rr = ctx.mg_solve(d(b), p, precision, 0.0, 2, check=False)
+        assert st == ib.IB_ENOTCONV and cyc == 2
+        runs.append(p.cpu().numpy())
+    assert np.array_equal(runs[0], runs[1])
+    o = O.mg_solve(bx, by, b, h, precision=precision, tol=0.0, max_cycles=2)
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert np.abs(runs[0] - o.p).max() <= tol * np.abs(o.p).max()
