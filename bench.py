@@ -33,6 +33,7 @@ import workloads as W  # noqa: E402
 METRIC = ("pressure-solve ms & steps/s, FP64 MG vs mixed/NN-start at equal residual; %HBM")
 WORKLOADS = {
     "multidrop1024": dict(n=1024, kind="multi"),
+    "multidrop512": dict(n=512, kind="multi16"),
     "multidrop2048": dict(n=2048, kind="multi"),
     "oscillating256": dict(n=256, kind="osc"),
     "static64": dict(n=64, kind="static"),
@@ -43,6 +44,8 @@ def make_markers(name, seed_offset=0):
     wl = WORKLOADS[name]
     if wl["kind"] == "multi":
         return W.multidrop(wl["n"], seed=1811 + seed_offset)
+    if wl["kind"] == "multi16":  # a quarter of the 1024^2 case, drops of the same size in cells
+        return W.multidrop(wl["n"], ndrops=16, rmin=0.02, rmax=0.06, seed=1811 + seed_offset)
     if wl["kind"] == "osc":
         return W.oscillating_drop(seed=1808 + seed_offset)
     return W.static_drop(wl["n"], 0.25, 128)
@@ -267,10 +270,28 @@ def run_ours(args):
 
     # kernel durations on this step's data: back-to-back launches between two
     # CUDA events on the context stream (ib_bench_kernel)
-    us32, cells = ctx.bench_kernel(0, 50)
+    us32, cells = ctx.bench_kernel(4, 50)  # the step's top kernel: prolongation + two FP32 sweeps
     us64, _ = ctx.bench_kernel(1, 50)
     usb, pairs = ctx.bench_kernel(2, 10)
-    ach32 = 20.0 * cells / (us32 * 1e-6) / 1e9
+    # per-level durations of the mixed cycle's kernels (same method)
+    levels = []
+    for lev in range(16):
+        try:
+            t_down, c_l = ctx.bench_kernel(3, 20, lev)
+        except ib.IBError:
+            break
+        t_up, _ = ctx.bench_kernel(4, 20, lev)
+        t_s2, _ = ctx.bench_kernel(0, 20, lev)
+        t_64, _ = ctx.bench_kernel(1, 20, lev)
+        levels.append({"level": lev, "cells": int(c_l), "sweeps2_restrict_us": t_down,
+                       "prolong_sweeps2_us": t_up, "sweeps2_us": t_s2, "fp64_sweep_us": t_64})
+    t_tail, c_tail = ctx.bench_kernel(5, 20)
+    t_res, _ = ctx.bench_kernel(6, 20)
+    kernel_table = {"levels": levels, "fp32_tail_us": t_tail, "fp32_tail_first_level_cells": int(c_tail),
+                    "fp64_residual_norm_us": t_res}
+    # algorithmic bytes per fine cell: read p, b, beta_x, beta_y (16) and the
+    # coarse correction (4 B per 4 cells), write p (4)
+    ach32 = 21.0 * cells / (us32 * 1e-6) / 1e9
     ach64 = 40.0 * cells / (us64 * 1e-6) / 1e9
     roof64 = {"kernel": "k_rbgs_sweep<double> (fine level, one red-black sweep)", "bound": "hbm",
               "achieved": ach64, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -346,7 +367,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(2 * ctx.M * 8),
                 "d2h_bytes_per_step": int(n * n * 8 + 2 * ctx.M * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": ("k_rbgs2_f32 (fine level, two fused FP32 red-black sweeps)"
+        "roofline": {"kernel": ("k_smooth2_f32<2> (fine level: prolongation + two FP32 red-black sweeps)"
                                 if args.precision == 1 else
                                 "k_rbgs_sweep<double> (fine level, one red-black sweep)"),
                      "bound": "hbm", "achieved": ach32 if args.precision == 1 else ach64,
@@ -354,13 +375,14 @@ def run_ours(args):
                      "frac": (ach32 if args.precision == 1 else ach64) / pk["hbm_gbs"],
                      "traffic": None, "peak_source": pk_kind,
                      "avg_launch_us": us32 if args.precision == 1 else us64,
-                     "algorithmic_bytes_per_cell": 20.0 if args.precision == 1 else 40.0,
+                     "algorithmic_bytes_per_cell": 21.0 if args.precision == 1 else 40.0,
                      "cells_per_launch": int(cells),
                      "timing": "50 back-to-back launches on the step's fine-level data, "
                                "CUDA events on the launching stream",
                      "in_step_avg_launch_us": avg_sweep * 1e3, "in_step_launches": sweep_n},
         "roofline_fp64_sweep": roof64,
         "band_strip_areas": band,
+        "mixed_cycle_kernels": kernel_table,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, t = cpu_baseline(name, 1)

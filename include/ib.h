@@ -223,13 +223,18 @@ ib_status ib_profile_end(double *total_ms, int *launches);
 /* Kernel timing on the context's current data: `reps` back-to-back launches
  * of one kernel between two CUDA events on the context stream (after one
  * untimed launch); *us_per_launch = their mean duration, *units = the work
- * units of one launch.  which = 0: fine-level FP32 smoother (two fused
- * red-black sweeps; units = cells), 1: fine-level FP64 sweep (cells), 2: band
- * strip areas of the last Heaviside pass (units = (cell, segment) pairs).
- * The smoother launches overwrite the level-0 correction scratch, the
- * strip-area launches recompute the same per-pair values: the context's
- * state is unchanged.  Needs a prior solve (0, 1) / Heaviside pass (2).    */
-ib_status ib_bench_kernel(ib_ctx *ctx, int which, int reps, double *us_per_launch, double *units);
+ * units of one launch.  which (at multigrid level `level`, 0 = finest):
+ * 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps + residual +
+ * restriction, 4 FP32 prolongation + sweeps (units = cells of the level);
+ * 5 the FP32 single-CTA lower cycle (cells of its first level), 6 the FP64
+ * residual norm of the mixed solve (cells); 2 band strip areas of the last
+ * Heaviside pass (units = (cell, segment) pairs; level ignored).  Only solve
+ * scratch is overwritten (second iterate buffers, coarse right-hand sides,
+ * FP32 residual, norm partials) and the strip areas are recomputed: the
+ * context's state is unchanged.  Needs a prior solve (or, for 2, Heaviside
+ * pass); IB_EINVAL if the kernel does not run at that level.              */
+ib_status ib_bench_kernel(ib_ctx *ctx, int which, int level, int reps, double *us_per_launch,
+                          double *units);
 
 /* Checkpoint: every field, the AB2 history, markers and the step counter,
  * written to / read from a binary file at `path` (host I/O, synchronises).

@@ -100,7 +100,7 @@ def lib():
                                _P],
             "cnn_infer": [_P, _i32, _i32, _d, _P, _P, _P, _P],
             "cnn_set_scale": [_P, _d], "cnn_set_coarsen": [_P, _i32],
-            "ib_bench_kernel": [_P, C.c_int, C.c_int, _P, _P],
+            "ib_bench_kernel": [_P, C.c_int, C.c_int, C.c_int, _P, _P],
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
@@ -315,11 +315,12 @@ class Context:
         lib().ib_last_solve(self._h, C.byref(cyc), C.byref(rr))
         return cyc.value, rr.value
 
-    def bench_kernel(self, which: int, reps: int = 50):
+    def bench_kernel(self, which: int, reps: int = 50, level: int = 0):
         """(us per launch, work units per launch) of `reps` back-to-back
         launches of one kernel on the current data (see ib_bench_kernel)."""
         us, units = C.c_double(0.0), C.c_double(0.0)
-        _check(lib().ib_bench_kernel(self._h, which, reps, C.byref(us), C.byref(units)), self._h)
+        _check(lib().ib_bench_kernel(self._h, which, level, reps, C.byref(us), C.byref(units)),
+               self._h)
         return us.value, units.value
 
     def use_graphs(self, enable: bool):

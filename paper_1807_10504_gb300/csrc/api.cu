@@ -424,29 +424,30 @@ ib_status ib_profile_end(double *total_ms, int *launches)
     return prof_end(total_ms, launches) ? IB_OK : IB_ECUDA;
 }
 
-ib_status ib_bench_kernel(ib_ctx *c, int which, int reps, double *us_per_launch, double *units)
+ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_per_launch,
+                          double *units)
 {
-    if (!c || which < 0 || which > 2 || reps < 1 || !us_per_launch) return IB_EINVAL;
-    if (which < 2 && !c->mg_ready) return fail(c, IB_EINVAL, "no multigrid hierarchy yet");
+    if (!c || which < 0 || which > 6 || reps < 1 || !us_per_launch) return IB_EINVAL;
+    if (which != 2 && !c->mg_ready) return fail(c, IB_EINVAL, "no multigrid hierarchy yet");
     double u = 0.0;
-    if (which < 2) {
-        u = (double)c->cfg.nx * c->cfg.ny;
-    } else {
+    if (which == 2) {
         uint32_t np = 0;
         cudaError_t e = cudaMemcpyAsync(&np, c->mk.npairs, 4, cudaMemcpyDeviceToHost, c->s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
         if (e != cudaSuccess) return cuda_check(c, e, "pair count");
         u = (double)std::min(np, c->mk.pair_cap);
     }
+    auto one = [&]() -> bool {
+        if (which == 2) { launch_band_area(c->mk, c->s); return true; }
+        const long cells = mg_bench_op(c->mg, which, level, c->s);
+        if (cells < 0) return false;
+        u = (double)cells;
+        return true;
+    };
+    if (!one()) return fail(c, IB_EINVAL, "no such kernel at this level");  // warm-up
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    auto one = [&]() {
-        if (which == 0) mg_fine_smoother(c->mg, 1, c->s);
-        else if (which == 1) mg_fine_smoother(c->mg, 0, c->s);
-        else launch_band_area(c->mk, c->s);
-    };
-    one();  // warm-up
     cudaEventRecord(e0, c->s);
     for (int r = 0; r < reps; r++) one();
     cudaEventRecord(e1, c->s);

@@ -106,9 +106,8 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys);
 size_t mg_layout(MG &mg, int nx, int ny, double h, char *base);
 cudaError_t mg_alloc(MG &mg, int nx, int ny, double h);
 void mg_free(MG &mg);
-// One fine-level smoother launch on the current hierarchy data (precision 1:
-// two fused FP32 sweeps, 0: one FP64 sweep), for kernel timing.
-void mg_fine_smoother(MG &mg, int precision, cudaStream_t s);
+// One launch of one cycle kernel on the hierarchy's current data, for timing.
+long mg_bench_op(MG &mg, int op, int level, cudaStream_t s);
 // Copy level-0 coefficients (walls forced to 0) and build the hierarchy.
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s);
 // Runs the solve on level-0 arrays of the hierarchy; p is read/written in place.

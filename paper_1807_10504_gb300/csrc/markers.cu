@@ -739,49 +739,107 @@ __device__ __forceinline__ void narrow(double alpha, double beta, double rbeta, 
     else if (alpha < 0.0) hi = -INFINITY;
 }
 
-// Area of the unit square cut by the half-planes L[0..n-1] (n = 2 or 3), by
-// Green's theorem: area = 1/2 of the boundary integral of x dy - y dx.  On the
-// square's bottom and left edges the integrand vanishes; the right edge
-// contributes the length of its part inside every half-plane, and so does the
-// top edge; a line, traversed with its inside on the left from P(s0) to
-// P(s1), P(s) = c (a, b) + s (b, -a), contributes (s1 - s0) cross(P(0), (b, -a))
-// = -(s1 - s0) c.  Each piece is an interval cut down by the other
-// constraints; r01, r02, r12 are the reciprocals of the pairwise
-// determinants a_i b_j - b_i a_j.  The result equals clipping the square by
-// the half-planes in turn and taking the shoelace area, up to rounding.
-template <int n>
-__device__ __forceinline__ double cut_area(const CellLine *L, double r01, double r02, double r12)
+// Areas of the unit square cut by half-planes, by Green's theorem: area =
+// 1/2 of the boundary integral of x dy - y dx.  On the square's bottom and
+// left edges the integrand vanishes; the right edge contributes the length
+// of its part inside every half-plane, and so does the top edge; a line,
+// traversed with its inside on the left from P(s0) to P(s1), P(s) =
+// c (a, b) + s (b, -a), contributes (s1 - s0) cross(P(0), (b, -a)) =
+// -(s1 - s0) c.  Each piece is an interval cut down by the other
+// constraints.  The result equals clipping the square by the half-planes in
+// turn and taking the shoelace area, up to rounding.
+//
+// A cell meets the two normal edges of a segment and one offset line at a
+// time: the pieces' intervals under the normal edges alone are formed once
+// (RailCut, which also gives the area a0 of the cell between the normal
+// edges) and each cutting offset line only narrows them further.
+
+// A line lying on the top or right edge with the square on its inner side
+// traces the same boundary as that edge: its own piece is not counted.
+__device__ __forceinline__ bool on_edge(const CellLine &L)
 {
-    double lo = 0.0, hi = 1.0, acc;
+    return (L.a == 0.0 && L.b < 0.0 && L.b - L.c == 0.0) || (L.b == 0.0 && L.a < 0.0 && L.a - L.c == 0.0);
+}
+
+// Interval of line L's own piece inside the unit square.
+__device__ __forceinline__ void square_piece(const CellLine &L, double &lo, double &hi)
+{
+    const double px = L.c * L.a, py = L.c * L.b;
+    lo = -INFINITY; hi = INFINITY;
+    narrow(px, L.b, L.rb, lo, hi);              // x >= 0
+    narrow(1.0 - px, -L.b, -L.rb, lo, hi);      // x <= 1
+    narrow(py, -L.a, -L.ra, lo, hi);            // y >= 0
+    narrow(1.0 - py, L.a, L.ra, lo, hi);        // y <= 1
+}
+
+// Narrow line J's piece by half-plane I (rIJ = 1 / (a_I b_J - b_I a_J)).
+__device__ __forceinline__ void cross_narrow(const CellLine &I, const CellLine &J, double rIJ,
+                                             double &lo, double &hi)
+{
+    const double px = J.c * J.a, py = J.c * J.b;
+    narrow(I.a * px + I.b * py - I.c, I.a * J.b - I.b * J.a, rIJ, lo, hi);
+}
+
+struct RailCut {
+    double Rlo, Rhi, Tlo, Thi;  // right edge (y) and top edge (x) inside both normal edges
+    double Plo[2], Phi[2];      // normal-edge pieces (s)
+    bool piece[2];              // normal edge j cuts the cell and has a piece of its own
+};
+
+// L[0], L[1]: the normal edges (on = cuts the cell); r01 = 1 / D_01.
+__device__ __forceinline__ void rail_cut(const CellLine *L, double r01, RailCut &rc)
+{
+    rc.Rlo = 0.0; rc.Rhi = 1.0; rc.Tlo = 0.0; rc.Thi = 1.0;
 #pragma unroll
-    for (int j = 0; j < n; j++) narrow(L[j].a - L[j].c, L[j].b, L[j].rb, lo, hi);  // x = 1
+    for (int j = 0; j < 2; j++) {
+        narrow(L[j].a - L[j].c, L[j].b, L[j].rb, rc.Rlo, rc.Rhi);  // x = 1
+        narrow(L[j].b - L[j].c, L[j].a, L[j].ra, rc.Tlo, rc.Thi);  // y = 1
+    }
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        rc.piece[j] = L[j].on && !on_edge(L[j]);
+        rc.Plo[j] = 0.0; rc.Phi[j] = 0.0;
+        if (!rc.piece[j]) continue;
+        square_piece(L[j], rc.Plo[j], rc.Phi[j]);
+        if (L[1 - j].on) cross_narrow(L[1 - j], L[j], j == 1 ? r01 : -r01, rc.Plo[j], rc.Phi[j]);
+    }
+}
+
+// Area of the cell between the normal edges (no offset line).
+__device__ __forceinline__ double rail_area(const CellLine *L, const RailCut &rc)
+{
+    double acc = fmax(rc.Rhi - rc.Rlo, 0.0);
+    acc += fmax(rc.Thi - rc.Tlo, 0.0);
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+        if (rc.piece[j]) acc -= L[j].c * fmax(rc.Phi[j] - rc.Plo[j], 0.0);
+    return 0.5 * acc;
+}
+
+// Area of the cell between the normal edges and inside offset line O;
+// r0O, r1O = 1 / D_0O, 1 / D_1O.
+__device__ __forceinline__ double rail_line_area(const CellLine *L, const RailCut &rc,
+                                                 const CellLine &O, double r0O, double r1O)
+{
+    double lo = rc.Rlo, hi = rc.Rhi, acc;
+    narrow(O.a - O.c, O.b, O.rb, lo, hi);
     acc = fmax(hi - lo, 0.0);
-    lo = 0.0; hi = 1.0;
-#pragma unroll
-    for (int j = 0; j < n; j++) narrow(L[j].b - L[j].c, L[j].a, L[j].ra, lo, hi);  // y = 1
+    lo = rc.Tlo; hi = rc.Thi;
+    narrow(O.b - O.c, O.a, O.ra, lo, hi);
     acc += fmax(hi - lo, 0.0);
 #pragma unroll
-    for (int j = 0; j < n; j++) {
-        const double a = L[j].a, b = L[j].b, c = L[j].c, px = c * a, py = c * b;
-        // a line lying on the top or right edge with the square on its inner
-        // side traces the same boundary as that edge: count it once
-        const bool on_edge = (a == 0.0 && b < 0.0 && b - c == 0.0) || (b == 0.0 && a < 0.0 && a - c == 0.0);
-        if (!L[j].on || on_edge) continue;
-        lo = -INFINITY; hi = INFINITY;
-        narrow(px, b, L[j].rb, lo, hi);             // x >= 0
-        narrow(1.0 - px, -b, -L[j].rb, lo, hi);     // x <= 1
-        narrow(py, -a, -L[j].ra, lo, hi);           // y >= 0
-        narrow(1.0 - py, a, L[j].ra, lo, hi);       // y <= 1
+    for (int j = 0; j < 2; j++) {
+        if (!rc.piece[j]) continue;
+        lo = rc.Plo[j]; hi = rc.Phi[j];
+        cross_narrow(O, L[j], j == 0 ? -r0O : -r1O, lo, hi);  // D_Oj = -D_jO
+        acc -= L[j].c * fmax(hi - lo, 0.0);
+    }
+    if (!on_edge(O)) {
+        square_piece(O, lo, hi);
 #pragma unroll
-        for (int i = 0; i < n; i++) {
-            if (i == j || !L[i].on) continue;
-            const double beta = L[i].a * b - L[i].b * a;
-            // beta = D_ij; the reciprocals are of D_01, D_02, D_12 and D_ji = -D_ij
-            const double r = (i < j) ? ((i == 0) ? (j == 1 ? r01 : r02) : r12)
-                                     : -((j == 0) ? (i == 1 ? r01 : r02) : r12);
-            narrow(L[i].a * px + L[i].b * py - L[i].c, beta, r, lo, hi);
-        }
-        acc -= c * fmax(hi - lo, 0.0);
+        for (int i = 0; i < 2; i++)
+            if (L[i].on) cross_narrow(L[i], O, i == 0 ? r0O : r1O, lo, hi);
+        acc -= O.c * fmax(hi - lo, 0.0);
     }
     return 0.5 * acc;
 }
@@ -790,7 +848,7 @@ __device__ __forceinline__ double cut_area(const CellLine *L, double r01, double
 // sum and total.  Convex, well-conditioned strips: P is the cell square cut by the slab's normal
 // edges that cross it (area a0), S_o = area(P on the inner side of offset line
 // o) for o = 0..5 (a0 or 0 when the FP32 test finds the line clear of the
-// cell, else cut_area in FP64), and strip k has area S_k - S_k+1.  Other
+// cell, else rail_line_area in FP64), and strip k has area S_k - S_k+1.  Other
 // segments (folded strips, lines within 0.001 rad of a grid axis): each
 // quadrilateral is clipped against the cell (Sutherland-Hodgman).
 __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const double *__restrict__ sl,
@@ -825,12 +883,13 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
     int side[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) side[q] = cell_side(Lf[q], gi, gj);
-    // slots 0, 1: the normal edges that cut the cell (others constrain nothing)
-    CellLine L[3];
+    // the normal edges; one that does not cut the cell constrains nothing
+    CellLine L[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) L[q] = cell_line(Ld + 5 * q, di, dj, side[q] == 0);
-    const double r01 = Ld[40];
-    const double a0 = (side[0] == 0 || side[1] == 0) ? cut_area<2>(L, r01, 0.0, 0.0) : 1.0;
+    RailCut rc;
+    rail_cut(L, Ld[40], rc);
+    const double a0 = (side[0] == 0 || side[1] == 0) ? rail_area(L, rc) : 1.0;
     double S[6];
 #pragma unroll
     for (int o = 0; o < 6; o++) {
@@ -840,8 +899,8 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
         } else if (side[q] < 0) {
             S[o] = 0.0;
         } else {
-            L[2] = cell_line(Ld + 5 * q, di, dj, true);
-            S[o] = cut_area<3>(L, r01, Ld[41 + 2 * o], Ld[42 + 2 * o]);
+            const CellLine O = cell_line(Ld + 5 * q, di, dj, true);
+            S[o] = rail_line_area(L, rc, O, Ld[41 + 2 * o], Ld[42 + 2 * o]);
         }
     }
 #pragma unroll

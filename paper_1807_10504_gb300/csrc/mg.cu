@@ -156,7 +156,9 @@ __device__ __forceinline__ void cp_async4(void *d, const void *src, bool v)
 // to zero); the last black phase also covers the tile's one-cell ring so
 // that the residual sees final neighbours (halo 5).  MODE 2: p + P e_c (the
 // bilinear prolongation of the coarse correction) is formed while staging,
-// then the sweeps (halo 4).  Each mode equals the separate kernels in turn.
+// then the sweeps (halo 4), and with xadd != NULL (the finest level of the
+// defect-correction cycle) the result is also added to the FP64 iterate.
+// Each mode equals the separate kernels in turn.
 // The iterate is read from pin and the tile written to p (a different
 // buffer): blocks read their neighbours' tiles as halo, so an in-place update
 // would let a block see values another block has already smoothed.
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(FT)
 k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
               const float *__restrict__ by, const float *__restrict__ invd,
               const float *__restrict__ b, const float *__restrict__ pin, float *__restrict__ p,
-              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp)
+              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp,
+              double *__restrict__ xadd)
 {
     pdl_enter();
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
@@ -272,7 +275,10 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     for (int k = threadIdx.x; k < FH * FW; k += FT) {
         const int r = HA + k / FW, c = XO + (k - (k / FW) * FW);
         const int gi = gi0 + c, gj = gj0 + r;
-        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+        if (gi < nx && gj < ny) {
+            p[(long)gj * nx + gi] = ps[r][c];
+            if (MODE == 2 && xadd) xadd[(long)gj * nx + gi] += (double)ps[r][c];
+        }
     }
 }
 
@@ -554,18 +560,40 @@ __device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, i
     const T *bx = v.bx[l], *by = v.by[l], *invd = v.iv[l], *r = v.r[l];
     T *e = v.e[l];
     const T h2 = g.h2[l];
+    // the cells of this thread (colour-compacted index q = t + NT k), located
+    // once per level: row j and the column of colour 0 (red); colour 1 is the
+    // other cell of the pair
+    constexpr int KMAX = 4;
+    int jq[KMAX], iq[KMAX];
+    const int nk = (nh - t + NT - 1) / NT;
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+        const int q = t + NT * k;
+        const int j = q / hx;
+        jq[k] = j;
+        iq[k] = 2 * (q - j * hx);
+    }
+    auto upd = [&](int i, int j) {
+        const int k = j * nx + i, kx = j * (nx + 1) + i;
+        const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
+        const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
+        T sm = bx[kx + 1] * pE;
+        sm = fma(bx[kx], pW, sm);
+        sm = fma(by[k + nx], pN, sm);
+        sm = fma(by[k], pS, sm);
+        e[k] = (sm - h2 * r[k]) * invd[k];
+    };
     for (int s = 0; s < nsw; s++)
         for (int color = 0; color < 2; color++) {
-            for (int q = t; q < nh; q += NT) {
-                const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1), k = j * nx + i;
-                const int kx = j * (nx + 1) + i;
-                const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
-                const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
-                T sm = bx[kx + 1] * pE;
-                sm = fma(bx[kx], pW, sm);
-                sm = fma(by[k + nx], pN, sm);
-                sm = fma(by[k], pS, sm);
-                e[k] = (sm - h2 * r[k]) * invd[k];
+            if (nk <= KMAX) {
+#pragma unroll
+                for (int k = 0; k < KMAX; k++)
+                    if (k < nk) upd(iq[k] + ((jq[k] + color) & 1), jq[k]);
+            } else {
+                for (int q = t; q < nh; q += NT) {
+                    const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1);
+                    upd(i, j);
+                }
             }
             gsync<NT>();
         }
@@ -847,7 +875,7 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
             T *nxt = other(a, cur);
             launch_pdl(k_smooth2_f32<0>, g2, FT, 0, s, v.nx, v.ny, h2, 0.0f, a.bx, a.by, a.invd, a.r,
                        (const float *)cur, nxt, (float *)nullptr, (float *)nullptr,
-                       (const float *)nullptr);
+                       (const float *)nullptr, (double *)nullptr);
             cur = nxt;
             if (pr) prof_mark(s, false);
         }
@@ -872,8 +900,10 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
 // ends in its canonical buffer (copied back when the sweep count is odd).
 // FP32 cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
 // restriction going down, prolongation + sweeps going up).
+// xadd (FP32 fused cycle only): the FP64 iterate that the level-0 result
+// is added to by the last launch; returns whether that was done.
 template <typename T>
-void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
+bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *xadd = nullptr)
 {
     auto lvT = [&](int l) -> LevelT<T> & {
         if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
@@ -895,7 +925,8 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
                 T *nxt = other(a, cur[l]);
                 launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
                            (float)(1.0 / (v.h * v.h)), a.bx, a.by, a.invd, a.r,
-                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr);
+                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr,
+                           (double *)nullptr);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -937,7 +968,7 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
                 T *nxt = other(a, cur[l]);
                 launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f,
                            a.bx, a.by, a.invd, a.r, (const float *)cur[l], nxt, (float *)nullptr,
-                           (float *)nullptr, (const float *)cur[l + 1]);
+                           (float *)nullptr, (const float *)cur[l + 1], l == 0 ? xadd : nullptr);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -952,6 +983,7 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
     if (cur[0] != lvT(0).e)
         cudaMemcpyAsync(lvT(0).e, cur[0], (size_t)mg.lv[0].nx * mg.lv[0].ny * sizeof(T),
                         cudaMemcpyDeviceToDevice, s);
+    return fused && lt > 0 && xadd;
 }
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -1102,10 +1134,66 @@ void mg_free(MG &mg)
     mg.L = 0;
 }
 
-void mg_fine_smoother(MG &mg, int precision, cudaStream_t s)
+// One launch of one kernel of the cycle on the hierarchy's current data, for
+// kernel timing: op 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps +
+// restriction, 4 FP32 prolongation + sweeps (all at `level`), 5 FP32 tail,
+// 6 FP64 residual norm of the mixed solve (level 0).  Returns the cells of
+// the level, or -1 if the op does not exist there.  Writes only solve
+// scratch (second iterate buffers, coarse right-hand sides and corrections,
+// FP32 residual, norm partials).
+long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
 {
-    if (precision) smooth<float>(mg.lv[0], mg.lv[0].f, mg.lv[0].f.e, 2, false, s);
-    else smooth<double>(mg.lv[0], mg.lv[0].d, mg.lv[0].d.e, 1, false, s);
+    if (level < 0 || level >= mg.L) return -1;
+    Level &v = mg.lv[level];
+    const long cells = (long)v.nx * v.ny;
+    dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
+    switch (op) {
+    case 0: smooth<float>(v, v.f, v.f.e, 2, false, s); return cells;
+    case 1: smooth<double>(v, v.d, v.d.e, 1, false, s); return cells;
+    case 3:
+        if (level >= mg.tail_f) return -1;
+        note_launch();
+        launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
+                   (float)(1.0 / (v.h * v.h)), v.f.bx, v.f.by, v.f.invd, v.f.r,
+                   (const float *)v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
+                   (const float *)nullptr, (double *)nullptr);
+        return cells;
+    case 4:
+        if (level >= mg.tail_f) return -1;
+        note_launch();
+        launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f, v.f.bx,
+                   v.f.by, v.f.invd, v.f.r, (const float *)v.f.e, v.f.e2, (float *)nullptr,
+                   (float *)nullptr, (const float *)mg.lv[level + 1].f.e, (double *)nullptr);
+        return cells;
+    case 5: {
+        const int lt = mg.tail_f, L = mg.L;
+        TailArgs<float> ta;
+        ta.lt = lt;
+        ta.nl = L;
+        for (int l = lt; l < L; l++) {
+            Level &w = mg.lv[l];
+            ta.nx[l] = w.nx; ta.ny[l] = w.ny;
+            ta.h2[l] = (float)(w.h * w.h); ta.ih2[l] = (float)(1.0 / (w.h * w.h));
+            ta.e[l] = w.f.e2; ta.r[l] = w.f.r; ta.bx[l] = w.f.bx; ta.by[l] = w.f.by; ta.invd[l] = w.f.invd;
+        }
+        const long nc = (long)mg.lv[L - 1].nx * mg.lv[L - 1].ny;
+        ta.ainvT = mg.lu + nc * nc;
+        ta.nu1 = 2;
+        ta.nu2 = 2;
+        note_launch();
+        launch_pdl(k_tail<float>, 1, 1024, tail_smem_bytes(ta), s, ta);
+        return (long)mg.lv[lt].nx * mg.lv[lt].ny;
+    }
+    case 6: {
+        Level &v0 = mg.lv[0];
+        note_launch();
+        launch_pdl(k_resnorm, mg.red_blocks, kRedT, 0, s, v0.nx, v0.ny, 1.0 / (v0.h * v0.h), v0.d.bx,
+                   v0.d.by, (const double *)v0.d.r, (const double *)v0.d.e, v0.f.r, v0.f.e,
+                   mg.red + 8, mg.red_count, mg.red + 2);
+        return (long)v0.nx * v0.ny;
+    }
+    default: return -1;
+    }
 }
 
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
@@ -1191,9 +1279,10 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
             if (precision == 0) {
                 vcycle<double>(mg, nu1, nu2, s);
             } else {
-                vcycle<float>(mg, nu1, nu2, s);
-                note_launch();
-                k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
+                if (!vcycle<float>(mg, nu1, nu2, s, e0)) {
+                    note_launch();
+                    k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
+                }
             }
             c++;
             ce = resnorm();
@@ -1276,9 +1365,10 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
             if (sg.precision == 0) {
                 vcycle<double>(mg, sg.nu1, sg.nu2, cb);
             } else {
-                vcycle<float>(mg, sg.nu1, sg.nu2, cb);
-                note_launch();
-                launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
+                if (!vcycle<float>(mg, sg.nu1, sg.nu2, cb, e0)) {
+                    note_launch();
+                    launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
+                }
             }
             resnorm(cb);
             note_launch();
