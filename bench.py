@@ -211,6 +211,21 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.ncu_cnn:
+        # network inference on this step's system inside a profiler range
+        net = ib.Net(seed=0)
+        net.set_coarsen(args.cnn_coarsen)
+        b, rho = ctx.get("b"), ctx.get("rho")
+        net.infer(b[None], rho[None])
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            net.infer(b[None], rho[None])
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        ctx.close()
+        return 0
+
     if args.ncu:
         torch.cuda.profiler.start()
         for k in range(args.steps):
@@ -413,6 +428,9 @@ def main():
                     help="run the network on the grid coarsened by 2^k")
     ap.add_argument("--no-graphs", action="store_true",
                     help="solve with one launch per kernel (for kernel profilers)")
+    ap.add_argument("--ncu-cnn", action="store_true",
+                    help="after the warm-up steps, only network inference on the step's system "
+                         "inside a CUDA profiler range (random weights); prints no JSON")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + timed steps, the timed steps inside a CUDA profiler "
                          "range (for ncu --profile-from-start off); prints no JSON")

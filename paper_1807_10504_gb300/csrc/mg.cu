@@ -156,9 +156,7 @@ __device__ __forceinline__ void cp_async4(void *d, const void *src, bool v)
 // to zero); the last black phase also covers the tile's one-cell ring so
 // that the residual sees final neighbours (halo 5).  MODE 2: p + P e_c (the
 // bilinear prolongation of the coarse correction) is formed while staging,
-// then the sweeps (halo 4), and with xadd != NULL (the finest level of the
-// defect-correction cycle) the result is also added to the FP64 iterate.
-// Each mode equals the separate kernels in turn.
+// then the sweeps (halo 4).  Each mode equals the separate kernels in turn.
 // The iterate is read from pin and the tile written to p (a different
 // buffer): blocks read their neighbours' tiles as halo, so an in-place update
 // would let a block see values another block has already smoothed.
@@ -167,8 +165,7 @@ __global__ void __launch_bounds__(FT)
 k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
               const float *__restrict__ by, const float *__restrict__ invd,
               const float *__restrict__ b, const float *__restrict__ pin, float *__restrict__ p,
-              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp,
-              double *__restrict__ xadd)
+              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp)
 {
     pdl_enter();
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
@@ -275,10 +272,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     for (int k = threadIdx.x; k < FH * FW; k += FT) {
         const int r = HA + k / FW, c = XO + (k - (k / FW) * FW);
         const int gi = gi0 + c, gj = gj0 + r;
-        if (gi < nx && gj < ny) {
-            p[(long)gj * nx + gi] = ps[r][c];
-            if (MODE == 2 && xadd) xadd[(long)gj * nx + gi] += (double)ps[r][c];
-        }
+        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
     }
 }
 
@@ -415,15 +409,20 @@ __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restr
 // inverse by Gauss-Jordan elimination with partial pivoting (first maximal
 // |pivot|), stored transposed (Ainv^T) so that the per-cycle solve x = A'^-1 r
 // is one coalesced matrix-vector product.  One CTA; A and the inverse live in
-// the scratch `A` (2 n^2).
+// shared memory when 2 n^2 doubles fit in 96 KB, else in the scratch `A`.
 __global__ void __launch_bounds__(1024)
 k_coarse_inv(int nx, int ny, double h, const double *__restrict__ bx,
-             const double *__restrict__ by, double *__restrict__ A, double *__restrict__ AinvT)
+             const double *__restrict__ by, double *__restrict__ Ag, double *__restrict__ AinvT,
+             int in_smem)
 {
+    extern __shared__ __align__(16) double cinv_sm[];
     const int n = nx * ny;
     const double hh = h * h;
-    double *X = AinvT;  // identity, then the inverse (row-major), transposed at the end
-    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
+    // A and X (identity, then the inverse, row-major) in shared memory when
+    // they fit, else in the global scratch
+    double *A = in_smem ? cinv_sm : Ag;
+    double *X = in_smem ? cinv_sm + (size_t)n * n : AinvT;
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
         A[k] = 0.0;
         X[k] = (k / n == k % n) ? 1.0 : 0.0;
     }
@@ -432,57 +431,72 @@ k_coarse_inv(int nx, int ny, double h, const double *__restrict__ bx,
         int i = c % nx, j = c / nx;
         long kx = (long)j * (nx + 1) + i, kc = c;
         double d = 0.0;
-        if (i + 1 < nx) { d += bx[kx + 1] * (0.0 - 1.0); A[(long)(c + 1) * n + c] = bx[kx + 1] * (1.0 - 0.0) / hh; }
-        if (i > 0) { d -= bx[kx] * (1.0 - 0.0); A[(long)(c - 1) * n + c] = -bx[kx] * (0.0 - 1.0) / hh; }
-        if (j + 1 < ny) { d += by[kc + nx] * (0.0 - 1.0); A[(long)(c + nx) * n + c] = by[kc + nx] * (1.0 - 0.0) / hh; }
-        if (j > 0) { d -= by[kc] * (1.0 - 0.0); A[(long)(c - nx) * n + c] = -by[kc] * (0.0 - 1.0) / hh; }
-        A[(long)c * n + c] = d / hh;
+        if (i + 1 < nx) { d += bx[kx + 1] * (0.0 - 1.0); A[(c + 1) * n + c] = bx[kx + 1] * (1.0 - 0.0) / hh; }
+        if (i > 0) { d -= bx[kx] * (1.0 - 0.0); A[(c - 1) * n + c] = -bx[kx] * (0.0 - 1.0) / hh; }
+        if (j + 1 < ny) { d += by[kc + nx] * (0.0 - 1.0); A[(c + nx) * n + c] = by[kc + nx] * (1.0 - 0.0) / hh; }
+        if (j > 0) { d -= by[kc] * (1.0 - 0.0); A[(c - nx) * n + c] = -by[kc] * (0.0 - 1.0) / hh; }
+        A[c * n + c] = d / hh;
     }
     __syncthreads();
     __shared__ double s0;
     if (threadIdx.x == 0) s0 = A[0];
     __syncthreads();
-    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] += s0;
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] += s0;
     __syncthreads();
     __shared__ int pr;
+    __shared__ double dpiv;
     for (int c = 0; c < n; c++) {
-        if (threadIdx.x == 0) {
-            int best = c;
-            for (int r = c + 1; r < n; r++)
-                if (fabs(A[(long)r * n + c]) > fabs(A[(long)best * n + c])) best = r;
-            pr = best;
+        if (threadIdx.x < 32) {  // pivot: first row of maximal |A[r][c]|, r >= c (warp argmax)
+            int best = -1;
+            double bv = -1.0;
+            for (int r = c + threadIdx.x; r < n; r += 32) {
+                const double v = fabs(A[r * n + c]);
+                if (v > bv) { bv = v; best = r; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
+            }
+            if (threadIdx.x == 0) pr = best;
         }
         __syncthreads();
         if (pr != c)
             for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double t = A[(long)c * n + k]; A[(long)c * n + k] = A[(long)pr * n + k]; A[(long)pr * n + k] = t;
-                t = X[(long)c * n + k]; X[(long)c * n + k] = X[(long)pr * n + k]; X[(long)pr * n + k] = t;
+                double t = A[c * n + k]; A[c * n + k] = A[pr * n + k]; A[pr * n + k] = t;
+                t = X[c * n + k]; X[c * n + k] = X[pr * n + k]; X[pr * n + k] = t;
             }
         __syncthreads();
-        __shared__ double dpiv;
-        if (threadIdx.x == 0) dpiv = A[(long)c * n + c];
+        if (threadIdx.x == 0) dpiv = A[c * n + c];
         __syncthreads();
         const double d = dpiv;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) { A[(long)c * n + k] /= d; X[(long)c * n + k] /= d; }
+        for (int k = threadIdx.x; k < n; k += blockDim.x) { A[c * n + k] /= d; X[c * n + k] /= d; }
         __syncthreads();
-        for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
-            const int r = (int)(k / n), q = (int)(k % n);
+        for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+            const int r = k / n, q = k - r * n;
             if (r == c) continue;
-            const double f = A[(long)r * n + c];
-            if (q != c) A[(long)r * n + q] -= f * A[(long)c * n + q];
-            X[(long)r * n + q] -= f * X[(long)c * n + q];
+            const double f = A[r * n + c];
+            if (q != c) A[r * n + q] -= f * A[c * n + q];
+            X[r * n + q] -= f * X[c * n + q];
         }
         __syncthreads();
         for (int r = threadIdx.x; r < n; r += blockDim.x)
-            if (r != c) A[(long)r * n + c] = 0.0;
+            if (r != c) A[r * n + c] = 0.0;
         __syncthreads();
     }
-    // transpose X in place through A (A is no longer needed)
-    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) A[k] = X[k];
-    __syncthreads();
-    for (long k = threadIdx.x; k < (long)n * n; k += blockDim.x) {
-        const int r = (int)(k / n), q = (int)(k % n);
-        AinvT[(long)q * n + r] = A[k];
+    // transposed inverse out (through A when X is the output array itself)
+    if (in_smem) {
+        for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+            const int r = k / n, q = k - r * n;
+            AinvT[q * n + r] = X[k];
+        }
+    } else {
+        for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = X[k];
+        __syncthreads();
+        for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+            const int r = k / n, q = k - r * n;
+            AinvT[q * n + r] = A[k];
+        }
     }
 }
 
@@ -560,40 +574,18 @@ __device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, i
     const T *bx = v.bx[l], *by = v.by[l], *invd = v.iv[l], *r = v.r[l];
     T *e = v.e[l];
     const T h2 = g.h2[l];
-    // the cells of this thread (colour-compacted index q = t + NT k), located
-    // once per level: row j and the column of colour 0 (red); colour 1 is the
-    // other cell of the pair
-    constexpr int KMAX = 4;
-    int jq[KMAX], iq[KMAX];
-    const int nk = (nh - t + NT - 1) / NT;
-#pragma unroll
-    for (int k = 0; k < KMAX; k++) {
-        const int q = t + NT * k;
-        const int j = q / hx;
-        jq[k] = j;
-        iq[k] = 2 * (q - j * hx);
-    }
-    auto upd = [&](int i, int j) {
-        const int k = j * nx + i, kx = j * (nx + 1) + i;
-        const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
-        const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
-        T sm = bx[kx + 1] * pE;
-        sm = fma(bx[kx], pW, sm);
-        sm = fma(by[k + nx], pN, sm);
-        sm = fma(by[k], pS, sm);
-        e[k] = (sm - h2 * r[k]) * invd[k];
-    };
     for (int s = 0; s < nsw; s++)
         for (int color = 0; color < 2; color++) {
-            if (nk <= KMAX) {
-#pragma unroll
-                for (int k = 0; k < KMAX; k++)
-                    if (k < nk) upd(iq[k] + ((jq[k] + color) & 1), jq[k]);
-            } else {
-                for (int q = t; q < nh; q += NT) {
-                    const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1);
-                    upd(i, j);
-                }
+            for (int q = t; q < nh; q += NT) {
+                const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1), k = j * nx + i;
+                const int kx = j * (nx + 1) + i;
+                const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
+                const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
+                T sm = bx[kx + 1] * pE;
+                sm = fma(bx[kx], pW, sm);
+                sm = fma(by[k + nx], pN, sm);
+                sm = fma(by[k], pS, sm);
+                e[k] = (sm - h2 * r[k]) * invd[k];
             }
             gsync<NT>();
         }
@@ -875,7 +867,7 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
             T *nxt = other(a, cur);
             launch_pdl(k_smooth2_f32<0>, g2, FT, 0, s, v.nx, v.ny, h2, 0.0f, a.bx, a.by, a.invd, a.r,
                        (const float *)cur, nxt, (float *)nullptr, (float *)nullptr,
-                       (const float *)nullptr, (double *)nullptr);
+                       (const float *)nullptr);
             cur = nxt;
             if (pr) prof_mark(s, false);
         }
@@ -900,10 +892,8 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
 // ends in its canonical buffer (copied back when the sweep count is odd).
 // FP32 cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
 // restriction going down, prolongation + sweeps going up).
-// xadd (FP32 fused cycle only): the FP64 iterate that the level-0 result
-// is added to by the last launch; returns whether that was done.
 template <typename T>
-bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *xadd = nullptr)
+void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
 {
     auto lvT = [&](int l) -> LevelT<T> & {
         if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
@@ -925,8 +915,7 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *xadd = nullptr)
                 T *nxt = other(a, cur[l]);
                 launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
                            (float)(1.0 / (v.h * v.h)), a.bx, a.by, a.invd, a.r,
-                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr,
-                           (double *)nullptr);
+                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -968,7 +957,7 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *xadd = nullptr)
                 T *nxt = other(a, cur[l]);
                 launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f,
                            a.bx, a.by, a.invd, a.r, (const float *)cur[l], nxt, (float *)nullptr,
-                           (float *)nullptr, (const float *)cur[l + 1], l == 0 ? xadd : nullptr);
+                           (float *)nullptr, (const float *)cur[l + 1]);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -983,7 +972,6 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *xadd = nullptr)
     if (cur[0] != lvT(0).e)
         cudaMemcpyAsync(lvT(0).e, cur[0], (size_t)mg.lv[0].nx * mg.lv[0].ny * sizeof(T),
                         cudaMemcpyDeviceToDevice, s);
-    return fused && lt > 0 && xadd;
 }
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -1068,7 +1056,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         nxs[L] = nx; nys[L] = ny; L++;
     }
     const long nc = (long)nxs[L - 1] * nys[L - 1];
-    mg.red_blocks = 2 * 152;
+    mg.red_blocks = 8 * 152;  // residual-norm blocks: several per SM to hide FP64 and load latency
     char *q = base;
     size_t off = 0;
     auto take = [&](size_t b) -> void * {
@@ -1156,14 +1144,14 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
         launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
                    (float)(1.0 / (v.h * v.h)), v.f.bx, v.f.by, v.f.invd, v.f.r,
                    (const float *)v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
-                   (const float *)nullptr, (double *)nullptr);
+                   (const float *)nullptr);
         return cells;
     case 4:
         if (level >= mg.tail_f) return -1;
         note_launch();
         launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f, v.f.bx,
                    v.f.by, v.f.invd, v.f.r, (const float *)v.f.e, v.f.e2, (float *)nullptr,
-                   (float *)nullptr, (const float *)mg.lv[level + 1].f.e, (double *)nullptr);
+                   (float *)nullptr, (const float *)mg.lv[level + 1].f.e);
         return cells;
     case 5: {
         const int lt = mg.tail_f, L = mg.L;
@@ -1228,7 +1216,11 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     Level &vc = mg.lv[L - 1];
     note_launch();
     const size_t nc2 = (size_t)vc.nx * vc.ny * vc.nx * vc.ny;
-    k_coarse_inv<<<1, 1024, 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu, mg.lu + nc2);
+    const size_t cbytes = 2 * nc2 * sizeof(double);
+    const int in_smem = cbytes <= 96 * 1024;
+    if (in_smem) cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    k_coarse_inv<<<1, 1024, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
+                                                       mg.lu + nc2, in_smem);
 }
 
 // Host-driven solve: one launch per kernel and a host read of the residual
@@ -1279,10 +1271,9 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
             if (precision == 0) {
                 vcycle<double>(mg, nu1, nu2, s);
             } else {
-                if (!vcycle<float>(mg, nu1, nu2, s, e0)) {
-                    note_launch();
-                    k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
-                }
+                vcycle<float>(mg, nu1, nu2, s);
+                note_launch();
+                k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
             }
             c++;
             ce = resnorm();
@@ -1365,10 +1356,9 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
             if (sg.precision == 0) {
                 vcycle<double>(mg, sg.nu1, sg.nu2, cb);
             } else {
-                if (!vcycle<float>(mg, sg.nu1, sg.nu2, cb, e0)) {
-                    note_launch();
-                    launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
-                }
+                vcycle<float>(mg, sg.nu1, sg.nu2, cb);
+                note_launch();
+                launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
             }
             resnorm(cb);
             note_launch();

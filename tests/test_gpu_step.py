@@ -103,3 +103,40 @@ def test_step_errors(T, ib):
     with pytest.raises(ib.IBError) as e:
         ctx.ns_step(0.05, 1, 1)
     assert e.value.status == ib.IB_EMARKER
+
+
+def test_oscillating_drop_precisions_and_period(T, ib):
+    # The 256^2 oscillating drop (r = 0.2 (1 + 0.05 cos 2 theta), density
+    # ratio 1000, viscosity ratio 100, sigma 1, 512 markers, relocation every
+    # 10 steps): (1) after 2000 steps the FP32-smoothing path agrees with the
+    # FP64 path to 1e-6 on u, v and p; (2) the first extremum of the x-extent
+    # falls at half the n = 2 capillary period of the closed form, 2 pi
+    # sqrt((rho_d + rho_a) r^3 / ((n^3 - n) sigma)), within 5 %.
+    n, h = 256, 1.0 / 256
+    mk = W.oscillating_drop()
+    dt = W.capillary_dt(h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    res = {}
+    for prec in (0, 1):
+        cfg = ib.Config(nx=n, ny=n, h=h, precision=prec, tol=1e-10, max_cycles=200, spread=1,
+                        relocate_every=10)
+        ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+        ctx.ns_step(dt, 2000, 1)
+        res[prec] = {k: ctx.get_host(k) for k in ("u", "v", "p")}
+        if prec == 1:
+            ext, ts = [], []
+            for k in range(150):
+                ctx.ns_step(dt, 20, 1)
+                X, Y = ctx.markers()
+                ext.append(float(X.max() - X.min()) - float(Y.max() - Y.min()))
+                ts.append((2000 + 20 * (k + 1)) * dt)
+        ctx.close()
+    for k in ("u", "v", "p"):
+        scale = np.abs(res[0][k]).max()
+        assert np.abs(res[1][k] - res[0][k]).max() <= 1e-6 * scale, k
+    ext = np.array(ext)
+    i = int(np.argmin(ext))  # the drop starts elongated in x: first minimum at T/2
+    assert 0 < i < len(ext) - 1
+    a, b, c = np.polyfit(np.array(ts[i - 1:i + 2]), ext[i - 1:i + 2], 2)
+    t_half = -b / (2 * a)
+    T2 = 2 * np.pi * np.sqrt((1.0 + 1e-3) * 0.2 ** 3 / (6 * 1.0))
+    assert abs(2 * t_half - T2) <= 0.05 * T2, (2 * t_half, T2)
