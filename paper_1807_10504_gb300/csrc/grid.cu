@@ -28,21 +28,20 @@ __global__ void k_cells_props(int n, double rho_g, double drho, double mu_g,
 __global__ void k_face_beta(int nx, int ny, const double *__restrict__ rho,
                             double *__restrict__ bx, double *__restrict__ by)
 {
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long nxf = (long)(nx + 1) * ny;
-    if (k < nxf) {
-        int j = (int)(k / (nx + 1)), i = (int)(k - (long)j * (nx + 1));
+    // one row of x-faces (j < ny) and of y-faces (j <= ny) per blockIdx.y
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (j < ny && i <= nx) {
+        const long k = (long)j * (nx + 1) + i;
         bx[k] = (i == 0 || i == nx)
                     ? 0.0
-                    : 1.0 / (0.5 * (rho[(long)j * nx + i - 1] + rho[(long)j * nx + i]));
-        return;
+                    : recip_nr(0.5 * (rho[(long)j * nx + i - 1] + rho[(long)j * nx + i]));
     }
-    k -= nxf;
-    if (k >= (long)nx * (ny + 1)) return;
-    int j = (int)(k / nx), i = (int)(k - (long)j * nx);
-    by[k] = (j == 0 || j == ny)
-                ? 0.0
-                : 1.0 / (0.5 * (rho[(long)(j - 1) * nx + i] + rho[(long)j * nx + i]));
+    if (i < nx) {
+        const long k = (long)j * nx + i;
+        by[k] = (j == 0 || j == ny)
+                    ? 0.0
+                    : recip_nr(0.5 * (rho[(long)(j - 1) * nx + i] + rho[(long)j * nx + i]));
+    }
 }
 
 __global__ void k_rhs(int nx, int ny, double ih, double idt,
@@ -159,7 +158,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
                                 muS * (uc - uS)) * ih2;
             const double rf = 0.5 * (sr[R][C - 1] + sr[R][C]);
             const double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
-            us[k] = uc + dt * ((vis - ae) / rf + gx);
+            us[k] = uc + dt * ((vis - ae) * recip_nr(rf) + gx);
             au[k] = adv;
         }
         if (i == nx - 1) { us[k + 1] = 0.0; au[k + 1] = 0.0; }  // right wall face
@@ -184,7 +183,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
                                 muW * (vc - vW)) * ih2;
             const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
-            vs[k] = vc + dt * ((vis - ae) / rf + gy);
+            vs[k] = vc + dt * ((vis - ae) * recip_nr(rf) + gy);
             av[k] = adv;
         }
         if (j == ny - 1) { vs[k + nx] = 0.0; av[k + nx] = 0.0; }  // top wall face
@@ -201,9 +200,9 @@ void launch_coeffs(int nx, int ny, double rho_g, double rho_l, double mu_g,
     note_launch();
     k_cells_props<<<cdiv(n, kT), kT, 0, s>>>((int)n, rho_g, rho_l - rho_g, mu_g,
                                              mu_l - mu_g, H, rho, mu);
-    long nf = (long)(nx + 1) * ny + (long)nx * (ny + 1);
+    dim3 gb(cdiv(nx + 1, 128), ny + 1);
     note_launch();
-    k_face_beta<<<cdiv(nf, kT), kT, 0, s>>>(nx, ny, rho, bx, by);
+    k_face_beta<<<gb, 128, 0, s>>>(nx, ny, rho, bx, by);
 }
 
 void launch_rhs(int nx, int ny, double h, double dt, const double *us,

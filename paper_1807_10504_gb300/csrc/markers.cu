@@ -118,12 +118,16 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
                            const double *__restrict__ nym, float4 *__restrict__ sbox,
                            double *__restrict__ sv, float4 *__restrict__ sb5,
                            double *__restrict__ sl, float4 *__restrict__ slf,
-                           uint8_t *__restrict__ scvx)
+                           uint8_t *__restrict__ scvx, double *__restrict__ sinv)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     int nm = next[m];
     const double gxa = gx[m], gya = gy[m], gxb = gx[nm], gyb = gy[nm];
+    {
+        const double ex = gxb - gxa, ey = gyb - gya;  // 1 / |segment|^2 (grid units)
+        sinv[m] = 1.0 / (ex * ex + ey * ey);
+    }
     const double nax = nxm[m], nay = nym[m], nbx = nxm[nm], nby = nym[nm];
     // corner o (offset o - 2.5 cells) on the normal at m: (2o, 2o+1); at next m: 12 + (2o, 2o+1)
     double *v = sv + (long)m * 24;
@@ -501,20 +505,27 @@ __device__ int gather_candidates(int bi, int bj, int nx, int ny,
                                  const uint32_t *__restrict__ ids, uint32_t *cand,
                                  uint32_t *tmp, uint32_t *flags)
 {
-    __shared__ uint32_t rowoff[kBlk + 2 * kSearch + 1];
+    constexpr int kRows = kBlk + 2 * kSearch;  // at most 22 rows: one warp
+    __shared__ uint32_t rowoff[kRows + 1], rowsrc[kRows];
     __shared__ int total;
     const int ia = max(bi * kBlk - kSearch, 0), ib = min(bi * kBlk + kBlk - 1 + kSearch, nx - 1);
     const int ja = max(bj * kBlk - kSearch, 0), jb = min(bj * kBlk + kBlk - 1 + kSearch, ny - 1);
     const int nrows = jb - ja + 1;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int r = 0; r < nrows; r++) {
-            rowoff[r] = acc;
-            long base = (long)(ja + r) * nx;
-            acc += cell_start[base + ib + 1] - cell_start[base + ia];
+    if (threadIdx.x < 32) {  // per row: first id and count, then an exclusive warp scan
+        const int r = threadIdx.x;
+        uint32_t src = 0, cnt = 0;
+        if (r < nrows) {
+            const long base = (long)(ja + r) * nx;
+            src = cell_start[base + ia];
+            cnt = cell_start[base + ib + 1] - src;
         }
-        rowoff[nrows] = acc;
-        total = (int)acc;
+        uint32_t inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (r >= o) inc += v;
+        }
+        if (r < nrows) { rowoff[r] = inc - cnt; rowsrc[r] = src; }
+        if (r == 31) { rowoff[nrows] = inc; total = (int)inc; }
     }
     __syncthreads();
     int n = total;
@@ -522,13 +533,10 @@ __device__ int gather_candidates(int bi, int bj, int nx, int ny,
         if (threadIdx.x == 0) atomicOr(&flags[1], 1u);
         n = kMaxCand;
     }
-    for (int r = 0; r < nrows; r++) {
-        long base = (long)(ja + r) * nx;
-        uint32_t s = cell_start[base + ia], cnt = rowoff[r + 1] - rowoff[r];
-        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
-            uint32_t q = rowoff[r] + t;
-            if ((int)q < n) tmp[q] = ids[s + t];
-        }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        int r = 0;
+        while (r + 1 < nrows && rowoff[r + 1] <= (uint32_t)q) r++;
+        tmp[q] = ids[rowsrc[r] + (uint32_t)q - rowoff[r]];
     }
     __syncthreads();
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -960,13 +968,13 @@ k_band_sum(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
 // before evaluating the survivors exactly in FP64, in ascending id.
 constexpr int kIrrT = 2 * kBT;  // one thread per face of the block
 __global__ void __launch_bounds__(kIrrT)
-k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ bactive,
+k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ bactive,
                const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
                const int32_t *__restrict__ next, const double *__restrict__ gx,
-               const double *__restrict__ gy, const float *__restrict__ gxf,
-               const float *__restrict__ gyf, const double *__restrict__ fmag,
-               const double *__restrict__ H, double *__restrict__ Fx, double *__restrict__ Fy,
-               uint32_t *__restrict__ flags)
+               const double *__restrict__ gy, const double *__restrict__ sinv,
+               const float *__restrict__ gxf, const float *__restrict__ gyf,
+               const double *__restrict__ fmag, const double *__restrict__ H,
+               double *__restrict__ Fx, double *__restrict__ Fy, uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
     __shared__ float4 seg[kMaxCand];   // FP32 candidate segments: start, direction
@@ -1017,9 +1025,10 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
     const double dH = wdH[threadIdx.x];
     const double qx = dir == 0 ? (double)i : (double)i + 0.5;
     const double qy = dir == 0 ? (double)j + 0.5 : (double)j;
-    // FP32 screen: squared distances carry an error far below 0.05 (grid
-    // units, coordinates < 2^15), so the exact nearest segment is among those
-    // within best + 0.05 of the FP32 minimum.
+    // FP32 screen: for faces within the band (distance below ~4 cells) and
+    // coordinates below 2^12 cells the FP32 squared distances carry an error
+    // below 2e-3 (grid units), so the exact nearest segment is among those
+    // within best + 0.01 of the FP32 minimum.
     const float fqx = (float)qx, fqy = (float)qy;
     auto d2f = [&](int q) {
         const float4 sg = seg[q];
@@ -1030,21 +1039,21 @@ k_spread_irrot(int nx, int ny, double h, int bnx, const uint32_t *__restrict__ b
     };
     float best32 = INFINITY;
     for (int q = 0; q < n; q++) best32 = fminf(best32, d2f(q));
-    const float lim = best32 + 0.05f;
+    const float lim = best32 + 0.01f;
     double best = INFINITY, fb = 0.0;
     for (int q = 0; q < n; q++) {
         if (d2f(q) > lim) continue;
         const int m = (int)cand[q], nm = next[m];
         const double ax = gx[m], ay = gy[m];
         const double ex = gx[nm] - ax, ey = gy[nm] - ay;
-        double t = ((qx - ax) * ex + (qy - ay) * ey) / (ex * ex + ey * ey);
+        double t = ((qx - ax) * ex + (qy - ay) * ey) * sinv[m];
         if (t < 0.0) t = 0.0;
         if (t > 1.0) t = 1.0;
         const double dx = ax + t * ex - qx, dy = ay + t * ey - qy;
         const double d2 = dx * dx + dy * dy;
         if (d2 < best) { best = d2; fb = (1.0 - t) * fmag[m] + t * fmag[nm]; }
     }
-    const double F = fb * dH / h;
+    const double F = fb * dH * ih;
     if (dir == 0) Fx[(long)j * (nx + 1) + i] = F;
     else Fy[(long)j * nx + i] = F;
 }
@@ -1303,7 +1312,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     const size_t pair_cap = (size_t)M * 64 + 4096;
     mk.pair_cap = (uint32_t)pair_cap;
     size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
-                   al((size_t)M * 24 * 8) + al((size_t)M * kSegLine * 8) + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) +
+                   al((size_t)M * 24 * 8) + al((size_t)M * kSegLine * 8) + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) + al(M * 8) +
                    al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
@@ -1326,6 +1335,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.slf = (float4 *)take((size_t)M * 8 * 16);
     mk.sb5 = (float4 *)take((size_t)M * 5 * 16);
     mk.scvx = (uint8_t *)take(M);
+    mk.sinv = (double *)take(M * 8);
     mk.npairs = (uint32_t *)take(64);
     mk.pseg = (uint32_t *)take(pair_cap * 4); mk.pcell = (uint32_t *)take(pair_cap * 4);
     mk.pacc = (double *)take(pair_cap * 8); mk.pcov = (double *)take(pair_cap * 8);
@@ -1376,7 +1386,7 @@ void launch_geometry(Markers &mk, double sigma, cudaStream_t s)
     note_launch();
     k_segments<<<cdiv(mk.M, 32), 32, 0, s>>>(  // FP64-heavy: spread over all SMs
         mk.M, mk.next, mk.gx, mk.gy, mk.nxm, mk.nym, mk.sbox,
-                                            mk.sv, mk.sb5, mk.sl, mk.slf, mk.scvx);
+                                            mk.sv, mk.sb5, mk.sl, mk.slf, mk.scvx, mk.sinv);
     note_launch();
     k_drop_yrange<<<cdiv((long)mk.ndrops * 32, kT), kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.Y,
                                                                mk.dyr, mk.dyk);
@@ -1472,9 +1482,9 @@ void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
     cudaMemsetAsync(Fy, 0, (size_t)mk.nx * (mk.ny + 1) * 8, s);
     dim3 g(mk.bnx, mk.bny);
     note_launch();
-    k_spread_irrot<<<g, kIrrT, 0, s>>>(mk.nx, mk.ny, mk.h, mk.bnx, mk.bactive, mk.cell_start,
-                                     mk.ids, mk.next, mk.gx, mk.gy, mk.gxf, mk.gyf, fmag, H, Fx,
-                                     Fy, mk.flags);
+    k_spread_irrot<<<g, kIrrT, 0, s>>>(mk.nx, mk.ny, 1.0 / mk.h, mk.bnx, mk.bactive, mk.cell_start,
+                                       mk.ids, mk.next, mk.gx, mk.gy, mk.sinv, mk.gxf, mk.gyf, fmag,
+                                       H, Fx, Fy, mk.flags);
 }
 
 size_t relocate_smem(int maxn)

@@ -175,7 +175,11 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     __shared__ __align__(16) float bs[PH][PW];
     __shared__ __align__(16) float ds[PH][PW];
     __shared__ __align__(16) float ys[PH + 1][PW];
-    __shared__ float xs[PH][PW + 1];
+    // x-faces: row r holds the faces gi0 .. gi0 + PW from column xoff[r] on
+    // (the 16-byte-aligned copy of a row of (nx + 1) faces starts up to three
+    // faces early)
+    __shared__ __align__(16) float xs[PH][PW + 8];
+    __shared__ int xoff[PH];
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
     const long nxf = nx + 1;
     const int nxc = nx / 2, nyc = ny / 2;
@@ -220,10 +224,32 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[o] : 0.0f;
         }
     }
-    for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
-        const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
-        const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj < ny;
-        cp_async4(&xs[r][c], in ? bx + (long)gj * nxf + gi : bx, in);
+    if (vec) {
+        constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per row, worst alignment
+        const long nbx = nxf * ny;
+        for (int k = threadIdx.x; k < PH * NC; k += FT) {
+            const int r = k / NC, q = k - r * NC, gj = gj0 + r;
+            if (gj < 0 || gj >= ny) {
+                cp_async16(&xs[r][4 * q], bx, false);
+                if (q == 0) xoff[r] = 0;
+                continue;
+            }
+            const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
+            if (q == 0) xoff[r] = (int)(start - a0);
+            const long e0 = a0 + 4 * q;
+            if (e0 + 4 <= nbx) {
+                cp_async16(&xs[r][4 * q], bx + e0, true);
+            } else {
+                for (int t = 0; t < 4; t++) cp_async4(&xs[r][4 * q + t], bx + (e0 + t < nbx ? e0 + t : 0), e0 + t < nbx);
+            }
+        }
+    } else {
+        for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
+            const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
+            const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj < ny;
+            cp_async4(&xs[r][c], in ? bx + (long)gj * nxf + gi : bx, in);
+            if (c == 0) xoff[r] = 0;
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
@@ -239,8 +265,9 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             const int c = XO - q + 2 * cc + ((gi0 + XO - q + gj + color) & 1);
             const int gi = gi0 + c;
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
-            float sm = xs[r][c + 1] * ps[r][c + 1];
-            sm = fmaf(xs[r][c], ps[r][c - 1], sm);
+            const int xc = c + xoff[r];
+            float sm = xs[r][xc + 1] * ps[r][c + 1];
+            sm = fmaf(xs[r][xc], ps[r][c - 1], sm);
             sm = fmaf(ys[r + 1][c], ps[r + 1][c], sm);
             sm = fmaf(ys[r][c], ps[r - 1][c], sm);
             ps[r][c] = (sm - h2 * bs[r][c]) * ds[r][c];
@@ -257,8 +284,9 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
                 const float cc = ps[r][c];
                 const float pE = gi + 1 < nx ? ps[r][c + 1] : cc, pW = gi > 0 ? ps[r][c - 1] : cc;
                 const float pN = gj + 1 < ny ? ps[r + 1][c] : cc, pS = gj > 0 ? ps[r - 1][c] : cc;
-                float s = xs[r][c + 1] * (pE - cc);
-                s -= xs[r][c] * (cc - pW);
+                const int xc = c + xoff[r];
+                float s = xs[r][xc + 1] * (pE - cc);
+                s -= xs[r][xc] * (cc - pW);
                 s += ys[r + 1][c] * (pN - cc);
                 s -= ys[r][c] * (cc - pS);
                 return bs[r][c] - s * ih2;
@@ -373,14 +401,13 @@ __global__ void k_coarsen_beta(int nx, int ny, const double *__restrict__ bx,
 // row) from the finer level (mean of the two fine faces; at level 0 the
 // caller's faces with the walls set to zero), their FP32 copies, and the FP64
 // and FP32 inverse diagonals (the cell's four faces, recomputed locally).
-__global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
-                               const double *__restrict__ fby, double *__restrict__ bx,
-                               double *__restrict__ by, float *__restrict__ bxf,
-                               float *__restrict__ byf, double *__restrict__ invd,
-                               float *__restrict__ invdf)
+__device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, int i, int j,
+                                                  const double *__restrict__ fbx,
+                                                  const double *__restrict__ fby,
+                                                  double *__restrict__ bx, double *__restrict__ by,
+                                                  float *__restrict__ bxf, float *__restrict__ byf,
+                                                  double *__restrict__ invd, float *__restrict__ invdf)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i >= nx) return;
     const int fnx = 2 * nx;  // finer level width (unused at level 0)
     auto xface = [&](int I, int J) -> double {   // coefficient of x-face (I, J)
         if (I == 0 || I == nx) return 0.0;
@@ -399,9 +426,43 @@ __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restr
     if (i == nx - 1) { bx[kx + 1] = e; bxf[kx + 1] = (float)e; }
     if (j == ny - 1) { by[kc + nx] = n; byf[kc + nx] = (float)n; }
     const double d = e + w + n + s;
-    const double id = d > 0.0 ? 1.0 / d : 0.0;
+    const double id = d > 0.0 ? recip_nr(d) : 0.0;
     invd[kc] = id;
     invdf[kc] = (float)id;
+}
+
+__global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
+                               const double *__restrict__ fby, double *__restrict__ bx,
+                               double *__restrict__ by, float *__restrict__ bxf,
+                               float *__restrict__ byf, double *__restrict__ invd,
+                               float *__restrict__ invdf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    level_coeffs_cell(nx, ny, level0, i, j, fbx, fby, bx, by, bxf, byf, invd, invdf);
+}
+
+// The small levels (from `first` on) in one CTA, level after level; a level
+// reads the faces the previous one wrote (same block: visible after the
+// barrier).
+struct LevelCoeffArgs {
+    int first, nl;
+    int nx[16], ny[16];
+    double *bx[16], *by[16], *invd[16];
+    float *bxf[16], *byf[16], *invdf[16];
+};
+
+__global__ void __launch_bounds__(1024) k_level_coeffs_small(LevelCoeffArgs a)
+{
+    for (int l = a.first; l < a.nl; l++) {
+        const int nx = a.nx[l], ny = a.ny[l];
+        for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
+            const int j = k / nx, i = k - j * nx;
+            level_coeffs_cell(nx, ny, l == 0, i, j, a.bx[l - 1], a.by[l - 1], a.bx[l], a.by[l], a.bxf[l],
+                              a.byf[l], a.invd[l], a.invdf[l]);
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------ coarsest solve
@@ -1187,13 +1248,29 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 {
     const int L = mg.L;
-    for (int l = 0; l < L; l++) {
+    // levels above 4096 cells one launch each, the rest in one CTA
+    int lsmall = 1;
+    while (lsmall < L && (long)mg.lv[lsmall].nx * mg.lv[lsmall].ny > 4096) lsmall++;
+    for (int l = 0; l < lsmall; l++) {
         Level &v = mg.lv[l];
         const double *fbx = l == 0 ? bx : mg.lv[l - 1].d.bx, *fby = l == 0 ? by : mg.lv[l - 1].d.by;
         dim3 g(cdiv(v.nx, 128), v.ny);
         note_launch();
         k_level_coeffs<<<g, 128, 0, s>>>(v.nx, v.ny, l == 0, fbx, fby, v.d.bx, v.d.by, v.f.bx, v.f.by,
                                          v.d.invd, v.f.invd);
+    }
+    if (lsmall < L) {
+        LevelCoeffArgs a;
+        a.first = lsmall;
+        a.nl = L;
+        for (int l = 0; l < L; l++) {
+            Level &v = mg.lv[l];
+            a.nx[l] = v.nx; a.ny[l] = v.ny;
+            a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd;
+            a.bxf[l] = v.f.bx; a.byf[l] = v.f.by; a.invdf[l] = v.f.invd;
+        }
+        note_launch();
+        k_level_coeffs_small<<<1, 1024, 0, s>>>(a);
     }
     {
         // shared memory of the single-CTA tail (set here, outside any capture)
@@ -1219,8 +1296,8 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     const size_t cbytes = 2 * nc2 * sizeof(double);
     const int in_smem = cbytes <= 96 * 1024;
     if (in_smem) cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
-    k_coarse_inv<<<1, 1024, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
-                                                       mg.lu + nc2, in_smem);
+    k_coarse_inv<<<1, 256, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
+                                                      mg.lu + nc2, in_smem);
 }
 
 // Host-driven solve: one launch per kernel and a host read of the residual
