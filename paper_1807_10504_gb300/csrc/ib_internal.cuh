@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of the library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,11 +71,27 @@ struct LevelT {
     T *e2 = nullptr;  // second iterate buffer: sweeps read one and write the other
 };
 
+// Tensor maps (TMA descriptors) of one fused FP32 smoother launch: windows of
+// the iterate read, the right-hand side, 1/diag and beta_y, and the word that
+// a timed-out staging wait sets.
+struct TileMaps {
+    CUtensorMap p, b, d, y;
+    int *fault;
+};
+
+// A level's FP32 smoother maps for one window shape (both iterate buffers).
+struct LevelTma {
+    CUtensorMap e, e2, r, invd, by;
+};
+
 struct Level {
     int nx = 0, ny = 0;
     double h = 0;
     LevelT<double> d;
     LevelT<float> f;
+    bool tma = false;  // tm[] valid: the FP32 smoother stages by TMA on this level
+    LevelTma tm[2];    // [0] 72 x 24 windows (halo 4), [1] 80 x 26 windows (halo 5)
+    int *fault = nullptr;
 };
 
 struct SolveCtl {
@@ -83,7 +100,7 @@ struct SolveCtl {
     int cycles;
     double rr;
     int zero_p;
-    int pad;
+    int fault;  // set by a kernel whose bounded wait timed out
 };
 
 struct SolveGraph {

@@ -30,7 +30,9 @@
 //  * the FP32 instantiations of the same kernels form the inner cycle of the
 //    defect-correction solve; the residual, the update and the coarsest
 //    solve stay FP64.
+#include <cudaTypedefs.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <atomic>
@@ -147,85 +149,110 @@ __device__ __forceinline__ void cp_async4(void *d, const void *src, bool v)
                  "l"(src), "r"(v ? 4 : 0));
 }
 
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Bounded wait for phase 0 of a shared-memory barrier; false on time-out.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long *bar)
+{
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 22) && !done; it++)
+        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, P;\n}\n"
+                     : "=r"(done) : "r"(smem_addr(bar)) : "memory");
+    return done != 0;
+}
+
+// One 2-D tensor copy global -> shared completing on `bar`; the box (set in
+// the map) lands densely, row-major, at dst; cells outside the array read 0.
+__device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, int x, int y,
+                                          unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
+}
+
 // Two red-black sweeps in one launch (FP32 inner cycle), staged in shared
-// memory by asynchronous copies issued before the first wait; the sweeps run
-// from shared memory on shrinking rings (red, black, red, black) so that the
-// tile's result equals two global sweeps.  MODE 0: the sweeps alone (halo 4).
-// MODE 1: the sweeps, then the residual b - A p of the tile's cells averaged
-// over 2x2 children into the coarse right-hand side (coarse correction set
-// to zero); the last black phase also covers the tile's one-cell ring so
-// that the residual sees final neighbours (halo 5).  MODE 2: p + P e_c (the
-// bilinear prolongation of the coarse correction) is formed while staging,
-// then the sweeps (halo 4).  Each mode equals the separate kernels in turn.
+// memory; the sweeps run from shared memory on shrinking rings (red, black,
+// red, black) so that the tile's result equals two global sweeps.  MODE 0:
+// the sweeps alone (halo 4).  MODE 1: the sweeps, then the residual b - A p
+// of the tile's cells averaged over 2x2 children into the coarse right-hand
+// side (coarse correction set to zero); the last black phase also covers the
+// tile's one-cell ring so that the residual sees final neighbours (halo 5).
+// MODE 2: p + P e_c (the bilinear prolongation of the coarse correction) is
+// formed while staging, then the sweeps (halo 4).  Each mode equals the
+// separate kernels in turn.
+// Staging: with TMA (widths that are a multiple of 4), one thread issues
+// tensor copies of the iterate, right-hand side, 1/diag and beta_y windows
+// (zero outside the grid) onto one barrier while all threads copy the x-face
+// rows (rows of nx + 1 faces are not 16-byte aligned, so no tensor map
+// describes them) with 16-byte asynchronous copies; otherwise every array
+// goes through asynchronous copies.  A barrier wait that times out records
+// tm.fault and the block skips its tile.
 // The iterate is read from pin and the tile written to p (a different
 // buffer): blocks read their neighbours' tiles as halo, so an in-place update
 // would let a block see values another block has already smoothed.
-template <int MODE>
+template <int MODE, bool TMA>
 __global__ void __launch_bounds__(FT)
 k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
               const float *__restrict__ by, const float *__restrict__ invd,
               const float *__restrict__ b, const float *__restrict__ pin, float *__restrict__ p,
-              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp)
+              float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp,
+              const __grid_constant__ TileMaps tm)
 {
     pdl_enter();
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
     constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
     constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA;
-    __shared__ __align__(16) float ps[PH][PW];
-    __shared__ __align__(16) float bs[PH][PW];
-    __shared__ __align__(16) float ds[PH][PW];
-    __shared__ __align__(16) float ys[PH + 1][PW];
+    __shared__ __align__(128) float ps[PH][PW];
+    __shared__ __align__(128) float bs[PH][PW];
+    __shared__ __align__(128) float ds[PH][PW];
+    __shared__ __align__(128) float ys[PH + 1][PW];
     // x-faces: row r holds the faces gi0 .. gi0 + PW from column xoff[r] on
     // (the 16-byte-aligned copy of a row of (nx + 1) faces starts up to three
     // faces early)
     __shared__ __align__(16) float xs[PH][PW + 8];
     __shared__ int xoff[PH];
+    __shared__ __align__(8) unsigned long long bar;
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
     const long nxf = nx + 1;
     const int nxc = nx / 2, nyc = ny / 2;
-    // p + P e_c at fine cell (gi, gj) (MODE 2)
-    auto pro = [&](int gi, int gj) {
+    // P e_c at fine cell (gi, gj) (MODE 2)
+    auto cor = [&](int gi, int gj) {
         const int I = gi >> 1, J = gj >> 1;
         const int I2 = min(max(I + ((gi & 1) ? 1 : -1), 0), nxc - 1);
         const int J2 = min(max(J + ((gj & 1) ? 1 : -1), 0), nyc - 1);
         const float c00 = ecp[(long)J * nxc + I], c10 = ecp[(long)J * nxc + I2];
         const float c01 = ecp[(long)J2 * nxc + I], c11 = ecp[(long)J2 * nxc + I2];
-        return pin[(long)gj * nx + gi] + (9.0f * c00 + 3.0f * c10 + 3.0f * c01 + c11) * 0.0625f;
+        return (9.0f * c00 + 3.0f * c10 + 3.0f * c01 + c11) * 0.0625f;
     };
-    const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
-    if (vec) {
-        constexpr int V = PW / 4;  // float4 per row
-        for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
-            const int r = k / V, c4 = k - r * V, gj = gj0 + r;
-            const long o = (long)gj * nx + gi0 + 4 * c4;
-            if (r < PH) {
-                const bool in = gj >= 0 && gj < ny;
-                if (MODE == 2) {
-                    for (int q = 0; q < 4; q++) ps[r][4 * c4 + q] = in ? pro(gi0 + 4 * c4 + q, gj) : 0.0f;
-                } else {
-                    cp_async16(&ps[r][4 * c4], in ? pin + o : pin, in);
-                }
-                cp_async16(&bs[r][4 * c4], in ? b + o : b, in);
-                cp_async16(&ds[r][4 * c4], in ? invd + o : invd, in);
-            }
-            const bool iny = gj >= 0 && gj <= ny;
-            cp_async16(&ys[r][4 * c4], iny ? by + o : by, iny);
+    auto pro = [&](int gi, int gj) { return pin[(long)gj * nx + gi] + cor(gi, gj); };
+    if constexpr (TMA) {
+        // tensor copies land on 128-byte boundaries (checked, not assumed)
+        if (((smem_addr(&ps[0][0]) | smem_addr(&bs[0][0]) | smem_addr(&ds[0][0]) |
+              smem_addr(&ys[0][0])) & 127u) != 0) {
+            if (threadIdx.x == 0) *tm.fault = 2;
+            return;
         }
-    } else {
-        for (int k = threadIdx.x; k < (PH + 1) * PW; k += FT) {
-            const int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
-            const long o = (long)gj * nx + gi;
-            if (r < PH) {
-                const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-                ps[r][c] = in ? (MODE == 2 ? pro(gi, gj) : pin[o]) : 0.0f;
-                bs[r][c] = in ? b[o] : 0.0f;
-                ds[r][c] = in ? invd[o] : 0.0f;
-            }
-            ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[o] : 0.0f;
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)));
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         }
-    }
-    if (vec) {
-        constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per row, worst alignment
+        __syncthreads();  // the barrier is initialised before any thread waits on it
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::);
+            constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                         ::"r"(smem_addr(&bar)), "r"(kBytes));
+            tma_load2(&ps[0][0], &tm.p, gi0, gj0, &bar);
+            tma_load2(&bs[0][0], &tm.b, gi0, gj0, &bar);
+            tma_load2(&ds[0][0], &tm.d, gi0, gj0, &bar);
+            tma_load2(&ys[0][0], &tm.y, gi0, gj0, &bar);
+        }
+        constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per x-face row, worst alignment
         const long nbx = nxf * ny;
         for (int k = threadIdx.x; k < PH * NC; k += FT) {
             const int r = k / NC, q = k - r * NC, gj = gj0 + r;
@@ -237,22 +264,105 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
             if (q == 0) xoff[r] = (int)(start - a0);
             const long e0 = a0 + 4 * q;
-            if (e0 + 4 <= nbx) {
+            const int c0 = (int)(e0 - start);  // window column of face e0
+            if (e0 >= 0 && e0 + 4 <= nbx && gi0 + c0 >= 0 && gi0 + c0 + 3 <= nx) {
                 cp_async16(&xs[r][4 * q], bx + e0, true);
             } else {
-                for (int t = 0; t < 4; t++) cp_async4(&xs[r][4 * q + t], bx + (e0 + t < nbx ? e0 + t : 0), e0 + t < nbx);
+                for (int t = 0; t < 4; t++) {
+                    const int gi = gi0 + c0 + t;
+                    const bool ok = gi >= 0 && gi <= nx;
+                    cp_async4(&xs[r][4 * q + t], ok ? bx + e0 + t : bx, ok);
+                }
             }
         }
-    } else {
-        for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
-            const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
-            const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj < ny;
-            cp_async4(&xs[r][c], in ? bx + (long)gj * nxf + gi : bx, in);
-            if (c == 0) xoff[r] = 0;
+        // the prolongation of the coarse correction overlaps the copies
+        constexpr int NPRO = MODE == 2 ? (PH * PW + FT - 1) / FT : 1;
+        float pc[NPRO];
+        if constexpr (MODE == 2) {
+#pragma unroll
+            for (int i = 0; i < NPRO; i++) {
+                const int k = threadIdx.x + i * FT, r = k / PW, c = k - r * PW;
+                const int gi = gi0 + c, gj = gj0 + r;
+                pc[i] = (k < PH * PW && gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? cor(gi, gj) : 0.0f;
+            }
         }
+        asm volatile("cp.async.wait_all;\n" ::);
+        if (!mbar_wait0(&bar)) {
+            *tm.fault = 1;
+            mbar_wait0(&bar);  // copies still in flight land before the block leaves
+            return;
+        }
+        if constexpr (MODE == 2) {
+#pragma unroll
+            for (int i = 0; i < NPRO; i++) {
+                const int k = threadIdx.x + i * FT, r = k / PW, c = k - r * PW;
+                if (k < PH * PW) ps[r][c] += pc[i];
+            }
+        }
+        __syncthreads();
+    } else {
+        const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
+        if (vec) {
+            constexpr int V = PW / 4;  // float4 per row
+            for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
+                const int r = k / V, c4 = k - r * V, gj = gj0 + r;
+                const long o = (long)gj * nx + gi0 + 4 * c4;
+                if (r < PH) {
+                    const bool in = gj >= 0 && gj < ny;
+                    if (MODE == 2) {
+                        for (int q = 0; q < 4; q++) ps[r][4 * c4 + q] = in ? pro(gi0 + 4 * c4 + q, gj) : 0.0f;
+                    } else {
+                        cp_async16(&ps[r][4 * c4], in ? pin + o : pin, in);
+                    }
+                    cp_async16(&bs[r][4 * c4], in ? b + o : b, in);
+                    cp_async16(&ds[r][4 * c4], in ? invd + o : invd, in);
+                }
+                const bool iny = gj >= 0 && gj <= ny;
+                cp_async16(&ys[r][4 * c4], iny ? by + o : by, iny);
+            }
+        } else {
+            for (int k = threadIdx.x; k < (PH + 1) * PW; k += FT) {
+                const int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
+                const long o = (long)gj * nx + gi;
+                if (r < PH) {
+                    const bool in = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+                    ps[r][c] = in ? (MODE == 2 ? pro(gi, gj) : pin[o]) : 0.0f;
+                    bs[r][c] = in ? b[o] : 0.0f;
+                    ds[r][c] = in ? invd[o] : 0.0f;
+                }
+                ys[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? by[o] : 0.0f;
+            }
+        }
+        if (vec) {
+            constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per row, worst alignment
+            const long nbx = nxf * ny;
+            for (int k = threadIdx.x; k < PH * NC; k += FT) {
+                const int r = k / NC, q = k - r * NC, gj = gj0 + r;
+                if (gj < 0 || gj >= ny) {
+                    cp_async16(&xs[r][4 * q], bx, false);
+                    if (q == 0) xoff[r] = 0;
+                    continue;
+                }
+                const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
+                if (q == 0) xoff[r] = (int)(start - a0);
+                const long e0 = a0 + 4 * q;
+                if (e0 + 4 <= nbx) {
+                    cp_async16(&xs[r][4 * q], bx + e0, true);
+                } else {
+                    for (int t = 0; t < 4; t++) cp_async4(&xs[r][4 * q + t], bx + (e0 + t < nbx ? e0 + t : 0), e0 + t < nbx);
+                }
+            }
+        } else {
+            for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
+                const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
+                const bool in = gi >= 0 && gi <= nx && gj >= 0 && gj < ny;
+                cp_async4(&xs[r][c], in ? bx + (long)gj * nxf + gi : bx, in);
+                if (c == 0) xoff[r] = 0;
+            }
+        }
+        asm volatile("cp.async.wait_all;\n" ::);
+        __syncthreads();
     }
-    asm volatile("cp.async.wait_all;\n" ::);
-    __syncthreads();
     // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q)
     constexpr int Q0 = HA - 1;  // outermost ring updated
 #pragma unroll
@@ -911,6 +1021,33 @@ __global__ void k_finalize(long n, const double *__restrict__ e0, const double *
 template <typename T>
 T *other(LevelT<T> &a, T *cur) { return cur == a.e ? a.e2 : a.e; }
 
+// One fused FP32 smoother launch of MODE on level v: reads the iterate from
+// pin (one of the level's two buffers) and writes p; stages by TMA where the
+// level has tensor maps.
+template <int MODE>
+void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, float *p,
+                    float *rc, float *ecz, const float *ecp, cudaStream_t s)
+{
+    dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
+    const float h2 = (float)(v.h * v.h), ih2 = MODE == 1 ? (float)(1.0 / (v.h * v.h)) : 0.0f;
+    TileMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    note_launch();
+    if (v.tma && (pin == a.e || pin == a.e2)) {
+        const LevelTma &w = v.tm[MODE == 1 ? 1 : 0];
+        tm.p = pin == a.e ? w.e : w.e2;
+        tm.b = w.r;
+        tm.d = w.invd;
+        tm.y = w.by;
+        tm.fault = v.fault;
+        launch_pdl(k_smooth2_f32<MODE, true>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by, a.invd,
+                   a.r, pin, p, rc, ecz, ecp, tm);
+    } else {
+        launch_pdl(k_smooth2_f32<MODE, false>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by,
+                   a.invd, a.r, pin, p, rc, ecz, ecp, tm);
+    }
+}
+
 // nsw sweeps on one level, reading the iterate from cur and leaving it in the
 // returned buffer: FP32 in fused pairs, FP64 one sweep per launch (the FP64
 // sweep is bound by the FP64 pipe, where fusing only adds halo work).
@@ -920,15 +1057,11 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
     const T h2 = (T)(v.h * v.h);
     int k = 0;
     if constexpr (sizeof(T) == 4) {
-        dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
         for (; k + 2 <= nsw; k += 2) {
             const bool pr = fine && prof_on(kProfSweep32);
             if (pr) prof_mark(s, true);
-            note_launch();
             T *nxt = other(a, cur);
-            launch_pdl(k_smooth2_f32<0>, g2, FT, 0, s, v.nx, v.ny, h2, 0.0f, a.bx, a.by, a.invd, a.r,
-                       (const float *)cur, nxt, (float *)nullptr, (float *)nullptr,
-                       (const float *)nullptr);
+            launch_smooth2<0>(v, a, cur, nxt, nullptr, nullptr, nullptr, s);
             cur = nxt;
             if (pr) prof_mark(s, false);
         }
@@ -969,14 +1102,10 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
         LevelT<T> &a = lvT(l), &c = lvT(l + 1);
         if (fused) {
             if constexpr (f32) {
-                dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
                 const bool pr = l == 0 && prof_on(kProfSweep32);
                 if (pr) prof_mark(s, true);
-                note_launch();
                 T *nxt = other(a, cur[l]);
-                launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
-                           (float)(1.0 / (v.h * v.h)), a.bx, a.by, a.invd, a.r,
-                           (const float *)cur[l], nxt, c.r, c.e, (const float *)nullptr);
+                launch_smooth2<1>(v, a, cur[l], nxt, c.r, c.e, nullptr, s);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -1011,14 +1140,10 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
         LevelT<T> &a = lvT(l);
         if (fused) {
             if constexpr (f32) {
-                dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
                 const bool pr = l == 0 && prof_on(kProfSweep32);
                 if (pr) prof_mark(s, true);
-                note_launch();
                 T *nxt = other(a, cur[l]);
-                launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f,
-                           a.bx, a.by, a.invd, a.r, (const float *)cur[l], nxt, (float *)nullptr,
-                           (float *)nullptr, (const float *)cur[l + 1]);
+                launch_smooth2<2>(v, a, cur[l], nxt, nullptr, nullptr, cur[l + 1], s);
                 if (pr) prof_mark(s, false);
                 cur[l] = nxt;
             }
@@ -1108,6 +1233,55 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys)
     return (long)nx * ny <= kMaxCoarsest;
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null where the driver lacks it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return fn;
+}
+
+// 2-D map of a row-major FP32 array of w x hgt values with a bw x bh box
+// (no swizzle, zero fill outside the array).
+static bool map2d(CUtensorMap *m, const float *base, int w, int hgt, int bw, int bh)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || w < bw || hgt < bh || (w & 3) != 0 || ((uintptr_t)base & 15) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)hgt};
+    const cuuint64_t strides[1] = {(cuuint64_t)w * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh}, es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of a level's FP32 smoother operands for both window shapes
+// (FW + 2 XO) x (FH + 2 HA) with (XO, HA) = (4, 4) and (8, 5); beta_y windows
+// have one more row.  Needs rows of a multiple of 4 values (16-byte strides).
+static bool encode_level_maps(Level &v)
+{
+    const LevelT<float> &a = v.f;
+    for (int k = 0; k < 2; k++) {
+        const int bw = FW + 2 * (k ? 8 : 4), bh = FH + 2 * (k ? 5 : 4);
+        LevelTma &w = v.tm[k];
+        if (!map2d(&w.e, a.e, v.nx, v.ny, bw, bh) || !map2d(&w.e2, a.e2, v.nx, v.ny, bw, bh) ||
+            !map2d(&w.r, a.r, v.nx, v.ny, bw, bh) || !map2d(&w.invd, a.invd, v.nx, v.ny, bw, bh) ||
+            !map2d(&w.by, a.by, v.nx, v.ny + 1, bw, bh + 1))
+            return false;
+    }
+    return true;
+}
+
 size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
 {
     int nxs[16], nys[16], L = 0;
@@ -1142,6 +1316,11 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
     mg.red = (double *)take((size_t)(mg.red_blocks + 16) * 8);
     mg.red_count = (unsigned *)take(64);
     mg.ctl = (SolveCtl *)take(sizeof(SolveCtl));
+    for (int l = 0; l < L; l++) {
+        Level &v = mg.lv[l];
+        v.fault = base ? &mg.ctl->fault : nullptr;
+        v.tma = base && encode_level_maps(v);
+    }
     int t = 0;
     while (t < L && (long)nxs[t] * nys[t] > kTailCells) t++;
     mg.tail = std::min(t, L - 1);
@@ -1195,24 +1374,17 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
     if (level < 0 || level >= mg.L) return -1;
     Level &v = mg.lv[level];
     const long cells = (long)v.nx * v.ny;
-    dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
     switch (op) {
     case 0: smooth<float>(v, v.f, v.f.e, 2, false, s); return cells;
     case 1: smooth<double>(v, v.d, v.d.e, 1, false, s); return cells;
     case 3:
         if (level >= mg.tail_f) return -1;
-        note_launch();
-        launch_pdl(k_smooth2_f32<1>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h),
-                   (float)(1.0 / (v.h * v.h)), v.f.bx, v.f.by, v.f.invd, v.f.r,
-                   (const float *)v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
-                   (const float *)nullptr);
+        launch_smooth2<1>(v, v.f, v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
+                          nullptr, s);
         return cells;
     case 4:
         if (level >= mg.tail_f) return -1;
-        note_launch();
-        launch_pdl(k_smooth2_f32<2>, g2, FT, 0, s, v.nx, v.ny, (float)(v.h * v.h), 0.0f, v.f.bx,
-                   v.f.by, v.f.invd, v.f.r, (const float *)v.f.e, v.f.e2, (float *)nullptr,
-                   (float *)nullptr, (const float *)mg.lv[level + 1].f.e);
+        launch_smooth2<2>(v, v.f, v.f.e, v.f.e2, nullptr, nullptr, mg.lv[level + 1].f.e, s);
         return cells;
     case 5: {
         const int lt = mg.tail_f, L = mg.L;
@@ -1361,8 +1533,11 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
         k_sum<<<RB, kRedT, 0, s>>>(n, e0, part, mg.red_count, res + 3);
         note_launch();
         k_apply_mean<<<cdiv(n, 256), 256, 0, s>>>(n, e0, res + 3, p);
-        ce = cudaGetLastError();
+        int fault = 0;  // pageable landing (the no-allocation solve has no pinned control block)
+        ce = cudaMemcpyAsync(&fault, &mg.ctl->fault, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
+        if (fault) { err = "a smoother's staging wait timed out"; return IB_ECUDA; }
         if (!isfinite(rr)) { st = IB_ENAN; err = "non-finite residual"; }
         else if (rr > tol) { st = IB_ENOTCONV; err = "cycle cap reached above tolerance"; }
     }
@@ -1499,6 +1674,7 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
     if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { err = cudaGetErrorString(e); return IB_ECUDA; }
+    if (mg.ctl_host->fault) { err = "a smoother's staging wait timed out"; return IB_ECUDA; }
     const int c = mg.ctl_host->cycles;
     const double rr = mg.ctl_host->rr;
     note_launch((int)(sg->outer_kernels + (unsigned long long)c * sg->body_kernels));

@@ -46,9 +46,12 @@ extern "C" ib_status mg_solve_noalloc(int32_t nx, int32_t ny, double h, const do
     cudaStream_t s = (cudaStream_t)stream;
     ibk::mg_layout(g_mg, nx, ny, h, (char *)g_scratch_dev[dev]);
     g_mg.red_host = g_read_back;
-    // the reduction's block counter must start at zero; everything else in the
-    // scratch is written before it is read
-    if (cudaMemsetAsync(g_mg.red_count, 0, 64, s) != cudaSuccess) return IB_ECUDA;
+    // the reduction's block counter and the control block (its fault word)
+    // must start at zero; everything else in the scratch is written before it
+    // is read
+    if (cudaMemsetAsync(g_mg.red_count, 0, 64, s) != cudaSuccess ||
+        cudaMemsetAsync(g_mg.ctl, 0, sizeof(ibk::SolveCtl), s) != cudaSuccess)
+        return IB_ECUDA;
     ibk::mg_build(g_mg, bx, by, s);
     if (cudaGetLastError() != cudaSuccess) return IB_ECUDA;
     return ibk::mg_run_direct(g_mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles_out,
