@@ -122,6 +122,41 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_source(rel, name):
+    """The text of kernel `name` in source file `rel` (its signature line to
+    the first closing brace in column 0) and the file's compile-time integer
+    constants, which set its tiles."""
+    with open(os.path.join(ROOT, rel)) as f:
+        lines = f.read().split("\n")
+    start = next(i for i, ln in enumerate(lines)
+                 if ln.startswith(name + "(") or ("__global__" in ln and " " + name + "(" in ln))
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    consts = [ln for ln in lines if ln.lstrip().startswith("constexpr int")]
+    return "\n".join(consts + lines[start:end + 1])
+
+
+def source_sha(rel, name):
+    import hashlib
+    return hashlib.sha256(kernel_source(rel, name).encode()).hexdigest()
+
+
+def traffic_per_launch(kernel, cells):
+    """DRAM bytes (read + write) of one launch over `cells` cells, from the
+    per-cell figure of an ncu capture recorded in profiles/traffic.json; None
+    when the kernel's source file has changed since that capture."""
+    try:
+        with open(TRAFFIC) as f:
+            rec = json.load(f)[kernel]
+        if source_sha(rec["source"], rec["function"]) != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_cell"] * cells
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def cpu_baseline(name, steps=1):
     import oracle as O
     O.build()
@@ -235,7 +270,7 @@ def run_ours(args):
         ctx.close()
         return 0
 
-    sweep_kind = ib.PROF_SWEEP32 if args.precision == 1 else ib.PROF_SWEEP64
+    sweep_kind = ib.PROF_SWEEP32 if args.precision >= 1 else ib.PROF_SWEEP64
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     cycles = []
@@ -269,7 +304,7 @@ def run_ours(args):
     b = ctx.get("b")
     solve = {}
     pk, pk_kind = peaks()
-    for prec, label in ((0, "fp64"), (1, "mixed")):
+    for prec, label in ((0, "fp64"), (1, "mixed"), (2, "mixed2")):
         times, cyc = [], None
         for rep in range(3 + 5):
             p = torch.zeros((n, n), dtype=torch.float64, device="cuda")
@@ -304,14 +339,19 @@ def run_ours(args):
     t_res, _ = ctx.bench_kernel(6, 20)
     kernel_table = {"levels": levels, "fp32_tail_us": t_tail, "fp32_tail_first_level_cells": int(c_tail),
                     "fp64_residual_norm_us": t_res}
-    # algorithmic bytes per fine cell: read p, b, beta_x, beta_y (16) and the
-    # coarse correction (4 B per 4 cells), write p (4)
-    ach32 = 21.0 * cells / (us32 * 1e-6) / 1e9
-    ach64 = 40.0 * cells / (us64 * 1e-6) / 1e9
-    roof64 = {"kernel": "k_rbgs_sweep<double> (fine level, one red-black sweep)", "bound": "hbm",
+    # algorithmic bytes per fine cell.  FP32 prolongation + sweeps at level 0
+    # (defect correction): read the FP32 iterate, b, 1/diag, beta_x, beta_y
+    # (20) and the coarse correction (4 B per 4 cells), read and write the
+    # FP64 iterate (16).  FP64 sweep on the pre-scaled stencil: read p, bt
+    # (16) and the four weights (32), write p (8).
+    B32, B64 = 37.0, 56.0
+    ach32 = B32 * cells / (us32 * 1e-6) / 1e9
+    ach64 = B64 * cells / (us64 * 1e-6) / 1e9
+    roof64 = {"kernel": "k_rbgs_sweep_w (fine level, one FP64 red-black sweep)", "bound": "hbm",
               "achieved": ach64, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": ach64 / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
-              "avg_launch_us": us64, "algorithmic_bytes_per_cell": 40}
+              "frac": ach64 / pk["hbm_gbs"], "traffic": traffic_per_launch("k_rbgs_sweep_w", cells),
+              "peak_source": pk_kind, "avg_launch_us": us64, "algorithmic_bytes_per_cell": B64,
+              "algorithmic_bytes": B64 * cells}
     band = {"kernel": "k_band_area", "avg_launch_us": usb, "pairs": int(pairs),
             "ns_per_pair": 1e3 * usb / max(pairs, 1)}
 
@@ -334,18 +374,19 @@ def run_ours(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             p = net.infer(b[None], rho[None])[0]
-            st, cyc, rr = ctx.mg_solve(b, p, 1, 1e-10, 200)
+            st, cyc, rr = ctx.mg_solve(b, p, 2, 1e-10, 200)
             e1.record(stream)
             torch.cuda.synchronize()
             if rep >= 3:
                 times.append(e0.elapsed_time(e1))
         solve["mixed_cnn"] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr,
+                              "solver": "mixed2 (two FP32 V-cycles per FP64 residual)",
                               "inference_grid": n >> args.cnn_coarsen,
                               "train": {"samples": args.cnn_samples, "steps": len(losses),
                                         "final_loss": losses[-1], "seconds": train_s}}
         del net
     solve["speedup_vs_fp64"] = {k: solve["fp64"]["ms"] / solve[k]["ms"]
-                                for k in ("mixed", "mixed_cnn") if k in solve}
+                                for k in ("mixed", "mixed2", "mixed_cnn") if k in solve}
 
     # end to end through the C ABI with host buffers: markers in, pressure out
     Xh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
@@ -368,12 +409,14 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32" if args.precision == 1 else "f64", "data": "synthetic",
+        "dtype": "f64+f32" if args.precision >= 1 else "f64", "data": "synthetic",
         "config": {"workload": name, "nx": n, "ny": n, "drops": int(mk.ndrops),
                    "markers": int(mk.M), "density_ratio": 1000, "viscosity_ratio": 100,
                    "spread": "irrotational", "relocate_every": 10, "tol": 1e-10,
-                   "solver": ("FP32 V(2,2) in FP64 defect correction" if args.precision == 1
-                              else "FP64 V(2,2)"),
+                   "solver": {0: "FP64 V(2,2)",
+                              1: "FP32 V(2,2) in FP64 defect correction",
+                              2: "FP32 V(2,2), two per FP64 residual, in FP64 defect correction"
+                              }[args.precision],
                    "warm_start": "previous pressure", "l2": "flushed before each step (256 MiB)",
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
@@ -382,15 +425,18 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(2 * ctx.M * 8),
                 "d2h_bytes_per_step": int(n * n * 8 + 2 * ctx.M * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": ("k_smooth2_f32<2> (fine level: prolongation + two FP32 red-black sweeps)"
-                                if args.precision == 1 else
-                                "k_rbgs_sweep<double> (fine level, one red-black sweep)"),
-                     "bound": "hbm", "achieved": ach32 if args.precision == 1 else ach64,
+        "roofline": {"kernel": ("k_smooth2_f32<2> (fine level: prolongation + two FP32 red-black "
+                                "sweeps + FP64 update)" if args.precision >= 1 else
+                                "k_rbgs_sweep_w (fine level, one FP64 red-black sweep)"),
+                     "bound": "hbm", "achieved": ach32 if args.precision >= 1 else ach64,
                      "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": (ach32 if args.precision == 1 else ach64) / pk["hbm_gbs"],
-                     "traffic": None, "peak_source": pk_kind,
-                     "avg_launch_us": us32 if args.precision == 1 else us64,
-                     "algorithmic_bytes_per_cell": 21.0 if args.precision == 1 else 40.0,
+                     "frac": (ach32 if args.precision >= 1 else ach64) / pk["hbm_gbs"],
+                     "traffic": traffic_per_launch("k_smooth2_f32<2>" if args.precision >= 1
+                                                   else "k_rbgs_sweep_w", cells),
+                     "peak_source": pk_kind,
+                     "avg_launch_us": us32 if args.precision >= 1 else us64,
+                     "algorithmic_bytes_per_cell": B32 if args.precision >= 1 else B64,
+                     "algorithmic_bytes": (B32 if args.precision >= 1 else B64) * cells,
                      "cells_per_launch": int(cells),
                      "timing": "50 back-to-back launches on the step's fine-level data, "
                                "CUDA events on the launching stream",
@@ -419,7 +465,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="multidrop1024", choices=list(WORKLOADS))
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned warm start")
     ap.add_argument("--cnn-samples", type=int, default=800)

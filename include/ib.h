@@ -52,9 +52,12 @@ typedef struct ib_config {
     int32_t spread;           /* 0: conventional, Sec. 3.1 Eq. (delta_vec);
                                  1: irrotational, Sec. 3.2 Eq. (delta_hea_xy) */
     int32_t precision;        /* 0: FP64 multigrid; 1: FP32 V-cycles inside FP64
-                                 defect correction (residual, coarsest solve FP64) */
+                                 defect correction (residual, coarsest solve FP64),
+                                 one V-cycle per FP64 residual; 2: the same with
+                                 two V-cycles per FP64 residual */
     double tol;               /* relative residual ||b - A p||_2 / ||b||_2 */
-    int32_t max_cycles;       /* V-cycles (or outer iterations) per solve */
+    int32_t max_cycles;       /* V-cycles per solve (tested before each outer
+                                 step: precision 2 may pass it by one) */
     int32_t nu1, nu2;         /* pre/post red-black Gauss-Seidel sweeps */
     int32_t relocate_every;   /* B-spline relocation period in steps, 0 = never */
 } ib_config;
@@ -137,8 +140,11 @@ ib_status mg_setup(ib_ctx *ctx, const double *bx, const double *by);
 
 /* Solve div(beta grad p) = rhs - mean(rhs) with the coefficients of the last
  * mg_setup (or ns_step) to ||b - A p||_2 <= tol ||b||_2 by V(nu1,nu2)
- * cycles (precision 0) or FP64 defect correction around FP32 V-cycles
- * (precision 1); p (device cell array) is the initial guess on entry and
+ * cycles (precision 0) or FP64 defect correction around FP32 V-cycles, one
+ * (precision 1) or two (precision 2, the second starting from the first's
+ * correction) per FP64 residual; *cycles_out counts V-cycles.  The residual,
+ * its norm, the update of p and the coarsest solve stay FP64.  p (device
+ * cell array) is the initial guess on entry and
  * the mean-zero solution on exit; rhs (device) is not modified.  cycles_out,
  * relres_out are host pointers (may be NULL).  Returns IB_ENOTCONV when the
  * cap is reached (p holds the last iterate) and IB_ENAN on a non-finite
@@ -225,12 +231,14 @@ ib_status ib_profile_end(double *total_ms, int *launches);
  * untimed launch); *us_per_launch = their mean duration, *units = the work
  * units of one launch.  which (at multigrid level `level`, 0 = finest):
  * 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps + residual +
- * restriction, 4 FP32 prolongation + sweeps (units = cells of the level);
- * 5 the FP32 single-CTA lower cycle (cells of its first level), 6 the FP64
- * residual norm of the mixed solve (cells); 2 band strip areas of the last
- * Heaviside pass (units = (cell, segment) pairs; level ignored).  Only solve
- * scratch is overwritten (second iterate buffers, coarse right-hand sides,
- * FP32 residual, norm partials) and the strip areas are recomputed: the
+ * restriction, 4 FP32 prolongation + sweeps (at level 0 with the FP64
+ * update of the defect correction, as in the solve) (units = cells of the
+ * level); 5 the FP32 single-CTA lower cycle (cells of its first level), 6 the
+ * FP64 residual norm of the mixed solve (cells); 2 band strip areas of the
+ * last Heaviside pass (units = (cell, segment) pairs; level ignored).  Only
+ * solve scratch is overwritten (second iterate buffers, coarse right-hand
+ * sides, the solver's level-0 FP64 iterate copy, FP32 residual, norm
+ * partials) and the strip areas are recomputed: the
  * context's state is unchanged.  Needs a prior solve (or, for 2, Heaviside
  * pass); IB_EINVAL if the kernel does not run at that level.              */
 ib_status ib_bench_kernel(ib_ctx *ctx, int which, int level, int reps, double *us_per_launch,

@@ -190,7 +190,7 @@ def mg_solve(bx, by, b, h, p0=None, precision=0, tol=1e-10, max_cycles=100,
     ny, nx = b.shape
     p = np.zeros((ny, nx)) if p0 is None else _f64(p0).copy()
     cyc, rel = _i(0), _d(0.0)
-    hist = np.zeros(max_cycles + 1)
+    hist = np.zeros(max_cycles + 2)
     st = lib().or_mg_solve(nx, ny, h, _f64(bx), _f64(by), _f64(b), p, precision, tol,
                            max_cycles, nu1, nu2, C.byref(cyc), C.byref(rel), hist)
     return MGResult(p, st, cyc.value, rel.value, hist[: cyc.value + 1])

@@ -380,7 +380,12 @@ static void vcycle_f(olev *L, int l, int nl, int nu1, int nu2)
 
 /* Solve A p = b - mean(b) to ||b0 - A p||_2 <= tol ||b0||_2, then remove the
  * mean of p.  precision 0: FP64 V-cycles on p.  precision 1: FP64 defect
- * correction, p += V32(b0 - A p), with the inner cycle in FP32.
+ * correction, p += V32(b0 - A p), with the inner cycle in FP32.  precision 2:
+ * the same with two FP32 V-cycles on the defect equation per FP64 residual
+ * (the second starts from the first's correction).  *cycles counts V-cycles
+ * (FP32 ones in the mixed modes); the cap is tested before each outer step,
+ * so it may be passed by one; hist (max_cycles + 2 entries) gets the relative
+ * residual after each cycle, NaN where none is formed.
  * Returns 0 converged, 3 cycle cap reached, 4 non-finite residual.          */
 int or_mg_solve(int nx, int ny, double h, const double *bx, const double *by,
                 const double *b, double *p, int precision, double tol,
@@ -435,14 +440,19 @@ int or_mg_solve(int nx, int ny, double h, const double *bx, const double *by,
                 vcycle_d(L, 0, nl, nu1, nu2);
                 memcpy(p, L[0].e, n0 * sizeof(double));
             } else {
+                int inner = precision == 2 ? 2 : 1;
                 for (size_t k = 0; k < n0; k++) { L[0].rf[k] = (float)res[k]; L[0].ef[k] = 0.0f; }
-                vcycle_f(L, 0, nl, nu1, nu2);
+                for (int q = 0; q < inner; q++) vcycle_f(L, 0, nl, nu1, nu2);
                 for (size_t k = 0; k < n0; k++) p[k] += (double)L[0].ef[k];
+                c += inner - 1;
             }
             c++;
             or_residual(nx, ny, h, bx, by, b0, p, res);
             rr = norm2_of(n0, res) / nb;
-            if (hist) hist[c] = rr;
+            if (hist) {
+                if (precision == 2) hist[c - 1] = NAN;  /* no residual between inner cycles */
+                hist[c] = rr;
+            }
         }
         double mp = mean_of(n0, p);
         for (size_t k = 0; k < n0; k++) p[k] -= mp;

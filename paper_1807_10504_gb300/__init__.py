@@ -398,11 +398,14 @@ class Net:
         estimate interpolated back); 0 = the solve grid itself."""
         _check(lib().cnn_set_coarsen(self._h, int(levels)), None, "cnn_set_coarsen")
 
-    def infer(self, rhs, rho, h=None):
+    def infer(self, rhs, rho, h=None, out=None):
+        """Pressure estimate for a batch (B, N, N) of right-hand sides and
+        densities; written to ``out`` when given (repeated calls with the same
+        arguments replay a recorded CUDA graph of the launches)."""
         torch = _torch()
         B, N = rhs.shape[0], rhs.shape[-1]
         h = 1.0 / N if h is None else h
-        p0 = torch.empty((B, N, N), dtype=torch.float64, device="cuda")
+        p0 = torch.empty((B, N, N), dtype=torch.float64, device="cuda") if out is None else out
         _check(lib().cnn_infer(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p0), _stream()),
                None, "cnn_infer")
         return p0

@@ -30,10 +30,26 @@ struct ib_ctx {
     struct ib_cnn *cnn = nullptr;   // attached warm-start network (not owned)
 };
 
+// An inference of the network recorded as a CUDA graph, keyed by every value
+// the launches bake in (pointers, sizes, the output scale and the workspace
+// it was recorded against).
+struct CnnGraph {
+    int B = 0, N = 0, coarsen = 0;
+    double h = 0, scale = 0;
+    const double *rhs = nullptr, *rho = nullptr;
+    double *p0 = nullptr;
+    const void *amem = nullptr, *cbuf = nullptr;
+    cudaGraphExec_t exec = nullptr;   // null: seen once, not recorded yet
+    unsigned long long kernels = 0;
+};
+
 struct ib_cnn {
     ibk::Cnn *n = nullptr;
     int coarsen = 0;   // inference grid = solve grid / 2^coarsen
     std::string err;
+    std::vector<CnnGraph> graphs;
+    cudaStream_t cap = nullptr;   // private stream the graphs are recorded on
+    bool no_graphs = false;
 };
 
 namespace {
@@ -44,6 +60,70 @@ ib_status fail(ib_ctx *c, ib_status st, const std::string &msg)
 {
     if (c) c->err = msg;
     return st;
+}
+
+// One inference of the network (cnn_infer_levels) on stream s.  A call whose
+// key was seen before replays a CUDA graph of the same launches (recorded on
+// the handle's private stream on the second call, once the first has sized
+// the workspace), so the ~30 small launches of a coarse-grid inference cost
+// one launch; the first call of a key, and every call if recording fails,
+// runs the launches directly.
+cudaError_t cnn_run(ib_cnn *h, int B, int N, double hs, const double *rhs, const double *rho,
+                    double *p0, cudaStream_t s)
+{
+    Cnn &n = *h->n;
+    const double scale = cnn_get_scale(n);
+    CnnGraph *g = nullptr;
+    for (auto &q : h->graphs)
+        if (q.B == B && q.N == N && q.coarsen == h->coarsen && q.h == hs && q.scale == scale &&
+            q.rhs == rhs && q.rho == rho && q.p0 == p0)
+            g = &q;
+    if (g && (g->amem != cnn_workspace_ptr(n) || g->cbuf != cnn_cbuf_ptr(n))) {
+        // the workspace moved since: forget the recording
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        g->amem = cnn_workspace_ptr(n);
+        g->cbuf = cnn_cbuf_ptr(n);
+    }
+    if (!h->no_graphs && g && !g->exec) {
+        cudaError_t e = h->cap ? cudaSuccess : cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        const unsigned long long k0 = launch_count();
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ei = cnn_infer_levels(n, B, N, hs, rhs, rho, p0, h->coarsen, h->cap);
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamEndCapture(h->cap, &gr);
+            if (e == cudaSuccess) e = ei;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+        }
+        g->kernels = launch_count() - k0;
+        note_launch(-(int)g->kernels);  // recording issues no kernel
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+            h->no_graphs = true;
+        }
+    }
+    if (!h->no_graphs && g && g->exec) {
+        note_launch((int)g->kernels);
+        return cudaGraphLaunch(g->exec, s);
+    }
+    cudaError_t e = cnn_infer_levels(n, B, N, hs, rhs, rho, p0, h->coarsen, s);
+    if (e == cudaSuccess && !g && !h->no_graphs) {
+        if (h->graphs.size() >= 8) {
+            if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        CnnGraph q;
+        q.B = B; q.N = N; q.coarsen = h->coarsen; q.h = hs; q.scale = scale;
+        q.rhs = rhs; q.rho = rho; q.p0 = p0;
+        q.amem = cnn_workspace_ptr(n);
+        q.cbuf = cnn_cbuf_ptr(n);
+        h->graphs.push_back(q);
+    }
+    return e;
 }
 
 ib_status cuda_check(ib_ctx *c, cudaError_t e, const char *what)
@@ -162,7 +242,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     const ib_config &g = *cfg;
     if (g.nx < 2 || g.ny < 2 || (long)g.nx * g.ny > (1L << 28) || !(g.h > 0) || g.nu1 < 0 ||
         g.nu2 < 0 || g.max_cycles < 0 || !(g.tol >= 0) || g.kernel < 0 || g.kernel > 1 ||
-        g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 1)
+        g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2)
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -346,7 +426,7 @@ ib_status mg_setup(ib_ctx *c, const double *bx, const double *by)
 ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, double tol,
                    int max_cycles, int *cycles_out, double *relres_out)
 {
-    if (!c || !rhs || !p || precision < 0 || precision > 1 || max_cycles < 0 || !(tol >= 0))
+    if (!c || !rhs || !p || precision < 0 || precision > 2 || max_cycles < 0 || !(tol >= 0))
         return IB_EINVAL;
     if (!c->mg_ready) return fail(c, IB_EINVAL, "mg_setup (or ns_step) has not loaded coefficients");
     int cyc = 0;
@@ -384,8 +464,7 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (st != IB_OK) return st;
         if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
         if (warm == 2) {
-            cudaError_t ce = cnn_infer_levels(*c->cnn->n, 1, g.nx, g.h, c->b, c->rho, c->p,
-                                              c->cnn->coarsen, c->s);
+            cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
             if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
         }
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
@@ -492,6 +571,9 @@ void cnn_destroy(ib_cnn *h)
 {
     if (!h) return;
     cudaDeviceSynchronize();
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (h->cap) cudaStreamDestroy(h->cap);
     ibk::cnn_free(h->n);
     delete h;
 }
@@ -560,7 +642,7 @@ ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rh
 {
     if (!h || B < 1 || N < 4 || N % (4 << h->coarsen) || !(hs > 0) || !rhs || !rho || !p0)
         return IB_EINVAL;
-    cudaError_t e = ibk::cnn_infer_levels(*h->n, B, N, hs, rhs, rho, p0, h->coarsen, (cudaStream_t)stream);
+    cudaError_t e = cnn_run(h, B, N, hs, rhs, rho, p0, (cudaStream_t)stream);
     if (e == cudaErrorMemoryAllocation) return IB_ENOMEM;
     return e == cudaSuccess ? IB_OK : IB_ECUDA;
 }

@@ -973,6 +973,8 @@ cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, 
 }
 
 void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }
+const void *cnn_workspace_ptr(const Cnn &n) { return n.amem; }
+const void *cnn_cbuf_ptr(const Cnn &n) { return n.cbuf; }
 double cnn_get_scale(const Cnn &n) { return n.out_scale; }
 
 size_t cnn_nparam(const Cnn &n) { return n.nparam; }

@@ -69,6 +69,9 @@ template <typename T>
 struct LevelT {
     T *e = nullptr, *r = nullptr, *bx = nullptr, *by = nullptr, *invd = nullptr;
     T *e2 = nullptr;  // second iterate buffer: sweeps read one and write the other
+    // FP64 levels only: the pre-scaled stencil of the sweep, 4 weights per
+    // cell (W, E, S, N) = beta_f / diag, and the right-hand side h^2 b / diag
+    T *w = nullptr, *bt = nullptr;
 };
 
 // Tensor maps (TMA descriptors) of one fused FP32 smoother launch: windows of
@@ -236,6 +239,8 @@ cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, 
                              double *p0, int levels, cudaStream_t s);
 void cnn_set_scale(Cnn &n, double c);
 double cnn_get_scale(const Cnn &n);
+const void *cnn_workspace_ptr(const Cnn &n);  // current activation workspace (moves when it grows)
+const void *cnn_cbuf_ptr(const Cnn &n);       // current coarse-grid buffer
 size_t cnn_nparam(const Cnn &n);
 float *cnn_weights(Cnn &n);
 float *cnn_grads(Cnn &n);

@@ -134,6 +134,65 @@ k_rbgs_sweep(int nx, int ny, T h2, const T *__restrict__ bx, const T *__restrict
     }
 }
 
+// The FP64 sweep on the pre-scaled stencil: p_c <- sum_f w_{c,f} p_nb(f) - bt_c
+// with w_{c,f} = beta_f / diag_c and bt_c = h^2 b_c / diag_c, the update of
+// k_rbgs_sweep ((sum_f beta_f p_nb - h^2 b_c) / diag_c) in four FP64 FMAs
+// instead of six.  This part issues FP64 at 1/70 of its FP32 rate, so the
+// six-operation sweep is bound by the FP64 pipe before HBM; the weights cost
+// 8 more bytes per cell (w 32 B + bt 8 B in place of beta_x, beta_y, 1/diag
+// and b) and move the bound back towards memory.  Same tiling as
+// k_rbgs_sweep: red on the tile and its one-cell ring, then black on the
+// tile, from a shared-memory copy of the iterate with a 2-cell halo.
+__global__ void __launch_bounds__(TT)
+k_rbgs_sweep_w(int nx, int ny, const double2 *__restrict__ w, const double *__restrict__ bt,
+               const double *__restrict__ pin, double *__restrict__ p)
+{
+    pdl_enter();
+    __shared__ double ps[TH + 4][TW + 4];
+    const int gi0 = blockIdx.x * TW - 2, gj0 = blockIdx.y * TH - 2;
+    for (int k = threadIdx.x; k < (TH + 4) * (TW + 4); k += TT) {
+        int r = k / (TW + 4), c = k - r * (TW + 4);
+        int gi = gi0 + c, gj = gj0 + r;
+        ps[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj < ny) ? pin[(long)gj * nx + gi] : 0.0;
+    }
+    __syncthreads();
+    constexpr int RW = (TW + 2) / 2;
+    for (int k = threadIdx.x; k < (TH + 2) * RW; k += TT) {
+        const int r = 1 + k / RW, cc = k - (r - 1) * RW;
+        const int gj = gj0 + r;
+        const int c = 1 + 2 * cc + ((gi0 + 1 + gj) & 1);
+        const int gi = gi0 + c;
+        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
+        const long kc = (long)gj * nx + gi;
+        const double2 we = w[2 * kc], sn = w[2 * kc + 1];
+        double s = fma(we.x, ps[r][c - 1], -bt[kc]);
+        s = fma(we.y, ps[r][c + 1], s);
+        s = fma(sn.x, ps[r - 1][c], s);
+        ps[r][c] = fma(sn.y, ps[r + 1][c], s);
+    }
+    __syncthreads();
+    constexpr int BW = TW / 2;
+    for (int k = threadIdx.x; k < TH * BW; k += TT) {
+        const int r = 2 + k / BW, cc = k - (r - 2) * BW;
+        const int gj = gj0 + r;
+        const int c = 2 + 2 * cc + ((gi0 + gj + 1) & 1);
+        const int gi = gi0 + c;
+        if (gi >= nx || gj >= ny) continue;
+        const long kc = (long)gj * nx + gi;
+        const double2 we = w[2 * kc], sn = w[2 * kc + 1];
+        double s = fma(we.x, ps[r][c - 1], -bt[kc]);
+        s = fma(we.y, ps[r][c + 1], s);
+        s = fma(sn.x, ps[r - 1][c], s);
+        ps[r][c] = fma(sn.y, ps[r + 1][c], s);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < TH * TW; k += TT) {
+        int r = 2 + k / TW, c = 2 + (k - (r - 2) * TW);
+        int gi = gi0 + c, gj = gj0 + r;
+        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+    }
+}
+
 constexpr int FW = 64, FH = 16, FT = 256;
 
 // Asynchronous global -> shared copies (both addresses aligned to the size);
@@ -183,8 +242,9 @@ __device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, int
 // side (coarse correction set to zero); the last black phase also covers the
 // tile's one-cell ring so that the residual sees final neighbours (halo 5).
 // MODE 2: p + P e_c (the bilinear prolongation of the coarse correction) is
-// formed while staging, then the sweeps (halo 4).  Each mode equals the
-// separate kernels in turn.
+// formed while staging, then the sweeps (halo 4); with p64 (the finest level
+// of a defect-correction cycle) the result is added to the FP64 iterate
+// instead of being stored.  Each mode equals the separate kernels in turn.
 // Staging: with TMA (widths that are a multiple of 4), one thread issues
 // tensor copies of the iterate, right-hand side, 1/diag and beta_y windows
 // (zero outside the grid) onto one barrier while all threads copy the x-face
@@ -201,7 +261,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
               const float *__restrict__ by, const float *__restrict__ invd,
               const float *__restrict__ b, const float *__restrict__ pin, float *__restrict__ p,
               float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp,
-              const __grid_constant__ TileMaps tm)
+              double *__restrict__ p64, const __grid_constant__ TileMaps tm)
 {
     pdl_enter();
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
@@ -410,7 +470,10 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     for (int k = threadIdx.x; k < FH * FW; k += FT) {
         const int r = HA + k / FW, c = XO + (k - (k / FW) * FW);
         const int gi = gi0 + c, gj = gj0 + r;
-        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+        if (gi < nx && gj < ny) {
+            if (MODE == 2 && p64) p64[(long)gj * nx + gi] += (double)ps[r][c];
+            else p[(long)gj * nx + gi] = ps[r][c];
+        }
     }
 }
 
@@ -431,12 +494,14 @@ __device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
 }
 
 // Coarse residual = average of the four children's b - A p; zeroes the coarse
-// correction.
+// correction.  With btc, also the coarse right-hand side of the pre-scaled
+// FP64 sweep, h_c^2 rc / diag_c.
 template <typename T>
 __global__ void k_restrict_residual(int nx, int ny, T ih2, const T *__restrict__ bx,
                                     const T *__restrict__ by, const T *__restrict__ b,
                                     const T *__restrict__ p, T *__restrict__ rc,
-                                    T *__restrict__ ec)
+                                    T *__restrict__ ec, T h2c, const T *__restrict__ invdc,
+                                    T *__restrict__ btc)
 {
     pdl_enter();
     int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
@@ -448,8 +513,10 @@ __global__ void k_restrict_residual(int nx, int ny, T ih2, const T *__restrict__
     T r01 = b[(long)(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * ih2;
     T r11 = b[(long)(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * ih2;
     long kc = (long)J * nxc + I;
-    rc[kc] = T(0.25) * (r00 + r10 + r01 + r11);
+    const T rv = T(0.25) * (r00 + r10 + r01 + r11);
+    rc[kc] = rv;
     if (ec) ec[kc] = T(0);
+    if (btc) btc[kc] = rv * h2c * invdc[kc];
 }
 
 template <typename T>
@@ -516,7 +583,8 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
                                                   const double *__restrict__ fby,
                                                   double *__restrict__ bx, double *__restrict__ by,
                                                   float *__restrict__ bxf, float *__restrict__ byf,
-                                                  double *__restrict__ invd, float *__restrict__ invdf)
+                                                  double *__restrict__ invd, float *__restrict__ invdf,
+                                                  double *__restrict__ w4)
 {
     const int fnx = 2 * nx;  // finer level width (unused at level 0)
     auto xface = [&](int I, int J) -> double {   // coefficient of x-face (I, J)
@@ -539,17 +607,19 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
     const double id = d > 0.0 ? recip_nr(d) : 0.0;
     invd[kc] = id;
     invdf[kc] = (float)id;
+    reinterpret_cast<double2 *>(w4)[2 * kc] = make_double2(w * id, e * id);
+    reinterpret_cast<double2 *>(w4)[2 * kc + 1] = make_double2(s * id, n * id);
 }
 
 __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
                                const double *__restrict__ fby, double *__restrict__ bx,
                                double *__restrict__ by, float *__restrict__ bxf,
                                float *__restrict__ byf, double *__restrict__ invd,
-                               float *__restrict__ invdf)
+                               float *__restrict__ invdf, double *__restrict__ w4)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
-    level_coeffs_cell(nx, ny, level0, i, j, fbx, fby, bx, by, bxf, byf, invd, invdf);
+    level_coeffs_cell(nx, ny, level0, i, j, fbx, fby, bx, by, bxf, byf, invd, invdf, w4);
 }
 
 // The small levels (from `first` on) in one CTA, level after level; a level
@@ -558,7 +628,7 @@ __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restr
 struct LevelCoeffArgs {
     int first, nl;
     int nx[16], ny[16];
-    double *bx[16], *by[16], *invd[16];
+    double *bx[16], *by[16], *invd[16], *w4[16];
     float *bxf[16], *byf[16], *invdf[16];
 };
 
@@ -569,7 +639,7 @@ __global__ void __launch_bounds__(1024) k_level_coeffs_small(LevelCoeffArgs a)
         for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
             const int j = k / nx, i = k - j * nx;
             level_coeffs_cell(nx, ny, l == 0, i, j, a.bx[l - 1], a.by[l - 1], a.bx[l], a.by[l], a.bxf[l],
-                              a.byf[l], a.invd[l], a.invdf[l]);
+                              a.byf[l], a.invd[l], a.invdf[l], a.w4[l]);
         }
         __syncthreads();
     }
@@ -901,8 +971,9 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
 // --------------------------------------------------------------- reductions
 // Deterministic sum: each block folds a fixed strided slice in a fixed order
 // and a fixed tree; the last block to finish folds the block partials.
+// Returns true in the one thread that wrote the total.
 template <typename F>
-__device__ void block_fold_and_finish(double v, double *part, unsigned *count,
+__device__ bool block_fold_and_finish(double v, double *part, unsigned *count,
                                       double *out)
 {
     __shared__ double sh[kRedT];
@@ -920,7 +991,7 @@ __device__ void block_fold_and_finish(double v, double *part, unsigned *count,
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     double s = 0.0;
     for (int k = threadIdx.x; k < (int)gridDim.x; k += kRedT) s += ((volatile double *)part)[k];
@@ -933,7 +1004,24 @@ __device__ void block_fold_and_finish(double v, double *part, unsigned *count,
     if (threadIdx.x == 0) {
         *out = sh[0];
         *count = 0u;
+        return true;
     }
+    return false;
+}
+
+// Convergence test of the device-side solve loop (one thread, after the
+// residual norm res[2] is final): updates the cycle count and relative
+// residual and sets the WHILE condition.
+__device__ void solve_check(SolveCtl *ctl, const double *res, cudaGraphConditionalHandle hnd,
+                            int first, int inc)
+{
+    const double nb = sqrt(res[1]);
+    if (first) { ctl->cycles = 0; ctl->zero_p = nb == 0.0 ? 1 : 0; }
+    else ctl->cycles += inc;
+    const double rr = nb == 0.0 ? 0.0 : sqrt(res[2]) / nb;
+    ctl->rr = rr;
+    const unsigned go = (nb != 0.0 && rr > ctl->tol && ctl->cycles < ctl->max_cycles && isfinite(rr)) ? 1u : 0u;
+    cudaGraphSetConditional(hnd, go);
 }
 
 struct NoOp {};
@@ -947,16 +1035,19 @@ k_sum(long n, const double *__restrict__ a, double *part, unsigned *count, doubl
     block_fold_and_finish<NoOp>(s, part, count, out);
 }
 
-// r0 = b - sum/n; accumulates sum r0^2.
+// r0 = b - sum/n; accumulates sum r0^2.  With bt, also the right-hand side
+// of the pre-scaled FP64 sweep, h^2 r0 / diag.
 __global__ void __launch_bounds__(kRedT)
 k_sub_mean(long n, const double *__restrict__ b, const double *__restrict__ sum,
-           double *__restrict__ r0, double *part, unsigned *count, double *out)
+           double *__restrict__ r0, double h2, const double *__restrict__ invd,
+           double *__restrict__ bt, double *part, unsigned *count, double *out)
 {
     const double m = *sum / (double)n;
     double s = 0.0;
     for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT) {
         double v = b[k] - m;
         r0[k] = v;
+        if (bt) bt[k] = v * h2 * invd[k];
         s += v * v;
     }
     block_fold_and_finish<NoOp>(s, part, count, out);
@@ -969,13 +1060,16 @@ __global__ void k_apply_mean(long n, double *__restrict__ p, const double *__res
     if (k < n) dst[k] = p[k] - *sum / (double)n;
 }
 
-// sum (b0 - A p)^2 over the fine grid, FP64.  With rf != NULL also writes the
-// FP32 residual and zeroes the FP32 correction for the inner cycle.
+// sum (b0 - A p)^2 over the fine grid, FP64, into res[2].  With rf != NULL
+// also writes the FP32 residual and zeroes the FP32 correction for the inner
+// cycle.  check = 1 (first) or 2 (after `inc` cycles): the block that
+// finishes the sum also runs the convergence test of the graph's solve loop.
 __global__ void __launch_bounds__(kRedT)
 k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
           const double *__restrict__ by, const double *__restrict__ b0,
           const double *__restrict__ p, float *__restrict__ rf, float *__restrict__ ef,
-          double *part, unsigned *count, double *out)
+          double *part, unsigned *count, double *res, SolveCtl *ctl,
+          cudaGraphConditionalHandle hnd, int check, int inc)
 {
     pdl_enter();
     double s = 0.0;
@@ -986,7 +1080,8 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
             s += r * r;
             if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
         }
-    block_fold_and_finish<NoOp>(s, part, count, out);
+    if (block_fold_and_finish<NoOp>(s, part, count, res + 2) && check)
+        solve_check(ctl, res, hnd, check == 1, inc);
 }
 
 __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restrict__ p)
@@ -994,20 +1089,6 @@ __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restric
     pdl_enter();
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) p[k] += (double)e[k];
-}
-
-// Convergence test of the device-side solve loop (one thread): updates the
-// cycle count and relative residual and sets the WHILE condition.
-__global__ void k_check(SolveCtl *ctl, const double *res, cudaGraphConditionalHandle hnd, int first)
-{
-    pdl_enter();
-    const double nb = sqrt(res[1]);
-    if (first) { ctl->cycles = 0; ctl->zero_p = nb == 0.0 ? 1 : 0; }
-    else ctl->cycles += 1;
-    const double rr = nb == 0.0 ? 0.0 : sqrt(res[2]) / nb;
-    ctl->rr = rr;
-    const unsigned go = (nb != 0.0 && rr > ctl->tol && ctl->cycles < ctl->max_cycles && isfinite(rr)) ? 1u : 0u;
-    cudaGraphSetConditional(hnd, go);
 }
 
 __global__ void k_finalize(long n, const double *__restrict__ e0, const double *__restrict__ sum,
@@ -1026,7 +1107,8 @@ T *other(LevelT<T> &a, T *cur) { return cur == a.e ? a.e2 : a.e; }
 // level has tensor maps.
 template <int MODE>
 void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, float *p,
-                    float *rc, float *ecz, const float *ecp, cudaStream_t s)
+                    float *rc, float *ecz, const float *ecp, cudaStream_t s,
+                    double *p64 = nullptr)
 {
     dim3 g2(cdiv(v.nx, FW), cdiv(v.ny, FH));
     const float h2 = (float)(v.h * v.h), ih2 = MODE == 1 ? (float)(1.0 / (v.h * v.h)) : 0.0f;
@@ -1041,10 +1123,10 @@ void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, fl
         tm.y = w.by;
         tm.fault = v.fault;
         launch_pdl(k_smooth2_f32<MODE, true>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by, a.invd,
-                   a.r, pin, p, rc, ecz, ecp, tm);
+                   a.r, pin, p, rc, ecz, ecp, p64, tm);
     } else {
         launch_pdl(k_smooth2_f32<MODE, false>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by,
-                   a.invd, a.r, pin, p, rc, ecz, ecp, tm);
+                   a.invd, a.r, pin, p, rc, ecz, ecp, p64, tm);
     }
 }
 
@@ -1072,8 +1154,12 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
         if (pr) prof_mark(s, true);
         note_launch();
         T *nxt = other(a, cur);
-        launch_pdl(k_rbgs_sweep<T>, g, TT, 0, s, v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r,
-                   (const T *)cur, nxt);
+        if constexpr (sizeof(T) == 8)
+            launch_pdl(k_rbgs_sweep_w, g, TT, 0, s, v.nx, v.ny, (const double2 *)a.w,
+                       (const double *)a.bt, (const double *)cur, nxt);
+        else
+            launch_pdl(k_rbgs_sweep<T>, g, TT, 0, s, v.nx, v.ny, h2, a.bx, a.by, a.invd, a.r,
+                       (const T *)cur, nxt);
         cur = nxt;
         if (pr) prof_mark(s, false);
     }
@@ -1085,9 +1171,12 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
 // start in the canonical buffer, which the restriction zeroes, and level 0
 // ends in its canonical buffer (copied back when the sweep count is odd).
 // FP32 cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
-// restriction going down, prolongation + sweeps going up).
+// restriction going down, prolongation + sweeps going up); given add64 (the
+// FP64 iterate of the defect correction), such a cycle adds its level-0
+// result to it in the last smoother and returns true (the FP32 level-0
+// iterate is then not stored).
 template <typename T>
-void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
+bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *add64 = nullptr)
 {
     auto lvT = [&](int l) -> LevelT<T> & {
         if constexpr (sizeof(T) == 8) return mg.lv[l].d; else return mg.lv[l].f;
@@ -1113,8 +1202,13 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
             cur[l] = smooth<T>(v, a, cur[l], nu1, l == 0, s);
             dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
             note_launch();
+            // the next level's pre-scaled right-hand side where it is swept by
+            // k_rbgs_sweep_w (FP64, above the tail)
+            const bool wt = sizeof(T) == 8 && l + 1 < lt;
+            const double hc = mg.lv[l + 1].h;
             launch_pdl(k_restrict_residual<T>, gr, 128, 0, s, v.nx, v.ny, (T)(1.0 / (v.h * v.h)),
-                       a.bx, a.by, a.r, (const T *)cur[l], c.r, c.e);
+                       a.bx, a.by, a.r, (const T *)cur[l], c.r, c.e, (T)(hc * hc),
+                       (const T *)c.invd, wt ? c.bt : (T *)nullptr);
         }
         cur[l + 1] = c.e;
     }
@@ -1142,6 +1236,11 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
             if constexpr (f32) {
                 const bool pr = l == 0 && prof_on(kProfSweep32);
                 if (pr) prof_mark(s, true);
+                if (l == 0 && add64) {
+                    launch_smooth2<2>(v, a, cur[0], nullptr, nullptr, nullptr, cur[1], s, add64);
+                    if (pr) prof_mark(s, false);
+                    return true;
+                }
                 T *nxt = other(a, cur[l]);
                 launch_smooth2<2>(v, a, cur[l], nxt, nullptr, nullptr, cur[l + 1], s);
                 if (pr) prof_mark(s, false);
@@ -1158,6 +1257,7 @@ void vcycle(MG &mg, int nu1, int nu2, cudaStream_t s)
     if (cur[0] != lvT(0).e)
         cudaMemcpyAsync(lvT(0).e, cur[0], (size_t)mg.lv[0].nx * mg.lv[0].ny * sizeof(T),
                         cudaMemcpyDeviceToDevice, s);
+    return false;
 }
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -1307,6 +1407,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         v.d.e = (double *)take(n * 8); v.d.e2 = (double *)take(n * 8);
         v.d.r = (double *)take(n * 8); v.d.invd = (double *)take(n * 8);
         v.d.bx = (double *)take(fx * 8); v.d.by = (double *)take(fy * 8);
+        v.d.w = (double *)take(n * 32); v.d.bt = (double *)take(n * 8);
         v.f.e = (float *)take(n * 4); v.f.e2 = (float *)take(n * 4);
         v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
         v.f.bx = (float *)take(fx * 4); v.f.by = (float *)take(fy * 4);
@@ -1364,11 +1465,12 @@ void mg_free(MG &mg)
 
 // One launch of one kernel of the cycle on the hierarchy's current data, for
 // kernel timing: op 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps +
-// restriction, 4 FP32 prolongation + sweeps (all at `level`), 5 FP32 tail,
-// 6 FP64 residual norm of the mixed solve (level 0).  Returns the cells of
-// the level, or -1 if the op does not exist there.  Writes only solve
-// scratch (second iterate buffers, coarse right-hand sides and corrections,
-// FP32 residual, norm partials).
+// restriction, 4 FP32 prolongation + sweeps (+ the FP64 update at level 0),
+// all at `level`; 5 FP32 tail, 6 FP64 residual norm of the mixed solve
+// (level 0).  Returns the cells of the level, or -1 if the op does not exist
+// there.  Writes only solve scratch (second iterate buffers, coarse
+// right-hand sides and corrections, the level-0 FP64 iterate copy, FP32
+// residual, norm partials).
 long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
 {
     if (level < 0 || level >= mg.L) return -1;
@@ -1382,9 +1484,10 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
         launch_smooth2<1>(v, v.f, v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
                           nullptr, s);
         return cells;
-    case 4:
+    case 4:  // at level 0 with the FP64 update, as in the defect-correction cycle
         if (level >= mg.tail_f) return -1;
-        launch_smooth2<2>(v, v.f, v.f.e, v.f.e2, nullptr, nullptr, mg.lv[level + 1].f.e, s);
+        launch_smooth2<2>(v, v.f, v.f.e, v.f.e2, nullptr, nullptr, mg.lv[level + 1].f.e, s,
+                          level == 0 ? v.d.e : nullptr);
         return cells;
     case 5: {
         const int lt = mg.tail_f, L = mg.L;
@@ -1410,7 +1513,8 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
         note_launch();
         launch_pdl(k_resnorm, mg.red_blocks, kRedT, 0, s, v0.nx, v0.ny, 1.0 / (v0.h * v0.h), v0.d.bx,
                    v0.d.by, (const double *)v0.d.r, (const double *)v0.d.e, v0.f.r, v0.f.e,
-                   mg.red + 8, mg.red_count, mg.red + 2);
+                   mg.red + 8, mg.red_count, mg.red, (SolveCtl *)nullptr,
+                   (cudaGraphConditionalHandle)0, 0, 0);
         return (long)v0.nx * v0.ny;
     }
     default: return -1;
@@ -1429,7 +1533,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         dim3 g(cdiv(v.nx, 128), v.ny);
         note_launch();
         k_level_coeffs<<<g, 128, 0, s>>>(v.nx, v.ny, l == 0, fbx, fby, v.d.bx, v.d.by, v.f.bx, v.f.by,
-                                         v.d.invd, v.f.invd);
+                                         v.d.invd, v.f.invd, v.d.w);
     }
     if (lsmall < L) {
         LevelCoeffArgs a;
@@ -1438,7 +1542,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         for (int l = 0; l < L; l++) {
             Level &v = mg.lv[l];
             a.nx[l] = v.nx; a.ny[l] = v.ny;
-            a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd;
+            a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd; a.w4[l] = v.d.w;
             a.bxf[l] = v.f.bx; a.byf[l] = v.f.by; a.invdf[l] = v.f.invd;
         }
         note_launch();
@@ -1491,7 +1595,8 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
     note_launch();
     k_sum<<<RB, kRedT, 0, s>>>(n, rhs, part, mg.red_count, res + 0);
     note_launch();
-    k_sub_mean<<<RB, kRedT, 0, s>>>(n, rhs, res + 0, b0, part, mg.red_count, res + 1);
+    k_sub_mean<<<RB, kRedT, 0, s>>>(n, rhs, res + 0, b0, v0.h * v0.h, v0.d.invd,
+                                    precision ? nullptr : v0.d.bt, part, mg.red_count, res + 1);
     auto resnorm = [&]() {
         const bool pr = prof_on(kProfResnorm);
         if (pr) prof_mark(s, true);
@@ -1499,7 +1604,7 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
         k_resnorm<<<RB, kRedT, 0, s>>>(v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
                                        precision ? v0.f.r : nullptr,
                                        precision ? v0.f.e : nullptr, part, mg.red_count,
-                                       res + 2);
+                                       res, nullptr, (cudaGraphConditionalHandle)0, 0, 0);
         if (pr) prof_mark(s, false);
         cudaMemcpyAsync(mg.red_host, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
         return cudaStreamSynchronize(s);
@@ -1520,9 +1625,15 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
             if (precision == 0) {
                 vcycle<double>(mg, nu1, nu2, s);
             } else {
-                vcycle<float>(mg, nu1, nu2, s);
-                note_launch();
-                k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
+                const int inner = precision == 2 ? 2 : 1;
+                bool added = false;
+                for (int q = 0; q < inner; q++)
+                    added = vcycle<float>(mg, nu1, nu2, s, q == inner - 1 ? e0 : nullptr);
+                if (!added) {
+                    note_launch();
+                    k_add_f32<<<cdiv(n, 256), 256, 0, s>>>(n, v0.f.e, e0);
+                }
+                c += inner - 1;
             }
             c++;
             ce = resnorm();
@@ -1567,26 +1678,26 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
     note_launch();
     k_sum<<<RB, kRedT, 0, c>>>(n, sg.rhs, part, mg.red_count, res + 0);
     note_launch();
-    k_sub_mean<<<RB, kRedT, 0, c>>>(n, sg.rhs, res + 0, b0, part, mg.red_count, res + 1);
-    auto resnorm = [&](cudaStream_t st) {
-        note_launch();
-        launch_pdl(k_resnorm, RB, kRedT, 0, st, v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
-                   sg.precision ? v0.f.r : nullptr, sg.precision ? v0.f.e : nullptr, part,
-                   mg.red_count, res + 2);
-    };
-    resnorm(c);
+    k_sub_mean<<<RB, kRedT, 0, c>>>(n, sg.rhs, res + 0, b0, v0.h * v0.h, v0.d.invd,
+                                    sg.precision ? nullptr : v0.d.bt, part, mg.red_count, res + 1);
     cudaStreamCaptureStatus cs;
     cudaGraph_t g;
     const cudaGraphNode_t *deps;
     const cudaGraphEdgeData *ed;
     size_t nd;
-    cudaGraphConditionalHandle hnd;
+    cudaGraphConditionalHandle hnd = 0;
     unsigned long long kb0 = 0, kb1 = 0;
+    // residual norm + convergence test (check 1: before the loop, 2: in its body)
+    auto resnorm = [&](cudaStream_t st, int check) {
+        note_launch();
+        launch_pdl(k_resnorm, RB, kRedT, 0, st, v0.nx, v0.ny, ih2, v0.d.bx, v0.d.by, b0, e0,
+                   sg.precision ? v0.f.r : nullptr, sg.precision ? v0.f.e : nullptr, part,
+                   mg.red_count, res, mg.ctl, hnd, check, sg.precision == 2 ? 2 : 1);
+    };
     e = cudaStreamGetCaptureInfo(c, &cs, nullptr, &g, &deps, &ed, &nd);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hnd, g, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
-        note_launch();
-        k_check<<<1, 1, 0, c>>>(mg.ctl, res, hnd, 1);
+        resnorm(c, 1);
         e = cudaStreamGetCaptureInfo(c, &cs, nullptr, &g, &deps, &ed, &nd);
     }
     cudaGraphNode_t wnode;
@@ -1608,13 +1719,16 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
             if (sg.precision == 0) {
                 vcycle<double>(mg, sg.nu1, sg.nu2, cb);
             } else {
-                vcycle<float>(mg, sg.nu1, sg.nu2, cb);
-                note_launch();
-                launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
+                const int inner = sg.precision == 2 ? 2 : 1;
+                bool added = false;
+                for (int q = 0; q < inner; q++)
+                    added = vcycle<float>(mg, sg.nu1, sg.nu2, cb, q == inner - 1 ? e0 : nullptr);
+                if (!added) {
+                    note_launch();
+                    launch_pdl(k_add_f32, cdiv(n, 256), 256, 0, cb, n, v0.f.e, e0);
+                }
             }
-            resnorm(cb);
-            note_launch();
-            launch_pdl(k_check, 1, 1, 0, cb, mg.ctl, res, hnd, 0);
+            resnorm(cb, 2);
             e = cudaStreamEndCapture(cb, &body);
         }
         kb1 = launch_count();
@@ -1710,7 +1824,8 @@ void launch_restrict_residual(int nx, int ny, double h, const double *bx,
 {
     dim3 gr(cdiv(nx / 2, 128), ny / 2);
     note_launch();
-    k_restrict_residual<double><<<gr, 128, 0, s>>>(nx, ny, 1.0 / (h * h), bx, by, b, p, rc, ec);
+    k_restrict_residual<double><<<gr, 128, 0, s>>>(nx, ny, 1.0 / (h * h), bx, by, b, p, rc, ec, 0.0,
+                                                   nullptr, nullptr);
 }
 
 void launch_prolong_add(int nxc, int nyc, const double *ec, double *ef, cudaStream_t s)

@@ -219,3 +219,29 @@ def test_trained_network_gains_over_cold_start(T):
     assert np.linalg.norm(est - ref) < 0.5 * np.linalg.norm(ref)
     st, cyc_cnn, rr = ctx.mg_solve(b, p0, 1, 1e-10, 200)
     assert st == 0 and rr <= 1e-10 and cyc_cnn <= cyc_cold
+
+
+def test_recorded_inference_replays_the_direct_launches(T):
+    # From the second call with the same arguments on, inference replays a
+    # CUDA graph recorded from the same launches: bitwise equal to the direct
+    # run, and after a training step (weights updated in place, workspace
+    # grown) the replay uses the new weights like a direct run does.
+    import paper_1807_10504_gb300 as ib
+    B, N = 1, 64
+    rhs, rho, p = batch(B, N, 9)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    drhs, drho = d(rhs), d(rho)
+    net = ib.Net(seed=3)
+    net.set_coarsen(1)
+    out = T.empty((B, N, N), dtype=T.float64, device="cuda")
+    first = net.infer(drhs, drho, out=out).clone()
+    for _ in range(3):
+        assert T.equal(net.infer(drhs, drho, out=out), first)
+    net.scale = fitted_scale(rhs, p)
+    net.train_step(d(rhs), d(rho), d(p), lr=2e-3)
+    replay = net.infer(drhs, drho, out=out).clone()
+    replay2 = net.infer(drhs, drho, out=out).clone()
+    other = T.empty((B, N, N), dtype=T.float64, device="cuda")
+    direct = net.infer(drhs, drho, out=other)  # a new key: direct launches
+    assert T.equal(replay, direct) and T.equal(replay2, direct)
+    assert not T.equal(replay, first)

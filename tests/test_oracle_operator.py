@@ -117,7 +117,7 @@ def test_coarsen_beta_is_mean_of_fine_faces(O):
 
 
 @pytest.mark.parametrize("n", [8, 16, 32])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_mg_matches_dense_direct_solve(O, n, precision):
     h = 1 / n
     rho, mu, bx, by = _betas(n, 7 + n)
@@ -158,3 +158,21 @@ def test_mg_levels_rule(O):
     assert O.mg_levels(64, 64) == [(64, 64), (32, 32), (16, 16), (8, 8), (4, 4)]
     assert O.mg_levels(256, 1024)[-1] == (4, 16)
     assert O.mg_levels(12, 12) == [(12, 12), (6, 6)]
+
+
+def test_two_inner_cycles_per_fp64_residual(O):
+    # precision 2 runs FP32 V-cycles in pairs between FP64 residuals: an even
+    # cycle count, no residual formed after the first cycle of a pair, and the
+    # iterate after 2k cycles equals k outer steps of one-cycle defect
+    # correction only in the limit (both converge to the dense solution).
+    n, h = 32, 1 / 32
+    rho, mu, bx, by = _betas(n, 41)
+    b = W.random_cells(n, n, 42)
+    r2 = O.mg_solve(bx, by, b, h, precision=2, tol=1e-12, max_cycles=200)
+    r1 = O.mg_solve(bx, by, b, h, precision=1, tol=1e-12, max_cycles=200)
+    assert r2.status == 0 and r2.cycles % 2 == 0
+    assert np.all(np.isnan(r2.hist[1::2])) and np.all(np.isfinite(r2.hist[0::2]))
+    # per V-cycle the pair contracts like two single cycles
+    assert r2.cycles <= r1.cycles + 2
+    pd = O.dense_solve(bx, by, b, h)
+    assert np.abs(r2.p - pd).max() <= 1e-9 * np.abs(pd).max()
