@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ib_oracle.c")
+_SRC_AXI = os.path.join(_HERE, "ib_oracle_axi.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 IB_OK, IB_EINVAL, IB_ENOMEM, IB_ENOTCONV, IB_ENAN, IB_EMARKER = 0, 1, 2, 3, 4, 5
@@ -27,12 +28,13 @@ IB_OK, IB_EINVAL, IB_ENOMEM, IB_ENOTCONV, IB_ENAN, IB_EMARKER = 0, 1, 2, 3, 4, 5
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, no contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ib_oracle.h"))
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC_AXI),
+        os.path.getmtime(os.path.join(_HERE, "ib_oracle.h"))
     ):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"]
+             "-o", tmp, _SRC, _SRC_AXI, "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -81,6 +83,17 @@ def lib():
             "or_spread_irrot": (None, [_i, _i, _d, _d, _d, _i, _D, _D, _i, _I32, _D, _D,
                                        _D, _D]),
             "or_bspline_relocate": (_i, [_i, _D, _D, _i, _I32, _d, _D, _D]),
+            "or_apply_A_axi": (None, [_i, _i, _d, _D, _D, _D, _D]),
+            "or_axi_weights": (None, [_i, _i, _d, _D, _D, _D, _D]),
+            "or_divergence_axi": (None, [_i, _i, _d, _D, _D, _D]),
+            "or_rhs_axi": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D]),
+            "or_predictor_axi": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _i, _d, _d,
+                                        _D, _D, _D, _D]),
+            "or_curvature_axi": (None, [_i, _D, _D, _i, _I32, _D, _D, _D, _D]),
+            "or_spread_conv_axi": (None, [_i, _i, _i, _d, _i, _D, _D, _D, _D, _D, _D, _D,
+                                          _D]),
+            "or_interp_axi": (None, [_i, _i, _i, _d, _D, _D, _i, _D, _D, _D, _D]),
+            "or_drop_com_axi": (None, [_i, _D, _D, _I32, _i, C.POINTER(_d), C.POINTER(_d)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -310,6 +323,97 @@ def bspline_relocate(X, Y, drop_start, h):
 
 
 # --------------------------------------------------------------------------
+# Axisymmetric (r, z) form (ib_oracle_axi.c): x = r from the axis, the drop
+# given as its full closed meridian curve (right half and mirror image).
+def apply_A_axi(bx, by, p, h):
+    ny, nx = p.shape
+    out = np.empty((ny, nx))
+    lib().or_apply_A_axi(nx, ny, h, _f64(bx), _f64(by), _f64(p), out)
+    return out
+
+
+def axi_weights(bx, by, h):
+    ny, nx = bx.shape[0], by.shape[1]
+    bxa, bya = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_axi_weights(nx, ny, h, _f64(bx), _f64(by), bxa, bya)
+    return bxa, bya
+
+
+def divergence_axi(u, v, h):
+    ny, nx = u.shape[0], v.shape[1]
+    d = np.empty((ny, nx))
+    lib().or_divergence_axi(nx, ny, h, _f64(u), _f64(v), d)
+    return d
+
+
+def rhs_axi(us, vs, Fx, Fy, bx, by, h, dt):
+    ny, nx = us.shape[0], vs.shape[1]
+    b = np.empty((ny, nx))
+    lib().or_rhs_axi(nx, ny, h, dt, _f64(us), _f64(vs), _f64(Fx), _f64(Fy), _f64(bx),
+                     _f64(by), b)
+    return b
+
+
+def predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0)):
+    ny, nx = rho.shape
+    have = au_prev is not None
+    aup = _f64(au_prev) if have else np.zeros((ny, nx + 1))
+    avp = _f64(av_prev) if have else np.zeros((ny + 1, nx))
+    us, vs = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    au, av = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_predictor_axi(nx, ny, h, dt, _f64(rho), _f64(mu), _f64(u), _f64(v), aup, avp,
+                           int(have), float(g[0]), float(g[1]), us, vs, au, av)
+    return us, vs, au, av
+
+
+def curvature_axi(X, Y, drop_start):
+    M = len(X)
+    k, nxm, nym, ds = (np.empty(M) for _ in range(4))
+    lib().or_curvature_axi(M, _f64(X), _f64(Y), len(drop_start) - 1, _ds(drop_start), k,
+                           nxm, nym, ds)
+    return k, nxm, nym, ds
+
+
+def spread_conv_axi(X, Y, fmag, nxm, nym, ds, nx, ny, h, kernel=0):
+    Fx, Fy = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    lib().or_spread_conv_axi(kernel, nx, ny, h, len(X), _f64(X), _f64(Y), _f64(fmag),
+                             _f64(nxm), _f64(nym), _f64(ds), Fx, Fy)
+    return Fx, Fy
+
+
+def interp_axi(u, v, X, Y, h, kernel=0):
+    ny, nx = u.shape[0], v.shape[1]
+    U, V = np.empty(len(X)), np.empty(len(X))
+    lib().or_interp_axi(kernel, nx, ny, h, _f64(u), _f64(v), len(X), _f64(X), _f64(Y), U, V)
+    return U, V
+
+
+def drop_com_axi(X, Y, drop_start, d=0):
+    vol, zc = _d(0.0), _d(0.0)
+    lib().or_drop_com_axi(len(X), _f64(X), _f64(Y), _ds(drop_start), int(d), C.byref(vol),
+                          C.byref(zc))
+    return vol.value, zc.value
+
+
+def symmetrise(X, Y, drop_start):
+    """Mirror symmetry of each drop's closed meridian curve about r = 0:
+    marker k of a drop of n (n even) pairs with marker (n - k) mod n; each
+    pair is replaced by its symmetric mean (markers 0 and n/2 land on the
+    axis)."""
+    X, Y = _f64(X).copy(), _f64(Y).copy()
+    ds_ = _ds(drop_start)
+    for d in range(len(ds_) - 1):
+        s, e = int(ds_[d]), int(ds_[d + 1])
+        n = e - s
+        k = np.arange(n)
+        p = (n - k) % n
+        x, y = X[s:e].copy(), Y[s:e].copy()
+        X[s:e] = 0.5 * (x - x[p])
+        Y[s:e] = 0.5 * (y + y[p])
+    return X, Y
+
+
+# --------------------------------------------------------------------------
 # One time step (Section 2.1 fractional step, force in the projection as in
 # Section 3.2 Eq. (ns2_new)); the order of the stages is that of the method:
 # relocate markers (every `relocate_every` steps), curvature, Heaviside and
@@ -337,6 +441,7 @@ class Config:
     nu1: int = 2
     nu2: int = 2
     relocate_every: int = 10  # 0 = never
+    axisym: int = 0           # 1: (r, z) with x = r from the axis (x0 = 0)
 
 
 @dataclass
@@ -360,6 +465,8 @@ def init_state(cfg: Config, X, Y, drop_start) -> State:
 
 
 def ns_step(cfg: Config, st: State, dt: float) -> State:
+    if cfg.axisym:
+        return _ns_step_axi(cfg, st, dt)
     h = cfg.h
     if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
         st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
@@ -381,6 +488,42 @@ def ns_step(cfg: Config, st: State, dt: float) -> State:
     st.u, st.v, st.p, st.au, st.av = u, v, res.p, au, av
     st.X = st.X + dt * U
     st.Y = st.Y + dt * V
+    st.step += 1
+    st.last = dict(H=H, rho=rho, bx=bx, by=by, Fx=Fx, Fy=Fy, b=b, cycles=res.cycles,
+                   relres=res.relres, status=res.status, kappa=kap)
+    return st
+
+
+def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
+    """The same stages in the axisymmetric form: the meridian curve is kept
+    mirror-symmetric (after relocation and after advection), curvature adds
+    the azimuthal term, the Heaviside and the irrotational force are the
+    planar ones of the full curve on the real cells, the conventional force
+    is ring-weighted, and the pressure equation is solved as the symmetric
+    r-weighted system (coefficients r_face beta, right-hand side r_i b)."""
+    h = cfg.h
+    if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
+        st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
+        st.X, st.Y = symmetrise(st.X, st.Y, st.drop_start)
+    kap, nxm, nym, ds = curvature_axi(st.X, st.Y, st.drop_start)
+    fmag = cfg.sigma * kap
+    H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, 0.0, cfg.y0)
+    rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
+    us, vs, au, av = predictor_axi(rho, mu, st.u, st.v, h, dt, st.au, st.av, (0.0, cfg.gy))
+    if cfg.spread == 0:
+        Fx, Fy = spread_conv_axi(st.X, st.Y - cfg.y0, fmag, nxm, nym, ds, cfg.nx, cfg.ny, h,
+                                 cfg.kernel)
+    else:
+        Fx, Fy = spread_irrot(st.X, st.Y, st.drop_start, fmag, H, h, 0.0, cfg.y0)
+    b = rhs_axi(us, vs, Fx, Fy, bx, by, h, dt)
+    bxa, bya = axi_weights(bx, by, h)
+    r = (np.arange(cfg.nx) + 0.5) * h
+    res = mg_solve(bxa, bya, b * r[None, :], h, st.p, cfg.precision, cfg.tol, cfg.max_cycles,
+                   cfg.nu1, cfg.nu2)
+    u, v = correct(us, vs, res.p, Fx, Fy, bx, by, h, dt)
+    U, V = interp_axi(u, v, st.X, st.Y - cfg.y0, h, cfg.kernel)
+    st.u, st.v, st.p, st.au, st.av = u, v, res.p, au, av
+    st.X, st.Y = symmetrise(st.X + dt * U, st.Y + dt * V, st.drop_start)
     st.step += 1
     st.last = dict(H=H, rho=rho, bx=bx, by=by, Fx=Fx, Fy=Fy, b=b, cycles=res.cycles,
                    relres=res.relres, status=res.status, kappa=kap)

@@ -107,4 +107,29 @@ int or_bspline_relocate(int M, const double *X, const double *Y, int ndrops,
                         const int32_t *drop_start, double h, double *Xo,
                         double *Yo);
 
+/* ---- axisymmetric (r, z) form, ib_oracle_axi.c (x = r from the axis) ---- */
+void or_apply_A_axi(int nx, int ny, double h, const double *bx, const double *by,
+                    const double *p, double *out);
+void or_axi_weights(int nx, int ny, double h, const double *bx, const double *by,
+                    double *bxa, double *bya);
+void or_divergence_axi(int nx, int ny, double h, const double *u, const double *v,
+                       double *d);
+void or_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,
+                const double *Fx, const double *Fy, const double *bx, const double *by,
+                double *b);
+void or_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
+                      const double *mu, const double *u, const double *v,
+                      const double *au_prev, const double *av_prev, int have_prev,
+                      double gx, double gy, double *us, double *vs, double *au, double *av);
+void or_curvature_axi(int M, const double *X, const double *Y, int ndrops,
+                      const int32_t *drop_start, double *kappa, double *nxm, double *nym,
+                      double *ds);
+void or_spread_conv_axi(int kernel, int nx, int ny, double h, int M, const double *X,
+                        const double *Y, const double *fmag, const double *nxm,
+                        const double *nym, const double *ds, double *Fx, double *Fy);
+void or_interp_axi(int kernel, int nx, int ny, double h, const double *u, const double *v,
+                   int M, const double *X, const double *Y, double *U, double *V);
+void or_drop_com_axi(int M, const double *X, const double *Y, const int32_t *drop_start,
+                     int d, double *volume, double *zc);
+
 #endif

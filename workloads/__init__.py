@@ -16,6 +16,13 @@ viscosity ratio 100; sigma = 1):
   multidrop_N        N x N unit box (N = 1024, 2048), 64 non-overlapping drops,
                      radii U[0.01, 0.03], 256 markers each (seed 1811), drops at
                      least 8 cells from the walls and 8 cells apart.
+  axisymmetric drops (x = r from the axis, y = z): the drop's full closed
+                     meridian curve, marker 0 on the axis at the bottom, n/2 on
+                     the axis at the top, marker k and n - k mirror images.
+  freefall_axi       256 x 1024 cells over 4D x 16D (D = 1 mm), water drop
+                     (rho 1000, mu 1e-3) in air (rho 1.2, mu 1.8e-5),
+                     sigma = 0.072, g = 9.81, drop centre 4D above the bottom,
+                     1024 markers on the full meridian (512 on the half profile).
 """
 from __future__ import annotations
 
@@ -74,6 +81,48 @@ def elliptic_drop(cx, cy, r, beta, n_markers) -> Markers:
     """Section 5.2 Eq. (osc): x = cx + r cos(t) beta, y = cy + r sin(t) / beta."""
     th = 2.0 * np.pi * np.arange(n_markers) / n_markers
     return join([(cx + r * np.cos(th) * beta, cy + r * np.sin(th) / beta)])
+
+
+def axi_drop(zc, radius_fn, n) -> Markers:
+    """Axisymmetric drop centred on the axis at height zc: its full meridian
+    curve r(theta) (counter-clockwise from the bottom axis point, theta =
+    -pi/2 + 2 pi k / n, n even), markers k and n - k mirror images."""
+    assert n % 2 == 0
+    th = -0.5 * np.pi + 2.0 * np.pi * np.arange(n // 2 + 1) / n
+    r = radius_fn(th)
+    x, y = r * np.cos(th), zc + r * np.sin(th)
+    x[0] = x[-1] = 0.0
+    return join([_mirror(x, y)])
+
+
+def _mirror(x, y):
+    """Full closed curve from its right half (axis point to axis point):
+    markers n - k are the reflections of markers k."""
+    return np.concatenate([x, -x[-2:0:-1]]), np.concatenate([y, y[-2:0:-1]])
+
+
+def axi_sphere(zc, R, n) -> Markers:
+    return axi_drop(zc, lambda t: np.full_like(t, R), n)
+
+
+def axi_elliptic_drop(zc, r, beta, n) -> Markers:
+    """Section 5.2 Eq. (osc) about (0, zc): r' = r cos(t) beta, z = zc + r sin(t) / beta."""
+    assert n % 2 == 0
+    th = -0.5 * np.pi + 2.0 * np.pi * np.arange(n // 2 + 1) / n
+    x, y = r * np.cos(th) * beta, zc + r * np.sin(th) / beta
+    x[0] = x[-1] = 0.0
+    return join([_mirror(x, y)])
+
+
+def freefall_axi(n_markers=1024):
+    """The free-fall water drop (SI units): returns (markers, constants)."""
+    D = 1e-3
+    nr, nz = 256, 1024
+    h = 4 * D / nr
+    mk = axi_sphere(4 * D, 0.5 * D, n_markers)
+    const = dict(nx=nr, ny=nz, h=h, rho_l=1000.0, rho_g=1.2, mu_l=1e-3, mu_g=1.8e-5,
+                 sigma=0.072, g=9.81)
+    return mk, const
 
 
 def multidrop(n_cells=1024, ndrops=64, rmin=0.01, rmax=0.03, n_per_drop=256,
