@@ -60,6 +60,12 @@ typedef struct ib_config {
                                  step: precision 2 may pass it by one) */
     int32_t nu1, nu2;         /* pre/post red-black Gauss-Seidel sweeps */
     int32_t relocate_every;   /* B-spline relocation period in steps, 0 = never */
+    int32_t axisym;           /* 1: axisymmetric (r, z), Sec. 2.1 and Sec. 4 Eq. (curv_ax):
+                                 x = r with the axis at x0 = 0, y = z; each drop is
+                                 its full closed meridian curve (right half and its
+                                 mirror image, an even number of markers, marker k
+                                 and n - k mirror images, 0 and n/2 on the axis);
+                                 gx must be 0.  0: planar */
 } ib_config;
 
 typedef struct ib_ctx ib_ctx;
@@ -100,7 +106,9 @@ ib_status ib_marker_geometry(ib_ctx *ctx, double *kappa, double *nx,
 
 /* Marker-to-cell binning: key = floor((Y-y0)/h)*nx + floor((X-x0)/h) and the
  * marker ids ordered by (key, id); device outputs (uint32, nmarkers each;
- * either may be NULL) and cell_start (uint32, nx*ny+1, may be NULL).      */
+ * either may be NULL) and cell_start (uint32, nx*ny+1, may be NULL).
+ * Planar contexts only (IB_EINVAL in axisymmetric mode, whose binning grid
+ * carries ghost columns).                                                  */
 ib_status ib_marker_sort(ib_ctx *ctx, uint32_t *keys_sorted,
                          uint32_t *ids_sorted, uint32_t *cell_start);
 
@@ -330,6 +338,28 @@ ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt,
                           const double *av_prev, int32_t have_prev, double gx,
                           double gy, double *us, double *vs, double *au,
                           double *av, void *stream);
+
+/* Axisymmetric (r, z) forms (Section 2.1 in cylindrical coordinates; x = r
+ * from the axis, cell i at r = (i + 1/2) h, x-face i at r = i h).
+ * Predictor: the same AB2 + viscous update on ring control volumes (fluxes
+ * times their face radius over the volume radius; the radial component adds
+ * -mu u / r^2), u = 0 on the axis and walls, gy the axial body acceleration.
+ * Right-hand side: r_i div(u* / dt + beta F) with the axisymmetric
+ * divergence (the right-hand side of the r-weighted pressure equation).
+ * Weights: bxa = r_face bx, bya = r_i by (its coefficients).               */
+ib_status ib_op_predictor_axi(int32_t nx, int32_t ny, double h, double dt,
+                              const double *rho, const double *mu,
+                              const double *u, const double *v,
+                              const double *au_prev, const double *av_prev,
+                              int32_t have_prev, double gy, double *us,
+                              double *vs, double *au, double *av, void *stream);
+ib_status ib_op_rhs_axi(int32_t nx, int32_t ny, double h, double dt,
+                        const double *us, const double *vs, const double *Fx,
+                        const double *Fy, const double *bx, const double *by,
+                        double *b, void *stream);
+ib_status ib_op_axi_weights(int32_t nx, int32_t ny, double h, const double *bx,
+                            const double *by, double *bxa, double *bya,
+                            void *stream);
 
 #ifdef __cplusplus
 }

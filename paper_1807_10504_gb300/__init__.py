@@ -36,6 +36,7 @@ EXPORTS = [
     "ib_profile_end", "ib_bench_kernel", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
+    "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights",
 ]
 
 
@@ -52,7 +53,7 @@ class ib_config(C.Structure):
                 ("gx", C.c_double), ("gy", C.c_double), ("kernel", C.c_int32),
                 ("spread", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_cycles", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
-                ("relocate_every", C.c_int32)]
+                ("relocate_every", C.c_int32), ("axisym", C.c_int32)]
 
 
 _lib = None
@@ -104,6 +105,10 @@ def lib():
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
+            "ib_op_predictor_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _P,
+                                    _P, _P, _P, _P],
+            "ib_op_rhs_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P],
+            "ib_op_axi_weights": [_i32, _i32, _d, _P, _P, _P, _P, _P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -182,6 +187,7 @@ class Config:
     nu1: int = 2
     nu2: int = 2
     relocate_every: int = 10
+    axisym: int = 0
 
     def c(self) -> ib_config:
         return ib_config(**{k: getattr(self, k) for k, _ in ib_config._fields_})
@@ -512,6 +518,33 @@ def ib_op_correct(us, vs, p, Fx, Fy, bx, by, h, dt):
     _op("ib_op_correct", nx, ny, h, dt, _ptr(us), _ptr(vs), _ptr(p), _ptr(Fx), _ptr(Fy),
         _ptr(bx), _ptr(by), _ptr(u), _ptr(v))
     return u, v
+
+
+def ib_op_predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, gy=0.0):
+    torch = _torch()
+    ny, nx = rho.shape
+    us, vs, au, av = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(u),
+                      torch.empty_like(v))
+    have = au_prev is not None
+    _op("ib_op_predictor_axi", nx, ny, h, dt, _ptr(rho), _ptr(mu), _ptr(u), _ptr(v),
+        _ptr(au_prev), _ptr(av_prev), int(have), float(gy), _ptr(us), _ptr(vs), _ptr(au),
+        _ptr(av))
+    return us, vs, au, av
+
+
+def ib_op_rhs_axi(us, vs, Fx, Fy, bx, by, h, dt):
+    ny, nx = us.shape[0], vs.shape[1]
+    b = _torch().empty((ny, nx), dtype=us.dtype, device=us.device)
+    _op("ib_op_rhs_axi", nx, ny, h, dt, _ptr(us), _ptr(vs), _ptr(Fx), _ptr(Fy), _ptr(bx),
+        _ptr(by), _ptr(b))
+    return b
+
+
+def ib_op_axi_weights(bx, by, h):
+    ny, nx = bx.shape[0], by.shape[1]
+    bxa, bya = _torch().empty_like(bx), _torch().empty_like(by)
+    _op("ib_op_axi_weights", nx, ny, h, _ptr(bx), _ptr(by), _ptr(bxa), _ptr(bya))
+    return bxa, bya
 
 
 def ib_op_predictor(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0)):

@@ -23,6 +23,7 @@ SOURCES = {
     "api.cu": [],
     "noalloc.cu": [],
     "cnn.cu": [],
+    "axi.cu": [],
 }
 
 

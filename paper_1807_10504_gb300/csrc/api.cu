@@ -28,6 +28,13 @@ struct ib_ctx {
     bool mg_ready = false;
     uint32_t *flags_host = nullptr;
     struct ib_cnn *cnn = nullptr;   // attached warm-start network (not owned)
+    // axisymmetric mode: ghost columns G of the marker grid (origin -G h), the
+    // velocity continued onto it, the Heaviside and forces computed on it, the
+    // r-weighted pressure coefficients and the ring force magnitudes
+    int G = 0;
+    double *uw = nullptr, *vw = nullptr, *Hw = nullptr, *Fxw = nullptr, *Fyw = nullptr,
+           *bxa = nullptr, *bya = nullptr, *fr = nullptr;
+    void *amem = nullptr;
 };
 
 // An inference of the network recorded as a CUDA graph, keyed by every value
@@ -140,17 +147,38 @@ ib_status launch_check(ib_ctx *c, const char *what)
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Orientation and wall distance of host marker arrays.
+// Ghost columns of the axisymmetric marker grid: the mirror half of the
+// widest drop plus 8 cells, a multiple of 8, at most nx; 0 if it does not fit.
+int axi_ghost(const ib_config &g, const double *X, int M)
+{
+    double w = 0.0;
+    for (int m = 0; m < M; m++) w = fmax(w, fabs(X[m]));
+    const long G = ((long)ceil(w / g.h) + 8 + 7) / 8 * 8;
+    return G <= g.nx ? (int)G : 0;
+}
+
 ib_status check_markers_host(ib_ctx *c, const ib_config &g, const double *X, const double *Y,
                              const int32_t *ds, int nd)
 {
     const double m3 = 3.0 * g.h;
+    const double xlo = g.axisym ? -c->G * g.h : g.x0;  // the axisymmetric marker grid's left edge
     for (int d = 0; d < nd; d++) {
         int s = ds[d], e = ds[d + 1];
         if (e - s < 3) return fail(c, IB_EINVAL, "a drop needs at least 3 markers");
+        if (g.axisym) {
+            const int n = e - s;
+            if (n % 2) return fail(c, IB_EMARKER, "an axisymmetric drop needs an even marker count");
+            for (int k = 0; k <= n / 2; k++) {
+                const int p = (n - k) % n;
+                if (X[s + k] != -X[s + p] || Y[s + k] != Y[s + p])
+                    return fail(c, IB_EMARKER, "an axisymmetric drop must be a mirror-symmetric "
+                                               "meridian curve (marker k mirrors n - k)");
+            }
+        }
         double a = 0.0;
         for (int m = s; m < e; m++) {
             int n = (m + 1 == e) ? s : m + 1;
-            if (!(X[m] >= g.x0 + m3 && X[m] <= g.x0 + g.nx * g.h - m3 && Y[m] >= g.y0 + m3 &&
+            if (!(X[m] >= xlo + m3 && X[m] <= g.x0 + g.nx * g.h - m3 && Y[m] >= g.y0 + m3 &&
                   Y[m] <= g.y0 + g.ny * g.h - m3))
                 return fail(c, IB_EMARKER, "marker outside the domain or within 3 cells of a wall");
             a += X[m] * Y[n] - X[n] * Y[m];
@@ -158,6 +186,62 @@ ib_status check_markers_host(ib_ctx *c, const ib_config &g, const double *X, con
         if (!(a > 0.0)) return fail(c, IB_EMARKER, "drop markers are not counter-clockwise");
     }
     return IB_OK;
+}
+
+// Marker geometry (curvature, normals, arc weights, force magnitude), with
+// the azimuthal curvature added in axisymmetric mode.
+void geometry(ib_ctx *c)
+{
+    launch_geometry(c->mk, c->cfg.sigma, c->s);
+    if (c->cfg.axisym) launch_axi_curvature(c->mk, c->cfg.sigma, c->s);
+}
+
+// Heaviside onto the real cells (through the wide grid in axisymmetric mode).
+void heaviside_into(ib_ctx *c, double *H)
+{
+    if (!c->cfg.axisym) {
+        launch_heaviside(c->mk, H, c->s);
+        return;
+    }
+    launch_heaviside(c->mk, c->Hw, c->s);
+    launch_axi_fold(c->cfg.nx, c->cfg.ny, c->G, c->cfg.h, 0, c->Hw, nullptr, nullptr, H, nullptr,
+                    nullptr, c->s);
+}
+
+// Face force of one spreading mode onto the real faces, after geometry,
+// sorting and (mode 1) the Heaviside H of the real cells.  Axisymmetric:
+// conventional spreading of the ring magnitudes sigma kappa |r| on the wide
+// grid, folded with division by the face radius; irrotational spreading on
+// the wide grid's Heaviside (set by heaviside_into), folded.
+void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double *Fx, double *Fy)
+{
+    const ib_config &g = c->cfg;
+    if (!g.axisym) {
+        if (mode == 0) launch_spread_conv(c->mk, g.kernel, fmag, Fx, Fy, c->s);
+        else launch_spread_irrot(c->mk, fmag, H, Fx, Fy, c->s);
+        return;
+    }
+    if (mode == 0) {
+        launch_axi_ring(c->mk, fmag, c->fr, c->s);
+        launch_spread_conv(c->mk, g.kernel, c->fr, c->Fxw, c->Fyw, c->s);
+    } else {
+        launch_spread_irrot(c->mk, fmag, c->Hw, c->Fxw, c->Fyw, c->s);
+    }
+    launch_axi_fold(g.nx, g.ny, c->G, g.h, mode == 0, nullptr, c->Fxw, c->Fyw, nullptr, Fx, Fy, c->s);
+}
+
+// Velocity at the markers (and optional advection), continued across the
+// axis in axisymmetric mode; the curve is re-symmetrised after a move.
+void interp_into(ib_ctx *c, const double *u, const double *v, double *U, double *V, double dt_move)
+{
+    const ib_config &g = c->cfg;
+    if (!g.axisym) {
+        launch_interp(c->mk, g.kernel, u, v, U, V, dt_move, c->s);
+        return;
+    }
+    launch_axi_extend(g.nx, g.ny, c->G, u, v, c->uw, c->vw, c->s);
+    launch_interp(c->mk, g.kernel, c->uw, c->vw, U, V, dt_move, c->s);
+    if (dt_move != 0.0) launch_axi_symmetrise(c->mk, c->s);
 }
 
 ib_status read_flags(ib_ctx *c)
@@ -199,16 +283,12 @@ double *field_ptr(ib_ctx *c, int which, size_t *n)
 ib_status spread_into(ib_ctx *c, int mode, const double *fmag, double *Fx, double *Fy, double *H)
 {
     Markers &mk = c->mk;
-    launch_geometry(mk, c->cfg.sigma, c->s);
+    geometry(c);
     launch_sort(mk, c->s);
     const double *f = fmag ? fmag : mk.fmag;
-    if (mode == 0) {
-        launch_spread_conv(mk, c->cfg.kernel, f, Fx, Fy, c->s);
-    } else {
-        double *Hd = H ? H : c->H;
-        launch_heaviside(mk, Hd, c->s);
-        launch_spread_irrot(mk, f, Hd, Fx, Fy, c->s);
-    }
+    double *Hd = H ? H : c->H;
+    if (mode == 1) heaviside_into(c, Hd);
+    force_into(c, mode, f, Hd, Fx, Fy);
     return launch_check(c, "spread");
 }
 
@@ -229,6 +309,7 @@ void ib_destroy(ib_ctx *c)
     mg_free(c->mg);
     markers_free(c->mk);
     if (c->fmem) cudaFree(c->fmem);
+    if (c->amem) cudaFree(c->amem);
     if (c->flags_host) cudaFreeHost(c->flags_host);
     delete c;
 }
@@ -242,7 +323,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     const ib_config &g = *cfg;
     if (g.nx < 2 || g.ny < 2 || (long)g.nx * g.ny > (1L << 28) || !(g.h > 0) || g.nu1 < 0 ||
         g.nu2 < 0 || g.max_cycles < 0 || !(g.tol >= 0) || g.kernel < 0 || g.kernel > 1 ||
-        g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2)
+        g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2 || g.axisym < 0 ||
+        g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)))
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -254,6 +336,10 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     ib_ctx *c = new ib_ctx();
     c->cfg = g;
     c->s = (cudaStream_t)stream;
+    if (g.axisym) {
+        c->G = axi_ghost(g, X, M);
+        if (!c->G) { delete c; return IB_EMARKER; }
+    }
     ib_status st = check_markers_host(c, g, X, Y, drop_start, ndrops);
     if (st != IB_OK) { delete c; return st; }
     const size_t nc = (size_t)g.nx * g.ny, fx = (size_t)(g.nx + 1) * g.ny, fy = (size_t)g.nx * (g.ny + 1);
@@ -271,7 +357,27 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     c->b = take(nc * 8);
     cudaError_t e = cudaMemset(c->fmem, 0, bytes);
     if (e == cudaSuccess) e = mg_alloc(c->mg, g.nx, g.ny, g.h);
-    if (e == cudaSuccess) e = markers_alloc(c->mk, M, ndrops, g.nx, g.ny, g.h, g.x0, g.y0, drop_start);
+    if (e == cudaSuccess && g.axisym) {
+        const long nw = g.nx + c->G;
+        const size_t wx = (size_t)(nw + 1) * g.ny, wy = (size_t)nw * (g.ny + 1), wc = (size_t)nw * g.ny;
+        const size_t ab = 2 * al(wx * 8) + 2 * al(wy * 8) + al(wc * 8) + al(fx * 8) + al(fy * 8) + al((size_t)M * 8);
+        e = cudaMalloc(&c->amem, ab);
+        if (e == cudaSuccess) {
+            char *a = (char *)c->amem;
+            auto tk = [&](size_t b) { char *r = a; a += al(b); return (double *)r; };
+            c->uw = tk(wx * 8); c->Fxw = tk(wx * 8);
+            c->vw = tk(wy * 8); c->Fyw = tk(wy * 8);
+            c->Hw = tk(wc * 8);
+            c->bxa = tk(fx * 8); c->bya = tk(fy * 8);
+            c->fr = tk((size_t)M * 8);
+            e = cudaMemset(c->amem, 0, ab);
+        } else {
+            c->amem = nullptr;
+        }
+    }
+    if (e == cudaSuccess)
+        e = g.axisym ? markers_alloc(c->mk, M, ndrops, g.nx + c->G, g.ny, g.h, -c->G * g.h, g.y0, drop_start)
+                     : markers_alloc(c->mk, M, ndrops, g.nx, g.ny, g.h, g.x0, g.y0, drop_start);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->flags_host, 64);
     if (e == cudaSuccess) e = cudaMemcpy(c->mk.X, X, (size_t)M * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->mk.Y, Y, (size_t)M * 8, cudaMemcpyHostToDevice);
@@ -340,7 +446,7 @@ ib_status ib_set_field(ib_ctx *c, int which, const double *src, int where)
 ib_status ib_marker_geometry(ib_ctx *c, double *kappa, double *nx, double *ny, double *ds)
 {
     if (!c) return IB_EINVAL;
-    launch_geometry(c->mk, c->cfg.sigma, c->s);
+    geometry(c);
     const size_t b = (size_t)c->mk.M * 8;
     cudaError_t e = cudaSuccess;
     if (kappa && e == cudaSuccess) e = cudaMemcpyAsync(kappa, c->mk.kappa, b, cudaMemcpyDeviceToDevice, c->s);
@@ -360,6 +466,7 @@ __global__ void k_gather_keys(int M, const uint32_t *key, const uint32_t *ids, u
 ib_status ib_marker_sort(ib_ctx *c, uint32_t *keys_sorted, uint32_t *ids_sorted, uint32_t *cell_start)
 {
     if (!c) return IB_EINVAL;
+    if (c->cfg.axisym) return fail(c, IB_EINVAL, "marker binning is exposed for planar contexts only");
     Markers &mk = c->mk;
     launch_sort(mk, c->s);
     if (keys_sorted) { note_launch(); k_gather_keys<<<cdiv(mk.M, 256), 256, 0, c->s>>>(mk.M, mk.key, mk.ids, keys_sorted);
@@ -376,7 +483,7 @@ ib_status ib_marker_sort(ib_ctx *c, uint32_t *keys_sorted, uint32_t *ids_sorted,
 ib_status ib_interp(ib_ctx *c, const double *u, const double *v, double *U, double *V)
 {
     if (!c || !u || !v || !U || !V) return IB_EINVAL;
-    launch_interp(c->mk, c->cfg.kernel, u, v, U, V, 0.0, c->s);
+    interp_into(c, u, v, U, V, 0.0);
     return launch_check(c, "interp");
 }
 
@@ -398,9 +505,9 @@ ib_status ib_spread(ib_ctx *c, int mode, const double *fmag, double *Fx, double 
 ib_status ib_heaviside(ib_ctx *c, double *H)
 {
     if (!c || !H) return IB_EINVAL;
-    launch_geometry(c->mk, c->cfg.sigma, c->s);
+    geometry(c);
     launch_sort(c->mk, c->s);
-    launch_heaviside(c->mk, H, c->s);
+    heaviside_into(c, H);
     ib_status st = launch_check(c, "heaviside");
     if (st != IB_OK) return st;
     return read_flags(c);
@@ -410,6 +517,7 @@ ib_status ib_relocate(ib_ctx *c)
 {
     if (!c) return IB_EINVAL;
     launch_relocate(c->mk, c->s);
+    if (c->cfg.axisym) launch_axi_symmetrise(c->mk, c->s);
     ib_status st = launch_check(c, "relocate");
     if (st != IB_OK) return st;
     return read_flags(c);
@@ -441,25 +549,40 @@ ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, doubl
 ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
 {
     if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 2) return IB_EINVAL;
+    if (warm == 2 && c->cfg.axisym)
+        return fail(c, IB_EINVAL, "the network warm start is trained for the planar equation");
     if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % (4 << c->cnn->coarsen) != 0))
         return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid "
                                   "(side a multiple of 4 * 2^coarsen)");
     const ib_config &g = c->cfg;
     Markers &mk = c->mk;
     for (int it = 0; it < nsteps; it++) {
-        if (g.relocate_every > 0 && c->step % g.relocate_every == 0) launch_relocate(mk, c->s);
-        launch_geometry(mk, g.sigma, c->s);
+        if (g.relocate_every > 0 && c->step % g.relocate_every == 0) {
+            launch_relocate(mk, c->s);
+            if (g.axisym) launch_axi_symmetrise(mk, c->s);
+        }
+        geometry(c);
         launch_sort(mk, c->s);
-        launch_heaviside(mk, c->H, c->s);
+        heaviside_into(c, c->H);
         launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, c->H, c->rho, c->mu, c->bx,
                       c->by, c->s);
-        mg_build(c->mg, c->bx, c->by, c->s);
+        if (g.axisym) {
+            // the r-weighted pressure operator (r_face beta) and right-hand side (r_i b)
+            launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
+            mg_build(c->mg, c->bxa, c->bya, c->s);
+            launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
+                                 c->have_prev, 0.0, g.gy, c->us, c->vs, c->au, c->av, c->s);
+        } else {
+            mg_build(c->mg, c->bx, c->by, c->s);
+            launch_predictor(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
+                             c->have_prev, g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
+        }
         c->mg_ready = true;
-        launch_predictor(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
-                         c->have_prev, g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
-        if (g.spread == 0) launch_spread_conv(mk, g.kernel, mk.fmag, c->Fx, c->Fy, c->s);
-        else launch_spread_irrot(mk, mk.fmag, c->H, c->Fx, c->Fy, c->s);
-        launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
+        force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy);
+        if (g.axisym)
+            launch_rhs_axi(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
+        else
+            launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
         ib_status st = launch_check(c, "step");
         if (st != IB_OK) return st;
         if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
@@ -472,7 +595,7 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (st != IB_OK && st != IB_ENOTCONV) return st;
         launch_correct(g.nx, g.ny, g.h, dt, c->us, c->vs, c->p, c->Fx, c->Fy, c->bx, c->by, c->u,
                        c->v, c->s);
-        launch_interp(mk, g.kernel, c->u, c->v, mk.U, mk.V, dt, c->s);
+        interp_into(c, c->u, c->v, mk.U, mk.V, dt);
         launch_validate(mk, c->s);
         c->have_prev = 1;
         c->step++;
@@ -825,6 +948,36 @@ ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt, const dou
     OPCHK(!have_prev || (au_prev && av_prev));
     launch_predictor(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx, gy, us, vs,
                      au, av, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_predictor_axi(int32_t nx, int32_t ny, double h, double dt, const double *rho,
+                              const double *mu, const double *u, const double *v,
+                              const double *au_prev, const double *av_prev, int32_t have_prev,
+                              double gy, double *us, double *vs, double *au, double *av,
+                              void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && rho && mu && u && v && us && vs && au && av);
+    OPCHK(!have_prev || (au_prev && av_prev));
+    launch_predictor_axi(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, 0.0, gy, us,
+                         vs, au, av, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_rhs_axi(int32_t nx, int32_t ny, double h, double dt, const double *us,
+                        const double *vs, const double *Fx, const double *Fy, const double *bx,
+                        const double *by, double *b, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && dt > 0 && us && vs && Fx && Fy && bx && by && b);
+    launch_rhs_axi(nx, ny, h, dt, us, vs, Fx, Fy, bx, by, b, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_axi_weights(int32_t nx, int32_t ny, double h, const double *bx, const double *by,
+                            double *bxa, double *bya, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && bx && by && bxa && bya);
+    launch_axi_weights(nx, ny, h, bx, by, bxa, bya, (cudaStream_t)stream);
     return op_done();
 }
 

@@ -1,0 +1,333 @@
+// Axisymmetric (r, z) form of the time step (Section 2.1: the planar
+// discretisation carried over to the cylindrical coordinate system; Section 4
+// Eq. (curv_ax)).  Grid: x = r from the axis (r = 0 at the left edge),
+// y = z; cell (i, j) centred at r = (i + 1/2) h, x-face i at r = i h (face 0
+// is the axis, where u = 0).  Operators are finite-volume balances of ring
+// control volumes (volume r h^2 per radian, face areas r_face h).
+//
+// The pressure equation (1/r) d/dr (r beta dp/dr) + d/dz (beta dp/dz) = b is
+// solved as r times itself: the planar 5-point operator with coefficients
+// r_face beta and right-hand side r_i b, which the multigrid handles
+// unchanged (the axis face has zero weight).
+//
+// Markers: a drop is its full closed meridian curve (right half and mirror
+// image at r < 0), kept mirror-symmetric.  The marker kernels run unchanged
+// on a planar grid widened by G ghost columns at r < 0 (origin -G h); the
+// velocity field is continued into the ghost columns by symmetry (u odd, w
+// even) before interpolation, and the Heaviside and face forces computed on
+// the wide grid are folded back onto the real cells and faces (the
+// conventional ring force divided by the face radius).
+#include <math.h>
+
+#include "ib_internal.cuh"
+
+namespace ibk {
+namespace {
+
+constexpr int kT = 256;
+
+// Tiled predictor in ring control volumes: the planar kernel's staging and
+// node averages; every flux carries the radius of its face and each balance
+// is divided by the radius of its control volume; the radial component adds
+// -mu_face u / r^2 (vector diffusion).
+constexpr int PX = 32, PY = 8;
+__global__ void __launch_bounds__(PX * PY)
+k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ rho,
+                const double *__restrict__ mu, const double *__restrict__ u,
+                const double *__restrict__ v, const double *__restrict__ aup,
+                const double *__restrict__ avp, int have_prev, double gx, double gy,
+                double *__restrict__ us, double *__restrict__ vs, double *__restrict__ au,
+                double *__restrict__ av)
+{
+    constexpr int W = PX + 2, Hh = PY + 2;
+    __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
+    __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
+    const int i0 = blockIdx.x * PX, j0 = blockIdx.y * PY;
+    const int t = threadIdx.y * PX + threadIdx.x;
+    const long nxf = nx + 1;
+    for (int k = t; k < Hh * (W + 1); k += PX * PY) {
+        const int r = k / (W + 1), c = k - r * (W + 1), gi = i0 - 1 + c, gj = j0 - 1 + r;
+        const bool inj = gj >= 0 && gj < ny;
+        if (c < W) {
+            const bool in = inj && gi >= 0 && gi < nx;
+            const long o = (long)gj * nx + gi;
+            sr[r][c] = in ? rho[o] : 0.0;
+            sm[r][c] = in ? mu[o] : 0.0;
+        }
+        su[r][c] = (inj && gi >= 0 && gi <= nx) ? u[(long)gj * nxf + gi] : 0.0;
+    }
+    for (int k = t; k < (Hh + 1) * W; k += PX * PY) {
+        const int r = k / W, c = k - r * W, gi = i0 - 1 + c, gj = j0 - 1 + r;
+        sv[r][c] = (gi >= 0 && gi < nx && gj >= 0 && gj <= ny) ? v[(long)gj * nx + gi] : 0.0;
+    }
+    __syncthreads();
+    for (int k = t; k < (PY + 1) * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double *r0 = &sr[r][c], *r1 = &sr[r + 1][c];
+        const double *m0 = &sm[r][c], *m1 = &sm[r + 1][c];
+        const bool wx = I == 0 || I == nx, wy = J == 0 || J == ny;
+        nr[r][c] = 0.25 * (r0[0] + r0[1] + r1[0] + r1[1]);
+        if (!wx && !wy) nm[r][c] = 0.25 * (m0[0] + m0[1] + m1[0] + m1[1]);
+        else if (wy && !wx) nm[r][c] = J == 0 ? 0.5 * (m1[0] + m1[1]) : 0.5 * (m0[0] + m0[1]);
+        else if (wx && !wy) nm[r][c] = I == 0 ? 0.5 * (m0[1] + m1[1]) : 0.5 * (m0[0] + m1[0]);
+        else nm[r][c] = 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
+    if (i >= nx || j >= ny) return;
+    const int R = ty + 1, C = tx + 1;
+    const double h2 = h * h;
+    // radial face (i, j) at r = i h, control volume [r_(i-1), r_i]
+    {
+        const long k = (long)j * nxf + i;
+        if (i == 0) {
+            us[k] = 0.0; au[k] = 0.0;
+        } else {
+            const double r0 = i * h, rE = (i + 0.5) * h, rW = (i - 0.5) * h;
+            const double uc = su[R][C], uE = su[R][C + 1], uW = su[R][C - 1];
+            const double uN = (j + 1 < ny) ? su[R + 1][C] : -uc;
+            const double uS = (j > 0) ? su[R - 1][C] : -uc;
+            const double aE = 0.5 * (uE + uc), aW = 0.5 * (uc + uW);
+            const double fE = rE * sr[R][C] * aE * aE, fW = rW * sr[R][C - 1] * aW * aW;
+            double gN = 0.0, gS = 0.0;
+            if (j + 1 < ny)
+                gN = r0 * nr[ty + 1][tx] * (0.5 * (sv[R + 1][C - 1] + sv[R + 1][C])) * (0.5 * (uc + uN));
+            if (j > 0) gS = r0 * nr[ty][tx] * (0.5 * (sv[R][C - 1] + sv[R][C])) * (0.5 * (uc + uS));
+            const double muN = nm[ty + 1][tx], muS = nm[ty][tx];
+            const double adv = ((fE - fW) + (gN - gS)) / (r0 * h);
+            const double muf = 0.5 * (sm[R][C - 1] + sm[R][C]);
+            const double vis = (rE * sm[R][C] * (uE - uc) - rW * sm[R][C - 1] * (uc - uW) +
+                                r0 * muN * (uN - uc) - r0 * muS * (uc - uS)) / (r0 * h2) -
+                               muf * uc / (r0 * r0);
+            const double rf = 0.5 * (sr[R][C - 1] + sr[R][C]);
+            const double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
+            us[k] = uc + dt * ((vis - ae) / rf + gx);
+            au[k] = adv;
+        }
+        if (i == nx - 1) { us[k + 1] = 0.0; au[k + 1] = 0.0; }
+    }
+    // axial face (i, j) at r = (i + 1/2) h, control volume [i h, (i + 1) h]
+    {
+        const long k = (long)j * nx + i;
+        if (j == 0) {
+            vs[k] = 0.0; av[k] = 0.0;
+        } else {
+            const double r0 = (i + 0.5) * h, rE = (i + 1) * h, rW = i * h;
+            const double vc = sv[R][C], vN = sv[R + 1][C], vS = sv[R - 1][C];
+            const double vE = (i + 1 < nx) ? sv[R][C + 1] : -vc;
+            const double vW = (i > 0) ? sv[R][C - 1] : vc;  // symmetric across the axis
+            const double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
+            const double fN = r0 * sr[R][C] * aN * aN, fS = r0 * sr[R - 1][C] * aS * aS;
+            double gE = 0.0, gW = 0.0;
+            if (i + 1 < nx)
+                gE = rE * nr[ty][tx + 1] * (0.5 * (su[R - 1][C + 1] + su[R][C + 1])) * (0.5 * (vc + vE));
+            if (i > 0) gW = rW * nr[ty][tx] * (0.5 * (su[R - 1][C] + su[R][C])) * (0.5 * (vc + vW));
+            const double muE = nm[ty][tx + 1], muW = nm[ty][tx];
+            const double adv = ((fN - fS) + (gE - gW)) / (r0 * h);
+            const double vis = (r0 * sm[R][C] * (vN - vc) - r0 * sm[R - 1][C] * (vc - vS) +
+                                rE * muE * (vE - vc) - rW * muW * (vc - vW)) / (r0 * h2);
+            const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
+            const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
+            vs[k] = vc + dt * ((vis - ae) / rf + gy);
+            av[k] = adv;
+        }
+        if (j == ny - 1) { vs[k + nx] = 0.0; av[k + nx] = 0.0; }
+    }
+}
+
+// r_i b with b = div(u*/dt + beta F) in the axisymmetric divergence: the
+// right-hand side of the r-weighted pressure equation.
+__global__ void k_rhs_axi(int nx, int ny, double h, double idt, const double *__restrict__ us,
+                          const double *__restrict__ vs, const double *__restrict__ Fx,
+                          const double *__restrict__ Fy, const double *__restrict__ bx,
+                          const double *__restrict__ by, double *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const long xw = (long)j * (nx + 1) + i, ys = (long)j * nx + i, yn = ys + nx;
+    const double qE = us[xw + 1] * idt + bx[xw + 1] * Fx[xw + 1];
+    const double qW = us[xw] * idt + bx[xw] * Fx[xw];
+    const double qN = vs[yn] * idt + by[yn] * Fy[yn];
+    const double qS = vs[ys] * idt + by[ys] * Fy[ys];
+    const double ri = (i + 0.5) * h;
+    const double bb = ((i + 1) * h * qE - i * h * qW) / (ri * h) + (qN - qS) / h;
+    b[ys] = ri * bb;
+}
+
+// Coefficients of the r-weighted pressure operator: r_face beta_x, r_i beta_y.
+__global__ void k_axi_weights(int nx, int ny, double h, const double *__restrict__ bx,
+                              const double *__restrict__ by, double *__restrict__ bxa,
+                              double *__restrict__ bya)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (j < ny && i <= nx) {
+        const long k = (long)j * (nx + 1) + i;
+        bxa[k] = (i * h) * bx[k];
+    }
+    if (i < nx) {
+        const long k = (long)j * nx + i;
+        bya[k] = ((i + 0.5) * h) * by[k];
+    }
+}
+
+// Velocity on the wide marker grid (G ghost columns at r < 0): u odd and w
+// even across the axis (x-face -i mirrors face i, cell -1-i mirrors cell i).
+__global__ void k_axi_extend(int nx, int ny, int G, const double *__restrict__ u,
+                             const double *__restrict__ v, double *__restrict__ uw,
+                             double *__restrict__ vw)
+{
+    const int iw = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int nw = nx + G;
+    if (j < ny && iw <= nw) {
+        const int i = iw - G;
+        const double val = i >= 0 ? u[(long)j * (nx + 1) + i] : -u[(long)j * (nx + 1) - i];
+        uw[(long)j * (nw + 1) + iw] = val;
+    }
+    if (iw < nw) {
+        const int i = iw - G;
+        vw[(long)j * nw + iw] = v[(long)j * nx + (i >= 0 ? i : -1 - i)];
+    }
+}
+
+// Real cells and faces from the wide grid: H, and the face forces (divided
+// by the face radius for the ring-weighted conventional force); the axis and
+// the outer wall carry no radial force.
+__global__ void k_axi_fold(int nx, int ny, int G, double h, int ring, const double *__restrict__ Hw,
+                           const double *__restrict__ Fxw, const double *__restrict__ Fyw,
+                           double *__restrict__ H, double *__restrict__ Fx, double *__restrict__ Fy)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int nw = nx + G;
+    if (Hw && j < ny && i < nx) H[(long)j * nx + i] = Hw[(long)j * nw + i + G];
+    if (!Fxw) return;
+    if (j < ny && i <= nx) {
+        double f = 0.0;
+        if (i > 0 && i < nx) {
+            f = Fxw[(long)j * (nw + 1) + i + G];
+            if (ring) f /= i * h;
+        }
+        Fx[(long)j * (nx + 1) + i] = f;
+    }
+    if (i < nx) {
+        double f = Fyw[(long)j * nw + i + G];
+        if (ring) f /= (i + 0.5) * h;
+        Fy[(long)j * nx + i] = f;
+    }
+}
+
+// Section 4 Eq. (curv_ax): the planar (meridian) curvature of k_geometry plus
+// the azimuthal -n_r / r (its limit, the meridian curvature, on the axis);
+// force magnitude sigma kappa.
+__global__ void k_axi_curvature(int M, double sigma, const double *__restrict__ X,
+                                const double *__restrict__ nxm, const double *__restrict__ ds,
+                                double *__restrict__ kappa, double *__restrict__ fmag)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double x = X[m], k = kappa[m];
+    const double kaz = fabs(x) <= 1e-9 * ds[m] ? k : -nxm[m] / x;
+    const double kk = k + kaz;
+    kappa[m] = kk;
+    fmag[m] = sigma * kk;
+}
+
+// Ring magnitude of the conventional spreading: fmag |r| (the force per unit
+// length of the marker's ring, up to the 2 pi shared with the face rings).
+__global__ void k_axi_ring(int M, const double *__restrict__ fmag, const double *__restrict__ X,
+                           double *__restrict__ fr)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) fr[m] = fmag[m] * fabs(X[m]);
+}
+
+// Mirror symmetry of each drop's meridian curve: marker k of a drop of n
+// pairs with (n - k) mod n; each pair becomes its symmetric mean (one thread
+// per pair, k = 0 .. n/2; markers 0 and n/2 land on the axis).
+__global__ void k_axi_symmetrise(int ndrops, const int32_t *__restrict__ drop_start,
+                                 double *__restrict__ X, double *__restrict__ Y)
+{
+    const int d = blockIdx.y;
+    if (d >= ndrops) return;
+    const int s = drop_start[d], n = drop_start[d + 1] - s;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n / 2) return;
+    const int p = (n - k) % n;
+    const double xk = X[s + k], xp = X[s + p], yk = Y[s + k], yp = Y[s + p];
+    const double x = 0.5 * (xk - xp), y = 0.5 * (yk + yp);
+    X[s + k] = x;
+    Y[s + k] = y;
+    if (p != k) {
+        X[s + p] = 0.5 * (xp - xk);
+        Y[s + p] = y;
+    }
+}
+
+}  // namespace
+
+void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
+                          const double *mu, const double *u, const double *v,
+                          const double *au_prev, const double *av_prev, int have_prev,
+                          double gx, double gy, double *us, double *vs, double *au, double *av,
+                          cudaStream_t s)
+{
+    dim3 g(cdiv(nx, PX), cdiv(ny, PY)), b(PX, PY);
+    note_launch();
+    k_predictor_axi<<<g, b, 0, s>>>(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx,
+                                    gy, us, vs, au, av);
+}
+
+void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,
+                    const double *Fx, const double *Fy, const double *bx, const double *by,
+                    double *b, cudaStream_t s)
+{
+    dim3 g(cdiv(nx, 128), ny);
+    note_launch();
+    k_rhs_axi<<<g, 128, 0, s>>>(nx, ny, h, 1.0 / dt, us, vs, Fx, Fy, bx, by, b);
+}
+
+void launch_axi_weights(int nx, int ny, double h, const double *bx, const double *by,
+                        double *bxa, double *bya, cudaStream_t s)
+{
+    dim3 g(cdiv(nx + 1, 128), ny + 1);
+    note_launch();
+    k_axi_weights<<<g, 128, 0, s>>>(nx, ny, h, bx, by, bxa, bya);
+}
+
+void launch_axi_extend(int nx, int ny, int G, const double *u, const double *v, double *uw,
+                       double *vw, cudaStream_t s)
+{
+    dim3 g(cdiv(nx + G + 1, 128), ny + 1);
+    note_launch();
+    k_axi_extend<<<g, 128, 0, s>>>(nx, ny, G, u, v, uw, vw);
+}
+
+void launch_axi_fold(int nx, int ny, int G, double h, int ring, const double *Hw, const double *Fxw,
+                     const double *Fyw, double *H, double *Fx, double *Fy, cudaStream_t s)
+{
+    dim3 g(cdiv(nx + 1, 128), ny + 1);
+    note_launch();
+    k_axi_fold<<<g, 128, 0, s>>>(nx, ny, G, h, ring, Hw, Fxw, Fyw, H, Fx, Fy);
+}
+
+void launch_axi_curvature(Markers &mk, double sigma, cudaStream_t s)
+{
+    note_launch();
+    k_axi_curvature<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, sigma, mk.X, mk.nxm, mk.ds, mk.kappa,
+                                                  mk.fmag);
+}
+
+void launch_axi_ring(const Markers &mk, const double *fmag, double *fr, cudaStream_t s)
+{
+    note_launch();
+    k_axi_ring<<<cdiv(mk.M, kT), kT, 0, s>>>(mk.M, fmag, mk.X, fr);
+}
+
+void launch_axi_symmetrise(Markers &mk, cudaStream_t s)
+{
+    dim3 g(cdiv(mk.max_drop / 2 + 1, kT), mk.ndrops);
+    note_launch();
+    k_axi_symmetrise<<<g, kT, 0, s>>>(mk.ndrops, mk.drop_start, mk.X, mk.Y);
+}
+
+}  // namespace ibk

@@ -64,6 +64,22 @@ void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       int have_prev, double gx, double gy, double *us,
                       double *vs, double *au, double *av, cudaStream_t s);
 
+// ------------------------------------------------------------ axisymmetric
+void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
+                          const double *mu, const double *u, const double *v,
+                          const double *au_prev, const double *av_prev, int have_prev,
+                          double gx, double gy, double *us, double *vs, double *au, double *av,
+                          cudaStream_t s);
+void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,
+                    const double *Fx, const double *Fy, const double *bx, const double *by,
+                    double *b, cudaStream_t s);
+void launch_axi_weights(int nx, int ny, double h, const double *bx, const double *by,
+                        double *bxa, double *bya, cudaStream_t s);
+void launch_axi_extend(int nx, int ny, int G, const double *u, const double *v, double *uw,
+                       double *vw, cudaStream_t s);
+void launch_axi_fold(int nx, int ny, int G, double h, int ring, const double *Hw, const double *Fxw,
+                     const double *Fyw, double *H, double *Fx, double *Fy, cudaStream_t s);
+
 // ---------------------------------------------------------------- multigrid
 template <typename T>
 struct LevelT {
@@ -223,6 +239,9 @@ void launch_band_area(const Markers &mk, cudaStream_t s);
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
                          double *Fx, double *Fy, cudaStream_t s);
 void launch_relocate(Markers &mk, cudaStream_t s);
+void launch_axi_curvature(Markers &mk, double sigma, cudaStream_t s);
+void launch_axi_ring(const Markers &mk, const double *fmag, double *fr, cudaStream_t s);
+void launch_axi_symmetrise(Markers &mk, cudaStream_t s);
 
 // ---------------------------------------------------------------- CNN
 struct Cnn;
