@@ -31,12 +31,16 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = ("pressure-solve ms & steps/s, FP64 MG vs mixed/NN-start at equal residual; %HBM")
+SOLVERS = {0: "FP64 V(2,2)",
+           1: "FP32 V(2,2) in FP64 defect correction",
+           2: "FP32 V(2,2), two per FP64 residual, in FP64 defect correction"}
 WORKLOADS = {
     "multidrop1024": dict(n=1024, kind="multi"),
     "multidrop512": dict(n=512, kind="multi16"),
     "multidrop2048": dict(n=2048, kind="multi"),
     "oscillating256": dict(n=256, kind="osc"),
     "static64": dict(n=64, kind="static"),
+    "freefall_axi": dict(n=256, kind="freefall"),
 }
 
 
@@ -48,7 +52,25 @@ def make_markers(name, seed_offset=0):
         return W.multidrop(wl["n"], ndrops=16, rmin=0.02, rmax=0.06, seed=1811 + seed_offset)
     if wl["kind"] == "osc":
         return W.oscillating_drop(seed=1808 + seed_offset)
+    if wl["kind"] == "freefall":
+        return W.freefall_axi()[0]
     return W.static_drop(wl["n"], 0.25, 128)
+
+
+def problem(name):
+    """Grid, physical constants and time step of a workload: (nx, ny, Config
+    keyword arguments shared by the library and the oracle, dt).  Planar
+    workloads: unit box, density ratio 1000, viscosity ratio 100, sigma 1.
+    freefall_axi: the axisymmetric water drop in air (SI units) under gravity
+    in the non-inertial frame."""
+    if WORKLOADS[name]["kind"] == "freefall":
+        _, c = W.freefall_axi()
+        kw = dict(h=c["h"], rho_l=c["rho_l"], rho_g=c["rho_g"], mu_l=c["mu_l"], mu_g=c["mu_g"],
+                  sigma=c["sigma"], gy=-c["g"], axisym=1, frame=1)
+        dt = W.capillary_dt(c["h"], c["rho_l"], c["rho_g"], c["sigma"], c["mu_l"], c["mu_g"])
+        return c["nx"], c["ny"], kw, dt
+    n = WORKLOADS[name]["n"]
+    return n, n, dict(h=1.0 / n), W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
 
 
 def max_over_ranks(x: float) -> float:
@@ -161,10 +183,9 @@ def cpu_baseline(name, steps=1):
     import oracle as O
     O.build()
     mk = make_markers(name)
-    n = WORKLOADS[name]["n"]
-    cfg = O.Config(nx=n, ny=n, h=1.0 / n, precision=1, spread=1, relocate_every=10)
+    nx, ny, kw, dt = problem(name)
+    cfg = O.Config(nx=nx, ny=ny, precision=2, spread=1, relocate_every=10, **kw)
     st = O.init_state(cfg, mk.X, mk.Y, mk.drop_start)
-    dt = W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
     t0 = time.perf_counter()
     for _ in range(steps):
         O.ns_step(cfg, st, dt)
@@ -183,10 +204,9 @@ def run_reference(args):
     import oracle as O
     O.build()
     mk = make_markers(name)
-    n = WORKLOADS[name]["n"]
-    cfg = O.Config(nx=n, ny=n, h=1.0 / n, precision=1, spread=1, relocate_every=10)
+    nx, ny, kw, dt = problem(name)
+    cfg = O.Config(nx=nx, ny=ny, precision=args.precision, spread=1, relocate_every=10, **kw)
     st = O.init_state(cfg, mk.X, mk.Y, mk.drop_start)
-    dt = W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
     done, t = 0, 0.0
     while done < args.steps and (done == 0 or t < 60.0):
         t0 = time.perf_counter()
@@ -198,8 +218,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / done, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": name, "solver": "FP32 V(2,2) in FP64 defect correction",
+        "vs_baseline": None, "dtype": "f64+f32" if args.precision >= 1 else "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "nx": nx, "ny": ny, "solver": SOLVERS[args.precision],
                    "tol": 1e-10},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{done} of the {args.steps} requested oracle time steps of "
@@ -223,17 +244,19 @@ def run_ours(args):
         dist.init_process_group("nccl")
     ib.lib()
     name = args.workload
-    n = WORKLOADS[name]["n"]
-    h = 1.0 / n
+    nx, ny, kw, dt = problem(name)
+    axi = bool(kw.get("axisym"))
+    if axi:
+        args.no_cnn = True  # the network is trained for the planar equation
+    h = kw["h"]
     mk = make_markers(name, seed_offset=rank)  # independent problem per rank
-    cfg = ib.Config(nx=n, ny=n, h=h, precision=args.precision, spread=1, relocate_every=10,
-                    tol=1e-10, max_cycles=200)
+    cfg = ib.Config(nx=nx, ny=ny, precision=args.precision, spread=1, relocate_every=10,
+                    tol=1e-10, max_cycles=200, **kw)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
     if args.no_graphs:
         ctx.use_graphs(False)
-    dt = W.capillary_dt(h, cfg.rho_l, cfg.rho_g, cfg.sigma, cfg.mu_l, cfg.mu_g)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
@@ -307,7 +330,7 @@ def run_ours(args):
     for prec, label in ((0, "fp64"), (1, "mixed"), (2, "mixed2")):
         times, cyc = [], None
         for rep in range(3 + 5):
-            p = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+            p = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -381,7 +404,7 @@ def run_ours(args):
                 times.append(e0.elapsed_time(e1))
         solve["mixed_cnn"] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr,
                               "solver": "mixed2 (two FP32 V-cycles per FP64 residual)",
-                              "inference_grid": n >> args.cnn_coarsen,
+                              "inference_grid": nx >> args.cnn_coarsen,
                               "train": {"samples": args.cnn_samples, "steps": len(losses),
                                         "final_loss": losses[-1], "seconds": train_s}}
         del net
@@ -391,7 +414,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: markers in, pressure out
     Xh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
     Yh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
-    ph = torch.empty((n, n), dtype=torch.float64).pin_memory().numpy()
+    ph = torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy()
     ctx.get_markers_host(Xh, Yh)
     e2e_steps = max(3, args.steps // 2)
     barrier()
@@ -410,20 +433,20 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision >= 1 else "f64", "data": "synthetic",
-        "config": {"workload": name, "nx": n, "ny": n, "drops": int(mk.ndrops),
-                   "markers": int(mk.M), "density_ratio": 1000, "viscosity_ratio": 100,
+        "config": {"workload": name, "nx": nx, "ny": ny, "drops": int(mk.ndrops),
+                   "markers": int(mk.M),
+                   "density_ratio": round(cfg.rho_l / cfg.rho_g, 2),
+                   "viscosity_ratio": round(cfg.mu_l / cfg.mu_g, 2),
+                   "geometry": "axisymmetric (r, z), non-inertial frame" if axi else "planar",
                    "spread": "irrotational", "relocate_every": 10, "tol": 1e-10,
-                   "solver": {0: "FP64 V(2,2)",
-                              1: "FP32 V(2,2) in FP64 defect correction",
-                              2: "FP32 V(2,2), two per FP64 residual, in FP64 defect correction"
-                              }[args.precision],
+                   "solver": SOLVERS[args.precision],
                    "warm_start": "previous pressure", "l2": "flushed before each step (256 MiB)",
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
         "clocks": clocks,
         "e2e": {"value": ws * e2e_steps / e2e_t, "unit": "steps/s",
                 "h2d_bytes_per_step": int(2 * ctx.M * 8),
-                "d2h_bytes_per_step": int(n * n * 8 + 2 * ctx.M * 8)},
+                "d2h_bytes_per_step": int(nx * ny * 8 + 2 * ctx.M * 8)},
         "gpu_launches": int(launches),
         "roofline": {"kernel": ("k_smooth2_f32<2> (fine level: prolongation + two FP32 red-black "
                                 "sweeps + FP64 update)" if args.precision >= 1 else
@@ -445,6 +468,14 @@ def run_ours(args):
         "band_strip_areas": band,
         "mixed_cycle_kernels": kernel_table,
     }
+    if axi:
+        # the drop's fall so far: every ns_step of this run advanced it by dt
+        com, S, vf, wb = ctx.frame_state()
+        nsteps = args.warmup + 2 * args.steps + e2e_steps
+        line["frame"] = {"steps": nsteps, "dt_s": dt, "t_s": nsteps * dt,
+                         "drop_velocity_m_s": vf, "drop_centre_m": com,
+                         "release_acceleration_m_s2": -kw["gy"] * (cfg.rho_l - cfg.rho_g)
+                                                      / (cfg.rho_l + 0.5 * cfg.rho_g)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, t = cpu_baseline(name, 1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",

@@ -66,6 +66,17 @@ typedef struct ib_config {
                                  mirror image, an even number of markers, marker k
                                  and n - k mirror images, 0 and n/2 on the axis);
                                  gx must be 0.  0: planar */
+    int32_t frame;            /* axisymmetric only.  1: non-inertial frame following drop 0,
+                                 Sec. 2.4 Eqs. (fictitious), (fic_1), (fic_2): every step
+                                 all fluid gets the axial acceleration S = (c1 (COM_o - COM_n)
+                                 - c2 (COM_n - COM_(n-1))) / dt^2 (COM: drop 0's
+                                 volume-weighted axial centre, COM_o its value at
+                                 ib_init), the frame velocity Vf changes by -S dt, and
+                                 the ambient fluid enters at z = 0, leaves at z = Lz
+                                 and slides along the outer wall with axial velocity
+                                 -Vf (a laboratory at rest seen from the frame).
+                                 0: fixed walls */
+    double c1, c2;            /* the constants of Eq. (fictitious) (the paper: 0.1, 0.1) */
 } ib_config;
 
 typedef struct ib_ctx ib_ctx;
@@ -171,6 +182,12 @@ ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
  * multiple of 4).  The last step's cycles and residual are returned by
  * ib_last_solve.                                                           */
 ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
+/* Non-inertial frame (cfg.frame = 1): out[0] drop 0's axial centre of mass,
+ * out[1] the acceleration S of the next step, out[2] the frame velocity Vf
+ * (the drop's velocity in the laboratory, up to its small drift in the
+ * frame), out[3] the boundary velocity -Vf; host array, synchronises.
+ * IB_EINVAL without a frame.                                               */
+ib_status ib_frame_state(ib_ctx *ctx, double *out);
 ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
 
 /* ---------------------------------------------------------------------- */
@@ -343,7 +360,10 @@ ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt,
  * from the axis, cell i at r = (i + 1/2) h, x-face i at r = i h).
  * Predictor: the same AB2 + viscous update on ring control volumes (fluxes
  * times their face radius over the volume radius; the radial component adds
- * -mu u / r^2), u = 0 on the axis and walls, gy the axial body acceleration.
+ * -mu u / r^2), u = 0 on the axis and walls, gy the axial body acceleration;
+ * frame: NULL (fixed walls) or device doubles whose slot 3 is an extra axial
+ * acceleration S and slot 5 the axial velocity wb of the z boundaries and
+ * the outer wall (the non-inertial frame's record).
  * Right-hand side: r_i div(u* / dt + beta F) with the axisymmetric
  * divergence (the right-hand side of the r-weighted pressure equation).
  * Weights: bxa = r_face bx, bya = r_i by (its coefficients).               */
@@ -351,8 +371,9 @@ ib_status ib_op_predictor_axi(int32_t nx, int32_t ny, double h, double dt,
                               const double *rho, const double *mu,
                               const double *u, const double *v,
                               const double *au_prev, const double *av_prev,
-                              int32_t have_prev, double gy, double *us,
-                              double *vs, double *au, double *av, void *stream);
+                              int32_t have_prev, double gy, const double *frame,
+                              double *us, double *vs, double *au, double *av,
+                              void *stream);
 ib_status ib_op_rhs_axi(int32_t nx, int32_t ny, double h, double dt,
                         const double *us, const double *vs, const double *Fx,
                         const double *Fy, const double *bx, const double *by,

@@ -88,7 +88,7 @@ def lib():
             "or_divergence_axi": (None, [_i, _i, _d, _D, _D, _D]),
             "or_rhs_axi": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D]),
             "or_predictor_axi": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _i, _d, _d,
-                                        _D, _D, _D, _D]),
+                                        _d, _D, _D, _D, _D]),
             "or_curvature_axi": (None, [_i, _D, _D, _i, _I32, _D, _D, _D, _D]),
             "or_spread_conv_axi": (None, [_i, _i, _i, _d, _i, _D, _D, _D, _D, _D, _D, _D,
                                           _D]),
@@ -354,7 +354,7 @@ def rhs_axi(us, vs, Fx, Fy, bx, by, h, dt):
     return b
 
 
-def predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0)):
+def predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0), wb=0.0):
     ny, nx = rho.shape
     have = au_prev is not None
     aup = _f64(au_prev) if have else np.zeros((ny, nx + 1))
@@ -362,7 +362,7 @@ def predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, g=(0.0, 0.0)
     us, vs = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
     au, av = np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
     lib().or_predictor_axi(nx, ny, h, dt, _f64(rho), _f64(mu), _f64(u), _f64(v), aup, avp,
-                           int(have), float(g[0]), float(g[1]), us, vs, au, av)
+                           int(have), float(g[0]), float(g[1]), float(wb), us, vs, au, av)
     return us, vs, au, av
 
 
@@ -442,6 +442,9 @@ class Config:
     nu2: int = 2
     relocate_every: int = 10  # 0 = never
     axisym: int = 0           # 1: (r, z) with x = r from the axis (x0 = 0)
+    frame: int = 0            # 1: non-inertial frame following drop 0 (axisym only)
+    c1: float = 0.1           # Section 2.4 Eq. (fictitious) constants
+    c2: float = 0.1
 
 
 @dataclass
@@ -454,6 +457,7 @@ class State:
     drop_start: np.ndarray
     au: np.ndarray | None = None
     av: np.ndarray | None = None
+    frame: dict | None = None  # non-inertial frame: com0, com_prev, S, Vf
     step: int = 0
     last: dict = field(default_factory=dict)
 
@@ -502,6 +506,11 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
     is ring-weighted, and the pressure equation is solved as the symmetric
     r-weighted system (coefficients r_face beta, right-hand side r_i b)."""
     h = cfg.h
+    if cfg.frame and st.frame is None:
+        c0 = drop_com_axi(st.X, st.Y, st.drop_start, 0)[1]
+        st.frame = dict(com0=c0, com_prev=c0, S=0.0, Vf=0.0)
+    S = st.frame["S"] if cfg.frame else 0.0
+    wb = -st.frame["Vf"] if cfg.frame else 0.0
     if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
         st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
         st.X, st.Y = symmetrise(st.X, st.Y, st.drop_start)
@@ -509,7 +518,8 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, 0.0, cfg.y0)
     rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
-    us, vs, au, av = predictor_axi(rho, mu, st.u, st.v, h, dt, st.au, st.av, (0.0, cfg.gy))
+    us, vs, au, av = predictor_axi(rho, mu, st.u, st.v, h, dt, st.au, st.av, (0.0, cfg.gy + S),
+                                   wb)
     if cfg.spread == 0:
         Fx, Fy = spread_conv_axi(st.X, st.Y - cfg.y0, fmag, nxm, nym, ds, cfg.nx, cfg.ny, h,
                                  cfg.kernel)
@@ -521,9 +531,21 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
     res = mg_solve(bxa, bya, b * r[None, :], h, st.p, cfg.precision, cfg.tol, cfg.max_cycles,
                    cfg.nu1, cfg.nu2)
     u, v = correct(us, vs, res.p, Fx, Fy, bx, by, h, dt)
+    v[0, :] = wb      # the z boundaries keep their prescribed axial velocity
+    v[-1, :] = wb
     U, V = interp_axi(u, v, st.X, st.Y - cfg.y0, h, cfg.kernel)
     st.u, st.v, st.p, st.au, st.av = u, v, res.p, au, av
     st.X, st.Y = symmetrise(st.X + dt * U, st.Y + dt * V, st.drop_start)
+    if cfg.frame:
+        # Section 2.4 Eqs. (fictitious), (fic_1), (fic_2), read as a restoring
+        # law on drop 0's centre of mass: the acceleration all fluid feels in
+        # the next step, S = (c1 (COM_o - COM_n) - c2 (COM_n - COM_{n-1})) / dt^2;
+        # the frame velocity changed by -S dt during this step.
+        f = st.frame
+        com = drop_com_axi(st.X, st.Y, st.drop_start, 0)[1]
+        f["Vf"] = f["Vf"] - f["S"] * dt
+        f["S"] = (cfg.c1 * (f["com0"] - com) - cfg.c2 * (com - f["com_prev"])) / (dt * dt)
+        f["com_prev"] = com
     st.step += 1
     st.last = dict(H=H, rho=rho, bx=bx, by=by, Fx=Fx, Fy=Fy, b=b, cycles=res.cycles,
                    relres=res.relres, status=res.status, kappa=kap)

@@ -120,7 +120,8 @@ void or_rhs_axi(int nx, int ny, double h, double dt, const double *us, const dou
 void or_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                       const double *mu, const double *u, const double *v,
                       const double *au_prev, const double *av_prev, int have_prev,
-                      double gx, double gy, double *us, double *vs, double *au, double *av);
+                      double gx, double gy, double wb, double *us, double *vs, double *au,
+                      double *av);
 void or_curvature_axi(int M, const double *X, const double *Y, int ndrops,
                       const int32_t *drop_start, double *kappa, double *nxm, double *nym,
                       double *ds);

@@ -95,12 +95,17 @@ void or_rhs_axi(int nx, int ny, double h, double dt, const double *us, const dou
  * (mu the two-cell face average), the term that makes div(mu grad u) the
  * vector operator in cylindrical coordinates (reading: the paper's
  * div(mu grad u) form, no swirl).  u = 0 on the axis and the outer wall;
- * no-slip walls at z = 0, Lz by a reflected ghost value; (gx, gy) a uniform
- * body acceleration (gx = 0 on a symmetric problem).                       */
+ * the boundaries z = 0, Lz and the outer wall r = R move axially with
+ * velocity wb (0: fixed walls; in the drop's frame of Section 2.4 the
+ * ambient fluid streams past with wb): v = wb on the z boundary faces, and
+ * the reflected ghost value of a no-slip wall moving at wb is 2 wb - v
+ * (u's ghost -u at z = 0, Lz); (gx, gy) a uniform body acceleration (gx = 0
+ * on a symmetric problem).                                                 */
 void or_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                       const double *mu, const double *u, const double *v,
                       const double *au_prev, const double *av_prev, int have_prev,
-                      double gx, double gy, double *us, double *vs, double *au, double *av)
+                      double gx, double gy, double wb, double *us, double *vs, double *au,
+                      double *av)
 {
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++) {
@@ -143,10 +148,10 @@ void or_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
     for (int j = 0; j <= ny; j++)
         for (int i = 0; i < nx; i++) {
             size_t k = YF(i, j);
-            if (j == 0 || j == ny) { vs[k] = 0.0; av[k] = 0.0; continue; }
+            if (j == 0 || j == ny) { vs[k] = wb; av[k] = 0.0; continue; }
             double r0 = rc(i, h), rE = rf(i + 1, h), rW = rf(i, h);
             double vc = v[k], vN = v[YF(i, j + 1)], vS = v[YF(i, j - 1)];
-            double vE = (i + 1 < nx) ? v[YF(i + 1, j)] : -vc;
+            double vE = (i + 1 < nx) ? v[YF(i + 1, j)] : 2.0 * wb - vc;
             double vW = (i > 0) ? v[YF(i - 1, j)] : vc;  /* symmetric across the axis */
             double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
             double fN = r0 * rho[CC(i, j)] * aN * aN;

@@ -36,7 +36,7 @@ EXPORTS = [
     "ib_profile_end", "ib_bench_kernel", "mg_solve_noalloc", "cnn_init", "cnn_destroy", "cnn_num_params",
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
-    "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights",
+    "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
 ]
 
 
@@ -53,7 +53,8 @@ class ib_config(C.Structure):
                 ("gx", C.c_double), ("gy", C.c_double), ("kernel", C.c_int32),
                 ("spread", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_cycles", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
-                ("relocate_every", C.c_int32), ("axisym", C.c_int32)]
+                ("relocate_every", C.c_int32), ("axisym", C.c_int32), ("frame", C.c_int32),
+                ("c1", C.c_double), ("c2", C.c_double)]
 
 
 _lib = None
@@ -106,7 +107,8 @@ def lib():
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
                                 _P, _P, _P, _P],
             "ib_op_predictor_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _P,
-                                    _P, _P, _P, _P],
+                                    _P, _P, _P, _P, _P],
+            "ib_frame_state": [_P, _P],
             "ib_op_rhs_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P],
             "ib_op_axi_weights": [_i32, _i32, _d, _P, _P, _P, _P, _P],
         }
@@ -188,6 +190,9 @@ class Config:
     nu2: int = 2
     relocate_every: int = 10
     axisym: int = 0
+    frame: int = 0
+    c1: float = 0.1
+    c2: float = 0.1
 
     def c(self) -> ib_config:
         return ib_config(**{k: getattr(self, k) for k, _ in ib_config._fields_})
@@ -300,6 +305,13 @@ class Context:
 
     def relocate(self):
         _check(lib().ib_relocate(self._h), self._h)
+
+    def frame_state(self):
+        """(centre of mass, next acceleration S, frame velocity Vf, boundary
+        velocity) of the non-inertial frame."""
+        out = np.zeros(4)
+        _check(lib().ib_frame_state(self._h, out.ctypes.data), self._h)
+        return tuple(float(x) for x in out)
 
     def mg_setup(self, bx, by):
         torch = _torch()
@@ -520,15 +532,23 @@ def ib_op_correct(us, vs, p, Fx, Fy, bx, by, h, dt):
     return u, v
 
 
-def ib_op_predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, gy=0.0):
+def ib_op_predictor_axi(rho, mu, u, v, h, dt, au_prev=None, av_prev=None, gy=0.0, S=None,
+                        wb=None):
+    """Axisymmetric predictor; S (extra axial acceleration) and wb (axial
+    velocity of the z boundaries and the outer wall) go in a frame record."""
     torch = _torch()
     ny, nx = rho.shape
     us, vs, au, av = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(u),
                       torch.empty_like(v))
     have = au_prev is not None
+    frame = None
+    if S is not None or wb is not None:
+        frame = torch.zeros(8, dtype=torch.float64, device=u.device)
+        frame[3] = float(S or 0.0)
+        frame[5] = float(wb or 0.0)
     _op("ib_op_predictor_axi", nx, ny, h, dt, _ptr(rho), _ptr(mu), _ptr(u), _ptr(v),
-        _ptr(au_prev), _ptr(av_prev), int(have), float(gy), _ptr(us), _ptr(vs), _ptr(au),
-        _ptr(av))
+        _ptr(au_prev), _ptr(av_prev), int(have), float(gy), _ptr(frame), _ptr(us), _ptr(vs),
+        _ptr(au), _ptr(av))
     return us, vs, au, av
 
 

@@ -34,6 +34,7 @@ struct ib_ctx {
     int G = 0;
     double *uw = nullptr, *vw = nullptr, *Hw = nullptr, *Fxw = nullptr, *Fyw = nullptr,
            *bxa = nullptr, *bya = nullptr, *fr = nullptr;
+    double *frame = nullptr;   // non-inertial frame record (kFrSlots doubles)
     void *amem = nullptr;
 };
 
@@ -324,7 +325,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (g.nx < 2 || g.ny < 2 || (long)g.nx * g.ny > (1L << 28) || !(g.h > 0) || g.nu1 < 0 ||
         g.nu2 < 0 || g.max_cycles < 0 || !(g.tol >= 0) || g.kernel < 0 || g.kernel > 1 ||
         g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2 || g.axisym < 0 ||
-        g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)))
+        g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)) || g.frame < 0 || g.frame > 1 ||
+        (g.frame && (!g.axisym || !(g.c1 >= 0) || !(g.c2 >= 0))))
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -360,7 +362,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess && g.axisym) {
         const long nw = g.nx + c->G;
         const size_t wx = (size_t)(nw + 1) * g.ny, wy = (size_t)nw * (g.ny + 1), wc = (size_t)nw * g.ny;
-        const size_t ab = 2 * al(wx * 8) + 2 * al(wy * 8) + al(wc * 8) + al(fx * 8) + al(fy * 8) + al((size_t)M * 8);
+        const size_t ab = 2 * al(wx * 8) + 2 * al(wy * 8) + al(wc * 8) + al(fx * 8) + al(fy * 8) +
+                          al((size_t)M * 8) + al(kFrSlots * 8);
         e = cudaMalloc(&c->amem, ab);
         if (e == cudaSuccess) {
             char *a = (char *)c->amem;
@@ -370,6 +373,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
             c->Hw = tk(wc * 8);
             c->bxa = tk(fx * 8); c->bya = tk(fy * 8);
             c->fr = tk((size_t)M * 8);
+            c->frame = tk(kFrSlots * 8);
             e = cudaMemset(c->amem, 0, ab);
         } else {
             c->amem = nullptr;
@@ -381,6 +385,10 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->flags_host, 64);
     if (e == cudaSuccess) e = cudaMemcpy(c->mk.X, X, (size_t)M * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->mk.Y, Y, (size_t)M * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && g.frame) {
+        launch_axi_frame(c->mk, 1.0, g.c1, g.c2, 1, c->frame, c->s);
+        e = cudaStreamSynchronize(c->s);
+    }
     if (e != cudaSuccess) {
         ib_status r = (e == cudaErrorMemoryAllocation) ? IB_ENOMEM : IB_ECUDA;
         ib_destroy(c);
@@ -571,7 +579,8 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
             launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
             mg_build(c->mg, c->bxa, c->bya, c->s);
             launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
-                                 c->have_prev, 0.0, g.gy, c->us, c->vs, c->au, c->av, c->s);
+                                 c->have_prev, 0.0, g.gy, g.frame ? c->frame : nullptr, c->us,
+                                 c->vs, c->au, c->av, c->s);
         } else {
             mg_build(c->mg, c->bx, c->by, c->s);
             launch_predictor(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
@@ -595,7 +604,9 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (st != IB_OK && st != IB_ENOTCONV) return st;
         launch_correct(g.nx, g.ny, g.h, dt, c->us, c->vs, c->p, c->Fx, c->Fy, c->bx, c->by, c->u,
                        c->v, c->s);
+        if (g.frame) launch_axi_zbc(g.nx, g.ny, c->frame, c->v, c->s);
         interp_into(c, c->u, c->v, mk.U, mk.V, dt);
+        if (g.frame) launch_axi_frame(mk, dt, g.c1, g.c2, 0, c->frame, c->s);
         launch_validate(mk, c->s);
         c->have_prev = 1;
         c->step++;
@@ -661,6 +672,18 @@ ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_
     if (e != cudaSuccess) return cuda_check(c, e, "kernel timing");
     *us_per_launch = 1e3 * ms / reps;
     if (units) *units = u;
+    return IB_OK;
+}
+
+ib_status ib_frame_state(ib_ctx *c, double *out)
+{
+    if (!c || !out) return IB_EINVAL;
+    if (!c->cfg.frame) return fail(c, IB_EINVAL, "no non-inertial frame");
+    double f[kFrSlots];
+    cudaError_t e = cudaMemcpyAsync(f, c->frame, sizeof(f), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_check(c, e, "frame state");
+    out[0] = f[kFrCom]; out[1] = f[kFrS]; out[2] = f[kFrVf]; out[3] = f[kFrWb];
     return IB_OK;
 }
 
@@ -954,13 +977,13 @@ ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt, const dou
 ib_status ib_op_predictor_axi(int32_t nx, int32_t ny, double h, double dt, const double *rho,
                               const double *mu, const double *u, const double *v,
                               const double *au_prev, const double *av_prev, int32_t have_prev,
-                              double gy, double *us, double *vs, double *au, double *av,
-                              void *stream)
+                              double gy, const double *frame, double *us, double *vs, double *au,
+                              double *av, void *stream)
 {
     OPCHK(nx > 0 && ny > 0 && h > 0 && rho && mu && u && v && us && vs && au && av);
     OPCHK(!have_prev || (au_prev && av_prev));
-    launch_predictor_axi(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, 0.0, gy, us,
-                         vs, au, av, (cudaStream_t)stream);
+    launch_predictor_axi(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, 0.0, gy, frame,
+                         us, vs, au, av, (cudaStream_t)stream);
     return op_done();
 }
 

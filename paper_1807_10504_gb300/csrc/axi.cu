@@ -29,17 +29,21 @@ constexpr int kT = 256;
 // Tiled predictor in ring control volumes: the planar kernel's staging and
 // node averages; every flux carries the radius of its face and each balance
 // is divided by the radius of its control volume; the radial component adds
-// -mu_face u / r^2 (vector diffusion).
+// -mu_face u / r^2 (vector diffusion).  With a frame record (non-inertial
+// frame, see k_axi_frame) the axial body acceleration adds its S and the
+// boundaries z = 0, Lz and the outer wall move axially with its wb: v = wb
+// on the z boundary faces, the outer wall's reflected ghost is 2 wb - v.
 constexpr int PX = 32, PY = 8;
 __global__ void __launch_bounds__(PX * PY)
 k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ rho,
                 const double *__restrict__ mu, const double *__restrict__ u,
                 const double *__restrict__ v, const double *__restrict__ aup,
                 const double *__restrict__ avp, int have_prev, double gx, double gy,
-                double *__restrict__ us, double *__restrict__ vs, double *__restrict__ au,
-                double *__restrict__ av)
+                const double *__restrict__ frame, double *__restrict__ us,
+                double *__restrict__ vs, double *__restrict__ au, double *__restrict__ av)
 {
     constexpr int W = PX + 2, Hh = PY + 2;
+    const double gz = gy + (frame ? frame[kFrS] : 0.0), wb = frame ? frame[kFrWb] : 0.0;
     __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
     __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
     const int i0 = blockIdx.x * PX, j0 = blockIdx.y * PY;
@@ -111,11 +115,11 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
     {
         const long k = (long)j * nx + i;
         if (j == 0) {
-            vs[k] = 0.0; av[k] = 0.0;
+            vs[k] = wb; av[k] = 0.0;
         } else {
             const double r0 = (i + 0.5) * h, rE = (i + 1) * h, rW = i * h;
             const double vc = sv[R][C], vN = sv[R + 1][C], vS = sv[R - 1][C];
-            const double vE = (i + 1 < nx) ? sv[R][C + 1] : -vc;
+            const double vE = (i + 1 < nx) ? sv[R][C + 1] : 2.0 * wb - vc;
             const double vW = (i > 0) ? sv[R][C - 1] : vc;  // symmetric across the axis
             const double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
             const double fN = r0 * sr[R][C] * aN * aN, fS = r0 * sr[R - 1][C] * aS * aS;
@@ -129,10 +133,10 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
                                 rE * muE * (vE - vc) - rW * muW * (vc - vW)) / (r0 * h2);
             const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
-            vs[k] = vc + dt * ((vis - ae) / rf + gy);
+            vs[k] = vc + dt * ((vis - ae) / rf + gz);
             av[k] = adv;
         }
-        if (j == ny - 1) { vs[k + nx] = 0.0; av[k + nx] = 0.0; }
+        if (j == ny - 1) { vs[k + nx] = wb; av[k + nx] = 0.0; }
     }
 }
 
@@ -263,18 +267,88 @@ __global__ void k_axi_symmetrise(int ndrops, const int32_t *__restrict__ drop_st
     }
 }
 
+// Prescribed axial velocity wb of the z boundary faces (frame record).
+__global__ void k_axi_zbc(int nx, int ny, const double *__restrict__ frame, double *__restrict__ v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const double wb = frame[kFrWb];
+    v[i] = wb;
+    v[(long)ny * nx + i] = wb;
+}
+
+// Volume-weighted axial centre of drop d: the right half of its meridian
+// (markers 0 .. n/2, from the bottom axis point to the top one) closed along
+// the axis, by Green's theorem per straight edge,
+//   int int r dA = sum (z2 - z1)(r1^2 + r1 r2 + r2^2) / 6,
+//   int int r z dA = sum (z2 - z1)(r1^2 (3 z1 + z2) + 2 r1 r2 (z1 + z2)
+//                                  + r2^2 (z1 + 3 z2)) / 24,
+// summed edge by edge in marker order (the axis edge adds nothing).
+__device__ double drop_zc(const double *X, const double *Y, int s, int n)
+{
+    double I1 = 0.0, I2 = 0.0;
+    for (int k = 0; k < n / 2; k++) {
+        const double r1 = X[s + k], z1 = Y[s + k], r2 = X[s + k + 1], z2 = Y[s + k + 1];
+        I1 += (z2 - z1) * (r1 * r1 + r1 * r2 + r2 * r2) / 6.0;
+        I2 += (z2 - z1) * (r1 * r1 * (3.0 * z1 + z2) + 2.0 * r1 * r2 * (z1 + z2) +
+                           r2 * r2 * (z1 + 3.0 * z2)) / 24.0;
+    }
+    return I1 != 0.0 ? I2 / I1 : 0.0;
+}
+
+// Non-inertial frame following drop 0 (Section 2.4 Eqs. (fictitious),
+// (fic_1), (fic_2), read as a restoring law on the drop's centre of mass):
+// after a step that applied acceleration S to all fluid, the frame velocity
+// Vf changes by -S dt and the next step's S = (c1 (COM_o - COM_n) -
+// c2 (COM_n - COM_(n-1))) / dt^2; the ambient fluid at rest in the
+// laboratory streams past the frame with wb = -Vf.  init: COM_o = COM_(n-1)
+// = the current centre, S = Vf = wb = 0.  One thread.
+__global__ void k_axi_frame(const double *__restrict__ X, const double *__restrict__ Y,
+                            const int32_t *__restrict__ drop_start, double dt, double c1,
+                            double c2, int init, double *__restrict__ frame)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int s = drop_start[0], n = drop_start[1] - s;
+    const double com = drop_zc(X, Y, s, n);
+    if (init) {
+        frame[kFrCom0] = com; frame[kFrComPrev] = com; frame[kFrCom] = com;
+        frame[kFrS] = 0.0; frame[kFrVf] = 0.0; frame[kFrWb] = 0.0;
+        return;
+    }
+    const double vf = frame[kFrVf] - frame[kFrS] * dt;
+    const double S = (c1 * (frame[kFrCom0] - com) - c2 * (com - frame[kFrComPrev])) / (dt * dt);
+    frame[kFrVf] = vf;
+    frame[kFrS] = S;
+    frame[kFrComPrev] = com;
+    frame[kFrCom] = com;
+    frame[kFrWb] = -vf;
+}
+
 }  // namespace
 
 void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                           const double *mu, const double *u, const double *v,
                           const double *au_prev, const double *av_prev, int have_prev,
-                          double gx, double gy, double *us, double *vs, double *au, double *av,
-                          cudaStream_t s)
+                          double gx, double gy, const double *frame, double *us, double *vs,
+                          double *au, double *av, cudaStream_t s)
 {
     dim3 g(cdiv(nx, PX), cdiv(ny, PY)), b(PX, PY);
     note_launch();
     k_predictor_axi<<<g, b, 0, s>>>(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx,
-                                    gy, us, vs, au, av);
+                                    gy, frame, us, vs, au, av);
+}
+
+void launch_axi_zbc(int nx, int ny, const double *frame, double *v, cudaStream_t s)
+{
+    note_launch();
+    k_axi_zbc<<<cdiv(nx, 128), 128, 0, s>>>(nx, ny, frame, v);
+}
+
+void launch_axi_frame(const Markers &mk, double dt, double c1, double c2, int init, double *frame,
+                      cudaStream_t s)
+{
+    note_launch();
+    k_axi_frame<<<1, 32, 0, s>>>(mk.X, mk.Y, mk.drop_start, dt, c1, c2, init, frame);
 }
 
 void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,

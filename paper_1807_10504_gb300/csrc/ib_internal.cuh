@@ -65,11 +65,16 @@ void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       double *vs, double *au, double *av, cudaStream_t s);
 
 // ------------------------------------------------------------ axisymmetric
+// Record of the non-inertial frame (device doubles): reference, previous and
+// current centre of mass of drop 0, the next step's acceleration S, the frame
+// velocity Vf and the boundary velocity wb = -Vf.
+enum FrameSlot { kFrCom0 = 0, kFrComPrev = 1, kFrCom = 2, kFrS = 3, kFrVf = 4, kFrWb = 5, kFrSlots = 8 };
 void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                           const double *mu, const double *u, const double *v,
                           const double *au_prev, const double *av_prev, int have_prev,
-                          double gx, double gy, double *us, double *vs, double *au, double *av,
-                          cudaStream_t s);
+                          double gx, double gy, const double *frame, double *us, double *vs,
+                          double *au, double *av, cudaStream_t s);
+void launch_axi_zbc(int nx, int ny, const double *frame, double *v, cudaStream_t s);
 void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,
                     const double *Fx, const double *Fy, const double *bx, const double *by,
                     double *b, cudaStream_t s);
@@ -242,6 +247,8 @@ void launch_relocate(Markers &mk, cudaStream_t s);
 void launch_axi_curvature(Markers &mk, double sigma, cudaStream_t s);
 void launch_axi_ring(const Markers &mk, const double *fmag, double *fr, cudaStream_t s);
 void launch_axi_symmetrise(Markers &mk, cudaStream_t s);
+void launch_axi_frame(const Markers &mk, double dt, double c1, double c2, int init, double *frame,
+                      cudaStream_t s);
 
 // ---------------------------------------------------------------- CNN
 struct Cnn;

@@ -109,6 +109,13 @@ def test_predictor_rhs_weights_match_oracle(T, ib, O):
                             (0.0, -9.81))
         for g, r in zip((us, vs, au, av), o):
             assert np.abs(g.cpu().numpy() - r).max() <= 1e-12 * max(np.abs(r).max(), 1.0)
+    # with a frame record: extra axial acceleration S, moving boundaries wb
+    us, vs, au, av = ib.ib_op_predictor_axi(d(rho), d(mu), d(u), d(v), h, dt, d(aup), d(avp),
+                                            gy=-9.81, S=0.37, wb=0.21)
+    o = O.predictor_axi(rho, mu, u, v, h, dt, aup, avp, (0.0, -9.81 + 0.37), 0.21)
+    for g, r in zip((us, vs, au, av), o):
+        assert np.abs(g.cpu().numpy() - r).max() <= 1e-12 * max(np.abs(r).max(), 1.0)
+    assert np.all(vs.cpu().numpy()[[0, -1]] == 0.21)
     us, vs = W.random_faces(nx, ny, 45)
     us[:, 0] = 0.0
     b = ib.ib_op_rhs_axi(d(us), d(vs), d(Fx), d(Fy), d(bx), d(by), h, dt).cpu().numpy()
@@ -177,3 +184,33 @@ def test_rejects_curves_that_are_not_meridians(T, ib):
     with pytest.raises(ib.IBError):  # the axis must be at x0 = 0
         ib.Context(ib.Config(nx=32, ny=64, h=1 / 32, axisym=1, x0=0.1), mk.X, mk.Y,
                    mk.drop_start)
+
+
+def test_free_fall_frame_matches_oracle(T, ib, O):
+    # Gravity and the non-inertial frame (Section 2.4): 40 steps of a dense
+    # sphere released from rest; the frame record, the fields and the markers
+    # follow the oracle's.  The frame's acceleration divides centre-of-mass
+    # differences by dt^2 (~6e-7 here), which lifts rounding differences of
+    # the positions (~1e-16) to ~1e-10 in S, so the fields compare at 1e-8.
+    nx, ny, h, R = 32, 96, 1 / 32, 0.25
+    mk = W.axi_sphere(1.0, R, 96)
+    kw = dict(axisym=1, frame=1, gy=-1.0, relocate_every=10, spread=1, tol=1e-11)
+    ctx = ib.Context(ib.Config(nx=nx, ny=ny, h=h, **kw), mk.X, mk.Y, mk.drop_start)
+    ocfg = O.Config(nx=nx, ny=ny, h=h, **kw)
+    st = O.init_state(ocfg, mk.X, mk.Y, mk.drop_start)
+    dt = W.capillary_dt(h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    for _ in range(40):
+        ctx.ns_step(dt, 1, 1)
+        O.ns_step(ocfg, st, dt)
+    com, S, vf, wb = ctx.frame_state()
+    f = st.frame
+    assert abs(vf - f["Vf"]) <= 1e-7 * abs(f["Vf"]) and abs(wb + vf) == 0.0
+    assert abs(com - f["com_prev"]) <= 1e-12
+    assert abs(S - f["S"]) <= 1e-6 * max(abs(f["S"]), 1.0)
+    for name, ref in (("p", st.p), ("u", st.u), ("v", st.v)):
+        assert rel(ctx.get(name).cpu().numpy(), ref) <= 1e-8, name
+    X, Y = (a.cpu().numpy() for a in ctx.markers())
+    assert np.abs(X - st.X).max() <= 1e-12 and np.abs(Y - st.Y).max() <= 1e-12
+    with pytest.raises(ib.IBError):  # the frame needs the axisymmetric form
+        ib.Context(ib.Config(nx=32, ny=32, h=1 / 32, frame=1), *W.circle(0.5, 0.5, 0.2, 32),
+                   np.array([0, 32], np.int32))
