@@ -77,6 +77,13 @@ typedef struct ib_config {
                                  -Vf (a laboratory at rest seen from the frame).
                                  0: fixed walls */
     double c1, c2;            /* the constants of Eq. (fictitious) (the paper: 0.1, 0.1) */
+    int32_t mass_every;       /* Sec. 2.5: every mass_every steps (after the first), each
+                                 drop whose enclosed area (planar) or volume of revolution
+                                 (axisymmetric) differs from its value at ib_init by more
+                                 than mass_tol (relative) is offset along its inward
+                                 normals by the bisection root that restores it (the
+                                 paper: every 20 steps, 1e-6).  0: never */
+    double mass_tol;
 } ib_config;
 
 typedef struct ib_ctx ib_ctx;
@@ -88,7 +95,11 @@ typedef struct ib_ctx ib_ctx;
  * ndrops+1 entries, copied in.  Fields start at zero.
  * Errors: IB_EINVAL (sizes, grid that cannot coarsen to <= 1024 coarsest
  * cells, more than 2^20 markers), IB_EMARKER, IB_ENOMEM, IB_ECUDA; on error
- * *out is NULL and nothing stays allocated.                                */
+ * *out is NULL and nothing stays allocated.  Levels halve while both sides
+ * are even and >= 8; the coarsest level's dense inverse is rebuilt with the
+ * coefficients (every time step) at O(n^3) in one CTA, so grid sides with a
+ * large odd factor (200 = 8 x 25 ends at 25 x 25: ~60 ms a step) are slow;
+ * sides of the form 2^k times a small odd number coarsen to tens of cells. */
 ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X,
                   const double *Y, const int32_t *drop_start, int32_t ndrops,
                   void *stream);
@@ -188,6 +199,11 @@ ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
  * frame), out[3] the boundary velocity -Vf; host array, synchronises.
  * IB_EINVAL without a frame.                                               */
 ib_status ib_frame_state(ib_ctx *ctx, double *out);
+/* Section 2.5 measure correction of the current markers against the drops'
+ * measures at ib_init (tolerance cfg.mass_tol, or 1e-6 if it is 0); eps
+ * (host, ndrops, may be NULL) receives each drop's normal offset (0 where
+ * none was needed).  Synchronises.                                          */
+ib_status ib_mass_correct(ib_ctx *ctx, double *eps);
 ib_status ib_last_solve(const ib_ctx *ctx, int *cycles, double *relres);
 
 /* ---------------------------------------------------------------------- */

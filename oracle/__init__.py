@@ -94,6 +94,8 @@ def lib():
                                           _D]),
             "or_interp_axi": (None, [_i, _i, _i, _d, _D, _D, _i, _D, _D, _D, _D]),
             "or_drop_com_axi": (None, [_i, _D, _D, _I32, _i, C.POINTER(_d), C.POINTER(_d)]),
+            "or_drop_measure": (_d, [_i, _D, _D, _i]),
+            "or_mass_correct": (_i, [_i, _D, _D, _i, _I32, _D, _i, _d, _d, _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -395,6 +397,28 @@ def drop_com_axi(X, Y, drop_start, d=0):
     return vol.value, zc.value
 
 
+def drop_measures(X, Y, drop_start, axisym=0):
+    """Section 2.5: enclosed area (planar) or volume of revolution of each drop."""
+    ds_ = _ds(drop_start)
+    X, Y = _f64(X), _f64(Y)
+    return np.array([lib().or_drop_measure(int(ds_[d + 1] - ds_[d]),
+                                           np.ascontiguousarray(X[ds_[d]:ds_[d + 1]]),
+                                           np.ascontiguousarray(Y[ds_[d]:ds_[d + 1]]), int(axisym))
+                     for d in range(len(ds_) - 1)])
+
+
+def mass_correct(X, Y, drop_start, A0, h, axisym=0, tol=1e-6):
+    """Section 2.5: bisection offset along the inward normals restoring each
+    drop's initial measure A0 where it drifted by more than tol.  Returns
+    (X, Y, eps per drop)."""
+    M = len(X)
+    Xo, Yo = np.empty(M), np.empty(M)
+    eps = np.empty(len(drop_start) - 1)
+    lib().or_mass_correct(M, _f64(X), _f64(Y), len(drop_start) - 1, _ds(drop_start), _f64(A0),
+                          int(axisym), float(tol), float(h), Xo, Yo, eps)
+    return Xo, Yo, eps
+
+
 def symmetrise(X, Y, drop_start):
     """Mirror symmetry of each drop's closed meridian curve about r = 0:
     marker k of a drop of n (n even) pairs with marker (n - k) mod n; each
@@ -442,6 +466,8 @@ class Config:
     nu2: int = 2
     relocate_every: int = 10  # 0 = never
     axisym: int = 0           # 1: (r, z) with x = r from the axis (x0 = 0)
+    mass_every: int = 0       # Section 2.5 measure check period in steps, 0 = never
+    mass_tol: float = 1e-6
     frame: int = 0            # 1: non-inertial frame following drop 0 (axisym only)
     c1: float = 0.1           # Section 2.4 Eq. (fictitious) constants
     c2: float = 0.1
@@ -458,6 +484,7 @@ class State:
     au: np.ndarray | None = None
     av: np.ndarray | None = None
     frame: dict | None = None  # non-inertial frame: com0, com_prev, S, Vf
+    A0: np.ndarray | None = None  # initial drop measures (Section 2.5)
     step: int = 0
     last: dict = field(default_factory=dict)
 
@@ -465,15 +492,30 @@ class State:
 def init_state(cfg: Config, X, Y, drop_start) -> State:
     return State(u=np.zeros((cfg.ny, cfg.nx + 1)), v=np.zeros((cfg.ny + 1, cfg.nx)),
                  p=np.zeros((cfg.ny, cfg.nx)), X=_f64(X).copy(), Y=_f64(Y).copy(),
-                 drop_start=_ds(drop_start).copy())
+                 drop_start=_ds(drop_start).copy(),
+                 A0=drop_measures(X, Y, drop_start, cfg.axisym))
+
+
+def _markers_update(cfg: Config, st: State):
+    """Marker upkeep at the start of a step: B-spline relocation (every
+    relocate_every steps), then the Section 2.5 measure correction (every
+    mass_every steps after the first); axisymmetric curves re-symmetrised."""
+    if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
+        st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, cfg.h)
+        if cfg.axisym:
+            st.X, st.Y = symmetrise(st.X, st.Y, st.drop_start)
+    if cfg.mass_every > 0 and st.step > 0 and st.step % cfg.mass_every == 0:
+        st.X, st.Y, _ = mass_correct(st.X, st.Y, st.drop_start, st.A0, cfg.h, cfg.axisym,
+                                     cfg.mass_tol)
+        if cfg.axisym:
+            st.X, st.Y = symmetrise(st.X, st.Y, st.drop_start)
 
 
 def ns_step(cfg: Config, st: State, dt: float) -> State:
     if cfg.axisym:
         return _ns_step_axi(cfg, st, dt)
     h = cfg.h
-    if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
-        st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
+    _markers_update(cfg, st)
     kap, nxm, nym, ds = curvature(st.X, st.Y, st.drop_start)
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, cfg.x0, cfg.y0)
@@ -511,9 +553,7 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
         st.frame = dict(com0=c0, com_prev=c0, S=0.0, Vf=0.0)
     S = st.frame["S"] if cfg.frame else 0.0
     wb = -st.frame["Vf"] if cfg.frame else 0.0
-    if cfg.relocate_every > 0 and st.step % cfg.relocate_every == 0:
-        st.X, st.Y = bspline_relocate(st.X, st.Y, st.drop_start, h)
-        st.X, st.Y = symmetrise(st.X, st.Y, st.drop_start)
+    _markers_update(cfg, st)
     kap, nxm, nym, ds = curvature_axi(st.X, st.Y, st.drop_start)
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, 0.0, cfg.y0)

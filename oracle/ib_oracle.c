@@ -1178,3 +1178,70 @@ int or_bspline_relocate(int M, const double *X, const double *Y, int ndrops,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Section 2.5 (conservation of mass): the area a drop's markers enclose
+ * (planar: the shoelace sum in marker order; axisymmetric: the volume of
+ * revolution 2 pi sum (z2 - z1)(r1^2 + r1 r2 + r2^2) / 6 over the right
+ * half of the meridian, markers 0 .. n/2, the axis edge adding nothing).   */
+double or_drop_measure(int n, const double *X, const double *Y, int axisym)
+{
+    double a = 0.0;
+    if (!axisym) {
+        for (int k = 0; k < n; k++) {
+            int q = (k + 1 == n) ? 0 : k + 1;
+            a += X[k] * Y[q] - X[q] * Y[k];
+        }
+        return 0.5 * a;
+    }
+    for (int k = 0; k < n / 2; k++) {
+        double r1 = X[k], z1 = Y[k], r2 = X[k + 1], z2 = Y[k + 1];
+        a += (z2 - z1) * (r1 * r1 + r1 * r2 + r2 * r2) / 6.0;
+    }
+    return 2.0 * 3.14159265358979323846 * a;
+}
+
+/* Section 2.5: where |A_n - A_o| > tol A_o, every marker of the drop moves
+ * by one offset eps along its inward unit normal (the normals of the
+ * uncorrected markers, as in or_curvature), eps found by bisection on
+ * [-h, h] (moving inward shrinks the drop) until the bracket is below
+ * 1e-13 h or 80 halvings: eps = the bracket's midpoint.  A0 per drop;
+ * eps_out (per drop, may be NULL) gets 0 where no correction was needed.
+ * Returns the number of drops corrected.                                  */
+int or_mass_correct(int M, const double *X, const double *Y, int ndrops,
+                    const int32_t *drop_start, const double *A0, int axisym, double tol,
+                    double h, double *Xo, double *Yo, double *eps_out)
+{
+    double *kap = (double *)malloc((size_t)M * sizeof(double));
+    double *nxm = (double *)malloc((size_t)M * sizeof(double));
+    double *nym = (double *)malloc((size_t)M * sizeof(double));
+    double *dsm = (double *)malloc((size_t)M * sizeof(double));
+    or_curvature(M, X, Y, ndrops, drop_start, kap, nxm, nym, dsm);
+    memcpy(Xo, X, (size_t)M * sizeof(double));
+    memcpy(Yo, Y, (size_t)M * sizeof(double));
+    int corrected = 0;
+    for (int d = 0; d < ndrops; d++) {
+        int s = drop_start[d], n = drop_start[d + 1] - s;
+        double A = or_drop_measure(n, X + s, Y + s, axisym);
+        if (eps_out) eps_out[d] = 0.0;
+        if (!(fabs(A - A0[d]) > tol * A0[d])) continue;
+        double lo = -h, hi = h;
+        for (int it = 0; it < 80 && hi - lo > 1e-13 * h; it++) {
+            double mid = 0.5 * (lo + hi);
+            for (int k = 0; k < n; k++) {
+                Xo[s + k] = X[s + k] + mid * nxm[s + k];
+                Yo[s + k] = Y[s + k] + mid * nym[s + k];
+            }
+            if (or_drop_measure(n, Xo + s, Yo + s, axisym) > A0[d]) lo = mid; else hi = mid;
+        }
+        double eps = 0.5 * (lo + hi);
+        for (int k = 0; k < n; k++) {
+            Xo[s + k] = X[s + k] + eps * nxm[s + k];
+            Yo[s + k] = Y[s + k] + eps * nym[s + k];
+        }
+        if (eps_out) eps_out[d] = eps;
+        corrected++;
+    }
+    free(kap); free(nxm); free(nym); free(dsm);
+    return corrected;
+}

@@ -107,6 +107,13 @@ int or_bspline_relocate(int M, const double *X, const double *Y, int ndrops,
                         const int32_t *drop_start, double h, double *Xo,
                         double *Yo);
 
+/* Section 2.5: enclosed area (planar) or volume of revolution (axisymmetric)
+ * of one drop, and the bisection correction of every drop's measure.      */
+double or_drop_measure(int n, const double *X, const double *Y, int axisym);
+int or_mass_correct(int M, const double *X, const double *Y, int ndrops,
+                    const int32_t *drop_start, const double *A0, int axisym, double tol,
+                    double h, double *Xo, double *Yo, double *eps_out);
+
 /* ---- axisymmetric (r, z) form, ib_oracle_axi.c (x = r from the axis) ---- */
 void or_apply_A_axi(int nx, int ny, double h, const double *bx, const double *by,
                     const double *p, double *out);

@@ -37,6 +37,7 @@ EXPORTS = [
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
+    "ib_mass_correct",
 ]
 
 
@@ -54,7 +55,8 @@ class ib_config(C.Structure):
                 ("spread", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_cycles", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("relocate_every", C.c_int32), ("axisym", C.c_int32), ("frame", C.c_int32),
-                ("c1", C.c_double), ("c2", C.c_double)]
+                ("c1", C.c_double), ("c2", C.c_double), ("mass_every", C.c_int32),
+                ("mass_tol", C.c_double)]
 
 
 _lib = None
@@ -108,7 +110,7 @@ def lib():
                                 _P, _P, _P, _P],
             "ib_op_predictor_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _P,
                                     _P, _P, _P, _P, _P],
-            "ib_frame_state": [_P, _P],
+            "ib_frame_state": [_P, _P], "ib_mass_correct": [_P, _P],
             "ib_op_rhs_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P],
             "ib_op_axi_weights": [_i32, _i32, _d, _P, _P, _P, _P, _P],
         }
@@ -193,6 +195,8 @@ class Config:
     frame: int = 0
     c1: float = 0.1
     c2: float = 0.1
+    mass_every: int = 0
+    mass_tol: float = 1e-6
 
     def c(self) -> ib_config:
         return ib_config(**{k: getattr(self, k) for k, _ in ib_config._fields_})
@@ -305,6 +309,13 @@ class Context:
 
     def relocate(self):
         _check(lib().ib_relocate(self._h), self._h)
+
+    def mass_correct(self):
+        """Section 2.5 measure correction of the current markers; returns the
+        normal offset of each drop (0 where none was needed)."""
+        eps = np.zeros(self.ndrops)
+        _check(lib().ib_mass_correct(self._h, eps.ctypes.data), self._h)
+        return eps
 
     def frame_state(self):
         """(centre of mass, next acceleration S, frame velocity Vf, boundary

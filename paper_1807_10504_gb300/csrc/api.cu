@@ -35,6 +35,8 @@ struct ib_ctx {
     double *uw = nullptr, *vw = nullptr, *Hw = nullptr, *Fxw = nullptr, *Fyw = nullptr,
            *bxa = nullptr, *bya = nullptr, *fr = nullptr;
     double *frame = nullptr;   // non-inertial frame record (kFrSlots doubles)
+    double *A0 = nullptr;      // per drop: measure at ib_init (Section 2.5), then eps scratch
+    void *dmem = nullptr;
     void *amem = nullptr;
 };
 
@@ -231,6 +233,16 @@ void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double
     launch_axi_fold(g.nx, g.ny, c->G, g.h, mode == 0, nullptr, c->Fxw, c->Fyw, nullptr, Fx, Fy, c->s);
 }
 
+// Section 2.5 measure correction: normals of the current markers, then the
+// per-drop bisection offset (re-symmetrised in axisymmetric mode).
+void mass_correct(ib_ctx *c, double *eps)
+{
+    const ib_config &g = c->cfg;
+    launch_geometry(c->mk, g.sigma, c->s);
+    launch_mass_correct(c->mk, c->A0, g.axisym, g.mass_tol > 0 ? g.mass_tol : 1e-6, eps, c->s);
+    if (g.axisym) launch_axi_symmetrise(c->mk, c->s);
+}
+
 // Velocity at the markers (and optional advection), continued across the
 // axis in axisymmetric mode; the curve is re-symmetrised after a move.
 void interp_into(ib_ctx *c, const double *u, const double *v, double *U, double *V, double dt_move)
@@ -311,6 +323,7 @@ void ib_destroy(ib_ctx *c)
     markers_free(c->mk);
     if (c->fmem) cudaFree(c->fmem);
     if (c->amem) cudaFree(c->amem);
+    if (c->dmem) cudaFree(c->dmem);
     if (c->flags_host) cudaFreeHost(c->flags_host);
     delete c;
 }
@@ -326,7 +339,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
         g.nu2 < 0 || g.max_cycles < 0 || !(g.tol >= 0) || g.kernel < 0 || g.kernel > 1 ||
         g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2 || g.axisym < 0 ||
         g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)) || g.frame < 0 || g.frame > 1 ||
-        (g.frame && (!g.axisym || !(g.c1 >= 0) || !(g.c2 >= 0))))
+        (g.frame && (!g.axisym || !(g.c1 >= 0) || !(g.c2 >= 0))) || g.mass_every < 0 ||
+        !(g.mass_tol >= 0))
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -388,6 +402,14 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess && g.frame) {
         launch_axi_frame(c->mk, 1.0, g.c1, g.c2, 1, c->frame, c->s);
         e = cudaStreamSynchronize(c->s);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
+    if (e == cudaSuccess) {
+        c->A0 = (double *)c->dmem;
+        launch_drop_measure(c->mk, g.axisym, c->A0, c->s);
+        e = cudaStreamSynchronize(c->s);
+    } else {
+        c->dmem = nullptr;
     }
     if (e != cudaSuccess) {
         ib_status r = (e == cudaErrorMemoryAllocation) ? IB_ENOMEM : IB_ECUDA;
@@ -569,6 +591,7 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
             launch_relocate(mk, c->s);
             if (g.axisym) launch_axi_symmetrise(mk, c->s);
         }
+        if (g.mass_every > 0 && c->step > 0 && c->step % g.mass_every == 0) mass_correct(c, nullptr);
         geometry(c);
         launch_sort(mk, c->s);
         heaviside_into(c, c->H);
@@ -673,6 +696,18 @@ ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_
     *us_per_launch = 1e3 * ms / reps;
     if (units) *units = u;
     return IB_OK;
+}
+
+ib_status ib_mass_correct(ib_ctx *c, double *eps)
+{
+    if (!c) return IB_EINVAL;
+    mass_correct(c, eps ? c->A0 + al((size_t)c->mk.ndrops * 8) / 8 : nullptr);
+    ib_status st = launch_check(c, "mass correction");
+    if (st != IB_OK || !eps) return st;
+    cudaError_t e = cudaMemcpyAsync(eps, c->A0 + al((size_t)c->mk.ndrops * 8) / 8,
+                                    (size_t)c->mk.ndrops * 8, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    return cuda_check(c, e, "mass correction");
 }
 
 ib_status ib_frame_state(ib_ctx *c, double *out)

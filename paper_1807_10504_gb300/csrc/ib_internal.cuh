@@ -244,6 +244,9 @@ void launch_band_area(const Markers &mk, cudaStream_t s);
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
                          double *Fx, double *Fy, cudaStream_t s);
 void launch_relocate(Markers &mk, cudaStream_t s);
+void launch_drop_measure(const Markers &mk, int axisym, double *A, cudaStream_t s);
+void launch_mass_correct(Markers &mk, const double *A0, int axisym, double tol, double *eps,
+                         cudaStream_t s);
 void launch_axi_curvature(Markers &mk, double sigma, cudaStream_t s);
 void launch_axi_ring(const Markers &mk, const double *fmag, double *fr, cudaStream_t s);
 void launch_axi_symmetrise(Markers &mk, cudaStream_t s);

@@ -1493,6 +1493,91 @@ size_t relocate_smem(int maxn)
            (size_t)2 * maxn * 8 + (size_t)4 * maxn * 8 + (size_t)6 * maxn * 8 + (size_t)(maxn + 1) * 8 + 64;
 }
 
+// ------------------------------------------------------------ measure correction
+// Section 2.5 (conservation of mass).  The measure of drop markers shifted by
+// e along the normals: planar, the enclosed area by the shoelace sum in
+// marker order; axisymmetric, the volume of revolution 2 pi sum (z2 - z1)
+// (r1^2 + r1 r2 + r2^2) / 6 over the right half of the meridian (markers
+// 0 .. n/2).  Serial in marker order (one thread per drop), so that the
+// bisection below takes each decision on the same sum as a serial program.
+// nx == NULL: the markers as they are.
+__device__ double drop_measure(int n, const double *X, const double *Y, const double *nx,
+                               const double *ny, double e, int axisym)
+{
+    auto px = [&](int k) { return nx ? X[k] + e * nx[k] : X[k]; };
+    auto py = [&](int k) { return nx ? Y[k] + e * ny[k] : Y[k]; };
+    double a = 0.0;
+    if (!axisym) {
+        for (int k = 0; k < n; k++) {
+            const int q = (k + 1 == n) ? 0 : k + 1;
+            a += px(k) * py(q) - px(q) * py(k);
+        }
+        return 0.5 * a;
+    }
+    for (int k = 0; k < n / 2; k++) {
+        const double r1 = px(k), z1 = py(k), r2 = px(k + 1), z2 = py(k + 1);
+        a += (z2 - z1) * (r1 * r1 + r1 * r2 + r2 * r2) / 6.0;
+    }
+    return 2.0 * 3.14159265358979323846 * a;
+}
+
+// Initial measure of every drop (one thread per drop).
+__global__ void k_drop_measure(int ndrops, const int32_t *__restrict__ drop_start,
+                               const double *__restrict__ X, const double *__restrict__ Y,
+                               int axisym, double *__restrict__ A)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndrops) return;
+    const int s = drop_start[d], n = drop_start[d + 1] - s;
+    A[d] = drop_measure(n, X + s, Y + s, nullptr, nullptr, 0.0, axisym);
+}
+
+// Where |A - A0| > tol A0, one offset eps along the inward unit normals (of
+// the uncorrected markers) restores the measure: bisection on [-h, h] until
+// the bracket is below 1e-13 h or 80 halvings, eps its midpoint.  One thread
+// per drop; eps (may be NULL) gets 0 where nothing moved.
+__global__ void k_mass_correct(int ndrops, const int32_t *__restrict__ drop_start,
+                               const double *__restrict__ A0, int axisym, double tol, double h,
+                               const double *__restrict__ nxm, const double *__restrict__ nym,
+                               double *__restrict__ X, double *__restrict__ Y,
+                               double *__restrict__ eps_out)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndrops) return;
+    const int s = drop_start[d], n = drop_start[d + 1] - s;
+    const double a0 = A0[d];
+    const double A = drop_measure(n, X + s, Y + s, nullptr, nullptr, 0.0, axisym);
+    if (eps_out) eps_out[d] = 0.0;
+    if (!(fabs(A - a0) > tol * a0)) return;
+    double lo = -h, hi = h;
+    for (int it = 0; it < 80 && hi - lo > 1e-13 * h; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (drop_measure(n, X + s, Y + s, nxm + s, nym + s, mid, axisym) > a0) lo = mid;
+        else hi = mid;
+    }
+    const double eps = 0.5 * (lo + hi);
+    for (int k = 0; k < n; k++) {
+        X[s + k] = X[s + k] + eps * nxm[s + k];
+        Y[s + k] = Y[s + k] + eps * nym[s + k];
+    }
+    if (eps_out) eps_out[d] = eps;
+}
+
+void launch_drop_measure(const Markers &mk, int axisym, double *A, cudaStream_t s)
+{
+    note_launch();
+    k_drop_measure<<<cdiv(mk.ndrops, 128), 128, 0, s>>>(mk.ndrops, mk.drop_start, mk.X, mk.Y,
+                                                        axisym, A);
+}
+
+void launch_mass_correct(Markers &mk, const double *A0, int axisym, double tol, double *eps,
+                         cudaStream_t s)
+{
+    note_launch();
+    k_mass_correct<<<cdiv(mk.ndrops, 128), 128, 0, s>>>(mk.ndrops, mk.drop_start, A0, axisym, tol,
+                                                        mk.h, mk.nxm, mk.nym, mk.X, mk.Y, eps);
+}
+
 void launch_relocate(Markers &mk, cudaStream_t s)
 {
     size_t sm = relocate_smem(mk.max_drop);

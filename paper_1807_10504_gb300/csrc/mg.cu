@@ -1572,8 +1572,8 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     const size_t cbytes = 2 * nc2 * sizeof(double);
     const int in_smem = cbytes <= 96 * 1024;
     if (in_smem) cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
-    k_coarse_inv<<<1, 256, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
-                                                      mg.lu + nc2, in_smem);
+    k_coarse_inv<<<1, 1024, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
+                                                       mg.lu + nc2, in_smem);
 }
 
 // Host-driven solve: one launch per kernel and a host read of the residual

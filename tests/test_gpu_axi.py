@@ -214,3 +214,37 @@ def test_free_fall_frame_matches_oracle(T, ib, O):
     with pytest.raises(ib.IBError):  # the frame needs the axisymmetric form
         ib.Context(ib.Config(nx=32, ny=32, h=1 / 32, frame=1), *W.circle(0.5, 0.5, 0.2, 32),
                    np.array([0, 32], np.int32))
+
+
+def test_axisymmetric_oscillation_period(T, ib):
+    # Section 5.2's axisymmetric oscillating drop at the paper's grid 0.01 (the
+    # domain 1.28 x 2.56 instead of 2 x 2, so that the multigrid coarsens to
+    # 4 x 8 cells; the walls stay 5 radii away), R = 0.2 about the axis
+    # deformed by Eq. (osc) with beta = 1.03, drop
+    # density 1 and ambient 0.01 (the densities that reproduce the printed
+    # periods), viscosities 0.01 / 1e-5, sigma 1, irrotational spreading with
+    # B-spline relocation.  The first extremum of the r-extent minus the
+    # z-extent falls at half the closed-form n = 2 period of Eq. (aosc_p),
+    # 2 pi sqrt(((n+1) rho_d + n rho_a) r^3 / (n (n-1)(n+1)(n+2) sigma)) =
+    # 0.19935, within 5 % (the paper's own discrepancy at this grid: 1.53 %).
+    h = 0.01
+    mk = W.axi_elliptic_drop(1.28, 0.2, 1.03, 256)
+    cfg = ib.Config(nx=128, ny=256, h=h, axisym=1, rho_l=1.0, rho_g=0.01, mu_l=0.01, mu_g=1e-5,
+                    sigma=1.0, spread=1, relocate_every=10, precision=2, tol=1e-10,
+                    max_cycles=200)
+    ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+    dt = W.capillary_dt(h, 1.0, 0.01, 1.0, 0.01, 1e-5)
+    ext, ts = [], []
+    for k in range(110):
+        ctx.ns_step(dt, 10, 1)
+        X, Y = ctx.markers()
+        ext.append(float(X.max() - X.min()) - float(Y.max() - Y.min()))
+        ts.append(10 * (k + 1) * dt)
+    ext = np.array(ext)
+    i = int(np.argmin(ext))  # starts wider in r than tall in z: first minimum at T/2
+    assert 0 < i < len(ext) - 1
+    a, b, c = np.polyfit(np.array(ts[i - 1:i + 2]), ext[i - 1:i + 2], 2)
+    t_half = -b / (2 * a)
+    Ta = 2 * np.pi * np.sqrt((3 * 1.0 + 2 * 0.01) * 0.2 ** 3 / (2 * 1 * 3 * 4 * 1.0))
+    assert abs(Ta - 0.19935) < 1e-5
+    assert abs(2 * t_half - Ta) <= 0.05 * Ta, (2 * t_half, Ta)

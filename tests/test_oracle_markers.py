@@ -286,3 +286,29 @@ def test_row_inside_equals_pointwise_crossing_number(O):
     for j in range(0, n, 3):
         for i in range(n):
             assert chi[j, i] == O.inside_cell(i, j, mk.X, mk.Y, mk.drop_start, h)
+
+
+def test_mass_correction_restores_the_measure(O):
+    # Section 2.5: a regular polygon offset inward along its normals by 0.3 h
+    # stays regular with the same normals; the bisection correction towards
+    # the original area (planar) or volume of revolution (axisymmetric)
+    # recovers the original markers and measure.
+    h = 1 / 64
+    for axisym in (0, 1):
+        mk = W.axi_sphere(0.5, 0.25, 128) if axisym else W.static_drop(64, 0.25, 128)
+        A0 = O.drop_measures(mk.X, mk.Y, mk.drop_start, axisym)
+        if axisym:
+            assert abs(A0[0] - 4 / 3 * np.pi * 0.25**3) < 2e-3 * A0[0]
+        else:
+            assert abs(A0[0] - np.pi * 0.25**2) < 1e-3 * A0[0]
+        k, nxm, nym, ds = O.curvature(mk.X, mk.Y, mk.drop_start)
+        Xs, Ys = mk.X + 0.3 * h * nxm, mk.Y + 0.3 * h * nym
+        assert O.drop_measures(Xs, Ys, mk.drop_start, axisym)[0] < A0[0]
+        Xc, Yc, eps = O.mass_correct(Xs, Ys, mk.drop_start, A0, h, axisym)
+        assert abs(eps[0] + 0.3 * h) < 1e-12 * h
+        assert np.abs(Xc - mk.X).max() < 1e-13 and np.abs(Yc - mk.Y).max() < 1e-13
+        A = O.drop_measures(Xc, Yc, mk.drop_start, axisym)[0]
+        assert abs(A - A0[0]) < 1e-12 * A0[0]
+        # within the tolerance nothing moves
+        Xn, Yn, e0 = O.mass_correct(mk.X, mk.Y, mk.drop_start, A0 * (1 + 5e-7), h, axisym)
+        assert e0[0] == 0.0 and np.array_equal(Xn, mk.X)
