@@ -84,6 +84,15 @@ typedef struct ib_config {
                                  normals by the bisection root that restores it (the
                                  paper: every 20 steps, 1e-6).  0: never */
     double mass_tol;
+    int32_t viscous;          /* 0: explicit viscous term; 1: Crank-Nicolson (Sec. 2.1):
+                                 the explicit predictor with half the viscosity, then
+                                 u* - dt / (2 rho_f) D(u*) = that, per component, by
+                                 cn_sweeps red-black Gauss-Seidel sweeps (the system's
+                                 off-diagonal / diagonal ratio is at most 2s / (1 + 2s),
+                                 s = nu dt / h^2, and a sweep contracts the error by
+                                 about its square: 20 sweeps reach ~1e-12 for s <= 0.5;
+                                 larger steps need more) */
+    int32_t cn_sweeps;
 } ib_config;
 
 typedef struct ib_ctx ib_ctx;
@@ -394,6 +403,14 @@ ib_status ib_op_rhs_axi(int32_t nx, int32_t ny, double h, double dt,
                         const double *us, const double *vs, const double *Fx,
                         const double *Fy, const double *bx, const double *by,
                         double *b, void *stream);
+/* Crank-Nicolson viscous solve (Section 2.1): nsweeps red-black sweeps on
+ * u* - dt / (2 rho_f) D(u*) = u_e for both components (planar, or
+ * axisymmetric with fixed outer wall), starting from u_e; boundary faces keep
+ * u_e's values.  ue, ve: inputs; us, vs: outputs (device face arrays).     */
+ib_status ib_op_cn_solve(int32_t nx, int32_t ny, double h, double dt,
+                         const double *rho, const double *mu, int32_t axisym,
+                         int32_t nsweeps, const double *ue, const double *ve,
+                         double *us, double *vs, void *stream);
 ib_status ib_op_axi_weights(int32_t nx, int32_t ny, double h, const double *bx,
                             const double *by, double *bxa, double *bya,
                             void *stream);

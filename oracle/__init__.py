@@ -95,6 +95,7 @@ def lib():
             "or_interp_axi": (None, [_i, _i, _i, _d, _D, _D, _i, _D, _D, _D, _D]),
             "or_drop_com_axi": (None, [_i, _D, _D, _I32, _i, C.POINTER(_d), C.POINTER(_d)]),
             "or_drop_measure": (_d, [_i, _D, _D, _i]),
+            "or_cn_solve": (None, [_i, _i, _d, _d, _D, _D, _i, _d, _i, _D, _D]),
             "or_mass_correct": (_i, [_i, _D, _D, _i, _I32, _D, _i, _d, _d, _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
@@ -397,6 +398,16 @@ def drop_com_axi(X, Y, drop_start, d=0):
     return vol.value, zc.value
 
 
+def cn_solve(rho, mu, ue, ve, h, dt, nsweeps, axisym=0, wb=0.0):
+    """Section 2.1 Crank-Nicolson: nsweeps red-black sweeps on
+    u* - dt / (2 rho_f) D(u*) = u_e per component."""
+    ny, nx = rho.shape
+    us, vs = _f64(ue).copy(), _f64(ve).copy()
+    lib().or_cn_solve(nx, ny, h, dt, _f64(rho), _f64(mu), int(axisym), float(wb), int(nsweeps),
+                      us, vs)
+    return us, vs
+
+
 def drop_measures(X, Y, drop_start, axisym=0):
     """Section 2.5: enclosed area (planar) or volume of revolution of each drop."""
     ds_ = _ds(drop_start)
@@ -468,6 +479,8 @@ class Config:
     axisym: int = 0           # 1: (r, z) with x = r from the axis (x0 = 0)
     mass_every: int = 0       # Section 2.5 measure check period in steps, 0 = never
     mass_tol: float = 1e-6
+    viscous: int = 0          # 0 explicit, 1 Crank-Nicolson (Section 2.1)
+    cn_sweeps: int = 20       # red-black sweeps of the Crank-Nicolson solve
     frame: int = 0            # 1: non-inertial frame following drop 0 (axisym only)
     c1: float = 0.1           # Section 2.4 Eq. (fictitious) constants
     c2: float = 0.1
@@ -520,7 +533,12 @@ def ns_step(cfg: Config, st: State, dt: float) -> State:
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, cfg.x0, cfg.y0)
     rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
-    us, vs, au, av = predictor(rho, mu, st.u, st.v, h, dt, st.au, st.av, (cfg.gx, cfg.gy))
+    if cfg.viscous:
+        us, vs, au, av = predictor(rho, 0.5 * mu, st.u, st.v, h, dt, st.au, st.av,
+                                   (cfg.gx, cfg.gy))
+        us, vs = cn_solve(rho, mu, us, vs, h, dt, cfg.cn_sweeps)
+    else:
+        us, vs, au, av = predictor(rho, mu, st.u, st.v, h, dt, st.au, st.av, (cfg.gx, cfg.gy))
     if cfg.spread == 0:
         Fx, Fy = spread_conv(st.X, st.Y, fmag, nxm, nym, ds, cfg.nx, cfg.ny, h, cfg.x0,
                              cfg.y0, cfg.kernel)
@@ -558,8 +576,13 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, 0.0, cfg.y0)
     rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
-    us, vs, au, av = predictor_axi(rho, mu, st.u, st.v, h, dt, st.au, st.av, (0.0, cfg.gy + S),
-                                   wb)
+    if cfg.viscous:
+        us, vs, au, av = predictor_axi(rho, 0.5 * mu, st.u, st.v, h, dt, st.au, st.av,
+                                       (0.0, cfg.gy + S), wb)
+        us, vs = cn_solve(rho, mu, us, vs, h, dt, cfg.cn_sweeps, 1, wb)
+    else:
+        us, vs, au, av = predictor_axi(rho, mu, st.u, st.v, h, dt, st.au, st.av,
+                                       (0.0, cfg.gy + S), wb)
     if cfg.spread == 0:
         Fx, Fy = spread_conv_axi(st.X, st.Y - cfg.y0, fmag, nxm, nym, ds, cfg.nx, cfg.ny, h,
                                  cfg.kernel)

@@ -1245,3 +1245,99 @@ int or_mass_correct(int M, const double *X, const double *Y, int ndrops,
     free(kap); free(nxm); free(nym); free(dsm);
     return corrected;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Crank-Nicolson viscous step (Section 2.1: Crank-Nicolson for the viscous
+ * term).  With u_e the explicit predictor of this step computed with half
+ * the viscosity (AB2 advection, half of D(u^n), body force), the
+ * intermediate velocity solves
+ *     u* - (dt / (2 rho_f)) D(u*) = u_e
+ * per component, D the discrete div(mu grad) of or_predictor (cell mu on the
+ * normal faces, node averages on the tangential ones, the reflected ghost of
+ * a no-slip wall moving with axial velocity wb; axisymmetric: fluxes times
+ * their face radius over the volume radius and -mu_f u / r^2 on the radial
+ * component).  Solved by nsweeps red-black Gauss-Seidel sweeps in place on
+ * each component's interior faces, red = (i + j) even first, u then v;
+ * boundary faces keep their values.                                        */
+static void cn_coeffs_u(int nx, int ny, double h, const double *mu, int axisym, int i, int j,
+                        double c[4], double *extra)
+{
+    /* c = {E, W, N, S} with D(u) = sum c_k (u_k - u) - extra u; a wall
+     * neighbour (ghost -u) gives c_k = 0 and extra += 2 c */
+    double r0 = axisym ? i * h : 1.0, rE = axisym ? (i + 0.5) * h : 1.0,
+           rW = axisym ? (i - 0.5) * h : 1.0;
+    double s = 1.0 / (r0 * h * h);
+    double muN = (j + 1 < ny) ? 0.25 * (mu[CC(i - 1, j)] + mu[CC(i, j)] + mu[CC(i - 1, j + 1)] + mu[CC(i, j + 1)])
+                              : 0.5 * (mu[CC(i - 1, j)] + mu[CC(i, j)]);
+    double muS = (j > 0) ? 0.25 * (mu[CC(i - 1, j - 1)] + mu[CC(i, j - 1)] + mu[CC(i - 1, j)] + mu[CC(i, j)])
+                         : 0.5 * (mu[CC(i - 1, j)] + mu[CC(i, j)]);
+    c[0] = rE * mu[CC(i, j)] * s;
+    c[1] = rW * mu[CC(i - 1, j)] * s;
+    double cN = r0 * muN * s, cS = r0 * muS * s;
+    *extra = 0.0;
+    if (j + 1 < ny) c[2] = cN; else { c[2] = 0.0; *extra += 2.0 * cN; }
+    if (j > 0) c[3] = cS; else { c[3] = 0.0; *extra += 2.0 * cS; }
+    if (axisym) *extra += 0.5 * (mu[CC(i - 1, j)] + mu[CC(i, j)]) / (r0 * r0);
+}
+
+static void cn_coeffs_v(int nx, int ny, double h, const double *mu, int axisym, int i, int j,
+                        double c[4], double *extra, double *wall)
+{
+    /* c = {E, W, N, S}; *wall: the coefficient of the moving-wall ghost
+     * 2 wb - v at the outer wall (E side of the last column): D gets
+     * cE (2 wb - 2 v), i.e. extra += 2 cE and a source 2 cE wb            */
+    double r0 = axisym ? (i + 0.5) * h : 1.0, rE = axisym ? (i + 1) * h : 1.0,
+           rW = axisym ? i * h : 1.0;
+    double s = 1.0 / (r0 * h * h);
+    double muE = (i + 1 < nx) ? 0.25 * (mu[CC(i, j - 1)] + mu[CC(i + 1, j - 1)] + mu[CC(i, j)] + mu[CC(i + 1, j)])
+                              : 0.5 * (mu[CC(i, j - 1)] + mu[CC(i, j)]);
+    double muW = (i > 0) ? 0.25 * (mu[CC(i - 1, j - 1)] + mu[CC(i, j - 1)] + mu[CC(i - 1, j)] + mu[CC(i, j)])
+                         : 0.5 * (mu[CC(i, j - 1)] + mu[CC(i, j)]);
+    c[2] = r0 * mu[CC(i, j)] * s;
+    c[3] = r0 * mu[CC(i, j - 1)] * s;
+    double cE = rE * muE * s, cW = rW * muW * s;
+    *extra = 0.0;
+    *wall = 0.0;
+    if (i + 1 < nx) c[0] = cE; else { c[0] = 0.0; *extra += 2.0 * cE; *wall = 2.0 * cE; }
+    if (i > 0) c[1] = cW;
+    else if (axisym) c[1] = 0.0;            /* the axis: zero area (rW = 0) */
+    else { c[1] = 0.0; *extra += 2.0 * cW; } /* planar left wall */
+}
+
+void or_cn_solve(int nx, int ny, double h, double dt, const double *rho, const double *mu,
+                 int axisym, double wb, int nsweeps, double *us, double *vs)
+{
+    double *ue = (double *)malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *ve = (double *)malloc((size_t)nx * (ny + 1) * sizeof(double));
+    memcpy(ue, us, (size_t)(nx + 1) * ny * sizeof(double));
+    memcpy(ve, vs, (size_t)nx * (ny + 1) * sizeof(double));
+    for (int sw = 0; sw < nsweeps; sw++) {
+        for (int color = 0; color < 2; color++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 1; i < nx; i++) {
+                    if (((i + j) & 1) != color) continue;
+                    double c[4], ex;
+                    cn_coeffs_u(nx, ny, h, mu, axisym, i, j, c, &ex);
+                    double tau = dt / (2.0 * 0.5 * (rho[CC(i - 1, j)] + rho[CC(i, j)]));
+                    double nb = c[0] * us[XF(i + 1, j)] + c[1] * us[XF(i - 1, j)];
+                    if (j + 1 < ny) nb += c[2] * us[XF(i, j + 1)];
+                    if (j > 0) nb += c[3] * us[XF(i, j - 1)];
+                    us[XF(i, j)] = (ue[XF(i, j)] + tau * nb) /
+                                   (1.0 + tau * (c[0] + c[1] + c[2] + c[3] + ex));
+                }
+        for (int color = 0; color < 2; color++)
+            for (int j = 1; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    if (((i + j) & 1) != color) continue;
+                    double c[4], ex, wall;
+                    cn_coeffs_v(nx, ny, h, mu, axisym, i, j, c, &ex, &wall);
+                    double tau = dt / (2.0 * 0.5 * (rho[CC(i, j - 1)] + rho[CC(i, j)]));
+                    double nb = c[2] * vs[YF(i, j + 1)] + c[3] * vs[YF(i, j - 1)] + wall * wb;
+                    if (i + 1 < nx) nb += c[0] * vs[YF(i + 1, j)];
+                    if (i > 0) nb += c[1] * vs[YF(i - 1, j)];
+                    vs[YF(i, j)] = (ve[YF(i, j)] + tau * nb) /
+                                   (1.0 + tau * (c[0] + c[1] + c[2] + c[3] + ex));
+                }
+    }
+    free(ue); free(ve);
+}

@@ -107,6 +107,10 @@ int or_bspline_relocate(int M, const double *X, const double *Y, int ndrops,
                         const int32_t *drop_start, double h, double *Xo,
                         double *Yo);
 
+/* Section 2.1 Crank-Nicolson viscous step: nsweeps red-black sweeps on
+ * u* - dt / (2 rho_f) D(u*) = u_e, (us, vs) = u_e on entry.               */
+void or_cn_solve(int nx, int ny, double h, double dt, const double *rho, const double *mu,
+                 int axisym, double wb, int nsweeps, double *us, double *vs);
 /* Section 2.5: enclosed area (planar) or volume of revolution (axisymmetric)
  * of one drop, and the bisection correction of every drop's measure.      */
 double or_drop_measure(int n, const double *X, const double *Y, int axisym);

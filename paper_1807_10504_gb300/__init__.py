@@ -37,7 +37,7 @@ EXPORTS = [
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
-    "ib_mass_correct",
+    "ib_mass_correct", "ib_op_cn_solve",
 ]
 
 
@@ -56,7 +56,7 @@ class ib_config(C.Structure):
                 ("max_cycles", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("relocate_every", C.c_int32), ("axisym", C.c_int32), ("frame", C.c_int32),
                 ("c1", C.c_double), ("c2", C.c_double), ("mass_every", C.c_int32),
-                ("mass_tol", C.c_double)]
+                ("mass_tol", C.c_double), ("viscous", C.c_int32), ("cn_sweeps", C.c_int32)]
 
 
 _lib = None
@@ -111,6 +111,7 @@ def lib():
             "ib_op_predictor_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _P,
                                     _P, _P, _P, _P, _P],
             "ib_frame_state": [_P, _P], "ib_mass_correct": [_P, _P],
+            "ib_op_cn_solve": [_i32, _i32, _d, _d, _P, _P, _i32, _i32, _P, _P, _P, _P, _P],
             "ib_op_rhs_axi": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _P, _P],
             "ib_op_axi_weights": [_i32, _i32, _d, _P, _P, _P, _P, _P],
         }
@@ -197,6 +198,8 @@ class Config:
     c2: float = 0.1
     mass_every: int = 0
     mass_tol: float = 1e-6
+    viscous: int = 0
+    cn_sweeps: int = 20
 
     def c(self) -> ib_config:
         return ib_config(**{k: getattr(self, k) for k, _ in ib_config._fields_})
@@ -569,6 +572,15 @@ def ib_op_rhs_axi(us, vs, Fx, Fy, bx, by, h, dt):
     _op("ib_op_rhs_axi", nx, ny, h, dt, _ptr(us), _ptr(vs), _ptr(Fx), _ptr(Fy), _ptr(bx),
         _ptr(by), _ptr(b))
     return b
+
+
+def ib_op_cn_solve(rho, mu, ue, ve, h, dt, nsweeps, axisym=0):
+    torch = _torch()
+    ny, nx = rho.shape
+    us, vs = torch.empty_like(ue), torch.empty_like(ve)
+    _op("ib_op_cn_solve", nx, ny, h, dt, _ptr(rho), _ptr(mu), int(axisym), int(nsweeps), _ptr(ue),
+        _ptr(ve), _ptr(us), _ptr(vs))
+    return us, vs
 
 
 def ib_op_axi_weights(bx, by, h):

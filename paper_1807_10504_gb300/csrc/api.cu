@@ -35,6 +35,7 @@ struct ib_ctx {
     double *uw = nullptr, *vw = nullptr, *Hw = nullptr, *Fxw = nullptr, *Fyw = nullptr,
            *bxa = nullptr, *bya = nullptr, *fr = nullptr;
     double *frame = nullptr;   // non-inertial frame record (kFrSlots doubles)
+    double *ue = nullptr, *ve = nullptr, *mh = nullptr;  // Crank-Nicolson: u_e and mu / 2
     double *A0 = nullptr;      // per drop: measure at ib_init (Section 2.5), then eps scratch
     void *dmem = nullptr;
     void *amem = nullptr;
@@ -340,7 +341,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
         g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2 || g.axisym < 0 ||
         g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)) || g.frame < 0 || g.frame > 1 ||
         (g.frame && (!g.axisym || !(g.c1 >= 0) || !(g.c2 >= 0))) || g.mass_every < 0 ||
-        !(g.mass_tol >= 0))
+        !(g.mass_tol >= 0) || g.viscous < 0 || g.viscous > 1 || (g.viscous && g.cn_sweeps < 1))
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -359,18 +360,18 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     ib_status st = check_markers_host(c, g, X, Y, drop_start, ndrops);
     if (st != IB_OK) { delete c; return st; }
     const size_t nc = (size_t)g.nx * g.ny, fx = (size_t)(g.nx + 1) * g.ny, fy = (size_t)g.nx * (g.ny + 1);
-    size_t bytes = al(fx * 8) * 6 + al(fy * 8) * 6 + al(nc * 8) * 5;
+    size_t bytes = al(fx * 8) * 6 + al(fy * 8) * 6 + al(nc * 8) * 6;
     if (cudaMalloc(&c->fmem, bytes) != cudaSuccess) { c->fmem = nullptr; ib_destroy(c); return IB_ENOMEM; }
     char *q = (char *)c->fmem;
     auto take = [&](size_t b) { char *r = q; q += al(b); return (double *)r; };
     c->u = take(fx * 8); c->us = take(fx * 8); c->au = take(fx * 8);
     c->bx = take(fx * 8); c->Fx = take(fx * 8);
-    double *spare_x = take(fx * 8); (void)spare_x;
+    c->ue = take(fx * 8);
     c->v = take(fy * 8); c->vs = take(fy * 8); c->av = take(fy * 8);
     c->by = take(fy * 8); c->Fy = take(fy * 8);
-    double *spare_y = take(fy * 8); (void)spare_y;
+    c->ve = take(fy * 8);
     c->p = take(nc * 8); c->H = take(nc * 8); c->rho = take(nc * 8); c->mu = take(nc * 8);
-    c->b = take(nc * 8);
+    c->b = take(nc * 8); c->mh = take(nc * 8);
     cudaError_t e = cudaMemset(c->fmem, 0, bytes);
     if (e == cudaSuccess) e = mg_alloc(c->mg, g.nx, g.ny, g.h);
     if (e == cudaSuccess && g.axisym) {
@@ -597,17 +598,30 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         heaviside_into(c, c->H);
         launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, c->H, c->rho, c->mu, c->bx,
                       c->by, c->s);
+        // explicit viscous term, or Crank-Nicolson: the explicit predictor with
+        // half the viscosity, then the implicit half
+        const double *mup = c->mu;
+        if (g.viscous) {
+            launch_scale((long)g.nx * g.ny, 0.5, c->mu, c->mh, c->s);
+            mup = c->mh;
+        }
         if (g.axisym) {
             // the r-weighted pressure operator (r_face beta) and right-hand side (r_i b)
             launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
             mg_build(c->mg, c->bxa, c->bya, c->s);
-            launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
+            launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av,
                                  c->have_prev, 0.0, g.gy, g.frame ? c->frame : nullptr, c->us,
                                  c->vs, c->au, c->av, c->s);
         } else {
             mg_build(c->mg, c->bx, c->by, c->s);
-            launch_predictor(g.nx, g.ny, g.h, dt, c->rho, c->mu, c->u, c->v, c->au, c->av,
+            launch_predictor(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av,
                              c->have_prev, g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
+        }
+        if (g.viscous) {
+            cudaMemcpyAsync(c->ue, c->us, (size_t)(g.nx + 1) * g.ny * 8, cudaMemcpyDeviceToDevice, c->s);
+            cudaMemcpyAsync(c->ve, c->vs, (size_t)g.nx * (g.ny + 1) * 8, cudaMemcpyDeviceToDevice, c->s);
+            launch_cn_solve(g.nx, g.ny, g.h, dt, c->rho, c->mu, g.axisym, g.frame ? c->frame : nullptr,
+                            g.cn_sweeps, c->ue, c->ve, c->us, c->vs, c->s);
         }
         c->mg_ready = true;
         force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy);
@@ -1028,6 +1042,18 @@ ib_status ib_op_rhs_axi(int32_t nx, int32_t ny, double h, double dt, const doubl
 {
     OPCHK(nx > 0 && ny > 0 && h > 0 && dt > 0 && us && vs && Fx && Fy && bx && by && b);
     launch_rhs_axi(nx, ny, h, dt, us, vs, Fx, Fy, bx, by, b, (cudaStream_t)stream);
+    return op_done();
+}
+
+ib_status ib_op_cn_solve(int32_t nx, int32_t ny, double h, double dt, const double *rho,
+                         const double *mu, int32_t axisym, int32_t nsweeps, const double *ue,
+                         const double *ve, double *us, double *vs, void *stream)
+{
+    OPCHK(nx > 0 && ny > 0 && h > 0 && dt > 0 && nsweeps >= 0 && rho && mu && ue && ve && us && vs);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyAsync(us, ue, (size_t)(nx + 1) * ny * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(vs, ve, (size_t)nx * (ny + 1) * 8, cudaMemcpyDeviceToDevice, s);
+    launch_cn_solve(nx, ny, h, dt, rho, mu, axisym ? 1 : 0, nullptr, nsweeps, ue, ve, us, vs, s);
     return op_done();
 }
 

@@ -190,7 +190,92 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
     }
 }
 
+// Crank-Nicolson viscous step (Section 2.1): one red-black colour of a
+// Gauss-Seidel sweep on u* - dt / (2 rho_f) D(u*) = u_e for both components
+// at once (they do not couple), in place, boundary faces fixed.  D is the
+// predictor's div(mu grad): cell mu on normal faces, node averages on
+// tangential ones, a no-slip wall by the reflected ghost (moving with the
+// frame's axial velocity wb at the axisymmetric outer wall); axisymmetric:
+// fluxes times their face radius over the volume radius and -mu_f u / r^2
+// on the radial component, zero flux through the axis.
+__global__ void k_cn_sweep(int nx, int ny, double h, double dt, const double *__restrict__ rho,
+                           const double *__restrict__ mu, int axisym,
+                           const double *__restrict__ frame, int color,
+                           const double *__restrict__ ue, const double *__restrict__ ve,
+                           double *__restrict__ us, double *__restrict__ vs)
+{
+    const long nxf = nx + 1;
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nu = nxf * ny;
+    auto M = [&](int i, int j) { return mu[(long)j * nx + i]; };
+    if (k < nu) {
+        const int j = (int)(k / nxf), i = (int)(k - (long)j * nxf);
+        if (i == 0 || i == nx || ((i + j) & 1) != color) return;
+        const double r0 = axisym ? i * h : 1.0, rE = axisym ? (i + 0.5) * h : 1.0,
+                     rW = axisym ? (i - 0.5) * h : 1.0;
+        const double s = 1.0 / (r0 * h * h);
+        const double muN = (j + 1 < ny) ? 0.25 * (M(i - 1, j) + M(i, j) + M(i - 1, j + 1) + M(i, j + 1))
+                                        : 0.5 * (M(i - 1, j) + M(i, j));
+        const double muS = (j > 0) ? 0.25 * (M(i - 1, j - 1) + M(i, j - 1) + M(i - 1, j) + M(i, j))
+                                   : 0.5 * (M(i - 1, j) + M(i, j));
+        const double cE = rE * M(i, j) * s, cW = rW * M(i - 1, j) * s;
+        const double cN = r0 * muN * s, cS = r0 * muS * s;
+        double ex = 0.0, nb = cE * us[k + 1] + cW * us[k - 1], cs = cE + cW;
+        if (j + 1 < ny) { nb += cN * us[k + nxf]; cs += cN; } else ex += 2.0 * cN;
+        if (j > 0) { nb += cS * us[k - nxf]; cs += cS; } else ex += 2.0 * cS;
+        if (axisym) ex += 0.5 * (M(i - 1, j) + M(i, j)) / (r0 * r0);
+        const double tau = dt / (2.0 * (0.5 * (rho[(long)j * nx + i - 1] + rho[(long)j * nx + i])));
+        us[k] = (ue[k] + tau * nb) / (1.0 + tau * (cs + ex));
+        return;
+    }
+    k -= nu;
+    if (k >= (long)nx * (ny + 1)) return;
+    const int j = (int)(k / nx), i = (int)(k - (long)j * nx);
+    if (j == 0 || j == ny || ((i + j) & 1) != color) return;
+    const double r0 = axisym ? (i + 0.5) * h : 1.0, rE = axisym ? (i + 1) * h : 1.0,
+                 rW = axisym ? i * h : 1.0;
+    const double s = 1.0 / (r0 * h * h);
+    const double muE = (i + 1 < nx) ? 0.25 * (M(i, j - 1) + M(i + 1, j - 1) + M(i, j) + M(i + 1, j))
+                                    : 0.5 * (M(i, j - 1) + M(i, j));
+    const double muW = (i > 0) ? 0.25 * (M(i - 1, j - 1) + M(i, j - 1) + M(i - 1, j) + M(i, j))
+                               : 0.5 * (M(i, j - 1) + M(i, j));
+    const double cN = r0 * M(i, j) * s, cS = r0 * M(i, j - 1) * s;
+    const double cE = rE * muE * s, cW = rW * muW * s;
+    const double wb = frame ? frame[kFrWb] : 0.0;
+    double ex = 0.0, nb = cN * vs[k + nx] + cS * vs[k - nx], cs = cN + cS;
+    if (i + 1 < nx) { nb += cE * vs[k + 1]; cs += cE; } else { ex += 2.0 * cE; nb += 2.0 * cE * wb; }
+    if (i > 0) { nb += cW * vs[k - 1]; cs += cW; }
+    else if (!axisym) ex += 2.0 * cW;
+    const double tau = dt / (2.0 * (0.5 * (rho[(long)(j - 1) * nx + i] + rho[(long)j * nx + i])));
+    vs[k] = (ve[k] + tau * nb) / (1.0 + tau * (cs + ex));
+}
+
+__global__ void k_scale(long n, double a, const double *__restrict__ x, double *__restrict__ y)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) y[k] = a * x[k];
+}
+
 }  // namespace
+
+void launch_cn_solve(int nx, int ny, double h, double dt, const double *rho, const double *mu,
+                     int axisym, const double *frame, int nsweeps, const double *ue,
+                     const double *ve, double *us, double *vs, cudaStream_t s)
+{
+    const long nf = (long)(nx + 1) * ny + (long)nx * (ny + 1);
+    for (int sw = 0; sw < nsweeps; sw++)
+        for (int c = 0; c < 2; c++) {
+            note_launch();
+            k_cn_sweep<<<cdiv(nf, kT), kT, 0, s>>>(nx, ny, h, dt, rho, mu, axisym, frame, c, ue, ve,
+                                                   us, vs);
+        }
+}
+
+void launch_scale(long n, double a, const double *x, double *y, cudaStream_t s)
+{
+    note_launch();
+    k_scale<<<cdiv(n, kT), kT, 0, s>>>(n, a, x, y);
+}
 
 void launch_coeffs(int nx, int ny, double rho_g, double rho_l, double mu_g,
                    double mu_l, const double *H, double *rho, double *mu,

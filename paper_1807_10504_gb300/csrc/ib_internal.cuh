@@ -64,6 +64,14 @@ void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       int have_prev, double gx, double gy, double *us,
                       double *vs, double *au, double *av, cudaStream_t s);
 
+// Crank-Nicolson viscous solve: nsweeps red-black sweeps of
+// u* - dt / (2 rho_f) D(u*) = u_e on both components; (us, vs) hold the
+// starting iterate (u_e itself) and receive u*.
+void launch_cn_solve(int nx, int ny, double h, double dt, const double *rho, const double *mu,
+                     int axisym, const double *frame, int nsweeps, const double *ue,
+                     const double *ve, double *us, double *vs, cudaStream_t s);
+void launch_scale(long n, double a, const double *x, double *y, cudaStream_t s);
+
 // ------------------------------------------------------------ axisymmetric
 // Record of the non-inertial frame (device doubles): reference, previous and
 // current centre of mass of drop 0, the next step's acceleration S, the frame

@@ -153,3 +153,45 @@ def test_static_drop_steps_stay_quiet(O):
         out[spread, reloc] = max(np.abs(st.u).max(), np.abs(st.v).max())
     assert out[1, 0] < 1e-9
     assert out[0, 10] > 1e-3 and out[1, 10] < 1e-2 * out[0, 10]
+
+
+@pytest.mark.parametrize("axisym", [0, 1])
+def test_crank_nicolson_solve_against_dense_operator(O, axisym):
+    # Section 2.1's Crank-Nicolson viscous step: u* - dt/(2 rho_f) D(u*) = u_e.
+    # D is built column by column from the explicit predictor itself (the
+    # difference of a step with mu and with mu = 0 isolates dt D(u) / rho_f,
+    # advection being quadratic is cancelled by using the same u), and the
+    # dense system is solved directly; 30 red-black sweeps must agree.
+    nx, ny, h, dt = 8, 10, 0.1, 4e-3
+    H = W.random_H(nx, ny, 51)
+    rho, mu, bx, by = O.coeffs(H, 1e-3, 1.0, 1e-4, 1e-2)
+    mu = mu * 20.0  # make the viscous coupling strong (s ~ 0.8 in the gas)
+    ue, ve = W.random_faces(nx, ny, 52)
+    ue[:, [0, -1]] = 0.0
+    ve[[0, -1], :] = 0.0
+    pred = O.predictor_axi if axisym else O.predictor
+    nu, nv = (nx + 1) * ny, nx * (ny + 1)
+
+    def Dop(x):
+        u, v = x[:nu].reshape(ny, nx + 1), x[nu:].reshape(ny + 1, nx)
+        a = pred(rho, mu, u, v, h, dt)
+        b = pred(rho, 0 * mu, u, v, h, dt)
+        return np.concatenate([((a[0] - b[0]) / 2).ravel(), ((a[1] - b[1]) / 2).ravel()])
+
+    # interior unknowns only (boundary faces keep their values)
+    mask = np.ones(nu + nv, bool)
+    iu = np.arange(nu).reshape(ny, nx + 1)
+    iv = nu + np.arange(nv).reshape(ny + 1, nx)
+    mask[iu[:, [0, -1]].ravel()] = False
+    mask[iv[[0, -1], :].ravel()] = False
+    idx = np.flatnonzero(mask)
+    A = np.zeros((len(idx), len(idx)))
+    for c, k in enumerate(idx):
+        e = np.zeros(nu + nv)
+        e[k] = 1.0
+        A[:, c] = e[idx] - Dop(e)[idx]          # (I - dt/(2 rho) D) e
+    x_e = np.concatenate([ue.ravel(), ve.ravel()])
+    xd = np.linalg.solve(A, x_e[idx])
+    us, vs = O.cn_solve(rho, mu, ue, ve, h, dt, 30, axisym)
+    got = np.concatenate([us.ravel(), vs.ravel()])[idx]
+    assert np.abs(got - xd).max() <= 1e-11 * np.abs(xd).max()
