@@ -93,6 +93,14 @@ typedef struct ib_config {
                                  about its square: 20 sweeps reach ~1e-12 for s <= 0.5;
                                  larger steps need more) */
     int32_t cn_sweeps;
+    int32_t indicator;        /* density and viscosity from 0: the polygon Heaviside H;
+                                 1: the indicator I of Sec. 2.2 Eq. (ind_psn),
+                                 div grad I = div(delta vector), the conventional
+                                 spreading of the inward normals times the arc weights
+                                 (ring-weighted, r-weighted equation, in axisymmetric
+                                 form); Neumann walls, I = 0 on average along the walls
+                                 (not the axis), clipped to [0, 1]; solved by the FP64
+                                 multigrid to 1e-12 from the previous step's I */
 } ib_config;
 
 typedef struct ib_ctx ib_ctx;

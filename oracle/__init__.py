@@ -398,6 +398,40 @@ def drop_com_axi(X, Y, drop_start, d=0):
     return vol.value, zc.value
 
 
+def indicator_poisson(X, Y, drop_start, nx, ny, h, x0=0.0, y0=0.0, kernel=0, axisym=0,
+                      tol=1e-12):
+    """Section 2.2 Eq. (ind_psn): the indicator I of the conventional scheme,
+    div grad I = div(delta vector), the delta vector being the conventional
+    spreading (Eq. (delta)) of the markers' inward unit normals times their
+    arc weights (ring-weighted in the axisymmetric form, where the equation is
+    the r-weighted one).  Neumann walls; the free constant makes the mean of
+    the cells along the walls zero (the axis is not a wall); clipped to [0, 1] (reading: I is a volume
+    fraction).  Returns I."""
+    k, nxm, nym, ds = curvature(X, Y, drop_start)
+    ones = np.ones(len(X))
+    if axisym:
+        Gx, Gy = spread_conv_axi(X, _f64(Y) - y0, ones, nxm, nym, ds, nx, ny, h, kernel)
+    else:
+        Gx, Gy = spread_conv(X, Y, ones, nxm, nym, ds, nx, ny, h, x0, y0, kernel)
+    bx = np.ones((ny, nx + 1))
+    by = np.ones((ny + 1, nx))
+    bx[:, [0, -1]] = 0.0
+    by[[0, -1], :] = 0.0
+    zx, zy = np.zeros_like(bx), np.zeros_like(by)
+    if axisym:
+        b = rhs_axi(Gx, Gy, zx, zy, bx, by, h, 1.0)
+        bxa, bya = axi_weights(bx, by, h)
+        r = (np.arange(nx) + 0.5) * h
+        res = mg_solve(bxa, bya, b * r[None, :], h, tol=tol, max_cycles=300)
+    else:
+        b = rhs(Gx, Gy, zx, zy, bx, by, h, 1.0)
+        res = mg_solve(bx, by, b, h, tol=tol, max_cycles=300)
+    I = res.p
+    # the cells along the walls (the axis column is not a wall)
+    ring = np.concatenate([I[0], I[-1], I[1:-1, -1]] + ([] if axisym else [I[1:-1, 0]]))
+    return np.clip(I - ring.mean(), 0.0, 1.0)
+
+
 def cn_solve(rho, mu, ue, ve, h, dt, nsweeps, axisym=0, wb=0.0):
     """Section 2.1 Crank-Nicolson: nsweeps red-black sweeps on
     u* - dt / (2 rho_f) D(u*) = u_e per component."""
@@ -480,6 +514,7 @@ class Config:
     mass_every: int = 0       # Section 2.5 measure check period in steps, 0 = never
     mass_tol: float = 1e-6
     viscous: int = 0          # 0 explicit, 1 Crank-Nicolson (Section 2.1)
+    indicator: int = 0        # properties from 0: polygon Heaviside, 1: Eq. (ind_psn)
     cn_sweeps: int = 20       # red-black sweeps of the Crank-Nicolson solve
     frame: int = 0            # 1: non-inertial frame following drop 0 (axisym only)
     c1: float = 0.1           # Section 2.4 Eq. (fictitious) constants
@@ -532,7 +567,9 @@ def ns_step(cfg: Config, st: State, dt: float) -> State:
     kap, nxm, nym, ds = curvature(st.X, st.Y, st.drop_start)
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, cfg.x0, cfg.y0)
-    rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
+    Ip = H if not cfg.indicator else indicator_poisson(st.X, st.Y, st.drop_start, cfg.nx,
+                                                        cfg.ny, h, cfg.x0, cfg.y0, cfg.kernel)
+    rho, mu, bx, by = coeffs(Ip, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
     if cfg.viscous:
         us, vs, au, av = predictor(rho, 0.5 * mu, st.u, st.v, h, dt, st.au, st.av,
                                    (cfg.gx, cfg.gy))
@@ -575,7 +612,9 @@ def _ns_step_axi(cfg: Config, st: State, dt: float) -> State:
     kap, nxm, nym, ds = curvature_axi(st.X, st.Y, st.drop_start)
     fmag = cfg.sigma * kap
     H = heaviside(st.X, st.Y, st.drop_start, cfg.nx, cfg.ny, h, 0.0, cfg.y0)
-    rho, mu, bx, by = coeffs(H, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
+    Ip = H if not cfg.indicator else indicator_poisson(st.X, st.Y, st.drop_start, cfg.nx,
+                                                        cfg.ny, h, 0.0, cfg.y0, cfg.kernel, 1)
+    rho, mu, bx, by = coeffs(Ip, cfg.rho_g, cfg.rho_l, cfg.mu_g, cfg.mu_l)
     if cfg.viscous:
         us, vs, au, av = predictor_axi(rho, 0.5 * mu, st.u, st.v, h, dt, st.au, st.av,
                                        (0.0, cfg.gy + S), wb)

@@ -56,7 +56,8 @@ class ib_config(C.Structure):
                 ("max_cycles", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("relocate_every", C.c_int32), ("axisym", C.c_int32), ("frame", C.c_int32),
                 ("c1", C.c_double), ("c2", C.c_double), ("mass_every", C.c_int32),
-                ("mass_tol", C.c_double), ("viscous", C.c_int32), ("cn_sweeps", C.c_int32)]
+                ("mass_tol", C.c_double), ("viscous", C.c_int32), ("cn_sweeps", C.c_int32),
+                ("indicator", C.c_int32)]
 
 
 _lib = None
@@ -200,6 +201,7 @@ class Config:
     mass_tol: float = 1e-6
     viscous: int = 0
     cn_sweeps: int = 20
+    indicator: int = 0
 
     def c(self) -> ib_config:
         return ib_config(**{k: getattr(self, k) for k, _ in ib_config._fields_})

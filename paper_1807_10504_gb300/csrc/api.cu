@@ -36,6 +36,10 @@ struct ib_ctx {
            *bxa = nullptr, *bya = nullptr, *fr = nullptr;
     double *frame = nullptr;   // non-inertial frame record (kFrSlots doubles)
     double *ue = nullptr, *ve = nullptr, *mh = nullptr;  // Crank-Nicolson: u_e and mu / 2
+    // indicator function (Eq. (ind_psn)): unit coefficients, the solution
+    // carried between steps, the wall mean
+    double *ibx = nullptr, *iby = nullptr, *isol = nullptr, *iref = nullptr, *ione = nullptr;
+    void *imem = nullptr;
     double *A0 = nullptr;      // per drop: measure at ib_init (Section 2.5), then eps scratch
     void *dmem = nullptr;
     void *amem = nullptr;
@@ -234,6 +238,26 @@ void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double
     launch_axi_fold(g.nx, g.ny, c->G, g.h, mode == 0, nullptr, c->Fxw, c->Fyw, nullptr, Fx, Fy, c->s);
 }
 
+// Indicator function of Section 2.2 Eq. (ind_psn) into I (after geometry and
+// sorting): the conventional spreading of the unit normals (ring-weighted in
+// axisymmetric mode) into Fx, Fy (scratch here), its divergence into b,
+// the FP64 multigrid on unit (r-weighted) coefficients to 1e-12 from the
+// previous step's solution, the wall mean removed and [0, 1] clipping.  The
+// hierarchy is rebuilt with the pressure coefficients afterwards.
+ib_status indicator_into(ib_ctx *c, double *I)
+{
+    const ib_config &g = c->cfg;
+    force_into(c, 0, c->ione, nullptr, c->Fx, c->Fy);
+    launch_div_faces(g.nx, g.ny, g.h, g.axisym, c->Fx, c->Fy, c->b, c->s);
+    mg_build(c->mg, c->ibx, c->iby, c->s);
+    int cyc = 0;
+    double rr = 0.0;
+    ib_status st = mg_run(c->mg, c->b, c->isol, 0, 1e-12, 300, g.nu1, g.nu2, &cyc, &rr, c->s, c->err);
+    if (st != IB_OK) return st;
+    launch_indicator_finish(g.nx, g.ny, g.axisym, c->isol, c->iref, I, c->s);
+    return IB_OK;
+}
+
 // Section 2.5 measure correction: normals of the current markers, then the
 // per-drop bisection offset (re-symmetrised in axisymmetric mode).
 void mass_correct(ib_ctx *c, double *eps)
@@ -325,6 +349,7 @@ void ib_destroy(ib_ctx *c)
     if (c->fmem) cudaFree(c->fmem);
     if (c->amem) cudaFree(c->amem);
     if (c->dmem) cudaFree(c->dmem);
+    if (c->imem) cudaFree(c->imem);
     if (c->flags_host) cudaFreeHost(c->flags_host);
     delete c;
 }
@@ -341,7 +366,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
         g.spread < 0 || g.spread > 1 || g.precision < 0 || g.precision > 2 || g.axisym < 0 ||
         g.axisym > 1 || (g.axisym && (g.x0 != 0.0 || g.gx != 0.0)) || g.frame < 0 || g.frame > 1 ||
         (g.frame && (!g.axisym || !(g.c1 >= 0) || !(g.c2 >= 0))) || g.mass_every < 0 ||
-        !(g.mass_tol >= 0) || g.viscous < 0 || g.viscous > 1 || (g.viscous && g.cn_sweeps < 1))
+        !(g.mass_tol >= 0) || g.viscous < 0 || g.viscous > 1 || (g.viscous && g.cn_sweeps < 1) ||
+        g.indicator < 0 || g.indicator > 1)
         return IB_EINVAL;
     std::vector<int> nxs, nys;
     if (!mg_levels(g.nx, g.ny, nxs, nys)) return IB_EINVAL;
@@ -403,6 +429,26 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess && g.frame) {
         launch_axi_frame(c->mk, 1.0, g.c1, g.c2, 1, c->frame, c->s);
         e = cudaStreamSynchronize(c->s);
+    }
+    if (e == cudaSuccess && g.indicator) {
+        const size_t ib = al(fx * 8) + al(fy * 8) + al(nc * 8) + al(8) + al((size_t)M * 8);
+        e = cudaMalloc(&c->imem, ib);
+        if (e == cudaSuccess) {
+            char *a = (char *)c->imem;
+            c->ibx = (double *)a; a += al(fx * 8);
+            c->iby = (double *)a; a += al(fy * 8);
+            c->isol = (double *)a; a += al(nc * 8);
+            c->iref = (double *)a; a += al(8);
+            c->ione = (double *)a;
+            e = cudaMemset(c->imem, 0, ib);
+            if (e == cudaSuccess) {
+                launch_unit_beta(g.nx, g.ny, g.h, g.axisym, c->ibx, c->iby, c->s);
+                launch_fill(M, 1.0, c->ione, c->s);
+                e = cudaStreamSynchronize(c->s);
+            }
+        } else {
+            c->imem = nullptr;
+        }
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
@@ -596,7 +642,13 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         geometry(c);
         launch_sort(mk, c->s);
         heaviside_into(c, c->H);
-        launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, c->H, c->rho, c->mu, c->bx,
+        const double *prop = c->H;
+        if (g.indicator) {
+            ib_status is = indicator_into(c, c->mh);
+            if (is != IB_OK) return is;
+            prop = c->mh;
+        }
+        launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, prop, c->rho, c->mu, c->bx,
                       c->by, c->s);
         // explicit viscous term, or Crank-Nicolson: the explicit predictor with
         // half the viscosity, then the implicit half

@@ -250,6 +250,63 @@ __global__ void k_cn_sweep(int nx, int ny, double h, double dt, const double *__
     vs[k] = (ve[k] + tau * nb) / (1.0 + tau * (cs + ex));
 }
 
+// Indicator function of Section 2.2 Eq. (ind_psn), div grad I = div G:
+// the right-hand side div G of the face field G (the spread delta vector),
+// r_i times the axisymmetric divergence in that form; unit coefficients with
+// the walls at zero (r_face for the axisymmetric form).
+__global__ void k_div_faces(int nx, int ny, double h, int axisym, const double *__restrict__ Gx,
+                            const double *__restrict__ Gy, double *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const long xw = (long)j * (nx + 1) + i, ys = (long)j * nx + i, yn = ys + nx;
+    if (!axisym) {
+        b[ys] = (Gx[xw + 1] - Gx[xw] + Gy[yn] - Gy[ys]) / h;
+        return;
+    }
+    const double ri = (i + 0.5) * h;
+    b[ys] = ri * (((i + 1) * h * Gx[xw + 1] - i * h * Gx[xw]) / (ri * h) + (Gy[yn] - Gy[ys]) / h);
+}
+
+__global__ void k_unit_beta(int nx, int ny, double h, int axisym, double *__restrict__ bx,
+                            double *__restrict__ by)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (j < ny && i <= nx) bx[(long)j * (nx + 1) + i] = (i == 0 || i == nx) ? 0.0 : (axisym ? i * h : 1.0);
+    if (i < nx) by[(long)j * nx + i] = (j == 0 || j == ny) ? 0.0 : (axisym ? (i + 0.5) * h : 1.0);
+}
+
+// I = clamp(sol - mean over the cells along the walls (the axis column is not
+// a wall), 0, 1); the mean in a fixed order (bottom row, top row, then the
+// right column and, planar, the left column, each in index order) by one
+// thread into *ref, then the shift by a grid of threads.
+__global__ void k_wall_mean(int nx, int ny, int axisym, const double *__restrict__ sol,
+                            double *__restrict__ ref)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    long cnt = 0;
+    for (int i = 0; i < nx; i++) { s += sol[i]; cnt++; }
+    for (int i = 0; i < nx; i++) { s += sol[(long)(ny - 1) * nx + i]; cnt++; }
+    for (int j = 1; j < ny - 1; j++) { s += sol[(long)j * nx + nx - 1]; cnt++; }
+    if (!axisym)
+        for (int j = 1; j < ny - 1; j++) { s += sol[(long)j * nx]; cnt++; }
+    *ref = s / (double)cnt;
+}
+
+__global__ void k_shift_clip(long n, const double *__restrict__ sol, const double *__restrict__ ref,
+                             double *__restrict__ I)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) I[k] = fmin(fmax(sol[k] - *ref, 0.0), 1.0);
+}
+
+__global__ void k_fill(long n, double a, double *__restrict__ y)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) y[k] = a;
+}
+
 __global__ void k_scale(long n, double a, const double *__restrict__ x, double *__restrict__ y)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,6 +326,35 @@ void launch_cn_solve(int nx, int ny, double h, double dt, const double *rho, con
             k_cn_sweep<<<cdiv(nf, kT), kT, 0, s>>>(nx, ny, h, dt, rho, mu, axisym, frame, c, ue, ve,
                                                    us, vs);
         }
+}
+
+void launch_div_faces(int nx, int ny, double h, int axisym, const double *Gx, const double *Gy,
+                      double *b, cudaStream_t s)
+{
+    note_launch();
+    k_div_faces<<<dim3(cdiv(nx, 128), ny), 128, 0, s>>>(nx, ny, h, axisym, Gx, Gy, b);
+}
+
+void launch_unit_beta(int nx, int ny, double h, int axisym, double *bx, double *by, cudaStream_t s)
+{
+    note_launch();
+    k_unit_beta<<<dim3(cdiv(nx + 1, 128), ny + 1), 128, 0, s>>>(nx, ny, h, axisym, bx, by);
+}
+
+void launch_indicator_finish(int nx, int ny, int axisym, const double *sol, double *ref, double *I,
+                             cudaStream_t s)
+{
+    note_launch();
+    k_wall_mean<<<1, 32, 0, s>>>(nx, ny, axisym, sol, ref);
+    const long n = (long)nx * ny;
+    note_launch();
+    k_shift_clip<<<cdiv(n, kT), kT, 0, s>>>(n, sol, ref, I);
+}
+
+void launch_fill(long n, double a, double *y, cudaStream_t s)
+{
+    note_launch();
+    k_fill<<<cdiv(n, kT), kT, 0, s>>>(n, a, y);
 }
 
 void launch_scale(long n, double a, const double *x, double *y, cudaStream_t s)

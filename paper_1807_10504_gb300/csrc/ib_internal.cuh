@@ -71,6 +71,15 @@ void launch_cn_solve(int nx, int ny, double h, double dt, const double *rho, con
                      int axisym, const double *frame, int nsweeps, const double *ue,
                      const double *ve, double *us, double *vs, cudaStream_t s);
 void launch_scale(long n, double a, const double *x, double *y, cudaStream_t s);
+void launch_fill(long n, double a, double *y, cudaStream_t s);
+// Indicator function (Section 2.2 Eq. (ind_psn)): right-hand side div G, the
+// unit (or r-weighted) coefficients, and the shift to zero along the walls
+// with clipping to [0, 1].
+void launch_div_faces(int nx, int ny, double h, int axisym, const double *Gx, const double *Gy,
+                      double *b, cudaStream_t s);
+void launch_unit_beta(int nx, int ny, double h, int axisym, double *bx, double *by, cudaStream_t s);
+void launch_indicator_finish(int nx, int ny, int axisym, const double *sol, double *ref, double *I,
+                             cudaStream_t s);
 
 // ------------------------------------------------------------ axisymmetric
 // Record of the non-inertial frame (device doubles): reference, previous and

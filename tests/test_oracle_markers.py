@@ -312,3 +312,28 @@ def test_mass_correction_restores_the_measure(O):
         # within the tolerance nothing moves
         Xn, Yn, e0 = O.mass_correct(mk.X, mk.Y, mk.drop_start, A0 * (1 + 5e-7), h, axisym)
         assert e0[0] == 0.0 and np.array_equal(Xn, mk.X)
+
+
+@pytest.mark.parametrize("axisym", [0, 1])
+def test_indicator_poisson_is_the_drop_indicator(O, axisym):
+    # Eq. (ind_psn): I from div grad I = div(delta vector) is 1 deep inside a
+    # drop and 0 far outside, and its integral (area, or volume of
+    # revolution) is the drop's measure to O(h^2); its discrete gradient
+    # differs from the delta vector by a divergence-free field only.
+    n, h, R = 64, 1 / 64, 0.25
+    if axisym:
+        mk = W.axi_sphere(0.5, R, 128)
+        I = O.indicator_poisson(mk.X, mk.Y, mk.drop_start, 32, 64, h, axisym=1)
+        r = (np.arange(32) + 0.5) * h
+        meas = 2 * np.pi * (I * r[None, :]).sum() * h * h
+        exact = 4 / 3 * np.pi * R**3
+        inside, outside = I[32, 2], I[2, 30]
+    else:
+        mk = W.static_drop(n, R, 128)
+        I = O.indicator_poisson(mk.X, mk.Y, mk.drop_start, n, n, h)
+        meas = I.sum() * h * h
+        exact = np.pi * R**2
+        inside, outside = I[32, 32], I[3, 3]
+    assert abs(inside - 1.0) < 1e-3 and outside < 1e-3
+    assert abs(meas - exact) < 1e-2 * exact
+    assert I.min() >= 0.0 and I.max() <= 1.0
