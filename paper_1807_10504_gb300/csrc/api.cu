@@ -11,6 +11,15 @@
 
 #include "ib_internal.cuh"
 
+// A recorded phase of a time step: its launches as a CUDA graph, keyed by
+// the time step and the step's options.
+struct StepGraph {
+    double dt = 0.0;
+    int key = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+};
+
 struct ib_ctx {
     ib_config cfg;
     cudaStream_t s = nullptr;
@@ -40,6 +49,14 @@ struct ib_ctx {
     // carried between steps, the wall mean
     double *ibx = nullptr, *iby = nullptr, *isol = nullptr, *iref = nullptr, *ione = nullptr;
     void *imem = nullptr;
+    // side stream of a step: the multigrid hierarchy is built there while the
+    // predictor, spreading and right-hand side run on s
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // recorded step phases (see run_recorded) and their capture stream
+    std::vector<StepGraph> sgraphs;
+    cudaStream_t cap = nullptr;
+    bool step_graphs_off = false;
     double *A0 = nullptr;      // per drop: measure at ib_init (Section 2.5), then eps scratch
     void *dmem = nullptr;
     void *amem = nullptr;
@@ -221,21 +238,22 @@ void heaviside_into(ib_ctx *c, double *H)
 // conventional spreading of the ring magnitudes sigma kappa |r| on the wide
 // grid, folded with division by the face radius; irrotational spreading on
 // the wide grid's Heaviside (set by heaviside_into), folded.
-void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double *Fx, double *Fy)
+void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double *Fx, double *Fy,
+                cudaStream_t s)
 {
     const ib_config &g = c->cfg;
     if (!g.axisym) {
-        if (mode == 0) launch_spread_conv(c->mk, g.kernel, fmag, Fx, Fy, c->s);
-        else launch_spread_irrot(c->mk, fmag, H, Fx, Fy, c->s);
+        if (mode == 0) launch_spread_conv(c->mk, g.kernel, fmag, Fx, Fy, s);
+        else launch_spread_irrot(c->mk, fmag, H, Fx, Fy, s);
         return;
     }
     if (mode == 0) {
-        launch_axi_ring(c->mk, fmag, c->fr, c->s);
-        launch_spread_conv(c->mk, g.kernel, c->fr, c->Fxw, c->Fyw, c->s);
+        launch_axi_ring(c->mk, fmag, c->fr, s);
+        launch_spread_conv(c->mk, g.kernel, c->fr, c->Fxw, c->Fyw, s);
     } else {
-        launch_spread_irrot(c->mk, fmag, c->Hw, c->Fxw, c->Fyw, c->s);
+        launch_spread_irrot(c->mk, fmag, c->Hw, c->Fxw, c->Fyw, s);
     }
-    launch_axi_fold(g.nx, g.ny, c->G, g.h, mode == 0, nullptr, c->Fxw, c->Fyw, nullptr, Fx, Fy, c->s);
+    launch_axi_fold(g.nx, g.ny, c->G, g.h, mode == 0, nullptr, c->Fxw, c->Fyw, nullptr, Fx, Fy, s);
 }
 
 // Indicator function of Section 2.2 Eq. (ind_psn) into I (after geometry and
@@ -247,7 +265,7 @@ void force_into(ib_ctx *c, int mode, const double *fmag, const double *H, double
 ib_status indicator_into(ib_ctx *c, double *I)
 {
     const ib_config &g = c->cfg;
-    force_into(c, 0, c->ione, nullptr, c->Fx, c->Fy);
+    force_into(c, 0, c->ione, nullptr, c->Fx, c->Fy, c->s);
     launch_div_faces(g.nx, g.ny, g.h, g.axisym, c->Fx, c->Fy, c->b, c->s);
     mg_build(c->mg, c->ibx, c->iby, c->s);
     int cyc = 0;
@@ -326,8 +344,135 @@ ib_status spread_into(ib_ctx *c, int mode, const double *fmag, double *Fx, doubl
     const double *f = fmag ? fmag : mk.fmag;
     double *Hd = H ? H : c->H;
     if (mode == 1) heaviside_into(c, Hd);
-    force_into(c, mode, f, Hd, Fx, Fy);
+    force_into(c, mode, f, Hd, Fx, Fy, c->s);
     return launch_check(c, "spread");
+}
+
+// The launches of one time step before the pressure solve, on c->s: marker
+// upkeep (relocation, measure correction), geometry, binning, Heaviside (or
+// the indicator), properties and face coefficients; then, with the side
+// stream, the multigrid hierarchy and the face force next to the predictor
+// (and the Crank-Nicolson solve); the right-hand side; p = 0 for a cold start.
+ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
+{
+    const ib_config &g = c->cfg;
+    Markers &mk = c->mk;
+    if (reloc) {
+        launch_relocate(mk, c->s);
+        if (g.axisym) launch_axi_symmetrise(mk, c->s);
+    }
+    if (mass) mass_correct(c, nullptr);
+    geometry(c);
+    launch_sort(mk, c->s);
+    heaviside_into(c, c->H);
+    const double *prop = c->H;
+    if (g.indicator) {
+        ib_status is = indicator_into(c, c->mh);
+        if (is != IB_OK) return is;
+        prop = c->mh;
+    }
+    launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, prop, c->rho, c->mu, c->bx, c->by,
+                  c->s);
+    // explicit viscous term, or Crank-Nicolson: the explicit predictor with
+    // half the viscosity, then the implicit half
+    const double *mup = c->mu;
+    if (g.viscous) {
+        launch_scale((long)g.nx * g.ny, 0.5, c->mu, c->mh, c->s);
+        mup = c->mh;
+    }
+    // on the side stream, overlapping the predictor: the hierarchy of the
+    // pressure coefficients (the r-weighted operator r_face beta in
+    // axisymmetric form), then the face force, which depends on neither
+    if (g.axisym) launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
+    cudaEventRecord(c->ev_fork, c->s);
+    cudaStreamWaitEvent(c->s2, c->ev_fork, 0);
+    mg_build(c->mg, g.axisym ? c->bxa : c->bx, g.axisym ? c->bya : c->by, c->s2);
+    force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s2);
+    cudaEventRecord(c->ev_join, c->s2);
+    if (g.axisym)
+        launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
+                             0.0, g.gy, g.frame ? c->frame : nullptr, c->us, c->vs, c->au, c->av,
+                             c->s);
+    else
+        launch_predictor(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
+                         g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
+    if (g.viscous) {
+        cudaMemcpyAsync(c->ue, c->us, (size_t)(g.nx + 1) * g.ny * 8, cudaMemcpyDeviceToDevice, c->s);
+        cudaMemcpyAsync(c->ve, c->vs, (size_t)g.nx * (g.ny + 1) * 8, cudaMemcpyDeviceToDevice, c->s);
+        launch_cn_solve(g.nx, g.ny, g.h, dt, c->rho, c->mu, g.axisym, g.frame ? c->frame : nullptr,
+                        g.cn_sweeps, c->ue, c->ve, c->us, c->vs, c->s);
+    }
+    c->mg_ready = true;
+    cudaStreamWaitEvent(c->s, c->ev_join, 0);  // the hierarchy and the force are complete
+    if (g.axisym)
+        launch_rhs_axi(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
+    else
+        launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
+    if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
+    return launch_check(c, "step");
+}
+
+// The launches after the pressure solve: velocity correction, the frame's
+// boundary velocity, marker advection (re-symmetrised), the frame update and
+// the marker check.
+ib_status step_post(ib_ctx *c, double dt)
+{
+    const ib_config &g = c->cfg;
+    Markers &mk = c->mk;
+    launch_correct(g.nx, g.ny, g.h, dt, c->us, c->vs, c->p, c->Fx, c->Fy, c->bx, c->by, c->u, c->v,
+                   c->s);
+    if (g.frame) launch_axi_zbc(g.nx, g.ny, c->frame, c->v, c->s);
+    interp_into(c, c->u, c->v, mk.U, mk.V, dt);
+    if (g.frame) launch_axi_frame(mk, dt, g.c1, g.c2, 0, c->frame, c->s);
+    launch_validate(mk, c->s);
+    return launch_check(c, "step");
+}
+
+// Runs fn's launches on c->s through a CUDA graph recorded the first time
+// (dt, key) is seen: recorded on the private stream c->cap (c->s points at
+// it meanwhile), then replayed on c->s.  Direct launches while graphs are
+// off or per-kernel timing is active, and for good if recording fails.
+template <typename F>
+ib_status run_recorded(ib_ctx *c, double dt, int key, F fn)
+{
+    if (!c->mg.use_graphs || profiling_active() || c->step_graphs_off) return fn();
+    StepGraph *sg = nullptr;
+    for (auto &q : c->sgraphs)
+        if (q.dt == dt && q.key == key) sg = &q;
+    if (!sg) {
+        if (c->sgraphs.size() >= 16) {
+            cudaGraphExecDestroy(c->sgraphs.front().exec);
+            c->sgraphs.erase(c->sgraphs.begin());
+        }
+        cudaStream_t user = c->s;
+        c->s = c->cap;
+        const unsigned long long k0 = launch_count();
+        cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        ib_status st = IB_OK;
+        cudaGraph_t gr = nullptr;
+        if (e == cudaSuccess) {
+            st = fn();
+            e = cudaStreamEndCapture(c->cap, &gr);
+        }
+        c->s = user;
+        StepGraph q;
+        q.dt = dt;
+        q.key = key;
+        q.kernels = launch_count() - k0;
+        note_launch(-(int)q.kernels);  // recording launches nothing
+        if (e == cudaSuccess && st == IB_OK) e = cudaGraphInstantiate(&q.exec, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess || st != IB_OK || !q.exec) {
+            cudaGetLastError();
+            c->err.clear();
+            c->step_graphs_off = true;
+            return fn();
+        }
+        c->sgraphs.push_back(q);
+        sg = &c->sgraphs.back();
+    }
+    note_launch((int)sg->kernels);
+    return cuda_check(c, cudaGraphLaunch(sg->exec, c->s), "step graph");
 }
 
 }  // namespace
@@ -350,6 +495,12 @@ void ib_destroy(ib_ctx *c)
     if (c->amem) cudaFree(c->amem);
     if (c->dmem) cudaFree(c->dmem);
     if (c->imem) cudaFree(c->imem);
+    for (auto &q : c->sgraphs)
+        if (q.exec) cudaGraphExecDestroy(q.exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->s2) cudaStreamDestroy(c->s2);
     if (c->flags_host) cudaFreeHost(c->flags_host);
     delete c;
 }
@@ -450,6 +601,17 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
             c->imem = nullptr;
         }
     }
+    if (e == cudaSuccess) {
+        // highest priority: the side stream's small kernels (single-CTA
+        // coefficient and coarse-inverse builds) take free SM slots ahead of
+        // the predictor's blocks instead of waiting for its grid to drain
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        e = cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
         c->A0 = (double *)c->dmem;
@@ -632,58 +794,17 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid "
                                   "(side a multiple of 4 * 2^coarsen)");
     const ib_config &g = c->cfg;
-    Markers &mk = c->mk;
     for (int it = 0; it < nsteps; it++) {
-        if (g.relocate_every > 0 && c->step % g.relocate_every == 0) {
-            launch_relocate(mk, c->s);
-            if (g.axisym) launch_axi_symmetrise(mk, c->s);
-        }
-        if (g.mass_every > 0 && c->step > 0 && c->step % g.mass_every == 0) mass_correct(c, nullptr);
-        geometry(c);
-        launch_sort(mk, c->s);
-        heaviside_into(c, c->H);
-        const double *prop = c->H;
-        if (g.indicator) {
-            ib_status is = indicator_into(c, c->mh);
-            if (is != IB_OK) return is;
-            prop = c->mh;
-        }
-        launch_coeffs(g.nx, g.ny, g.rho_g, g.rho_l, g.mu_g, g.mu_l, prop, c->rho, c->mu, c->bx,
-                      c->by, c->s);
-        // explicit viscous term, or Crank-Nicolson: the explicit predictor with
-        // half the viscosity, then the implicit half
-        const double *mup = c->mu;
-        if (g.viscous) {
-            launch_scale((long)g.nx * g.ny, 0.5, c->mu, c->mh, c->s);
-            mup = c->mh;
-        }
-        if (g.axisym) {
-            // the r-weighted pressure operator (r_face beta) and right-hand side (r_i b)
-            launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
-            mg_build(c->mg, c->bxa, c->bya, c->s);
-            launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av,
-                                 c->have_prev, 0.0, g.gy, g.frame ? c->frame : nullptr, c->us,
-                                 c->vs, c->au, c->av, c->s);
-        } else {
-            mg_build(c->mg, c->bx, c->by, c->s);
-            launch_predictor(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av,
-                             c->have_prev, g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
-        }
-        if (g.viscous) {
-            cudaMemcpyAsync(c->ue, c->us, (size_t)(g.nx + 1) * g.ny * 8, cudaMemcpyDeviceToDevice, c->s);
-            cudaMemcpyAsync(c->ve, c->vs, (size_t)g.nx * (g.ny + 1) * 8, cudaMemcpyDeviceToDevice, c->s);
-            launch_cn_solve(g.nx, g.ny, g.h, dt, c->rho, c->mu, g.axisym, g.frame ? c->frame : nullptr,
-                            g.cn_sweeps, c->ue, c->ve, c->us, c->vs, c->s);
-        }
-        c->mg_ready = true;
-        force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy);
-        if (g.axisym)
-            launch_rhs_axi(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
-        else
-            launch_rhs(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
-        ib_status st = launch_check(c, "step");
+        const bool reloc = g.relocate_every > 0 && c->step % g.relocate_every == 0;
+        const bool mass = g.mass_every > 0 && c->step > 0 && c->step % g.mass_every == 0;
+        // the launches before the pressure solve replay a recorded graph once
+        // the step's shape has been seen (not with the indicator's inner solve
+        // or the network, which synchronise with the host)
+        const bool rec = c->have_prev && !g.indicator && warm != 2;
+        const int key = (reloc ? 1 : 0) | (mass ? 2 : 0) | (warm == 0 ? 4 : 0);
+        ib_status st = rec ? run_recorded(c, dt, key, [&] { return step_pre(c, dt, reloc, mass, warm); })
+                           : step_pre(c, dt, reloc, mass, warm);
         if (st != IB_OK) return st;
-        if (warm == 0) cudaMemsetAsync(c->p, 0, (size_t)g.nx * g.ny * 8, c->s);
         if (warm == 2) {
             cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
             if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
@@ -691,19 +812,16 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                     &c->last_cycles, &c->last_relres, c->s, c->err);
         if (st != IB_OK && st != IB_ENOTCONV) return st;
-        launch_correct(g.nx, g.ny, g.h, dt, c->us, c->vs, c->p, c->Fx, c->Fy, c->bx, c->by, c->u,
-                       c->v, c->s);
-        if (g.frame) launch_axi_zbc(g.nx, g.ny, c->frame, c->v, c->s);
-        interp_into(c, c->u, c->v, mk.U, mk.V, dt);
-        if (g.frame) launch_axi_frame(mk, dt, g.c1, g.c2, 0, c->frame, c->s);
-        launch_validate(mk, c->s);
+        const ib_status sp = rec ? run_recorded(c, dt, 64, [&] { return step_post(c, dt); })
+                                 : step_post(c, dt);
+        if (sp != IB_OK) return sp;
         c->have_prev = 1;
         c->step++;
         ib_status fs = read_flags(c);
         if (fs != IB_OK) return fs;
         if (st != IB_OK) return st;
     }
-    return launch_check(c, "step");
+    return IB_OK;
 }
 
 unsigned long long ib_launch_count(void) { return launch_count(); }

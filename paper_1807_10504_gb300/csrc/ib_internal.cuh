@@ -36,7 +36,14 @@ __device__ __forceinline__ double recip_nr(double x)
     return fma(r, e, r);
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (one
+// host call the first time a larger value is needed, none afterwards, so
+// that launches recorded into a CUDA graph make no such call).
+void raise_smem_limit(const void *kernel, int bytes);
+
 // Process-wide count of kernel launches issued by this library.
+// True while per-kernel event timing is active (no graph replays then).
+bool profiling_active();
 void note_launch(int n = 1);
 unsigned long long launch_count();
 

@@ -1581,7 +1581,7 @@ void launch_mass_correct(Markers &mk, const double *A0, int axisym, double tol, 
 void launch_relocate(Markers &mk, cudaStream_t s)
 {
     size_t sm = relocate_smem(mk.max_drop);
-    cudaFuncSetAttribute(k_relocate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void *)k_relocate, (int)sm);
     note_launch();
     k_relocate<<<mk.ndrops, kT, sm, s>>>(mk.X, mk.Y, mk.drop_start, mk.h, mk.max_drop, mk.Xn,
                                          mk.Yn, mk.flags);

@@ -36,6 +36,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "ib_internal.cuh"
 
@@ -1280,6 +1283,24 @@ void note_launch(int n) { g_launches += (unsigned long long)(long long)n; }
 unsigned long long launch_count() { return g_launches.load(); }
 bool prof_on(int kind) { return g_prof.kind == kind && g_prof.n < kProfMax; }
 static bool prof_active() { return g_prof.kind >= 0; }
+bool profiling_active() { return prof_active(); }
+
+void raise_smem_limit(const void *kernel, int bytes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> set;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto &e : set)
+        if (e.first == kernel) {
+            if (bytes > e.second) {
+                cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                e.second = bytes;
+            }
+            return;
+        }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    set.emplace_back(kernel, bytes);
+}
 void prof_mark(cudaStream_t s, bool start)
 {
     if (start) {
@@ -1561,17 +1582,15 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
             ef += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
         }
         const size_t inv = tail_inv_bytes(mg.lv[L - 1].nx * mg.lv[L - 1].ny);
-        cudaFuncSetAttribute(k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((e * 8 + 7) & ~(size_t)7) + inv));
-        cudaFuncSetAttribute(k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((ef * 4 + 7) & ~(size_t)7) + inv));
+        raise_smem_limit((const void *)k_tail<double>, (int)(((e * 8 + 7) & ~(size_t)7) + inv));
+        raise_smem_limit((const void *)k_tail<float>, (int)(((ef * 4 + 7) & ~(size_t)7) + inv));
     }
     Level &vc = mg.lv[L - 1];
     note_launch();
     const size_t nc2 = (size_t)vc.nx * vc.ny * vc.nx * vc.ny;
     const size_t cbytes = 2 * nc2 * sizeof(double);
     const int in_smem = cbytes <= 96 * 1024;
-    if (in_smem) cudaFuncSetAttribute(k_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cbytes);
+    if (in_smem) raise_smem_limit((const void *)k_coarse_inv, (int)cbytes);
     k_coarse_inv<<<1, 1024, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
                                                        mg.lu + nc2, in_smem);
 }
