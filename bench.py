@@ -260,7 +260,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
-        ctx.ns_step(dt, 1, 1)
+        ctx.ns_step(dt, 1, args.warm)
     torch.cuda.synchronize()
 
     def barrier():
@@ -287,7 +287,7 @@ def run_ours(args):
     if args.ncu:
         torch.cuda.profiler.start()
         for k in range(args.steps):
-            ctx.ns_step(dt, 1, 1)
+            ctx.ns_step(dt, 1, args.warm)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         ctx.close()
@@ -303,7 +303,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        c, _ = ctx.ns_step(dt, 1, 1)
+        c, _ = ctx.ns_step(dt, 1, args.warm)
         ev[k][1].record(stream)
         cycles.append(c)
     barrier()
@@ -318,7 +318,7 @@ def run_ours(args):
     ib.profile_begin(sweep_kind)
     for k in range(args.steps):
         flush.zero_()
-        ctx.ns_step(dt, 1, 1)
+        ctx.ns_step(dt, 1, args.warm)
     barrier()
     sweep_ms, sweep_n = ib.profile_end()
 
@@ -421,7 +421,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_markers_host(Xh, Yh)
-        ctx.ns_step(dt, 1, 1)
+        ctx.ns_step(dt, 1, args.warm)
         ctx.get_host("p", ph)
         ctx.get_markers_host(Xh, Yh)
     barrier()
@@ -440,7 +440,9 @@ def run_ours(args):
                    "geometry": "axisymmetric (r, z), non-inertial frame" if axi else "planar",
                    "spread": "irrotational", "relocate_every": 10, "tol": 1e-10,
                    "solver": SOLVERS[args.precision],
-                   "warm_start": "previous pressure", "l2": "flushed before each step (256 MiB)",
+                   "warm_start": {0: "zero", 1: "previous pressure",
+                                  3: "2 p^n - p^(n-1)"}[args.warm],
+                   "l2": "flushed before each step (256 MiB)",
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
         "clocks": clocks,
@@ -497,6 +499,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="multidrop1024", choices=list(WORKLOADS))
     ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2])
+    ap.add_argument("--warm", type=int, default=1, choices=[0, 1, 3],
+                    help="pressure initial guess of each step: 0 zero, 1 previous pressure, "
+                         "3 extrapolated from the previous two")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned warm start")
     ap.add_argument("--cnn-samples", type=int, default=800)

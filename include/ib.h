@@ -202,12 +202,15 @@ ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
 
 /* One or more time steps of Section 2.1's fractional step with the force in
  * the projection (Sec. 3.2 Eq. (ns2_new)): [B-spline relocation every
- * relocate_every steps], curvature, Heaviside, rho/mu/beta (Eq.
- * (indicator)), AB2 advection + explicit viscous predictor (Eqs. (ad_bf),
- * (cr_ni)), spreading, rhs, pressure solve, correction, interpolation and
- * marker advection X += dt U.  warm: 0 zero initial pressure, 1 previous
- * step's pressure, 2 the attached network's estimate (square grid, side a
- * multiple of 4).  The last step's cycles and residual are returned by
+ * relocate_every steps, Sec. 2.5 measure correction every mass_every],
+ * curvature, Heaviside (or the indicator), rho/mu/beta (Eq. (indicator)),
+ * AB2 advection + viscous predictor (Eqs. (ad_bf), (cr_ni); explicit or
+ * Crank-Nicolson), spreading, rhs, pressure solve, correction,
+ * interpolation and marker advection X += dt U.  warm: the pressure solve's
+ * initial guess, 0 zero, 1 the previous step's pressure, 2 the attached
+ * network's estimate (square grid, side a multiple of 4), 3 the previous
+ * two steps' pressures extrapolated in time, 2 p^n - p^(n-1) (p^n until two
+ * exist).  The last step's cycles and residual are returned by
  * ib_last_solve.                                                           */
 ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
 /* Non-inertial frame (cfg.frame = 1): out[0] drop 0's axial centre of mass,

@@ -45,6 +45,8 @@ struct ib_ctx {
            *bxa = nullptr, *bya = nullptr, *fr = nullptr;
     double *frame = nullptr;   // non-inertial frame record (kFrSlots doubles)
     double *ue = nullptr, *ve = nullptr, *mh = nullptr;  // Crank-Nicolson: u_e and mu / 2
+    double *pprev = nullptr;   // the previous step's pressure (warm start 3)
+    bool have_pprev = false;
     // indicator function (Eq. (ind_psn)): unit coefficients, the solution
     // carried between steps, the wall mean
     double *ibx = nullptr, *iby = nullptr, *isol = nullptr, *iref = nullptr, *ione = nullptr;
@@ -537,7 +539,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     ib_status st = check_markers_host(c, g, X, Y, drop_start, ndrops);
     if (st != IB_OK) { delete c; return st; }
     const size_t nc = (size_t)g.nx * g.ny, fx = (size_t)(g.nx + 1) * g.ny, fy = (size_t)g.nx * (g.ny + 1);
-    size_t bytes = al(fx * 8) * 6 + al(fy * 8) * 6 + al(nc * 8) * 6;
+    size_t bytes = al(fx * 8) * 6 + al(fy * 8) * 6 + al(nc * 8) * 7;
     if (cudaMalloc(&c->fmem, bytes) != cudaSuccess) { c->fmem = nullptr; ib_destroy(c); return IB_ENOMEM; }
     char *q = (char *)c->fmem;
     auto take = [&](size_t b) { char *r = q; q += al(b); return (double *)r; };
@@ -548,7 +550,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     c->by = take(fy * 8); c->Fy = take(fy * 8);
     c->ve = take(fy * 8);
     c->p = take(nc * 8); c->H = take(nc * 8); c->rho = take(nc * 8); c->mu = take(nc * 8);
-    c->b = take(nc * 8); c->mh = take(nc * 8);
+    c->b = take(nc * 8); c->mh = take(nc * 8); c->pprev = take(nc * 8);
     cudaError_t e = cudaMemset(c->fmem, 0, bytes);
     if (e == cudaSuccess) e = mg_alloc(c->mg, g.nx, g.ny, g.h);
     if (e == cudaSuccess && g.axisym) {
@@ -787,7 +789,7 @@ ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, doubl
 
 ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
 {
-    if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 2) return IB_EINVAL;
+    if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 3) return IB_EINVAL;
     if (warm == 2 && c->cfg.axisym)
         return fail(c, IB_EINVAL, "the network warm start is trained for the planar equation");
     if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % (4 << c->cnn->coarsen) != 0))
@@ -808,6 +810,15 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
         if (warm == 2) {
             cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
             if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
+        }
+        if (warm == 3) {
+            // p0 = 2 p^n - p^(n-1) once two pressures are known, else p^n
+            const long n = (long)g.nx * g.ny;
+            if (c->have_pprev) launch_extrapolate(n, c->p, c->pprev, c->s);
+            else cudaMemcpyAsync(c->pprev, c->p, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->s);
+            c->have_pprev = true;
+        } else {
+            c->have_pprev = false;
         }
         st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                     &c->last_cycles, &c->last_relres, c->s, c->err);

@@ -301,6 +301,17 @@ __global__ void k_shift_clip(long n, const double *__restrict__ sol, const doubl
     if (k < n) I[k] = fmin(fmax(sol[k] - *ref, 0.0), 1.0);
 }
 
+// Initial guess of the pressure solve extrapolated in time: p <- 2 p - q,
+// q <- the old p (p^n and p^(n-1) in, p0 = 2 p^n - p^(n-1) and p^n out).
+__global__ void k_extrapolate(long n, double *__restrict__ p, double *__restrict__ q)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double t = p[k];
+    p[k] = 2.0 * t - q[k];
+    q[k] = t;
+}
+
 __global__ void k_fill(long n, double a, double *__restrict__ y)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,6 +360,12 @@ void launch_indicator_finish(int nx, int ny, int axisym, const double *sol, doub
     const long n = (long)nx * ny;
     note_launch();
     k_shift_clip<<<cdiv(n, kT), kT, 0, s>>>(n, sol, ref, I);
+}
+
+void launch_extrapolate(long n, double *p, double *q, cudaStream_t s)
+{
+    note_launch();
+    k_extrapolate<<<cdiv(n, kT), kT, 0, s>>>(n, p, q);
 }
 
 void launch_fill(long n, double a, double *y, cudaStream_t s)

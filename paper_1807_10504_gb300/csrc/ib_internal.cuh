@@ -79,6 +79,7 @@ void launch_cn_solve(int nx, int ny, double h, double dt, const double *rho, con
                      const double *ve, double *us, double *vs, cudaStream_t s);
 void launch_scale(long n, double a, const double *x, double *y, cudaStream_t s);
 void launch_fill(long n, double a, double *y, cudaStream_t s);
+void launch_extrapolate(long n, double *p, double *q, cudaStream_t s);
 // Indicator function (Section 2.2 Eq. (ind_psn)): right-hand side div G, the
 // unit (or r-weighted) coefficients, and the shift to zero along the walls
 // with clipping to [0, 1].

@@ -140,3 +140,27 @@ def test_oscillating_drop_precisions_and_period(T, ib):
     t_half = -b / (2 * a)
     T2 = 2 * np.pi * np.sqrt((1.0 + 1e-3) * 0.2 ** 3 / (6 * 1.0))
     assert abs(2 * t_half - T2) <= 0.05 * T2, (2 * t_half, T2)
+
+
+def test_extrapolated_warm_start_reaches_the_same_solution(T, ib):
+    # warm = 3 starts each pressure solve from 2 p^n - p^(n-1): the solution
+    # after each step is the one from the previous-pressure start (same
+    # tolerance) and no more V-cycles are needed.
+    import numpy as np
+    n, h = 128, 1 / 128
+    mk = W.oscillating_drop(n_markers=256)
+    dt = W.capillary_dt(h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    out = {}
+    for warm in (1, 3):
+        cfg = ib.Config(nx=n, ny=n, h=h, precision=2, tol=1e-11, spread=1, relocate_every=10)
+        ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+        cyc = []
+        for _ in range(30):
+            c, rr = ctx.ns_step(dt, 1, warm)
+            assert rr <= 1e-11
+            cyc.append(c)
+        out[warm] = (ctx.get_host("p"), ctx.get_host("u"), sum(cyc[5:]))
+        ctx.close()
+    p1, p3 = out[1][0], out[3][0]
+    assert np.abs(p1 - p3).max() <= 1e-7 * np.abs(p1).max()
+    assert out[3][2] <= out[1][2]
