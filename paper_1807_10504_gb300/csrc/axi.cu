@@ -283,17 +283,32 @@ __global__ void k_axi_zbc(int nx, int ny, const double *__restrict__ frame, doub
 //   int int r dA = sum (z2 - z1)(r1^2 + r1 r2 + r2^2) / 6,
 //   int int r z dA = sum (z2 - z1)(r1^2 (3 z1 + z2) + 2 r1 r2 (z1 + z2)
 //                                  + r2^2 (z1 + 3 z2)) / 24,
-// summed edge by edge in marker order (the axis edge adds nothing).
+// (the axis edge adds nothing).  One block of kFrT threads: thread t sums
+// edges t, t + kFrT, ... and the partial sums meet in a fixed tree, so the
+// result is the same on every run; the constant factors are applied once.
+constexpr int kFrT = 256;
 __device__ double drop_zc(const double *X, const double *Y, int s, int n)
 {
+    __shared__ double a1[kFrT], a2[kFrT];
     double I1 = 0.0, I2 = 0.0;
-    for (int k = 0; k < n / 2; k++) {
+    for (int k = threadIdx.x; k < n / 2; k += kFrT) {
         const double r1 = X[s + k], z1 = Y[s + k], r2 = X[s + k + 1], z2 = Y[s + k + 1];
-        I1 += (z2 - z1) * (r1 * r1 + r1 * r2 + r2 * r2) / 6.0;
+        I1 += (z2 - z1) * (r1 * r1 + r1 * r2 + r2 * r2);
         I2 += (z2 - z1) * (r1 * r1 * (3.0 * z1 + z2) + 2.0 * r1 * r2 * (z1 + z2) +
-                           r2 * r2 * (z1 + 3.0 * z2)) / 24.0;
+                           r2 * r2 * (z1 + 3.0 * z2));
     }
-    return I1 != 0.0 ? I2 / I1 : 0.0;
+    a1[threadIdx.x] = I1;
+    a2[threadIdx.x] = I2;
+    __syncthreads();
+    for (int o = kFrT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            a1[threadIdx.x] += a1[threadIdx.x + o];
+            a2[threadIdx.x] += a2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const double J1 = a1[0] / 6.0, J2 = a2[0] / 24.0;
+    return J1 != 0.0 ? J2 / J1 : 0.0;
 }
 
 // Non-inertial frame following drop 0 (Section 2.4 Eqs. (fictitious),
@@ -302,14 +317,15 @@ __device__ double drop_zc(const double *X, const double *Y, int s, int n)
 // Vf changes by -S dt and the next step's S = (c1 (COM_o - COM_n) -
 // c2 (COM_n - COM_(n-1))) / dt^2; the ambient fluid at rest in the
 // laboratory streams past the frame with wb = -Vf.  init: COM_o = COM_(n-1)
-// = the current centre, S = Vf = wb = 0.  One thread.
-__global__ void k_axi_frame(const double *__restrict__ X, const double *__restrict__ Y,
-                            const int32_t *__restrict__ drop_start, double dt, double c1,
-                            double c2, int init, double *__restrict__ frame)
+// = the current centre, S = Vf = wb = 0.  One block.
+__global__ void __launch_bounds__(kFrT)
+k_axi_frame(const double *__restrict__ X, const double *__restrict__ Y,
+            const int32_t *__restrict__ drop_start, double dt, double c1, double c2, int init,
+            double *__restrict__ frame)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int s = drop_start[0], n = drop_start[1] - s;
     const double com = drop_zc(X, Y, s, n);
+    if (threadIdx.x != 0) return;
     if (init) {
         frame[kFrCom0] = com; frame[kFrComPrev] = com; frame[kFrCom] = com;
         frame[kFrS] = 0.0; frame[kFrVf] = 0.0; frame[kFrWb] = 0.0;
@@ -348,7 +364,7 @@ void launch_axi_frame(const Markers &mk, double dt, double c1, double c2, int in
                       cudaStream_t s)
 {
     note_launch();
-    k_axi_frame<<<1, 32, 0, s>>>(mk.X, mk.Y, mk.drop_start, dt, c1, c2, init, frame);
+    k_axi_frame<<<1, kFrT, 0, s>>>(mk.X, mk.Y, mk.drop_start, dt, c1, c2, init, frame);
 }
 
 void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,

@@ -650,26 +650,27 @@ __global__ void __launch_bounds__(1024) k_level_coeffs_small(LevelCoeffArgs a)
 
 // ------------------------------------------------------------ coarsest solve
 // Dense A' = A + s 1 1^T (s = A_00, removes the constant null space), then its
-// inverse by Gauss-Jordan elimination with partial pivoting (first maximal
-// |pivot|), stored transposed (Ainv^T) so that the per-cycle solve x = A'^-1 r
-// is one coalesced matrix-vector product.  One CTA; A and the inverse live in
-// shared memory when 2 n^2 doubles fit in 96 KB, else in the scratch `A`.
+// inverse, stored transposed (Ainv^T) so that the per-cycle solve x = A'^-1 r
+// is one coalesced matrix-vector product.  A is negative semi-definite with
+// the constants as null space and s < 0, so A' is negative definite and
+// Gauss-Jordan elimination needs no pivoting: in place, column by column,
+// row c is scaled by 1 / A'_cc and eliminated from every other row, the
+// eliminated column becoming the inverse's (n^3 multiply-adds, all on one
+// SM's FP64 pipe: the size of the coarsest level decides its cost).  One
+// CTA; A' lives in shared memory when n^2 + n doubles fit in 96 KB, else in
+// the scratch `Ag`.
 __global__ void __launch_bounds__(1024)
 k_coarse_inv(int nx, int ny, double h, const double *__restrict__ bx,
              const double *__restrict__ by, double *__restrict__ Ag, double *__restrict__ AinvT,
              int in_smem)
 {
     extern __shared__ __align__(16) double cinv_sm[];
+    __shared__ double colc[kMaxCoarsest];
+    __shared__ double invp;
     const int n = nx * ny;
     const double hh = h * h;
-    // A and X (identity, then the inverse, row-major) in shared memory when
-    // they fit, else in the global scratch
     double *A = in_smem ? cinv_sm : Ag;
-    double *X = in_smem ? cinv_sm + (size_t)n * n : AinvT;
-    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
-        A[k] = 0.0;
-        X[k] = (k / n == k % n) ? 1.0 : 0.0;
-    }
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.0;
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         int i = c % nx, j = c / nx;
@@ -687,60 +688,27 @@ k_coarse_inv(int nx, int ny, double h, const double *__restrict__ bx,
     __syncthreads();
     for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] += s0;
     __syncthreads();
-    __shared__ int pr;
-    __shared__ double dpiv;
     for (int c = 0; c < n; c++) {
-        if (threadIdx.x < 32) {  // pivot: first row of maximal |A[r][c]|, r >= c (warp argmax)
-            int best = -1;
-            double bv = -1.0;
-            for (int r = c + threadIdx.x; r < n; r += 32) {
-                const double v = fabs(A[r * n + c]);
-                if (v > bv) { bv = v; best = r; }
-            }
-            for (int o = 16; o; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
-            }
-            if (threadIdx.x == 0) pr = best;
-        }
+        if (threadIdx.x == 0) invp = 1.0 / A[c * n + c];
         __syncthreads();
-        if (pr != c)
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double t = A[c * n + k]; A[c * n + k] = A[pr * n + k]; A[pr * n + k] = t;
-                t = X[c * n + k]; X[c * n + k] = X[pr * n + k]; X[pr * n + k] = t;
-            }
+        const double ip = invp;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) colc[r] = A[r * n + c];
         __syncthreads();
-        if (threadIdx.x == 0) dpiv = A[c * n + c];
+        // row c scaled (its pivot entry becomes 1 / pivot)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) A[c * n + k] = (k == c) ? ip : A[c * n + k] * ip;
         __syncthreads();
-        const double d = dpiv;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) { A[c * n + k] /= d; X[c * n + k] /= d; }
-        __syncthreads();
+        // every other row: subtract its column-c multiple of row c; the
+        // eliminated entry becomes -A'_rc / pivot
         for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
             const int r = k / n, q = k - r * n;
             if (r == c) continue;
-            const double f = A[r * n + c];
-            if (q != c) A[r * n + q] -= f * A[c * n + q];
-            X[r * n + q] -= f * X[c * n + q];
+            A[k] = (q == c) ? -colc[r] * ip : A[k] - colc[r] * A[c * n + q];
         }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x)
-            if (r != c) A[r * n + c] = 0.0;
         __syncthreads();
     }
-    // transposed inverse out (through A when X is the output array itself)
-    if (in_smem) {
-        for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
-            const int r = k / n, q = k - r * n;
-            AinvT[q * n + r] = X[k];
-        }
-    } else {
-        for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = X[k];
-        __syncthreads();
-        for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
-            const int r = k / n, q = k - r * n;
-            AinvT[q * n + r] = A[k];
-        }
+    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
+        const int r = k / n, q = k - r * n;
+        AinvT[q * n + r] = A[k];
     }
 }
 
@@ -1588,7 +1556,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
     Level &vc = mg.lv[L - 1];
     note_launch();
     const size_t nc2 = (size_t)vc.nx * vc.ny * vc.nx * vc.ny;
-    const size_t cbytes = 2 * nc2 * sizeof(double);
+    const size_t cbytes = nc2 * sizeof(double);
     const int in_smem = cbytes <= 96 * 1024;
     if (in_smem) raise_smem_limit((const void *)k_coarse_inv, (int)cbytes);
     k_coarse_inv<<<1, 1024, in_smem ? cbytes : 0, s>>>(vc.nx, vc.ny, vc.h, vc.d.bx, vc.d.by, mg.lu,
