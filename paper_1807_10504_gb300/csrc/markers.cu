@@ -357,26 +357,37 @@ __global__ void k_interp(int M, int kernel, int nx, int ny, double h, double x0,
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     double Xm = X[m], Ym = Y[m];
+    // the kernel is a product phi(dx) phi(dy): its 4 + 4 factors once per
+    // component (the same values the 4 x 4 products use)
+    double px[4], py[4];
     double sx = (Xm - x0) / h, sy = (Ym - y0) / h - 0.5;
     int i0 = (int)floor(sx) - 1, j0 = (int)floor(sy) - 1;
+    for (int a = 0; a < 4; a++) {
+        px[a] = phi(kernel, (double)(i0 + a) - sx);
+        py[a] = phi(kernel, (double)(j0 + a) - sy);
+    }
     double acc = 0.0;
     for (int b = 0; b < 4; b++)
         for (int a = 0; a < 4; a++) {
             int i = i0 + a, j = j0 + b;
             if (i < 0 || i > nx || j < 0 || j > ny - 1) continue;
-            acc += u[(long)j * (nx + 1) + i] * (phi(kernel, (double)i - sx) * phi(kernel, (double)j - sy));
+            acc += u[(long)j * (nx + 1) + i] * (px[a] * py[b]);
         }
     double Um = acc;
     sx = (Xm - x0) / h - 0.5;
     sy = (Ym - y0) / h;
     i0 = (int)floor(sx) - 1;
     j0 = (int)floor(sy) - 1;
+    for (int a = 0; a < 4; a++) {
+        px[a] = phi(kernel, (double)(i0 + a) - sx);
+        py[a] = phi(kernel, (double)(j0 + a) - sy);
+    }
     acc = 0.0;
     for (int b = 0; b < 4; b++)
         for (int a = 0; a < 4; a++) {
             int i = i0 + a, j = j0 + b;
             if (i < 0 || i > nx - 1 || j < 0 || j > ny) continue;
-            acc += v[(long)j * nx + i] * (phi(kernel, (double)i - sx) * phi(kernel, (double)j - sy));
+            acc += v[(long)j * nx + i] * (px[a] * py[b]);
         }
     double Vm = acc;
     if (U) U[m] = Um;
@@ -738,13 +749,44 @@ __device__ __forceinline__ CellLine cell_line(const double *l, double di, double
     return L;
 }
 
+// Comparisons and selections of doubles on their bit patterns, in integer
+// instructions: this part issues FP64 compares and min/max on its reduced
+// FP64 pipe.  A double's 64-bit key, flipped below zero, orders like the
+// number (finite values and infinities; -0 and +0 adjacent), so the maxima
+// and minima below select exactly what fmax / fmin would.
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool dpos(double x)  // x > 0
+{
+    return __double_as_longlong(x) > 0;
+}
+__device__ __forceinline__ bool dneg(double x)  // x < 0
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool dzero(double x)  // x == 0
+{
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) == 0;
+}
+// fmax(x, 0): x if it is positive (finite or +inf), else 0 (also for a NaN,
+// as fmax gives for the empty interval -inf - (-inf))
+__device__ __forceinline__ double dmax0(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return (b > 0 && b <= 0x7ff0000000000000LL) ? x : 0.0;
+}
+
 // Narrow [lo, hi] to the s with alpha + beta s >= 0 (rbeta = 1 / beta).
 __device__ __forceinline__ void narrow(double alpha, double beta, double rbeta, double &lo, double &hi)
 {
     const double q = -alpha * rbeta;
-    if (beta > 0.0) lo = fmax(lo, q);
-    else if (beta < 0.0) hi = fmin(hi, q);
-    else if (alpha < 0.0) hi = -INFINITY;
+    if (dpos(beta)) { if (dkey(q) > dkey(lo)) lo = q; }
+    else if (dneg(beta)) { if (dkey(q) < dkey(hi)) hi = q; }
+    else if (dneg(alpha)) hi = -INFINITY;
 }
 
 // Areas of the unit square cut by half-planes, by Green's theorem: area =
@@ -766,7 +808,7 @@ __device__ __forceinline__ void narrow(double alpha, double beta, double rbeta, 
 // traces the same boundary as that edge: its own piece is not counted.
 __device__ __forceinline__ bool on_edge(const CellLine &L)
 {
-    return (L.a == 0.0 && L.b < 0.0 && L.b - L.c == 0.0) || (L.b == 0.0 && L.a < 0.0 && L.a - L.c == 0.0);
+    return (dzero(L.a) && dneg(L.b) && dzero(L.b - L.c)) || (dzero(L.b) && dneg(L.a) && dzero(L.a - L.c));
 }
 
 // Interval of line L's own piece inside the unit square.
@@ -816,11 +858,11 @@ __device__ __forceinline__ void rail_cut(const CellLine *L, double r01, RailCut 
 // Area of the cell between the normal edges (no offset line).
 __device__ __forceinline__ double rail_area(const CellLine *L, const RailCut &rc)
 {
-    double acc = fmax(rc.Rhi - rc.Rlo, 0.0);
-    acc += fmax(rc.Thi - rc.Tlo, 0.0);
+    double acc = dmax0(rc.Rhi - rc.Rlo);
+    acc += dmax0(rc.Thi - rc.Tlo);
 #pragma unroll
     for (int j = 0; j < 2; j++)
-        if (rc.piece[j]) acc -= L[j].c * fmax(rc.Phi[j] - rc.Plo[j], 0.0);
+        if (rc.piece[j]) acc -= L[j].c * dmax0(rc.Phi[j] - rc.Plo[j]);
     return 0.5 * acc;
 }
 
@@ -831,23 +873,23 @@ __device__ __forceinline__ double rail_line_area(const CellLine *L, const RailCu
 {
     double lo = rc.Rlo, hi = rc.Rhi, acc;
     narrow(O.a - O.c, O.b, O.rb, lo, hi);
-    acc = fmax(hi - lo, 0.0);
+    acc = dmax0(hi - lo);
     lo = rc.Tlo; hi = rc.Thi;
     narrow(O.b - O.c, O.a, O.ra, lo, hi);
-    acc += fmax(hi - lo, 0.0);
+    acc += dmax0(hi - lo);
 #pragma unroll
     for (int j = 0; j < 2; j++) {
         if (!rc.piece[j]) continue;
         lo = rc.Plo[j]; hi = rc.Phi[j];
         cross_narrow(O, L[j], j == 0 ? -r0O : -r1O, lo, hi);  // D_Oj = -D_jO
-        acc -= L[j].c * fmax(hi - lo, 0.0);
+        acc -= L[j].c * dmax0(hi - lo);
     }
     if (!on_edge(O)) {
         square_piece(O, lo, hi);
 #pragma unroll
         for (int i = 0; i < 2; i++)
             if (L[i].on) cross_narrow(L[i], O, i == 0 ? r0O : r1O, lo, hi);
-        acc -= O.c * fmax(hi - lo, 0.0);
+        acc -= O.c * dmax0(hi - lo);
     }
     return 0.5 * acc;
 }
