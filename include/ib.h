@@ -42,7 +42,7 @@ typedef enum {
 } ib_status;
 
 typedef struct ib_config {
-    int32_t nx, ny;           /* cells; multigrid halves both while even and >= 8 */
+    int32_t nx, ny;           /* cells; multigrid halves both while even, down to <= 16 cells */
     double h, x0, y0;         /* cell size and lower-left corner */
     double rho_g, rho_l;      /* ambient (H = 0) and drop (H = 1) density */
     double mu_g, mu_l;        /* ambient and drop dynamic viscosity */
@@ -113,10 +113,11 @@ typedef struct ib_ctx ib_ctx;
  * Errors: IB_EINVAL (sizes, grid that cannot coarsen to <= 1024 coarsest
  * cells, more than 2^20 markers), IB_EMARKER, IB_ENOMEM, IB_ECUDA; on error
  * *out is NULL and nothing stays allocated.  Levels halve while both sides
- * are even and >= 8; the coarsest level's dense inverse is rebuilt with the
- * coefficients (every time step) at O(n^3) in one CTA, so grid sides with a
- * large odd factor (200 = 8 x 25 ends at 25 x 25: ~60 ms a step) are slow;
- * sides of the form 2^k times a small odd number coarsen to tens of cells. */
+ * are even and the level has more than 16 cells; the coarsest level's dense
+ * inverse is rebuilt with the coefficients (every time step) at O(n^3) in
+ * one CTA, so grid sides with a large odd factor (200 = 8 x 25 ends at
+ * 25 x 25: tens of ms a step) are slow; sides of the form 2^k times a small
+ * odd number coarsen to a few cells.                                        */
 ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X,
                   const double *Y, const int32_t *drop_start, int32_t ndrops,
                   void *stream);

@@ -176,7 +176,7 @@ int or_mg_levels(int nx, int ny, int *nxs, int *nys, int maxlev)
 {
     int L = 0;
     nxs[L] = nx; nys[L] = ny; L++;
-    while (L < maxlev && nx % 2 == 0 && ny % 2 == 0 && nx >= 8 && ny >= 8) {
+    while (L < maxlev && nx % 2 == 0 && ny % 2 == 0 && nx * ny > 16) {
         nx /= 2; ny /= 2;
         nxs[L] = nx; nys[L] = ny; L++;
     }

@@ -393,11 +393,11 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
     cudaEventRecord(c->ev_join, c->s2);
     if (g.axisym)
         launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
-                             0.0, g.gy, g.frame ? c->frame : nullptr, c->us, c->vs, c->au, c->av,
-                             c->s);
+                             0.0, g.gy, g.frame ? c->frame : nullptr, c->bx, c->by, c->us, c->vs,
+                             c->au, c->av, c->s);
     else
         launch_predictor(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
-                         g.gx, g.gy, c->us, c->vs, c->au, c->av, c->s);
+                         g.gx, g.gy, c->bx, c->by, c->us, c->vs, c->au, c->av, c->s);
     if (g.viscous) {
         cudaMemcpyAsync(c->ue, c->us, (size_t)(g.nx + 1) * g.ny * 8, cudaMemcpyDeviceToDevice, c->s);
         cudaMemcpyAsync(c->ve, c->vs, (size_t)g.nx * (g.ny + 1) * 8, cudaMemcpyDeviceToDevice, c->s);
@@ -1199,7 +1199,8 @@ ib_status ib_op_predictor(int32_t nx, int32_t ny, double h, double dt, const dou
 {
     OPCHK(nx > 0 && ny > 0 && h > 0 && rho && mu && u && v && us && vs && au && av);
     OPCHK(!have_prev || (au_prev && av_prev));
-    launch_predictor(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx, gy, us, vs,
+    launch_predictor(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx, gy, nullptr,
+                     nullptr, us, vs,
                      au, av, (cudaStream_t)stream);
     return op_done();
 }
@@ -1213,7 +1214,7 @@ ib_status ib_op_predictor_axi(int32_t nx, int32_t ny, double h, double dt, const
     OPCHK(nx > 0 && ny > 0 && h > 0 && rho && mu && u && v && us && vs && au && av);
     OPCHK(!have_prev || (au_prev && av_prev));
     launch_predictor_axi(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, 0.0, gy, frame,
-                         us, vs, au, av, (cudaStream_t)stream);
+                         nullptr, nullptr, us, vs, au, av, (cudaStream_t)stream);
     return op_done();
 }
 

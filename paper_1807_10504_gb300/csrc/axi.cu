@@ -39,7 +39,8 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
                 const double *__restrict__ mu, const double *__restrict__ u,
                 const double *__restrict__ v, const double *__restrict__ aup,
                 const double *__restrict__ avp, int have_prev, double gx, double gy,
-                const double *__restrict__ frame, double *__restrict__ us,
+                const double *__restrict__ frame, const double *__restrict__ bx,
+                const double *__restrict__ by, double *__restrict__ us,
                 double *__restrict__ vs, double *__restrict__ au, double *__restrict__ av)
 {
     constexpr int W = PX + 2, Hh = PY + 2;
@@ -104,9 +105,10 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
             const double vis = (rE * sm[R][C] * (uE - uc) - rW * sm[R][C - 1] * (uc - uW) +
                                 r0 * muN * (uN - uc) - r0 * muS * (uc - uS)) / (r0 * h2) -
                                muf * uc / (r0 * r0);
-            const double rf = 0.5 * (sr[R][C - 1] + sr[R][C]);
+            // 1 / rho_face: the plain face coefficient beta when given
+            const double irf = bx ? bx[k] : 1.0 / (0.5 * (sr[R][C - 1] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
-            us[k] = uc + dt * ((vis - ae) / rf + gx);
+            us[k] = uc + dt * ((vis - ae) * irf + gx);
             au[k] = adv;
         }
         if (i == nx - 1) { us[k + 1] = 0.0; au[k + 1] = 0.0; }
@@ -131,9 +133,9 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
             const double adv = ((fN - fS) + (gE - gW)) / (r0 * h);
             const double vis = (r0 * sm[R][C] * (vN - vc) - r0 * sm[R - 1][C] * (vc - vS) +
                                 rE * muE * (vE - vc) - rW * muW * (vc - vW)) / (r0 * h2);
-            const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
+            const double irf = by ? by[k] : 1.0 / (0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
-            vs[k] = vc + dt * ((vis - ae) / rf + gz);
+            vs[k] = vc + dt * ((vis - ae) * irf + gz);
             av[k] = adv;
         }
         if (j == ny - 1) { vs[k + nx] = wb; av[k + nx] = 0.0; }
@@ -345,13 +347,14 @@ k_axi_frame(const double *__restrict__ X, const double *__restrict__ Y,
 void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                           const double *mu, const double *u, const double *v,
                           const double *au_prev, const double *av_prev, int have_prev,
-                          double gx, double gy, const double *frame, double *us, double *vs,
-                          double *au, double *av, cudaStream_t s)
+                          double gx, double gy, const double *frame, const double *bx,
+                          const double *by, double *us, double *vs, double *au, double *av,
+                          cudaStream_t s)
 {
     dim3 g(cdiv(nx, PX), cdiv(ny, PY)), b(PX, PY);
     note_launch();
     k_predictor_axi<<<g, b, 0, s>>>(nx, ny, h, dt, rho, mu, u, v, au_prev, av_prev, have_prev, gx,
-                                    gy, frame, us, vs, au, av);
+                                    gy, frame, bx, by, us, vs, au, av);
 }
 
 void launch_axi_zbc(int nx, int ny, const double *frame, double *v, cudaStream_t s)

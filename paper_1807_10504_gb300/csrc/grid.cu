@@ -94,7 +94,8 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
             const double *__restrict__ rho, const double *__restrict__ mu,
             const double *__restrict__ u, const double *__restrict__ v,
             const double *__restrict__ aup, const double *__restrict__ avp,
-            int have_prev, double gx, double gy, double *__restrict__ us,
+            int have_prev, double gx, double gy, const double *__restrict__ bx,
+            const double *__restrict__ by, double *__restrict__ us,
             double *__restrict__ vs, double *__restrict__ au, double *__restrict__ av)
 {
     constexpr int W = PX + 2, Hh = PY + 2;  // staged window: cells / faces i0-1 .. i0+PX
@@ -156,9 +157,11 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
             const double adv = (fE - fW) * ih + (gN - gS) * ih;
             const double vis = (sm[R][C] * (uE - uc) - sm[R][C - 1] * (uc - uW) + muN * (uN - uc) -
                                 muS * (uc - uS)) * ih2;
-            const double rf = 0.5 * (sr[R][C - 1] + sr[R][C]);
+            // 1 / rho_face: the face coefficient beta when given (the same
+            // reciprocal of the same rho), else formed here
+            const double irf = bx ? bx[k] : recip_nr(0.5 * (sr[R][C - 1] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * aup[k] : adv;
-            us[k] = uc + dt * ((vis - ae) * recip_nr(rf) + gx);
+            us[k] = uc + dt * ((vis - ae) * irf + gx);
             au[k] = adv;
         }
         if (i == nx - 1) { us[k + 1] = 0.0; au[k + 1] = 0.0; }  // right wall face
@@ -181,9 +184,9 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
             const double adv = (fN - fS) * ih + (gE - gW) * ih;
             const double vis = (sm[R][C] * (vN - vc) - sm[R - 1][C] * (vc - vS) + muE * (vE - vc) -
                                 muW * (vc - vW)) * ih2;
-            const double rf = 0.5 * (sr[R - 1][C] + sr[R][C]);
+            const double irf = by ? by[k] : recip_nr(0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
-            vs[k] = vc + dt * ((vis - ae) * recip_nr(rf) + gy);
+            vs[k] = vc + dt * ((vis - ae) * irf + gy);
             av[k] = adv;
         }
         if (j == ny - 1) { vs[k + nx] = 0.0; av[k + nx] = 0.0; }  // top wall face
@@ -416,13 +419,14 @@ void launch_correct(int nx, int ny, double h, double dt, const double *us,
 void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       const double *mu, const double *u, const double *v,
                       const double *au_prev, const double *av_prev,
-                      int have_prev, double gx, double gy, double *us,
-                      double *vs, double *au, double *av, cudaStream_t s)
+                      int have_prev, double gx, double gy, const double *bx,
+                      const double *by, double *us, double *vs, double *au, double *av,
+                      cudaStream_t s)
 {
     dim3 g(cdiv(nx, PX), cdiv(ny, PY)), b(PX, PY);
     note_launch();
     k_predictor<<<g, b, 0, s>>>(nx, ny, 1.0 / h, 1.0 / (h * h), dt, rho, mu, u, v, au_prev,
-                                av_prev, have_prev, gx, gy, us, vs, au, av);
+                                av_prev, have_prev, gx, gy, bx, by, us, vs, au, av);
 }
 
 }  // namespace ibk

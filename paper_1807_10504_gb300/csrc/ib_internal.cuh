@@ -65,11 +65,14 @@ void launch_correct(int nx, int ny, double h, double dt, const double *us,
                     const double *vs, const double *p, const double *Fx,
                     const double *Fy, const double *bx, const double *by,
                     double *u, double *v, cudaStream_t s);
+// bx, by: the face coefficients 1 / rho_face of the same rho (k_face_beta),
+// or NULL to form the reciprocals in the kernel
 void launch_predictor(int nx, int ny, double h, double dt, const double *rho,
                       const double *mu, const double *u, const double *v,
                       const double *au_prev, const double *av_prev,
-                      int have_prev, double gx, double gy, double *us,
-                      double *vs, double *au, double *av, cudaStream_t s);
+                      int have_prev, double gx, double gy, const double *bx,
+                      const double *by, double *us, double *vs, double *au, double *av,
+                      cudaStream_t s);
 
 // Crank-Nicolson viscous solve: nsweeps red-black sweeps of
 // u* - dt / (2 rho_f) D(u*) = u_e on both components; (us, vs) hold the
@@ -97,8 +100,9 @@ enum FrameSlot { kFrCom0 = 0, kFrComPrev = 1, kFrCom = 2, kFrS = 3, kFrVf = 4, k
 void launch_predictor_axi(int nx, int ny, double h, double dt, const double *rho,
                           const double *mu, const double *u, const double *v,
                           const double *au_prev, const double *av_prev, int have_prev,
-                          double gx, double gy, const double *frame, double *us, double *vs,
-                          double *au, double *av, cudaStream_t s);
+                          double gx, double gy, const double *frame, const double *bx,
+                          const double *by, double *us, double *vs, double *au, double *av,
+                          cudaStream_t s);
 void launch_axi_zbc(int nx, int ny, const double *frame, double *v, cudaStream_t s);
 void launch_rhs_axi(int nx, int ny, double h, double dt, const double *us, const double *vs,
                     const double *Fx, const double *Fy, const double *bx, const double *by,

@@ -1315,7 +1315,7 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys)
 {
     nxs.assign(1, nx);
     nys.assign(1, ny);
-    while ((int)nxs.size() < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && nx >= 8 && ny >= 8) {
+    while ((int)nxs.size() < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && (long)nx * ny > 16) {
         nx /= 2; ny /= 2;
         nxs.push_back(nx); nys.push_back(ny);
     }
@@ -1375,7 +1375,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
 {
     int nxs[16], nys[16], L = 0;
     nxs[0] = nx; nys[0] = ny; L = 1;
-    while (L < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && nx >= 8 && ny >= 8) {
+    while (L < kMaxLv && nx % 2 == 0 && ny % 2 == 0 && (long)nx * ny > 16) {
         nx /= 2; ny /= 2;
         nxs[L] = nx; nys[L] = ny; L++;
     }

@@ -155,9 +155,12 @@ def test_mg_status_codes(O):
 
 
 def test_mg_levels_rule(O):
+    # halve while both sides are even and the level has more than 16 cells
     assert O.mg_levels(64, 64) == [(64, 64), (32, 32), (16, 16), (8, 8), (4, 4)]
-    assert O.mg_levels(256, 1024)[-1] == (4, 16)
-    assert O.mg_levels(12, 12) == [(12, 12), (6, 6)]
+    assert O.mg_levels(256, 1024)[-1] == (2, 8)
+    assert O.mg_levels(12, 12) == [(12, 12), (6, 6), (3, 3)]
+    assert O.mg_levels(20, 12) == [(20, 12), (10, 6), (5, 3)]
+    assert O.mg_levels(16, 2) == [(16, 2), (8, 1)] and O.mg_levels(8, 2) == [(8, 2)]
 
 
 def test_two_inner_cycles_per_fp64_residual(O):
