@@ -53,8 +53,8 @@ struct ib_ctx {
     void *imem = nullptr;
     // side stream of a step: the multigrid hierarchy is built there while the
     // predictor, spreading and right-hand side run on s
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t s2 = nullptr, s3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     // recorded step phases (see run_recorded) and their capture stream
     std::vector<StepGraph> sgraphs;
     cudaStream_t cap = nullptr;
@@ -382,15 +382,18 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
         launch_scale((long)g.nx * g.ny, 0.5, c->mu, c->mh, c->s);
         mup = c->mh;
     }
-    // on the side stream, overlapping the predictor: the hierarchy of the
+    // on two side streams, overlapping the predictor: the hierarchy of the
     // pressure coefficients (the r-weighted operator r_face beta in
-    // axisymmetric form), then the face force, which depends on neither
+    // axisymmetric form), and the face force; neither depends on the other
+    // or on the predictor
     if (g.axisym) launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
     cudaEventRecord(c->ev_fork, c->s);
     cudaStreamWaitEvent(c->s2, c->ev_fork, 0);
+    cudaStreamWaitEvent(c->s3, c->ev_fork, 0);
     mg_build(c->mg, g.axisym ? c->bxa : c->bx, g.axisym ? c->bya : c->by, c->s2);
-    force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s2);
     cudaEventRecord(c->ev_join, c->s2);
+    force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s3);
+    cudaEventRecord(c->ev_join3, c->s3);
     if (g.axisym)
         launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
                              0.0, g.gy, g.frame ? c->frame : nullptr, c->bx, c->by, c->us, c->vs,
@@ -405,7 +408,8 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
                         g.cn_sweeps, c->ue, c->ve, c->us, c->vs, c->s);
     }
     c->mg_ready = true;
-    cudaStreamWaitEvent(c->s, c->ev_join, 0);  // the hierarchy and the force are complete
+    cudaStreamWaitEvent(c->s, c->ev_join, 0);   // the hierarchy is complete
+    cudaStreamWaitEvent(c->s, c->ev_join3, 0);  // and the force
     if (g.axisym)
         launch_rhs_axi(g.nx, g.ny, g.h, dt, c->us, c->vs, c->Fx, c->Fy, c->bx, c->by, c->b, c->s);
     else
@@ -502,7 +506,9 @@ void ib_destroy(ib_ctx *c)
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->s2) cudaStreamDestroy(c->s2);
+    if (c->s3) cudaStreamDestroy(c->s3);
     if (c->flags_host) cudaFreeHost(c->flags_host);
     delete c;
 }
@@ -610,10 +616,12 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
         e = cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->s3, cudaStreamNonBlocking, hi);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
         c->A0 = (double *)c->dmem;
