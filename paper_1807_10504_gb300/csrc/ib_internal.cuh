@@ -36,6 +36,15 @@ __device__ __forceinline__ double recip_nr(double x)
     return fma(r, e, r);
 }
 
+// 1/x for any nonzero finite x of either sign (0 for x = 0): recip_nr where
+// |x| lies well inside the FP32 normal range, the FP64 division elsewhere.
+__device__ __forceinline__ double recip_any(double x)
+{
+    const double a = fabs(x);
+    if (x == 0.0) return 0.0;
+    return (a > 1e-30 && a < 1e30) ? recip_nr(x) : 1.0 / x;
+}
+
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (one
 // host call the first time a larger value is needed, none afterwards, so
 // that launches recorded into a CUDA graph make no such call).

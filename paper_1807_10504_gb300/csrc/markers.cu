@@ -102,7 +102,7 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
 __device__ __forceinline__ void left_of(double px, double py, double qx, double qy, double *l)
 {
     const double dx = qx - px, dy = qy - py, len = sqrt(dx * dx + dy * dy);
-    const double il = len > 0.0 ? 1.0 / len : 0.0;
+    const double il = recip_any(len);
     const double nx_ = -dy * il, ny_ = dx * il;
     l[0] = nx_; l[1] = ny_; l[2] = nx_ * px + ny_ * py;
 }
@@ -126,7 +126,7 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     const double gxa = gx[m], gya = gy[m], gxb = gx[nm], gyb = gy[nm];
     {
         const double ex = gxb - gxa, ey = gyb - gya;  // 1 / |segment|^2 (grid units)
-        sinv[m] = 1.0 / (ex * ex + ey * ey);
+        sinv[m] = recip_any(ex * ex + ey * ey);
     }
     const double nax = nxm[m], nay = nym[m], nbx = nxm[nm], nby = nym[nm];
     // corner o (offset o - 2.5 cells) on the normal at m: (2o, 2o+1); at next m: 12 + (2o, 2o+1)
@@ -164,7 +164,7 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     // each offset line, which the per-cell area formula would otherwise
     // recompute for every cell the segment meets.
     double *d = sl + (long)m * kSegLine;
-    auto rcp = [](double v) { return v != 0.0 ? 1.0 / v : 0.0; };
+    auto rcp = [](double v) { return recip_any(v); };
     for (int q = 0; q < 8; q++) {
         d[5 * q + 0] = L[q][0]; d[5 * q + 1] = L[q][1]; d[5 * q + 2] = L[q][2];
         d[5 * q + 3] = rcp(L[q][0]); d[5 * q + 4] = rcp(L[q][1]);
