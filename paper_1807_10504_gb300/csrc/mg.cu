@@ -293,28 +293,9 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         return (9.0f * c00 + 3.0f * c10 + 3.0f * c01 + c11) * 0.0625f;
     };
     auto pro = [&](int gi, int gj) { return pin[(long)gj * nx + gi] + cor(gi, gj); };
-    if constexpr (TMA) {
-        // tensor copies land on 128-byte boundaries (checked, not assumed)
-        if (((smem_addr(&ps[0][0]) | smem_addr(&bs[0][0]) | smem_addr(&ds[0][0]) |
-              smem_addr(&ys[0][0])) & 127u) != 0) {
-            if (threadIdx.x == 0) *tm.fault = 2;
-            return;
-        }
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)));
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-        }
-        __syncthreads();  // the barrier is initialised before any thread waits on it
-        if (threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::);
-            constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                         ::"r"(smem_addr(&bar)), "r"(kBytes));
-            tma_load2(&ps[0][0], &tm.p, gi0, gj0, &bar);
-            tma_load2(&bs[0][0], &tm.b, gi0, gj0, &bar);
-            tma_load2(&ds[0][0], &tm.d, gi0, gj0, &bar);
-            tma_load2(&ys[0][0], &tm.y, gi0, gj0, &bar);
-        }
+    // x-faces of the window rows by asynchronous copies: 16-byte copies of
+    // whole in-range chunks, single faces (zero beyond the walls) at the ends
+    auto load_xfaces = [&]() {
         constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per x-face row, worst alignment
         const long nbx = nxf * ny;
         for (int k = threadIdx.x; k < PH * NC; k += FT) {
@@ -338,6 +319,30 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
                 }
             }
         }
+    };
+    if constexpr (TMA) {
+        // tensor copies land on 128-byte boundaries (checked, not assumed)
+        if (((smem_addr(&ps[0][0]) | smem_addr(&bs[0][0]) | smem_addr(&ds[0][0]) |
+              smem_addr(&ys[0][0])) & 127u) != 0) {
+            if (threadIdx.x == 0) *tm.fault = 2;
+            return;
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)));
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        }
+        __syncthreads();  // the barrier is initialised before any thread waits on it
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::);
+            constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                         ::"r"(smem_addr(&bar)), "r"(kBytes));
+            tma_load2(&ps[0][0], &tm.p, gi0, gj0, &bar);
+            tma_load2(&bs[0][0], &tm.b, gi0, gj0, &bar);
+            tma_load2(&ds[0][0], &tm.d, gi0, gj0, &bar);
+            tma_load2(&ys[0][0], &tm.y, gi0, gj0, &bar);
+        }
+        load_xfaces();
         // the prolongation of the coarse correction overlaps the copies
         constexpr int NPRO = MODE == 2 ? (PH * PW + FT - 1) / FT : 1;
         float pc[NPRO];
@@ -364,14 +369,18 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         }
         __syncthreads();
     } else {
-        const bool vec = (nx & 3) == 0 && gi0 >= 0 && gi0 + PW <= nx;
+        // rows of a multiple of 4 cells: every 4-cell chunk of the window
+        // (gi0 and the window width are multiples of 4) lies wholly inside or
+        // wholly outside the grid
+        const bool vec = (nx & 3) == 0;
         if (vec) {
             constexpr int V = PW / 4;  // float4 per row
             for (int k = threadIdx.x; k < (PH + 1) * V; k += FT) {
-                const int r = k / V, c4 = k - r * V, gj = gj0 + r;
-                const long o = (long)gj * nx + gi0 + 4 * c4;
+                const int r = k / V, c4 = k - r * V, gj = gj0 + r, gc = gi0 + 4 * c4;
+                const bool inx = gc >= 0 && gc + 4 <= nx;
+                const long o = (long)gj * nx + gc;
                 if (r < PH) {
-                    const bool in = gj >= 0 && gj < ny;
+                    const bool in = inx && gj >= 0 && gj < ny;
                     if (MODE == 2) {
                         for (int q = 0; q < 4; q++) ps[r][4 * c4 + q] = in ? pro(gi0 + 4 * c4 + q, gj) : 0.0f;
                     } else {
@@ -380,7 +389,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
                     cp_async16(&bs[r][4 * c4], in ? b + o : b, in);
                     cp_async16(&ds[r][4 * c4], in ? invd + o : invd, in);
                 }
-                const bool iny = gj >= 0 && gj <= ny;
+                const bool iny = inx && gj >= 0 && gj <= ny;
                 cp_async16(&ys[r][4 * c4], iny ? by + o : by, iny);
             }
         } else {
@@ -397,24 +406,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             }
         }
         if (vec) {
-            constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per row, worst alignment
-            const long nbx = nxf * ny;
-            for (int k = threadIdx.x; k < PH * NC; k += FT) {
-                const int r = k / NC, q = k - r * NC, gj = gj0 + r;
-                if (gj < 0 || gj >= ny) {
-                    cp_async16(&xs[r][4 * q], bx, false);
-                    if (q == 0) xoff[r] = 0;
-                    continue;
-                }
-                const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
-                if (q == 0) xoff[r] = (int)(start - a0);
-                const long e0 = a0 + 4 * q;
-                if (e0 + 4 <= nbx) {
-                    cp_async16(&xs[r][4 * q], bx + e0, true);
-                } else {
-                    for (int t = 0; t < 4; t++) cp_async4(&xs[r][4 * q + t], bx + (e0 + t < nbx ? e0 + t : 0), e0 + t < nbx);
-                }
-            }
+            load_xfaces();
         } else {
             for (int k = threadIdx.x; k < PH * (PW + 1); k += FT) {
                 const int r = k / (PW + 1), c = k - r * (PW + 1), gi = gi0 + c, gj = gj0 + r;
@@ -723,17 +715,51 @@ struct TailArgs {
     const T *bx[kMaxLv], *by[kMaxLv], *invd[kMaxLv];
     const double *ainvT;   // coarsest inverse, transposed
     int nu1, nu2;
+    // shared-memory layout (tail_prepare): element offset of each level's
+    // arrays, byte offset of the coarsest inverse (-1: read from ainvT)
+    int off[kMaxLv];
+    int inv_off;
 };
 
+// Shared-memory layout of the tail levels.  A level above the coarsest (even
+// nx, ny) is split by colour: cell (i, j) of colour c = (i + j) & 1 sits at
+// slot j * nx/2 + i/2 of colour c's block, and block c starts at
+// c * (n/2 + kTailPad).  A colour phase then reads every array at
+// consecutive slots from consecutive threads, free of bank conflicts (row-
+// major storage would read every other word).  Each level holds e, r, 1/diag
+// and the beta of each cell's east and north face (the west and south faces
+// are the east and north faces of the neighbours, held by the other colour),
+// one array after the other.  The coarsest level (odd sizes allowed, solved
+// directly) keeps row-major e and r only.  The coarsest level's inverse
+// (FP64, 8-byte aligned) follows when it takes at most 64 KB; otherwise the
+// solve reads it from global memory.
+constexpr int kTailPad = 16;
+constexpr size_t kTailInvMax = 64 * 1024;
+__host__ __device__ inline size_t tail_level_elems(int nx, int ny, bool coarsest)
+{
+    const size_t n = (size_t)nx * ny;
+    return coarsest ? 2 * n : 5 * (n + 2 * kTailPad);
+}
+
+__host__ __device__ inline size_t tail_inv_bytes(int nco)
+{
+    const size_t b = (size_t)nco * nco * sizeof(double);
+    return b <= kTailInvMax ? b : 0;
+}
+
+// Fills a.off / a.inv_off; returns the dynamic shared memory of the launch.
 template <typename T>
-__host__ __device__ size_t tail_smem_elems(const TailArgs<T> &a)
+size_t tail_prepare(TailArgs<T> &a)
 {
     size_t n = 0;
     for (int l = a.lt; l < a.nl; l++) {
-        size_t c = (size_t)a.nx[l] * a.ny[l];
-        n += 3 * c + (size_t)(a.nx[l] + 1) * a.ny[l] + (size_t)a.nx[l] * (a.ny[l] + 1);
+        a.off[l] = (int)n;
+        n += tail_level_elems(a.nx[l], a.ny[l], l == a.nl - 1);
     }
-    return n;
+    const size_t lv = (n * sizeof(T) + 7) & ~(size_t)7;
+    const size_t inv = tail_inv_bytes(a.nx[a.nl - 1] * a.ny[a.nl - 1]);
+    a.inv_off = inv ? (int)lv : -1;
+    return lv + inv;
 }
 
 // One element (4 or 8 bytes) global -> shared by an asynchronous copy.
@@ -762,11 +788,19 @@ __device__ __forceinline__ void stage_array(T *d, const T *src, int n, int tid, 
     for (int k = done + tid; k < n; k += nthr) cp_async_elem(d + k, src + k);
 }
 
-// Shared-memory view of the tail levels (one copy per block).
+// A split level's arrays (pointers into the kernel's shared memory).
 template <typename T>
-struct TailView {
-    T *e[kMaxLv], *r[kMaxLv], *bx[kMaxLv], *by[kMaxLv], *iv[kMaxLv];
+struct TailLv {
+    T *e, *r, *iv, *cx, *cy;
 };
+
+template <typename T>
+__device__ __forceinline__ TailLv<T> tail_lv(const TailArgs<T> &g, T *sm, int l)
+{
+    const int s = g.nx[l] * g.ny[l] + 2 * kTailPad;
+    T *b = sm + g.off[l];
+    return {b, b + s, b + 2 * s, b + 3 * s, b + 4 * s};
+}
 
 // Work of one level by a group of NT threads (thread index t): the whole
 // block (NT = 1024), warps 0-3 (128, named barrier 1) or warp 0 (32), chosen
@@ -779,164 +813,323 @@ __device__ __forceinline__ void gsync()
     else __syncwarp();
 }
 
+// Walk of the slots q = t, t + NT, ... of a w-wide grid as (row, column)
+// without a division per step.
+struct Walk {
+    int a, b, da, db, w;
+    __device__ Walk(int t, int NT, int w_) : w(w_)
+    {
+        a = t / w; b = t - a * w; da = NT / w; db = NT - da * w;
+    }
+    __device__ void next()
+    {
+        a += da; b += db;
+        if (b >= w) { b -= w; a++; }
+    }
+};
+
+// Red-black Gauss-Seidel on a split level: colour phases first .. 2 nsw - 1
+// (phase 2s + c sweeps colour c of sweep s).  Same arithmetic, in the same
+// order, as the row-major update (beta_E p_E + beta_W p_W + beta_N p_N +
+// beta_S p_S - h^2 r) / diag, with p = 0 beyond the walls.
+// Two consecutive values of a row (8 or 16 bytes, aligned: nx is even).
+template <typename T> struct Pair;
+template <> struct Pair<float> { using V = float2; };
+template <> struct Pair<double> { using V = double2; };
+
+// One colour phase on a split level with nx a multiple of 4: each thread
+// updates the cells of slots m, m + 1 (m even) of one row with paired
+// shared-memory loads.  In row j the cells of colour c are i = 2m + o,
+// o = (j + c) & 1; their west / east neighbours are the other colour's slots
+// m - 1 + o and m + o of the same row.
 template <typename T, int NT>
-__device__ void tail_smooth(const TailArgs<T> &g, const TailView<T> &v, int l, int nsw, int t)
+__device__ __forceinline__ void tail_phase2(const TailArgs<T> &g, const TailLv<T> &v, int l, int c, int t)
 {
-    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, nh = hx * ny;  // nx even: nx / 2 per colour and row
-    const T *bx = v.bx[l], *by = v.by[l], *invd = v.iv[l], *r = v.r[l];
-    T *e = v.e[l];
+    using P2 = typename Pair<T>::V;
+    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, bl = hx * ny + kTailPad, hp = hx / 2;
+    const int oc = c * bl, ob = bl - oc;
     const T h2 = g.h2[l];
-    for (int s = 0; s < nsw; s++)
-        for (int color = 0; color < 2; color++) {
-            for (int q = t; q < nh; q += NT) {
-                const int j = q / hx, i = 2 * (q - j * hx) + ((j + color) & 1), k = j * nx + i;
-                const int kx = j * (nx + 1) + i;
-                const T pE = (i + 1 < nx) ? e[k + 1] : T(0), pW = (i > 0) ? e[k - 1] : T(0);
-                const T pN = (j + 1 < ny) ? e[k + nx] : T(0), pS = (j > 0) ? e[k - nx] : T(0);
-                T sm = bx[kx + 1] * pE;
-                sm = fma(bx[kx], pW, sm);
-                sm = fma(by[k + nx], pN, sm);
-                sm = fma(by[k], pS, sm);
-                e[k] = (sm - h2 * r[k]) * invd[k];
-            }
+    auto ld2 = [](const T *a, int k) { return *reinterpret_cast<const P2 *>(a + k); };
+    Walk w(t, NT, hp);
+    for (int q = t; q < hp * ny; q += NT, w.next()) {
+        const int j = w.a, m = 2 * w.b, o = (j + c) & 1, k = j * hx + m;
+        const P2 eo = ld2(v.e, ob + k), xo = ld2(v.cx, ob + k);
+        T pW0, pE0, pW1, pE1, bW0, bW1;
+        if (o == 0) {
+            pW0 = m > 0 ? v.e[ob + k - 1] : T(0);
+            bW0 = m > 0 ? v.cx[ob + k - 1] : T(0);
+            pE0 = eo.x; pW1 = eo.x; pE1 = eo.y; bW1 = xo.x;
+        } else {
+            pW0 = eo.x; pE0 = eo.y; pW1 = eo.y;
+            pE1 = m + 2 < hx ? v.e[ob + k + 2] : T(0);
+            bW0 = xo.x; bW1 = xo.y;
+        }
+        P2 eN, eS, yS;
+        if (j + 1 < ny) eN = ld2(v.e, ob + k + hx); else eN.x = eN.y = T(0);
+        if (j > 0) { eS = ld2(v.e, ob + k - hx); yS = ld2(v.cy, ob + k - hx); }
+        else { eS.x = eS.y = T(0); yS.x = yS.y = T(0); }
+        const P2 xc = ld2(v.cx, oc + k), yc = ld2(v.cy, oc + k), rc = ld2(v.r, oc + k), dc = ld2(v.iv, oc + k);
+        T s0 = xc.x * pE0;
+        s0 = fma(bW0, pW0, s0);
+        s0 = fma(yc.x, eN.x, s0);
+        s0 = fma(yS.x, eS.x, s0);
+        T s1 = xc.y * pE1;
+        s1 = fma(bW1, pW1, s1);
+        s1 = fma(yc.y, eN.y, s1);
+        s1 = fma(yS.y, eS.y, s1);
+        P2 out;
+        out.x = (s0 - h2 * rc.x) * dc.x;
+        out.y = (s1 - h2 * rc.y) * dc.y;
+        *reinterpret_cast<P2 *>(v.e + oc + k) = out;
+    }
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void tail_smooth(const TailArgs<T> &g, T *sm, int l, int nsw, int first, int t)
+{
+    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, nh = hx * ny, bl = nh + kTailPad;
+    const TailLv<T> v = tail_lv(g, sm, l);
+    const T h2 = g.h2[l];
+    if ((nx & 3) == 0) {
+        for (int ph = first; ph < 2 * nsw; ph++) {
+            tail_phase2<T, NT>(g, v, l, ph & 1, t);
             gsync<NT>();
         }
+        return;
+    }
+    for (int ph = first; ph < 2 * nsw; ph++) {
+        const int c = ph & 1, oc = c * bl, ob = bl - oc;
+        Walk w(t, NT, hx);
+        for (int q = t; q < nh; q += NT, w.next()) {
+            const int j = w.a, m = w.b, o = (j + c) & 1, i = 2 * m + o, k = j * hx + m;
+            const T pE = (i + 1 < nx) ? v.e[ob + k + o] : T(0);
+            const T pW = (i > 0) ? v.e[ob + k - 1 + o] : T(0);
+            const T bW = (i > 0) ? v.cx[ob + k - 1 + o] : T(0);
+            const T pN = (j + 1 < ny) ? v.e[ob + k + hx] : T(0);
+            const T pS = (j > 0) ? v.e[ob + k - hx] : T(0);
+            const T bS = (j > 0) ? v.cy[ob + k - hx] : T(0);
+            T s = v.cx[oc + k] * pE;
+            s = fma(bW, pW, s);
+            s = fma(v.cy[oc + k], pN, s);
+            s = fma(bS, pS, s);
+            v.e[oc + k] = (s - h2 * v.r[oc + k]) * v.iv[oc + k];
+        }
+        gsync<NT>();
+    }
 }
 
+// Coarse residual of a split level l: the average of the four children's
+// b - A p, with A p in the order E, W, N, S as flux_sum.  The coarse
+// correction starts at zero; with fold, the red cells of a split coarse level
+// get the result of the first red sweep from that zero start,
+// (0 - h_c^2 r_c) / diag_c, so its smoothing starts with the black phase.
 template <typename T, int NT>
-__device__ void tail_restrict(const TailArgs<T> &g, const TailView<T> &v, int l, int t)
+__device__ __forceinline__ void tail_restrict(const TailArgs<T> &g, T *sm, int l, int fold, int t)
 {
-    const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nc = nxc * (ny / 2);
-    const T *bx = v.bx[l], *by = v.by[l], *b = v.r[l], *p = v.e[l];
-    const T ih2 = g.ih2[l];
-    for (int k = t; k < nc; k += NT) {
-        const int J = k / nxc, I = k - J * nxc, i = 2 * I, j = 2 * J;
-        T r00 = b[j * nx + i] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
-        T r10 = b[j * nx + i + 1] - flux_sum(nx, ny, i + 1, j, bx, by, p) * ih2;
-        T r01 = b[(j + 1) * nx + i] - flux_sum(nx, ny, i, j + 1, bx, by, p) * ih2;
-        T r11 = b[(j + 1) * nx + i + 1] - flux_sum(nx, ny, i + 1, j + 1, bx, by, p) * ih2;
-        v.r[l + 1][k] = T(0.25) * (r00 + r10 + r01 + r11);
-        v.e[l + 1][k] = T(0);
+    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, bl = hx * ny + kTailPad;
+    const int nxc = nx / 2, nyc = ny / 2, nc = nxc * nyc;
+    const bool cnat = l + 1 == g.nl - 1;
+    const int hxc = nxc / 2, blc = nc / 2 + kTailPad;
+    const TailLv<T> v = tail_lv(g, sm, l);
+    const T ih2 = g.ih2[l], h2c = g.h2[l + 1];
+    T *ec = sm + g.off[l + 1];
+    T *rc = cnat ? ec + nc : ec + nc + 2 * kTailPad;
+    const T *ivc = ec + 2 * (nc + 2 * kTailPad);  // split coarse level only
+    auto res = [&](int i, int j) {
+        const int c = (i + j) & 1, oc = c * bl, ob = bl - oc, o = i & 1, k = j * hx + (i >> 1);
+        const T pc = v.e[oc + k];
+        const T pE = (i + 1 < nx) ? v.e[ob + k + o] : pc;
+        const T pW = (i > 0) ? v.e[ob + k - 1 + o] : pc;
+        const T bW = (i > 0) ? v.cx[ob + k - 1 + o] : T(0);
+        const T pN = (j + 1 < ny) ? v.e[ob + k + hx] : pc;
+        const T pS = (j > 0) ? v.e[ob + k - hx] : pc;
+        const T bS = (j > 0) ? v.cy[ob + k - hx] : T(0);
+        T s = v.cx[oc + k] * (pE - pc);
+        s -= bW * (pc - pW);
+        s += v.cy[oc + k] * (pN - pc);
+        s -= bS * (pc - pS);
+        return v.r[oc + k] - s * ih2;
+    };
+    Walk w(t, NT, nxc);
+    for (int k = t; k < nc; k += NT, w.next()) {
+        const int J = w.a, I = w.b, i = 2 * I, j = 2 * J;
+        T acc = res(i, j);
+        acc += res(i + 1, j);
+        acc += res(i, j + 1);
+        acc += res(i + 1, j + 1);
+        const T rv = T(0.25) * acc;
+        if (cnat) {
+            rc[k] = rv;
+            ec[k] = T(0);
+        } else {
+            const int cc = (I + J) & 1, kc = cc * blc + J * hxc + (I >> 1);
+            rc[kc] = rv;
+            ec[kc] = (fold && cc == 0) ? (T(0) - h2c * rv) * ivc[kc] : T(0);
+        }
+    }
+    gsync<NT>();
+}
+
+// e_l += P e_{l+1} (bilinear, weights 9/16, 3/16, 3/16, 1/16).  With
+// black_only, the red cells are left out: the red phase that follows
+// overwrites them without reading them.
+template <typename T, int NT>
+__device__ __forceinline__ void tail_prolong(const TailArgs<T> &g, T *sm, int l, int black_only, int t)
+{
+    const int nx = g.nx[l], ny = g.ny[l], hx = nx / 2, nh = hx * ny, bl = nh + kTailPad;
+    const int nxc = nx / 2, nyc = ny / 2, hxc = nxc / 2, blc = nxc * nyc / 2 + kTailPad;
+    const bool cnat = l + 1 == g.nl - 1;
+    const T *ec = sm + g.off[l + 1];
+    T *ef = sm + g.off[l];
+    auto at = [&](int I, int J) {
+        return cnat ? ec[J * nxc + I] : ec[((I + J) & 1) * blc + J * hxc + (I >> 1)];
+    };
+    for (int c = black_only ? 1 : 0; c < 2; c++) {
+        Walk w(t, NT, hx);
+        for (int q = t; q < nh; q += NT, w.next()) {
+            const int j = w.a, m = w.b, i = 2 * m + ((j + c) & 1);
+            const int I = m, J = j >> 1;
+            const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
+            const int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
+            const T c00 = at(I, J), c10 = at(I2, J), c01 = at(I, J2), c11 = at(I2, J2);
+            ef[c * bl + j * hx + m] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
+        }
     }
     gsync<NT>();
 }
 
 template <typename T, int NT>
-__device__ void tail_prolong(const TailArgs<T> &g, const TailView<T> &v, int l, int t)
-{
-    const int nx = g.nx[l], ny = g.ny[l], nxc = nx / 2, nyc = ny / 2;
-    const T *ec = v.e[l + 1];
-    T *ef = v.e[l];
-    for (int k = t; k < nx * ny; k += NT) {
-        const int j = k / nx, i = k - j * nx;
-        const int I = i >> 1, J = j >> 1;
-        const int I2 = min(max(I + ((i & 1) ? 1 : -1), 0), nxc - 1);
-        const int J2 = min(max(J + ((j & 1) ? 1 : -1), 0), nyc - 1);
-        const T c00 = ec[J * nxc + I], c10 = ec[J * nxc + I2];
-        const T c01 = ec[J2 * nxc + I], c11 = ec[J2 * nxc + I2];
-        ef[k] += (T(9) * c00 + T(3) * c10 + T(3) * c01 + c11) * T(0.0625);
-    }
-    gsync<NT>();
-}
-
-template <typename T, int NT>
-__device__ void tail_down(const TailArgs<T> &g, const TailView<T> &v, int l0, int l1, int t)
+__device__ __forceinline__ void tail_down(const TailArgs<T> &g, T *sm, int l0, int l1, int t)
 {
     for (int l = l0; l < l1; l++) {
-        tail_smooth<T, NT>(g, v, l, g.nu1, t);
-        tail_restrict<T, NT>(g, v, l, t);
+        tail_smooth<T, NT>(g, sm, l, g.nu1, (l > g.lt && g.nu1 > 0) ? 1 : 0, t);
+        tail_restrict<T, NT>(g, sm, l, g.nu1 > 0, t);
     }
 }
 
 template <typename T, int NT>
-__device__ void tail_up(const TailArgs<T> &g, const TailView<T> &v, int l0, int l1, int t)
+__device__ __forceinline__ void tail_up(const TailArgs<T> &g, T *sm, int l0, int l1, int t)
 {
     for (int l = l1 - 1; l >= l0; l--) {
-        tail_prolong<T, NT>(g, v, l, t);
-        tail_smooth<T, NT>(g, v, l, g.nu2, t);
+        tail_prolong<T, NT>(g, sm, l, g.nu2 > 0, t);
+        tail_smooth<T, NT>(g, sm, l, g.nu2, 0, t);
     }
-}
-
-// Dynamic shared memory of the tail kernel: the levels' arrays, then the
-// coarsest level's inverse (FP64, 8-byte aligned) when it takes at most
-// 64 KB (else the solve reads it from global memory).
-constexpr size_t kTailInvMax = 64 * 1024;
-__host__ __device__ inline size_t tail_inv_bytes(int nco)
-{
-    const size_t b = (size_t)nco * nco * sizeof(double);
-    return b <= kTailInvMax ? b : 0;
-}
-
-template <typename T>
-__host__ __device__ size_t tail_smem_bytes(const TailArgs<T> &a)
-{
-    const size_t lv = tail_smem_elems(a) * sizeof(T);
-    return ((lv + 7) & ~(size_t)7) + tail_inv_bytes(a.nx[a.nl - 1] * a.ny[a.nl - 1]);
 }
 
 // The lower V-cycle (levels lt..L-1) in one CTA: the coefficients, the
-// level-lt iterate and right-hand side and the coarsest inverse are copied
-// into shared memory, the cycle runs there, and the level-lt iterate is
-// copied back.  Levels of at least 512 cells use the whole block, those of
-// at least 128 cells warps 0-3, the rest and the coarsest solve warp 0.
+// level-lt iterate and right-hand side and the coarsest inverse are loaded
+// into shared memory (into the colour-split layout: pairs of row neighbours
+// are loaded together and stored to their two colours), the cycle runs
+// there, and the level-lt iterate is copied back.  Levels of at least 512
+// cells use the whole block, those of at least 128 cells warps 0-3, the rest
+// and the coarsest solve warp 0.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_tail(TailArgs<T> g)
+__global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs<T> g)
 {
+    using P2 = typename Pair<T>::V;
     pdl_enter();
     extern __shared__ __align__(16) unsigned char tail_sm[];
     __shared__ double xs[kMaxCoarsest];
-    __shared__ TailView<T> v;
-    __shared__ double *ainv;
+    T *sm = reinterpret_cast<T *>(tail_sm);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int L = g.nl, lc = L - 1, nco = g.nx[lc] * g.ny[lc];
-    if (tid == 0) {
-        T *q = (T *)tail_sm;
-        for (int l = g.lt; l < g.nl; l++) {
-            const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
-            v.e[l] = q; v.r[l] = q + c; v.iv[l] = q + 2 * c; v.bx[l] = q + 3 * c; v.by[l] = q + 3 * c + fx;
-            q += 3 * c + fx + fy;
+    const double *ainv = g.inv_off >= 0 ? reinterpret_cast<const double *>(tail_sm + g.inv_off) : g.ainvT;
+    if (g.inv_off >= 0)
+        stage_array(reinterpret_cast<double *>(tail_sm + g.inv_off), g.ainvT, nco * nco, tid, nthr);
+    if (g.lt == lc) {
+        stage_array(sm + g.off[lc], g.e[lc], nco, tid, nthr);
+        stage_array(sm + g.off[lc] + nco, g.r[lc], nco, tid, nthr);
+    }
+    // pairs of row neighbours of all split levels, numbered level by level;
+    // a batch of kStage pairs per thread has all its loads in flight before
+    // its stores
+    constexpr int kStage = sizeof(T) == 4 ? 4 : 2;
+    int npairs = 0;
+    for (int l = g.lt; l < lc; l++) npairs += g.nx[l] * g.ny[l] / 2;
+    for (int base = 0; base < npairs; base += kStage * nthr) {
+        P2 d[kStage], yn[kStage], ev[kStage], rv[kStage];
+        T x0[kStage], x1[kStage];
+        int s0[kStage], s1[kStage], lv[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; u++) {
+            int q = base + u * nthr + tid, l = g.lt;
+            lv[u] = -1;
+            if (q >= npairs) continue;
+            while (q >= g.nx[l] * g.ny[l] / 2) { q -= g.nx[l] * g.ny[l] / 2; l++; }
+            // cells (i, j), (i + 1, j): colours c and 1 - c, slot m of both
+            const int nx = g.nx[l], hx = nx / 2, bl = nx * g.ny[l] / 2 + kTailPad;
+            const int j = q / hx, m = q - j * hx, i = 2 * m, k = j * nx + i, c = j & 1;
+            lv[u] = l;
+            s0[u] = c * bl + j * hx + m;
+            s1[u] = (1 - c) * bl + j * hx + m;
+            d[u] = __ldg(reinterpret_cast<const P2 *>(g.invd[l] + k));
+            yn[u] = __ldg(reinterpret_cast<const P2 *>(g.by[l] + k + nx));
+            x0[u] = __ldg(g.bx[l] + (long)j * (nx + 1) + i + 1);
+            x1[u] = __ldg(g.bx[l] + (long)j * (nx + 1) + i + 2);
+            if (l == g.lt) {
+                ev[u] = __ldg(reinterpret_cast<const P2 *>(g.e[l] + k));
+                rv[u] = __ldg(reinterpret_cast<const P2 *>(g.r[l] + k));
+            }
         }
-        ainv = tail_inv_bytes(nco) ? (double *)(tail_sm + ((tail_smem_elems(g) * sizeof(T) + 7) & ~(size_t)7))
-                                   : const_cast<double *>(g.ainvT);
+#pragma unroll
+        for (int u = 0; u < kStage; u++) {
+            const int l = lv[u];
+            if (l < 0) continue;
+            const TailLv<T> v = tail_lv(g, sm, l);
+            v.iv[s0[u]] = d[u].x; v.iv[s1[u]] = d[u].y;
+            v.cy[s0[u]] = yn[u].x; v.cy[s1[u]] = yn[u].y;
+            v.cx[s0[u]] = x0[u]; v.cx[s1[u]] = x1[u];
+            if (l == g.lt) {
+                v.e[s0[u]] = ev[u].x; v.e[s1[u]] = ev[u].y;
+                v.r[s0[u]] = rv[u].x; v.r[s1[u]] = rv[u].y;
+            }
+        }
     }
-    __syncthreads();
-    // stage with asynchronous copies, all in flight before the wait
-    for (int l = g.lt; l < g.nl; l++) {
-        const int c = g.nx[l] * g.ny[l], fx = (g.nx[l] + 1) * g.ny[l], fy = g.nx[l] * (g.ny[l] + 1);
-        stage_array(v.iv[l], g.invd[l], c, tid, nthr);
-        if (l == g.lt) { stage_array(v.e[l], g.e[l], c, tid, nthr); stage_array(v.r[l], g.r[l], c, tid, nthr); }
-        stage_array(v.bx[l], g.bx[l], fx, tid, nthr);
-        stage_array(v.by[l], g.by[l], fy, tid, nthr);
-    }
-    if (tail_inv_bytes(nco)) stage_array(ainv, g.ainvT, nco * nco, tid, nthr);
     asm volatile("cp.async.wait_all;\n" ::);
     __syncthreads();
     int lb = g.lt;  // first level of warps 0-3
     while (lb < lc && g.nx[lb] * g.ny[lb] >= 512) lb++;
     int lw = lb;    // first level of warp 0
     while (lw < lc && g.nx[lw] * g.ny[lw] >= 128) lw++;
-    tail_down<T, 1024>(g, v, g.lt, lb, tid);
+    tail_down<T, 1024>(g, sm, g.lt, lb, tid);
     if (tid < 128) {
-        tail_down<T, 128>(g, v, lb, lw, tid);
+        tail_down<T, 128>(g, sm, lb, lw, tid);
         if (tid < 32) {
-            tail_down<T, 32>(g, v, lw, lc, tid);
+            tail_down<T, 32>(g, sm, lw, lc, tid);
             // coarsest: x = A'^{-1} r, one row of the inverse per lane
-            for (int k = tid; k < nco; k += 32) xs[k] = (double)v.r[lc][k];
+            T *ecs = sm + g.off[lc];
+            const T *rcs = ecs + nco;
+            for (int k = tid; k < nco; k += 32) xs[k] = (double)rcs[k];
             __syncwarp();
             for (int k = tid; k < nco; k += 32) {
                 double acc = 0.0;
                 for (int q = 0; q < nco; q++) acc += ainv[q * nco + k] * xs[q];
-                v.e[lc][k] = (T)acc;
+                ecs[k] = (T)acc;
             }
             __syncwarp();
-            tail_up<T, 32>(g, v, lw, lc, tid);
+            tail_up<T, 32>(g, sm, lw, lc, tid);
         }
         gsync<128>();
-        tail_up<T, 128>(g, v, lb, lw, tid);
+        tail_up<T, 128>(g, sm, lb, lw, tid);
     }
     __syncthreads();
-    tail_up<T, 1024>(g, v, g.lt, lb, tid);
-    for (int k = tid; k < g.nx[g.lt] * g.ny[g.lt]; k += nthr) g.e[g.lt][k] = v.e[g.lt][k];
+    tail_up<T, 1024>(g, sm, g.lt, lb, tid);
+    const int nx0 = g.nx[g.lt], n0 = nx0 * g.ny[g.lt];
+    T *eo = g.e[g.lt];
+    if (g.lt == lc) {
+        for (int k = tid; k < n0; k += nthr) eo[k] = sm[g.off[lc] + k];
+    } else {
+        const int hx = nx0 / 2, bl = n0 / 2 + kTailPad;
+        const T *es = sm + g.off[g.lt];
+        Walk w(tid, nthr, hx);
+        for (int q = tid; q < n0 / 2; q += nthr, w.next()) {
+            const int j = w.a, m = w.b, c = j & 1;
+            P2 o;
+            o.x = es[c * bl + j * hx + m];
+            o.y = es[(1 - c) * bl + j * hx + m];
+            *reinterpret_cast<P2 *>(eo + j * nx0 + 2 * m) = o;
+        }
+    }
 }
 
 // --------------------------------------------------------------- reductions
@@ -1198,7 +1391,7 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *add64 = nullptr)
     ta.nu1 = nu1;
     ta.nu2 = nu2;
     note_launch();
-    const size_t smem = tail_smem_bytes(ta);
+    const size_t smem = tail_prepare(ta);
     launch_pdl(k_tail<T>, 1, 1024, smem, s, ta);
     for (int l = lt - 1; l >= 0; l--) {
         Level &v = mg.lv[l];
@@ -1494,7 +1687,8 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
         ta.nu1 = 2;
         ta.nu2 = 2;
         note_launch();
-        launch_pdl(k_tail<float>, 1, 1024, tail_smem_bytes(ta), s, ta);
+        const size_t smem = tail_prepare(ta);
+        launch_pdl(k_tail<float>, 1, 1024, smem, s, ta);
         return (long)mg.lv[lt].nx * mg.lv[lt].ny;
     }
     case 6: {
@@ -1541,14 +1735,8 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         // shared memory of the single-CTA tail (set here, outside any capture)
         size_t e = 0;
         size_t ef = 0;
-        for (int l = mg.tail; l < L; l++) {
-            size_t c = (size_t)mg.lv[l].nx * mg.lv[l].ny;
-            e += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
-        }
-        for (int l = mg.tail_f; l < L; l++) {
-            size_t c = (size_t)mg.lv[l].nx * mg.lv[l].ny;
-            ef += 3 * c + (size_t)(mg.lv[l].nx + 1) * mg.lv[l].ny + (size_t)mg.lv[l].nx * (mg.lv[l].ny + 1);
-        }
+        for (int l = mg.tail; l < L; l++) e += tail_level_elems(mg.lv[l].nx, mg.lv[l].ny, l == L - 1);
+        for (int l = mg.tail_f; l < L; l++) ef += tail_level_elems(mg.lv[l].nx, mg.lv[l].ny, l == L - 1);
         const size_t inv = tail_inv_bytes(mg.lv[L - 1].nx * mg.lv[L - 1].ny);
         raise_smem_limit((const void *)k_tail<double>, (int)(((e * 8 + 7) & ~(size_t)7) + inv));
         raise_smem_limit((const void *)k_tail<float>, (int)(((ef * 4 + 7) & ~(size_t)7) + inv));
