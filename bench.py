@@ -150,14 +150,18 @@ TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 def kernel_source(rel, name):
     """The text of kernel `name` in source file `rel` (its signature line to
     the first closing brace in column 0) and the file's compile-time integer
-    constants, which set its tiles."""
+    constants that the kernel names (they set its tiles)."""
+    import re
     with open(os.path.join(ROOT, rel)) as f:
         lines = f.read().split("\n")
     start = next(i for i, ln in enumerate(lines)
                  if ln.startswith(name + "(") or ("__global__" in ln and " " + name + "(" in ln))
     end = next(i for i in range(start, len(lines)) if lines[i] == "}")
-    consts = [ln for ln in lines if ln.lstrip().startswith("constexpr int")]
-    return "\n".join(consts + lines[start:end + 1])
+    body = "\n".join(lines[start:end + 1])
+    words = set(re.findall(r"[A-Za-z_]\w*", body))
+    consts = [ln for ln in lines if ln.startswith("constexpr int")
+              and set(re.findall(r"([A-Za-z_]\w*)\s*=", ln)) & words]
+    return "\n".join(consts) + "\n" + body
 
 
 def source_sha(rel, name):
