@@ -248,6 +248,9 @@ struct Markers {
     float4 *slf = nullptr;                 // the same in FP32 (nx, ny, c, |n|)
     uint8_t *scvx = nullptr;               // per segment: 1 = half-plane path (strips convex, lines well conditioned)
     double *sinv = nullptr;                // per segment: 1 / |segment|^2 in grid units
+    double *rfit = nullptr;                // relocation: per-drop control points and knot arc lengths
+    double *rpar = nullptr;                // relocation: per drop (g, tau, arc length, failed)
+    double *rwts = nullptr;                // relocation: per marker, its four basis weights
     uint32_t pair_cap = 0;                 // capacity of the band (cell, segment) pair list
     uint32_t *npairs = nullptr;            // pairs claimed by the last band pass
     uint32_t *pseg = nullptr, *pcell = nullptr;  // pair list: segment, cell index

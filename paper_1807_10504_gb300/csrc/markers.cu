@@ -1101,17 +1101,29 @@ k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ 
 }
 
 // ------------------------------------------------------------ B-spline
-// One CTA per drop.  Same steps as the definition: chord-length parameters,
-// g = round(L / 1.5h) spans (4 <= g <= n), periodic cubic basis by the
-// Cox-de Boor recursion, normal equations accumulated in ascending marker
-// order, Cholesky in the matrix's envelope (band of 3 plus the last three
-// rows, which is where the cyclic wrap fills in), arc length by 8-point
-// Gauss-Legendre per span, 12 Newton steps per new marker.
-__device__ void bspl_basis(double s, double tau, int g, int *idx, double *w, double *dw)
+// Section 4: relocation along a periodic cubic B-spline fitted to each drop
+// by least squares.  Same steps as the definition: chord-length parameters,
+// g = round(L / 1.5h) spans (4 <= g <= n), normal equations accumulated in
+// ascending marker order, Cholesky in the matrix's envelope (band of 3 plus
+// the last three rows, which is where the cyclic wrap fills in), arc length
+// by 8-point Gauss-Legendre per span, 12 Newton steps per new marker.  Two
+// kernels: the fit (one CTA per drop) and the placement of the new markers
+// (one thread per marker over the whole grid).
+// The basis follows the same arithmetic as a serial program: the span of a
+// parameter is floor(s / tau) and the weights come from the Cox-de Boor
+// recursion on knots t_k = k tau, so that relocated markers agree with it to
+// rounding of the same operations.
+__device__ __forceinline__ int bspl_span(double s, double tau, int g)
 {
     int q = (int)floor(s / tau);
     if (q > g - 1) q = g - 1;
     if (q < 0) q = 0;
+    return q;
+}
+
+__device__ void bspl_basis(double s, double tau, int g, int *idx, double *w, double *dw)
+{
+    const int q = bspl_span(s, tau, g);
     double N[4][4];
     N[0][0] = 1.0;
     for (int d = 1; d <= 3; d++)
@@ -1184,62 +1196,103 @@ __device__ double gval(const double *Gc, int g, int r, int c)
     return 0.0;
 }
 
-__device__ int env_solve(Env &L, const double *Gc, int g, double *b)
+// Cholesky factorisation in the envelope by warp 0 (lane t of 32), each
+// entry by the sums of a dense Cholesky in ascending order: per column c,
+// lane 0 takes the diagonal while lanes 1..6 take the envelope rows below it
+// (c+1..c+3 and the dense last three rows), whose sums need only earlier
+// columns; their division by the diagonal follows.  Returns -1 (in every
+// lane) if not positive definite.
+__device__ int env_factor(Env &L, const double *Gc, int g, int t)
 {
-    // factorisation (sequential, ascending sums as in a dense Cholesky)
     for (int c = 0; c < g; c++) {
-        double s = gval(Gc, g, c, c);
-        for (int k = L.first(c); k < c; k++) { double v = L.get(c, k); s -= v * v; }
+        // envelope row of lane t (t >= 1): the (t-1)-th of the ascending walk
+        int r = -1;
+        if (t >= 1 && t <= 6) {
+            int k = 0;
+            for (int q = c + 1; q < g; q = (q == c + 3 && q + 1 < g - 3) ? g - 3 : q + 1) {
+                if (L.is_band(q) && q - 3 > c) continue;
+                if (++k == t) { r = q; break; }
+            }
+        }
+        double acc = 0.0;
+        if (t == 0) {
+            acc = gval(Gc, g, c, c);
+            for (int k = L.first(c); k < c; k++) { double v = L.get(c, k); acc -= v * v; }
+        } else if (r >= 0) {
+            acc = gval(Gc, g, r, c);
+            for (int k = max(L.first(r), L.first(c)); k < c; k++) acc -= L.get(r, k) * L.get(c, k);
+        }
+        const double s = __shfl_sync(0xffffffffu, acc, 0);
         if (!(s > 0.0)) return -1;
-        double d = sqrt(s);
-        L.set(c, c, d);
-        for (int r = c + 1; r < g; r++) {
-            if (L.is_band(r) && r - 3 > c) continue;  // outside the envelope
-            double t = gval(Gc, g, r, c);
-            for (int k = max(L.first(r), L.first(c)); k < c; k++) t -= L.get(r, k) * L.get(c, k);
-            L.set(r, c, t / d);
-        }
-    }
-    for (int r = 0; r < g; r++) {
-        double s = b[r];
-        for (int k = L.first(r); k < r; k++) s -= L.get(r, k) * b[k];
-        b[r] = s / L.get(r, r);
-    }
-    for (int r = g - 1; r >= 0; r--) {
-        double s = b[r];
-        for (int k = r + 1; k < g; k++) {
-            if (L.is_band(k) && k - 3 > r) continue;
-            s -= L.get(k, r) * b[k];
-        }
-        b[r] = s / L.get(r, r);
+        const double d = sqrt(s);
+        if (t == 0) L.set(c, c, d);
+        else if (r >= 0) L.set(r, c, acc / d);
+        __syncwarp();
     }
     return 0;
 }
 
+// L L^T x = b for the two right-hand sides bx, by (in place), each in the
+// order of a single-right-hand-side solve.
+__device__ void env_subst(const Env &L, int g, double *bx, double *by)
+{
+    for (int r = 0; r < g; r++) {
+        double s = bx[r], t = by[r];
+        for (int k = L.first(r); k < r; k++) { const double l = L.get(r, k); s -= l * bx[k]; t -= l * by[k]; }
+        bx[r] = s / L.get(r, r);
+        by[r] = t / L.get(r, r);
+    }
+    for (int r = g - 1; r >= 0; r--) {
+        double s = bx[r], t = by[r];
+        for (int k = r + 1; k < g; k = (k == r + 3 && k + 1 < g - 3) ? g - 3 : k + 1) {
+            if (L.is_band(k) && k - 3 > r) continue;
+            const double l = L.get(k, r);
+            s -= l * bx[k];
+            t -= l * by[k];
+        }
+        bx[r] = s / L.get(r, r);
+        by[r] = t / L.get(r, r);
+    }
+}
+
+// Per-drop fit results: at offset 3 * s0 + d of fit (s0 the drop's first
+// marker, n its markers, g <= n) the control points cx[g], cy[g] and the
+// cumulative arc length at the knots cum[g + 1]; par[4d .. 4d+3] = (g, tau,
+// total arc length, failed).
+__device__ __forceinline__ long fit_base(int s0, int d) { return 3L * s0 + d; }
+
 __global__ void __launch_bounds__(kT)
-k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
-           const int32_t *__restrict__ drop_start, double h, int maxn,
-           double *__restrict__ Xo, double *__restrict__ Yo, uint32_t *__restrict__ flags)
+k_reloc_fit(const double *__restrict__ X, const double *__restrict__ Y,
+            const int32_t *__restrict__ drop_start, double h, int maxn,
+            double *__restrict__ fit, double *__restrict__ par, double *__restrict__ wts,
+            uint32_t *__restrict__ flags)
 {
     extern __shared__ double sm[];
     const int d = blockIdx.x, s0 = drop_start[d], n = drop_start[d + 1] - s0;
-    // shared layout: sp[n+1], qs[maxg+1] (as double), Gc[4g], cx[g], cy[g],
-    // band[4g], dense[6g], cum[g+1]
+    // shared layout: sp[n+1], qs[maxg+1] and span[maxn] (ints), Gc[4g],
+    // cx[g], cy[g], band[4g], dense[6g], cum[g+1]
     const int maxg = maxn;
     double *sp = sm;
     int *qs = (int *)(sp + maxn + 1);
+    int *span = qs + (maxg + 1);
     double *Gc = (double *)(qs + 2 * (maxg + 1));
     double *cx = Gc + 4 * maxg, *cy = cx + maxg, *band = cy + maxg, *dense = band + 4 * maxg;
     double *cum = dense + 6 * maxg;
     __shared__ int g_s, bad;
     __shared__ double tau_s;
+    // chord lengths in parallel (cx as scratch), their running sum in marker
+    // order by one thread
+    for (int m = threadIdx.x; m < n; m += kT) {
+        const int a = s0 + m, b = s0 + (m + 1 == n ? 0 : m + 1);
+        const double dx = X[b] - X[a], dy = Y[b] - Y[a];
+        cx[m] = sqrt(dx * dx + dy * dy);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         double L = 0.0;
         for (int m = 0; m < n; m++) {
-            int a = s0 + m, b = s0 + (m + 1) % n;
             sp[m] = L;
-            double dx = X[b] - X[a], dy = Y[b] - Y[a];
-            L += sqrt(dx * dx + dy * dy);
+            L += cx[m];
         }
         int g = (int)floor(L / (1.5 * h) + 0.5);
         if (g < 4) g = 4;
@@ -1247,19 +1300,27 @@ k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
         g_s = g;
         tau_s = L / g;
         bad = 0;
-        // first marker of every span (parameters ascend with m)
-        int q = 0;
-        for (int k = 0; k <= g; k++) qs[k] = n;
-        for (int m = 0; m < n; m++) {
-            int qq = (int)floor(sp[m] / tau_s);
-            if (qq > g - 1) qq = g - 1;
-            while (q <= qq) { qs[q] = m; q++; }
-        }
-        while (q <= g) { qs[q] = n; q++; }
     }
     __syncthreads();
     const int g = g_s;
     const double tau = tau_s;
+    // each marker's span and basis weights once (wts, 4 per marker); the
+    // first marker of every span (parameters ascend with m): qs[k] is the
+    // first marker of span >= k, n if none
+    for (int m = threadIdx.x; m < n; m += kT) {
+        int idx[4];
+        double w[4], dw[4];
+        bspl_basis(sp[m], tau, g, idx, w, dw);
+        span[m] = bspl_span(sp[m], tau, g);
+        for (int r = 0; r < 4; r++) wts[4L * (s0 + m) + r] = w[r];
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < n; m += kT) {
+        const int lo = m == 0 ? 0 : span[m - 1] + 1;
+        for (int k = lo; k <= span[m]; k++) qs[k] = m;
+    }
+    for (int k = span[n - 1] + 1 + threadIdx.x; k <= g; k += kT) qs[k] = n;
+    __syncthreads();
     // normal equations: entry (i, i+d) and rhs i, markers of spans i..i+3 in
     // ascending marker order
     for (int e = threadIdx.x; e < 5 * g; e += kT) {
@@ -1273,11 +1334,13 @@ k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
         for (int t = 0; t < 4; t++) {
             if (t > 0 && sp4[t] == sp4[t - 1]) continue;
             for (int m = qs[sp4[t]]; m < qs[sp4[t] + 1]; m++) {
-                int idx[4];
-                double w[4], dw[4];
-                bspl_basis(sp[m], tau, g, idx, w, dw);
+                const double *w = wts + 4L * (s0 + m);
                 int a = -1, b = -1;
-                for (int r = 0; r < 4; r++) { if (idx[r] == i) a = r; if (idx[r] == jcol) b = r; }
+                for (int r = 0; r < 4; r++) {
+                    const int k = span[m] - 3 + r, id = ((k % g) + g) % g;
+                    if (id == i) a = r;
+                    if (id == jcol) b = r;
+                }
                 if (a < 0) continue;
                 if (dd < 4) { if (b >= 0) acc += w[a] * w[b]; }
                 else { acc += w[a] * X[s0 + m]; accy += w[a] * Y[s0 + m]; }
@@ -1287,14 +1350,21 @@ k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
         else { cx[i] = acc; cy[i] = accy; }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         Env L{g, band, dense};
-        if (env_solve(L, Gc, g, cx) != 0 || env_solve(L, Gc, g, cy) != 0) bad = 1;
+        const int f = env_factor(L, Gc, g, threadIdx.x);
+        if (threadIdx.x == 0) {
+            if (f != 0) bad = 1;
+            else env_subst(L, g, cx, cy);
+        }
     }
     __syncthreads();
+    double *out = fit + fit_base(s0, d);
     if (bad) {
-        if (threadIdx.x == 0) atomicOr(&flags[2], 1u);
-        for (int m = threadIdx.x; m < n; m += kT) { Xo[s0 + m] = X[s0 + m]; Yo[s0 + m] = Y[s0 + m]; }
+        if (threadIdx.x == 0) {
+            atomicOr(&flags[2], 1u);
+            par[4 * d] = (double)g; par[4 * d + 1] = tau; par[4 * d + 2] = 0.0; par[4 * d + 3] = 1.0;
+        }
         return;
     }
     for (int q = threadIdx.x; q < g; q += kT) cum[q + 1] = gl_len(q * tau, (q + 1) * tau, tau, g, cx, cy);
@@ -1302,34 +1372,78 @@ k_relocate(const double *__restrict__ X, const double *__restrict__ Y,
     if (threadIdx.x == 0) {
         cum[0] = 0.0;
         for (int q = 0; q < g; q++) cum[q + 1] = cum[q] + cum[q + 1];
+        par[4 * d] = (double)g; par[4 * d + 1] = tau; par[4 * d + 2] = cum[g]; par[4 * d + 3] = 0.0;
     }
     __syncthreads();
-    const double Lp = cum[g];
-    for (int m = threadIdx.x; m < n; m += kT) {
-        double target = Lp * (double)m / (double)n;
-        int lo = 0, hi = g - 1;  // largest q <= g-1 with cum[q] <= target
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (cum[mid] <= target) lo = mid; else hi = mid - 1;
-        }
-        int q = lo;
-        double a = q * tau, b = (q + 1) * tau;
-        double seg = cum[q + 1] - cum[q];
-        double s = a + tau * (target - cum[q]) / seg;
-        for (int it = 0; it < 12; it++) {
-            double f = cum[q] + gl_len(a, s, tau, g, cx, cy) - target;
-            double sp_ = bspl_speed(s, tau, g, cx, cy);
+    for (int q = threadIdx.x; q < g; q += kT) { out[q] = cx[q]; out[n + q] = cy[q]; }
+    for (int q = threadIdx.x; q <= g; q += kT) out[2 * n + q] = cum[q];
+}
+
+// New marker m of its drop at arc length L m / n along the fitted curve: the
+// span by bisection of the knot arc lengths, then 12 Newton steps on the
+// partial arc length, kept in the span.  With LN = 8 lanes per marker (few
+// markers: the FP64 latency of one thread's steps dominates), lane k
+// evaluates the k-th Gauss-Legendre term of the partial arc length and lane
+// 0 also the speed at s; every lane then sums the eight terms in order, so
+// all lanes carry the same s.  With LN = 1 (many markers: FP64 throughput
+// dominates) one thread does all.  A drop whose fit failed keeps its markers.
+constexpr int kPlaceT = 64;
+template <int LN>
+__global__ void __launch_bounds__(kPlaceT)
+k_reloc_place(int M, const double *__restrict__ X, const double *__restrict__ Y,
+              const int32_t *__restrict__ drop_of, const int32_t *__restrict__ drop_start,
+              const double *__restrict__ fit, const double *__restrict__ par,
+              double *__restrict__ Xo, double *__restrict__ Yo)
+{
+    const int lane = LN == 8 ? (threadIdx.x & 7) : 0, tid = blockIdx.x * kPlaceT + threadIdx.x;
+    const int j = LN == 8 ? tid >> 3 : tid;
+    const unsigned grp = 0xffu << (threadIdx.x & 24);  // the eight lanes of this marker
+    if (j >= M) return;  // whole groups leave together (groups of LN lanes)
+    const int d = drop_of[j], s0 = drop_start[d], n = drop_start[d + 1] - s0, m = j - s0;
+    if (par[4 * d + 3] != 0.0) {
+        if (lane == 0) { Xo[j] = X[j]; Yo[j] = Y[j]; }
+        return;
+    }
+    const int g = (int)par[4 * d];
+    const double tau = par[4 * d + 1], Lp = par[4 * d + 2];
+    const double *cx = fit + fit_base(s0, d), *cy = cx + n, *cum = cx + 2 * n;
+    const double target = Lp * (double)m / (double)n;
+    int lo = 0, hi = g - 1;  // largest q <= g-1 with cum[q] <= target
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cum[mid] <= target) lo = mid; else hi = mid - 1;
+    }
+    const int q = lo;
+    const double a = q * tau, b = (q + 1) * tau;
+    const double seg = cum[q + 1] - cum[q];
+    double s = a + tau * (target - cum[q]) / seg;
+    for (int it = 0; it < 12; it++) {
+        if constexpr (LN == 1) {
+            const double f = cum[q] + gl_len(a, s, tau, g, cx, cy) - target;
+            const double sp_ = bspl_speed(s, tau, g, cx, cy);
             s -= f / sp_;
             if (s < a) s = a;
             if (s > b) s = b;
+            continue;
         }
-        int idx[4];
-        double w[4], dw[4], px = 0.0, py = 0.0;
-        bspl_basis(s, tau, g, idx, w, dw);
-        for (int r = 0; r < 4; r++) { px += cx[idx[r]] * w[r]; py += cy[idx[r]] * w[r]; }
-        Xo[s0 + m] = px;
-        Yo[s0 + m] = py;
+        // cum[q] + gl_len(a, s) - target, the Gauss-Legendre sum as gl_len
+        const double mid = 0.5 * (a + s), half = 0.5 * (s - a);
+        const double term = cGLW[lane] * bspl_speed(mid + half * cGLX[lane], tau, g, cx, cy);
+        const double sp_ = lane == 0 ? bspl_speed(s, tau, g, cx, cy) : 0.0;
+        double sum = 0.0;
+        for (int k = 0; k < 8; k++) sum += __shfl_sync(grp, term, k, 8);
+        const double f = cum[q] + sum * half - target;
+        s -= f / __shfl_sync(grp, sp_, 0, 8);
+        if (s < a) s = a;
+        if (s > b) s = b;
     }
+    if (lane != 0) return;
+    int idx[4];
+    double w[4], dw[4], px = 0.0, py = 0.0;
+    bspl_basis(s, tau, g, idx, w, dw);
+    for (int r = 0; r < 4; r++) { px += cx[idx[r]] * w[r]; py += cy[idx[r]] * w[r]; }
+    Xo[j] = px;
+    Yo[j] = py;
 }
 
 }  // namespace
@@ -1353,7 +1467,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     // per segment; 64 per segment covers segments up to ~9 cells long.
     const size_t pair_cap = (size_t)M * 64 + 4096;
     mk.pair_cap = (uint32_t)pair_cap;
-    size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 +
+    size_t bytes = al(M * 8) * 13 + al(M * 4) * 2 + al(M * 16) + al(ndrops * 16) * 2 + al((3 * (size_t)M + ndrops) * 8) + al((size_t)ndrops * 32) + al((size_t)M * 32) +
                    al((size_t)M * 24 * 8) + al((size_t)M * kSegLine * 8) + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) + al(M * 8) +
                    al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
@@ -1372,6 +1486,9 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.sbox = (float4 *)take(M * 16);
     mk.dyr = (double2 *)take(ndrops * 16);
     mk.dyk = (ulonglong2 *)take(ndrops * 16);
+    mk.rfit = (double *)take((3 * (size_t)M + ndrops) * 8);
+    mk.rpar = (double *)take((size_t)ndrops * 32);
+    mk.rwts = (double *)take((size_t)M * 32);
     mk.sv = (double *)take((size_t)M * 24 * 8);
     mk.sl = (double *)take((size_t)M * kSegLine * 8);
     mk.slf = (float4 *)take((size_t)M * 8 * 16);
@@ -1623,10 +1740,19 @@ void launch_mass_correct(Markers &mk, const double *A0, int axisym, double tol, 
 void launch_relocate(Markers &mk, cudaStream_t s)
 {
     size_t sm = relocate_smem(mk.max_drop);
-    raise_smem_limit((const void *)k_relocate, (int)sm);
+    raise_smem_limit((const void *)k_reloc_fit, (int)sm);
     note_launch();
-    k_relocate<<<mk.ndrops, kT, sm, s>>>(mk.X, mk.Y, mk.drop_start, mk.h, mk.max_drop, mk.Xn,
-                                         mk.Yn, mk.flags);
+    k_reloc_fit<<<mk.ndrops, kT, sm, s>>>(mk.X, mk.Y, mk.drop_start, mk.h, mk.max_drop, mk.rfit,
+                                          mk.rpar, mk.rwts, mk.flags);
+    note_launch();
+    if (mk.M < 4096)
+        k_reloc_place<8><<<cdiv(8 * mk.M, kPlaceT), kPlaceT, 0, s>>>(mk.M, mk.X, mk.Y, mk.drop_of,
+                                                                     mk.drop_start, mk.rfit, mk.rpar,
+                                                                     mk.Xn, mk.Yn);
+    else
+        k_reloc_place<1><<<cdiv(mk.M, kPlaceT), kPlaceT, 0, s>>>(mk.M, mk.X, mk.Y, mk.drop_of,
+                                                                 mk.drop_start, mk.rfit, mk.rpar,
+                                                                 mk.Xn, mk.Yn);
     cudaMemcpyAsync(mk.X, mk.Xn, (size_t)mk.M * 8, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(mk.Y, mk.Yn, (size_t)mk.M * 8, cudaMemcpyDeviceToDevice, s);
 }

@@ -122,6 +122,22 @@ def test_relocation(T, ib, O, case):
     assert np.abs(Y.cpu().numpy() - oY).max() <= 1e-12
 
 
+def test_relocation_many_markers(T, ib, O):
+    """The 1024^2 workload's 64 drops (16384 markers): the placement kernel
+    takes one thread per marker at this count (eight lanes per marker below
+    4096 markers, as in the cases above); every relocated marker against the
+    oracle."""
+    n = 1024
+    mk = W.multidrop(n)
+    assert mk.X.size >= 4096
+    cfg, ctx = make(ib, n, mk)
+    ctx.relocate()
+    X, Y = ctx.markers()
+    oX, oY = O.bspline_relocate(mk.X, mk.Y, mk.drop_start, 1.0 / n)
+    assert np.abs(X.cpu().numpy() - oX).max() <= 1e-12
+    assert np.abs(Y.cpu().numpy() - oY).max() <= 1e-12
+
+
 def test_marker_errors(T, ib):
     X, Y = W.circle(0.5, 0.5, 0.2, 40)
     cfg = ib.Config(nx=32, ny=32, h=1 / 32)
