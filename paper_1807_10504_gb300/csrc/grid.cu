@@ -85,9 +85,15 @@ __global__ void k_correct(int nx, int ny, double ih, double dt,
 
 // Tiled predictor: a 32 x 8 block of cells stages rho, mu, u and v with a
 // one-cell ring in shared memory, forms the node averages of rho and mu once
-// per node (four cells inside, the two wall cells on a wall), and each
-// thread then updates the x-face left of and the y-face below its cell (and
-// the wall face on the far side for the last column / row).
+// per node (four cells inside, the two wall cells on a wall), then every
+// flux that two faces share once per tile: per cell the advective flux
+// rho a^2 and the viscous flux mu du of each component, per node the
+// advective flux rho_n a_v a_u and the viscous flux mu_n du of each
+// component (the reflected ghost folded in at a wall node, zero advective
+// flux there).  Each thread then updates the x-face left of and the y-face
+// below its cell (and the wall face on the far side for the last column /
+// row) from differences of those fluxes, in the order of the per-face
+// formula, so each face gets the same value as if it formed them itself.
 constexpr int PX = 32, PY = 8;
 __global__ void __launch_bounds__(PX * PY)
 k_predictor(int nx, int ny, double ih, double ih2, double dt,
@@ -101,6 +107,11 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
     constexpr int W = PX + 2, Hh = PY + 2;  // staged window: cells / faces i0-1 .. i0+PX
     __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
     __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
+    // shared fluxes: x-momentum at cells i0-1 .. i0+PX-1 (fx, vx) and nodes
+    // (i0 .. i0+PX-1, j0 .. j0+PY) (gx, wx); y-momentum at cells j0-1 ..
+    // j0+PY-1 (fy, vy) and nodes (i0 .. i0+PX, j0 .. j0+PY-1) (gy, wy)
+    __shared__ double fx[PY][PX + 1], vx[PY][PX + 1], gxn[PY + 1][PX], wxn[PY + 1][PX];
+    __shared__ double fy[PY + 1][PX], vy[PY + 1][PX], gyn[PY][PX + 1], wyn[PY][PX + 1];
     const int i0 = blockIdx.x * PX, j0 = blockIdx.y * PY;
     const int t = threadIdx.y * PX + threadIdx.x;
     const long nxf = nx + 1;
@@ -136,6 +147,45 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         else nm[r][c] = 0.0;  // corner: never used
     }
     __syncthreads();
+    // cell fluxes: x-momentum of cell (i0-1+c, j0+r), window (r+1, c)
+    for (int k = t; k < PY * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1);
+        const double a = 0.5 * (su[r + 1][c + 1] + su[r + 1][c]);
+        fx[r][c] = sr[r + 1][c] * a * a;
+        vx[r][c] = sm[r + 1][c] * (su[r + 1][c + 1] - su[r + 1][c]);
+    }
+    // y-momentum of cell (i0+c, j0-1+r), window (r, c+1)
+    for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
+        const int r = k / PX, c = k - r * PX;
+        const double a = 0.5 * (sv[r + 1][c + 1] + sv[r][c + 1]);
+        fy[r][c] = sr[r][c + 1] * a * a;
+        vy[r][c] = sm[r][c + 1] * (sv[r + 1][c + 1] - sv[r][c + 1]);
+    }
+    // node fluxes of the x-momentum at node (I, J) = (i0+c, j0+r): between
+    // u(I, J-1) (window (r, c+1)) and u(I, J) (window (r+1, c+1))
+    for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
+        const int r = k / PX, c = k - r * PX, I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double ub = su[r][c + 1], ut = su[r + 1][c + 1];
+        gxn[r][c] = (J > 0 && J < ny)
+                        ? nr[r][c] * (0.5 * (sv[r + 1][c] + sv[r + 1][c + 1])) * (0.5 * (ub + ut))
+                        : 0.0;
+        const double uT = J < ny ? ut : -ub, uB = J > 0 ? ub : -ut;
+        wxn[r][c] = nm[r][c] * (uT - uB);
+    }
+    // node fluxes of the y-momentum at node (I, J) = (i0+c, j0+r): between
+    // v(I-1, J) (window (r+1, c)) and v(I, J) (window (r+1, c+1))
+    for (int k = t; k < PY * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double vl = sv[r + 1][c], vr = sv[r + 1][c + 1];
+        gyn[r][c] = (I > 0 && I < nx)
+                        ? nr[r][c] * (0.5 * (su[r][c + 1] + su[r + 1][c + 1])) * (0.5 * (vl + vr))
+                        : 0.0;
+        const double vR = I < nx ? vr : -vl, vL = I > 0 ? vl : -vr;
+        wyn[r][c] = nm[r][c] * (vR - vL);
+    }
+    __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
     if (i >= nx || j >= ny) return;
     const int R = ty + 1, C = tx + 1;  // window index of cell (i, j)
@@ -145,18 +195,9 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         if (i == 0) {
             us[k] = 0.0; au[k] = 0.0;
         } else {
-            const double uc = su[R][C], uE = su[R][C + 1], uW = su[R][C - 1];
-            const double uN = (j + 1 < ny) ? su[R + 1][C] : -uc;
-            const double uS = (j > 0) ? su[R - 1][C] : -uc;
-            const double aE = 0.5 * (uE + uc), aW = 0.5 * (uc + uW);
-            const double fE = sr[R][C] * aE * aE, fW = sr[R][C - 1] * aW * aW;
-            double gN = 0.0, gS = 0.0;
-            if (j + 1 < ny) gN = nr[ty + 1][tx] * (0.5 * (sv[R + 1][C - 1] + sv[R + 1][C])) * (0.5 * (uc + uN));
-            if (j > 0) gS = nr[ty][tx] * (0.5 * (sv[R][C - 1] + sv[R][C])) * (0.5 * (uc + uS));
-            const double muN = nm[ty + 1][tx], muS = nm[ty][tx];
-            const double adv = (fE - fW) * ih + (gN - gS) * ih;
-            const double vis = (sm[R][C] * (uE - uc) - sm[R][C - 1] * (uc - uW) + muN * (uN - uc) -
-                                muS * (uc - uS)) * ih2;
+            const double uc = su[R][C];
+            const double adv = (fx[ty][tx + 1] - fx[ty][tx]) * ih + (gxn[ty + 1][tx] - gxn[ty][tx]) * ih;
+            const double vis = (vx[ty][tx + 1] - vx[ty][tx] + wxn[ty + 1][tx] - wxn[ty][tx]) * ih2;
             // 1 / rho_face: the face coefficient beta when given (the same
             // reciprocal of the same rho), else formed here
             const double irf = bx ? bx[k] : recip_nr(0.5 * (sr[R][C - 1] + sr[R][C]));
@@ -172,18 +213,9 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         if (j == 0) {
             vs[k] = 0.0; av[k] = 0.0;
         } else {
-            const double vc = sv[R][C], vN = sv[R + 1][C], vS = sv[R - 1][C];
-            const double vE = (i + 1 < nx) ? sv[R][C + 1] : -vc;
-            const double vW = (i > 0) ? sv[R][C - 1] : -vc;
-            const double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
-            const double fN = sr[R][C] * aN * aN, fS = sr[R - 1][C] * aS * aS;
-            double gE = 0.0, gW = 0.0;
-            if (i + 1 < nx) gE = nr[ty][tx + 1] * (0.5 * (su[R - 1][C + 1] + su[R][C + 1])) * (0.5 * (vc + vE));
-            if (i > 0) gW = nr[ty][tx] * (0.5 * (su[R - 1][C] + su[R][C])) * (0.5 * (vc + vW));
-            const double muE = nm[ty][tx + 1], muW = nm[ty][tx];
-            const double adv = (fN - fS) * ih + (gE - gW) * ih;
-            const double vis = (sm[R][C] * (vN - vc) - sm[R - 1][C] * (vc - vS) + muE * (vE - vc) -
-                                muW * (vc - vW)) * ih2;
+            const double vc = sv[R][C];
+            const double adv = (fy[ty + 1][tx] - fy[ty][tx]) * ih + (gyn[ty][tx + 1] - gyn[ty][tx]) * ih;
+            const double vis = (vy[ty + 1][tx] - vy[ty][tx] + wyn[ty][tx + 1] - wyn[ty][tx]) * ih2;
             const double irf = by ? by[k] : recip_nr(0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
             vs[k] = vc + dt * ((vis - ae) * irf + gy);
