@@ -47,6 +47,12 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
     const double gz = gy + (frame ? frame[kFrS] : 0.0), wb = frame ? frame[kFrWb] : 0.0;
     __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
     __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
+    // fluxes two faces share, with their radius (as the planar predictor):
+    // radial momentum at cells i0-1 .. i0+PX-1 and nodes (i0 .. i0+PX-1,
+    // j0 .. j0+PY); axial momentum at cells j0-1 .. j0+PY-1 and nodes
+    // (i0 .. i0+PX, j0 .. j0+PY-1)
+    __shared__ double fx[PY][PX + 1], vx[PY][PX + 1], gxn[PY + 1][PX], wxn[PY + 1][PX];
+    __shared__ double fy[PY + 1][PX], vy[PY + 1][PX], gyn[PY][PX + 1], wyn[PY][PX + 1];
     const int i0 = blockIdx.x * PX, j0 = blockIdx.y * PY;
     const int t = threadIdx.y * PX + threadIdx.x;
     const long nxf = nx + 1;
@@ -79,6 +85,45 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
         else nm[r][c] = 0.0;
     }
     __syncthreads();
+    // radial momentum of cell (i0-1+c, j0+r) at its outer radius (gi + 1/2) h
+    for (int k = t; k < PY * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1), gi = i0 - 1 + c;
+        const double rc = (gi + 0.5) * h, a = 0.5 * (su[r + 1][c + 1] + su[r + 1][c]);
+        fx[r][c] = rc * sr[r + 1][c] * a * a;
+        vx[r][c] = rc * sm[r + 1][c] * (su[r + 1][c + 1] - su[r + 1][c]);
+    }
+    // axial momentum of cell (i0+c, j0-1+r) at the column's radius (gi + 1/2) h
+    for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
+        const int r = k / PX, c = k - r * PX, gi = i0 + c;
+        const double rc = (gi + 0.5) * h, a = 0.5 * (sv[r + 1][c + 1] + sv[r][c + 1]);
+        fy[r][c] = rc * sr[r][c + 1] * a * a;
+        vy[r][c] = rc * sm[r][c + 1] * (sv[r + 1][c + 1] - sv[r][c + 1]);
+    }
+    // radial momentum at node (I, J) = (i0+c, j0+r), radius I h: between
+    // u(I, J-1) and u(I, J); reflected ghost at the bottom and top walls
+    for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
+        const int r = k / PX, c = k - r * PX, I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double rn = I * h, ub = su[r][c + 1], ut = su[r + 1][c + 1];
+        gxn[r][c] = (J > 0 && J < ny)
+                        ? rn * nr[r][c] * (0.5 * (sv[r + 1][c] + sv[r + 1][c + 1])) * (0.5 * (ub + ut))
+                        : 0.0;
+        const double uT = J < ny ? ut : -ub, uB = J > 0 ? ub : -ut;
+        wxn[r][c] = rn * nm[r][c] * (uT - uB);
+    }
+    // axial momentum at node (I, J), radius I h: between v(I-1, J) and
+    // v(I, J); at the outer wall the ghost 2 wb - v, at the axis v itself
+    for (int k = t; k < PY * (PX + 1); k += PX * PY) {
+        const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
+        if (I > nx || J > ny) continue;
+        const double rn = I * h, vl = sv[r + 1][c], vr = sv[r + 1][c + 1];
+        gyn[r][c] = (I > 0 && I < nx)
+                        ? rn * nr[r][c] * (0.5 * (su[r][c + 1] + su[r + 1][c + 1])) * (0.5 * (vl + vr))
+                        : 0.0;
+        const double vR = I < nx ? vr : 2.0 * wb - vl, vL = I > 0 ? vl : vr;
+        wyn[r][c] = rn * nm[r][c] * (vR - vL);
+    }
+    __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
     if (i >= nx || j >= ny) return;
     const int R = ty + 1, C = tx + 1;
@@ -89,21 +134,11 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
         if (i == 0) {
             us[k] = 0.0; au[k] = 0.0;
         } else {
-            const double r0 = i * h, rE = (i + 0.5) * h, rW = (i - 0.5) * h;
-            const double uc = su[R][C], uE = su[R][C + 1], uW = su[R][C - 1];
-            const double uN = (j + 1 < ny) ? su[R + 1][C] : -uc;
-            const double uS = (j > 0) ? su[R - 1][C] : -uc;
-            const double aE = 0.5 * (uE + uc), aW = 0.5 * (uc + uW);
-            const double fE = rE * sr[R][C] * aE * aE, fW = rW * sr[R][C - 1] * aW * aW;
-            double gN = 0.0, gS = 0.0;
-            if (j + 1 < ny)
-                gN = r0 * nr[ty + 1][tx] * (0.5 * (sv[R + 1][C - 1] + sv[R + 1][C])) * (0.5 * (uc + uN));
-            if (j > 0) gS = r0 * nr[ty][tx] * (0.5 * (sv[R][C - 1] + sv[R][C])) * (0.5 * (uc + uS));
-            const double muN = nm[ty + 1][tx], muS = nm[ty][tx];
-            const double adv = ((fE - fW) + (gN - gS)) / (r0 * h);
+            const double r0 = i * h;
+            const double uc = su[R][C];
+            const double adv = ((fx[ty][tx + 1] - fx[ty][tx]) + (gxn[ty + 1][tx] - gxn[ty][tx])) / (r0 * h);
             const double muf = 0.5 * (sm[R][C - 1] + sm[R][C]);
-            const double vis = (rE * sm[R][C] * (uE - uc) - rW * sm[R][C - 1] * (uc - uW) +
-                                r0 * muN * (uN - uc) - r0 * muS * (uc - uS)) / (r0 * h2) -
+            const double vis = (vx[ty][tx + 1] - vx[ty][tx] + wxn[ty + 1][tx] - wxn[ty][tx]) / (r0 * h2) -
                                muf * uc / (r0 * r0);
             // 1 / rho_face: the plain face coefficient beta when given
             const double irf = bx ? bx[k] : 1.0 / (0.5 * (sr[R][C - 1] + sr[R][C]));
@@ -119,20 +154,10 @@ k_predictor_axi(int nx, int ny, double h, double dt, const double *__restrict__ 
         if (j == 0) {
             vs[k] = wb; av[k] = 0.0;
         } else {
-            const double r0 = (i + 0.5) * h, rE = (i + 1) * h, rW = i * h;
-            const double vc = sv[R][C], vN = sv[R + 1][C], vS = sv[R - 1][C];
-            const double vE = (i + 1 < nx) ? sv[R][C + 1] : 2.0 * wb - vc;
-            const double vW = (i > 0) ? sv[R][C - 1] : vc;  // symmetric across the axis
-            const double aN = 0.5 * (vN + vc), aS = 0.5 * (vc + vS);
-            const double fN = r0 * sr[R][C] * aN * aN, fS = r0 * sr[R - 1][C] * aS * aS;
-            double gE = 0.0, gW = 0.0;
-            if (i + 1 < nx)
-                gE = rE * nr[ty][tx + 1] * (0.5 * (su[R - 1][C + 1] + su[R][C + 1])) * (0.5 * (vc + vE));
-            if (i > 0) gW = rW * nr[ty][tx] * (0.5 * (su[R - 1][C] + su[R][C])) * (0.5 * (vc + vW));
-            const double muE = nm[ty][tx + 1], muW = nm[ty][tx];
-            const double adv = ((fN - fS) + (gE - gW)) / (r0 * h);
-            const double vis = (r0 * sm[R][C] * (vN - vc) - r0 * sm[R - 1][C] * (vc - vS) +
-                                rE * muE * (vE - vc) - rW * muW * (vc - vW)) / (r0 * h2);
+            const double r0 = (i + 0.5) * h;
+            const double vc = sv[R][C];
+            const double adv = ((fy[ty + 1][tx] - fy[ty][tx]) + (gyn[ty][tx + 1] - gyn[ty][tx])) / (r0 * h);
+            const double vis = (vy[ty + 1][tx] - vy[ty][tx] + wyn[ty][tx + 1] - wyn[ty][tx]) / (r0 * h2);
             const double irf = by ? by[k] : 1.0 / (0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
             vs[k] = vc + dt * ((vis - ae) * irf + gz);
