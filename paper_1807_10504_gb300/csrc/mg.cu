@@ -1206,7 +1206,11 @@ k_sub_mean(long n, const double *__restrict__ b, const double *__restrict__ sum,
            double *__restrict__ r0, double h2, const double *__restrict__ invd,
            double *__restrict__ bt, double *part, unsigned *count, double *out)
 {
-    const double m = *sum / (double)n;
+    // the mean once per block (one FP64 division, the same value everywhere)
+    __shared__ double mb;
+    if (threadIdx.x == 0) mb = *sum / (double)n;
+    __syncthreads();
+    const double m = mb;
     double s = 0.0;
     for (long k = (long)blockIdx.x * kRedT + threadIdx.x; k < n; k += (long)gridDim.x * kRedT) {
         double v = b[k] - m;
@@ -1220,8 +1224,11 @@ k_sub_mean(long n, const double *__restrict__ b, const double *__restrict__ sum,
 __global__ void k_apply_mean(long n, double *__restrict__ p, const double *__restrict__ sum,
                              double *__restrict__ dst)
 {
+    __shared__ double mb;  // the mean once per block
+    if (threadIdx.x == 0) mb = *sum / (double)n;
+    __syncthreads();
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) dst[k] = p[k] - *sum / (double)n;
+    if (k < n) dst[k] = p[k] - mb;
 }
 
 // sum (b0 - A p)^2 over the fine grid, FP64, into res[2].  With rf != NULL
@@ -1258,8 +1265,11 @@ __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restric
 __global__ void k_finalize(long n, const double *__restrict__ e0, const double *__restrict__ sum,
                            const SolveCtl *__restrict__ ctl, double *__restrict__ p)
 {
+    __shared__ double mb;  // the mean once per block
+    if (threadIdx.x == 0) mb = *sum / (double)n;
+    __syncthreads();
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) p[k] = ctl->zero_p ? 0.0 : e0[k] - *sum / (double)n;
+    if (k < n) p[k] = ctl->zero_p ? 0.0 : e0[k] - mb;
 }
 
 // The other buffer of a level's iterate (sweeps read one and write the other).
