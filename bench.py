@@ -424,10 +424,8 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.set_markers_host(Xh, Yh)
-        ctx.ns_step(dt, 1, args.warm)
-        ctx.get_host("p", ph)
-        ctx.get_markers_host(Xh, Yh)
+        # one call per step: markers in, the step, pressure and markers out
+        ctx.ns_step_io(dt, args.warm, Xh, Yh, ph, Xh, Yh)
     barrier()
     e2e_t = max_over_ranks(time.perf_counter() - t0)
 

@@ -214,6 +214,18 @@ ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
  * exist).  The last step's cycles and residual are returned by
  * ib_last_solve.                                                           */
 ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
+
+/* One time step as ns_step(ctx, dt, 1, warm) with host buffers (pinned
+ * memory lets the copies run asynchronously): X_in, Y_in (M doubles each,
+ * or both NULL) replace the markers first, after the same host checks as
+ * ib_set_markers; p_out (nx*ny doubles, row-major), X_out, Y_out (M each;
+ * either may be NULL, X_out and Y_out together) receive the step's pressure
+ * and markers.  The copies are queued on the context's stream around the
+ * step, which synchronises with the host once at its end; the buffers are
+ * the caller's and must stay valid until the call returns.  Errors as
+ * ns_step; IB_EINVAL for an unpaired marker buffer.                       */
+ib_status ns_step_io(ib_ctx *ctx, double dt, int warm, const double *X_in, const double *Y_in,
+                     double *p_out, double *X_out, double *Y_out);
 /* Non-inertial frame (cfg.frame = 1): out[0] drop 0's axial centre of mass,
  * out[1] the acceleration S of the next step, out[2] the frame velocity Vf
  * (the drop's velocity in the laboratory, up to its small drift in the

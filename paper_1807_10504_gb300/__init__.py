@@ -37,7 +37,7 @@ EXPORTS = [
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
-    "ib_mass_correct", "ib_op_cn_solve",
+    "ib_mass_correct", "ib_op_cn_solve", "ns_step_io",
 ]
 
 
@@ -86,6 +86,7 @@ def lib():
             "ib_heaviside": [_P, _P], "ib_relocate": [_P], "mg_setup": [_P, _P, _P],
             "mg_solve": [_P, _P, _P, C.c_int, _d, C.c_int, C.POINTER(C.c_int), C.POINTER(_d)],
             "ns_step": [_P, _d, C.c_int, C.c_int],
+            "ns_step_io": [_P, _d, C.c_int, _P, _P, _P, _P, _P],
             "ib_last_solve": [_P, C.POINTER(C.c_int), C.POINTER(_d)],
             "ib_save": [_P, C.c_char_p], "ib_load": [_P, C.c_char_p],
             "ib_op_coeffs": [_i32, _i32, _d, _d, _d, _d, _P, _P, _P, _P, _P, _P],
@@ -345,6 +346,22 @@ class Context:
 
     def ns_step(self, dt, nsteps=1, warm=1):
         _check(lib().ns_step(self._h, dt, nsteps, warm), self._h)
+        cyc, rr = C.c_int(0), C.c_double(0.0)
+        lib().ib_last_solve(self._h, C.byref(cyc), C.byref(rr))
+        return cyc.value, rr.value
+
+    def ns_step_io(self, dt, warm=1, X=None, Y=None, p_out=None, X_out=None, Y_out=None):
+        """One time step with host numpy buffers (see ns_step_io): optional
+        markers in, optional pressure and markers out; returns (cycles,
+        relative residual) of the step's solve."""
+        def ptr(a):
+            if a is None:
+                return None
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be C-contiguous float64")
+            return a.ctypes.data
+        _check(lib().ns_step_io(self._h, dt, warm, ptr(X), ptr(Y), ptr(p_out), ptr(X_out),
+                                ptr(Y_out)), self._h)
         cyc, rr = C.c_int(0), C.c_double(0.0)
         lib().ib_last_solve(self._h, C.byref(cyc), C.byref(rr))
         return cyc.value, rr.value

@@ -795,7 +795,11 @@ ib_status mg_solve(ib_ctx *c, const double *rhs, double *p, int precision, doubl
     return st;
 }
 
-ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
+}  // extern "C"
+
+namespace {
+
+ib_status step_args(ib_ctx *c, double dt, int nsteps, int warm)
 {
     if (!c || !(dt > 0) || nsteps < 0 || warm < 0 || warm > 3) return IB_EINVAL;
     if (warm == 2 && c->cfg.axisym)
@@ -803,44 +807,91 @@ ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
     if (warm == 2 && (!c->cnn || c->cfg.nx != c->cfg.ny || c->cfg.nx % (4 << c->cnn->coarsen) != 0))
         return fail(c, IB_EINVAL, "warm start 2 needs an attached network and a square grid "
                                   "(side a multiple of 4 * 2^coarsen)");
+    return IB_OK;
+}
+
+// One time step; before_flags enqueues work on c->s ahead of the step's
+// final host synchronisation (the marker flags read).
+template <typename F>
+ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
+{
     const ib_config &g = c->cfg;
+    const bool reloc = g.relocate_every > 0 && c->step % g.relocate_every == 0;
+    const bool mass = g.mass_every > 0 && c->step > 0 && c->step % g.mass_every == 0;
+    // the launches before the pressure solve replay a recorded graph once
+    // the step's shape has been seen (not with the indicator's inner solve
+    // or the network, which synchronise with the host)
+    const bool rec = c->have_prev && !g.indicator && warm != 2;
+    const int key = (reloc ? 1 : 0) | (mass ? 2 : 0) | (warm == 0 ? 4 : 0);
+    ib_status st = rec ? run_recorded(c, dt, key, [&] { return step_pre(c, dt, reloc, mass, warm); })
+                       : step_pre(c, dt, reloc, mass, warm);
+    if (st != IB_OK) return st;
+    if (warm == 2) {
+        cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
+        if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
+    }
+    if (warm == 3) {
+        // p0 = 2 p^n - p^(n-1) once two pressures are known, else p^n
+        const long n = (long)g.nx * g.ny;
+        if (c->have_pprev) launch_extrapolate(n, c->p, c->pprev, c->s);
+        else cudaMemcpyAsync(c->pprev, c->p, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->s);
+        c->have_pprev = true;
+    } else {
+        c->have_pprev = false;
+    }
+    st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
+                &c->last_cycles, &c->last_relres, c->s, c->err);
+    if (st != IB_OK && st != IB_ENOTCONV) return st;
+    const ib_status sp = rec ? run_recorded(c, dt, 64, [&] { return step_post(c, dt); })
+                             : step_post(c, dt);
+    if (sp != IB_OK) return sp;
+    c->have_prev = 1;
+    c->step++;
+    before_flags();
+    ib_status fs = read_flags(c);
+    if (fs != IB_OK) return fs;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+ib_status ns_step(ib_ctx *c, double dt, int nsteps, int warm)
+{
+    ib_status st = step_args(c, dt, nsteps, warm);
+    if (st != IB_OK) return st;
     for (int it = 0; it < nsteps; it++) {
-        const bool reloc = g.relocate_every > 0 && c->step % g.relocate_every == 0;
-        const bool mass = g.mass_every > 0 && c->step > 0 && c->step % g.mass_every == 0;
-        // the launches before the pressure solve replay a recorded graph once
-        // the step's shape has been seen (not with the indicator's inner solve
-        // or the network, which synchronise with the host)
-        const bool rec = c->have_prev && !g.indicator && warm != 2;
-        const int key = (reloc ? 1 : 0) | (mass ? 2 : 0) | (warm == 0 ? 4 : 0);
-        ib_status st = rec ? run_recorded(c, dt, key, [&] { return step_pre(c, dt, reloc, mass, warm); })
-                           : step_pre(c, dt, reloc, mass, warm);
-        if (st != IB_OK) return st;
-        if (warm == 2) {
-            cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
-            if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
-        }
-        if (warm == 3) {
-            // p0 = 2 p^n - p^(n-1) once two pressures are known, else p^n
-            const long n = (long)g.nx * g.ny;
-            if (c->have_pprev) launch_extrapolate(n, c->p, c->pprev, c->s);
-            else cudaMemcpyAsync(c->pprev, c->p, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->s);
-            c->have_pprev = true;
-        } else {
-            c->have_pprev = false;
-        }
-        st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
-                    &c->last_cycles, &c->last_relres, c->s, c->err);
-        if (st != IB_OK && st != IB_ENOTCONV) return st;
-        const ib_status sp = rec ? run_recorded(c, dt, 64, [&] { return step_post(c, dt); })
-                                 : step_post(c, dt);
-        if (sp != IB_OK) return sp;
-        c->have_prev = 1;
-        c->step++;
-        ib_status fs = read_flags(c);
-        if (fs != IB_OK) return fs;
+        st = step_one(c, dt, warm, [] {});
         if (st != IB_OK) return st;
     }
     return IB_OK;
+}
+
+ib_status ns_step_io(ib_ctx *c, double dt, int warm, const double *X_in, const double *Y_in,
+                     double *p_out, double *X_out, double *Y_out)
+{
+    ib_status st = step_args(c, dt, 1, warm);
+    if (st != IB_OK) return st;
+    if ((X_in == nullptr) != (Y_in == nullptr) || (X_out == nullptr) != (Y_out == nullptr))
+        return fail(c, IB_EINVAL, "marker buffers come in pairs (X and Y)");
+    const size_t mb = (size_t)c->mk.M * 8;
+    if (X_in) {
+        st = check_markers_host(c, c->cfg, X_in, Y_in, c->mk.drop_start_h.data(), c->mk.ndrops);
+        if (st != IB_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(c->mk.X, X_in, mb, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->mk.Y, Y_in, mb, cudaMemcpyHostToDevice, c->s);
+        if (e != cudaSuccess) return cuda_check(c, e, "markers in");
+    }
+    cudaError_t ce = cudaSuccess;
+    st = step_one(c, dt, warm, [&] {
+        const size_t pb = (size_t)c->cfg.nx * c->cfg.ny * 8;
+        if (p_out) ce = cudaMemcpyAsync(p_out, c->p, pb, cudaMemcpyDeviceToHost, c->s);
+        if (X_out && ce == cudaSuccess) ce = cudaMemcpyAsync(X_out, c->mk.X, mb, cudaMemcpyDeviceToHost, c->s);
+        if (Y_out && ce == cudaSuccess) ce = cudaMemcpyAsync(Y_out, c->mk.Y, mb, cudaMemcpyDeviceToHost, c->s);
+    });
+    if (ce != cudaSuccess) return cuda_check(c, ce, "results out");
+    return st;
 }
 
 unsigned long long ib_launch_count(void) { return launch_count(); }

@@ -164,3 +164,34 @@ def test_extrapolated_warm_start_reaches_the_same_solution(T, ib):
     p1, p3 = out[1][0], out[3][0]
     assert np.abs(p1 - p3).max() <= 1e-7 * np.abs(p1).max()
     assert out[3][2] <= out[1][2]
+
+
+def test_ns_step_io_matches_separate_calls(T, ib):
+    """ns_step_io (markers in, step, pressure and markers out, one host
+    synchronisation) against ib_set_markers + ns_step + ib_get_field +
+    ib_get_markers on an identical context: bit-identical results, including
+    a relocation step; an unpaired marker buffer is rejected."""
+    n = 64
+    mk = W.oscillating_drop(128, 0.2, 0.05, 1e-3, 1808)
+    dt = W.capillary_dt(1.0 / n, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    ctxs = [ib.Context(ib.Config(nx=n, ny=n, h=1.0 / n, relocate_every=2, precision=2, tol=1e-10),
+                       mk.X, mk.Y, mk.drop_start) for _ in range(2)]
+    pin = lambda shape: T.empty(shape, dtype=T.float64).pin_memory().numpy()
+    M = ctxs[0].M
+    Xa, Ya, Xb, Yb = pin(M), pin(M), pin(M), pin(M)
+    pa, pb = pin((n, n)), pin((n, n))
+    ctxs[0].get_markers_host(Xa, Ya)
+    ctxs[1].get_markers_host(Xb, Yb)
+    for _ in range(3):
+        ctxs[0].set_markers_host(Xa, Ya)
+        ctxs[0].ns_step(dt, 1, 1)
+        ctxs[0].get_host("p", pa)
+        ctxs[0].get_markers_host(Xa, Ya)
+        ctxs[1].ns_step_io(dt, 1, Xb, Yb, pb, Xb, Yb)
+        assert np.array_equal(pa, pb)
+        assert np.array_equal(Xa, Xb) and np.array_equal(Ya, Yb)
+    with pytest.raises(ib.IBError) as e:
+        ctxs[1].ns_step_io(dt, 1, Xb, None)
+    assert e.value.status == ib.IB_EINVAL
+    for c in ctxs:
+        c.close()
