@@ -55,6 +55,7 @@ struct ib_ctx {
     // predictor, spreading and right-hand side run on s
     cudaStream_t s2 = nullptr, s3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
+    cudaEvent_t ev_sort_fork = nullptr, ev_sort_join = nullptr;  // the marker sort on s2
     // recorded step phases (see run_recorded) and their capture stream
     std::vector<StepGraph> sgraphs;
     cudaStream_t cap = nullptr;
@@ -364,8 +365,15 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
         if (g.axisym) launch_axi_symmetrise(mk, c->s);
     }
     if (mass) mass_correct(c, nullptr);
+    // the marker sort (integer work on the positions) on s2 next to the
+    // curvature and segment records; both read only X, Y and write disjoint
+    // arrays; they join before the band pairs, which need both
+    cudaEventRecord(c->ev_sort_fork, c->s);
+    cudaStreamWaitEvent(c->s2, c->ev_sort_fork, 0);
+    launch_sort(mk, c->s2);
+    cudaEventRecord(c->ev_sort_join, c->s2);
     geometry(c);
-    launch_sort(mk, c->s);
+    cudaStreamWaitEvent(c->s, c->ev_sort_join, 0);
     heaviside_into(c, c->H);
     const double *prop = c->H;
     if (g.indicator) {
@@ -507,6 +515,8 @@ void ib_destroy(ib_ctx *c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
+    if (c->ev_sort_fork) cudaEventDestroy(c->ev_sort_fork);
+    if (c->ev_sort_join) cudaEventDestroy(c->ev_sort_join);
     if (c->s2) cudaStreamDestroy(c->s2);
     if (c->s3) cudaStreamDestroy(c->s3);
     if (c->flags_host) cudaFreeHost(c->flags_host);
@@ -622,6 +632,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
         c->A0 = (double *)c->dmem;
