@@ -56,6 +56,7 @@ struct ib_ctx {
     cudaStream_t s2 = nullptr, s3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     cudaEvent_t ev_sort_fork = nullptr, ev_sort_join = nullptr;  // the marker sort on s2
+    cudaEvent_t ev_rows_fork = nullptr, ev_rows_join = nullptr;  // the rows inside on s3
     // recorded step phases (see run_recorded) and their capture stream
     std::vector<StepGraph> sgraphs;
     cudaStream_t cap = nullptr;
@@ -228,10 +229,10 @@ void geometry(ib_ctx *c)
 void heaviside_into(ib_ctx *c, double *H)
 {
     if (!c->cfg.axisym) {
-        launch_heaviside(c->mk, H, c->s);
+        launch_heaviside(c->mk, H, c->s, c->s3, c->ev_rows_fork, c->ev_rows_join);
         return;
     }
-    launch_heaviside(c->mk, c->Hw, c->s);
+    launch_heaviside(c->mk, c->Hw, c->s, c->s3, c->ev_rows_fork, c->ev_rows_join);
     launch_axi_fold(c->cfg.nx, c->cfg.ny, c->G, c->cfg.h, 0, c->Hw, nullptr, nullptr, H, nullptr,
                     nullptr, c->s);
 }
@@ -517,6 +518,8 @@ void ib_destroy(ib_ctx *c)
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->ev_sort_fork) cudaEventDestroy(c->ev_sort_fork);
     if (c->ev_sort_join) cudaEventDestroy(c->ev_sort_join);
+    if (c->ev_rows_fork) cudaEventDestroy(c->ev_rows_fork);
+    if (c->ev_rows_join) cudaEventDestroy(c->ev_rows_join);
     if (c->s2) cudaStreamDestroy(c->s2);
     if (c->s3) cudaStreamDestroy(c->s3);
     if (c->flags_host) cudaFreeHost(c->flags_host);
@@ -634,6 +637,8 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
         c->A0 = (double *)c->dmem;

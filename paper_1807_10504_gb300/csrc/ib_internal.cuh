@@ -280,7 +280,8 @@ void launch_interp(const Markers &mk, int kernel, const double *u,
                    cudaStream_t s);
 void launch_spread_conv(const Markers &mk, int kernel, const double *fmag,
                         double *Fx, double *Fy, cudaStream_t s);
-void launch_heaviside(const Markers &mk, double *H, cudaStream_t s);
+void launch_heaviside(const Markers &mk, double *H, cudaStream_t s, cudaStream_t side = nullptr,
+                      cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 void launch_band_area(const Markers &mk, cudaStream_t s);
 void launch_spread_irrot(const Markers &mk, const double *fmag, const double *H,
                          double *Fx, double *Fy, cudaStream_t s);

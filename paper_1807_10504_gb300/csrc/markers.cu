@@ -1618,11 +1618,22 @@ void launch_band_area(const Markers &mk, cudaStream_t s)
                                                  mk.pcov);
 }
 
-void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
+void launch_heaviside(const Markers &mk, double *H, cudaStream_t s, cudaStream_t side,
+                      cudaEvent_t ev_fork, cudaEvent_t ev_join)
 {
+    // the scanline fill of the rows inside the drops needs neither the
+    // sort nor the segment records: with a side stream it runs next to the
+    // band kernels, joining before the band sum that reads its H
+    cudaStream_t sr = s;
+    if (side) {
+        cudaEventRecord(ev_fork, s);
+        cudaStreamWaitEvent(side, ev_fork, 0);
+        sr = side;
+    }
     note_launch();
-    k_rows_inside<<<mk.ny, kT, 0, s>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.ykey,
-                                       mk.next, mk.drop_start, mk.dyk, H, mk.flags);
+    k_rows_inside<<<mk.ny, kT, 0, sr>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.ykey,
+                                        mk.next, mk.drop_start, mk.dyk, H, mk.flags);
+    if (side) cudaEventRecord(ev_join, side);
     dim3 g(mk.bnx, mk.bny);
     cudaMemsetAsync(mk.npairs, 0, sizeof(uint32_t), s);
     note_launch();
@@ -1630,6 +1641,7 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s)
                                    mk.scvx, mk.sbox, mk.pair_cap, mk.npairs, mk.pseg, mk.pcell,
                                    mk.crange, mk.flags);
     launch_band_area(mk, s);
+    if (side) cudaStreamWaitEvent(s, ev_join, 0);
     note_launch();
     k_band_sum<<<g, kBT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.crange, mk.pacc, mk.pcov, H);
 }
