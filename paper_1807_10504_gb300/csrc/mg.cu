@@ -1717,9 +1717,10 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
 void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
 {
     const int L = mg.L;
-    // levels above 4096 cells one launch each, the rest in one CTA
+    // levels above 1024 cells one launch each (their FP64 work spread over
+    // the SMs), the rest in one CTA
     int lsmall = 1;
-    while (lsmall < L && (long)mg.lv[lsmall].nx * mg.lv[lsmall].ny > 4096) lsmall++;
+    while (lsmall < L && (long)mg.lv[lsmall].nx * mg.lv[lsmall].ny > 1024) lsmall++;
     for (int l = 0; l < lsmall; l++) {
         Level &v = mg.lv[l];
         const double *fbx = l == 0 ? bx : mg.lv[l - 1].d.bx, *fby = l == 0 ? by : mg.lv[l - 1].d.by;
