@@ -266,7 +266,6 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
               float *__restrict__ rc, float *__restrict__ ecz, const float *__restrict__ ecp,
               double *__restrict__ p64, const __grid_constant__ TileMaps tm)
 {
-    pdl_enter();
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
     constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
     constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA;
@@ -332,17 +331,24 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         }
         __syncthreads();  // the barrier is initialised before any thread waits on it
+        // the coefficients (1/diag, beta_y, beta_x) are built before the
+        // solve and not written during it: their copies start before the
+        // wait for the previous grid, overlapping its tail; the iterate and
+        // right-hand side it writes follow the wait
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::);
             constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                          ::"r"(smem_addr(&bar)), "r"(kBytes));
-            tma_load2(&ps[0][0], &tm.p, gi0, gj0, &bar);
-            tma_load2(&bs[0][0], &tm.b, gi0, gj0, &bar);
             tma_load2(&ds[0][0], &tm.d, gi0, gj0, &bar);
             tma_load2(&ys[0][0], &tm.y, gi0, gj0, &bar);
         }
         load_xfaces();
+        pdl_enter();
+        if (threadIdx.x == 0) {
+            tma_load2(&ps[0][0], &tm.p, gi0, gj0, &bar);
+            tma_load2(&bs[0][0], &tm.b, gi0, gj0, &bar);
+        }
         // the prolongation of the coarse correction overlaps the copies
         constexpr int NPRO = MODE == 2 ? (PH * PW + FT - 1) / FT : 1;
         float pc[NPRO];
@@ -369,6 +375,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         }
         __syncthreads();
     } else {
+        pdl_enter();
         // rows of a multiple of 4 cells: every 4-cell chunk of the window
         // (gi0 and the window width are multiples of 4) lies wholly inside or
         // wholly outside the grid
@@ -1027,19 +1034,18 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs<T> g)
 {
     using P2 = typename Pair<T>::V;
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char tail_sm[];
     __shared__ double xs[kMaxCoarsest];
     T *sm = reinterpret_cast<T *>(tail_sm);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int L = g.nl, lc = L - 1, nco = g.nx[lc] * g.ny[lc];
     const double *ainv = g.inv_off >= 0 ? reinterpret_cast<const double *>(tail_sm + g.inv_off) : g.ainvT;
+    // the coefficients and the coarsest inverse are built before the solve
+    // and not written during it: they are staged before the wait for the
+    // previous grid (overlapping its tail); the level-lt iterate and
+    // right-hand side it writes after the wait
     if (g.inv_off >= 0)
         stage_array(reinterpret_cast<double *>(tail_sm + g.inv_off), g.ainvT, nco * nco, tid, nthr);
-    if (g.lt == lc) {
-        stage_array(sm + g.off[lc], g.e[lc], nco, tid, nthr);
-        stage_array(sm + g.off[lc] + nco, g.r[lc], nco, tid, nthr);
-    }
     // pairs of row neighbours of all split levels, numbered level by level;
     // a batch of kStage pairs per thread has all its loads in flight before
     // its stores
@@ -1047,7 +1053,7 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs<
     int npairs = 0;
     for (int l = g.lt; l < lc; l++) npairs += g.nx[l] * g.ny[l] / 2;
     for (int base = 0; base < npairs; base += kStage * nthr) {
-        P2 d[kStage], yn[kStage], ev[kStage], rv[kStage];
+        P2 d[kStage], yn[kStage];
         T x0[kStage], x1[kStage];
         int s0[kStage], s1[kStage], lv[kStage];
 #pragma unroll
@@ -1066,10 +1072,6 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs<
             yn[u] = __ldg(reinterpret_cast<const P2 *>(g.by[l] + k + nx));
             x0[u] = __ldg(g.bx[l] + (long)j * (nx + 1) + i + 1);
             x1[u] = __ldg(g.bx[l] + (long)j * (nx + 1) + i + 2);
-            if (l == g.lt) {
-                ev[u] = __ldg(reinterpret_cast<const P2 *>(g.e[l] + k));
-                rv[u] = __ldg(reinterpret_cast<const P2 *>(g.r[l] + k));
-            }
         }
 #pragma unroll
         for (int u = 0; u < kStage; u++) {
@@ -1079,10 +1081,24 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs<
             v.iv[s0[u]] = d[u].x; v.iv[s1[u]] = d[u].y;
             v.cy[s0[u]] = yn[u].x; v.cy[s1[u]] = yn[u].y;
             v.cx[s0[u]] = x0[u]; v.cx[s1[u]] = x1[u];
-            if (l == g.lt) {
-                v.e[s0[u]] = ev[u].x; v.e[s1[u]] = ev[u].y;
-                v.r[s0[u]] = rv[u].x; v.r[s1[u]] = rv[u].y;
-            }
+        }
+    }
+    pdl_enter();
+    if (g.lt == lc) {
+        stage_array(sm + g.off[lc], g.e[lc], nco, tid, nthr);
+        stage_array(sm + g.off[lc] + nco, g.r[lc], nco, tid, nthr);
+    } else {
+        // the level-lt iterate and right-hand side, pairs of row neighbours
+        const int nx = g.nx[g.lt], hx = nx / 2, n = nx * g.ny[g.lt], bl = n / 2 + kTailPad;
+        const TailLv<T> v = tail_lv(g, sm, g.lt);
+        Walk w(tid, nthr, hx);
+        for (int q = tid; q < n / 2; q += nthr, w.next()) {
+            const int j = w.a, m = w.b, k = j * nx + 2 * m, c = j & 1;
+            const P2 ev = *reinterpret_cast<const P2 *>(g.e[g.lt] + k);
+            const P2 rv = *reinterpret_cast<const P2 *>(g.r[g.lt] + k);
+            const int s0 = c * bl + j * hx + m, s1 = (1 - c) * bl + j * hx + m;
+            v.e[s0] = ev.x; v.e[s1] = ev.y;
+            v.r[s0] = rv.x; v.r[s1] = rv.y;
         }
     }
     asm volatile("cp.async.wait_all;\n" ::);
