@@ -171,7 +171,8 @@ void or_prolong_add(int nxc, int nyc, const double *ec, double *ef)
         }
 }
 
-/* Levels halve both sides while both are even and at least 8.              */
+/* Levels halve both sides while both are even and the level has more than
+ * 16 cells.                                                                 */
 int or_mg_levels(int nx, int ny, int *nxs, int *nys, int maxlev)
 {
     int L = 0;
