@@ -4,7 +4,8 @@ Ong & Miura (arXiv 1807.10504).
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA library and never imports it.  The arithmetic lives in
-``ib_oracle.c`` (built with ``-O2 -ffp-contract=off``); this module is argument
+``ib_oracle.c`` (built with ``-O3 -ffp-contract=off``; a second build adds
+``-fopenmp`` for the timed CPU baseline on all host cores); this module is argument
 marshalling plus the composition of one time step (Section 2.1 fractional
 step with the force in the projection, Section 3.2).
 """
@@ -21,26 +22,48 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ib_oracle.c")
 _SRC_AXI = os.path.join(_HERE, "ib_oracle_axi.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 IB_OK, IB_EINVAL, IB_ENOMEM, IB_ENOTCONV, IB_ENAN, IB_EMARKER = 0, 1, 2, 3, 4, 5
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, no contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, -O3, no
+    multiply-add contraction).  With ``openmp``, the same source with
+    ``-fopenmp`` into ``oracle/liboracle_omp.so``: its loops over independent
+    cells, faces or markers run on all host cores, with results identical bit
+    for bit (every sum keeps its serial order).  Returns the library path, or
+    raises if the compiler fails."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
         os.path.getmtime(_SRC), os.path.getmtime(_SRC_AXI),
         os.path.getmtime(os.path.join(_HERE, "ib_oracle.h"))
     ):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, _SRC_AXI, "-lm"]
+            ["gcc", "-O3", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+             *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, _SRC_AXI, "-lm"]
         )
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+def set_threads(openmp: bool) -> None:
+    """Route every following oracle call to the serial library (default) or
+    to its OpenMP build (all host cores; same results)."""
+    global _variant
+    _variant = "omp" if openmp else "serial"
+
+
+def threads() -> int:
+    """Host threads the current variant uses."""
+    if _variant == "serial":
+        return 1
+    return int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+
+
+_libs = {}
+_variant = "serial"
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 _I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -48,9 +71,9 @@ _i, _d = C.c_int, C.c_double
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+    L = _libs.get(_variant)
+    if L is None:
+        L = C.CDLL(build(openmp=_variant == "omp"))
         sig = {
             "or_phi": (_d, [_i, _d]),
             "or_heaviside_profile": (_d, [_d]),
@@ -102,8 +125,8 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-        _lib = L
-    return _lib
+        _libs[_variant] = L
+    return L
 
 
 def _f64(a):

@@ -6,7 +6,11 @@
  * CPU-baseline leg of the benchmark; never by the product path.  Written for
  * clarity, not speed: every routine is the definition (or the algorithm's
  * steps in the paper's order) with no blocking, fusion or reordering.  Built
- * with -O2 -ffp-contract=off so that no multiply-add is contracted.
+ * with -O3 -ffp-contract=off so that no multiply-add is contracted.  The
+ * OpenMP pragmas mark loops whose iterations touch disjoint outputs (cells
+ * of one colour, faces, markers); a build with -fopenmp runs them on all host
+ * cores for the timed CPU baseline with results identical bit for bit (no
+ * sum changes its order); without -fopenmp they are ignored.
  *
  * Parity status: every routine here is pinned by a CPU test against a closed
  * form, an invariant or a brute-force computation (tests/test_oracle_*.py),
@@ -86,6 +90,7 @@ void or_coeffs(int nx, int ny, double rho_g, double rho_l, double mu_g,
 void or_apply_A(int nx, int ny, double h, const double *bx, const double *by,
                 const double *p, double *out)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             double c = p[CC(i, j)];
@@ -102,6 +107,7 @@ void or_residual(int nx, int ny, double h, const double *bx, const double *by,
                  const double *b, const double *p, double *r)
 {
     or_apply_A(nx, ny, h, bx, by, p, r);
+    #pragma omp parallel for schedule(static)
     for (size_t k = 0; k < (size_t)nx * ny; k++) r[k] = b[k] - r[k];
 }
 
@@ -113,6 +119,7 @@ void or_rbgs(int nx, int ny, double h, const double *bx, const double *by,
 {
     for (int s = 0; s < nsweeps; s++)
         for (int color = 0; color < 2; color++)
+            #pragma omp parallel for schedule(static)
             for (int j = 0; j < ny; j++)
                 for (int i = 0; i < nx; i++) {
                     if (((i + j) & 1) != color) continue;
@@ -129,6 +136,7 @@ void or_rbgs(int nx, int ny, double h, const double *bx, const double *by,
 void or_restrict(int nx, int ny, const double *r, double *rc)
 {
     int nxc = nx / 2, nyc = ny / 2;
+    #pragma omp parallel for schedule(static)
     for (int J = 0; J < nyc; J++)
         for (int I = 0; I < nxc; I++)
             rc[(size_t)J * nxc + I] =
@@ -157,6 +165,7 @@ void or_coarsen_beta(int nx, int ny, const double *bx, const double *by,
 void or_prolong_add(int nxc, int nyc, const double *ec, double *ef)
 {
     int nx = 2 * nxc, ny = 2 * nyc;
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int I = i / 2, J = j / 2;
@@ -304,6 +313,7 @@ static void vcycle_d(olev *L, int l, int nl, int nu1, int nu2)
 static void apply_A_f(int nx, int ny, float h, const float *bx, const float *by,
                       const float *p, float *out)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             float c = p[CC(i, j)];
@@ -321,6 +331,7 @@ static void rbgs_f(int nx, int ny, float h, const float *bx, const float *by,
 {
     for (int s = 0; s < nsweeps; s++)
         for (int color = 0; color < 2; color++)
+            #pragma omp parallel for schedule(static)
             for (int j = 0; j < ny; j++)
                 for (int i = 0; i < nx; i++) {
                     if (((i + j) & 1) != color) continue;
@@ -355,7 +366,9 @@ static void vcycle_f(olev *L, int l, int nl, int nu1, int nu2)
     float h = (float)f->h;
     rbgs_f(nx, ny, h, f->bxf, f->byf, f->rf, f->ef, nu1);
     apply_A_f(nx, ny, h, f->bxf, f->byf, f->ef, f->tf);
+    #pragma omp parallel for schedule(static)
     for (size_t k = 0; k < (size_t)nx * ny; k++) f->tf[k] = f->rf[k] - f->tf[k];
+    #pragma omp parallel for schedule(static)
     for (int J = 0; J < c->ny; J++)
         for (int I = 0; I < c->nx; I++)
             c->rf[(size_t)J * c->nx + I] =
@@ -364,6 +377,7 @@ static void vcycle_f(olev *L, int l, int nl, int nu1, int nu2)
     memset(c->ef, 0, (size_t)c->nx * c->ny * sizeof(float));
     vcycle_f(L, l + 1, nl, nu1, nu2);
     int nxc = c->nx, nyc = c->ny;
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int I = i / 2, J = j / 2;
@@ -478,6 +492,7 @@ void or_rhs(int nx, int ny, double h, double dt, const double *us,
             const double *vs, const double *Fx, const double *Fy,
             const double *bx, const double *by, double *b)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             double divu = (us[XF(i + 1, j)] - us[XF(i, j)] + vs[YF(i, j + 1)] - vs[YF(i, j)]) / h;
@@ -492,12 +507,14 @@ void or_correct(int nx, int ny, double h, double dt, const double *us,
                 const double *Fy, const double *bx, const double *by,
                 double *u, double *v)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++) {
             if (i == 0 || i == nx) { u[XF(i, j)] = 0.0; continue; }
             double gp = (p[CC(i, j)] - p[CC(i - 1, j)]) / h;
             u[XF(i, j)] = us[XF(i, j)] + dt * (bx[XF(i, j)] * (Fx[XF(i, j)] - gp));
         }
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j <= ny; j++)
         for (int i = 0; i < nx; i++) {
             if (j == 0 || j == ny) { v[YF(i, j)] = 0.0; continue; }
@@ -509,6 +526,7 @@ void or_correct(int nx, int ny, double h, double dt, const double *us,
 void or_divergence(int nx, int ny, double h, const double *u, const double *v,
                    double *div)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++)
             div[CC(i, j)] = (u[XF(i + 1, j)] - u[XF(i, j)] + v[YF(i, j + 1)] - v[YF(i, j)]) / h;
@@ -530,6 +548,7 @@ void or_predictor(int nx, int ny, double h, double dt, const double *rho,
                   double gx, double gy, double *us, double *vs, double *au,
                   double *av)
 {
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++) {
             size_t k = XF(i, j);
@@ -565,6 +584,7 @@ void or_predictor(int nx, int ny, double h, double dt, const double *rho,
             us[k] = uc + dt * ((vis - ae) / rf + gx);
             au[k] = adv;
         }
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j <= ny; j++)
         for (int i = 0; i < nx; i++) {
             size_t k = YF(i, j);
@@ -644,6 +664,7 @@ void or_interp(int kernel, int nx, int ny, double h, double x0, double y0,
                const double *u, const double *v, int M, const double *X,
                const double *Y, double *U, double *V)
 {
+    #pragma omp parallel for schedule(static)
     for (int m = 0; m < M; m++) {
         double sx = (X[m] - x0) / h, sy = (Y[m] - y0) / h - 0.5;
         int i0 = (int)floor(sx) - 1, j0 = (int)floor(sy) - 1;
@@ -996,6 +1017,7 @@ void or_spread_irrot(int nx, int ny, double h, double x0, double y0, int M,
 {
     int *prv = (int *)malloc((size_t)M * sizeof(int)), *nxt = (int *)malloc((size_t)M * sizeof(int));
     links(M, ndrops, drop_start, prv, nxt);
+    #pragma omp parallel for schedule(dynamic, 4)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i <= nx; i++) {
             double F = 0.0;
@@ -1007,6 +1029,7 @@ void or_spread_irrot(int nx, int ny, double h, double x0, double y0, int M,
             }
             Fx[XF(i, j)] = F;
         }
+    #pragma omp parallel for schedule(dynamic, 4)
     for (int j = 0; j <= ny; j++)
         for (int i = 0; i < nx; i++) {
             double F = 0.0;

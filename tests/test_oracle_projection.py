@@ -195,3 +195,26 @@ def test_crank_nicolson_solve_against_dense_operator(O, axisym):
     us, vs = O.cn_solve(rho, mu, ue, ve, h, dt, 30, axisym)
     got = np.concatenate([us.ravel(), vs.ravel()])[idx]
     assert np.abs(got - xd).max() <= 1e-11 * np.abs(xd).max()
+
+
+def test_openmp_build_is_bitwise_identical(O):
+    # The timed CPU baseline may run the oracle's OpenMP build on all host
+    # cores; its loops write disjoint outputs and keep every sum serial, so
+    # two composed steps of a multi-drop case agree bit for bit.
+    mk = W.multidrop(128, ndrops=6, rmin=0.05, rmax=0.1, n_per_drop=64, seed=7)
+    dt = W.capillary_dt(1 / 128, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    out = {}
+    try:
+        for omp in (False, True):
+            O.set_threads(omp)
+            for prec in (0, 2):
+                cfg = O.Config(nx=128, ny=128, h=1 / 128, spread=1, relocate_every=1, precision=prec)
+                st = O.init_state(cfg, mk.X, mk.Y, mk.drop_start)
+                for _ in range(2):
+                    O.ns_step(cfg, st, dt)
+                out[omp, prec] = (st.u, st.v, st.p, st.X, st.Y)
+    finally:
+        O.set_threads(False)
+    for prec in (0, 2):
+        for a, b in zip(out[False, prec], out[True, prec]):
+            assert np.array_equal(a, b)
