@@ -196,7 +196,11 @@ ib_status mg_setup(ib_ctx *ctx, const double *bx, const double *by);
  * the mean-zero solution on exit; rhs (device) is not modified.  cycles_out,
  * relres_out are host pointers (may be NULL).  Returns IB_ENOTCONV when the
  * cap is reached (p holds the last iterate) and IB_ENAN on a non-finite
- * residual.                                                                */
+ * residual.  IB_ECUDA also reports a smoother fault (ib_last_error names it):
+ * a block whose wait for its staged tile ran out (50 ms) skips the tile and
+ * waits up to 0.5 s more for its copies to land; the solve's result is then
+ * not to be trusted, but the context stays usable and the next solve starts
+ * with a clear fault word.                                                 */
 ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
                    double tol, int max_cycles, int *cycles_out,
                    double *relres_out);
@@ -298,6 +302,13 @@ unsigned long long ib_launch_count(void);
  * the same.  Kernels inside the graph's device-side loop cannot be timed
  * one by one by events or kernel profilers, hence the switch.             */
 ib_status ib_use_graphs(ib_ctx *ctx, int enable);
+/* Test hook for the failure path above: with enable = 1, every TMA-staged
+ * FP32 smoother block (precision 1 and 2 solves, levels whose width is a
+ * multiple of 4), after its copies have landed, also waits on a barrier
+ * phase that nothing completes, so that its bounded wait runs out and the
+ * solve returns IB_ECUDA; enable = 0 restores normal operation.  Process-wide
+ * (a device variable of the current device); IB_ECUDA if it cannot be set. */
+ib_status ib_debug_stall_staging(int enable);
 ib_status ib_profile_begin(int kind);
 ib_status ib_profile_end(double *total_ms, int *launches);
 /* Kernel timing on the context's current data: `reps` back-to-back launches
@@ -344,7 +355,10 @@ ib_status ib_load(ib_ctx *ctx, const char *path);
  * device current); make that first call before any stream capture.  All
  * calls share the array and its contents persist between calls, so calls
  * that overlap on the GPU (other streams, other host threads) race; the call
- * is not thread-safe.  Status codes as mg_solve.                            */
+ * is not thread-safe.  precision 0, 1 or 2 as in mg_solve.  Status codes as
+ * mg_solve; mg_solve_noalloc_error() returns the last call's message (empty
+ * after a success; stored in the library, so it shares the one-caller-at-a-
+ * time rule of the scratch array).                                         */
 #define IB_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define IB_NOALLOC_MAX_CELLS 65536
 ib_status mg_solve_noalloc(int32_t nx, int32_t ny, double h, const double *bx,
@@ -352,6 +366,7 @@ ib_status mg_solve_noalloc(int32_t nx, int32_t ny, double h, const double *bx,
                            int precision, double tol, int max_cycles, int nu1,
                            int nu2, int *cycles_out, double *relres_out,
                            void *stream);
+const char *mg_solve_noalloc_error(void); /* never NULL */
 
 /* ---------------------------------------------------------------------- */
 /* Context-free grid operators (device arrays, launched on `stream`, no

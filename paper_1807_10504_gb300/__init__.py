@@ -37,7 +37,8 @@ EXPORTS = [
     "cnn_get_params", "cnn_set_params", "cnn_grad", "cnn_train_step", "cnn_infer",
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
-    "ib_mass_correct", "ib_op_cn_solve", "ns_step_io",
+    "ib_mass_correct", "ib_op_cn_solve", "ns_step_io", "mg_solve_noalloc_error",
+    "ib_debug_stall_staging",
 ]
 
 
@@ -125,6 +126,10 @@ def lib():
         L.ib_destroy.restype = None
         L.ib_last_error.argtypes = [_P]
         L.ib_last_error.restype = C.c_char_p
+        L.mg_solve_noalloc_error.argtypes = []
+        L.mg_solve_noalloc_error.restype = C.c_char_p
+        L.ib_debug_stall_staging.argtypes = [C.c_int]
+        L.ib_debug_stall_staging.restype = C.c_int
         L.ib_profile_begin.argtypes = [C.c_int]
         L.ib_profile_begin.restype = C.c_int
         L.ib_profile_end.argtypes = [C.POINTER(_d), C.POINTER(C.c_int)]
@@ -467,14 +472,30 @@ def mg_solve_noalloc(bx, by, rhs, p, h, precision=0, tol=1e-10, max_cycles=100, 
     """Pressure solve through ``mg_solve_noalloc``: scratch comes from a fixed
     device array inside the library, so nothing is allocated (for callers that
     cannot allocate device memory).  ``p`` is updated in place.  Returns
-    (status, cycles, relative residual)."""
+    (status, cycles, relative residual); ``noalloc_error()`` gives the
+    library's message for a failed call.  Arrays of the wrong shape raise
+    IBError(IB_EINVAL) before the call."""
     torch = _torch()
     ny, nx = p.shape
+    for name, a, shape in (("bx", bx, (ny, nx + 1)), ("by", by, (ny + 1, nx)),
+                           ("rhs", rhs, (ny, nx))):
+        if tuple(a.shape) != shape:
+            raise IBError(IB_EINVAL, f"{name} has shape {tuple(a.shape)}, expected {shape}")
     cyc, rr = C.c_int(0), C.c_double(0.0)
     st = lib().mg_solve_noalloc(nx, ny, h, _ptr(bx, torch.float64), _ptr(by, torch.float64),
                                 _ptr(rhs, torch.float64), _ptr(p, torch.float64), precision, tol,
                                 max_cycles, nu1, nu2, C.byref(cyc), C.byref(rr), _stream())
     return st, cyc.value, rr.value
+
+
+def noalloc_error() -> str:
+    return lib().mg_solve_noalloc_error().decode()
+
+
+def debug_stall_staging(enable: bool) -> None:
+    """Test hook: make every TMA-staged FP32 smoother block's bounded wait
+    run out (see ib_debug_stall_staging), or restore normal operation."""
+    _check(lib().ib_debug_stall_staging(1 if enable else 0), None, "ib_debug_stall_staging")
 
 
 # -------------------------------------------------------------- measurement

@@ -920,6 +920,11 @@ ib_status ib_use_graphs(ib_ctx *c, int enable)
     return IB_OK;
 }
 
+ib_status ib_debug_stall_staging(int enable)
+{
+    return set_stall_staging(enable) == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
 ib_status ib_profile_begin(int kind)
 {
     if (kind < 0 || kind > 2) return IB_EINVAL;

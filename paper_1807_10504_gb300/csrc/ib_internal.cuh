@@ -56,6 +56,11 @@ bool profiling_active();
 void note_launch(int n = 1);
 unsigned long long launch_count();
 
+// The message of a smoother fault word (1 staging time-out, 2 misaligned
+// tiles, 3 copies not landed), and the staging-stall test hook.
+const char *fault_message(int code);
+cudaError_t set_stall_staging(int on);
+
 // Optional CUDA-event timing of one kernel class, on the stream it runs on.
 enum ProfKind { kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2 };
 bool prof_on(int kind);

@@ -198,6 +198,12 @@ k_rbgs_sweep_w(int nx, int ny, const double2 *__restrict__ w, const double *__re
 
 constexpr int FW = 64, FH = 16, FT = 256;
 
+// Test hook (ib_debug_stall_staging): when nonzero, every TMA-staged smoother
+// block also waits, after its copies have landed, on a barrier phase that
+// nothing completes, so that its bounded wait runs out and the time-out
+// path (fault word, IB_ECUDA from the solve) can be tested without a fault.
+__device__ int g_stall_staging = 0;
+
 // Asynchronous global -> shared copies (both addresses aligned to the size);
 // src-size 0 writes zeros without reading.
 __device__ __forceinline__ void cp_async16(void *d, const void *src, bool v)
@@ -216,15 +222,37 @@ __device__ __forceinline__ unsigned smem_addr(const void *p)
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Bounded wait for phase 0 of a shared-memory barrier; false on time-out.
-__device__ __forceinline__ bool mbar_wait0(unsigned long long *bar)
+// Global timer (nanoseconds).
+__device__ __forceinline__ unsigned long long gtimer_ns()
 {
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; it++)
-        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Limits of the smoother's staging waits: the first wait for the tile's
+// copies (they take microseconds; the limit only has to outlast a context
+// switch), and the drain after a time-out, which must see the copies land
+// before the block leaves (its shared memory is their destination).
+constexpr unsigned long long kStageWaitNs = 50000000ull;   // 50 ms
+constexpr unsigned long long kDrainNs = 500000000ull;      // 0.5 s
+
+// Wait for phase `parity` of a shared-memory barrier: true once it has
+// completed, false when limit_ns of global time (or, should the timer stall,
+// 2^26 polls) have passed first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns)
+{
+    const unsigned long long t0 = gtimer_ns();
+    for (int it = 0; it < (1 << 26); it++) {
+        unsigned done;
+        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, P;\n}\n"
-                     : "=r"(done) : "r"(smem_addr(bar)) : "memory");
-    return done != 0;
+                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (gtimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
 }
 
 // One 2-D tensor copy global -> shared completing on `bar`; the box (set in
@@ -253,8 +281,10 @@ __device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, int
 // (zero outside the grid) onto one barrier while all threads copy the x-face
 // rows (rows of nx + 1 faces are not 16-byte aligned, so no tensor map
 // describes them) with 16-byte asynchronous copies; otherwise every array
-// goes through asynchronous copies.  A barrier wait that times out records
-// tm.fault and the block skips its tile.
+// goes through asynchronous copies.  A barrier wait that times out (50 ms)
+// makes the block skip its tile: it waits up to 0.5 s more for its copies to
+// land and raises the fault word to 1 (landed) or 3 (not landed); misaligned
+// shared memory raises it to 2.
 // The iterate is read from pin and the tile written to p (a different
 // buffer): blocks read their neighbours' tiles as halo, so an in-place update
 // would let a block see values another block has already smoothed.
@@ -278,7 +308,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     // faces early)
     __shared__ __align__(16) float xs[PH][PW + 8];
     __shared__ int xoff[PH];
-    __shared__ __align__(8) unsigned long long bar;
+    __shared__ __align__(8) unsigned long long bar, stall_bar;
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
     const long nxf = nx + 1;
     const int nxc = nx / 2, nyc = ny / 2;
@@ -323,11 +353,12 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         // tensor copies land on 128-byte boundaries (checked, not assumed)
         if (((smem_addr(&ps[0][0]) | smem_addr(&bs[0][0]) | smem_addr(&ds[0][0]) |
               smem_addr(&ys[0][0])) & 127u) != 0) {
-            if (threadIdx.x == 0) *tm.fault = 2;
+            if (threadIdx.x == 0) atomicMax(tm.fault, 2);
             return;
         }
         if (threadIdx.x == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&stall_bar)));
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         }
         __syncthreads();  // the barrier is initialised before any thread waits on it
@@ -361,9 +392,13 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
             }
         }
         asm volatile("cp.async.wait_all;\n" ::);
-        if (!mbar_wait0(&bar)) {
-            *tm.fault = 1;
-            mbar_wait0(&bar);  // copies still in flight land before the block leaves
+        bool ok = mbar_wait(&bar, 0, kStageWaitNs);
+        if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
+        // one verdict for the whole block (each thread's wait is bounded)
+        if (__syncthreads_or(!ok)) {
+            // skip the tile; the copies must land before the block leaves
+            const bool landed = mbar_wait(&bar, 0, kDrainNs);
+            if (threadIdx.x == 0) atomicMax(tm.fault, landed ? 1 : 3);
             return;
         }
         if constexpr (MODE == 2) {
@@ -1467,6 +1502,22 @@ struct Prof {
 }  // namespace
 
 void note_launch(int n) { g_launches += (unsigned long long)(long long)n; }
+
+const char *fault_message(int code)
+{
+    switch (code) {
+    case 1: return "a smoother's staging wait timed out (50 ms); its tile was skipped";
+    case 2: return "a smoother's shared-memory tiles are misaligned";
+    case 3: return "a smoother's staging copies did not land within 0.5 s";
+    default: return "a smoother reported an unknown fault";
+    }
+}
+
+cudaError_t set_stall_staging(int on)
+{
+    const int v = on ? 1 : 0;
+    return cudaMemcpyToSymbol(g_stall_staging, &v, sizeof(int));
+}
 unsigned long long launch_count() { return g_launches.load(); }
 bool prof_on(int kind) { return g_prof.kind == kind && g_prof.n < kProfMax; }
 static bool prof_active() { return g_prof.kind >= 0; }
@@ -1793,6 +1844,7 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
     double *res = mg.red;  // res[0] sum b, res[1] |b0|^2, res[2] |r|^2, res[3] sum p
     double *e0 = v0.d.e, *b0 = v0.d.r;
     const double ih2 = 1.0 / (v0.h * v0.h);
+    cudaMemsetAsync(&mg.ctl->fault, 0, sizeof(int), s);  // fault word of this solve
     cudaMemcpyAsync(e0, p, n * 8, cudaMemcpyDeviceToDevice, s);
     note_launch();
     k_sum<<<RB, kRedT, 0, s>>>(n, rhs, part, mg.red_count, res + 0);
@@ -1850,7 +1902,7 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
         ce = cudaMemcpyAsync(&fault, &mg.ctl->fault, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { err = cudaGetErrorString(ce); return IB_ECUDA; }
-        if (fault) { err = "a smoother's staging wait timed out"; return IB_ECUDA; }
+        if (fault) { err = fault_message(fault); return IB_ECUDA; }
         if (!isfinite(rr)) { st = IB_ENAN; err = "non-finite residual"; }
         else if (rr > tol) { st = IB_ENOTCONV; err = "cycle cap reached above tolerance"; }
     }
@@ -1876,6 +1928,7 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
     const unsigned long long k0 = launch_count();
     cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
+    cudaMemsetAsync(&mg.ctl->fault, 0, sizeof(int), c);  // fault word of this solve
     if (sg.p != e0) cudaMemcpyAsync(e0, sg.p, n * 8, cudaMemcpyDeviceToDevice, c);
     note_launch();
     k_sum<<<RB, kRedT, 0, c>>>(n, sg.rhs, part, mg.red_count, res + 0);
@@ -1990,7 +2043,7 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
     if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { err = cudaGetErrorString(e); return IB_ECUDA; }
-    if (mg.ctl_host->fault) { err = "a smoother's staging wait timed out"; return IB_ECUDA; }
+    if (mg.ctl_host->fault) { err = fault_message(mg.ctl_host->fault); return IB_ECUDA; }
     const int c = mg.ctl_host->cycles;
     const double rr = mg.ctl_host->rr;
     note_launch((int)(sg->outer_kernels + (unsigned long long)c * sg->body_kernels));

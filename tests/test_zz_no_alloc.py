@@ -40,7 +40,7 @@ def _reference(ib, T, n, bx, by, b, precision):
     return p.cpu().numpy(), cyc
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_noalloc_matches_context_solve_twice(T, precision):
     import paper_1807_10504_gb300 as ib
     d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -66,3 +66,12 @@ def test_noalloc_rejects_grids_above_the_limit(T):
     by = T.zeros((n + 1, n), dtype=T.float64, device="cuda")
     st, _, _ = ib.mg_solve_noalloc(bx, by, z, z.clone(), 1.0 / n)
     assert st == ib.IB_EINVAL
+    assert "IB_NOALLOC_MAX_CELLS" in ib.noalloc_error()
+    # arrays of the wrong shape are refused before the library reads them
+    m = 64
+    p = T.zeros((m, m), dtype=T.float64, device="cuda")
+    bad = T.zeros((m, m), dtype=T.float64, device="cuda")  # beta_x needs m x (m + 1)
+    byg = T.zeros((m + 1, m), dtype=T.float64, device="cuda")
+    with pytest.raises(ib.IBError) as e:
+        ib.mg_solve_noalloc(bad, byg, p.clone(), p, 1.0 / m)
+    assert e.value.status == ib.IB_EINVAL
