@@ -282,6 +282,147 @@ def run_reference(args):
     return 0
 
 
+# Algorithmic work per cell of the fused FP64 V(2,2) kernels (pre-scaled
+# stencil, flux-form residual).  Bytes: sweeps + residual + restriction read
+# p, bt, 4 weights (48), b, beta_x, beta_y (24), the coarse 1/diag (2), write
+# p (8) and the coarse rc, btc, e (6); prolongation + sweeps read p, bt, the
+# weights (48) and the coarse correction (2), write p (8).  FP64 operations
+# (an FMA counted as two): a sweep 8; the residual 13 and the restriction 1;
+# the prolongation 8.
+FP64_RESTRICT = {"bytes": 88.0, "flops": 2 * 8.0 + 14.0}
+FP64_PROLONG = {"bytes": 58.0, "flops": 2 * 8.0 + 8.0}
+# Per fine cell and V(2,2) cycle: SURVEY's fused minimum (84 B per level cell
+# x 4/3 levels) and the per-kernel (unfused) accounting (212 B x 4/3); FP64
+# operations of the FP64 cycle: (4 sweeps x 8 + 14 + 8) x 4/3 + the fine
+# residual norm (15).
+VCYCLE_BYTES_FUSED, VCYCLE_BYTES_UNFUSED = 112.0, 283.0
+VCYCLE_FP64_FLOPS = (4 * 8.0 + 14.0 + 8.0) * 4.0 / 3.0 + 15.0
+
+
+def timed_solve(torch, ctx, stream, flush, b, prec, start=None, reps=5, warm=3):
+    """Median CUDA-event time of a cold (or given-start) solve to 1e-10
+    through the solve graph; L2 flushed before each."""
+    times, cyc, rr = [], None, None
+    ny, nx = b.shape
+    for rep in range(warm + reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p = start() if start is not None else torch.zeros((ny, nx), dtype=torch.float64,
+                                                          device="cuda")
+        st, cyc, rr = ctx.mg_solve(b, p, prec, 1e-10, 200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= warm:
+            times.append(e0.elapsed_time(e1))
+    return {"ms": statistics.median(times), "cycles": cyc, "relres": rr}
+
+
+def per_vcycle(entry, cells, pk, fp64_peak, fp64):
+    """Per-V-cycle time and effective bandwidth (SURVEY's 112 and 283 B per
+    fine cell) of a solve entry; FP64 cycles also against the FP64 peak."""
+    us = 1e3 * entry["ms"] / max(entry["cycles"], 1)
+    out = {"us": us}
+    for label, B in (("fused_112B", VCYCLE_BYTES_FUSED), ("unfused_283B", VCYCLE_BYTES_UNFUSED)):
+        gbs = B * cells / (us * 1e-6) / 1e9
+        out[label] = {"GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
+    if fp64:
+        tf = VCYCLE_FP64_FLOPS * cells / (us * 1e-6) / 1e12
+        out["fp64"] = {"flops_per_cell": VCYCLE_FP64_FLOPS, "tflops": tf, "frac": tf / fp64_peak}
+    return out
+
+
+def solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak):
+    """Pressure solve alone on the context's last system, cold start: FP64,
+    precision 1, precision 2, and precision 2 from the network (inference
+    inside the timed region); per-V-cycle figures; the level-0 kernels timed
+    back to back on this data with their rooflines."""
+    b = ctx.get("b")
+    cells = nx * ny
+    solve = {}
+    for prec, label in ((0, "fp64"), (1, "mixed"), (2, "mixed2")):
+        solve[label] = timed_solve(torch, ctx, stream, flush, b, prec)
+    if net is not None:
+        rho = ctx.get("rho")
+        solve["mixed_cnn"] = timed_solve(torch, ctx, stream, flush, b, 2,
+                                         start=lambda: net.infer(b[None], rho[None])[0])
+        solve["mixed_cnn"]["solver"] = "mixed2 (two FP32 V-cycles per FP64 residual)"
+    solve["speedup_vs_fp64"] = {k: solve["fp64"]["ms"] / solve[k]["ms"]
+                                for k in ("mixed", "mixed2", "mixed_cnn") if k in solve}
+    solve["per_vcycle"] = {k: per_vcycle(solve[k], cells, pk, fp64_peak, k == "fp64")
+                           for k in ("fp64", "mixed", "mixed2")}
+    us32, c0 = ctx.bench_kernel(4, 50)
+    us64, _ = ctx.bench_kernel(1, 50)
+    usr, _ = ctx.bench_kernel(7, 50)
+    usp, _ = ctx.bench_kernel(8, 50)
+    usn, _ = ctx.bench_kernel(6, 50)
+
+    def roof(us, work, label):
+        gbs = work["bytes"] * c0 / (us * 1e-6) / 1e9
+        tf = work["flops"] * c0 / (us * 1e-6) / 1e12
+        return {"kernel": label, "avg_launch_us": us, "algorithmic_bytes_per_cell": work["bytes"],
+                "GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"], "fp64_flops_per_cell": work["flops"],
+                "fp64_tflops": tf, "frac_fp64": tf / fp64_peak,
+                "bound": "fp64" if tf / fp64_peak > gbs / pk["hbm_gbs"] else "hbm"}
+    kernels = {"level0": {
+        "cells": int(c0), "fp32_prolong_sweeps2_us": us32, "fp64_sweep_us": us64,
+        "fp64_sweeps2_restrict": roof(usr, FP64_RESTRICT, "k_smooth2_f64<1> (two FP64 sweeps + "
+                                      "residual + restriction)"),
+        "fp64_prolong_sweeps2": roof(usp, FP64_PROLONG, "k_smooth2_f64<2> (prolongation + two "
+                                     "FP64 sweeps)"),
+        "fp64_residual_norm": roof(usn, {"bytes": 32.0 + 8.0, "flops": 15.0},
+                                   "k_resnorm (FP64 residual, norm, FP32 copy)")},
+        "timing": "50 back-to-back launches on the level's data, CUDA events on the "
+                  "launching stream (1024^2 data is largely L2-resident; 2048^2 is not)"}
+    return solve, kernels
+
+
+def steps_rate(ctx, torch, stream, flush, dt, warm, K):
+    """Device-timed steps/s of K steps (CUDA events per step, L2 flushed
+    before each)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.ns_step(dt, 1, warm)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return K / (sum(a.elapsed_time(b) for a, b in ev) / 1e3)
+
+
+def scale_pass(ib, torch, args, stream, flush, net, pk, fp64_peak):
+    """The scale configuration's other grid (2048^2 by default): steps/s with
+    precision 2 and with the FP64 solver, the pressure solves and the level-0
+    kernels on its data (which does not fit in L2)."""
+    name = args.scale_workload
+    nx, ny, kw, dt = problem(name)
+    mk = make_markers(name)
+    out = {"workload": name, "nx": nx, "ny": ny, "drops": int(mk.ndrops), "markers": int(mk.M)}
+    for prec, key in ((2, "steps_per_s"), (0, "fp64_steps_per_s")):
+        cfg = ib.Config(nx=nx, ny=ny, precision=prec, spread=1, relocate_every=10, tol=1e-10,
+                        max_cycles=200, **kw)
+        c = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+        for _ in range(args.warmup):
+            c.ns_step(dt, 1, args.warm)
+        out[key] = steps_rate(c, torch, stream, flush, dt, args.warm, args.scale_steps)
+        if prec == 2:
+            solve, kernels = solve_and_kernels(ib, torch, c, stream, flush, nx, ny, net, pk,
+                                               fp64_peak)
+            if net is not None:
+                solve["mixed_cnn"]["inference_grid"] = nx >> args.cnn_coarsen
+            out["pressure_solve_ms"] = solve
+            out["kernels"] = kernels
+            us32 = kernels["level0"]["fp32_prolong_sweeps2_us"]
+            gbs = 37.0 * nx * ny / (us32 * 1e-6) / 1e9
+            out["roofline_fp32_smoother"] = {
+                "kernel": "k_smooth2_f32<2> (fine level)", "avg_launch_us": us32,
+                "algorithmic_bytes_per_cell": 37.0, "GB_s": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+                "traffic": traffic_per_launch("k_smooth2_f32<2>", nx * ny)}
+        c.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -372,42 +513,62 @@ def run_ours(args):
     barrier()
     sweep_ms, sweep_n = ib.profile_end()
 
-    # pressure solve alone, cold start, on this state's system: FP64 vs mixed,
-    # both through the solve graph
-    b = ctx.get("b")
-    solve = {}
     pk, pk_kind = peaks()
-    for prec, label in ((0, "fp64"), (1, "mixed"), (2, "mixed2")):
-        times, cyc = [], None
-        for rep in range(3 + 5):
-            p = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, cyc, rr = ctx.mg_solve(b, p, prec, 1e-10, 200)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if rep >= 3:
-                times.append(e0.elapsed_time(e1))
-        solve[label] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr}
+    fp64_peak = ib.probe_fp64()  # TFLOP/s, FMA chains on every SM
 
-    # kernel durations on this step's data: back-to-back launches between two
-    # CUDA events on the context stream (ib_bench_kernel)
-    us32, cells = ctx.bench_kernel(4, 50)  # the step's top kernel: prolongation + two FP32 sweeps
-    us64, _ = ctx.bench_kernel(1, 50)
+    # the same workload with the FP64 multigrid as the step's solver
+    fp64_rate = None
+    if args.precision != 0:
+        c64 = ib.Context(ib.Config(nx=nx, ny=ny, precision=0, spread=1, relocate_every=10,
+                                   tol=1e-10, max_cycles=200, **kw), mk.X, mk.Y, mk.drop_start)
+        for _ in range(args.warmup):
+            c64.ns_step(dt, 1, args.warm)
+        fp64_rate = steps_rate(c64, torch, stream, flush, dt, args.warm, args.steps)
+        c64.close()
+
+    # mixed precision from the learned warm start: a network trained here on
+    # solver-generated 128^2 samples (its own kernels), inference inside the
+    # timed region
+    net, train = None, None
+    if not args.no_cnn:
+        from paper_1807_10504_gb300 import warmstart as WS
+        t0 = time.perf_counter()
+        data = WS.generate(args.cnn_samples, n_cells=128, seed=0)
+        net = ib.Net(seed=0)
+        losses = WS.train(net, data, steps=args.cnn_steps, batch=16, lr=2e-3)
+        del data
+        train = {"samples": args.cnn_samples, "steps": len(losses), "final_loss": losses[-1],
+                 "seconds": time.perf_counter() - t0}
+        net.set_coarsen(args.cnn_coarsen)
+
+    solve, kernels = solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak)
+    if train is not None:
+        solve["mixed_cnn"]["train"] = train
+        solve["mixed_cnn"]["inference_grid"] = nx >> args.cnn_coarsen
+    us32, cells = kernels["level0"]["fp32_prolong_sweeps2_us"], kernels["level0"]["cells"]
+    us64 = kernels["level0"]["fp64_sweep_us"]
     usb, pairs = ctx.bench_kernel(2, 10)
     # per-level durations of the mixed cycle's kernels (same method)
     levels = []
     for lev in range(16):
-        try:
+        row = {"level": lev}
+        try:  # the FP32 cycle's kernels (levels above its single-CTA tail)
             t_down, c_l = ctx.bench_kernel(3, 20, lev)
+            row.update(cells=int(c_l), sweeps2_restrict_us=t_down,
+                       prolong_sweeps2_us=ctx.bench_kernel(4, 20, lev)[0],
+                       sweeps2_us=ctx.bench_kernel(0, 20, lev)[0])
         except ib.IBError:
+            pass
+        try:  # the FP64 cycle's fused kernels (levels above its tail)
+            t_r, c_l = ctx.bench_kernel(7, 20, lev)
+            row.update(cells=int(c_l), fp64_sweeps2_restrict_us=t_r,
+                       fp64_prolong_sweeps2_us=ctx.bench_kernel(8, 20, lev)[0],
+                       fp64_sweep_us=ctx.bench_kernel(1, 20, lev)[0])
+        except ib.IBError:
+            pass
+        if len(row) == 1:
             break
-        t_up, _ = ctx.bench_kernel(4, 20, lev)
-        t_s2, _ = ctx.bench_kernel(0, 20, lev)
-        t_64, _ = ctx.bench_kernel(1, 20, lev)
-        levels.append({"level": lev, "cells": int(c_l), "sweeps2_restrict_us": t_down,
-                       "prolong_sweeps2_us": t_up, "sweeps2_us": t_s2, "fp64_sweep_us": t_64})
+        levels.append(row)
     t_tail, c_tail = ctx.bench_kernel(5, 20)
     t_res, _ = ctx.bench_kernel(6, 20)
     kernel_table = {"levels": levels, "fp32_tail_us": t_tail, "fp32_tail_first_level_cells": int(c_tail),
@@ -424,42 +585,19 @@ def run_ours(args):
               "achieved": ach64, "peak": pk["hbm_gbs"], "unit": "GB/s",
               "frac": ach64 / pk["hbm_gbs"], "traffic": traffic_per_launch("k_rbgs_sweep_w", cells),
               "peak_source": pk_kind, "avg_launch_us": us64, "algorithmic_bytes_per_cell": B64,
-              "algorithmic_bytes": B64 * cells}
+              "algorithmic_bytes": B64 * cells,
+              "fp64": {"flops_per_cell": 8.0, "achieved_tflops": 8.0 * cells / (us64 * 1e-6) / 1e12,
+                       "peak_tflops": fp64_peak,
+                       "frac": 8.0 * cells / (us64 * 1e-6) / 1e12 / fp64_peak}}
     band = {"kernel": "k_band_area", "avg_launch_us": usb, "pairs": int(pairs),
             "ns_per_pair": 1e3 * usb / max(pairs, 1)}
 
-    # mixed precision from the learned warm start: a network trained here on
-    # solver-generated 128^2 samples (its own kernels), inference inside the
-    # timed region
-    if not args.no_cnn:
-        from paper_1807_10504_gb300 import warmstart as WS
-        t0 = time.perf_counter()
-        data = WS.generate(args.cnn_samples, n_cells=128, seed=0)
-        net = ib.Net(seed=0)
-        losses = WS.train(net, data, steps=args.cnn_steps, batch=16, lr=2e-3)
-        del data
-        train_s = time.perf_counter() - t0
-        net.set_coarsen(args.cnn_coarsen)
-        rho = ctx.get("rho")
-        times, cyc = [], None
-        for rep in range(3 + 5):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            p = net.infer(b[None], rho[None])[0]
-            st, cyc, rr = ctx.mg_solve(b, p, 2, 1e-10, 200)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if rep >= 3:
-                times.append(e0.elapsed_time(e1))
-        solve["mixed_cnn"] = {"ms": statistics.median(times), "cycles": cyc, "relres": rr,
-                              "solver": "mixed2 (two FP32 V-cycles per FP64 residual)",
-                              "inference_grid": nx >> args.cnn_coarsen,
-                              "train": {"samples": args.cnn_samples, "steps": len(losses),
-                                        "final_loss": losses[-1], "seconds": train_s}}
+    # the scale configuration's larger grid: 2048^2, same drops per unit area
+    scale = None
+    if args.scale_workload and args.scale_workload != name:
+        scale = scale_pass(ib, torch, args, stream, flush, net, pk, fp64_peak)
+    if net is not None:
         del net
-    solve["speedup_vs_fp64"] = {k: solve["fp64"]["ms"] / solve[k]["ms"]
-                                for k in ("mixed", "mixed2", "mixed_cnn") if k in solve}
 
     # end to end through the C ABI with host buffers: markers in, pressure out
     Xh = torch.empty(ctx.M, dtype=torch.float64).pin_memory().numpy()
@@ -493,6 +631,9 @@ def run_ours(args):
                    "l2": "flushed before each step (256 MiB)",
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
+        "fp64_steps_per_s": fp64_rate,
+        "fp64_peak_tflops": fp64_peak,
+        "fp64_kernels": kernels,
         "clocks": clocks,
         "e2e": {"value": ws * e2e_steps / e2e_t, "unit": "steps/s",
                 "h2d_bytes_per_step": int(2 * ctx.M * 8),
@@ -518,6 +659,8 @@ def run_ours(args):
         "band_strip_areas": band,
         "mixed_cycle_kernels": kernel_table,
     }
+    if scale is not None:
+        line["scale"] = scale
     if axi:
         # the drop's fall so far: every ns_step of this run advanced it by dt
         com, S, vf, wb = ctx.frame_state()
@@ -554,6 +697,10 @@ def main():
     ap.add_argument("--cnn-steps", type=int, default=800)
     ap.add_argument("--cnn-coarsen", type=int, default=1,
                     help="run the network on the grid coarsened by 2^k")
+    ap.add_argument("--scale-workload", default="multidrop2048",
+                    help="second grid of the scale configuration measured in the same run "
+                         "(empty to skip)")
+    ap.add_argument("--scale-steps", type=int, default=10)
     ap.add_argument("--no-graphs", action="store_true",
                     help="solve with one launch per kernel (for kernel profilers)")
     ap.add_argument("--ncu-cnn", action="store_true",

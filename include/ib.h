@@ -292,11 +292,16 @@ ib_status ib_attach_cnn(ib_ctx *ctx, ib_cnn *net);
 /* Measurement hooks.  ib_launch_count: kernels launched by this library in
  * this process so far.  ib_profile_begin(kind) starts CUDA-event timing, on
  * the launching stream, of every launch of one kernel class (0: fine-level
- * FP64 red-black sweep, 1: fine-level FP32 sweep, 2: fine-level FP64
- * residual norm); ib_profile_end synchronises on the recorded events and
+ * FP64 smoother launch (one sweep, or two fused in V(2,2)), 1: fine-level
+ * FP32 smoother launch, 2: fine-level FP64 residual norm); ib_profile_end synchronises on the recorded events and
  * returns their summed duration (ms) and count.  Timing is process-wide and
  * not thread-safe; at most 16384 launches are recorded.                    */
 unsigned long long ib_launch_count(void);
+/* FP64 FMA throughput of the current device (TFLOP/s, an FMA counted as two
+ * operations): three timed launches of independent FMA chains on every SM,
+ * CUDA events on `stream` (synchronises it).  The peak against which FP64-
+ * bound kernels are stated.                                                */
+ib_status ib_probe_fp64(void *stream, double *tflops);
 /* Solve with the captured CUDA graph (default, enable = 1) or with one launch
  * per kernel and a host residual check per cycle (enable = 0); results are
  * the same.  Kernels inside the graph's device-side loop cannot be timed
@@ -318,6 +323,8 @@ ib_status ib_profile_end(double *total_ms, int *launches);
  * 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps + residual +
  * restriction, 4 FP32 prolongation + sweeps (at level 0 with the FP64
  * update of the defect correction, as in the solve) (units = cells of the
+ * level); 7 FP64 two sweeps + residual + restriction, 8 FP64 prolongation +
+ * two sweeps (the fused V(2,2) kernels of the FP64 solve; cells of the
  * level); 5 the FP32 single-CTA lower cycle (cells of its first level), 6 the
  * FP64 residual norm of the mixed solve (cells); 2 band strip areas of the
  * last Heaviside pass (units = (cell, segment) pairs; level ignored).  Only

@@ -38,7 +38,7 @@ EXPORTS = [
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
     "ib_mass_correct", "ib_op_cn_solve", "ns_step_io", "mg_solve_noalloc_error",
-    "ib_debug_stall_staging",
+    "ib_debug_stall_staging", "ib_probe_fp64",
 ]
 
 
@@ -128,6 +128,8 @@ def lib():
         L.ib_last_error.restype = C.c_char_p
         L.mg_solve_noalloc_error.argtypes = []
         L.mg_solve_noalloc_error.restype = C.c_char_p
+        L.ib_probe_fp64.argtypes = [_P, C.POINTER(_d)]
+        L.ib_probe_fp64.restype = C.c_int
         L.ib_debug_stall_staging.argtypes = [C.c_int]
         L.ib_debug_stall_staging.restype = C.c_int
         L.ib_profile_begin.argtypes = [C.c_int]
@@ -486,6 +488,13 @@ def mg_solve_noalloc(bx, by, rhs, p, h, precision=0, tol=1e-10, max_cycles=100, 
                                 _ptr(rhs, torch.float64), _ptr(p, torch.float64), precision, tol,
                                 max_cycles, nu1, nu2, C.byref(cyc), C.byref(rr), _stream())
     return st, cyc.value, rr.value
+
+
+def probe_fp64() -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
+    t = C.c_double(0.0)
+    _check(lib().ib_probe_fp64(_stream(), C.byref(t)), None, "ib_probe_fp64")
+    return t.value
 
 
 def noalloc_error() -> str:

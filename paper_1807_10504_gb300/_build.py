@@ -24,6 +24,7 @@ SOURCES = {
     "noalloc.cu": [],
     "cnn.cu": [],
     "axi.cu": [],
+    "probe.cu": [],
 }
 
 

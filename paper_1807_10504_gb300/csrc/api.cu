@@ -939,7 +939,7 @@ ib_status ib_profile_end(double *total_ms, int *launches)
 ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_per_launch,
                           double *units)
 {
-    if (!c || which < 0 || which > 6 || reps < 1 || !us_per_launch) return IB_EINVAL;
+    if (!c || which < 0 || which > 8 || reps < 1 || !us_per_launch) return IB_EINVAL;
     if (which != 2 && !c->mg_ready) return fail(c, IB_EINVAL, "no multigrid hierarchy yet");
     double u = 0.0;
     if (which == 2) {

@@ -9,16 +9,15 @@
 // by Gauss-Jordan elimination in FP64).
 //
 // GB300 mapping:
-//  * sweeps are tiled (FP64: one red+black sweep per launch on a 64x16 tile
-//    with a 2-cell halo; FP32: two sweeps per launch on shrinking rings of a
-//    4-cell halo) and out of place: a launch reads the iterate from one buffer
-//    and writes its tiles to the other, since blocks read their neighbours'
-//    tiles as halo.  HBM traffic is one read of p, b, beta_x, beta_y, 1/diag
-//    and one write of p per launch (40 B/cell FP64 per sweep, 20 B/cell FP32
-//    per two sweeps, plus the 1/diag stream).
-//  * the FP32 cycle fuses the residual and restriction into the pre-smoothing
-//    launch and the prolongation into the post-smoothing launch, so a level
-//    costs two launches.
+//  * sweeps are tiled (two sweeps per launch on shrinking rings of a 4-cell
+//    halo; the FP64 sweep on a pre-scaled stencil, four weights and h^2 b /
+//    diag per cell; a single FP64 sweep per launch on a 2-cell halo for other
+//    sweep counts) and out of place: a launch reads the iterate from one
+//    buffer and writes its tiles to the other, since blocks read their
+//    neighbours' tiles as halo.
+//  * the V(2,2) cycle fuses the residual and restriction into the
+//    pre-smoothing launch and the prolongation into the post-smoothing
+//    launch, so a level costs two launches (FP32 and FP64).
 //  * kernels of the cycle use programmatic dependent launch: the next grid is
 //    scheduled while the previous one drains and waits (griddepcontrol) for
 //    its results.
@@ -528,6 +527,108 @@ __device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
     s += by[kc + nx] * (pN - c);
     s -= by[kc] * (c - pS);
     return s;
+}
+
+// Two FP64 red-black sweeps in one launch on the pre-scaled stencil of
+// k_rbgs_sweep_w (p_c <- sum_f w_f p_nb - bt_c, four FMAs a cell in the same
+// order), on a DW x DH tile: the iterate's window (halo HA) is staged in
+// shared memory and the sweeps run on shrinking rings (red, black, red,
+// black), each cell reading its weights and right-hand side from global
+// memory (L1 / L2), so the tile's result equals two global sweeps.  MODE 1:
+// then the residual b - A p of the tile's cells (the flux form of
+// k_restrict_residual, from beta and b) averaged over 2x2 children into the
+// coarse right-hand side rc, its pre-scaled copy btc = h_c^2 rc / diag_c
+// (when btc is given) and a zero coarse correction; the last black phase
+// covers the tile's one-cell ring so that the residual sees final values
+// (halo 5).  MODE 2: p + P e_c (bilinear prolongation of the coarse
+// correction) formed while staging, then the sweeps (halo 4).  The FP64 pipe
+// bounds the sweeps on this part, so the gain over separate launches is the
+// residual / restriction and prolongation passes and two of three launches
+// per level; tiles of 32 x 16 spread the small levels over more SMs.
+template <int MODE, int DW, int DH>
+__global__ void __launch_bounds__(256)
+k_smooth2_f64(int nx, int ny, double ih2, const double2 *__restrict__ w,
+              const double *__restrict__ bt, const double *__restrict__ bx,
+              const double *__restrict__ by, const double *__restrict__ b,
+              const double *__restrict__ pin, double *__restrict__ p, double *__restrict__ rc,
+              double *__restrict__ ecz, double h2c, const double *__restrict__ invdc,
+              double *__restrict__ btc, const double *__restrict__ ecp)
+{
+    constexpr int NT = 256;
+    constexpr int HA = MODE == 1 ? 5 : 4;
+    constexpr int PW = DW + 2 * HA, PH = DH + 2 * HA;
+    __shared__ double ps[PH][PW];
+    const int gi0 = blockIdx.x * DW - HA, gj0 = blockIdx.y * DH - HA;
+    const int nxc = nx / 2, nyc = ny / 2;
+    pdl_enter();
+    for (int k = threadIdx.x; k < PH * PW; k += NT) {
+        const int r = k / PW, c = k - r * PW, gi = gi0 + c, gj = gj0 + r;
+        double v = 0.0;
+        if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+            v = pin[(long)gj * nx + gi];
+            if (MODE == 2) {
+                const int I = gi >> 1, J = gj >> 1;
+                const int I2 = min(max(I + ((gi & 1) ? 1 : -1), 0), nxc - 1);
+                const int J2 = min(max(J + ((gj & 1) ? 1 : -1), 0), nyc - 1);
+                const double c00 = ecp[(long)J * nxc + I], c10 = ecp[(long)J * nxc + I2];
+                const double c01 = ecp[(long)J2 * nxc + I], c11 = ecp[(long)J2 * nxc + I2];
+                v += (9.0 * c00 + 3.0 * c10 + 3.0 * c01 + c11) / 16.0;
+            }
+        }
+        ps[r][c] = v;
+    }
+    __syncthreads();
+    // ring q: local rows [HA - q, HA + DH + q), columns [HA - q, HA + DW + q)
+#pragma unroll
+    for (int ph = 0; ph < 4; ph++) {
+        const int q = HA - 1 - ph, color = ph & 1;
+        const int wq = DW + 2 * q, hq = DH + 2 * q, hw = wq / 2;
+        for (int k = threadIdx.x; k < hq * hw; k += NT) {
+            const int rr = k / hw, cc = k - rr * hw;
+            const int r = HA - q + rr, gj = gj0 + r;
+            const int c = HA - q + 2 * cc + ((gi0 + HA - q + gj + color) & 1);
+            const int gi = gi0 + c;
+            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
+            const long kc = (long)gj * nx + gi;
+            const double2 we = w[2 * kc], sn = w[2 * kc + 1];
+            double sm = fma(we.x, ps[r][c - 1], -bt[kc]);
+            sm = fma(we.y, ps[r][c + 1], sm);
+            sm = fma(sn.x, ps[r - 1][c], sm);
+            ps[r][c] = fma(sn.y, ps[r + 1][c], sm);
+        }
+        __syncthreads();
+    }
+    if (MODE == 1) {
+        const long nxf = nx + 1;
+        for (int k = threadIdx.x; k < (DW / 2) * (DH / 2); k += NT) {
+            const int I = blockIdx.x * (DW / 2) + (k % (DW / 2));
+            const int J = blockIdx.y * (DH / 2) + (k / (DW / 2));
+            if (I >= nxc || J >= nyc) continue;
+            auto res = [&](int gi, int gj) {
+                const int r = gj - gj0, c = gi - gi0;
+                const long kc = (long)gj * nx + gi, kx = (long)gj * nxf + gi;
+                const double pc = ps[r][c];
+                const double pE = gi + 1 < nx ? ps[r][c + 1] : pc, pW = gi > 0 ? ps[r][c - 1] : pc;
+                const double pN = gj + 1 < ny ? ps[r + 1][c] : pc, pS = gj > 0 ? ps[r - 1][c] : pc;
+                double sf = bx[kx + 1] * (pE - pc);
+                sf -= bx[kx] * (pc - pW);
+                sf += by[kc + nx] * (pN - pc);
+                sf -= by[kc] * (pc - pS);
+                return b[kc] - sf * ih2;
+            };
+            const int i = 2 * I, j = 2 * J;
+            const double rv = 0.25 * (res(i, j) + res(i + 1, j) + res(i, j + 1) + res(i + 1, j + 1));
+            const long kcc = (long)J * nxc + I;
+            rc[kcc] = rv;
+            ecz[kcc] = 0.0;
+            if (btc) btc[kcc] = rv * h2c * invdc[kcc];
+        }
+    }
+    for (int k = threadIdx.x; k < DH * DW; k += NT) {
+        const int r = HA + k / DW, c = HA + (k % DW);
+        const int gi = gi0 + c, gj = gj0 + r;
+        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+    }
 }
 
 // Coarse residual = average of the four children's b - A p; zeroes the coarse
@@ -1355,6 +1456,29 @@ void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, fl
     }
 }
 
+// One fused FP64 smoother launch of MODE on level v (pin -> p): 64 x 32 tiles
+// from 512^2 cells up, 32 x 16 below (more tiles, so more SMs share the FP64
+// work of a small level).
+template <int MODE>
+void launch_smooth2_f64(const Level &v, const LevelT<double> &a, const double *pin, double *p,
+                        double *rc, double *ecz, double h2c, const double *invdc, double *btc,
+                        const double *ecp, cudaStream_t s)
+{
+    const double ih2 = 1.0 / (v.h * v.h);
+    note_launch();
+    if ((long)v.nx * v.ny >= (1L << 18)) {
+        dim3 g(cdiv(v.nx, 64), cdiv(v.ny, 32));
+        launch_pdl(k_smooth2_f64<MODE, 64, 32>, g, 256, 0, s, v.nx, v.ny, ih2, (const double2 *)a.w,
+                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by,
+                   (const double *)a.r, pin, p, rc, ecz, h2c, invdc, btc, ecp);
+    } else {
+        dim3 g(cdiv(v.nx, 32), cdiv(v.ny, 16));
+        launch_pdl(k_smooth2_f64<MODE, 32, 16>, g, 256, 0, s, v.nx, v.ny, ih2, (const double2 *)a.w,
+                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by,
+                   (const double *)a.r, pin, p, rc, ecz, h2c, invdc, btc, ecp);
+    }
+}
+
 // nsw sweeps on one level, reading the iterate from cur and leaving it in the
 // returned buffer: FP32 in fused pairs, FP64 one sweep per launch (the FP64
 // sweep is bound by the FP64 pipe, where fusing only adds halo work).
@@ -1395,8 +1519,9 @@ T *smooth(const Level &v, LevelT<T> &a, T *cur, int nsw, bool fine, cudaStream_t
 // iterate moves between its two buffers (cur[l]); the coarse corrections
 // start in the canonical buffer, which the restriction zeroes, and level 0
 // ends in its canonical buffer (copied back when the sweep count is odd).
-// FP32 cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
-// restriction going down, prolongation + sweeps going up); given add64 (the
+// Cycles with nu1 = nu2 = 2 use the fused kernels (sweeps + residual +
+// restriction going down, prolongation + sweeps going up; FP32 and FP64
+// alike, other sweep counts one launch per sweep); given add64 (the
 // FP64 iterate of the defect correction), such a cycle adds its level-0
 // result to it in the last smoother and returns true (the FP32 level-0
 // iterate is then not stored).
@@ -1408,21 +1533,27 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *add64 = nullptr)
     };
     const int L = mg.L, lt = sizeof(T) == 8 ? mg.tail : mg.tail_f;
     constexpr bool f32 = sizeof(T) == 4;
-    const bool fused = f32 && nu1 == 2 && nu2 == 2;
+    const bool fused = nu1 == 2 && nu2 == 2;
     T *cur[kMaxLv];
     for (int l = 0; l < L; l++) cur[l] = lvT(l).e;
     for (int l = 0; l < lt; l++) {
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l), &c = lvT(l + 1);
         if (fused) {
+            const bool pr = l == 0 && prof_on(f32 ? kProfSweep32 : kProfSweep64);
+            if (pr) prof_mark(s, true);
+            T *nxt = other(a, cur[l]);
             if constexpr (f32) {
-                const bool pr = l == 0 && prof_on(kProfSweep32);
-                if (pr) prof_mark(s, true);
-                T *nxt = other(a, cur[l]);
                 launch_smooth2<1>(v, a, cur[l], nxt, c.r, c.e, nullptr, s);
-                if (pr) prof_mark(s, false);
-                cur[l] = nxt;
+            } else {
+                // the next level's pre-scaled right-hand side where it is swept
+                // by the fused kernels (above the tail)
+                const double hc = mg.lv[l + 1].h;
+                launch_smooth2_f64<1>(v, a, cur[l], nxt, c.r, c.e, hc * hc, c.invd,
+                                      l + 1 < lt ? c.bt : nullptr, nullptr, s);
             }
+            if (pr) prof_mark(s, false);
+            cur[l] = nxt;
         } else {
             cur[l] = smooth<T>(v, a, cur[l], nu1, l == 0, s);
             dim3 gr(cdiv(v.nx / 2, 128), v.ny / 2);
@@ -1458,19 +1589,23 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *add64 = nullptr)
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l);
         if (fused) {
+            const bool pr = l == 0 && prof_on(f32 ? kProfSweep32 : kProfSweep64);
+            if (pr) prof_mark(s, true);
             if constexpr (f32) {
-                const bool pr = l == 0 && prof_on(kProfSweep32);
-                if (pr) prof_mark(s, true);
                 if (l == 0 && add64) {
                     launch_smooth2<2>(v, a, cur[0], nullptr, nullptr, nullptr, cur[1], s, add64);
                     if (pr) prof_mark(s, false);
                     return true;
                 }
-                T *nxt = other(a, cur[l]);
-                launch_smooth2<2>(v, a, cur[l], nxt, nullptr, nullptr, cur[l + 1], s);
-                if (pr) prof_mark(s, false);
-                cur[l] = nxt;
             }
+            T *nxt = other(a, cur[l]);
+            if constexpr (f32)
+                launch_smooth2<2>(v, a, cur[l], nxt, nullptr, nullptr, cur[l + 1], s);
+            else
+                launch_smooth2_f64<2>(v, a, cur[l], nxt, nullptr, nullptr, 0.0, nullptr, nullptr,
+                                      cur[l + 1], s);
+            if (pr) prof_mark(s, false);
+            cur[l] = nxt;
         } else {
             dim3 gp(cdiv(v.nx, 128), v.ny);
             note_launch();
@@ -1725,8 +1860,8 @@ void mg_free(MG &mg)
 // One launch of one kernel of the cycle on the hierarchy's current data, for
 // kernel timing: op 0 FP32 two-sweep smoother, 1 FP64 sweep, 3 FP32 sweeps +
 // restriction, 4 FP32 prolongation + sweeps (+ the FP64 update at level 0),
-// all at `level`; 5 FP32 tail, 6 FP64 residual norm of the mixed solve
-// (level 0).  Returns the cells of the level, or -1 if the op does not exist
+// 7 FP64 sweeps + restriction, 8 FP64 prolongation + sweeps, all at
+// `level`; 5 FP32 tail, 6 FP64 residual norm of the mixed solve (level 0).  Returns the cells of the level, or -1 if the op does not exist
 // there.  Writes only solve scratch (second iterate buffers, coarse
 // right-hand sides and corrections, the level-0 FP64 iterate copy, FP32
 // residual, norm partials).
@@ -1767,6 +1902,18 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
         const size_t smem = tail_prepare(ta);
         launch_pdl(k_tail<float>, 1, 1024, smem, s, ta);
         return (long)mg.lv[lt].nx * mg.lv[lt].ny;
+    }
+    case 7:
+    case 8: {  // the fused FP64 smoothers (7: sweeps + restriction, 8: prolongation + sweeps)
+        if (level >= mg.tail) return -1;
+        Level &c = mg.lv[level + 1];
+        if (op == 7)
+            launch_smooth2_f64<1>(v, v.d, v.d.e, v.d.e2, c.d.r, c.d.e2, c.h * c.h, c.d.invd,
+                                  level + 1 < mg.tail ? c.d.bt : nullptr, nullptr, s);
+        else
+            launch_smooth2_f64<2>(v, v.d, v.d.e, v.d.e2, nullptr, nullptr, 0.0, nullptr, nullptr,
+                                  c.d.e, s);
+        return cells;
     }
     case 6: {
         Level &v0 = mg.lv[0];
