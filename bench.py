@@ -283,20 +283,22 @@ def run_reference(args):
 
 
 # Algorithmic work per cell of the fused FP64 V(2,2) kernels (pre-scaled
-# stencil, flux-form residual).  Bytes: sweeps + residual + restriction read
-# p, bt, 4 weights (48), b, beta_x, beta_y (24), the coarse 1/diag (2), write
-# p (8) and the coarse rc, btc, e (6); prolongation + sweeps read p, bt, the
-# weights (48) and the coarse correction (2), write p (8).  FP64 operations
-# (an FMA counted as two): a sweep 8; the residual 13 and the restriction 1;
-# the prolongation 8.
-FP64_RESTRICT = {"bytes": 88.0, "flops": 2 * 8.0 + 14.0}
-FP64_PROLONG = {"bytes": 58.0, "flops": 2 * 8.0 + 8.0}
+# stencil; restricted residual from the red-black residual identity).
+# Bytes: sweeps + residual + restriction read p, bt, the 4 weights (48),
+# beta_x, beta_y (16), the coarse 1/diag (2), write p (8) and the coarse rc,
+# btc, e (6); prolongation + sweeps read p, bt, the weights (48) and the
+# coarse correction (2), write p (8).  FP64 operations (an FMA counted as
+# two): a sweep 8 a cell; the residual 7 per red cell plus a subtraction per
+# black cell, the restriction and pre-scaling 4 per coarse cell (5); the
+# prolongation 7.
+FP64_RESTRICT = {"bytes": 80.0, "flops": 2 * 8.0 + 5.0}
+FP64_PROLONG = {"bytes": 58.0, "flops": 2 * 8.0 + 7.0}
 # Per fine cell and V(2,2) cycle: SURVEY's fused minimum (84 B per level cell
 # x 4/3 levels) and the per-kernel (unfused) accounting (212 B x 4/3); FP64
-# operations of the FP64 cycle: (4 sweeps x 8 + 14 + 8) x 4/3 + the fine
-# residual norm (15).
+# operations of the FP64 cycle: (4 sweeps x 8 + 5 + 7) x 4/3 + the fine
+# residual norm of the convergence test (15).
 VCYCLE_BYTES_FUSED, VCYCLE_BYTES_UNFUSED = 112.0, 283.0
-VCYCLE_FP64_FLOPS = (4 * 8.0 + 14.0 + 8.0) * 4.0 / 3.0 + 15.0
+VCYCLE_FP64_FLOPS = (4 * 8.0 + 5.0 + 7.0) * 4.0 / 3.0 + 15.0
 
 
 def timed_solve(torch, ctx, stream, flush, b, prec, start=None, reps=5, warm=3):

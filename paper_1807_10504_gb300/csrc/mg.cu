@@ -534,25 +534,32 @@ __device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
 // order), on a DW x DH tile: the iterate's window (halo HA) is staged in
 // shared memory and the sweeps run on shrinking rings (red, black, red,
 // black), each cell reading its weights and right-hand side from global
-// memory (L1 / L2), so the tile's result equals two global sweeps.  MODE 1:
-// then the residual b - A p of the tile's cells (the flux form of
-// k_restrict_residual, from beta and b) averaged over 2x2 children into the
-// coarse right-hand side rc, its pre-scaled copy btc = h_c^2 rc / diag_c
-// (when btc is given) and a zero coarse correction; the last black phase
-// covers the tile's one-cell ring so that the residual sees final values
-// (halo 5).  MODE 2: p + P e_c (bilinear prolongation of the coarse
-// correction) formed while staging, then the sweeps (halo 4).  The FP64 pipe
-// bounds the sweeps on this part, so the gain over separate launches is the
-// residual / restriction and prolongation passes and two of three launches
-// per level; tiles of 32 x 16 spread the small levels over more SMs.
+// memory (L1 / L2), so the tile's result equals two global sweeps.
+// MODE 1: then the residual of the tile's cells averaged over 2x2 children
+// into the coarse right-hand side rc, its pre-scaled copy btc = h_c^2 rc /
+// diag_c (when btc is given) and a zero coarse correction.  The residual is
+// taken from the last black half-sweep instead of b - A p: a relaxed cell
+// satisfies its own equation, so after that half-sweep every black cell's
+// residual is zero (to rounding) and a red cell's is -(1/h^2) sum_f beta_f
+// delta_f, the deltas being the changes of its four black neighbours in that
+// half-sweep (the residual identity of red-black Gauss-Seidel; four FP64
+// operations for two cells instead of ten a cell).  The last black phase
+// covers the tile's one-cell ring (halo 5), stores the tile's black cells
+// and keeps their deltas in shared memory in place of the values.
+// MODE 2: p + P e_c (bilinear prolongation of the coarse correction) formed
+// while staging, then the sweeps (halo 4).
+// The FP64 pipe bounds these kernels on this part (its instruction rate, not
+// HBM), so the design counts FP64 instructions: fused sweeps, the residual
+// identity, prolongation in FMAs; tiles of 32 x 16 spread the small levels
+// over more SMs.
 template <int MODE, int DW, int DH>
 __global__ void __launch_bounds__(256)
 k_smooth2_f64(int nx, int ny, double ih2, const double2 *__restrict__ w,
               const double *__restrict__ bt, const double *__restrict__ bx,
-              const double *__restrict__ by, const double *__restrict__ b,
-              const double *__restrict__ pin, double *__restrict__ p, double *__restrict__ rc,
-              double *__restrict__ ecz, double h2c, const double *__restrict__ invdc,
-              double *__restrict__ btc, const double *__restrict__ ecp)
+              const double *__restrict__ by, const double *__restrict__ pin,
+              double *__restrict__ p, double *__restrict__ rc, double *__restrict__ ecz,
+              double h2c, const double *__restrict__ invdc, double *__restrict__ btc,
+              const double *__restrict__ ecp)
 {
     constexpr int NT = 256;
     constexpr int HA = MODE == 1 ? 5 : 4;
@@ -567,12 +574,13 @@ k_smooth2_f64(int nx, int ny, double ih2, const double2 *__restrict__ w,
         if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
             v = pin[(long)gj * nx + gi];
             if (MODE == 2) {
+                // (9 c00 + 3 c10 + 3 c01 + c11) / 16 in three FMAs and an add
                 const int I = gi >> 1, J = gj >> 1;
                 const int I2 = min(max(I + ((gi & 1) ? 1 : -1), 0), nxc - 1);
                 const int J2 = min(max(J + ((gj & 1) ? 1 : -1), 0), nyc - 1);
                 const double c00 = ecp[(long)J * nxc + I], c10 = ecp[(long)J * nxc + I2];
                 const double c01 = ecp[(long)J2 * nxc + I], c11 = ecp[(long)J2 * nxc + I2];
-                v += (9.0 * c00 + 3.0 * c10 + 3.0 * c01 + c11) / 16.0;
+                v = fma(fma(9.0, c00, fma(3.0, c10 + c01, c11)), 0.0625, v);
             }
         }
         ps[r][c] = v;
@@ -594,30 +602,36 @@ k_smooth2_f64(int nx, int ny, double ih2, const double2 *__restrict__ w,
             double sm = fma(we.x, ps[r][c - 1], -bt[kc]);
             sm = fma(we.y, ps[r][c + 1], sm);
             sm = fma(sn.x, ps[r - 1][c], sm);
-            ps[r][c] = fma(sn.y, ps[r + 1][c], sm);
+            sm = fma(sn.y, ps[r + 1][c], sm);
+            if (MODE == 1 && ph == 3) {
+                // last black half-sweep: tile cells go out now, every black
+                // cell of the ring keeps its change for the residual
+                if (r >= HA && r < HA + DH && c >= HA && c < HA + DW) p[kc] = sm;
+                ps[r][c] = sm - ps[r][c];
+            } else {
+                ps[r][c] = sm;
+            }
         }
         __syncthreads();
     }
     if (MODE == 1) {
         const long nxf = nx + 1;
+        // -(1/h^2) sum_f beta_f delta_f of a red cell (its neighbours are black)
+        auto sbd = [&](int gi, int gj) {
+            const int r = gj - gj0, c = gi - gi0;
+            const long kc = (long)gj * nx + gi, kx = (long)gj * nxf + gi;
+            double sf = bx[kx + 1] * ps[r][c + 1];
+            sf = fma(bx[kx], ps[r][c - 1], sf);
+            sf = fma(by[kc + nx], ps[r + 1][c], sf);
+            return fma(by[kc], ps[r - 1][c], sf);
+        };
+        const double kr = -0.25 * ih2;
         for (int k = threadIdx.x; k < (DW / 2) * (DH / 2); k += NT) {
             const int I = blockIdx.x * (DW / 2) + (k % (DW / 2));
             const int J = blockIdx.y * (DH / 2) + (k / (DW / 2));
             if (I >= nxc || J >= nyc) continue;
-            auto res = [&](int gi, int gj) {
-                const int r = gj - gj0, c = gi - gi0;
-                const long kc = (long)gj * nx + gi, kx = (long)gj * nxf + gi;
-                const double pc = ps[r][c];
-                const double pE = gi + 1 < nx ? ps[r][c + 1] : pc, pW = gi > 0 ? ps[r][c - 1] : pc;
-                const double pN = gj + 1 < ny ? ps[r + 1][c] : pc, pS = gj > 0 ? ps[r - 1][c] : pc;
-                double sf = bx[kx + 1] * (pE - pc);
-                sf -= bx[kx] * (pc - pW);
-                sf += by[kc + nx] * (pN - pc);
-                sf -= by[kc] * (pc - pS);
-                return b[kc] - sf * ih2;
-            };
-            const int i = 2 * I, j = 2 * J;
-            const double rv = 0.25 * (res(i, j) + res(i + 1, j) + res(i, j + 1) + res(i + 1, j + 1));
+            // children (2I, 2J) and (2I+1, 2J+1) are red, the other two black
+            const double rv = (sbd(2 * I, 2 * J) + sbd(2 * I + 1, 2 * J + 1)) * kr;
             const long kcc = (long)J * nxc + I;
             rc[kcc] = rv;
             ecz[kcc] = 0.0;
@@ -627,7 +641,8 @@ k_smooth2_f64(int nx, int ny, double ih2, const double2 *__restrict__ w,
     for (int k = threadIdx.x; k < DH * DW; k += NT) {
         const int r = HA + k / DW, c = HA + (k % DW);
         const int gi = gi0 + c, gj = gj0 + r;
-        if (gi < nx && gj < ny) p[(long)gj * nx + gi] = ps[r][c];
+        // MODE 1 stored its black cells in the last phase
+        if (gi < nx && gj < ny && (MODE != 1 || ((gi + gj) & 1) == 0)) p[(long)gj * nx + gi] = ps[r][c];
     }
 }
 
@@ -1469,13 +1484,13 @@ void launch_smooth2_f64(const Level &v, const LevelT<double> &a, const double *p
     if ((long)v.nx * v.ny >= (1L << 18)) {
         dim3 g(cdiv(v.nx, 64), cdiv(v.ny, 32));
         launch_pdl(k_smooth2_f64<MODE, 64, 32>, g, 256, 0, s, v.nx, v.ny, ih2, (const double2 *)a.w,
-                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by,
-                   (const double *)a.r, pin, p, rc, ecz, h2c, invdc, btc, ecp);
+                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by, pin, p, rc,
+                   ecz, h2c, invdc, btc, ecp);
     } else {
         dim3 g(cdiv(v.nx, 32), cdiv(v.ny, 16));
         launch_pdl(k_smooth2_f64<MODE, 32, 16>, g, 256, 0, s, v.nx, v.ny, ih2, (const double2 *)a.w,
-                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by,
-                   (const double *)a.r, pin, p, rc, ecz, h2c, invdc, btc, ecp);
+                   (const double *)a.bt, (const double *)a.bx, (const double *)a.by, pin, p, rc,
+                   ecz, h2c, invdc, btc, ecp);
     }
 }
 
