@@ -148,8 +148,9 @@ def test_static_sphere_step_matches_oracle(T, ib, O):
 def test_steps_match_oracle(T, ib, O, spread, precision):
     # A deforming ellipsoid (Section 5.2 Eq. (osc) about the axis, beta 1.1):
     # relocation every 2 steps (with re-symmetrisation), 4 steps; the FP64
-    # path to 1e-9 of the oracle, the mixed-precision path (refined to the
-    # same residual) to 1e-6.
+    # path to 1e-10 of the oracle (p relative to max |p|, u and w relative to
+    # the inertial-capillary velocity sqrt(sigma / (rho_l R))), the
+    # mixed-precision path (refined to the same residual) to 1e-6.
     nx, ny = 32, 64
     h = 1.0 / nx
     mk = W.axi_elliptic_drop(1.0, 0.25, 1.1, 128)
@@ -161,15 +162,19 @@ def test_steps_match_oracle(T, ib, O, spread, precision):
     for _ in range(4):
         ctx.ns_step(dt, 1, 1)
         O.ns_step(ocfg, st, dt)
-    tol = 1e-9 if precision == 0 else 1e-6
+    tol = 1e-10 if precision == 0 else 1e-6
     X, Y = (a.cpu().numpy() for a in ctx.markers())
     xtol = 1e-12 if precision == 0 else 1e-9
     assert np.abs(X - st.X).max() <= xtol and np.abs(Y - st.Y).max() <= xtol
     n = len(X)
     k = np.arange(n)
     assert np.array_equal(X, -X[(n - k) % n]) and np.array_equal(Y, Y[(n - k) % n])
-    for name, ref in (("p", st.p), ("u", st.u), ("v", st.v)):
-        assert rel(ctx.get(name).cpu().numpy(), ref) <= tol, name
+    U = np.sqrt(1.0 / (1.0 * 0.25))
+    ep = rel(ctx.get("p").cpu().numpy(), st.p)
+    assert ep <= tol, ep
+    for name, ref in (("u", st.u), ("v", st.v)):
+        e = np.abs(ctx.get(name).cpu().numpy() - ref).max() / U
+        assert e <= tol, (name, e)
 
 
 def test_rejects_curves_that_are_not_meridians(T, ib):
@@ -189,9 +194,11 @@ def test_rejects_curves_that_are_not_meridians(T, ib):
 def test_free_fall_frame_matches_oracle(T, ib, O):
     # Gravity and the non-inertial frame (Section 2.4): 40 steps of a dense
     # sphere released from rest; the frame record, the fields and the markers
-    # follow the oracle's.  The frame's acceleration divides centre-of-mass
-    # differences by dt^2 (~6e-7 here), which lifts rounding differences of
-    # the positions (~1e-16) to ~1e-10 in S, so the fields compare at 1e-8.
+    # follow the oracle's: p within 1e-10 of max |p|, u and w within 1e-10 of
+    # the inertial-capillary velocity (measured: ~2e-13 and ~6e-13).  The
+    # frame's acceleration divides centre-of-mass differences by dt^2 (~6e-7
+    # here), which lifts rounding differences of the positions (~1e-16) to
+    # ~1e-10 in S; S itself is compared at 1e-6.
     nx, ny, h, R = 32, 96, 1 / 32, 0.25
     mk = W.axi_sphere(1.0, R, 96)
     kw = dict(axisym=1, frame=1, gy=-1.0, relocate_every=10, spread=1, tol=1e-11)
@@ -207,8 +214,10 @@ def test_free_fall_frame_matches_oracle(T, ib, O):
     assert abs(vf - f["Vf"]) <= 1e-7 * abs(f["Vf"]) and abs(wb + vf) == 0.0
     assert abs(com - f["com_prev"]) <= 1e-12
     assert abs(S - f["S"]) <= 1e-6 * max(abs(f["S"]), 1.0)
-    for name, ref in (("p", st.p), ("u", st.u), ("v", st.v)):
-        assert rel(ctx.get(name).cpu().numpy(), ref) <= 1e-8, name
+    ep = rel(ctx.get("p").cpu().numpy(), st.p)
+    U = np.sqrt(1.0 / (1.0 * R))
+    eu = max(np.abs(ctx.get(n).cpu().numpy() - r).max() for n, r in (("u", st.u), ("v", st.v))) / U
+    assert ep <= 1e-10 and eu <= 1e-10, (ep, eu)
     X, Y = (a.cpu().numpy() for a in ctx.markers())
     assert np.abs(X - st.X).max() <= 1e-12 and np.abs(Y - st.Y).max() <= 1e-12
     with pytest.raises(ib.IBError):  # the frame needs the axisymmetric form

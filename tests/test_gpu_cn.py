@@ -61,8 +61,14 @@ def test_cn_steps_match_oracle(T, ib, O, axisym):
     for _ in range(5):
         ctx.ns_step(dt, 1, 1)
         O.ns_step(ocfg, st, dt)
-    for name, ref in (("p", st.p), ("u", st.u), ("v", st.v)):
+    # p within 1e-10 of max |p|; u, v within 1e-10 of the inertial-capillary
+    # velocity sqrt(sigma / (rho_l R)) (the viscous solve's sweeps are the
+    # oracle's, so only rounding separates them)
+    U = np.sqrt(1.0 / (1.0 * 0.25))
+    got = ctx.get("p").cpu().numpy()
+    assert np.abs(got - st.p).max() <= 1e-10 * np.abs(st.p).max(), np.abs(got - st.p).max()
+    for name, ref in (("u", st.u), ("v", st.v)):
         got = ctx.get(name).cpu().numpy()
-        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), name
+        assert np.abs(got - ref).max() <= 1e-10 * U, (name, np.abs(got - ref).max())
     X, Y = (a.cpu().numpy() for a in ctx.markers())
     assert np.abs(X - st.X).max() <= 1e-12 and np.abs(Y - st.Y).max() <= 1e-12

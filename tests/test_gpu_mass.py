@@ -82,4 +82,4 @@ def test_steps_with_correction_match_oracle(T, ib, O):
     X, Y = (a.cpu().numpy() for a in ctx.markers())
     assert np.abs(X - st.X).max() <= 1e-12 and np.abs(Y - st.Y).max() <= 1e-12
     p = ctx.get("p").cpu().numpy()
-    assert np.abs(p - st.p).max() <= 1e-9 * np.abs(st.p).max()
+    assert np.abs(p - st.p).max() <= 1e-10 * np.abs(st.p).max(), np.abs(p - st.p).max()
