@@ -273,6 +273,23 @@ ib_status cnn_grad(ib_cnn *net, int32_t B, int32_t N, double h, const double *rh
 ib_status cnn_train_step(ib_cnn *net, int32_t B, int32_t N, double h,
                          const double *rhs, const double *rho, const double *p,
                          float lr, float *loss, void *stream);
+/* The pressure scale c from training data (device FP64, B samples of
+ * N x N, cell size h): the median over the samples of
+ * rms(p - mean p) / (rms(b - mean b) h^2), samples with a constant b
+ * skipped, the mean of the two middle values for an even count.  Sets the
+ * network's scale and returns it in *c_out (host, may be NULL); synchronises.
+ * IB_EINVAL if no sample has a varying b.                                  */
+ib_status cnn_fit_scale(ib_cnn *net, int32_t B, int32_t N, double h, const double *rhs,
+                        const double *p, double *c_out, void *stream);
+/* Training run: cnn_fit_scale on all nsamples samples, then `steps` Adam
+ * steps, each on `batch` samples drawn with replacement by a SplitMix64
+ * stream of `seed` and gathered on the device, the learning rate
+ * lr0 * 0.1^(k / steps) at step k (a tenfold decay over the run).  losses
+ * (host, `steps` floats) receives each step's batch loss; one
+ * synchronisation at the end.                                              */
+ib_status cnn_train(ib_cnn *net, int32_t nsamples, int32_t N, double h, const double *rhs,
+                    const double *rho, const double *p, int32_t steps, int32_t batch,
+                    float lr0, uint64_t seed, float *losses, void *stream);
 /* p0 (device FP64, B x N x N) = network estimate of the pressure.  With
  * cnn_set_coarsen(net, k), k > 0, rhs and rho are first averaged over
  * 2^k x 2^k blocks, the network runs on that grid (cell size h 2^k) and its

@@ -88,21 +88,42 @@ def up2_bwd(g):
     return g.reshape(B, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(P, x, keep=False):
-    """x (B, N, N, 2) -> y (B, N, N, 1); with keep=True also the cache."""
+def bf16_round(a):
+    """The nearest bfloat16 value (8-bit significand, round to nearest, ties
+    to even) of each element, after rounding to binary32 (the storage of a
+    binary32 value as bfloat16); returned as float64."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def forward(P, x, keep=False, bf16=False):
+    """x (B, N, N, 2) -> y (B, N, N, 1); with keep=True also the cache.
+
+    bf16=True evaluates the network as BF16 activations with wider
+    accumulation (the precision the learned part is specified in): every
+    stored activation -- each hidden layer's output after bias and ReLU, and
+    each pooled tensor -- is rounded to BF16 (bf16_round); the sums inside a
+    convolution stay FP64 and the last layer's output is not rounded."""
     cache = {}
+    r = bf16_round if bf16 else _ident
 
     def conv(name, inp, relu):
         z = conv3x3(inp, P[name + ".w"], P[name + ".b"])
-        out = np.maximum(z, 0.0) if relu else z
+        out = r(np.maximum(z, 0.0)) if relu else z
         cache[name] = (inp, z)
         return out
 
     a = conv("c1a", x, True)
     s1 = conv("c1b", a, True)
-    a = conv("c2a", pool2(s1), True)
+    a = conv("c2a", r(pool2(s1)), True)
     s2 = conv("c2b", a, True)
-    a = conv("c3a", pool2(s2), True)
+    a = conv("c3a", r(pool2(s2)), True)
     t3 = conv("c3b", a, True)
     t4 = conv("c4", np.concatenate([up2(t3), s2], axis=3), True)
     a = conv("c5", np.concatenate([up2(t4), s1], axis=3), True)
@@ -110,9 +131,15 @@ def forward(P, x, keep=False):
     return (y, cache) if keep else y
 
 
-def backward(P, cache, gy):
-    """Gradients of sum(gy * forward(P, x)) w.r.t. every parameter and x."""
+def backward(P, cache, gy, bf16=False):
+    """Gradients of sum(gy * forward(P, x)) w.r.t. every parameter and x.
+
+    bf16=True: the BF16 counterpart of forward(bf16=True) -- every stored
+    gradient tensor (gy itself, each layer's input gradient, the folded
+    up-sampling gradients and the skip sums) is rounded to BF16; parameter
+    gradients stay FP64 sums."""
     G = {}
+    r = bf16_round if bf16 else _ident
 
     def conv_b(name, g, relu):
         inp, z = cache[name]
@@ -120,19 +147,19 @@ def backward(P, cache, gy):
             g = g * (z > 0)
         gx, gw, gb = conv3x3_bwd(inp, P[name + ".w"], g)
         G[name + ".w"], G[name + ".b"] = gw, gb
-        return gx
+        return r(gx)
 
     c2 = P["c4.w"].shape[0]
-    g = conv_b("c6", gy, False)
+    g = conv_b("c6", r(gy), False)
     g = conv_b("c5", g, True)
     g_up4, g_s1 = g[..., :c2], g[..., c2:]
-    g = conv_b("c4", up2_bwd(g_up4), True)
+    g = conv_b("c4", r(up2_bwd(g_up4)), True)
     g_up3, g_s2 = g[..., :c2], g[..., c2:]
-    g = conv_b("c3b", up2_bwd(g_up3), True)
+    g = conv_b("c3b", r(up2_bwd(g_up3)), True)
     g = conv_b("c3a", g, True)
-    g = conv_b("c2b", pool2_bwd(g) + g_s2, True)
+    g = conv_b("c2b", r(pool2_bwd(g) + g_s2), True)
     g = conv_b("c2a", g, True)
-    g = conv_b("c1b", pool2_bwd(g) + g_s1, True)
+    g = conv_b("c1b", r(pool2_bwd(g) + g_s1), True)
     gx = conv_b("c1a", g, True)
     return G, gx
 

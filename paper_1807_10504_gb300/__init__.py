@@ -38,7 +38,7 @@ EXPORTS = [
     "ib_attach_cnn", "ib_use_graphs", "cnn_set_scale", "cnn_get_scale", "cnn_set_coarsen",
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
     "ib_mass_correct", "ib_op_cn_solve", "ns_step_io", "mg_solve_noalloc_error",
-    "ib_debug_stall_staging", "ib_probe_fp64",
+    "ib_debug_stall_staging", "ib_probe_fp64", "cnn_fit_scale", "cnn_train",
 ]
 
 
@@ -106,6 +106,9 @@ def lib():
             "cnn_train_step": [_P, _i32, _i32, _d, _P, _P, _P, C.c_float, C.POINTER(C.c_float),
                                _P],
             "cnn_infer": [_P, _i32, _i32, _d, _P, _P, _P, _P],
+            "cnn_fit_scale": [_P, _i32, _i32, _d, _P, _P, C.POINTER(_d), _P],
+            "cnn_train": [_P, _i32, _i32, _d, _P, _P, _P, _i32, _i32, C.c_float, C.c_uint64, _P,
+                          _P],
             "cnn_set_scale": [_P, _d], "cnn_set_coarsen": [_P, _i32],
             "ib_bench_kernel": [_P, C.c_int, C.c_int, C.c_int, _P, _P],
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
@@ -450,6 +453,27 @@ class Net:
         _check(lib().cnn_train_step(self._h, B, N, h, _ptr(rhs), _ptr(rho), _ptr(p), lr,
                                     C.byref(loss), _stream()), None, "cnn_train_step")
         return loss.value
+
+    def fit_scale(self, rhs, p, h=None) -> float:
+        """Set (and return) the pressure scale c from samples (B, N, N) of the
+        right-hand side and the pressure (cnn_fit_scale)."""
+        B, N = rhs.shape[0], rhs.shape[-1]
+        h = 1.0 / N if h is None else h
+        c = C.c_double(0.0)
+        _check(lib().cnn_fit_scale(self._h, B, N, h, _ptr(rhs), _ptr(p), C.byref(c), _stream()),
+               None, "cnn_fit_scale")
+        return c.value
+
+    def train(self, rhs, rho, p, steps, batch=16, lr=2e-3, seed=0, h=None):
+        """A training run on samples (n, N, N) (cnn_train): the scale fit,
+        then `steps` Adam steps on random mini-batches with the learning rate
+        decaying tenfold; returns the list of batch losses."""
+        n, N = rhs.shape[0], rhs.shape[-1]
+        h = 1.0 / N if h is None else h
+        losses = np.empty(steps, np.float32)
+        _check(lib().cnn_train(self._h, n, N, h, _ptr(rhs), _ptr(rho), _ptr(p), steps, batch, lr,
+                               seed, losses.ctypes.data, _stream()), None, "cnn_train")
+        return losses.tolist()
 
     def set_coarsen(self, levels: int):
         """Run inference on the grid coarsened by 2^levels (inputs averaged,

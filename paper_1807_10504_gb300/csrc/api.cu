@@ -1094,6 +1094,33 @@ ib_status cnn_train_step(ib_cnn *h, int32_t B, int32_t N, double hs, const doubl
     return cudaGetLastError() == cudaSuccess ? IB_OK : IB_ECUDA;
 }
 
+ib_status cnn_fit_scale(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
+                        const double *p, double *c_out, void *stream)
+{
+    if (!h || B < 1 || N < 1 || !(hs > 0) || !rhs || !p) return IB_EINVAL;
+    double c = 0.0;
+    cudaError_t e = ibk::cnn_fit_scale(*h->n, B, N, hs, rhs, p, &c, (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return IB_EINVAL;
+    if (e == cudaErrorMemoryAllocation) return IB_ENOMEM;
+    if (e != cudaSuccess) return IB_ECUDA;
+    if (c_out) *c_out = c;
+    return IB_OK;
+}
+
+ib_status cnn_train(ib_cnn *h, int32_t nsamples, int32_t N, double hs, const double *rhs,
+                    const double *rho, const double *p, int32_t steps, int32_t batch, float lr0,
+                    uint64_t seed, float *losses, void *stream)
+{
+    if (!h || nsamples < 1 || N < 4 || N % 4 || !(hs > 0) || !rhs || !rho || !p || steps < 1 ||
+        batch < 1 || !(lr0 > 0.0f) || !losses)
+        return IB_EINVAL;
+    cudaError_t e = ibk::cnn_train_loop(*h->n, nsamples, N, hs, rhs, rho, p, steps, batch, lr0,
+                                        seed, losses, (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return IB_EINVAL;
+    if (e == cudaErrorMemoryAllocation) return IB_ENOMEM;
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
 ib_status cnn_infer(ib_cnn *h, int32_t B, int32_t N, double hs, const double *rhs,
                     const double *rho, double *p0, void *stream)
 {

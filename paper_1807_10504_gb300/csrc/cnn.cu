@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ib_internal.cuh"
@@ -586,6 +587,59 @@ __global__ void k_unpack_grad(int ci, int co, int cip, const float *__restrict__
 
 }  // namespace
 
+// rms of (a - mean a) of each sample (one CTA per sample, fixed order: the
+// mean first, then the squared deviations).
+__global__ void __launch_bounds__(256) k_sample_rms(int N2, const double *__restrict__ a,
+                                                    double *__restrict__ out)
+{
+    __shared__ double sh[256];
+    const double *x = a + (long)blockIdx.x * N2;
+    double t = 0.0;
+    for (int k = threadIdx.x; k < N2; k += 256) t += x[k];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double m = sh[0] / N2;
+    __syncthreads();
+    double q = 0.0;
+    for (int k = threadIdx.x; k < N2; k += 256) {
+        const double d = x[k] - m;
+        q += d * d;
+    }
+    sh[threadIdx.x] = q;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(sh[0] / N2);
+}
+
+// Mini-batch gather: sample idx[i] of each set into slot i.
+__global__ void k_gather3(long n, int N2, const int *__restrict__ idx, const double *__restrict__ a,
+                          const double *__restrict__ b, const double *__restrict__ c,
+                          double *__restrict__ ga, double *__restrict__ gb, double *__restrict__ gc)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long src = (long)idx[k / N2] * N2 + k % N2;
+    ga[k] = a[src];
+    gb[k] = b[src];
+    gc[k] = c[src];
+}
+
+// The batch loss (sum of the per-sample partials, in order) into out.
+__global__ void k_loss_record(int B, const float *__restrict__ lsum, float *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    float t = 0.0f;
+    for (int b = 0; b < B; b++) t += lsum[b];
+    *out = t;
+}
+
 // ======================================================================= host
 struct CnnLayer {
     int ci, co, cip, cop;     // real and padded channel counts
@@ -970,6 +1024,89 @@ cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, 
         k_prolong2<<<cdiv(m, 256), 256, 0, s>>>(m, N >> k, pk[k], pk[k - 1]);
     }
     return cudaGetLastError();
+}
+
+// The network's pressure scale from training data: c = the median over the
+// samples of rms(p - mean p) / (rms(b - mean b) h^2) (samples with b = const
+// skipped; the mean of the two middle values for an even count).  Sets it
+// and returns it in *c.
+cudaError_t cnn_fit_scale(Cnn &n, int B, int N, double h, const double *rhs, const double *p,
+                          double *c, cudaStream_t s)
+{
+    const int N2 = N * N;
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)2 * B * 8);
+    if (e != cudaSuccess) return e;
+    note_launch(2);
+    k_sample_rms<<<B, 256, 0, s>>>(N2, rhs, d);
+    k_sample_rms<<<B, 256, 0, s>>>(N2, p, d + B);
+    std::vector<double> hv((size_t)2 * B);
+    e = cudaMemcpyAsync(hv.data(), d, (size_t)2 * B * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return e;
+    std::vector<double> r;
+    for (int k = 0; k < B; k++)
+        if (hv[k] > 0.0) r.push_back(hv[B + k] / (hv[k] * h * h));
+    if (r.empty()) return cudaErrorInvalidValue;
+    std::sort(r.begin(), r.end());
+    const size_t m = r.size();
+    const double med = m % 2 ? r[m / 2] : 0.5 * (r[m / 2 - 1] + r[m / 2]);
+    if (!(med > 0.0)) return cudaErrorInvalidValue;
+    n.out_scale = med;
+    *c = med;
+    return cudaSuccess;
+}
+
+// Training: the pressure scale from all samples, then `steps` Adam steps on
+// mini-batches of `batch` samples drawn with replacement by a SplitMix64
+// stream of `seed`, the learning rate decaying tenfold over the run
+// (lr0 0.1^(k / steps)); the batch losses land in losses_host (steps floats)
+// with one synchronisation at the end.
+cudaError_t cnn_train_loop(Cnn &n, int ns, int N, double h, const double *rhs, const double *rho,
+                           const double *p, int steps, int batch, float lr0, unsigned long long seed,
+                           float *losses_host, cudaStream_t s)
+{
+    double c = 0.0;
+    cudaError_t e = cnn_fit_scale(n, ns, N, h, rhs, p, &c, s);
+    if (e != cudaSuccess) return e;
+    e = cnn_workspace(n, batch, N);
+    if (e != cudaSuccess) return e;
+    const long N2 = (long)N * N, nb = (long)batch * N2;
+    std::vector<int> idx((size_t)steps * batch);
+    unsigned long long st = seed;
+    for (auto &v : idx) {
+        st += 0x9E3779B97F4A7C15ULL;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        v = (int)((z ^ (z >> 31)) % (unsigned long long)ns);
+    }
+    char *mem = nullptr;
+    const size_t bytes = al((size_t)nb * 8) * 3 + al(idx.size() * 4) + al((size_t)steps * 4);
+    e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) return e;
+    double *gb = (double *)mem, *gr = (double *)(mem + al((size_t)nb * 8)),
+           *gp = (double *)(mem + 2 * al((size_t)nb * 8));
+    int *didx = (int *)(mem + 3 * al((size_t)nb * 8));
+    float *dloss = (float *)(mem + 3 * al((size_t)nb * 8) + al(idx.size() * 4));
+    e = cudaMemcpyAsync(didx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, s);
+    for (int k = 0; k < steps && e == cudaSuccess; k++) {
+        note_launch();
+        k_gather3<<<cdiv(nb, 256), 256, 0, s>>>(nb, (int)N2, didx + (size_t)k * batch, rhs, rho, p,
+                                                gb, gr, gp);
+        cnn_forward(n, batch, N, h, gb, gr, gp, s);
+        cnn_backward(n, batch, N, s);
+        note_launch();
+        k_loss_record<<<1, 32, 0, s>>>(batch, n.lsum, dloss + k);
+        cnn_adam(n, (float)((double)lr0 * pow(0.1, (double)k / (double)steps)), s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(losses_host, dloss, (size_t)steps * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mem);
+    return e;
 }
 
 void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }

@@ -314,6 +314,11 @@ void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s);
 cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
                              double *p0, int levels, cudaStream_t s);
 void cnn_set_scale(Cnn &n, double c);
+cudaError_t cnn_fit_scale(Cnn &n, int B, int N, double h, const double *rhs, const double *p,
+                          double *c, cudaStream_t s);
+cudaError_t cnn_train_loop(Cnn &n, int ns, int N, double h, const double *rhs, const double *rho,
+                           const double *p, int steps, int batch, float lr0, unsigned long long seed,
+                           float *losses_host, cudaStream_t s);
 double cnn_get_scale(const Cnn &n);
 const void *cnn_workspace_ptr(const Cnn &n);  // current activation workspace (moves when it grows)
 const void *cnn_cbuf_ptr(const Cnn &n);       // current coarse-grid buffer

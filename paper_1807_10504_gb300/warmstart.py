@@ -10,8 +10,6 @@ runs on the GPU through the C ABI; this module only sequences the calls.
 """
 from __future__ import annotations
 
-import time
-
 import numpy as np
 
 import workloads as W
@@ -67,35 +65,12 @@ def generate(n_samples, n_cells=128, seed=0, every=5, steps_per_run=40, precisio
     return B, R, P
 
 
-def pressure_scale(data):
-    """The constant c of the network's pressure scale s h^2 c: the median over
-    the samples of rms(p - mean p) / (rms(b - mean b) h^2), h = 1/N."""
+def train(net: Net, data, steps=1000, batch=16, lr=2e-3, seed=0):
+    """One training run on the solver-generated samples (``cnn_train``: the
+    pressure scale fitted from the data, then Adam on random mini-batches with
+    the learning rate decaying tenfold); returns the list of batch losses."""
     B, R, P = data
-    N = B.shape[-1]
-    b0 = B - B.mean(dim=(1, 2), keepdim=True)
-    p0 = P - P.mean(dim=(1, 2), keepdim=True)
-    sb = b0.pow(2).mean(dim=(1, 2)).sqrt()
-    sp = p0.pow(2).mean(dim=(1, 2)).sqrt()
-    return float((sp / (sb / N ** 2)).median())
-
-
-def train(net: Net, data, steps=1000, batch=16, lr=2e-3, seed=0, time_budget=None):
-    """Adam on random mini-batches; returns the list of batch losses.  Sets
-    the network's pressure scale from the data first."""
-    torch = _torch()
-    B, R, P = data
-    net.scale = pressure_scale(data)
-    gen = torch.Generator(device="cpu").manual_seed(seed)
-    losses = []
-    t0 = time.perf_counter()
-    for k in range(steps):
-        idx = torch.randint(0, B.shape[0], (batch,), generator=gen).cuda()
-        lr_k = lr * (0.1 ** (k / max(steps, 1)))  # exponential decay to lr / 10
-        losses.append(net.train_step(B[idx].contiguous(), R[idx].contiguous(),
-                                     P[idx].contiguous(), lr_k))
-        if time_budget is not None and time.perf_counter() - t0 > time_budget:
-            break
-    return losses
+    return net.train(B, R, P, steps, batch, lr, seed)
 
 
 def evaluate(net: Net, n_cells=512, ndrops=8, seed=1810, steps=6, precision=1, reps=5):

@@ -82,10 +82,20 @@ def test_forward_matches_oracle(T):
     d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
     p0 = net.infer(d(rhs), d(rho)).cpu().numpy()
     x, s, _ = oracle_inputs(rhs, rho, p)
-    y = OC.forward(Pq, x)[..., 0]
+    # the oracle with BF16 storage of every activation (its sums FP64): the
+    # kernels' sums are FP32, so a stored value can land one BF16 step away
+    # (~0.4 %) where the two sums straddle a rounding boundary; element by
+    # element within 2 BF16 steps of the output's own scale
+    y = OC.forward(Pq, x, bf16=True)[..., 0]
     ref = s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True))
-    err = np.linalg.norm(p0 - ref) / np.linalg.norm(ref)
-    assert err < 3e-2, err
+    scale = np.sqrt((ref ** 2).mean(axis=(1, 2), keepdims=True))
+    e = np.abs(p0 - ref) / scale
+    print("forward: max element error / rms", e.max(), "99.9%", np.quantile(e, 0.999))
+    assert e.max() <= 2 * 2.0 ** -8, e.max()
+    # and the FP64 network within BF16's bound in norm
+    y64 = OC.forward(Pq, x)[..., 0]
+    ref64 = s[:, None, None] * (y64 - y64.mean(axis=(1, 2), keepdims=True))
+    assert np.linalg.norm(p0 - ref64) / np.linalg.norm(ref64) < 3e-2
 
 
 def prolong2(c):
@@ -133,29 +143,34 @@ def test_gradients_match_oracle(T):
     net = ib.Net(seed=0)
     net.set_params(flat_of(P))
     rhs, rho, p = batch(B, N, 5)
-    c = fitted_scale(rhs, p)
-    net.scale = c
     d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    c = net.fit_scale(d(rhs), d(p))
+    assert abs(c - fitted_scale(rhs, p)) <= 1e-12 * c
     loss, g = net.grad(d(rhs), d(rho), d(p))
     x, s, t = oracle_inputs(rhs, rho, p, c)
-    y, cache = OC.forward(Pq, x, keep=True)
+    y, cache = OC.forward(Pq, x, keep=True, bf16=True)
     L, gy = OC.loss(y, t)
-    G, _ = OC.backward(Pq, cache, gy)
-    assert abs(loss - L) <= 3e-2 * L
+    G, _ = OC.backward(Pq, cache, gy, bf16=True)
+    assert abs(loss - L) <= 1e-2 * L, (loss, L)
     Gg = dict_of(g, P)
     # The last bias has an exactly zero gradient (the loss ignores constant
-    # shifts of the output); every other gradient must point the same way as
-    # the FP64 one (BF16 activations and gradients round at every layer, and
-    # the pixel sums cancel, so the relative error grows towards the input).
+    # shifts of the output).  Every other parameter gradient element by
+    # element against the oracle's BF16 replay (BF16 activations and
+    # gradients, FP64 sums): within 5 % of the layer's largest gradient
+    # (the kernels' FP32 sums move some stored values by one BF16 step, and
+    # those steps accumulate towards the input layers), so that a wrong
+    # channel, tap or pixel index fails at the scale of the layer.
     assert abs(Gg["c6.b"][0]) <= 2e-3 * np.linalg.norm(G["c6.w"])
+    worst = {}
     for n, _, _, _ in OC.LAYERS:
         for k in (".w", ".b"):
             if n + k == "c6.b":
                 continue
             a, ref = Gg[n + k].ravel(), G[n + k].ravel()
-            cos = a @ ref / (np.linalg.norm(a) * np.linalg.norm(ref))
-            err = np.linalg.norm(a - ref) / np.linalg.norm(ref)
-            assert cos > 0.99 and err < 0.15, (n + k, cos, err)
+            e = np.abs(a - ref).max() / np.abs(ref).max()
+            worst[n + k] = e
+            assert e <= 5e-2, (n + k, e)
+    print("gradients: max element error / layer max", worst)
 
 
 def test_training_reduces_loss_and_is_deterministic(T):
@@ -171,6 +186,17 @@ def test_training_reduces_loss_and_is_deterministic(T):
         runs.append((losses, net.get_params()))
     losses = runs[0][0]
     assert losses[-1] < 0.5 * losses[0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and runs[0][0] == runs[1][0]
+    # the training run behind the C ABI (mini-batches drawn on the host by a
+    # seeded stream, learning rate decaying tenfold): deterministic, and the
+    # loss falls
+    runs = []
+    for _ in range(2):
+        net = ib.Net(seed=4)
+        losses = net.train(d(rhs), d(rho), d(p), steps=60, batch=2, lr=2e-3, seed=9)
+        runs.append((losses, net.get_params(), net.scale))
+    assert runs[0][2] == fitted_scale(rhs, p) or abs(runs[0][2] / fitted_scale(rhs, p) - 1) < 1e-12
+    assert np.mean(runs[0][0][-10:]) < 0.5 * np.mean(runs[0][0][:10])
     assert np.array_equal(runs[0][1], runs[1][1]) and runs[0][0] == runs[1][0]
 
 

@@ -95,3 +95,39 @@ def test_first_adam_step_is_a_sign_step():
     V = {"a": np.zeros(3)}
     cnn.adam(P, G, M, V, 1, lr=0.1, eps=0.0)
     assert np.allclose(P["a"], [0.9, -1.9, 0.4], rtol=0, atol=1e-14)
+
+
+def test_bf16_rounding_matches_the_format():
+    # bfloat16 is binary32 with the significand cut to 8 bits, rounded to
+    # nearest with ties to even: the library's conversion is the reference
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    a = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000),
+                        [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 0.0, -0.0]])
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.bf16_round(a), ref)
+
+
+def test_bf16_replay_stores_bf16_and_stays_near_the_fp64_network():
+    # the BF16 replay's stored activations are BF16 values, its output is
+    # within BF16's relative precision of the FP64 network, and its gradients
+    # within BF16-storage error of the FP64 gradients (15 % in norm: the
+    # relative error grows towards the input layers)
+    P = cnn.init_params(seed=4)
+    x = np.random.default_rng(5).standard_normal((2, 16, 16, 2))
+    x = cnn.bf16_round(x)
+    y64, c64 = cnn.forward(P, x, keep=True)
+    y16, c16 = cnn.forward(P, x, keep=True, bf16=True)
+    for name in ("c1b", "c2a", "c4", "c5", "c6"):
+        inp = c16[name][0]
+        assert np.array_equal(cnn.bf16_round(inp), inp), name
+    assert np.linalg.norm(y16 - y64) / np.linalg.norm(y64) < 2e-2
+    t = np.random.default_rng(6).standard_normal(y64.shape)
+    _, g64 = cnn.loss(y64, t)
+    _, g16 = cnn.loss(y16, t)
+    G64, _ = cnn.backward(P, c64, g64)
+    G16, _ = cnn.backward(P, c16, g16, bf16=True)
+    for k in G64:
+        if k == "c6.b":
+            continue
+        assert np.linalg.norm(G16[k] - G64[k]) <= 0.15 * np.linalg.norm(G64[k]), k
