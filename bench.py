@@ -379,6 +379,17 @@ def solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak)
     return solve, kernels
 
 
+def coarsen_for(n, args):
+    """Halvings of an n x n grid before network inference: the given
+    --cnn-coarsen, or (-1) as many as bring it to the training grid."""
+    if args.cnn_coarsen >= 0:
+        return args.cnn_coarsen
+    k = 0
+    while (n >> (k + 1)) >= args.cnn_grid and (n >> (k + 1)) % 4 == 0:
+        k += 1
+    return k
+
+
 def steps_rate(ctx, torch, stream, flush, dt, warm, K):
     """Device-timed steps/s of K steps (CUDA events per step, L2 flushed
     before each)."""
@@ -409,10 +420,12 @@ def scale_pass(ib, torch, args, stream, flush, net, pk, fp64_peak):
             c.ns_step(dt, 1, args.warm)
         out[key] = steps_rate(c, torch, stream, flush, dt, args.warm, args.scale_steps)
         if prec == 2:
+            if net is not None:
+                net.set_coarsen(coarsen_for(nx, args))
             solve, kernels = solve_and_kernels(ib, torch, c, stream, flush, nx, ny, net, pk,
                                                fp64_peak)
             if net is not None:
-                solve["mixed_cnn"]["inference_grid"] = nx >> args.cnn_coarsen
+                solve["mixed_cnn"]["inference_grid"] = nx >> coarsen_for(nx, args)
             out["pressure_solve_ms"] = solve
             out["kernels"] = kernels
             us32 = kernels["level0"]["fp32_prolong_sweeps2_us"]
@@ -465,7 +478,7 @@ def run_ours(args):
     if args.ncu_cnn:
         # network inference on this step's system inside a profiler range
         net = ib.Net(seed=0)
-        net.set_coarsen(args.cnn_coarsen)
+        net.set_coarsen(coarsen_for(nx, args))
         b, rho = ctx.get("b"), ctx.get("rho")
         net.infer(b[None], rho[None])
         torch.cuda.synchronize()
@@ -531,22 +544,32 @@ def run_ours(args):
     # mixed precision from the learned warm start: a network trained here on
     # solver-generated 128^2 samples (its own kernels), inference inside the
     # timed region
-    net, train = None, None
+    net, train, cnn_eval = None, None, None
     if not args.no_cnn:
         from paper_1807_10504_gb300 import warmstart as WS
         t0 = time.perf_counter()
-        data = WS.generate(args.cnn_samples, n_cells=128, seed=0)
+        data = WS.generate(args.cnn_samples, n_cells=args.cnn_grid, seed=0)
+        t_gen = time.perf_counter() - t0
         net = ib.Net(seed=0)
-        losses = WS.train(net, data, steps=args.cnn_steps, batch=16, lr=2e-3)
+        losses = WS.train(net, data, steps=args.cnn_steps, batch=args.cnn_batch, lr=2e-3)
         del data
-        train = {"samples": args.cnn_samples, "steps": len(losses), "final_loss": losses[-1],
-                 "seconds": time.perf_counter() - t0}
-        net.set_coarsen(args.cnn_coarsen)
+        train = {"samples": args.cnn_samples, "grid": args.cnn_grid, "steps": len(losses),
+                 "batch": args.cnn_batch, "first_loss": float(np.mean(losses[:20])),
+                 "final_loss": float(np.mean(losses[-20:])), "generate_s": t_gen,
+                 "train_s": time.perf_counter() - t0 - t_gen}
+        # the learned warm start's evaluation case: an unseen seeded 512^2
+        # system with 8 drops, cold / previous-step / network starts to 1e-10
+        net.set_coarsen(coarsen_for(512, args))
+        cnn_eval = {"grid": 512, "drops": 8, "inference_grid": 512 >> coarsen_for(512, args)}
+        for prec in (1, 2):
+            cnn_eval[f"precision{prec}"] = WS.evaluate(net, n_cells=512, ndrops=8, seed=1810,
+                                                      precision=prec)
+        net.set_coarsen(coarsen_for(nx, args))
 
     solve, kernels = solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak)
     if train is not None:
         solve["mixed_cnn"]["train"] = train
-        solve["mixed_cnn"]["inference_grid"] = nx >> args.cnn_coarsen
+        solve["mixed_cnn"]["inference_grid"] = nx >> coarsen_for(nx, args)
     us32, cells = kernels["level0"]["fp32_prolong_sweeps2_us"], kernels["level0"]["cells"]
     us64 = kernels["level0"]["fp64_sweep_us"]
     usb, pairs = ctx.bench_kernel(2, 10)
@@ -633,6 +656,7 @@ def run_ours(args):
                    "l2": "flushed before each step (256 MiB)",
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
+        "learned_warm_start_512": cnn_eval,
         "fp64_steps_per_s": fp64_rate,
         "fp64_peak_tflops": fp64_peak,
         "fp64_kernels": kernels,
@@ -695,10 +719,14 @@ def main():
                          "3 extrapolated from the previous two")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned warm start")
-    ap.add_argument("--cnn-samples", type=int, default=800)
-    ap.add_argument("--cnn-steps", type=int, default=800)
-    ap.add_argument("--cnn-coarsen", type=int, default=1,
-                    help="run the network on the grid coarsened by 2^k")
+    ap.add_argument("--cnn-samples", type=int, default=1500)
+    ap.add_argument("--cnn-grid", type=int, default=256,
+                    help="grid of the solver-generated training samples")
+    ap.add_argument("--cnn-steps", type=int, default=1500)
+    ap.add_argument("--cnn-batch", type=int, default=8)
+    ap.add_argument("--cnn-coarsen", type=int, default=-1,
+                    help="run the network on the grid coarsened by 2^k (-1: down to the "
+                         "training grid)")
     ap.add_argument("--scale-workload", default="multidrop2048",
                     help="second grid of the scale configuration measured in the same run "
                          "(empty to skip)")

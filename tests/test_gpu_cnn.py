@@ -85,13 +85,14 @@ def test_forward_matches_oracle(T):
     # the oracle with BF16 storage of every activation (its sums FP64): the
     # kernels' sums are FP32, so a stored value can land one BF16 step away
     # (~0.4 %) where the two sums straddle a rounding boundary; element by
-    # element within 2 BF16 steps of the output's own scale
+    # element within one BF16 step (2^-8) of the output's rms (measured:
+    # 6e-4)
     y = OC.forward(Pq, x, bf16=True)[..., 0]
     ref = s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True))
     scale = np.sqrt((ref ** 2).mean(axis=(1, 2), keepdims=True))
     e = np.abs(p0 - ref) / scale
     print("forward: max element error / rms", e.max(), "99.9%", np.quantile(e, 0.999))
-    assert e.max() <= 2 * 2.0 ** -8, e.max()
+    assert e.max() <= 2.0 ** -8, e.max()
     # and the FP64 network within BF16's bound in norm
     y64 = OC.forward(Pq, x)[..., 0]
     ref64 = s[:, None, None] * (y64 - y64.mean(axis=(1, 2), keepdims=True))
@@ -127,10 +128,12 @@ def test_coarse_grid_inference_matches_oracle(T):
     p0 = net.infer(d(rhs), d(rho)).cpu().numpy()
     mean2 = lambda a: a.reshape(B, N // 2, 2, N // 2, 2).mean(axis=(2, 4))
     x, s, _ = oracle_inputs(mean2(rhs), mean2(rho), p[:, ::2, ::2])
-    y = OC.forward(Pq, x)[..., 0]
+    # element by element against the BF16 replay, as the full-grid forward
+    y = OC.forward(Pq, x, bf16=True)[..., 0]
     ref = prolong2(s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True)))
-    err = np.linalg.norm(p0 - ref) / np.linalg.norm(ref)
-    assert err < 3e-2, err
+    scale = np.sqrt((ref ** 2).mean(axis=(1, 2), keepdims=True))
+    e = np.abs(p0 - ref) / scale
+    assert e.max() <= 2.0 ** -8, e.max()
     with pytest.raises(ib.IBError):  # 2^1 * 4 does not divide 36
         net.infer(d(rhs[:, :36, :36]), d(rho[:, :36, :36]))
 
@@ -156,10 +159,11 @@ def test_gradients_match_oracle(T):
     # The last bias has an exactly zero gradient (the loss ignores constant
     # shifts of the output).  Every other parameter gradient element by
     # element against the oracle's BF16 replay (BF16 activations and
-    # gradients, FP64 sums): within 5 % of the layer's largest gradient
-    # (the kernels' FP32 sums move some stored values by one BF16 step, and
-    # those steps accumulate towards the input layers), so that a wrong
-    # channel, tap or pixel index fails at the scale of the layer.
+    # gradients, FP64 sums): within 5e-3 of the layer's largest gradient
+    # (measured: 7.5e-4 at most; the kernels' FP32 sums move some stored
+    # values by one BF16 step, and those steps accumulate towards the input
+    # layers), so that a wrong channel, tap or pixel index fails at the
+    # scale of the layer.
     assert abs(Gg["c6.b"][0]) <= 2e-3 * np.linalg.norm(G["c6.w"])
     worst = {}
     for n, _, _, _ in OC.LAYERS:
@@ -169,7 +173,7 @@ def test_gradients_match_oracle(T):
             a, ref = Gg[n + k].ravel(), G[n + k].ravel()
             e = np.abs(a - ref).max() / np.abs(ref).max()
             worst[n + k] = e
-            assert e <= 5e-2, (n + k, e)
+            assert e <= 5e-3, (n + k, e)
     print("gradients: max element error / layer max", worst)
 
 
@@ -193,7 +197,7 @@ def test_training_reduces_loss_and_is_deterministic(T):
     runs = []
     for _ in range(2):
         net = ib.Net(seed=4)
-        losses = net.train(d(rhs), d(rho), d(p), steps=60, batch=2, lr=2e-3, seed=9)
+        losses = net.train(d(rhs), d(rho), d(p), steps=200, batch=4, lr=2e-3, seed=9)
         runs.append((losses, net.get_params(), net.scale))
     assert runs[0][2] == fitted_scale(rhs, p) or abs(runs[0][2] / fitted_scale(rhs, p) - 1) < 1e-12
     assert np.mean(runs[0][0][-10:]) < 0.5 * np.mean(runs[0][0][:10])
@@ -219,16 +223,19 @@ def test_warm_start_reaches_the_same_tolerance(T):
 
 def test_trained_network_gains_over_cold_start(T):
     # What the learned part buys: a network trained by its own kernels on
-    # solver-generated 64^2 samples, evaluated on an unseen seeded 128^2
-    # multi-drop system.  Its estimate carries a fraction of the pressure's
-    # (mean-free) error of the zero start, multigrid from it reaches the same
-    # 1e-10 tolerance, and in no more V-cycles than from zero.
+    # 2000 solver-generated 128^2 samples, evaluated on an unseen seeded
+    # 128^2 multi-drop system.  Its estimate is within 10 % of the solution
+    # (mean-free, relative), multigrid from it reaches the same 1e-10
+    # tolerance, and in at least two fewer V-cycles than from zero with one
+    # FP32 V-cycle per FP64 residual (measured: 10 instead of 13), and fewer
+    # with two (measured: 10 instead of 14).
     import paper_1807_10504_gb300 as ib
     from paper_1807_10504_gb300 import warmstart as WS
-    data = WS.generate(300, n_cells=64, seed=1)
+    data = WS.generate(2000, n_cells=128, seed=1)
     net = ib.Net(seed=0)
-    losses = WS.train(net, data, steps=400, batch=16, lr=2e-3)
-    assert losses[-1] < 0.2 * losses[0]
+    losses = WS.train(net, data, steps=2000, batch=16, lr=2e-3)
+    del data
+    assert np.mean(losses[-20:]) < 0.01 * np.mean(losses[:20])
     n = 128
     mk = W.multidrop(n, ndrops=4, rmin=0.05, rmax=0.12, n_per_drop=200, seed=77, gap_cells=10)
     cfg = ib.Config(nx=n, ny=n, h=1.0 / n, precision=1)
@@ -236,15 +243,19 @@ def test_trained_network_gains_over_cold_start(T):
     dt = W.capillary_dt(cfg.h, cfg.rho_l, cfg.rho_g, cfg.sigma, cfg.mu_l, cfg.mu_g)
     ctx.ns_step(dt, 3, 1)
     b, rho = ctx.get("b"), ctx.get("rho")
-    p_ref = T.zeros_like(b)
-    st, cyc_cold, rr = ctx.mg_solve(b, p_ref, 1, 1e-10, 200)
-    assert st == 0
     p0 = net.infer(b[None], rho[None])[0]
-    ref = (p_ref - p_ref.mean()).cpu().numpy()
-    est = (p0 - p0.mean()).cpu().numpy()
-    assert np.linalg.norm(est - ref) < 0.5 * np.linalg.norm(ref)
-    st, cyc_cnn, rr = ctx.mg_solve(b, p0, 1, 1e-10, 200)
-    assert st == 0 and rr <= 1e-10 and cyc_cnn <= cyc_cold
+    for prec, gain in ((1, 2), (2, 1)):
+        p_ref = T.zeros_like(b)
+        st, cyc_cold, rr = ctx.mg_solve(b, p_ref, prec, 1e-10, 200)
+        assert st == 0
+        ref = (p_ref - p_ref.mean()).cpu().numpy()
+        est = (p0 - p0.mean()).cpu().numpy()
+        assert np.linalg.norm(est - ref) < 0.1 * np.linalg.norm(ref)
+        p = p0.clone()
+        st, cyc_cnn, rr = ctx.mg_solve(b, p, prec, 1e-10, 200)
+        print("precision", prec, "V-cycles cold", cyc_cold, "network start", cyc_cnn)
+        assert st == 0 and rr <= 1e-10 and cyc_cnn <= cyc_cold - gain, (prec, cyc_cold, cyc_cnn)
+    ctx.close()
 
 
 def test_recorded_inference_replays_the_direct_launches(T):
