@@ -229,6 +229,24 @@ def oracle_rate(name, openmp, precision=2, budget_s=0.0, max_steps=1):
         O.set_threads(False)
 
 
+FP64_OPS = os.path.join(ROOT, "profiles", "fp64_ops.json")
+
+
+def fp64_flops_per_unit(kernel):
+    """Executed FP64 operations (an FMA counted as two) per work unit of a
+    kernel from an ncu capture recorded in profiles/fp64_ops.json (the
+    kernel's DFMA, DADD and DMUL thread instructions over its units); None
+    when the kernel's source has changed since."""
+    try:
+        with open(FP64_OPS) as f:
+            rec = json.load(f)[kernel]
+        if source_sha(rec["source"], rec["function"]) != rec["source_sha256"]:
+            return None
+        return rec["fp64_flops_per_unit"]
+    except (OSError, KeyError, ValueError, StopIteration):
+        return None
+
+
 def cpu_baseline(name):
     """One oracle time step of the workload on one core, then the OpenMP
     build on all host cores (the reported baseline is the faster one)."""
@@ -616,6 +634,22 @@ def run_ours(args):
                        "frac": 8.0 * cells / (us64 * 1e-6) / 1e12 / fp64_peak}}
     band = {"kernel": "k_band_area", "avg_launch_us": usb, "pairs": int(pairs),
             "ns_per_pair": 1e3 * usb / max(pairs, 1)}
+    # the marker side and the predictor: FP64-bound kernels stated against
+    # the FP64 peak with their executed FP64 operations per unit (ncu)
+    marker_side = {}
+    for key, op, unit in (("k_band_area", 2, "(cell, segment) pair"), ("k_predictor", 9, "face"),
+                          ("k_spread_irrot", 10, "face")):
+        try:
+            us_k, units_k = (usb, pairs) if op == 2 else ctx.bench_kernel(op, 10)
+        except ib.IBError:
+            continue
+        fpu = fp64_flops_per_unit(key)
+        ent = {"avg_launch_us": us_k, "units": int(units_k), "unit": unit, "bound": "fp64",
+               "fp64_flops_per_unit": fpu}
+        if fpu is not None:
+            tf = fpu * units_k / (us_k * 1e-6) / 1e12
+            ent.update(fp64_tflops=tf, peak_tflops=fp64_peak, frac=tf / fp64_peak)
+        marker_side[key] = ent
 
     # the scale configuration's larger grid: 2048^2, same drops per unit area
     scale = None
@@ -683,6 +717,7 @@ def run_ours(args):
                      "in_step_avg_launch_us": avg_sweep * 1e3, "in_step_launches": sweep_n},
         "roofline_fp64_sweep": roof64,
         "band_strip_areas": band,
+        "fp64_marker_side": marker_side,
         "mixed_cycle_kernels": kernel_table,
     }
     if scale is not None:

@@ -344,7 +344,10 @@ ib_status ib_profile_end(double *total_ms, int *launches);
  * two sweeps (the fused V(2,2) kernels of the FP64 solve; cells of the
  * level); 5 the FP32 single-CTA lower cycle (cells of its first level), 6 the
  * FP64 residual norm of the mixed solve (cells); 2 band strip areas of the
- * last Heaviside pass (units = (cell, segment) pairs; level ignored).  Only
+ * last Heaviside pass (units = (cell, segment) pairs; level ignored); 9 the
+ * predictor on the current fields, 10 the irrotational face force (planar
+ * contexts) from the last step's H and marker forces (both into scratch
+ * the call allocates and frees; units = faces, (nx + 1) ny + nx (ny + 1)).  Only
  * solve scratch is overwritten (second iterate buffers, coarse right-hand
  * sides, the solver's level-0 FP64 iterate copy, FP32 residual, norm
  * partials) and the strip areas are recomputed: the

@@ -939,9 +939,19 @@ ib_status ib_profile_end(double *total_ms, int *launches)
 ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_per_launch,
                           double *units)
 {
-    if (!c || which < 0 || which > 8 || reps < 1 || !us_per_launch) return IB_EINVAL;
+    if (!c || which < 0 || which > 10 || reps < 1 || !us_per_launch) return IB_EINVAL;
     if (which != 2 && !c->mg_ready) return fail(c, IB_EINVAL, "no multigrid hierarchy yet");
-    double u = 0.0;
+    if (which == 10 && c->cfg.axisym)
+        return fail(c, IB_EINVAL, "the face-force timing is planar only");
+    const ib_config &g = c->cfg;
+    const long nfx = (long)(g.nx + 1) * g.ny, nfy = (long)g.nx * (g.ny + 1);
+    double u = which >= 9 ? (double)(nfx + nfy) : 0.0;
+    // the predictor and face-force timings write into scratch, not the state
+    double *scr = nullptr;
+    if (which >= 9) {
+        cudaError_t e = cudaMalloc(&scr, (size_t)(nfx + nfy) * 2 * 8);
+        if (e != cudaSuccess) return fail(c, IB_ENOMEM, "timing scratch");
+    }
     if (which == 2) {
         uint32_t np = 0;
         cudaError_t e = cudaMemcpyAsync(&np, c->mk.npairs, 4, cudaMemcpyDeviceToHost, c->s);
@@ -951,12 +961,30 @@ ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_
     }
     auto one = [&]() -> bool {
         if (which == 2) { launch_band_area(c->mk, c->s); return true; }
+        if (which == 9) {
+            double *us = scr, *vs = scr + nfx, *au = scr + nfx + nfy, *av = au + nfx;
+            if (g.axisym)
+                launch_predictor_axi(g.nx, g.ny, g.h, 1e-6, c->rho, c->mu, c->u, c->v, c->au, c->av,
+                                     c->have_prev, 0.0, g.gy, g.frame ? c->frame : nullptr, c->bx,
+                                     c->by, us, vs, au, av, c->s);
+            else
+                launch_predictor(g.nx, g.ny, g.h, 1e-6, c->rho, c->mu, c->u, c->v, c->au, c->av,
+                                 c->have_prev, g.gx, g.gy, c->bx, c->by, us, vs, au, av, c->s);
+            return true;
+        }
+        if (which == 10) {
+            launch_spread_irrot(c->mk, c->mk.fmag, c->H, scr, scr + nfx, c->s);
+            return true;
+        }
         const long cells = mg_bench_op(c->mg, which, level, c->s);
         if (cells < 0) return false;
         u = (double)cells;
         return true;
     };
-    if (!one()) return fail(c, IB_EINVAL, "no such kernel at this level");  // warm-up
+    if (!one()) {
+        if (scr) cudaFree(scr);
+        return fail(c, IB_EINVAL, "no such kernel at this level");  // warm-up
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -968,6 +996,7 @@ ib_status ib_bench_kernel(ib_ctx *c, int which, int level, int reps, double *us_
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (scr) cudaFree(scr);
     if (e != cudaSuccess) return cuda_check(c, e, "kernel timing");
     *us_per_launch = 1e3 * ms / reps;
     if (units) *units = u;

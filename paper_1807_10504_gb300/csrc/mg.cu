@@ -513,6 +513,215 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
     }
 }
 
+// The TMA-staged form of k_smooth2_f32 (widths a multiple of 4), written for
+// few instructions per cell: the profile of the general kernel at 2048^2
+// showed it issue-bound (~360 thread instructions a cell, 72 % issue
+// active, DRAM 30 %), its index arithmetic and per-cell global loads
+// outweighing the eight FMAs of two sweeps.  Here a colour phase maps warp w
+// to rows w, w + 8, ... of its ring and lane l to the row's cells l,
+// l + 32, ...; a cell's operands sit at fixed offsets from its flat shared
+// index (west/east faces, south/north faces, the four neighbours, b and
+// 1/diag) and tiles whose window lies inside the grid skip the bounds tests.
+// MODE 2 takes the coarse correction from a shared copy of its window
+// (14 x 38 coarse cells, loaded while the tensor copies are in flight) and
+// prolongs it one 2 x 2 block of fine cells per thread step (nine coarse
+// values for four fine ones); the FP64 iterate of a defect-correction cycle
+// is read into registers before the sweeps.  The arithmetic of every value
+// (the order of its FMAs) is that of k_smooth2_f32, so results agree bit for
+// bit.  Staging, the bounded barrier waits and the fault word are as there.
+template <int MODE>
+__global__ void __launch_bounds__(FT)
+k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
+               float *__restrict__ p, float *__restrict__ rc, float *__restrict__ ecz,
+               const float *__restrict__ ecp, double *__restrict__ p64,
+               const __grid_constant__ TileMaps tm)
+{
+    constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
+    constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
+    constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA, XW = PW + 8;
+    constexpr int CWW = FW / 2 + 6, CHH = FH / 2 + 6;  // coarse window (MODE 2): 38 x 14
+    __shared__ __align__(128) float ps[PH * PW];
+    __shared__ __align__(128) float bs[PH * PW];
+    __shared__ __align__(128) float ds[PH * PW];
+    __shared__ __align__(128) float ys[(PH + 1) * PW];
+    __shared__ __align__(16) float xs[PH * XW];
+    __shared__ float cs[MODE == 2 ? CHH * CWW : 1];
+    __shared__ int xoff[PH];
+    __shared__ __align__(8) unsigned long long bar, stall_bar;
+    const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
+    const long nxf = nx + 1;
+    const int nxc = nx / 2, nyc = ny / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // x-faces of the window rows by asynchronous copies: 16-byte copies of
+    // whole in-range chunks, single faces (zero beyond the walls) at the ends
+    auto load_xfaces = [&]() {
+        constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per x-face row, worst alignment
+        const long nbx = nxf * ny;
+        for (int k = tid; k < PH * NC; k += FT) {
+            const int r = k / NC, q = k - r * NC, gj = gj0 + r;
+            float *dst = xs + r * XW + 4 * q;
+            if (gj < 0 || gj >= ny) {
+                cp_async16(dst, bx, false);
+                if (q == 0) xoff[r] = 0;
+                continue;
+            }
+            const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
+            if (q == 0) xoff[r] = (int)(start - a0);
+            const long e0 = a0 + 4 * q;
+            const int c0 = (int)(e0 - start);  // window column of face e0
+            if (e0 >= 0 && e0 + 4 <= nbx && gi0 + c0 >= 0 && gi0 + c0 + 3 <= nx) {
+                cp_async16(dst, bx + e0, true);
+            } else {
+                for (int t = 0; t < 4; t++) {
+                    const int gi = gi0 + c0 + t;
+                    const bool ok = gi >= 0 && gi <= nx;
+                    cp_async4(dst + t, ok ? bx + e0 + t : bx, ok);
+                }
+            }
+        }
+    };
+    if (((smem_addr(ps) | smem_addr(bs) | smem_addr(ds) | smem_addr(ys)) & 127u) != 0) {
+        if (tid == 0) atomicMax(tm.fault, 2);
+        return;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&stall_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    __syncthreads();  // the barrier is initialised before any thread waits on it
+    // the coefficients (1/diag, beta_y, beta_x) are built before the solve
+    // and not written during it: their copies start before the wait for the
+    // previous grid; the iterate and right-hand side follow the wait
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                     ::"r"(smem_addr(&bar)), "r"(kBytes));
+        tma_load2(ds, &tm.d, gi0, gj0, &bar);
+        tma_load2(ys, &tm.y, gi0, gj0, &bar);
+    }
+    load_xfaces();
+    pdl_enter();
+    if (tid == 0) {
+        tma_load2(ps, &tm.p, gi0, gj0, &bar);
+        tma_load2(bs, &tm.b, gi0, gj0, &bar);
+    }
+    const int cI0 = blockIdx.x * (FW / 2) - 3, cJ0 = blockIdx.y * (FH / 2) - 3;
+    if constexpr (MODE == 2) {
+        // the coarse correction's window, while the tensor copies fly
+        for (int k = tid; k < CHH * CWW; k += FT) {
+            const int j = k / CWW, i = k - j * CWW, gI = cI0 + i, gJ = cJ0 + j;
+            cs[k] = (gI >= 0 && gI < nxc && gJ >= 0 && gJ < nyc) ? ecp[(long)gJ * nxc + gI] : 0.0f;
+        }
+    }
+    // the FP64 iterate of the tile (defect correction), read ahead
+    double v64[MODE == 2 ? (FW * FH) / FT : 1];
+    if constexpr (MODE == 2) {
+        if (p64) {
+#pragma unroll
+            for (int j = 0; j < (FW * FH) / FT; j++) {
+                const int k = tid + j * FT, gi = blockIdx.x * FW + (k % FW), gj = blockIdx.y * FH + k / FW;
+                v64[j] = (gi < nx && gj < ny) ? p64[(long)gj * nx + gi] : 0.0;
+            }
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    bool ok = mbar_wait(&bar, 0, kStageWaitNs);
+    if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
+    // one verdict for the whole block (each thread's wait is bounded)
+    if (__syncthreads_or(!ok)) {
+        // skip the tile; the copies must land before the block leaves
+        const bool landed = mbar_wait(&bar, 0, kDrainNs);
+        if (tid == 0) atomicMax(tm.fault, landed ? 1 : 3);
+        return;
+    }
+    const bool interior = gi0 >= 0 && gi0 + PW <= nx && gj0 >= 0 && gj0 + PH <= ny;
+    if constexpr (MODE == 2) {
+        // p += P e_c, one 2 x 2 block of fine cells (coarse cell (I, J)) per
+        // step: (9 c00 + 3 c10 + 3 c01 + c11) / 16 with the neighbours on the
+        // cell's side, clamped at the walls (zero gradient)
+        constexpr int BW = PW / 2, BH = PH / 2;
+        for (int kb = tid; kb < BW * BH; kb += FT) {
+            const int bj = kb / BW, bi = kb - bj * BW;
+            const int I = cI0 + 1 + bi, J = cJ0 + 1 + bj;
+            if (I < 0 || I >= nxc || J < 0 || J >= nyc) continue;
+            const int iW = max(I - 1, 0) - cI0, iC = I - cI0, iE = min(I + 1, nxc - 1) - cI0;
+            const int jS = (max(J - 1, 0) - cJ0) * CWW, jC = (J - cJ0) * CWW,
+                      jN = (min(J + 1, nyc - 1) - cJ0) * CWW;
+            const float c = cs[jC + iC];
+            const float cW = cs[jC + iW], cE = cs[jC + iE], cS = cs[jS + iC], cN = cs[jN + iC];
+            const float cSW = cs[jS + iW], cSE = cs[jS + iE], cNW = cs[jN + iW], cNE = cs[jN + iE];
+            float *q0 = ps + (2 * bj) * PW + 2 * bi;
+            q0[0] += (9.0f * c + 3.0f * cW + 3.0f * cS + cSW) * 0.0625f;
+            q0[1] += (9.0f * c + 3.0f * cE + 3.0f * cS + cSE) * 0.0625f;
+            q0[PW] += (9.0f * c + 3.0f * cW + 3.0f * cN + cNW) * 0.0625f;
+            q0[PW + 1] += (9.0f * c + 3.0f * cE + 3.0f * cN + cNE) * 0.0625f;
+        }
+        __syncthreads();
+    }
+    // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q)
+    constexpr int Q0 = HA - 1;  // outermost ring updated
+#pragma unroll
+    for (int ph = 0; ph < 4; ph++) {
+        const int q = Q0 - ph, color = ph & 1;
+        const int hq = FH + 2 * q, hw = (FW + 2 * q) / 2;
+        for (int rr = warp; rr < hq; rr += FT / 32) {
+            const int r = HA - q + rr, gj = gj0 + r;
+            const int c0 = XO - q + ((gi0 + XO - q + gj + color) & 1);
+            const int base = r * PW + c0, xbase = r * XW + xoff[r] + c0;
+            const bool rowin = interior || (gj >= 0 && gj < ny);
+            for (int cc = lane; cc < hw; cc += 32) {
+                const int o = base + 2 * cc;
+                if (!interior) {
+                    const int gi = gi0 + c0 + 2 * cc;
+                    if (!rowin || gi < 0 || gi >= nx) continue;
+                }
+                const int xo = xbase + 2 * cc;
+                float sm = xs[xo + 1] * ps[o + 1];
+                sm = fmaf(xs[xo], ps[o - 1], sm);
+                sm = fmaf(ys[o + PW], ps[o + PW], sm);
+                sm = fmaf(ys[o], ps[o - PW], sm);
+                ps[o] = (sm - h2 * bs[o]) * ds[o];
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == 1) {
+        // one coarse cell per thread: FW/2 x FH/2 = 32 x 8
+        const int I = blockIdx.x * (FW / 2) + (tid % (FW / 2));
+        const int J = blockIdx.y * (FH / 2) + (tid / (FW / 2));
+        if (I < nxc && J < nyc) {
+            auto res = [&](int gi, int gj) {
+                const int r = gj - gj0, c = gi - gi0, o = r * PW + c;
+                const float cc = ps[o];
+                const float pE = gi + 1 < nx ? ps[o + 1] : cc, pW = gi > 0 ? ps[o - 1] : cc;
+                const float pN = gj + 1 < ny ? ps[o + PW] : cc, pS = gj > 0 ? ps[o - PW] : cc;
+                const int xc = r * XW + c + xoff[r];
+                float sv = xs[xc + 1] * (pE - cc);
+                sv -= xs[xc] * (cc - pW);
+                sv += ys[o + PW] * (pN - cc);
+                sv -= ys[o] * (cc - pS);
+                return bs[o] - sv * ih2;
+            };
+            const int i = 2 * I, j = 2 * J;
+            const float r00 = res(i, j), r10 = res(i + 1, j), r01 = res(i, j + 1), r11 = res(i + 1, j + 1);
+            rc[(long)J * nxc + I] = 0.25f * (r00 + r10 + r01 + r11);
+            ecz[(long)J * nxc + I] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < (FW * FH) / FT; j++) {
+        const int k = tid + j * FT, col = k % FW, row = k / FW;
+        const int gi = blockIdx.x * FW + col, gj = blockIdx.y * FH + row;
+        if (gi < nx && gj < ny) {
+            const float v = ps[(HA + row) * PW + XO + col];
+            if (MODE == 2 && p64) p64[(long)gj * nx + gi] = v64[MODE == 2 ? j : 0] + (double)v;
+            else p[(long)gj * nx + gi] = v;
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T flux_sum(int nx, int ny, int i, int j, const T *bx,
                                       const T *by, const T *p)
@@ -1463,8 +1672,8 @@ void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, fl
         tm.d = w.invd;
         tm.y = w.by;
         tm.fault = v.fault;
-        launch_pdl(k_smooth2_f32<MODE, true>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by, a.invd,
-                   a.r, pin, p, rc, ecz, ecp, p64, tm);
+        launch_pdl(k_smooth2t_f32<MODE>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, p, rc, ecz, ecp,
+                   p64, tm);
     } else {
         launch_pdl(k_smooth2_f32<MODE, false>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by,
                    a.invd, a.r, pin, p, rc, ecz, ecp, p64, tm);
