@@ -516,12 +516,12 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
 // The TMA-staged form of k_smooth2_f32 (widths a multiple of 4), written for
 // few instructions per cell: the profile of the general kernel at 2048^2
 // showed it issue-bound (~360 thread instructions a cell, 72 % issue
-// active, DRAM 30 %), its index arithmetic and per-cell global loads
-// outweighing the eight FMAs of two sweeps.  Here a colour phase maps warp w
-// to rows w, w + 8, ... of its ring and lane l to the row's cells l,
-// l + 32, ...; a cell's operands sit at fixed offsets from its flat shared
+// active, DRAM 30 %, memory instructions an eighth of them), its index
+// arithmetic and per-cell global loads outweighing the eight FMAs of two
+// sweeps.  Here a cell's operands sit at fixed offsets from its flat shared
 // index (west/east faces, south/north faces, the four neighbours, b and
-// 1/diag) and tiles whose window lies inside the grid skip the bounds tests.
+// 1/diag), its colour parity comes from one per-tile sum, and tiles whose
+// window lies inside the grid skip the bounds tests.
 // MODE 2 takes the coarse correction from a shared copy of its window
 // (14 x 38 coarse cells, loaded while the tensor copies are in flight) and
 // prolongs it one 2 x 2 block of fine cells per thread step (nine coarse
@@ -551,7 +551,7 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
     const long nxf = nx + 1;
     const int nxc = nx / 2, nyc = ny / 2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     // x-faces of the window rows by asynchronous copies: 16-byte copies of
     // whole in-range chunks, single faces (zero beyond the walls) at the ends
     auto load_xfaces = [&]() {
@@ -660,30 +660,30 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
         }
         __syncthreads();
     }
-    // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q)
+    // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q);
+    // its cells of one colour, hq rows of hw, are dealt out to the threads
+    // in turn (the division by hw is by a constant)
     constexpr int Q0 = HA - 1;  // outermost ring updated
+    const int par0 = gi0 + gj0 + XO + HA;
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = Q0 - ph, color = ph & 1;
         const int hq = FH + 2 * q, hw = (FW + 2 * q) / 2;
-        for (int rr = warp; rr < hq; rr += FT / 32) {
-            const int r = HA - q + rr, gj = gj0 + r;
-            const int c0 = XO - q + ((gi0 + XO - q + gj + color) & 1);
-            const int base = r * PW + c0, xbase = r * XW + xoff[r] + c0;
-            const bool rowin = interior || (gj >= 0 && gj < ny);
-            for (int cc = lane; cc < hw; cc += 32) {
-                const int o = base + 2 * cc;
-                if (!interior) {
-                    const int gi = gi0 + c0 + 2 * cc;
-                    if (!rowin || gi < 0 || gi >= nx) continue;
-                }
-                const int xo = xbase + 2 * cc;
-                float sm = xs[xo + 1] * ps[o + 1];
-                sm = fmaf(xs[xo], ps[o - 1], sm);
-                sm = fmaf(ys[o + PW], ps[o + PW], sm);
-                sm = fmaf(ys[o], ps[o - PW], sm);
-                ps[o] = (sm - h2 * bs[o]) * ds[o];
+        for (int k = tid; k < hq * hw; k += FT) {
+            const int rr = k / hw, cc = k - rr * hw;
+            const int r = HA - q + rr;
+            // (gi + gj + color) even: column XO - q + 2 cc + parity
+            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+            if (!interior) {
+                const int gi = gi0 + c, gj = gj0 + r;
+                if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
             }
+            const int o = r * PW + c, xo = r * XW + xoff[r] + c;
+            float sm = xs[xo + 1] * ps[o + 1];
+            sm = fmaf(xs[xo], ps[o - 1], sm);
+            sm = fmaf(ys[o + PW], ps[o + PW], sm);
+            sm = fmaf(ys[o], ps[o - PW], sm);
+            ps[o] = (sm - h2 * bs[o]) * ds[o];
         }
         __syncthreads();
     }
