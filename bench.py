@@ -232,17 +232,18 @@ def oracle_rate(name, openmp, precision=2, budget_s=0.0, max_steps=1):
 FP64_OPS = os.path.join(ROOT, "profiles", "fp64_ops.json")
 
 
-def fp64_flops_per_unit(kernel):
-    """Executed FP64 operations (an FMA counted as two) per work unit of a
-    kernel from an ncu capture recorded in profiles/fp64_ops.json (the
-    kernel's DFMA, DADD and DMUL thread instructions over its units); None
-    when the kernel's source has changed since."""
+def fp64_record(kernel):
+    """The ncu record of a kernel in profiles/fp64_ops.json: executed FP64
+    operations per work unit (its DFMA, DADD and DMUL thread instructions,
+    an FMA counted as two, over its units) and the FP64 pipe's instruction
+    rate (% of peak) in that capture; None when the kernel's source has
+    changed since."""
     try:
         with open(FP64_OPS) as f:
             rec = json.load(f)[kernel]
         if source_sha(rec["source"], rec["function"]) != rec["source_sha256"]:
             return None
-        return rec["fp64_flops_per_unit"]
+        return rec
     except (OSError, KeyError, ValueError, StopIteration):
         return None
 
@@ -643,12 +644,17 @@ def run_ours(args):
             us_k, units_k = (usb, pairs) if op == 2 else ctx.bench_kernel(op, 10)
         except ib.IBError:
             continue
-        fpu = fp64_flops_per_unit(key)
-        ent = {"avg_launch_us": us_k, "units": int(units_k), "unit": unit, "bound": "fp64",
-               "fp64_flops_per_unit": fpu}
-        if fpu is not None:
-            tf = fpu * units_k / (us_k * 1e-6) / 1e12
-            ent.update(fp64_tflops=tf, peak_tflops=fp64_peak, frac=tf / fp64_peak)
+        rec = fp64_record(key)
+        ent = {"avg_launch_us": us_k, "units": int(units_k), "unit": unit, "bound": "fp64"}
+        if rec is not None:
+            # FP64 operations counted as flops; the pipe also issues FP64
+            # compares, min/max and conversions, which the capture's pipe
+            # rate includes
+            tf = rec["fp64_flops_per_unit"] * units_k / (us_k * 1e-6) / 1e12
+            ent.update(fp64_flops_per_unit=rec["fp64_flops_per_unit"], fp64_tflops=tf,
+                       peak_tflops=fp64_peak, frac=tf / fp64_peak,
+                       fp64_pipe_pct_ncu=rec["fp64_pipe_pct_ncu"],
+                       dram_bytes_per_unit_ncu=rec["dram_bytes_per_unit"])
         marker_side[key] = ent
 
     # the scale configuration's larger grid: 2048^2, same drops per unit area
