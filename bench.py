@@ -398,6 +398,37 @@ def solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak)
     return solve, kernels
 
 
+def static_drop_report(ib, steps=100):
+    """configs[0]: the 64^2 static drop (R = 0.25 centred, 128 equispaced
+    markers, density ratio 1000, viscosity ratio 100, sigma 1, FP64 solve to
+    1e-10) after `steps` time steps, with the conventional and the
+    irrotational spreading, markers as placed (curvature exactly 1/R) and
+    with B-spline relocation every 10 steps: the largest parasitic velocity
+    and the pressure jump of Section 5.1 Eq. (sd_pres_diff) (mean inside
+    r < R - 4h minus mean outside r > R + 4h) against sigma / R = 4."""
+    n, R = 64, 0.25
+    h = 1.0 / n
+    mk = W.static_drop(n, R, 128)
+    dt = W.capillary_dt(h, 1.0, 1e-3, 1.0, 1e-2, 1e-4)
+    c = (np.arange(n) + 0.5) * h
+    d = np.hypot(*np.meshgrid(c - 0.5, c - 0.5))
+    inside, outside = d < R - 4 * h, d > R + 4 * h
+    out = {"grid": n, "steps": steps, "dt": dt, "jump_exact": 1.0 / R}
+    for spread, sname in ((0, "conventional"), (1, "irrotational")):
+        for reloc in (0, 10):
+            cfg = ib.Config(nx=n, ny=n, h=h, spread=spread, relocate_every=reloc, precision=0,
+                            tol=1e-10, max_cycles=200)
+            ctx = ib.Context(cfg, mk.X, mk.Y, mk.drop_start)
+            ctx.ns_step(dt, steps, 1)
+            u, v, p = ctx.get_host("u"), ctx.get_host("v"), ctx.get_host("p")
+            jump = float(p[inside].mean() - p[outside].mean())
+            out[f"{sname}_relocate{reloc}"] = {
+                "max_u": float(max(np.abs(u).max(), np.abs(v).max())), "jump": jump,
+                "jump_rel_err": abs(jump - 1.0 / R) * R}
+            ctx.close()
+    return out
+
+
 def coarsen_for(n, args):
     """Halvings of an n x n grid before network inference: the given
     --cnn-coarsen, or (-1) as many as bring it to the training grid."""
@@ -697,6 +728,7 @@ def run_ours(args):
                    "mean_vcycles_per_step": statistics.mean(cycles)},
         "pressure_solve_ms": solve,
         "learned_warm_start_512": cnn_eval,
+        "static_drop_64": static_drop_report(ib),
         "fp64_steps_per_s": fp64_rate,
         "fp64_peak_tflops": fp64_peak,
         "fp64_kernels": kernels,

@@ -248,3 +248,20 @@ def test_ns_step_io_matches_separate_calls(T, ib):
     assert e.value.status == ib.IB_EINVAL
     for c in ctxs:
         c.close()
+
+
+def test_static_drop_100_steps_parasitic_currents_and_laplace_jump(T, ib):
+    """configs[0] (Section 5.1): the 64^2 static drop after 100 FP64 steps.
+    With markers as placed (curvature exactly 1/R) the irrotational force is
+    a discrete gradient balanced by the pressure: no parasitic current to
+    roundoff and the jump of Eq. (sd_pres_diff) equal to sigma / R = 4; the
+    conventional spreading drives parasitic currents.  With B-spline
+    relocation the fitted curvature varies slightly and the irrotational
+    currents stay two orders of magnitude below the conventional ones."""
+    import bench
+    rep = bench.static_drop_report(ib, 100)
+    irr, conv = rep["irrotational_relocate0"], rep["conventional_relocate0"]
+    assert irr["max_u"] < 1e-9 and irr["jump_rel_err"] < 1e-9, irr
+    assert conv["max_u"] > 1e-4 and conv["jump_rel_err"] < 0.05, conv
+    assert rep["irrotational_relocate10"]["max_u"] < 1e-2 * rep["conventional_relocate10"]["max_u"]
+    print("static drop, 100 steps:", rep)
