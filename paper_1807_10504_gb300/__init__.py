@@ -39,6 +39,7 @@ EXPORTS = [
     "ib_op_predictor_axi", "ib_op_rhs_axi", "ib_op_axi_weights", "ib_frame_state",
     "ib_mass_correct", "ib_op_cn_solve", "ns_step_io", "mg_solve_noalloc_error",
     "ib_debug_stall_staging", "ib_probe_fp64", "cnn_fit_scale", "cnn_train",
+    "cnn_set_tensor_path",
 ]
 
 
@@ -110,6 +111,7 @@ def lib():
             "cnn_train": [_P, _i32, _i32, _d, _P, _P, _P, _i32, _i32, C.c_float, C.c_uint64, _P,
                           _P],
             "cnn_set_scale": [_P, _d], "cnn_set_coarsen": [_P, _i32],
+            "cnn_set_tensor_path": [_P, _i32],
             "ib_bench_kernel": [_P, C.c_int, C.c_int, C.c_int, _P, _P],
             "ib_attach_cnn": [_P, _P], "ib_use_graphs": [_P, C.c_int],
             "ib_op_predictor": [_i32, _i32, _d, _d, _P, _P, _P, _P, _P, _P, _i32, _d, _d, _P,
@@ -474,6 +476,11 @@ class Net:
         _check(lib().cnn_train(self._h, n, N, h, _ptr(rhs), _ptr(rho), _ptr(p), steps, batch, lr,
                                seed, losses.ctypes.data, _stream()), None, "cnn_train")
         return losses.tolist()
+
+    def set_tensor_path(self, mode: int):
+        """1: forward convolutions on tcgen05 where the width is a multiple
+        of 128 (default); 0: the warp-level mma.sync kernel everywhere."""
+        _check(lib().cnn_set_tensor_path(self._h, int(mode)), None, "cnn_set_tensor_path")
 
     def set_coarsen(self, levels: int):
         """Run inference on the grid coarsened by 2^levels (inputs averaged,

@@ -1098,6 +1098,9 @@ static ib_status cnn_fb(ib_cnn *h, int32_t B, int32_t N, double hs, const double
         float t = 0.0f;
         for (float v : ls) t += v;
         *loss = t;
+        int f = 0;
+        if (e == cudaSuccess) e = ibk::cnn_take_fault(&f);
+        if (e == cudaSuccess && f) return IB_ECUDA;  // a tensor-core completion wait ran out
     }
     return cudaGetLastError() == cudaSuccess && e == cudaSuccess ? IB_OK : IB_ECUDA;
 }
@@ -1164,6 +1167,18 @@ ib_status cnn_set_coarsen(ib_cnn *h, int32_t levels)
 {
     if (!h || levels < 0 || levels > 6) return IB_EINVAL;
     h->coarsen = levels;
+    return IB_OK;
+}
+
+ib_status cnn_set_tensor_path(ib_cnn *h, int32_t mode)
+{
+    if (!h || mode < 0 || mode > 1) return IB_EINVAL;
+    ibk::cnn_set_tc(*h->n, mode);
+    // recorded inference graphs hold the other path's launches
+    cudaDeviceSynchronize();
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
     return IB_OK;
 }
 

@@ -192,6 +192,213 @@ k_conv_fwd(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restri
     }
 }
 
+// ---- fifth-generation tensor cores (tcgen05) --------------------------
+// Shared-memory matrix descriptor of a K-major operand without swizzling:
+// core matrices of 8 rows x 16 bytes stored as 128 contiguous bytes; lbo =
+// byte distance between core matrices adjacent along K, sbo = along M (or
+// N); start, lbo, sbo are multiples of 16 (encoded >> 4); bits 46-47 carry
+// the descriptor version (1).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
+// operands K-major, no negation or sparsity: D format bits 4-5 (1 = F32), A
+// and B format bits 7-9 and 10-12 (1 = BF16), N >> 3 in bits 17-22, M >> 4
+// in bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned long long cnn_gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for phase 0 of a shared-memory barrier: true once it has completed,
+// false when limit_ns of global time (or 2^26 polls) pass first.
+__device__ __forceinline__ bool cnn_mbar_wait(unsigned long long *bar, unsigned long long limit_ns)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    const unsigned long long t0 = cnn_gtimer();
+    for (int it = 0; it < (1 << 26); it++) {
+        unsigned done;
+        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, P;\n}\n" : "=r"(done) : "r"(a) : "memory");
+        if (done) return true;
+        if (cnn_gtimer() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// Set by a tensor-core convolution whose completion wait ran out (checked by
+// the synchronising network calls).
+__device__ int g_cnn_fault = 0;
+
+template <int N>
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r);
+template <>
+__device__ __forceinline__ void tmem_ld32<16>(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                 "%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld32<32>(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                 "%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,"
+                 "%31}, [%32];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                   "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                   "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+
+constexpr int kTcPix = 128;              // output pixels of a CTA (one row segment)
+constexpr int kTcNP = kTcPix + 2;        // input pixels of a staged row (with halo)
+
+template <int CIN, int COUT>
+constexpr size_t conv_tc_smem()
+{
+    return (size_t)(CIN / 8) * 3 * kTcNP * 16 + (size_t)9 * (CIN / 8) * COUT * 16 + 16;
+}
+
+// y = act(conv3x3(x) + bias) on the fifth-generation tensor cores: one CTA
+// (4 warps) computes a row segment of 128 output pixels as an implicit GEMM
+// D[128 x COUT] = sum over the 9 taps and 16-channel chunks of
+// A_tap[128 x 16] B_tap[16 x COUT] (tcgen05.mma kind::f16, M = 128,
+// N = COUT, K = 16: BF16 operands from shared memory, FP32 accumulators in
+// tensor memory), issued by one thread.  The three input rows the segment
+// needs (130 pixels each, zero outside the image; channels below CUP from the
+// half-resolution xu, nearest up-sampling, as k_conv_fwd) are staged
+// plane by plane, 8 channels a plane, pixels at 16-byte steps: a tap's A is
+// the same planes shifted by (dy, dx) pixels, so its core matrices (8
+// consecutive pixels x 8 channels) are 128 contiguous bytes, 128 bytes apart
+// along M and one plane apart along K.  The weights are staged
+// [tap][8-channel plane][cout][8].  The commit of the MMAs arrives on a
+// shared barrier (bounded wait); each warp then reads its 32 accumulator
+// lanes (one pixel a thread) and writes bias + ReLU as BF16 NHWC (and the
+// FP32 channel 0 when y32 is given).  W must be a multiple of 128.
+template <int CIN, int COUT, int CUP>
+__global__ void __launch_bounds__(128)
+k_conv_tc(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xu,
+          const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
+          bf16 *__restrict__ y, float *__restrict__ y32)
+{
+    static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32) && CUP % 8 == 0, "shapes");
+    constexpr int KP = CIN / 8;                  // 8-channel planes
+    constexpr uint32_t PL = 3 * kTcNP * 16;      // bytes of an input plane
+    constexpr uint32_t WPL = COUT * 16;          // bytes of a weight plane
+    extern __shared__ __align__(1024) unsigned char tc_sm[];
+    unsigned char *xs = tc_sm;
+    unsigned char *wsm = tc_sm + KP * PL;
+    unsigned long long *mbar = (unsigned long long *)(wsm + 9 * KP * WPL);
+    uint32_t *tslot = (uint32_t *)(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = W / kTcPix;
+    const int seg = blockIdx.x % segs, row = (blockIdx.x / segs) % H, bz = blockIdx.x / (segs * H);
+    const int x0 = seg * kTcPix;
+    if (warp == 0) {
+        // 32 accumulator columns (COUT <= 32), the minimum allocation
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"((unsigned)__cvta_generic_to_shared(tslot)), "r"(32u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n"
+                     ::"r"((unsigned)__cvta_generic_to_shared(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    // weights: [tap][plane][cout][8] from [cout][tap][CIN], 16-byte chunks
+    for (int k = tid; k < 9 * KP * COUT; k += 128) {
+        const int co = k % COUT, rest = k / COUT, k8 = rest % KP, tap = rest / KP;
+        const uint4 v = *(const uint4 *)(w + ((long)co * 9 + tap) * CIN + 8 * k8);
+        *(uint4 *)(wsm + ((tap * KP + k8) * COUT + co) * 16) = v;
+    }
+    // input rows row - 1 .. row + 1, pixels x0 - 1 .. x0 + 128
+    for (int k = tid; k < 3 * kTcNP * KP; k += 128) {
+        const int px = k % kTcNP, rest = k / kTcNP, r = rest % 3, k8 = rest / 3;
+        const int gy = row - 1 + r, gx = x0 - 1 + px;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+            v = *(const uint4 *)in_chunk<CIN, CUP>(x, xu, bz, H, W, gy, gx, k8);
+        *(uint4 *)(xs + k8 * PL + (r * kTcNP + px) * 16) = v;
+    }
+    // the operands, written by the generic proxy, are read by the tensor
+    // cores through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t taddr = *tslot;
+    if (tid == 0) {
+        const uint32_t xb = (unsigned)__cvta_generic_to_shared(xs);
+        const uint32_t wb = (unsigned)__cvta_generic_to_shared(wsm);
+        constexpr uint32_t idesc = umma_idesc_bf16(kTcPix, COUT);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; kc++) {
+                const uint64_t ad = umma_desc(xb + 2 * kc * PL + (dy * kTcNP + dx) * 16, PL, 128);
+                const uint64_t bd = umma_desc(wb + (tap * KP + 2 * kc) * WPL, WPL, 128);
+                const unsigned acc = (tap > 0 || kc > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                     ::"r"((unsigned)__cvta_generic_to_shared(mbar)) : "memory");
+    }
+    const bool done = cnn_mbar_wait(mbar, 50000000ull);
+    if (__syncthreads_or(!done)) {
+        // the MMAs did not complete in 50 ms: report, and let them finish
+        // before the accumulators are released
+        if (tid == 0) atomicExch(&g_cnn_fault, 1);
+        const bool late = cnn_mbar_wait(mbar, 500000000ull);
+        __syncthreads();
+        if (warp == 0 && late)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(32u));
+        return;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t acc[COUT];
+    tmem_ld32<COUT>(taddr + ((uint32_t)(32 * warp) << 16), acc);
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    const int gx = x0 + 32 * warp + lane;
+    const long off = (((long)bz * H + row) * W + gx) * COUT;
+    uint32_t packed[COUT / 2];
+#pragma unroll
+    for (int c = 0; c < COUT; c += 2) {
+        float v0 = __uint_as_float(acc[c]) + bias[c], v1 = __uint_as_float(acc[c + 1]) + bias[c + 1];
+        if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+        if (c == 0 && y32) y32[off / COUT] = v0;
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+        packed[c / 2] = *(uint32_t *)&b2;
+    }
+#pragma unroll
+    for (int q = 0; q < COUT / 8; q++)
+        *(uint4 *)(y + off + 8 * q) = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
+                                                 packed[4 * q + 3]);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(32u));
+}
+
 // Partial weight (and bias) gradients of one tap over a chunk of output
 // tiles: dW[co][tap][ci] += sum_p g[p][co] x[p + tap][ci], with
 // g = gy * [ymask > 0].  M = COUT, N = CIN, K = pixels (16 per step).
@@ -656,6 +863,7 @@ struct Cnn {
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // flat FP32
     void *wmem = nullptr;
     int step = 0;
+    int tc = 1;               // forward convolutions on tcgen05 where the width allows
     double out_scale = 1.0;   // c in the pressure scale s h^2 c
     // activation workspace, sized for B x N x N
     int capB = 0, capN = 0;
@@ -679,8 +887,23 @@ int g_sms = 0;
 
 template <int CIN, int COUT, int CUP, bool MASK>
 void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 *xmask, const bf16 *w,
-                 const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
+                 const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, bool tc = false)
 {
+    if constexpr (!MASK && (COUT == 16 || COUT == 32)) {
+        if (tc && W % kTcPix == 0) {
+            constexpr size_t smt = conv_tc_smem<CIN, COUT>();
+            static bool attr_tc = false;
+            if (!attr_tc) {
+                cudaFuncSetAttribute(k_conv_tc<CIN, COUT, CUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smt);
+                attr_tc = true;
+            }
+            note_launch();
+            k_conv_tc<CIN, COUT, CUP><<<B * H * (W / kTcPix), 128, smt, s>>>(B, H, W, x, xu, w, bias, relu, y,
+                                                                           y32);
+            return;
+        }
+    }
     constexpr size_t sm = conv_smem<CIN, COUT, MASK>();
     static bool attr = false;
     if (!attr) {
@@ -702,18 +925,18 @@ void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 
 
 template <int CIN, int COUT>
 void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
-              const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s)
+              const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, bool tc = false)
 {
     if (xmask) conv_launch<CIN, COUT, 0, true>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s);
-    else conv_launch<CIN, COUT, 0, false>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s);
+    else conv_launch<CIN, COUT, 0, false>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s, tc);
 }
 
 // Convolution of the concatenation up2(xu) ++ x (CUP channels from xu).
 template <int CIN, int COUT, int CUP>
 void conv_fwd_cat(int B, int H, int W, const bf16 *xu, const bf16 *x, const bf16 *w,
-                  const float *bias, int relu, bf16 *y, cudaStream_t s)
+                  const float *bias, int relu, bf16 *y, cudaStream_t s, bool tc = false)
 {
-    conv_launch<CIN, COUT, CUP, false>(B, H, W, x, xu, nullptr, w, bias, relu, y, nullptr, s);
+    conv_launch<CIN, COUT, CUP, false>(B, H, W, x, xu, nullptr, w, bias, relu, y, nullptr, s, tc);
 }
 
 template <int CIN, int COUT, int CUP = 0>
@@ -878,19 +1101,20 @@ void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double
     k_features<<<cdiv(P, 256), 256, 0, s>>>(P, N2, rhs, rho, p, n.stats, n.x, p ? n.t : nullptr);
     auto &L = n.L;
     auto bias = [&](int k) { return n.w + L[k].boff; };
-    conv_fwd<16, 16>(B, N, N, n.x, nullptr, L[0].wf, bias(0), 1, n.a1, nullptr, s);
-    conv_fwd<16, 16>(B, N, N, n.a1, nullptr, L[1].wf, bias(1), 1, n.s1, nullptr, s);
+    const bool tc = n.tc != 0;
+    conv_fwd<16, 16>(B, N, N, n.x, nullptr, L[0].wf, bias(0), 1, n.a1, nullptr, s, tc);
+    conv_fwd<16, 16>(B, N, N, n.a1, nullptr, L[1].wf, bias(1), 1, n.s1, nullptr, s, tc);
     note_launch();
     k_pool2<<<cdiv((long)B * H2 * H2 * 16, 256), 256, 0, s>>>((long)B * H2 * H2 * 16, H2, H2, 16, n.s1, n.p1);
-    conv_fwd<16, 32>(B, H2, H2, n.p1, nullptr, L[2].wf, bias(2), 1, n.a2, nullptr, s);
-    conv_fwd<32, 32>(B, H2, H2, n.a2, nullptr, L[3].wf, bias(3), 1, n.s2, nullptr, s);
+    conv_fwd<16, 32>(B, H2, H2, n.p1, nullptr, L[2].wf, bias(2), 1, n.a2, nullptr, s, tc);
+    conv_fwd<32, 32>(B, H2, H2, n.a2, nullptr, L[3].wf, bias(3), 1, n.s2, nullptr, s, tc);
     note_launch();
     k_pool2<<<cdiv((long)B * H4 * H4 * 32, 256), 256, 0, s>>>((long)B * H4 * H4 * 32, H4, H4, 32, n.s2, n.p2);
-    conv_fwd<32, 32>(B, H4, H4, n.p2, nullptr, L[4].wf, bias(4), 1, n.a3, nullptr, s);
-    conv_fwd<32, 32>(B, H4, H4, n.a3, nullptr, L[5].wf, bias(5), 1, n.t3, nullptr, s);
-    conv_fwd_cat<64, 32, 32>(B, H2, H2, n.t3, n.s2, L[6].wf, bias(6), 1, n.t4, s);  // up2(t3) ++ s2
-    conv_fwd_cat<48, 16, 32>(B, N, N, n.t4, n.s1, L[7].wf, bias(7), 1, n.a5, s);     // up2(t4) ++ s1
-    conv_fwd<16, 16>(B, N, N, n.a5, nullptr, L[8].wf, bias(8), 0, n.y, n.y32, s);
+    conv_fwd<32, 32>(B, H4, H4, n.p2, nullptr, L[4].wf, bias(4), 1, n.a3, nullptr, s, tc);
+    conv_fwd<32, 32>(B, H4, H4, n.a3, nullptr, L[5].wf, bias(5), 1, n.t3, nullptr, s, tc);
+    conv_fwd_cat<64, 32, 32>(B, H2, H2, n.t3, n.s2, L[6].wf, bias(6), 1, n.t4, s, tc);  // up2(t3) ++ s2
+    conv_fwd_cat<48, 16, 32>(B, N, N, n.t4, n.s1, L[7].wf, bias(7), 1, n.a5, s, tc);     // up2(t4) ++ s1
+    conv_fwd<16, 16>(B, N, N, n.a5, nullptr, L[8].wf, bias(8), 0, n.y, n.y32, s, tc);
 }
 
 // Loss and gradients of every parameter (into n.g, master layout).
@@ -1105,11 +1329,24 @@ cudaError_t cnn_train_loop(Cnn &n, int ns, int N, double h, const double *rhs, c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(losses_host, dloss, (size_t)steps * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int f = 0;
+    if (e == cudaSuccess) e = cnn_take_fault(&f);
+    if (e == cudaSuccess && f) e = cudaErrorLaunchFailure;  // a tensor-core completion wait ran out
     cudaFree(mem);
     return e;
 }
 
 void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }
+void cnn_set_tc(Cnn &n, int on) { n.tc = on ? 1 : 0; }
+
+// Reads and clears the tensor-core convolutions' fault word.
+cudaError_t cnn_take_fault(int *f)
+{
+    int z = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(f, g_cnn_fault, sizeof(int));
+    if (e == cudaSuccess && *f) e = cudaMemcpyToSymbol(g_cnn_fault, &z, sizeof(int));
+    return e;
+}
 const void *cnn_workspace_ptr(const Cnn &n) { return n.amem; }
 const void *cnn_cbuf_ptr(const Cnn &n) { return n.cbuf; }
 double cnn_get_scale(const Cnn &n) { return n.out_scale; }

@@ -314,6 +314,8 @@ void cnn_output(Cnn &n, int B, int N, double h, double *p0, cudaStream_t s);
 cudaError_t cnn_infer_levels(Cnn &n, int B, int N, double h, const double *rhs, const double *rho,
                              double *p0, int levels, cudaStream_t s);
 void cnn_set_scale(Cnn &n, double c);
+void cnn_set_tc(Cnn &n, int on);
+cudaError_t cnn_take_fault(int *f);
 cudaError_t cnn_fit_scale(Cnn &n, int B, int N, double h, const double *rhs, const double *p,
                           double *c, cudaStream_t s);
 cudaError_t cnn_train_loop(Cnn &n, int ns, int N, double h, const double *rhs, const double *rho,

@@ -282,3 +282,37 @@ def test_recorded_inference_replays_the_direct_launches(T):
     direct = net.infer(drhs, drho, out=other)  # a new key: direct launches
     assert T.equal(replay, direct) and T.equal(replay2, direct)
     assert not T.equal(replay, first)
+
+
+def test_tensor_core_path_matches_warp_path_and_oracle(T):
+    # At widths that are multiples of 128 the forward convolutions run on the
+    # fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+    # memory).  On a 256^2 batch (levels 256, 128 on tcgen05; 64 on mma.sync)
+    # the estimate agrees with the warp-level mma.sync path to FP32 summation
+    # order (one BF16 step of the output's rms at most), and both agree with
+    # the oracle's BF16 replay element by element as on the small grid.
+    import paper_1807_10504_gb300 as ib
+    B, N = 1, 256
+    P = OC.init_params(seed=3)
+    for n, _, co, _ in OC.LAYERS:
+        P[n + ".b"] = np.random.default_rng(len(n) + 11).standard_normal(co) * 0.05
+    Pq = {k: (bf16(v) if k.endswith(".w") else v.astype(np.float32).astype(np.float64)) for k, v in P.items()}
+    net = ib.Net(seed=0)
+    net.set_params(flat_of(P))
+    rhs, rho, p = batch(B, N, 21)
+    d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
+    drhs, drho = d(rhs), d(rho)
+    out = {}
+    for mode in (1, 0):
+        net.set_tensor_path(mode)
+        out[mode] = net.infer(drhs, drho).cpu().numpy()
+    x, s, _ = oracle_inputs(rhs, rho, p)
+    y = OC.forward(Pq, x, bf16=True)[..., 0]
+    ref = s[:, None, None] * (y - y.mean(axis=(1, 2), keepdims=True))
+    scale = np.sqrt((ref ** 2).mean(axis=(1, 2), keepdims=True))
+    e_tc_warp = np.abs(out[1] - out[0]).max() / scale.max()
+    e_tc = (np.abs(out[1] - ref) / scale).max()
+    e_warp = (np.abs(out[0] - ref) / scale).max()
+    print("256^2 forward: tcgen05 vs mma.sync", e_tc_warp, "tcgen05 vs oracle", e_tc,
+          "mma.sync vs oracle", e_warp)
+    assert e_tc_warp <= 2.0 ** -8 and e_tc <= 2.0 ** -8 and e_warp <= 2.0 ** -8
