@@ -529,6 +529,7 @@ def run_ours(args):
         # network inference on this step's system inside a profiler range
         net = ib.Net(seed=0)
         net.set_coarsen(coarsen_for(nx, args))
+        net.set_tensor_path(args.cnn_tensor_path)
         b, rho = ctx.get("b"), ctx.get("rho")
         net.infer(b[None], rho[None])
         torch.cuda.synchronize()
@@ -601,6 +602,7 @@ def run_ours(args):
         data = WS.generate(args.cnn_samples, n_cells=args.cnn_grid, seed=0)
         t_gen = time.perf_counter() - t0
         net = ib.Net(seed=0)
+        net.set_tensor_path(args.cnn_tensor_path)
         losses = WS.train(net, data, steps=args.cnn_steps, batch=args.cnn_batch, lr=2e-3)
         del data
         train = {"samples": args.cnn_samples, "grid": args.cnn_grid, "steps": len(losses),
@@ -797,6 +799,9 @@ def main():
                     help="grid of the solver-generated training samples")
     ap.add_argument("--cnn-steps", type=int, default=1500)
     ap.add_argument("--cnn-batch", type=int, default=8)
+    ap.add_argument("--cnn-tensor-path", type=int, default=1, choices=[0, 1, 2],
+                    help="forward convolutions: 0 mma.sync everywhere, 1 tcgen05 where faster, "
+                         "2 tcgen05 wherever the width allows")
     ap.add_argument("--cnn-coarsen", type=int, default=-1,
                     help="run the network on the grid coarsened by 2^k (-1: down to the "
                          "training grid)")

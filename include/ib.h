@@ -300,11 +300,14 @@ ib_status cnn_train(ib_cnn *net, int32_t nsamples, int32_t N, double h, const do
 ib_status cnn_infer(ib_cnn *net, int32_t B, int32_t N, double h, const double *rhs,
                     const double *rho, double *p0, void *stream);
 ib_status cnn_set_coarsen(ib_cnn *net, int32_t levels);   /* 0 .. 6 */
-/* Convolution path of the forward pass: 1 (default) fifth-generation tensor
- * cores (tcgen05.mma, FP32 accumulators in tensor memory) for layers whose
- * width is a multiple of 128, the warp-level mma.sync kernel elsewhere;
- * 0 the warp-level kernel for every layer.  The two agree to FP32
- * summation order.  The backward pass always uses the warp-level kernel.
+/* Convolution path of the forward pass: 0 the warp-level mma.sync kernel
+ * for every layer; 1 (default) the fifth-generation tensor cores
+ * (tcgen05.mma, FP32 accumulators in tensor memory) for the layer shapes
+ * where they measured faster (16 -> 32 channels) when the width is a
+ * multiple of 128, the warp-level kernel elsewhere; 2 tcgen05 for every
+ * layer whose width is a multiple of 128.  The paths accumulate in the same
+ * order and agree bit for bit.  The backward pass always uses the
+ * warp-level kernel.
  * cnn_grad and cnn_train return IB_ECUDA if a tensor-core completion wait
  * ran out (50 ms).                                                         */
 ib_status cnn_set_tensor_path(ib_cnn *net, int32_t mode);

@@ -478,8 +478,9 @@ class Net:
         return losses.tolist()
 
     def set_tensor_path(self, mode: int):
-        """1: forward convolutions on tcgen05 where the width is a multiple
-        of 128 (default); 0: the warp-level mma.sync kernel everywhere."""
+        """0: the warp-level mma.sync kernel everywhere; 1 (default): tcgen05
+        for the layer shapes where it is faster; 2: tcgen05 for every layer
+        whose width is a multiple of 128 (see cnn_set_tensor_path)."""
         _check(lib().cnn_set_tensor_path(self._h, int(mode)), None, "cnn_set_tensor_path")
 
     def set_coarsen(self, levels: int):

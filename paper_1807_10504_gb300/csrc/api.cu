@@ -1172,7 +1172,7 @@ ib_status cnn_set_coarsen(ib_cnn *h, int32_t levels)
 
 ib_status cnn_set_tensor_path(ib_cnn *h, int32_t mode)
 {
-    if (!h || mode < 0 || mode > 1) return IB_EINVAL;
+    if (!h || mode < 0 || mode > 2) return IB_EINVAL;
     ibk::cnn_set_tc(*h->n, mode);
     // recorded inference graphs hold the other path's launches
     cudaDeviceSynchronize();

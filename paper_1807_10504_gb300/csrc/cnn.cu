@@ -220,16 +220,18 @@ __device__ __forceinline__ unsigned long long cnn_gtimer()
     return t;
 }
 
-// Wait for phase 0 of a shared-memory barrier: true once it has completed,
-// false when limit_ns of global time (or 2^26 polls) pass first.
-__device__ __forceinline__ bool cnn_mbar_wait(unsigned long long *bar, unsigned long long limit_ns)
+// Wait for the phase of a shared-memory barrier with the given parity: true
+// once it has completed, false when limit_ns of global time (or 2^26 polls)
+// pass first.
+__device__ __forceinline__ bool cnn_mbar_wait(unsigned long long *bar, unsigned parity,
+                                              unsigned long long limit_ns)
 {
     const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
     const unsigned long long t0 = cnn_gtimer();
     for (int it = 0; it < (1 << 26); it++) {
         unsigned done;
-        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0;\n"
-                     " selp.u32 %0, 1, 0, P;\n}\n" : "=r"(done) : "r"(a) : "memory");
+        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, P;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return true;
         if (cnn_gtimer() - t0 > limit_ns) return false;
     }
@@ -267,40 +269,45 @@ __device__ __forceinline__ void tmem_ld32<32>(uint32_t taddr, uint32_t *r)
                  : "r"(taddr));
 }
 
-constexpr int kTcPix = 128;              // output pixels of a CTA (one row segment)
+constexpr int kTcPix = 128;              // output pixels of a row segment
 constexpr int kTcNP = kTcPix + 2;        // input pixels of a staged row (with halo)
 
 template <int CIN, int COUT>
 constexpr size_t conv_tc_smem()
 {
-    return (size_t)(CIN / 8) * 3 * kTcNP * 16 + (size_t)9 * (CIN / 8) * COUT * 16 + 16;
+    return (size_t)(CIN / 8) * 4 * kTcNP * 16 + (size_t)9 * (CIN / 8) * COUT * 16 + 16;
 }
 
-// y = act(conv3x3(x) + bias) on the fifth-generation tensor cores: one CTA
-// (4 warps) computes a row segment of 128 output pixels as an implicit GEMM
-// D[128 x COUT] = sum over the 9 taps and 16-channel chunks of
-// A_tap[128 x 16] B_tap[16 x COUT] (tcgen05.mma kind::f16, M = 128,
-// N = COUT, K = 16: BF16 operands from shared memory, FP32 accumulators in
-// tensor memory), issued by one thread.  The three input rows the segment
-// needs (130 pixels each, zero outside the image; channels below CUP from the
-// half-resolution xu, nearest up-sampling, as k_conv_fwd) are staged
-// plane by plane, 8 channels a plane, pixels at 16-byte steps: a tap's A is
-// the same planes shifted by (dy, dx) pixels, so its core matrices (8
+// y = act(conv3x3(x) + bias) on the fifth-generation tensor cores.  A work
+// unit is a strip of 128 output pixels (a row segment) over rpu rows;
+// each output row is an implicit GEMM D[128 x COUT] = sum over the 9 taps
+// and 16-channel chunks of A_tap[128 x 16] B_tap[16 x COUT]
+// (tcgen05.mma kind::f16, M = 128, N = COUT, K = 16: BF16 operands from
+// shared memory, FP32 accumulators in tensor memory), issued by one thread
+// and committed to a shared barrier (bounded wait).  Persistent: a CTA
+// allocates its accumulator columns and stages all weights once
+// ([tap][8-channel plane][cout][8]), then walks units.  Input rows live in a
+// ring of four slots, plane by plane (8 channels a plane, 130 pixels at
+// 16-byte steps, zero outside the image; channels below CUP from the
+// half-resolution xu, nearest up-sampling, as k_conv_fwd): a unit stages
+// its first three rows, then one new row per output row while the tensor
+// cores work on the previous one, and a tap's A is the
+// slot of row r - 1 + dy shifted by dx pixels, so its core matrices (8
 // consecutive pixels x 8 channels) are 128 contiguous bytes, 128 bytes apart
-// along M and one plane apart along K.  The weights are staged
-// [tap][8-channel plane][cout][8].  The commit of the MMAs arrives on a
-// shared barrier (bounded wait); each warp then reads its 32 accumulator
+// along M and one plane apart along K.  Each warp reads its 32 accumulator
 // lanes (one pixel a thread) and writes bias + ReLU as BF16 NHWC (and the
-// FP32 channel 0 when y32 is given).  W must be a multiple of 128.
+// FP32 channel 0 when y32 is given).  W must be a multiple of 128.  The
+// accumulation order (taps, then 16-channel chunks) is k_conv_fwd's.
 template <int CIN, int COUT, int CUP>
 __global__ void __launch_bounds__(128)
-k_conv_tc(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restrict__ xu,
+k_conv_tc(int B, int H, int W, int rpu, const bf16 *__restrict__ x, const bf16 *__restrict__ xu,
           const bf16 *__restrict__ w, const float *__restrict__ bias, int relu,
           bf16 *__restrict__ y, float *__restrict__ y32)
 {
     static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32) && CUP % 8 == 0, "shapes");
     constexpr int KP = CIN / 8;                  // 8-channel planes
-    constexpr uint32_t PL = 3 * kTcNP * 16;      // bytes of an input plane
+    constexpr uint32_t SL = kTcNP * 16;          // bytes of a row slot in a plane
+    constexpr uint32_t PL = 4 * SL;              // bytes of an input plane (4 slots)
     constexpr uint32_t WPL = COUT * 16;          // bytes of a weight plane
     extern __shared__ __align__(1024) unsigned char tc_sm[];
     unsigned char *xs = tc_sm;
@@ -308,9 +315,8 @@ k_conv_tc(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restric
     unsigned long long *mbar = (unsigned long long *)(wsm + 9 * KP * WPL);
     uint32_t *tslot = (uint32_t *)(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int segs = W / kTcPix;
-    const int seg = blockIdx.x % segs, row = (blockIdx.x / segs) % H, bz = blockIdx.x / (segs * H);
-    const int x0 = seg * kTcPix;
+    const int segs = W / kTcPix, bands = (H + rpu - 1) / rpu;
+    const int units = B * segs * bands;
     if (warp == 0) {
         // 32 accumulator columns (COUT <= 32), the minimum allocation
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
@@ -328,75 +334,102 @@ k_conv_tc(int B, int H, int W, const bf16 *__restrict__ x, const bf16 *__restric
         const uint4 v = *(const uint4 *)(w + ((long)co * 9 + tap) * CIN + 8 * k8);
         *(uint4 *)(wsm + ((tap * KP + k8) * COUT + co) * 16) = v;
     }
-    // input rows row - 1 .. row + 1, pixels x0 - 1 .. x0 + 128
-    for (int k = tid; k < 3 * kTcNP * KP; k += 128) {
-        const int px = k % kTcNP, rest = k / kTcNP, r = rest % 3, k8 = rest / 3;
-        const int gy = row - 1 + r, gx = x0 - 1 + px;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            v = *(const uint4 *)in_chunk<CIN, CUP>(x, xu, bz, H, W, gy, gx, k8);
-        *(uint4 *)(xs + k8 * PL + (r * kTcNP + px) * 16) = v;
-    }
-    // the operands, written by the generic proxy, are read by the tensor
-    // cores through the async proxy
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t taddr = *tslot;
-    if (tid == 0) {
-        const uint32_t xb = (unsigned)__cvta_generic_to_shared(xs);
-        const uint32_t wb = (unsigned)__cvta_generic_to_shared(wsm);
-        constexpr uint32_t idesc = umma_idesc_bf16(kTcPix, COUT);
-#pragma unroll 1
-        for (int tap = 0; tap < 9; tap++) {
-            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; kc++) {
-                const uint64_t ad = umma_desc(xb + 2 * kc * PL + (dy * kTcNP + dx) * 16, PL, 128);
-                const uint64_t bd = umma_desc(wb + (tap * KP + 2 * kc) * WPL, WPL, 128);
-                const unsigned acc = (tap > 0 || kc > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
+    const uint32_t xb = (unsigned)__cvta_generic_to_shared(xs);
+    const uint32_t wb = (unsigned)__cvta_generic_to_shared(wsm);
+    constexpr uint32_t idesc = umma_idesc_bf16(kTcPix, COUT);
+    unsigned phase = 0;
+    bool fail = false, stuck = false;
+    // input row gy of the strip at x0 into ring slot gy & 3
+    auto stage = [&](int bz, int gy, int x0) {
+        const int slot = gy & 3;
+        for (int k = tid; k < kTcNP * KP; k += 128) {
+            const int px = k % kTcNP, k8 = k / kTcNP, gx = x0 - 1 + px;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                v = *(const uint4 *)in_chunk<CIN, CUP>(x, xu, bz, H, W, gy, gx, k8);
+            *(uint4 *)(xs + k8 * PL + slot * SL + px * 16) = v;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                     ::"r"((unsigned)__cvta_generic_to_shared(mbar)) : "memory");
-    }
-    const bool done = cnn_mbar_wait(mbar, 50000000ull);
-    if (__syncthreads_or(!done)) {
-        // the MMAs did not complete in 50 ms: report, and let them finish
-        // before the accumulators are released
-        if (tid == 0) atomicExch(&g_cnn_fault, 1);
-        const bool late = cnn_mbar_wait(mbar, 500000000ull);
-        __syncthreads();
-        if (warp == 0 && late)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(32u));
-        return;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    uint32_t acc[COUT];
-    tmem_ld32<COUT>(taddr + ((uint32_t)(32 * warp) << 16), acc);
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    const int gx = x0 + 32 * warp + lane;
-    const long off = (((long)bz * H + row) * W + gx) * COUT;
-    uint32_t packed[COUT / 2];
+    };
+    for (int u = blockIdx.x; u < units && !fail; u += gridDim.x) {
+        const int seg = u % segs, band = (u / segs) % bands, bz = u / (segs * bands);
+        const int x0 = seg * kTcPix, r0 = band * rpu, r1 = min(r0 + rpu, H);
+        stage(bz, r0 - 1, x0);
+        stage(bz, r0, x0);
+        stage(bz, r0 + 1, x0);
+        for (int row = r0; row < r1; row++) {
+            // the operands, written by the generic proxy, are read by the
+            // tensor cores through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (tid == 0) {
+#pragma unroll 1
+                for (int tap = 0; tap < 9; tap++) {
+                    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+                    const uint32_t a0 = xb + ((row - 1 + dy) & 3) * SL + dx * 16;
 #pragma unroll
-    for (int c = 0; c < COUT; c += 2) {
-        float v0 = __uint_as_float(acc[c]) + bias[c], v1 = __uint_as_float(acc[c + 1]) + bias[c + 1];
-        if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-        if (c == 0 && y32) y32[off / COUT] = v0;
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-        packed[c / 2] = *(uint32_t *)&b2;
-    }
+                    for (int kc = 0; kc < CIN / 16; kc++) {
+                        const uint64_t ad = umma_desc(a0 + 2 * kc * PL, PL, 128);
+                        const uint64_t bd = umma_desc(wb + (tap * KP + 2 * kc) * WPL, WPL, 128);
+                        const unsigned acc = (tap > 0 || kc > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                     ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             ::"r"((unsigned)__cvta_generic_to_shared(mbar)) : "memory");
+            }
+            // the next row's input while the tensor cores work: its slot
+            // held row - 2, which no MMA of this row reads
+            if (row + 1 < r1) stage(bz, row + 2, x0);
+            const bool done = cnn_mbar_wait(mbar, phase, 50000000ull);
+            if (__syncthreads_or(!done)) {
+                // the MMAs did not complete in 50 ms: report and stop; wait
+                // up to 0.5 s more for them before the accumulators are
+                // released
+                if (tid == 0) atomicExch(&g_cnn_fault, 1);
+                stuck = !__syncthreads_and(cnn_mbar_wait(mbar, phase, 500000000ull));
+                fail = true;
+                break;
+            }
+            phase ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint32_t acc[COUT];
+            tmem_ld32<COUT>(taddr + ((uint32_t)(32 * warp) << 16), acc);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            const long off = (((long)bz * H + row) * W + x0 + 32 * warp + lane) * COUT;
+            uint32_t packed[COUT / 2];
 #pragma unroll
-    for (int q = 0; q < COUT / 8; q++)
-        *(uint4 *)(y + off + 8 * q) = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
-                                                 packed[4 * q + 3]);
+            for (int c = 0; c < COUT; c += 2) {
+                float v0 = __uint_as_float(acc[c]) + bias[c], v1 = __uint_as_float(acc[c + 1]) + bias[c + 1];
+                if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                if (c == 0 && y32) y32[off / COUT] = v0;
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                packed[c / 2] = *(uint32_t *)&b2;
+            }
+#pragma unroll
+            for (int q = 0; q < COUT / 8; q++)
+                *(uint4 *)(y + off + 8 * q) = make_uint4(packed[4 * q], packed[4 * q + 1],
+                                                         packed[4 * q + 2], packed[4 * q + 3]);
+            // the accumulators are read before the next row's MMAs overwrite
+            // them, and the ring slot of row - 1 before it is restaged
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(32u));
+    // MMAs that never completed leave their columns allocated rather than
+    // released under them
+    if (warp == 0 && !stuck)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(32u));
 }
 
 // Partial weight (and bias) gradients of one tap over a chunk of output
@@ -863,7 +896,7 @@ struct Cnn {
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // flat FP32
     void *wmem = nullptr;
     int step = 0;
-    int tc = 1;               // forward convolutions on tcgen05 where the width allows
+    int tc = 1;               // forward convolutions on tcgen05: 0 none, 1 where faster, 2 all that fit
     double out_scale = 1.0;   // c in the pressure scale s h^2 c
     // activation workspace, sized for B x N x N
     int capB = 0, capN = 0;
@@ -885,12 +918,18 @@ namespace {
 
 int g_sms = 0;
 
+// tc: 0 the warp-level kernel; 1 tcgen05 for the shapes where it measured
+// faster than the warp-level kernel (16 -> 32 channels: 8.7 against 12.2 us
+// at 128^2; the others are bound by operand staging and latency, where the
+// warp-level kernel's double-buffered 8 x 16 tiles stage less per output);
+// 2 tcgen05 wherever the width is a multiple of 128.
 template <int CIN, int COUT, int CUP, bool MASK>
 void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 *xmask, const bf16 *w,
-                 const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, bool tc = false)
+                 const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, int tc = 0)
 {
     if constexpr (!MASK && (COUT == 16 || COUT == 32)) {
-        if (tc && W % kTcPix == 0) {
+        const bool faster = CIN == 16 && COUT == 32 && CUP == 0;
+        if ((tc == 2 || (tc == 1 && faster)) && W % kTcPix == 0) {
             constexpr size_t smt = conv_tc_smem<CIN, COUT>();
             static bool attr_tc = false;
             if (!attr_tc) {
@@ -898,9 +937,22 @@ void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 
                                      (int)smt);
                 attr_tc = true;
             }
+            if (!g_sms) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+                if (g_sms <= 0) g_sms = 152;
+            }
+            // rows per unit: as many as keep every SM busy, up to 8 (a unit
+            // stages rpu + 2 input rows for rpu output rows); CTAs per SM by
+            // shared memory (at most 8: 256 of the 512 tensor-memory columns)
+            const int per_sm = std::max(1, std::min(8, (int)((227 * 1024) / smt)));
+            const long rows = (long)B * H * (W / kTcPix);
+            const int rpu = (int)std::max(1L, std::min(std::min((long)H, 8L), rows / g_sms));
+            const long units = (long)B * (W / kTcPix) * ((H + rpu - 1) / rpu);
+            const int grid = (int)std::min(units, (long)g_sms * per_sm);
             note_launch();
-            k_conv_tc<CIN, COUT, CUP><<<B * H * (W / kTcPix), 128, smt, s>>>(B, H, W, x, xu, w, bias, relu, y,
-                                                                           y32);
+            k_conv_tc<CIN, COUT, CUP><<<grid, 128, smt, s>>>(B, H, W, rpu, x, xu, w, bias, relu, y, y32);
             return;
         }
     }
@@ -925,7 +977,7 @@ void conv_launch(int B, int H, int W, const bf16 *x, const bf16 *xu, const bf16 
 
 template <int CIN, int COUT>
 void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 *w,
-              const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, bool tc = false)
+              const float *bias, int relu, bf16 *y, float *y32, cudaStream_t s, int tc = 0)
 {
     if (xmask) conv_launch<CIN, COUT, 0, true>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s);
     else conv_launch<CIN, COUT, 0, false>(B, H, W, x, nullptr, xmask, w, bias, relu, y, y32, s, tc);
@@ -934,7 +986,7 @@ void conv_fwd(int B, int H, int W, const bf16 *x, const bf16 *xmask, const bf16 
 // Convolution of the concatenation up2(xu) ++ x (CUP channels from xu).
 template <int CIN, int COUT, int CUP>
 void conv_fwd_cat(int B, int H, int W, const bf16 *xu, const bf16 *x, const bf16 *w,
-                  const float *bias, int relu, bf16 *y, cudaStream_t s, bool tc = false)
+                  const float *bias, int relu, bf16 *y, cudaStream_t s, int tc = 0)
 {
     conv_launch<CIN, COUT, CUP, false>(B, H, W, x, xu, nullptr, w, bias, relu, y, nullptr, s, tc);
 }
@@ -1101,7 +1153,7 @@ void cnn_forward(Cnn &n, int B, int N, double h, const double *rhs, const double
     k_features<<<cdiv(P, 256), 256, 0, s>>>(P, N2, rhs, rho, p, n.stats, n.x, p ? n.t : nullptr);
     auto &L = n.L;
     auto bias = [&](int k) { return n.w + L[k].boff; };
-    const bool tc = n.tc != 0;
+    const int tc = n.tc;
     conv_fwd<16, 16>(B, N, N, n.x, nullptr, L[0].wf, bias(0), 1, n.a1, nullptr, s, tc);
     conv_fwd<16, 16>(B, N, N, n.a1, nullptr, L[1].wf, bias(1), 1, n.s1, nullptr, s, tc);
     note_launch();
@@ -1337,7 +1389,7 @@ cudaError_t cnn_train_loop(Cnn &n, int ns, int N, double h, const double *rhs, c
 }
 
 void cnn_set_scale(Cnn &n, double c) { n.out_scale = c; }
-void cnn_set_tc(Cnn &n, int on) { n.tc = on ? 1 : 0; }
+void cnn_set_tc(Cnn &n, int mode) { n.tc = mode; }
 
 // Reads and clears the tensor-core convolutions' fault word.
 cudaError_t cnn_take_fault(int *f)
