@@ -307,7 +307,7 @@ def test_tensor_core_path_matches_warp_path_and_oracle(T):
     d = lambda a: T.from_numpy(np.ascontiguousarray(a)).cuda()
     drhs, drho = d(rhs), d(rho)
     out, ms = {}, {}
-    for mode in (2, 0):
+    for mode in (2, 1, 0):
         net.set_tensor_path(mode)
         out[mode] = net.infer(drhs, drho).cpu().numpy()
         o = T.empty((B, N, N), dtype=T.float64, device="cuda")
@@ -330,6 +330,7 @@ def test_tensor_core_path_matches_warp_path_and_oracle(T):
           {m: (err[m].max(), np.quantile(err[m], 0.999), np.median(err[m])) for m in (0, 2)},
           "| inference ms tcgen05 / mma.sync:", ms[2], ms[0])
     assert e_tc_warp == 0.0  # same accumulation order: bit for bit
+    assert np.array_equal(out[1], out[0])  # the default mix of the two paths
     for m in (0, 2):
         assert np.median(err[m]) <= 2.0 ** -12 and np.quantile(err[m], 0.999) <= 2.0 ** -6, m
         assert err[m].max() <= 2.0 ** -5, (m, err[m].max())
