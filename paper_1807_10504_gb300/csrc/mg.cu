@@ -661,54 +661,29 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
         __syncthreads();
     }
     // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q);
-    // its cells of one colour, hq rows of hw, are dealt out to the threads in
-    // pairs (cells c and c + 2 of a row share the index arithmetic and the
-    // neighbour between them; the division by the pair count is by a
-    // constant)
+    // its cells of one colour, hq rows of hw, are dealt out to the threads
+    // in turn (the division by hw is by a constant)
     constexpr int Q0 = HA - 1;  // outermost ring updated
     const int par0 = gi0 + gj0 + XO + HA;
-    auto relax = [&](int o, int xo) {
-        float sm = xs[xo + 1] * ps[o + 1];
-        sm = fmaf(xs[xo], ps[o - 1], sm);
-        sm = fmaf(ys[o + PW], ps[o + PW], sm);
-        sm = fmaf(ys[o], ps[o - PW], sm);
-        ps[o] = (sm - h2 * bs[o]) * ds[o];
-    };
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = Q0 - ph, color = ph & 1;
-        const int hq = FH + 2 * q, hw = (FW + 2 * q) / 2, hp = (hw + 1) / 2;
-        for (int k = tid; k < hq * hp; k += FT) {
-            const int rr = k / hp, cp = k - rr * hp;
+        const int hq = FH + 2 * q, hw = (FW + 2 * q) / 2;
+        for (int k = tid; k < hq * hw; k += FT) {
+            const int rr = k / hw, cc = k - rr * hw;
             const int r = HA - q + rr;
-            // (gi + gj + color) even: columns XO - q + 4 cp + parity and + 2
-            const int c = XO - q + 4 * cp + ((par0 - 2 * q + rr + color) & 1);
-            const bool two = 2 * cp + 1 < hw;
-            const int o = r * PW + c, xo = r * XW + xoff[r] + c;
-            if (interior) {
-                if (two) {
-                    // both cells: the centre neighbour ps[o + 1] loaded once
-                    const float pm = ps[o + 1];
-                    float s0 = xs[xo + 1] * pm;
-                    float s1 = xs[xo + 3] * ps[o + 3];
-                    s0 = fmaf(xs[xo], ps[o - 1], s0);
-                    s1 = fmaf(xs[xo + 2], pm, s1);
-                    s0 = fmaf(ys[o + PW], ps[o + PW], s0);
-                    s1 = fmaf(ys[o + PW + 2], ps[o + PW + 2], s1);
-                    s0 = fmaf(ys[o], ps[o - PW], s0);
-                    s1 = fmaf(ys[o + 2], ps[o - PW + 2], s1);
-                    ps[o] = (s0 - h2 * bs[o]) * ds[o];
-                    ps[o + 2] = (s1 - h2 * bs[o + 2]) * ds[o + 2];
-                } else {
-                    relax(o, xo);
-                }
-            } else {
-                const int gj = gj0 + r;
-                if (gj < 0 || gj >= ny) continue;
-                const int gi = gi0 + c;
-                if (gi >= 0 && gi < nx) relax(o, xo);
-                if (two && gi + 2 >= 0 && gi + 2 < nx) relax(o + 2, xo + 2);
+            // (gi + gj + color) even: column XO - q + 2 cc + parity
+            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+            if (!interior) {
+                const int gi = gi0 + c, gj = gj0 + r;
+                if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
             }
+            const int o = r * PW + c, xo = r * XW + xoff[r] + c;
+            float sm = xs[xo + 1] * ps[o + 1];
+            sm = fmaf(xs[xo], ps[o - 1], sm);
+            sm = fmaf(ys[o + PW], ps[o + PW], sm);
+            sm = fmaf(ys[o], ps[o - PW], sm);
+            ps[o] = (sm - h2 * bs[o]) * ds[o];
         }
         __syncthreads();
     }
