@@ -661,29 +661,42 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
         __syncthreads();
     }
     // ring q: local rows [HA - q, HA + FH + q), columns [XO - q, XO + FW + q);
-    // its cells of one colour, hq rows of hw, are dealt out to the threads
-    // in turn (the division by hw is by a constant)
+    // its cells of one colour: hq (even) rows of hw = FW/2 + q.  The first
+    // FW/2 cells of each row go in warp-sized chunks of 16 cells from each of
+    // two adjacent rows: same-colour cells of a row are two words apart and
+    // the two rows' parities differ (the pitch is even), so a chunk's 32
+    // lanes meet all 32 shared-memory banks once.  The last q cells of each
+    // row are dealt out flat.
     constexpr int Q0 = HA - 1;  // outermost ring updated
+    static_assert(PW % 2 == 0 && FW == 64, "bank pattern of the chunks");
     const int par0 = gi0 + gj0 + XO + HA;
+    const int lane = tid & 31, warp = tid >> 5;
+    auto relax = [&](int rr, int cc, int q, int color) {
+        const int r = HA - q + rr;
+        // (gi + gj + color) even: column XO - q + 2 cc + parity
+        const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+        if (!interior) {
+            const int gi = gi0 + c, gj = gj0 + r;
+            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) return;
+        }
+        const int o = r * PW + c, xo = r * XW + xoff[r] + c;
+        float sm = xs[xo + 1] * ps[o + 1];
+        sm = fmaf(xs[xo], ps[o - 1], sm);
+        sm = fmaf(ys[o + PW], ps[o + PW], sm);
+        sm = fmaf(ys[o], ps[o - PW], sm);
+        ps[o] = (sm - h2 * bs[o]) * ds[o];
+    };
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = Q0 - ph, color = ph & 1;
-        const int hq = FH + 2 * q, hw = (FW + 2 * q) / 2;
-        for (int k = tid; k < hq * hw; k += FT) {
-            const int rr = k / hw, cc = k - rr * hw;
-            const int r = HA - q + rr;
-            // (gi + gj + color) even: column XO - q + 2 cc + parity
-            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
-            if (!interior) {
-                const int gi = gi0 + c, gj = gj0 + r;
-                if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
-            }
-            const int o = r * PW + c, xo = r * XW + xoff[r] + c;
-            float sm = xs[xo + 1] * ps[o + 1];
-            sm = fmaf(xs[xo], ps[o - 1], sm);
-            sm = fmaf(ys[o + PW], ps[o + PW], sm);
-            sm = fmaf(ys[o], ps[o - PW], sm);
-            ps[o] = (sm - h2 * bs[o]) * ds[o];
+        const int hq = FH + 2 * q;
+        // chunks: (row pair g >> 1, half g & 1); lanes 0-15 the pair's first
+        // row, 16-31 its second
+        for (int g = warp; g < hq; g += FT / 32)
+            relax(2 * (g >> 1) + (lane >> 4), 16 * (g & 1) + (lane & 15), q, color);
+        for (int k = tid; k < hq * q; k += FT) {
+            const int rr = k / q;  // q >= 1 here
+            relax(rr, FW / 2 + (k - rr * q), q, color);
         }
         __syncthreads();
     }
