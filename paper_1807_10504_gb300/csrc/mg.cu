@@ -530,7 +530,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
 // (the order of its FMAs) is that of k_smooth2_f32, so results agree bit for
 // bit.  Staging, the bounded barrier waits and the fault word are as there.
 template <int MODE>
-__global__ void __launch_bounds__(FT)
+__global__ void __launch_bounds__(FT, MODE == 1 ? 5 : 6)  // as many CTAs as shared memory holds
 k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
                float *__restrict__ p, float *__restrict__ rc, float *__restrict__ ecz,
                const float *__restrict__ ecp, double *__restrict__ p64,
@@ -627,9 +627,16 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
         }
     }
     asm volatile("cp.async.wait_all;\n" ::);
-    bool ok = mbar_wait(&bar, 0, kStageWaitNs);
-    if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
-    // one verdict for the whole block (each thread's wait is bounded)
+    // the first warp waits for the tensor copies (a bounded wait) and the
+    // block barrier of the verdict passes the copied data on to the others;
+    // the other warps issue nothing while they wait there
+    const int lane = tid & 31, warp = tid >> 5;
+    bool ok = true;
+    if (warp == 0) {
+        ok = mbar_wait(&bar, 0, kStageWaitNs);
+        if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
+    }
+    // one verdict for the whole block
     if (__syncthreads_or(!ok)) {
         // skip the tile; the copies must land before the block leaves
         const bool landed = mbar_wait(&bar, 0, kDrainNs);
@@ -670,7 +677,6 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
     constexpr int Q0 = HA - 1;  // outermost ring updated
     static_assert(PW % 2 == 0 && FW == 64, "bank pattern of the chunks");
     const int par0 = gi0 + gj0 + XO + HA;
-    const int lane = tid & 31, warp = tid >> 5;
     auto relax = [&](int rr, int cc, int q, int color) {
         const int r = HA - q + rr;
         // (gi + gj + color) even: column XO - q + 2 cc + parity
