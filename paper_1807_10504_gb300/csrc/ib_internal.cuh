@@ -136,19 +136,23 @@ struct LevelT {
     // FP64 levels only: the pre-scaled stencil of the sweep, 4 weights per
     // cell (W, E, S, N) = beta_f / diag, and the right-hand side h^2 b / diag
     T *w = nullptr, *bt = nullptr;
+    // FP32 levels only: the x-face coefficients again, rows at a pitch of
+    // (nx + 1) rounded up to 4 values (zero padded), for tensor copies, whose
+    // row strides are multiples of 16 bytes
+    T *bxp = nullptr;
 };
 
 // Tensor maps (TMA descriptors) of one fused FP32 smoother launch: windows of
-// the iterate read, the right-hand side, 1/diag and beta_y, and the word that
-// a timed-out staging wait sets.
+// the iterate read, the right-hand side, 1/diag, beta_y and beta_x (padded
+// rows), and the word that a timed-out staging wait sets.
 struct TileMaps {
-    CUtensorMap p, b, d, y;
+    CUtensorMap p, b, d, y, x;
     int *fault;
 };
 
 // A level's FP32 smoother maps for one window shape (both iterate buffers).
 struct LevelTma {
-    CUtensorMap e, e2, r, invd, by;
+    CUtensorMap e, e2, r, invd, by, bxp;
 };
 
 struct Level {

@@ -528,59 +528,31 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
 // values for four fine ones); the FP64 iterate of a defect-correction cycle
 // is read into registers before the sweeps.  The arithmetic of every value
 // (the order of its FMAs) is that of k_smooth2_f32, so results agree bit for
-// bit.  Staging, the bounded barrier waits and the fault word are as there.
+// bit.  All five operand windows come by tensor copies, beta_x from the
+// level's padded-row copy (the packed rows of nx + 1 values have no 16-byte
+// stride); the bounded barrier waits and the fault word are as there.
 template <int MODE>
 __global__ void __launch_bounds__(FT, MODE == 1 ? 5 : 6)  // as many CTAs as shared memory holds
-k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
-               float *__restrict__ p, float *__restrict__ rc, float *__restrict__ ecz,
-               const float *__restrict__ ecp, double *__restrict__ p64,
+k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float *__restrict__ rc,
+               float *__restrict__ ecz, const float *__restrict__ ecp, double *__restrict__ p64,
                const __grid_constant__ TileMaps tm)
 {
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
     constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
-    constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA, XW = PW + 8;
+    constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA;
+    constexpr int XB = PW + 4;  // x-faces of a window row: PW + 1, copied 4 at a time
     constexpr int CWW = FW / 2 + 6, CHH = FH / 2 + 6;  // coarse window (MODE 2): 38 x 14
     __shared__ __align__(128) float ps[PH * PW];
     __shared__ __align__(128) float bs[PH * PW];
     __shared__ __align__(128) float ds[PH * PW];
     __shared__ __align__(128) float ys[(PH + 1) * PW];
-    __shared__ __align__(16) float xs[PH * XW];
+    __shared__ __align__(128) float xs[PH * XB];  // row r: faces gi0 .. gi0 + XB - 1
     __shared__ float cs[MODE == 2 ? CHH * CWW : 1];
-    __shared__ int xoff[PH];
     __shared__ __align__(8) unsigned long long bar, stall_bar;
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
-    const long nxf = nx + 1;
     const int nxc = nx / 2, nyc = ny / 2;
     const int tid = threadIdx.x;
-    // x-faces of the window rows by asynchronous copies: 16-byte copies of
-    // whole in-range chunks, single faces (zero beyond the walls) at the ends
-    auto load_xfaces = [&]() {
-        constexpr int NC = (PW + 1 + 3 + 3) / 4;  // 16-byte chunks per x-face row, worst alignment
-        const long nbx = nxf * ny;
-        for (int k = tid; k < PH * NC; k += FT) {
-            const int r = k / NC, q = k - r * NC, gj = gj0 + r;
-            float *dst = xs + r * XW + 4 * q;
-            if (gj < 0 || gj >= ny) {
-                cp_async16(dst, bx, false);
-                if (q == 0) xoff[r] = 0;
-                continue;
-            }
-            const long start = (long)gj * nxf + gi0, a0 = start & ~3L;
-            if (q == 0) xoff[r] = (int)(start - a0);
-            const long e0 = a0 + 4 * q;
-            const int c0 = (int)(e0 - start);  // window column of face e0
-            if (e0 >= 0 && e0 + 4 <= nbx && gi0 + c0 >= 0 && gi0 + c0 + 3 <= nx) {
-                cp_async16(dst, bx + e0, true);
-            } else {
-                for (int t = 0; t < 4; t++) {
-                    const int gi = gi0 + c0 + t;
-                    const bool ok = gi >= 0 && gi <= nx;
-                    cp_async4(dst + t, ok ? bx + e0 + t : bx, ok);
-                }
-            }
-        }
-    };
-    if (((smem_addr(ps) | smem_addr(bs) | smem_addr(ds) | smem_addr(ys)) & 127u) != 0) {
+    if (((smem_addr(ps) | smem_addr(bs) | smem_addr(ds) | smem_addr(ys) | smem_addr(xs)) & 127u) != 0) {
         if (tid == 0) atomicMax(tm.fault, 2);
         return;
     }
@@ -592,16 +564,17 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
     __syncthreads();  // the barrier is initialised before any thread waits on it
     // the coefficients (1/diag, beta_y, beta_x) are built before the solve
     // and not written during it: their copies start before the wait for the
-    // previous grid; the iterate and right-hand side follow the wait
+    // previous grid; the iterate and right-hand side follow the wait.  gi0
+    // is a multiple of 4: every copy starts on a 16-byte boundary.
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::);
-        constexpr unsigned kBytes = (3 * PH + PH + 1) * PW * 4;
+        constexpr unsigned kBytes = ((3 * PH + PH + 1) * PW + PH * XB) * 4;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      ::"r"(smem_addr(&bar)), "r"(kBytes));
         tma_load2(ds, &tm.d, gi0, gj0, &bar);
         tma_load2(ys, &tm.y, gi0, gj0, &bar);
+        tma_load2(xs, &tm.x, gi0, gj0, &bar);
     }
-    load_xfaces();
     pdl_enter();
     if (tid == 0) {
         tma_load2(ps, &tm.p, gi0, gj0, &bar);
@@ -626,7 +599,6 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
             }
         }
     }
-    asm volatile("cp.async.wait_all;\n" ::);
     // the first warp waits for the tensor copies (a bounded wait) and the
     // block barrier of the verdict passes the copied data on to the others;
     // the other warps issue nothing while they wait there
@@ -685,7 +657,7 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
             const int gi = gi0 + c, gj = gj0 + r;
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) return;
         }
-        const int o = r * PW + c, xo = r * XW + xoff[r] + c;
+        const int o = r * PW + c, xo = r * XB + c;
         float sm = xs[xo + 1] * ps[o + 1];
         sm = fmaf(xs[xo], ps[o - 1], sm);
         sm = fmaf(ys[o + PW], ps[o + PW], sm);
@@ -716,7 +688,7 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx
                 const float cc = ps[o];
                 const float pE = gi + 1 < nx ? ps[o + 1] : cc, pW = gi > 0 ? ps[o - 1] : cc;
                 const float pN = gj + 1 < ny ? ps[o + PW] : cc, pS = gj > 0 ? ps[o - PW] : cc;
-                const int xc = r * XW + c + xoff[r];
+                const int xc = r * XB + c;
                 float sv = xs[xc + 1] * (pE - cc);
                 sv -= xs[xc] * (cc - pW);
                 sv += ys[o + PW] * (pN - cc);
@@ -954,16 +926,22 @@ __global__ void k_coarsen_beta(int nx, int ny, const double *__restrict__ bx,
     byc[k] = 0.5 * (by[(long)(2 * J) * nx + 2 * I] + by[(long)(2 * J) * nx + 2 * I + 1]);
 }
 
+// Row pitch of the padded FP32 x-face copy: nx + 1 faces rounded up to a
+// multiple of 4 values (16 bytes).
+__host__ __device__ constexpr int xface_pitch(int nx) { return (nx + 4) & ~3; }
+
 // Coefficients of one level in one pass, one thread per cell: the cell's
 // west and south faces (and the east / north wall faces of the last column /
 // row) from the finer level (mean of the two fine faces; at level 0 the
-// caller's faces with the walls set to zero), their FP32 copies, and the FP64
-// and FP32 inverse diagonals (the cell's four faces, recomputed locally).
+// caller's faces with the walls set to zero), their FP32 copies (the x-faces
+// twice: packed and in padded rows), and the FP64 and FP32 inverse
+// diagonals (the cell's four faces, recomputed locally).
 __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, int i, int j,
                                                   const double *__restrict__ fbx,
                                                   const double *__restrict__ fby,
                                                   double *__restrict__ bx, double *__restrict__ by,
                                                   float *__restrict__ bxf, float *__restrict__ byf,
+                                                  float *__restrict__ bxp,
                                                   double *__restrict__ invd, float *__restrict__ invdf,
                                                   double *__restrict__ w4)
 {
@@ -984,6 +962,13 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
     by[kc] = s; byf[kc] = (float)s;
     if (i == nx - 1) { bx[kx + 1] = e; bxf[kx + 1] = (float)e; }
     if (j == ny - 1) { by[kc + nx] = n; byf[kc + nx] = (float)n; }
+    const int xp = xface_pitch(nx);
+    float *rowp = bxp + (long)j * xp;
+    rowp[i] = (float)w;
+    if (i == nx - 1) {
+        rowp[nx] = (float)e;
+        for (int t = nx + 1; t < xp; t++) rowp[t] = 0.0f;  // padding
+    }
     const double d = e + w + n + s;
     const double id = d > 0.0 ? recip_nr(d) : 0.0;
     invd[kc] = id;
@@ -995,12 +980,13 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
 __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
                                const double *__restrict__ fby, double *__restrict__ bx,
                                double *__restrict__ by, float *__restrict__ bxf,
-                               float *__restrict__ byf, double *__restrict__ invd,
-                               float *__restrict__ invdf, double *__restrict__ w4)
+                               float *__restrict__ byf, float *__restrict__ bxp,
+                               double *__restrict__ invd, float *__restrict__ invdf,
+                               double *__restrict__ w4)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nx) return;
-    level_coeffs_cell(nx, ny, level0, i, j, fbx, fby, bx, by, bxf, byf, invd, invdf, w4);
+    level_coeffs_cell(nx, ny, level0, i, j, fbx, fby, bx, by, bxf, byf, bxp, invd, invdf, w4);
 }
 
 // The small levels (from `first` on) in one CTA, level after level; a level
@@ -1010,7 +996,7 @@ struct LevelCoeffArgs {
     int first, nl;
     int nx[16], ny[16];
     double *bx[16], *by[16], *invd[16], *w4[16];
-    float *bxf[16], *byf[16], *invdf[16];
+    float *bxf[16], *byf[16], *bxp[16], *invdf[16];
 };
 
 __global__ void __launch_bounds__(1024) k_level_coeffs_small(LevelCoeffArgs a)
@@ -1020,7 +1006,7 @@ __global__ void __launch_bounds__(1024) k_level_coeffs_small(LevelCoeffArgs a)
         for (int k = threadIdx.x; k < nx * ny; k += blockDim.x) {
             const int j = k / nx, i = k - j * nx;
             level_coeffs_cell(nx, ny, l == 0, i, j, a.bx[l - 1], a.by[l - 1], a.bx[l], a.by[l], a.bxf[l],
-                              a.byf[l], a.invd[l], a.invdf[l], a.w4[l]);
+                              a.byf[l], a.bxp[l], a.invd[l], a.invdf[l], a.w4[l]);
         }
         __syncthreads();
     }
@@ -1691,8 +1677,8 @@ void launch_smooth2(const Level &v, const LevelT<float> &a, const float *pin, fl
         tm.d = w.invd;
         tm.y = w.by;
         tm.fault = v.fault;
-        launch_pdl(k_smooth2t_f32<MODE>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, p, rc, ecz, ecp,
-                   p64, tm);
+        tm.x = w.bxp;
+        launch_pdl(k_smooth2t_f32<MODE>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, p, rc, ecz, ecp, p64, tm);
     } else {
         launch_pdl(k_smooth2_f32<MODE, false>, g2, FT, 0, s, v.nx, v.ny, h2, ih2, a.bx, a.by,
                    a.invd, a.r, pin, p, rc, ecz, ecp, p64, tm);
@@ -2004,7 +1990,8 @@ static bool map2d(CUtensorMap *m, const float *base, int w, int hgt, int bw, int
 
 // Tensor maps of a level's FP32 smoother operands for both window shapes
 // (FW + 2 XO) x (FH + 2 HA) with (XO, HA) = (4, 4) and (8, 5); beta_y windows
-// have one more row.  Needs rows of a multiple of 4 values (16-byte strides).
+// have one more row, beta_x windows (padded rows) 4 more columns.  Needs
+// rows of a multiple of 4 values (16-byte strides).
 static bool encode_level_maps(Level &v)
 {
     const LevelT<float> &a = v.f;
@@ -2013,7 +2000,8 @@ static bool encode_level_maps(Level &v)
         LevelTma &w = v.tm[k];
         if (!map2d(&w.e, a.e, v.nx, v.ny, bw, bh) || !map2d(&w.e2, a.e2, v.nx, v.ny, bw, bh) ||
             !map2d(&w.r, a.r, v.nx, v.ny, bw, bh) || !map2d(&w.invd, a.invd, v.nx, v.ny, bw, bh) ||
-            !map2d(&w.by, a.by, v.nx, v.ny + 1, bw, bh + 1))
+            !map2d(&w.by, a.by, v.nx, v.ny + 1, bw, bh + 1) ||
+            !map2d(&w.bxp, a.bxp, xface_pitch(v.nx), v.ny, bw + 4, bh))
             return false;
     }
     return true;
@@ -2048,6 +2036,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         v.f.e = (float *)take(n * 4); v.f.e2 = (float *)take(n * 4);
         v.f.r = (float *)take(n * 4); v.f.invd = (float *)take(n * 4);
         v.f.bx = (float *)take(fx * 4); v.f.by = (float *)take(fy * 4);
+        v.f.bxp = (float *)take((size_t)xface_pitch(v.nx) * v.ny * 4);
     }
     mg.lu = (double *)take((size_t)nc * nc * 8 * 2);  // A' and its transposed inverse
     mg.piv = (int *)take((size_t)nc * 4);
@@ -2184,7 +2173,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         dim3 g(cdiv(v.nx, 128), v.ny);
         note_launch();
         k_level_coeffs<<<g, 128, 0, s>>>(v.nx, v.ny, l == 0, fbx, fby, v.d.bx, v.d.by, v.f.bx, v.f.by,
-                                         v.d.invd, v.f.invd, v.d.w);
+                                         v.f.bxp, v.d.invd, v.f.invd, v.d.w);
     }
     if (lsmall < L) {
         LevelCoeffArgs a;
@@ -2194,7 +2183,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
             Level &v = mg.lv[l];
             a.nx[l] = v.nx; a.ny[l] = v.ny;
             a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd; a.w4[l] = v.d.w;
-            a.bxf[l] = v.f.bx; a.byf[l] = v.f.by; a.invdf[l] = v.f.invd;
+            a.bxf[l] = v.f.bx; a.byf[l] = v.f.by; a.bxp[l] = v.f.bxp; a.invdf[l] = v.f.invd;
         }
         note_launch();
         k_level_coeffs_small<<<1, 1024, 0, s>>>(a);
