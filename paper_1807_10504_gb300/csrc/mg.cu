@@ -649,32 +649,43 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     constexpr int Q0 = HA - 1;  // outermost ring updated
     static_assert(PW % 2 == 0 && FW == 64, "bank pattern of the chunks");
     const int par0 = gi0 + gj0 + XO + HA;
-    auto relax = [&](int rr, int cc, int q, int color) {
-        const int r = HA - q + rr;
-        // (gi + gj + color) even: column XO - q + 2 cc + parity
-        const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
-        if (!interior) {
-            const int gi = gi0 + c, gj = gj0 + r;
-            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) return;
-        }
-        const int o = r * PW + c, xo = r * XB + c;
+    // one red-black update at shared offsets o (window) and xo (x-faces)
+    auto relax = [&](int o, int xo) {
         float sm = xs[xo + 1] * ps[o + 1];
         sm = fmaf(xs[xo], ps[o - 1], sm);
         sm = fmaf(ys[o + PW], ps[o + PW], sm);
         sm = fmaf(ys[o], ps[o - PW], sm);
         ps[o] = (sm - h2 * bs[o]) * ds[o];
     };
+    // outside an interior tile, cells beyond the walls are not updated
+    auto inside = [&](int r, int c) {
+        const int gi = gi0 + c, gj = gj0 + r;
+        return interior || (gi >= 0 && gi < nx && gj >= 0 && gj < ny);
+    };
+    constexpr int NW = FT / 32;  // warps; NW is even, so a warp's chunks keep one half
+    static_assert(NW % 2 == 0 && (FH + 2 * Q0) * Q0 <= FT, "chunk halves; one pass for the rest");
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = Q0 - ph, color = ph & 1;
         const int hq = FH + 2 * q;
-        // chunks: (row pair g >> 1, half g & 1); lanes 0-15 the pair's first
-        // row, 16-31 its second
-        for (int g = warp; g < hq; g += FT / 32)
-            relax(2 * (g >> 1) + (lane >> 4), 16 * (g & 1) + (lane & 15), q, color);
-        for (int k = tid; k < hq * q; k += FT) {
-            const int rr = k / q;  // q >= 1 here
-            relax(rr, FW / 2 + (k - rr * q), q, color);
+        {
+            // chunks g = warp, warp + NW, ...: row pair g >> 1, half g & 1;
+            // lanes 0-15 the pair's first row, 16-31 its second.  Along the
+            // loop the row advances by NW, the column and parity stay.
+            const int rr0 = 2 * (warp >> 1) + (lane >> 4);
+            const int cc = 16 * (warp & 1) + (lane & 15);
+            // (gi + gj + color) even: column XO - q + 2 cc + parity
+            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr0 + color) & 1);
+            int r = HA - q + rr0;
+            int o = r * PW + c, xo = r * XB + c;
+            for (int g = warp; g < hq; g += NW, r += NW, o += NW * PW, xo += NW * XB)
+                if (inside(r, c)) relax(o, xo);
+        }
+        if (tid < hq * q) {  // the last q cells of each row (hq * q <= FT)
+            const int rr = tid / q, cc = FW / 2 + (tid - rr * q);
+            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+            const int r = HA - q + rr;
+            if (inside(r, c)) relax(r * PW + c, r * XB + c);
         }
         __syncthreads();
     }
