@@ -540,13 +540,15 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     constexpr int HA = MODE == 1 ? 5 : 4;   // rows of halo
     constexpr int XO = MODE == 1 ? 8 : 4;   // columns of halo (a multiple of 4: 16-byte rows)
     constexpr int PW = FW + 2 * XO, PH = FH + 2 * HA;
-    constexpr int XB = PW + 4;  // x-faces of a window row: PW + 1, copied 4 at a time
     constexpr int CWW = FW / 2 + 6, CHH = FH / 2 + 6;  // coarse window (MODE 2): 38 x 14
     __shared__ __align__(128) float ps[PH * PW];
     __shared__ __align__(128) float bs[PH * PW];
     __shared__ __align__(128) float ds[PH * PW];
     __shared__ __align__(128) float ys[(PH + 1) * PW];
-    __shared__ __align__(128) float xs[PH * XB];  // row r: faces gi0 .. gi0 + XB - 1
+    // x-faces: row r holds faces gi0 .. gi0 + PW - 1, the west face of each
+    // window cell (no updated cell needs the east face of the window's last
+    // column), so one offset addresses all five windows
+    __shared__ __align__(128) float xs[PH * PW];
     __shared__ float cs[MODE == 2 ? CHH * CWW : 1];
     __shared__ __align__(8) unsigned long long bar, stall_bar;
     const int gi0 = blockIdx.x * FW - XO, gj0 = blockIdx.y * FH - HA;
@@ -568,7 +570,7 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     // is a multiple of 4: every copy starts on a 16-byte boundary.
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::);
-        constexpr unsigned kBytes = ((3 * PH + PH + 1) * PW + PH * XB) * 4;
+        constexpr unsigned kBytes = (4 * PH + PH + 1) * PW * 4;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
                      ::"r"(smem_addr(&bar)), "r"(kBytes));
         tma_load2(ds, &tm.d, gi0, gj0, &bar);
@@ -621,6 +623,23 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
         // step: (9 c00 + 3 c10 + 3 c01 + c11) / 16 with the neighbours on the
         // cell's side, clamped at the walls (zero gradient)
         constexpr int BW = PW / 2, BH = PH / 2;
+        // the window's blocks and all their neighbours inside the coarse
+        // grid: no range tests, no clamps, the nine values at fixed offsets
+        const bool cin = cI0 >= 0 && cI0 + BW + 1 < nxc && cJ0 >= 0 && cJ0 + BH + 1 < nyc;
+        if (cin) {
+            for (int kb = tid; kb < BW * BH; kb += FT) {
+                const int bj = kb / BW, bi = kb - bj * BW;
+                const float *c0 = cs + bj * CWW + bi;  // the block's south-west neighbour
+                const float cSW = c0[0], cS = c0[1], cSE = c0[2];
+                const float cW = c0[CWW], c = c0[CWW + 1], cE = c0[CWW + 2];
+                const float cNW = c0[2 * CWW], cN = c0[2 * CWW + 1], cNE = c0[2 * CWW + 2];
+                float *q0 = ps + (2 * bj) * PW + 2 * bi;
+                q0[0] += (9.0f * c + 3.0f * cW + 3.0f * cS + cSW) * 0.0625f;
+                q0[1] += (9.0f * c + 3.0f * cE + 3.0f * cS + cSE) * 0.0625f;
+                q0[PW] += (9.0f * c + 3.0f * cW + 3.0f * cN + cNW) * 0.0625f;
+                q0[PW + 1] += (9.0f * c + 3.0f * cE + 3.0f * cN + cNE) * 0.0625f;
+            }
+        } else
         for (int kb = tid; kb < BW * BH; kb += FT) {
             const int bj = kb / BW, bi = kb - bj * BW;
             const int I = cI0 + 1 + bi, J = cJ0 + 1 + bj;
@@ -649,10 +668,10 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     constexpr int Q0 = HA - 1;  // outermost ring updated
     static_assert(PW % 2 == 0 && FW == 64, "bank pattern of the chunks");
     const int par0 = gi0 + gj0 + XO + HA;
-    // one red-black update at shared offsets o (window) and xo (x-faces)
-    auto relax = [&](int o, int xo) {
-        float sm = xs[xo + 1] * ps[o + 1];
-        sm = fmaf(xs[xo], ps[o - 1], sm);
+    // one red-black update of the cell at shared offset o
+    auto relax = [&](int o) {
+        float sm = xs[o + 1] * ps[o + 1];
+        sm = fmaf(xs[o], ps[o - 1], sm);
         sm = fmaf(ys[o + PW], ps[o + PW], sm);
         sm = fmaf(ys[o], ps[o - PW], sm);
         ps[o] = (sm - h2 * bs[o]) * ds[o];
@@ -660,32 +679,33 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     // outside an interior tile, cells beyond the walls are not updated
     auto inside = [&](int r, int c) {
         const int gi = gi0 + c, gj = gj0 + r;
-        return interior || (gi >= 0 && gi < nx && gj >= 0 && gj < ny);
+        return gi >= 0 && gi < nx && gj >= 0 && gj < ny;
     };
     constexpr int NW = FT / 32;  // warps; NW is even, so a warp's chunks keep one half
     static_assert(NW % 2 == 0 && (FH + 2 * Q0) * Q0 <= FT, "chunk halves; one pass for the rest");
+    const int rr0 = 2 * (warp >> 1) + (lane >> 4);  // row of the warp's first chunk
+    const int cc0 = 16 * (warp & 1) + (lane & 15);
 #pragma unroll
     for (int ph = 0; ph < 4; ph++) {
         const int q = Q0 - ph, color = ph & 1;
         const int hq = FH + 2 * q;
-        {
-            // chunks g = warp, warp + NW, ...: row pair g >> 1, half g & 1;
-            // lanes 0-15 the pair's first row, 16-31 its second.  Along the
-            // loop the row advances by NW, the column and parity stay.
-            const int rr0 = 2 * (warp >> 1) + (lane >> 4);
-            const int cc = 16 * (warp & 1) + (lane & 15);
-            // (gi + gj + color) even: column XO - q + 2 cc + parity
-            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr0 + color) & 1);
-            int r = HA - q + rr0;
-            int o = r * PW + c, xo = r * XB + c;
-            for (int g = warp; g < hq; g += NW, r += NW, o += NW * PW, xo += NW * XB)
-                if (inside(r, c)) relax(o, xo);
+        // chunks g = warp + NW t: row pair g >> 1, half g & 1; lanes 0-15 the
+        // pair's first row, 16-31 its second.  Along t the row advances by
+        // NW, the column and parity stay; the trip count is a constant.
+        // (gi + gj + color) even: column XO - q + 2 cc + parity
+        const int c = XO - q + 2 * cc0 + ((par0 - 2 * q + rr0 + color) & 1);
+        const int r0 = HA - q + rr0, o0 = r0 * PW + c;
+        constexpr int NT = (FH + 2 * Q0 + NW - 1) / NW;  // enough for the largest ring
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            if (t * NW >= hq) break;  // constant after unrolling
+            if (warp + t * NW < hq && (interior || inside(r0 + t * NW, c))) relax(o0 + t * NW * PW);
         }
         if (tid < hq * q) {  // the last q cells of each row (hq * q <= FT)
             const int rr = tid / q, cc = FW / 2 + (tid - rr * q);
-            const int c = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+            const int cq = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
             const int r = HA - q + rr;
-            if (inside(r, c)) relax(r * PW + c, r * XB + c);
+            if (interior || inside(r, cq)) relax(r * PW + cq);
         }
         __syncthreads();
     }
@@ -699,9 +719,8 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
                 const float cc = ps[o];
                 const float pE = gi + 1 < nx ? ps[o + 1] : cc, pW = gi > 0 ? ps[o - 1] : cc;
                 const float pN = gj + 1 < ny ? ps[o + PW] : cc, pS = gj > 0 ? ps[o - PW] : cc;
-                const int xc = r * XB + c;
-                float sv = xs[xc + 1] * (pE - cc);
-                sv -= xs[xc] * (cc - pW);
+                float sv = xs[o + 1] * (pE - cc);
+                sv -= xs[o] * (cc - pW);
                 sv += ys[o + PW] * (pN - cc);
                 sv -= ys[o] * (cc - pS);
                 return bs[o] - sv * ih2;
@@ -2001,8 +2020,8 @@ static bool map2d(CUtensorMap *m, const float *base, int w, int hgt, int bw, int
 
 // Tensor maps of a level's FP32 smoother operands for both window shapes
 // (FW + 2 XO) x (FH + 2 HA) with (XO, HA) = (4, 4) and (8, 5); beta_y windows
-// have one more row, beta_x windows (padded rows) 4 more columns.  Needs
-// rows of a multiple of 4 values (16-byte strides).
+// have one more row; beta_x windows come from the padded rows.  Needs rows
+// of a multiple of 4 values (16-byte strides).
 static bool encode_level_maps(Level &v)
 {
     const LevelT<float> &a = v.f;
@@ -2012,7 +2031,7 @@ static bool encode_level_maps(Level &v)
         if (!map2d(&w.e, a.e, v.nx, v.ny, bw, bh) || !map2d(&w.e2, a.e2, v.nx, v.ny, bw, bh) ||
             !map2d(&w.r, a.r, v.nx, v.ny, bw, bh) || !map2d(&w.invd, a.invd, v.nx, v.ny, bw, bh) ||
             !map2d(&w.by, a.by, v.nx, v.ny + 1, bw, bh + 1) ||
-            !map2d(&w.bxp, a.bxp, xface_pitch(v.nx), v.ny, bw + 4, bh))
+            !map2d(&w.bxp, a.bxp, xface_pitch(v.nx), v.ny, bw, bh))
             return false;
     }
     return true;
