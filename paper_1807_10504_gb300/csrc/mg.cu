@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -583,28 +584,46 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
         tma_load2(bs, &tm.b, gi0, gj0, &bar);
     }
     const int cI0 = blockIdx.x * (FW / 2) - 3, cJ0 = blockIdx.y * (FH / 2) - 3;
+    const int lane = tid & 31, warp = tid >> 5;
+    // the coarse window inside the coarse grid (then so are the neighbours
+    // of all its prolonged blocks): no range tests
+    const bool cin = cI0 >= 0 && cI0 + CWW <= nxc && cJ0 >= 0 && cJ0 + CHH <= nyc;
     if constexpr (MODE == 2) {
         // the coarse correction's window, while the tensor copies fly
-        for (int k = tid; k < CHH * CWW; k += FT) {
-            const int j = k / CWW, i = k - j * CWW, gI = cI0 + i, gJ = cJ0 + j;
-            cs[k] = (gI >= 0 && gI < nxc && gJ >= 0 && gJ < nyc) ? ecp[(long)gJ * nxc + gI] : 0.0f;
+        static_assert(CWW > 32 && CWW <= 64, "a window row is one or two loads a lane");
+        if (cin) {
+            for (int j = warp; j < CHH; j += FT / 32) {
+                const float *src = ecp + (long)(cJ0 + j) * nxc + cI0;
+                cs[j * CWW + lane] = src[lane];
+                if (lane < CWW - 32) cs[j * CWW + 32 + lane] = src[32 + lane];
+            }
+        } else {
+            for (int k = tid; k < CHH * CWW; k += FT) {
+                const int j = k / CWW, i = k - j * CWW, gI = cI0 + i, gJ = cJ0 + j;
+                cs[k] = (gI >= 0 && gI < nxc && gJ >= 0 && gJ < nyc) ? ecp[(long)gJ * nxc + gI] : 0.0f;
+            }
         }
     }
+    // the tile's cells all inside the grid: no range tests on the global
+    // iterate (thread k of the block takes column k % FW of rows k / FW + 4 j)
+    const bool whole = (blockIdx.x + 1) * FW <= nx && (blockIdx.y + 1) * FH <= ny;
+    const int tcol = tid % FW, trow = tid / FW;
+    constexpr int RS = FT / FW;  // rows a pass of the block covers
     // the FP64 iterate of the tile (defect correction), read ahead
     double v64[MODE == 2 ? (FW * FH) / FT : 1];
     if constexpr (MODE == 2) {
         if (p64) {
+            const long g0 = (long)(blockIdx.y * FH + trow) * nx + blockIdx.x * FW + tcol;
 #pragma unroll
             for (int j = 0; j < (FW * FH) / FT; j++) {
-                const int k = tid + j * FT, gi = blockIdx.x * FW + (k % FW), gj = blockIdx.y * FH + k / FW;
-                v64[j] = (gi < nx && gj < ny) ? p64[(long)gj * nx + gi] : 0.0;
+                const int gi = blockIdx.x * FW + tcol, gj = blockIdx.y * FH + trow + RS * j;
+                v64[j] = (whole || (gi < nx && gj < ny)) ? p64[g0 + (long)RS * j * nx] : 0.0;
             }
         }
     }
     // the first warp waits for the tensor copies (a bounded wait) and the
     // block barrier of the verdict passes the copied data on to the others;
     // the other warps issue nothing while they wait there
-    const int lane = tid & 31, warp = tid >> 5;
     bool ok = true;
     if (warp == 0) {
         ok = mbar_wait(&bar, 0, kStageWaitNs);
@@ -623,9 +642,8 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
         // step: (9 c00 + 3 c10 + 3 c01 + c11) / 16 with the neighbours on the
         // cell's side, clamped at the walls (zero gradient)
         constexpr int BW = PW / 2, BH = PH / 2;
-        // the window's blocks and all their neighbours inside the coarse
-        // grid: no range tests, no clamps, the nine values at fixed offsets
-        const bool cin = cI0 >= 0 && cI0 + BW + 1 < nxc && cJ0 >= 0 && cJ0 + BH + 1 < nyc;
+        // cin: no range tests, no clamps, the nine values at fixed offsets
+        static_assert(CWW == BW + 2 && CHH == BH + 2, "coarse window = blocks + neighbours");
         if (cin) {
             for (int kb = tid; kb < BW * BH; kb += FT) {
                 const int bj = kb / BW, bi = kb - bj * BW;
@@ -685,30 +703,38 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     static_assert(NW % 2 == 0 && (FH + 2 * Q0) * Q0 <= FT, "chunk halves; one pass for the rest");
     const int rr0 = 2 * (warp >> 1) + (lane >> 4);  // row of the warp's first chunk
     const int cc0 = 16 * (warp & 1) + (lane & 15);
+    // the four phases, with (CHECK) or without the wall tests
+    auto sweeps = [&](auto check) {
+        constexpr bool CHECK = decltype(check)::value;
 #pragma unroll
-    for (int ph = 0; ph < 4; ph++) {
-        const int q = Q0 - ph, color = ph & 1;
-        const int hq = FH + 2 * q;
-        // chunks g = warp + NW t: row pair g >> 1, half g & 1; lanes 0-15 the
-        // pair's first row, 16-31 its second.  Along t the row advances by
-        // NW, the column and parity stay; the trip count is a constant.
-        // (gi + gj + color) even: column XO - q + 2 cc + parity
-        const int c = XO - q + 2 * cc0 + ((par0 - 2 * q + rr0 + color) & 1);
-        const int r0 = HA - q + rr0, o0 = r0 * PW + c;
-        constexpr int NT = (FH + 2 * Q0 + NW - 1) / NW;  // enough for the largest ring
+        for (int ph = 0; ph < 4; ph++) {
+            const int q = Q0 - ph, color = ph & 1;
+            const int hq = FH + 2 * q;
+            // chunks g = warp + NW t: row pair g >> 1, half g & 1; lanes 0-15
+            // the pair's first row, 16-31 its second.  Along t the row
+            // advances by NW, the column and parity stay; the trip count is
+            // a constant, and chunks with (t + 1) NW <= hq exist for every
+            // warp.  (gi + gj + color) even: column XO - q + 2 cc + parity
+            const int c = XO - q + 2 * cc0 + ((par0 - 2 * q + rr0 + color) & 1);
+            const int r0 = HA - q + rr0, o0 = r0 * PW + c;
+            constexpr int NT = (FH + 2 * Q0 + NW - 1) / NW;  // enough for the largest ring
 #pragma unroll
-        for (int t = 0; t < NT; t++) {
-            if (t * NW >= hq) break;  // constant after unrolling
-            if (warp + t * NW < hq && (interior || inside(r0 + t * NW, c))) relax(o0 + t * NW * PW);
+            for (int t = 0; t < NT; t++) {
+                if (t * NW >= hq) break;  // constant after unrolling
+                if ((t + 1) * NW <= hq || warp + t * NW < hq)
+                    if (!CHECK || inside(r0 + t * NW, c)) relax(o0 + t * NW * PW);
+            }
+            if (tid < hq * q) {  // the last q cells of each row (hq * q <= FT)
+                const int rr = tid / q, cc = FW / 2 + (tid - rr * q);
+                const int cq = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
+                const int r = HA - q + rr;
+                if (!CHECK || inside(r, cq)) relax(r * PW + cq);
+            }
+            __syncthreads();
         }
-        if (tid < hq * q) {  // the last q cells of each row (hq * q <= FT)
-            const int rr = tid / q, cc = FW / 2 + (tid - rr * q);
-            const int cq = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
-            const int r = HA - q + rr;
-            if (interior || inside(r, cq)) relax(r * PW + cq);
-        }
-        __syncthreads();
-    }
+    };
+    if (interior) sweeps(std::false_type{});
+    else sweeps(std::true_type{});
     if (MODE == 1) {
         // one coarse cell per thread: FW/2 x FH/2 = 32 x 8
         const int I = blockIdx.x * (FW / 2) + (tid % (FW / 2));
@@ -731,14 +757,17 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
             ecz[(long)J * nxc + I] = 0.0f;
         }
     }
+    {
+        const long g0 = (long)(blockIdx.y * FH + trow) * nx + blockIdx.x * FW + tcol;
 #pragma unroll
-    for (int j = 0; j < (FW * FH) / FT; j++) {
-        const int k = tid + j * FT, col = k % FW, row = k / FW;
-        const int gi = blockIdx.x * FW + col, gj = blockIdx.y * FH + row;
-        if (gi < nx && gj < ny) {
-            const float v = ps[(HA + row) * PW + XO + col];
-            if (MODE == 2 && p64) p64[(long)gj * nx + gi] = v64[MODE == 2 ? j : 0] + (double)v;
-            else p[(long)gj * nx + gi] = v;
+        for (int j = 0; j < (FW * FH) / FT; j++) {
+            const int gi = blockIdx.x * FW + tcol, gj = blockIdx.y * FH + trow + RS * j;
+            if (whole || (gi < nx && gj < ny)) {
+                const float v = ps[(HA + trow + RS * j) * PW + XO + tcol];
+                const long g = g0 + (long)RS * j * nx;
+                if (MODE == 2 && p64) p64[g] = v64[MODE == 2 ? j : 0] + (double)v;
+                else p[g] = v;
+            }
         }
     }
 }
