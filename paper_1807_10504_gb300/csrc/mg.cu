@@ -736,15 +736,26 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
     if (interior) sweeps(std::false_type{});
     else sweeps(std::true_type{});
     if (MODE == 1) {
-        // one coarse cell per thread: FW/2 x FH/2 = 32 x 8
-        const int I = blockIdx.x * (FW / 2) + (tid % (FW / 2));
-        const int J = blockIdx.y * (FH / 2) + (tid / (FW / 2));
+        // one coarse cell per thread: FW/2 x FH/2 = 32 x 8, a warp per
+        // coarse row.  Lanes 16-31 take the two children of a row in the
+        // other order, so that each step's reads of a warp fall on even
+        // words (lanes 0-15) and odd words (16-31): no bank conflicts.  The
+        // four residuals are summed in the fixed order all the same.
+        static_assert(FW / 2 == 32, "a warp per coarse row");
+        const int ti = tid % (FW / 2), tj = tid / (FW / 2);
+        const int I = blockIdx.x * (FW / 2) + ti, J = blockIdx.y * (FH / 2) + tj;
+        const int sx = lane >> 4;  // 1: east child first
         if (I < nxc && J < nyc) {
             auto res = [&](int gi, int gj) {
                 const int r = gj - gj0, c = gi - gi0, o = r * PW + c;
                 const float cc = ps[o];
-                const float pE = gi + 1 < nx ? ps[o + 1] : cc, pW = gi > 0 ? ps[o - 1] : cc;
-                const float pN = gj + 1 < ny ? ps[o + PW] : cc, pS = gj > 0 ? ps[o - PW] : cc;
+                float pE, pW, pN, pS;
+                if (interior) {  // every neighbour is in the grid
+                    pE = ps[o + 1]; pW = ps[o - 1]; pN = ps[o + PW]; pS = ps[o - PW];
+                } else {
+                    pE = gi + 1 < nx ? ps[o + 1] : cc; pW = gi > 0 ? ps[o - 1] : cc;
+                    pN = gj + 1 < ny ? ps[o + PW] : cc; pS = gj > 0 ? ps[o - PW] : cc;
+                }
                 float sv = xs[o + 1] * (pE - cc);
                 sv -= xs[o] * (cc - pW);
                 sv += ys[o + PW] * (pN - cc);
@@ -752,7 +763,10 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
                 return bs[o] - sv * ih2;
             };
             const int i = 2 * I, j = 2 * J;
-            const float r00 = res(i, j), r10 = res(i + 1, j), r01 = res(i, j + 1), r11 = res(i + 1, j + 1);
+            const float ra = res(i + sx, j), rb = res(i + 1 - sx, j);
+            const float rcN = res(i + sx, j + 1), rdN = res(i + 1 - sx, j + 1);
+            const float r00 = sx ? rb : ra, r10 = sx ? ra : rb;
+            const float r01 = sx ? rdN : rcN, r11 = sx ? rcN : rdN;
             rc[(long)J * nxc + I] = 0.25f * (r00 + r10 + r01 + r11);
             ecz[(long)J * nxc + I] = 0.0f;
         }
