@@ -645,18 +645,29 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
         // cin: no range tests, no clamps, the nine values at fixed offsets
         static_assert(CWW == BW + 2 && CHH == BH + 2, "coarse window = blocks + neighbours");
         if (cin) {
-            for (int kb = tid; kb < BW * BH; kb += FT) {
-                const int bj = kb / BW, bi = kb - bj * BW;
+            // block (bj, bi); sx = 1 takes the east children first
+            auto block = [&](int bj, int bi, int sx) {
                 const float *c0 = cs + bj * CWW + bi;  // the block's south-west neighbour
                 const float cSW = c0[0], cS = c0[1], cSE = c0[2];
                 const float cW = c0[CWW], c = c0[CWW + 1], cE = c0[CWW + 2];
                 const float cNW = c0[2 * CWW], cN = c0[2 * CWW + 1], cNE = c0[2 * CWW + 2];
+                const float v00 = (9.0f * c + 3.0f * cW + 3.0f * cS + cSW) * 0.0625f;
+                const float v10 = (9.0f * c + 3.0f * cE + 3.0f * cS + cSE) * 0.0625f;
+                const float v01 = (9.0f * c + 3.0f * cW + 3.0f * cN + cNW) * 0.0625f;
+                const float v11 = (9.0f * c + 3.0f * cE + 3.0f * cN + cNE) * 0.0625f;
                 float *q0 = ps + (2 * bj) * PW + 2 * bi;
-                q0[0] += (9.0f * c + 3.0f * cW + 3.0f * cS + cSW) * 0.0625f;
-                q0[1] += (9.0f * c + 3.0f * cE + 3.0f * cS + cSE) * 0.0625f;
-                q0[PW] += (9.0f * c + 3.0f * cW + 3.0f * cN + cNW) * 0.0625f;
-                q0[PW + 1] += (9.0f * c + 3.0f * cE + 3.0f * cN + cNE) * 0.0625f;
-            }
+                q0[sx] += sx ? v10 : v00;
+                q0[1 - sx] += sx ? v00 : v10;
+                q0[PW + sx] += sx ? v11 : v01;
+                q0[PW + 1 - sx] += sx ? v01 : v11;
+            };
+            // blocks 0-31 of a block row: a warp each, lanes 16-31 east
+            // children first (even words for lanes 0-15, odd for 16-31: no
+            // bank conflicts); blocks 32 on to the warps with fewer rows
+            static_assert(BW >= 32 && (BW - 32) * BH <= FT - 32 * (BH % (FT / 32)), "block split");
+            for (int bj = warp; bj < BH; bj += FT / 32) block(bj, lane, lane >> 4);
+            const int k = tid - 32 * (BH % (FT / 32));
+            if (k >= 0 && k < (BW - 32) * BH) block(k / (BW - 32), 32 + k % (BW - 32), 0);
         } else
         for (int kb = tid; kb < BW * BH; kb += FT) {
             const int bj = kb / BW, bi = kb - bj * BW;
@@ -724,8 +735,11 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
                 if ((t + 1) * NW <= hq || warp + t * NW < hq)
                     if (!CHECK || inside(r0 + t * NW, c)) relax(o0 + t * NW * PW);
             }
-            if (tid < hq * q) {  // the last q cells of each row (hq * q <= FT)
-                const int rr = tid / q, cc = FW / 2 + (tid - rr * q);
+            // the last q cells of each row (hq * q <= FT), first to the
+            // warps with one chunk fewer (from warp hq % NW on)
+            const int k = (tid + FT - 32 * (hq % NW)) % FT;
+            if (k < hq * q) {
+                const int rr = k / q, cc = FW / 2 + (k - rr * q);
                 const int cq = XO - q + 2 * cc + ((par0 - 2 * q + rr + color) & 1);
                 const int r = HA - q + rr;
                 if (!CHECK || inside(r, cq)) relax(r * PW + cq);
