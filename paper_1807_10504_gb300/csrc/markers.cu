@@ -898,7 +898,8 @@ __device__ __forceinline__ double rail_line_area(const CellLine *L, const RailCu
 // sum and total.  Convex, well-conditioned strips: P is the cell square cut by the slab's normal
 // edges that cross it (area a0), S_o = area(P on the inner side of offset line
 // o) for o = 0..5 (a0 or 0 when the FP32 test finds the line clear of the
-// cell, else rail_line_area in FP64), and strip k has area S_k - S_k+1.  Other
+// cell, else rail_line_area in FP64, the cut lines in ascending o), and strip
+// k has area S_k - S_k+1.  Other
 // segments (folded strips, lines within 0.001 rad of a grid axis): each
 // quadrilateral is clipped against the cell (Sutherland-Hodgman).
 __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const double *__restrict__ sl,
@@ -940,18 +941,24 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
     RailCut rc;
     rail_cut(L, Ld[40], rc);
     const double a0 = (side[0] == 0 || side[1] == 0) ? rail_area(L, rc) : 1.0;
+    // lines clear of the cell first; then the cut ones, lowest first: step
+    // k of the loop takes the k-th cut line of every lane's pair, so the
+    // FP64 area runs on converged warps whichever lines the pairs cut
     double S[6];
+    unsigned cut = 0;
 #pragma unroll
     for (int o = 0; o < 6; o++) {
-        const int q = 2 + o;
-        if (side[q] > 0) {
-            S[o] = a0;
-        } else if (side[q] < 0) {
-            S[o] = 0.0;
-        } else {
-            const CellLine O = cell_line(Ld + 5 * q, di, dj, true);
-            S[o] = rail_line_area(L, rc, O, Ld[41 + 2 * o], Ld[42 + 2 * o]);
-        }
+        S[o] = side[2 + o] > 0 ? a0 : 0.0;
+        if (side[2 + o] == 0) cut |= 1u << o;
+    }
+    while (cut) {
+        const int o = __ffs(cut) - 1;
+        cut &= cut - 1;
+        const CellLine O = cell_line(Ld + 5 * (2 + o), di, dj, true);
+        const double v = rail_line_area(L, rc, O, Ld[41 + 2 * o], Ld[42 + 2 * o]);
+#pragma unroll
+        for (int r = 0; r < 6; r++)
+            if (r == o) S[r] = v;
     }
 #pragma unroll
     for (int k = 0; k < 5; k++) {
@@ -1006,9 +1013,13 @@ k_band_sum(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
 // linear in the segment parameter between its two markers.  One thread per
 // face: the block's 128 faces are tested for dH != 0, the faces with work
 // are packed into a list (so the FP64 part runs on full warps), and each of
-// those screens the block's candidates (staged in shared memory in FP32)
-// before evaluating the survivors exactly in FP64, in ascending id.
+// those screens the block's candidates (staged in shared memory in FP32),
+// lists the survivors in ascending id and then evaluates them exactly in
+// FP64 in that order: step k of the evaluation takes the k-th survivor of
+// every face at once, so the FP64 instructions run on converged warps (a
+// face with more than kNear survivors evaluates them in a pass of its own).
 constexpr int kIrrT = 2 * kBT;  // one thread per face of the block
+constexpr int kNear = 8;        // survivors listed per face
 __global__ void __launch_bounds__(kIrrT)
 k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ bactive,
                const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ ids,
@@ -1023,6 +1034,7 @@ k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ 
     __shared__ float seg_il[kMaxCand]; // 1 / |direction|^2
     __shared__ uint8_t work[kIrrT];     // faces with dH != 0, packed
     __shared__ double wdH[kIrrT];
+    __shared__ uint16_t near_q[kNear][kIrrT];  // survivors of the FP32 screen, per face
     __shared__ int nwork;
     const int bi = blockIdx.x, bj = blockIdx.y;
     if (!bactive[bj * bnx + bi]) return;
@@ -1082,9 +1094,15 @@ k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ 
     float best32 = INFINITY;
     for (int q = 0; q < n; q++) best32 = fminf(best32, d2f(q));
     const float lim = best32 + 0.01f;
+    static_assert(kMaxCand <= 65536, "candidate index in 16 bits");
+    int cnt = 0;
+    for (int q = 0; q < n; q++)
+        if (!(d2f(q) > lim)) {
+            if (cnt < kNear) near_q[cnt][threadIdx.x] = (uint16_t)q;
+            cnt++;
+        }
     double best = INFINITY, fb = 0.0;
-    for (int q = 0; q < n; q++) {
-        if (d2f(q) > lim) continue;
+    auto eval = [&](int q) {
         const int m = (int)cand[q], nm = next[m];
         const double ax = gx[m], ay = gy[m];
         const double ex = gx[nm] - ax, ey = gy[nm] - ay;
@@ -1094,6 +1112,12 @@ k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ 
         const double dx = ax + t * ex - qx, dy = ay + t * ey - qy;
         const double d2 = dx * dx + dy * dy;
         if (d2 < best) { best = d2; fb = (1.0 - t) * fmag[m] + t * fmag[nm]; }
+    };
+    if (cnt <= kNear) {
+        for (int k = 0; k < cnt; k++) eval(near_q[k][threadIdx.x]);
+    } else {
+        for (int q = 0; q < n; q++)
+            if (!(d2f(q) > lim)) eval(q);
     }
     const double F = fb * dH * ih;
     if (dir == 0) Fx[(long)j * (nx + 1) + i] = F;
