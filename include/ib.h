@@ -321,7 +321,10 @@ ib_status ib_attach_cnn(ib_ctx *ctx, ib_cnn *net);
  * this process so far.  ib_profile_begin(kind) starts CUDA-event timing, on
  * the launching stream, of every launch of one kernel class (0: fine-level
  * FP64 smoother launch (one sweep, or two fused in V(2,2)), 1: fine-level
- * FP32 smoother launch, 2: fine-level FP64 residual norm); ib_profile_end synchronises on the recorded events and
+ * FP32 smoother launch, 2: fine-level FP64 residual norm, 3: the fine-level
+ * FP32 prolongation + post-smoothing launch that also adds the cycle's
+ * result to the FP64 iterate (defect correction), alone);
+ * ib_profile_end synchronises on the recorded events and
  * returns their summed duration (ms) and count.  Timing is process-wide and
  * not thread-safe; at most 16384 launches are recorded.                    */
 unsigned long long ib_launch_count(void);

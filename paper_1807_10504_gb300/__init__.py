@@ -540,7 +540,7 @@ def debug_stall_staging(enable: bool) -> None:
 
 
 # -------------------------------------------------------------- measurement
-PROF_SWEEP64, PROF_SWEEP32, PROF_RESNORM = 0, 1, 2
+PROF_SWEEP64, PROF_SWEEP32, PROF_RESNORM, PROF_PROLONG32 = 0, 1, 2, 3
 
 
 def launch_count() -> int:

@@ -927,7 +927,7 @@ ib_status ib_debug_stall_staging(int enable)
 
 ib_status ib_profile_begin(int kind)
 {
-    if (kind < 0 || kind > 2) return IB_EINVAL;
+    if (kind < 0 || kind > 3) return IB_EINVAL;
     return prof_begin(kind) ? IB_OK : IB_ECUDA;
 }
 

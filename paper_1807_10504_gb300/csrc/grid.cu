@@ -94,6 +94,11 @@ __global__ void k_correct(int nx, int ny, double ih, double dt,
 // below its cell (and the wall face on the far side for the last column /
 // row) from differences of those fluxes, in the order of the per-face
 // formula, so each face gets the same value as if it formed them itself.
+// The advective fluxes are kept without their power-of-two factors (the
+// 1/2 of each face average, the 1/4 of the node density): 4 rho a^2 per
+// cell, 16 rho_n a_v a_u per node, the factors folded into 1/h of the
+// difference.  Scaling by a power of two is exact, so every rounding is as
+// in the per-face formula (fewer FP64 multiplications, the same values).
 constexpr int PX = 32, PY = 8;
 __global__ void __launch_bounds__(PX * PY)
 k_predictor(int nx, int ny, double ih, double ih2, double dt,
@@ -140,7 +145,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         const double *r0 = &sr[r][c], *r1 = &sr[r + 1][c];  // rows J-1, J; columns I-1, I
         const double *m0 = &sm[r][c], *m1 = &sm[r + 1][c];
         const bool wx = I == 0 || I == nx, wy = J == 0 || J == ny;
-        nr[r][c] = 0.25 * (r0[0] + r0[1] + r1[0] + r1[1]);
+        nr[r][c] = r0[0] + r0[1] + r1[0] + r1[1];  // 4 rho_n
         if (!wx && !wy) nm[r][c] = 0.25 * (m0[0] + m0[1] + m1[0] + m1[1]);
         else if (wy && !wx) nm[r][c] = J == 0 ? 0.5 * (m1[0] + m1[1]) : 0.5 * (m0[0] + m0[1]);
         else if (wx && !wy) nm[r][c] = I == 0 ? 0.5 * (m0[1] + m1[1]) : 0.5 * (m0[0] + m1[0]);
@@ -150,15 +155,15 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
     // cell fluxes: x-momentum of cell (i0-1+c, j0+r), window (r+1, c)
     for (int k = t; k < PY * (PX + 1); k += PX * PY) {
         const int r = k / (PX + 1), c = k - r * (PX + 1);
-        const double a = 0.5 * (su[r + 1][c + 1] + su[r + 1][c]);
-        fx[r][c] = sr[r + 1][c] * a * a;
+        const double a = su[r + 1][c + 1] + su[r + 1][c];  // 2 a
+        fx[r][c] = sr[r + 1][c] * a * a;                   // 4 rho a^2
         vx[r][c] = sm[r + 1][c] * (su[r + 1][c + 1] - su[r + 1][c]);
     }
     // y-momentum of cell (i0+c, j0-1+r), window (r, c+1)
     for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
         const int r = k / PX, c = k - r * PX;
-        const double a = 0.5 * (sv[r + 1][c + 1] + sv[r][c + 1]);
-        fy[r][c] = sr[r][c + 1] * a * a;
+        const double a = sv[r + 1][c + 1] + sv[r][c + 1];  // 2 a
+        fy[r][c] = sr[r][c + 1] * a * a;                   // 4 rho a^2
         vy[r][c] = sm[r][c + 1] * (sv[r + 1][c + 1] - sv[r][c + 1]);
     }
     // node fluxes of the x-momentum at node (I, J) = (i0+c, j0+r): between
@@ -167,8 +172,8 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         const int r = k / PX, c = k - r * PX, I = i0 + c, J = j0 + r;
         if (I > nx || J > ny) continue;
         const double ub = su[r][c + 1], ut = su[r + 1][c + 1];
-        gxn[r][c] = (J > 0 && J < ny)
-                        ? nr[r][c] * (0.5 * (sv[r + 1][c] + sv[r + 1][c + 1])) * (0.5 * (ub + ut))
+        gxn[r][c] = (J > 0 && J < ny)  // 16 rho_n a_v a_u
+                        ? nr[r][c] * (sv[r + 1][c] + sv[r + 1][c + 1]) * (ub + ut)
                         : 0.0;
         const double uT = J < ny ? ut : -ub, uB = J > 0 ? ub : -ut;
         wxn[r][c] = nm[r][c] * (uT - uB);
@@ -179,8 +184,8 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
         if (I > nx || J > ny) continue;
         const double vl = sv[r + 1][c], vr = sv[r + 1][c + 1];
-        gyn[r][c] = (I > 0 && I < nx)
-                        ? nr[r][c] * (0.5 * (su[r][c + 1] + su[r + 1][c + 1])) * (0.5 * (vl + vr))
+        gyn[r][c] = (I > 0 && I < nx)  // 16 rho_n a_u a_v
+                        ? nr[r][c] * (su[r][c + 1] + su[r + 1][c + 1]) * (vl + vr)
                         : 0.0;
         const double vR = I < nx ? vr : -vl, vL = I > 0 ? vl : -vr;
         wyn[r][c] = nm[r][c] * (vR - vL);
@@ -189,6 +194,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
     const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
     if (i >= nx || j >= ny) return;
     const int R = ty + 1, C = tx + 1;  // window index of cell (i, j)
+    const double ih4 = 0.25 * ih, ih16 = 0.0625 * ih;  // the folded factors
     // x-face (i, j), left of cell (i, j)
     {
         const long k = (long)j * nxf + i;
@@ -196,7 +202,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
             us[k] = 0.0; au[k] = 0.0;
         } else {
             const double uc = su[R][C];
-            const double adv = (fx[ty][tx + 1] - fx[ty][tx]) * ih + (gxn[ty + 1][tx] - gxn[ty][tx]) * ih;
+            const double adv = (fx[ty][tx + 1] - fx[ty][tx]) * ih4 + (gxn[ty + 1][tx] - gxn[ty][tx]) * ih16;
             const double vis = (vx[ty][tx + 1] - vx[ty][tx] + wxn[ty + 1][tx] - wxn[ty][tx]) * ih2;
             // 1 / rho_face: the face coefficient beta when given (the same
             // reciprocal of the same rho), else formed here
@@ -214,7 +220,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
             vs[k] = 0.0; av[k] = 0.0;
         } else {
             const double vc = sv[R][C];
-            const double adv = (fy[ty + 1][tx] - fy[ty][tx]) * ih + (gyn[ty][tx + 1] - gyn[ty][tx]) * ih;
+            const double adv = (fy[ty + 1][tx] - fy[ty][tx]) * ih4 + (gyn[ty][tx + 1] - gyn[ty][tx]) * ih16;
             const double vis = (vy[ty + 1][tx] - vy[ty][tx] + wyn[ty][tx + 1] - wyn[ty][tx]) * ih2;
             const double irf = by ? by[k] : recip_nr(0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;

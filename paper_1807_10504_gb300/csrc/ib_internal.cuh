@@ -62,7 +62,7 @@ const char *fault_message(int code);
 cudaError_t set_stall_staging(int on);
 
 // Optional CUDA-event timing of one kernel class, on the stream it runs on.
-enum ProfKind { kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2 };
+enum ProfKind { kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2, kProfProlong32 = 3 };
 bool prof_on(int kind);
 void prof_mark(cudaStream_t s, bool start);
 bool prof_begin(int kind);

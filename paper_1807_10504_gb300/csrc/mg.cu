@@ -1905,7 +1905,8 @@ bool vcycle(MG &mg, int nu1, int nu2, cudaStream_t s, double *add64 = nullptr)
         Level &v = mg.lv[l];
         LevelT<T> &a = lvT(l);
         if (fused) {
-            const bool pr = l == 0 && prof_on(f32 ? kProfSweep32 : kProfSweep64);
+            const bool pr = l == 0 && (prof_on(f32 ? kProfSweep32 : kProfSweep64) ||
+                                       (f32 && add64 && prof_on(kProfProlong32)));
             if (pr) prof_mark(s, true);
             if constexpr (f32) {
                 if (l == 0 && add64) {
