@@ -147,26 +147,13 @@ def peaks():
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def kernel_source(rel, name):
-    """The text of kernel `name` in source file `rel` (its signature line to
-    the first closing brace in column 0) and the file's compile-time integer
-    constants that the kernel names (they set its tiles)."""
-    import re
-    with open(os.path.join(ROOT, rel)) as f:
-        lines = f.read().split("\n")
-    start = next(i for i, ln in enumerate(lines)
-                 if ln.startswith(name + "(") or ("__global__" in ln and " " + name + "(" in ln))
-    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
-    body = "\n".join(lines[start:end + 1])
-    words = set(re.findall(r"[A-Za-z_]\w*", body))
-    consts = [ln for ln in lines if ln.startswith("constexpr int")
-              and set(re.findall(r"([A-Za-z_]\w*)\s*=", ln)) & words]
-    return "\n".join(consts) + "\n" + body
-
-
 def source_sha(rel, name):
+    """Hash of the source file that holds kernel `name`: a recorded profile
+    figure stays valid only while nothing in that file (the kernel, the
+    device functions it inlines, its tile constants) has changed."""
     import hashlib
-    return hashlib.sha256(kernel_source(rel, name).encode()).hexdigest()
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
 
 
 def traffic_per_launch(kernel, cells):
