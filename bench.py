@@ -580,6 +580,21 @@ def run_ours(args):
     barrier()
     sweep_ms, sweep_n = ib.profile_end()
 
+    # where the step's time goes: the same K steps three more times, CUDA
+    # events on the context stream around one part of every step (the
+    # step's graphs replay as in the timed steps)
+    phases = {}
+    for key, kind in (("before_solve", ib.PROF_PRE), ("solve", ib.PROF_SOLVE),
+                      ("after_solve", ib.PROF_POST)):
+        ib.profile_begin(kind)
+        for k in range(args.steps):
+            flush.zero_()
+            ctx.ns_step(dt, 1, args.warm)
+        barrier()
+        ms, n = ib.profile_end()
+        phases[key] = ms / max(n, 1)
+    phases["unit"] = "ms per step"
+
     pk, pk_kind = peaks()
     fp64_peak = ib.probe_fp64()  # TFLOP/s, FMA chains on every SM
 
@@ -763,6 +778,7 @@ def run_ours(args):
                      "back_to_back_frac": B * cells / (us_b2b * 1e-6) / 1e9 / pk["hbm_gbs"],
                      "back_to_back_timing": "50 back-to-back launches on the step's "
                                             "fine-level data (largely L2-resident at 1024^2)"},
+        "step_phases": phases,
         "roofline_fp64_sweep": roof64,
         "band_strip_areas": band,
         "fp64_marker_side": marker_side,

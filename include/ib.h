@@ -323,7 +323,11 @@ ib_status ib_attach_cnn(ib_ctx *ctx, ib_cnn *net);
  * FP64 smoother launch (one sweep, or two fused in V(2,2)), 1: fine-level
  * FP32 smoother launch, 2: fine-level FP64 residual norm, 3: the fine-level
  * FP32 prolongation + post-smoothing launch that also adds the cycle's
- * result to the FP64 iterate (defect correction), alone);
+ * result to the FP64 iterate (defect correction), alone), or of one part of
+ * every ns_step on the context stream (4: the launches before the pressure
+ * solve, side streams joined; 5: the warm start and the pressure solve; 6:
+ * the launches after it).  Kinds 0-3 launch one kernel at a time (no CUDA
+ * graph replay while they are active); kinds 4-6 leave the graphs on.
  * ib_profile_end synchronises on the recorded events and
  * returns their summed duration (ms) and count.  Timing is process-wide and
  * not thread-safe; at most 16384 launches are recorded.                    */

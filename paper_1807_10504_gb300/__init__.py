@@ -541,6 +541,7 @@ def debug_stall_staging(enable: bool) -> None:
 
 # -------------------------------------------------------------- measurement
 PROF_SWEEP64, PROF_SWEEP32, PROF_RESNORM, PROF_PROLONG32 = 0, 1, 2, 3
+PROF_PRE, PROF_SOLVE, PROF_POST = 4, 5, 6  # the parts of ns_step
 
 
 def launch_count() -> int:

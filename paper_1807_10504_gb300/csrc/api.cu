@@ -840,9 +840,13 @@ ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
     // or the network, which synchronise with the host)
     const bool rec = c->have_prev && !g.indicator && warm != 2;
     const int key = (reloc ? 1 : 0) | (mass ? 2 : 0) | (warm == 0 ? 4 : 0);
+    const bool t_pre = prof_on(kProfPre), t_solve = prof_on(kProfSolve), t_post = prof_on(kProfPost);
+    if (t_pre) prof_mark(c->s, true);
     ib_status st = rec ? run_recorded(c, dt, key, [&] { return step_pre(c, dt, reloc, mass, warm); })
                        : step_pre(c, dt, reloc, mass, warm);
+    if (t_pre) prof_mark(c->s, false);
     if (st != IB_OK) return st;
+    if (t_solve) prof_mark(c->s, true);
     if (warm == 2) {
         cudaError_t ce = cnn_run(c->cnn, 1, g.nx, g.h, c->b, c->rho, c->p, c->s);
         if (ce != cudaSuccess) return cuda_check(c, ce, "network warm start");
@@ -858,9 +862,12 @@ ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
     }
     st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
                 &c->last_cycles, &c->last_relres, c->s, c->err);
+    if (t_solve) prof_mark(c->s, false);
     if (st != IB_OK && st != IB_ENOTCONV) return st;
+    if (t_post) prof_mark(c->s, true);
     const ib_status sp = rec ? run_recorded(c, dt, 64, [&] { return step_post(c, dt); })
                              : step_post(c, dt);
+    if (t_post) prof_mark(c->s, false);
     if (sp != IB_OK) return sp;
     c->have_prev = 1;
     c->step++;
@@ -927,7 +934,7 @@ ib_status ib_debug_stall_staging(int enable)
 
 ib_status ib_profile_begin(int kind)
 {
-    if (kind < 0 || kind > 3) return IB_EINVAL;
+    if (kind < 0 || kind > 6) return IB_EINVAL;
     return prof_begin(kind) ? IB_OK : IB_ECUDA;
 }
 

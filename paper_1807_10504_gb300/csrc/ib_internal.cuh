@@ -62,7 +62,13 @@ const char *fault_message(int code);
 cudaError_t set_stall_staging(int on);
 
 // Optional CUDA-event timing of one kernel class, on the stream it runs on.
-enum ProfKind { kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2, kProfProlong32 = 3 };
+// Per-launch kinds (0-3) time single kernels (one launch per kernel: no
+// graph replay meanwhile); phase kinds (4-6) time the parts of ns_step on the
+// context stream around their graphs.
+enum ProfKind {
+    kProfSweep64 = 0, kProfSweep32 = 1, kProfResnorm = 2, kProfProlong32 = 3,
+    kProfPre = 4, kProfSolve = 5, kProfPost = 6
+};
 bool prof_on(int kind);
 void prof_mark(cudaStream_t s, bool start);
 bool prof_begin(int kind);

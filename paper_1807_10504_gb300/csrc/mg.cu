@@ -1711,14 +1711,20 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
           cudaGraphConditionalHandle hnd, int check, int inc)
 {
     pdl_enter();
+    // an equal contiguous share of the cells per block (the grid is one
+    // wave of resident blocks), consecutive cells on consecutive threads
+    const long n = (long)nx * ny;
+    const long per = (n + gridDim.x - 1) / gridDim.x;
+    const long ke = min(n, (long)blockIdx.x * per + per);
+    long k = (long)blockIdx.x * per + threadIdx.x;
+    int j = (int)(k / nx), i = (int)(k - (long)j * nx);
     double s = 0.0;
-    for (int j = blockIdx.x; j < ny; j += gridDim.x)
-        for (int i = threadIdx.x; i < nx; i += kRedT) {
-            const long k = (long)j * nx + i;
-            const double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
-            s += r * r;
-            if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
-        }
+    for (; k < ke; k += kRedT) {
+        const double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
+        s += r * r;
+        if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
+        for (i += kRedT; i >= nx; i -= nx) j++;
+    }
     if (block_fold_and_finish<NoOp>(s, part, count, res + 2) && check)
         solve_check(ctl, res, hnd, check == 1, inc);
 }
@@ -1972,7 +1978,7 @@ cudaError_t set_stall_staging(int on)
 }
 unsigned long long launch_count() { return g_launches.load(); }
 bool prof_on(int kind) { return g_prof.kind == kind && g_prof.n < kProfMax; }
-static bool prof_active() { return g_prof.kind >= 0; }
+static bool prof_active() { return g_prof.kind >= 0 && g_prof.kind < kProfPre; }
 bool profiling_active() { return prof_active(); }
 
 void raise_smem_limit(const void *kernel, int bytes)
@@ -2095,6 +2101,26 @@ static bool encode_level_maps(Level &v)
     return true;
 }
 
+// Blocks of the reduction kernels (residual norm, sums): as many as are
+// resident at once on the device (one wave: each block's share of the cells
+// is then done in one go), at most 8 per SM of 152.
+static int resident_red_blocks()
+{
+    static int nb = 0;
+    if (nb == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_resnorm, kRedT, 0) != cudaSuccess ||
+            sms <= 0 || per <= 0) {
+            cudaGetLastError();
+            return 8 * 152;
+        }
+        nb = std::min(per * sms, 8 * 152);
+    }
+    return nb;
+}
+
 size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
 {
     int nxs[16], nys[16], L = 0;
@@ -2104,7 +2130,7 @@ size_t mg_layout(MG &mg, int nx, int ny, double h, char *base)
         nxs[L] = nx; nys[L] = ny; L++;
     }
     const long nc = (long)nxs[L - 1] * nys[L - 1];
-    mg.red_blocks = 8 * 152;  // residual-norm blocks: several per SM to hide FP64 and load latency
+    mg.red_blocks = resident_red_blocks();
     char *q = base;
     size_t off = 0;
     auto take = [&](size_t b) -> void * {
