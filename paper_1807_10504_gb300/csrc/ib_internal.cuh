@@ -22,14 +22,34 @@ constexpr int kMaxCross = 2048;      // interface crossings per grid row
 
 inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
 
-// 1/x for positive x within the FP32 normal range: the FP32 reciprocal
-// (__frcp_rn) refined by two Newton-Raphson steps r <- r + r (1 - x r) in
-// FP64; each step squares the relative error (2^-24 -> 2^-48 -> below the
-// FP64 rounding), so the result is within one unit in the last place of
-// 1.0 / x at a fraction of the FP64 division's cost on this part.
+// Conversions between double and float on integer instructions, for values
+// in the FP32 normal range: this part runs FP64 conversions on its reduced
+// FP64 pipe, at the rate of its FP64 arithmetic.  d2f_trunc keeps the top 23
+// mantissa bits (truncation, relative error below 2^-23); f2d_exact is exact.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = ((hi >> 20) & 0x7ffu) - 896u;  // FP64 bias 1023 -> FP32 bias 127
+    return __uint_as_float((hi & 0x80000000u) | (e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = ((u >> 23) & 0xffu) + 896u, m = u & 0x7fffffu;
+    const unsigned hi = (u & 0x80000000u) | (e << 20) | (m >> 3);
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | ((unsigned long long)(m & 7u) << 29)));
+}
+
+// 1/x for x of either sign within the FP32 normal range (about 1e-37 < |x|
+// < 1e37): the FP32 reciprocal (__frcp_rn) of x's leading bits refined by two
+// Newton-Raphson steps r <- r + r (1 - x r) in FP64; each step squares the
+// relative error (2^-22 -> 2^-44 -> below the FP64 rounding), so the result
+// is within one unit in the last place of 1.0 / x at a fraction of the FP64
+// division's cost on this part, with no FP64 conversion.
 __device__ __forceinline__ double recip_nr(double x)
 {
-    double r = (double)__frcp_rn((float)x);
+    double r = f2d_exact(__frcp_rn(d2f_trunc(x)));
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
@@ -40,9 +60,13 @@ __device__ __forceinline__ double recip_nr(double x)
 // |x| lies well inside the FP32 normal range, the FP64 division elsewhere.
 __device__ __forceinline__ double recip_any(double x)
 {
-    const double a = fabs(x);
-    if (x == 0.0) return 0.0;
-    return (a > 1e-30 && a < 1e30) ? recip_nr(x) : 1.0 / x;
+    // the tests on |x|'s bit pattern (ordered like the value), in integer
+    // instructions
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    if (a == 0) return 0.0;
+    const unsigned long long lo = (unsigned long long)__double_as_longlong(1e-30),
+                             hi = (unsigned long long)__double_as_longlong(1e30);
+    return (a > lo && a < hi) ? recip_nr(x) : 1.0 / x;
 }
 
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (one

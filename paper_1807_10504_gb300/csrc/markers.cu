@@ -139,12 +139,20 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
         v[2 * o] = ax[o]; v[2 * o + 1] = ay[o];
         v[12 + 2 * o] = bx[o]; v[12 + 2 * o + 1] = by[o];
     }
+    // minima and maxima of the (finite) corners compared on their bit
+    // patterns, in integer instructions (ordered like the values)
+    auto kb = [](double d) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+    };
+    auto dmin = [&](double a, double b) { return kb(a) <= kb(b) ? a : b; };
+    auto dmax = [&](double a, double b) { return kb(a) >= kb(b) ? a : b; };
     float fx0 = INFINITY, fx1 = -INFINITY, fy0 = INFINITY, fy1 = -INFINITY;
     for (int k = 0; k < 5; k++) {
-        double x0 = fmin(fmin(ax[k], ax[k + 1]), fmin(bx[k], bx[k + 1]));
-        double x1 = fmax(fmax(ax[k], ax[k + 1]), fmax(bx[k], bx[k + 1]));
-        double y0 = fmin(fmin(ay[k], ay[k + 1]), fmin(by[k], by[k + 1]));
-        double y1 = fmax(fmax(ay[k], ay[k + 1]), fmax(by[k], by[k + 1]));
+        double x0 = dmin(dmin(ax[k], ax[k + 1]), dmin(bx[k], bx[k + 1]));
+        double x1 = dmax(dmax(ax[k], ax[k + 1]), dmax(bx[k], bx[k + 1]));
+        double y0 = dmin(dmin(ay[k], ay[k + 1]), dmin(by[k], by[k + 1]));
+        double y1 = dmax(dmax(ay[k], ay[k + 1]), dmax(by[k], by[k + 1]));
         float4 f = make_float4(__double2float_rd(x0) - 1e-3f, __double2float_ru(x1) + 1e-3f,
                                __double2float_rd(y0) - 1e-3f, __double2float_ru(y1) + 1e-3f);
         sb5[(long)m * 5 + k] = f;
@@ -186,7 +194,8 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
         for (int c = 0; c < 4; c++) {
             const int c1 = (c + 1) & 3, c2 = (c + 2) & 3;
             const double cr = (qx[c1] - qx[c]) * (qy[c2] - qy[c1]) - (qy[c1] - qy[c]) * (qx[c2] - qx[c1]);
-            cvx = cvx && cr > 1e-6;
+            // cr > 1e-6 on the bit patterns (a negative cr has a negative one)
+            cvx = cvx && __double_as_longlong(cr) > __double_as_longlong(1e-6);
         }
     }
     // The half-plane path also wants every line at least 0.001 rad away from
@@ -194,9 +203,12 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     // meets it at an ill-conditioned point, which the area formula would use
     // twice (once per boundary piece); quadrilateral clipping has no such
     // sensitivity and takes those segments.
+    const long long k3 = __double_as_longlong(1e-3);
     for (int q = 0; q < 8; q++) {
-        const double aa = fabs(L[q][0]), bb = fabs(L[q][1]);
-        cvx = cvx && (aa == 0.0 || aa >= 1e-3) && (bb == 0.0 || bb >= 1e-3);
+        // |a| == 0 or |a| >= 1e-3, likewise b, on the bit patterns of |a|, |b|
+        const long long aa = __double_as_longlong(L[q][0]) & 0x7fffffffffffffffLL,
+                        bb = __double_as_longlong(L[q][1]) & 0x7fffffffffffffffLL;
+        cvx = cvx && (aa == 0 || aa >= k3) && (bb == 0 || bb >= k3);
     }
     scvx[m] = cvx ? 1 : 0;
 }
