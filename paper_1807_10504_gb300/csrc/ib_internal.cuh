@@ -41,6 +41,33 @@ __device__ __forceinline__ double f2d_exact(float f)
     return __longlong_as_double((long long)(((unsigned long long)hi << 32) | ((unsigned long long)(m & 7u) << 29)));
 }
 
+// (float)x, round to nearest even, on integer instructions where x is zero
+// or within the FP32 normal range (the hardware conversion elsewhere: FP32
+// subnormals, overflow, infinities, NaN); the result is the conversion's.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e >= 897u && e <= 1150u) {
+        unsigned r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;  // the 29 dropped bits
+        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float((hi & 0x80000000u) | r);
+    }
+    if ((b & 0x7fffffffffffffffULL) == 0) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+}
+// (double)f, exact, on integer instructions for zero and FP32 normals (the
+// hardware conversion for subnormals, infinities and NaN).
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u) return f2d_exact(f);
+    if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+    return (double)f;
+}
+
 // 1/x for x of either sign within the FP32 normal range (about 1e-37 < |x|
 // < 1e37): the FP32 reciprocal (__frcp_rn) of x's leading bits refined by two
 // Newton-Raphson steps r <- r + r (1 - x r) in FP64; each step squares the

@@ -75,7 +75,7 @@ __global__ void k_geometry(int M, const double *__restrict__ X, const double *__
     {
         double a = (X[m] - x0) / h, b = (Y[m] - y0) / h;
         gx[m] = a; gy[m] = b;
-        gxf[m] = (float)a; gyf[m] = (float)b;
+        gxf[m] = d2f_rn(a); gyf[m] = d2f_rn(b);
     }
     int pm, nm;
     nbrs(m, drop_of, drop_start, &pm, &nm);
@@ -176,8 +176,8 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     for (int q = 0; q < 8; q++) {
         d[5 * q + 0] = L[q][0]; d[5 * q + 1] = L[q][1]; d[5 * q + 2] = L[q][2];
         d[5 * q + 3] = rcp(L[q][0]); d[5 * q + 4] = rcp(L[q][1]);
-        slf[(long)m * 8 + q] = make_float4((float)L[q][0], (float)L[q][1], (float)L[q][2],
-                                           (float)sqrt(L[q][0] * L[q][0] + L[q][1] * L[q][1]));
+        slf[(long)m * 8 + q] = make_float4(d2f_rn(L[q][0]), d2f_rn(L[q][1]), d2f_rn(L[q][2]),
+                                           d2f_rn(sqrt(L[q][0] * L[q][0] + L[q][1] * L[q][1])));
     }
     d[40] = rcp(L[0][0] * L[1][1] - L[0][1] * L[1][0]);
     for (int o = 0; o < 6; o++) {
@@ -1095,7 +1095,7 @@ k_spread_irrot(int nx, int ny, double ih, int bnx, const uint32_t *__restrict__ 
     // coordinates below 2^12 cells the FP32 squared distances carry an error
     // below 2e-3 (grid units), so the exact nearest segment is among those
     // within best + 0.01 of the FP32 minimum.
-    const float fqx = (float)qx, fqy = (float)qy;
+    const float fqx = d2f_rn(qx), fqy = d2f_rn(qy);
     auto d2f = [&](int q) {
         const float4 sg = seg[q];
         float t = ((fqx - sg.x) * sg.z + (fqy - sg.y) * sg.w) * seg_il[q];

@@ -508,7 +508,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         const int r = HA + k / FW, c = XO + (k - (k / FW) * FW);
         const int gi = gi0 + c, gj = gj0 + r;
         if (gi < nx && gj < ny) {
-            if (MODE == 2 && p64) p64[(long)gj * nx + gi] += (double)ps[r][c];
+            if (MODE == 2 && p64) p64[(long)gj * nx + gi] += f2d(ps[r][c]);
             else p[(long)gj * nx + gi] = ps[r][c];
         }
     }
@@ -793,7 +793,7 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
             if (whole || (gi < nx && gj < ny)) {
                 const float v = ps[(HA + trow + RS * j) * PW + XO + tcol];
                 const long g = g0 + (long)RS * j * nx;
-                if (MODE == 2 && p64) p64[g] = v64[MODE == 2 ? j : 0] + (double)v;
+                if (MODE == 2 && p64) p64[g] = v64[MODE == 2 ? j : 0] + f2d(v);
                 else p[g] = v;
             }
         }
@@ -1045,21 +1045,23 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
     };
     const double w = xface(i, j), e = xface(i + 1, j), s = yface(i, j), n = yface(i, j + 1);
     const long kx = (long)j * (nx + 1) + i, kc = (long)j * nx + i;
-    bx[kx] = w; bxf[kx] = (float)w;
-    by[kc] = s; byf[kc] = (float)s;
-    if (i == nx - 1) { bx[kx + 1] = e; bxf[kx + 1] = (float)e; }
-    if (j == ny - 1) { by[kc + nx] = n; byf[kc + nx] = (float)n; }
+    // FP32 copies by d2f_rn: (float) on integer instructions
+    const float wf = d2f_rn(w);
+    bx[kx] = w; bxf[kx] = wf;
+    by[kc] = s; byf[kc] = d2f_rn(s);
+    if (i == nx - 1) { bx[kx + 1] = e; bxf[kx + 1] = d2f_rn(e); }
+    if (j == ny - 1) { by[kc + nx] = n; byf[kc + nx] = d2f_rn(n); }
     const int xp = xface_pitch(nx);
     float *rowp = bxp + (long)j * xp;
-    rowp[i] = (float)w;
+    rowp[i] = wf;
     if (i == nx - 1) {
-        rowp[nx] = (float)e;
+        rowp[nx] = d2f_rn(e);
         for (int t = nx + 1; t < xp; t++) rowp[t] = 0.0f;  // padding
     }
     const double d = e + w + n + s;
     const double id = d > 0.0 ? recip_nr(d) : 0.0;
     invd[kc] = id;
-    invdf[kc] = (float)id;
+    invdf[kc] = d2f_rn(id);
     reinterpret_cast<double2 *>(w4)[2 * kc] = make_double2(w * id, e * id);
     reinterpret_cast<double2 *>(w4)[2 * kc + 1] = make_double2(s * id, n * id);
 }
@@ -1722,7 +1724,7 @@ k_resnorm(int nx, int ny, double ih2, const double *__restrict__ bx,
     for (; k < ke; k += kRedT) {
         const double r = b0[k] - flux_sum(nx, ny, i, j, bx, by, p) * ih2;
         s += r * r;
-        if (rf) { rf[k] = (float)r; ef[k] = 0.0f; }
+        if (rf) { rf[k] = d2f_rn(r); ef[k] = 0.0f; }
         for (i += kRedT; i >= nx; i -= nx) j++;
     }
     if (block_fold_and_finish<NoOp>(s, part, count, res + 2) && check)
@@ -1733,7 +1735,7 @@ __global__ void k_add_f32(long n, const float *__restrict__ e, double *__restric
 {
     pdl_enter();
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) p[k] += (double)e[k];
+    if (k < n) p[k] += f2d(e[k]);
 }
 
 __global__ void k_finalize(long n, const double *__restrict__ e0, const double *__restrict__ sum,
