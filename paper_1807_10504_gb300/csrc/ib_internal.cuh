@@ -309,6 +309,7 @@ struct Markers {
     double2 *dyr = nullptr;                // per-drop [min Y, max Y]
     unsigned long long *ykey = nullptr;    // order-preserving integer key of each Y
     ulonglong2 *dyk = nullptr;             // keys of the per-drop Y range
+    unsigned long long *colkey = nullptr;  // order-preserving key of each column's centre x
     double *sv = nullptr;                  // per segment: 12 strip corner points (24 doubles)
     double *sl = nullptr;                  // per segment: 8 half-planes (a, b, c, 1/a, 1/b) + determinant reciprocals, FP64
     float4 *slf = nullptr;                 // the same in FP32 (nx, ny, c, |n|)

@@ -465,11 +465,22 @@ __global__ void k_spread_conv(int kernel, int nx, int ny, double h, double x0, d
 }
 
 // ------------------------------------------------------------ inside / outside
+// Order-preserving key of the centre x of every column, x0 + (i + 0.5) h,
+// formed once per context (the grid does not move; the same FP64 operations
+// as the crossing test would use per cell).
+__global__ void k_colkeys(int nx, double h, double x0, unsigned long long *__restrict__ ck)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nx) ck[i] = okey(x0 + ((double)i + 0.5) * h);
+}
+
 // One CTA per row: crossings of the row's centre line with every segment,
-// sorted, then a crossing count per cell centre.  Writes H = chi.
+// sorted, then a crossing count per cell centre (the centres' keys from
+// k_colkeys).  Writes H = chi.
 __global__ void __launch_bounds__(kT)
 k_rows_inside(int ndrops, int nx, double h, double x0, double y0, const double *__restrict__ X,
               const double *__restrict__ Y, const unsigned long long *__restrict__ ykey,
+              const unsigned long long *__restrict__ colkey,
               const int32_t *__restrict__ next, const int32_t *__restrict__ drop_start,
               const ulonglong2 *__restrict__ dyk, double *__restrict__ H,
               uint32_t *__restrict__ flags)
@@ -510,13 +521,13 @@ k_rows_inside(int ndrops, int nx, double h, double x0, double y0, const double *
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nx; i += kT) {
-        const unsigned long long kx = okey(x0 + ((double)i + 0.5) * h);
+        const unsigned long long kx = colkey[i];  // okey(x0 + (i + 0.5) h)
         int lo = 0, hi = n;  // first index with srt > px
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
             if (srt[mid] > kx) hi = mid; else lo = mid + 1;
         }
-        H[(long)j * nx + i] = (double)((n - lo) & 1);
+        H[(long)j * nx + i] = ((n - lo) & 1) ? 1.0 : 0.0;
     }
 }
 
@@ -1507,7 +1518,8 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
                    al((size_t)M * 24 * 8) + al((size_t)M * kSegLine * 8) + al((size_t)M * 8 * 16) + al((size_t)M * 5 * 16) + al(M * 8) + al(M) + al(M * 8) +
                    al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
-                   al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64);
+                   al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64) +
+                   al((size_t)nx * 8);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
     if (e != cudaSuccess) { mk.mem = nullptr; return e; }
     char *q = (char *)mk.mem;
@@ -1545,6 +1557,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.scan_part = (uint32_t *)take(nparts * 4);
     mk.bcount = (uint32_t *)take(nb * 4); mk.bactive = (uint32_t *)take(nb * 4);
     mk.flags = (uint32_t *)take(64);
+    mk.colkey = (unsigned long long *)take((size_t)nx * 8);
     std::vector<int32_t> dof(M), nxt(M);
     for (int d = 0; d < ndrops; d++)
         for (int m = drop_start_host[d]; m < drop_start_host[d + 1]; m++) {
@@ -1552,6 +1565,12 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
             nxt[m] = (m + 1 == drop_start_host[d + 1]) ? drop_start_host[d] : m + 1;
         }
     e = cudaMemset(mk.mem, 0, bytes);
+    if (e == cudaSuccess) {
+        // the column keys of the scanline fill (the grid does not move); the
+        // copies below, on the same legacy stream, follow the kernel
+        k_colkeys<<<cdiv(nx, kT), kT>>>(nx, h, x0, mk.colkey);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpy(mk.drop_start, drop_start_host, (ndrops + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(mk.drop_of, dof.data(), M * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(mk.next, nxt.data(), M * 4, cudaMemcpyHostToDevice);
@@ -1668,7 +1687,7 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s, cudaStream_t
     }
     note_launch();
     k_rows_inside<<<mk.ny, kT, 0, sr>>>(mk.ndrops, mk.nx, mk.h, mk.x0, mk.y0, mk.X, mk.Y, mk.ykey,
-                                        mk.next, mk.drop_start, mk.dyk, H, mk.flags);
+                                        mk.colkey, mk.next, mk.drop_start, mk.dyk, H, mk.flags);
     if (side) cudaEventRecord(ev_join, side);
     dim3 g(mk.bnx, mk.bny);
     cudaMemsetAsync(mk.npairs, 0, sizeof(uint32_t), s);
