@@ -320,7 +320,8 @@ struct Markers {
     double *rwts = nullptr;                // relocation: per marker, its four basis weights
     uint32_t pair_cap = 0;                 // capacity of the band (cell, segment) pair list
     uint32_t *npairs = nullptr;            // pairs claimed by the last band pass
-    uint32_t *pseg = nullptr, *pcell = nullptr;  // pair list: segment, cell index
+    uint32_t *pseg = nullptr, *pcell = nullptr;  // pair list: segment (top bit: listed for clipping), cell index
+    uint32_t *clip_list = nullptr;         // pairs of non-convex strips (the second word of npairs counts them)
     double *pacc = nullptr, *pcov = nullptr;     // per pair: sum A_k H_k, sum A_k
     uint2 *crange = nullptr;               // per cell of an active block: (first pair, count)
     float4 *sb5 = nullptr;                 // per segment: FP32 outward box of each of 5 strips

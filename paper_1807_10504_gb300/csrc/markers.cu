@@ -660,6 +660,11 @@ __device__ __forceinline__ int cell_side(float4 l, float fi, float fj)
 // varies from run to run, but each cell's pairs and their order do not: H is
 // deterministic.
 constexpr int kPairT = 256, kPairSub = kPairT / kBT;  // 4 threads per cell
+// Pairs of non-convex strips (quadrilateral clipping, long serial FP64 work)
+// are listed for the first kClipBlocks blocks of k_band_area, 32 pairs a
+// block, and marked in the segment id's top bit.
+constexpr int kClipBlocks = 32, kClipCap = kClipBlocks * 32;
+constexpr uint32_t kClipFlag = 0x80000000u;
 constexpr int kStage = 256;  // candidates whose slab tests are staged in shared memory
 __global__ void __launch_bounds__(kPairT)
 k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
@@ -667,6 +672,7 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
              const float4 *__restrict__ slf, const uint8_t *__restrict__ scvx,
              const float4 *__restrict__ sbox, uint32_t cap, uint32_t *__restrict__ npairs,
              uint32_t *__restrict__ pseg, uint32_t *__restrict__ pcell, uint2 *__restrict__ crange,
+             uint32_t *__restrict__ clip_list,
              uint32_t *__restrict__ flags)
 {
     __shared__ uint32_t cand[kMaxCand], tmp[kMaxCand];
@@ -747,7 +753,18 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
     }
     uint32_t o = base + excl;
     for (int q = q0; q < q1; q++)
-        if (meets(q)) { pseg[o] = cand[q]; pcell[o] = (uint32_t)cidx; o++; }
+        if (meets(q)) {
+            uint32_t seg = cand[q];
+            // a pair of a non-convex strip goes to the clip list of
+            // k_band_area (while it has room), marked in the id's top bit
+            if (!(q < kStage ? s_cvx[q] : scvx[seg])) {
+                const uint32_t at = atomicAdd(npairs + 1, 1u);
+                if (at < kClipCap) { clip_list[at] = o; seg |= kClipFlag; }
+            }
+            pseg[o] = seg;
+            pcell[o] = (uint32_t)cidx;
+            o++;
+        }
 }
 
 // A bounding line of a strip in the cell's local frame (the cell is the unit
@@ -991,10 +1008,15 @@ __device__ __forceinline__ void pair_area(uint32_t m, int ci, int cj, const doub
     }
 }
 
-// One pair per thread.
+// The first kClipBlocks blocks take the listed pairs of non-convex strips,
+// a group of 8 lanes per pair, lane k < 5 clipping strip k's quadrilateral;
+// lane 0 sums the strips in order, as one thread would.  Being dispatched
+// first, their long FP64 chains overlap the rest.  The other blocks take one
+// pair per thread (flat over the list), skipping the listed ones.
 __global__ void __launch_bounds__(256)
 k_band_area(int nx, const uint32_t *__restrict__ npairs, uint32_t cap,
             const uint32_t *__restrict__ pseg, const uint32_t *__restrict__ pcell,
+            const uint32_t *__restrict__ clip_list,
             const double *__restrict__ sl, const float4 *__restrict__ slf,
             const uint8_t *__restrict__ scvx, const double *__restrict__ sv,
             const float4 *__restrict__ sb5, double *__restrict__ pacc, double *__restrict__ pcov)
@@ -1002,11 +1024,52 @@ k_band_area(int nx, const uint32_t *__restrict__ npairs, uint32_t cap,
     const uint32_t total = min(*npairs, cap);
     double Hk[5];
     for (int k = 0; k < 5; k++) Hk[k] = strip_value(k);
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+    if (blockIdx.x < kClipBlocks) {
+        const uint32_t nc = min(npairs[1], (uint32_t)kClipCap);
+        const uint32_t idx = blockIdx.x * 32 + threadIdx.x / 8;
+        const int k = threadIdx.x % 8;
+        // every lane reaches the shuffles below; a group past the list's end
+        // (the same for its 8 lanes) only does no work
+        const bool live = idx < nc;
+        const uint32_t p = live ? clip_list[idx] : 0u;
+        const uint32_t m = live ? (pseg[p] & ~kClipFlag) : 0u, cell = live ? pcell[p] : 0u;
+        const int cj = (int)(cell / (uint32_t)nx), ci = (int)(cell - (uint32_t)cj * (uint32_t)nx);
+        const float gi = (float)ci, gj = (float)cj;
+        const double di = (double)ci, dj = (double)cj;
+        double A = 0.0;
+        bool hit = false;
+        if (live && k < 5) {
+            const float4 bb = sb5[(long)m * 5 + k];
+            hit = !(bb.x > gi + 1.0f || bb.y < gi || bb.z > gj + 1.0f || bb.w < gj);
+            if (hit) {
+                const double *v = sv + (long)m * 24;
+                double qx[4], qy[4];
+                qx[0] = v[2 * k] - di;            qy[0] = v[2 * k + 1] - dj;
+                qx[1] = v[12 + 2 * k] - di;       qy[1] = v[12 + 2 * k + 1] - dj;
+                qx[2] = v[12 + 2 * k + 2] - di;   qy[2] = v[12 + 2 * k + 3] - dj;
+                qx[3] = v[2 * k + 2] - di;        qy[3] = v[2 * k + 3] - dj;
+                A = clip_area_unit(qx, qy);
+            }
+        }
+        double acc = 0.0, cov = 0.0;
+        const int g0 = (threadIdx.x & 31) & ~7;  // the group's first lane
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            const double As = __shfl_sync(0xffffffffu, A, g0 + s);
+            const bool hs = __shfl_sync(0xffffffffu, hit, g0 + s);
+            if (hs) { acc += As * Hk[s]; cov += As; }
+        }
+        if (live && k == 0) { pacc[p] = acc; pcov[p] = cov; }
+        return;
+    }
+    const uint32_t stride = (gridDim.x - kClipBlocks) * blockDim.x;
+    for (uint32_t p = (blockIdx.x - kClipBlocks) * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const uint32_t seg = pseg[p];
+        if (seg & kClipFlag) continue;
         const uint32_t cell = pcell[p];
         const int cj = (int)(cell / (uint32_t)nx), ci = (int)(cell - (uint32_t)cj * (uint32_t)nx);
         double acc, cov;
-        pair_area(pseg[p], ci, cj, sl, slf, scvx, sv, sb5, Hk, acc, cov);
+        pair_area(seg, ci, cj, sl, slf, scvx, sv, sb5, Hk, acc, cov);
         pacc[p] = acc;
         pcov[p] = cov;
     }
@@ -1519,7 +1582,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
                    al(64) + al(pair_cap * 4) * 2 + al(pair_cap * 8) * 2 + al(ncell * 8) +
                    al((ndrops + 1) * 4) + al(M * 4) * 5 + al(ncell * 4) +
                    al((ncell + 1) * 4) + al(nparts * 4) + al(nb * 4) * 2 + al(64) +
-                   al((size_t)nx * 8);
+                   al((size_t)nx * 8) + al((size_t)kClipCap * 4);
     cudaError_t e = cudaMalloc(&mk.mem, bytes);
     if (e != cudaSuccess) { mk.mem = nullptr; return e; }
     char *q = (char *)mk.mem;
@@ -1558,6 +1621,7 @@ cudaError_t markers_alloc(Markers &mk, int M, int ndrops, int nx, int ny, double
     mk.bcount = (uint32_t *)take(nb * 4); mk.bactive = (uint32_t *)take(nb * 4);
     mk.flags = (uint32_t *)take(64);
     mk.colkey = (unsigned long long *)take((size_t)nx * 8);
+    mk.clip_list = (uint32_t *)take((size_t)kClipCap * 4);
     std::vector<int32_t> dof(M), nxt(M);
     for (int d = 0; d < ndrops; d++)
         for (int m = drop_start_host[d]; m < drop_start_host[d + 1]; m++) {
@@ -1651,7 +1715,8 @@ void launch_spread_conv(const Markers &mk, int kernel, const double *fmag, doubl
                                              fmag, mk.nxm, mk.nym, mk.ds, Fx, Fy);
 }
 
-// Grid of the flat pair kernel: 8 CTAs of 256 threads per SM, grid-stride.
+// Grid of the strip-area kernel: kClipBlocks clip blocks, then 8 CTAs of
+// 256 threads per SM for the flat pair loop (grid-stride).
 int band_area_grid()
 {
     static int sms = 0;
@@ -1661,7 +1726,7 @@ int band_area_grid()
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
     }
-    return 8 * sms;
+    return kClipBlocks + 8 * sms;
 }
 
 // Strip areas of the current band pair list (idempotent: pacc, pcov only).
@@ -1669,7 +1734,7 @@ void launch_band_area(const Markers &mk, cudaStream_t s)
 {
     note_launch();
     k_band_area<<<band_area_grid(), 256, 0, s>>>(mk.nx, mk.npairs, mk.pair_cap, mk.pseg, mk.pcell,
-                                                 mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5, mk.pacc,
+                                                 mk.clip_list, mk.sl, mk.slf, mk.scvx, mk.sv, mk.sb5, mk.pacc,
                                                  mk.pcov);
 }
 
@@ -1690,11 +1755,11 @@ void launch_heaviside(const Markers &mk, double *H, cudaStream_t s, cudaStream_t
                                         mk.colkey, mk.next, mk.drop_start, mk.dyk, H, mk.flags);
     if (side) cudaEventRecord(ev_join, side);
     dim3 g(mk.bnx, mk.bny);
-    cudaMemsetAsync(mk.npairs, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(mk.npairs, 0, 2 * sizeof(uint32_t), s);  // pairs, listed clip pairs
     note_launch();
     k_band_pairs<<<g, kPairT, 0, s>>>(mk.nx, mk.ny, mk.bnx, mk.bactive, mk.cell_start, mk.ids, mk.slf,
                                    mk.scvx, mk.sbox, mk.pair_cap, mk.npairs, mk.pseg, mk.pcell,
-                                   mk.crange, mk.flags);
+                                   mk.crange, mk.clip_list, mk.flags);
     launch_band_area(mk, s);
     if (side) cudaStreamWaitEvent(s, ev_join, 0);
     note_launch();
