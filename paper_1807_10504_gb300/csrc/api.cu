@@ -399,7 +399,7 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
     cudaEventRecord(c->ev_fork, c->s);
     cudaStreamWaitEvent(c->s2, c->ev_fork, 0);
     cudaStreamWaitEvent(c->s3, c->ev_fork, 0);
-    mg_build(c->mg, g.axisym ? c->bxa : c->bx, g.axisym ? c->bya : c->by, c->s2);
+    mg_build(c->mg, g.axisym ? c->bxa : c->bx, g.axisym ? c->bya : c->by, c->s2, g.precision == 0);
     cudaEventRecord(c->ev_join, c->s2);
     force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s3);
     cudaEventRecord(c->ev_join3, c->s3);
@@ -844,6 +844,9 @@ ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
     if (t_pre) prof_mark(c->s, true);
     ib_status st = rec ? run_recorded(c, dt, key, [&] { return step_pre(c, dt, reloc, mass, warm); })
                        : step_pre(c, dt, reloc, mass, warm);
+    // the step rebuilt the hierarchy, with the FP64 sweep weights only for an
+    // FP64 solver (a replayed graph runs no host code)
+    c->mg.fp64_w = g.precision == 0;
     if (t_pre) prof_mark(c->s, false);
     if (st != IB_OK) return st;
     if (t_solve) prof_mark(c->s, true);

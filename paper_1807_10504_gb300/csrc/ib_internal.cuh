@@ -254,6 +254,10 @@ struct MG {
     unsigned *red_count = nullptr;
     double *red_host = nullptr;   // pinned mirror of the results
     int red_blocks = 0;
+    // the FP64 sweep weights (LevelT<double>::w) match the coefficients: the
+    // build leaves them out (only FP64 cycles read them), ensure_fp64_w forms
+    // them before one
+    bool fp64_w = false;
     void *mem = nullptr;          // one allocation for all of the above
     size_t bytes = 0;
 };
@@ -267,8 +271,11 @@ cudaError_t mg_alloc(MG &mg, int nx, int ny, double h);
 void mg_free(MG &mg);
 // One launch of one cycle kernel on the hierarchy's current data, for timing.
 long mg_bench_op(MG &mg, int op, int level, cudaStream_t s);
-// Copy level-0 coefficients (walls forced to 0) and build the hierarchy.
-void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s);
+// Copy level-0 coefficients (walls forced to 0) and build the hierarchy; the
+// FP64 sweep weights too with with_w (for a solver that runs FP64 cycles).
+void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s, bool with_w = false);
+// The FP64 sweep weights of every level, if the last build left them out.
+void ensure_fp64_w(MG &mg, cudaStream_t s);
 // Runs the solve on level-0 arrays of the hierarchy; p is read/written in place.
 ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
                  int max_cycles, int nu1, int nu2, int *cycles, double *relres,

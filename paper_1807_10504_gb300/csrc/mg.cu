@@ -1062,8 +1062,37 @@ __device__ __forceinline__ void level_coeffs_cell(int nx, int ny, int level0, in
     const double id = d > 0.0 ? recip_nr(d) : 0.0;
     invd[kc] = id;
     invdf[kc] = d2f_rn(id);
-    reinterpret_cast<double2 *>(w4)[2 * kc] = make_double2(w * id, e * id);
-    reinterpret_cast<double2 *>(w4)[2 * kc + 1] = make_double2(s * id, n * id);
+    if (w4) {
+        reinterpret_cast<double2 *>(w4)[2 * kc] = make_double2(w * id, e * id);
+        reinterpret_cast<double2 *>(w4)[2 * kc + 1] = make_double2(s * id, n * id);
+    }
+}
+
+// The FP64 sweep weights w_f = beta_f / diag of every level from its faces
+// and inverse diagonal (the products level_coeffs_cell forms when given w4),
+// one thread per cell over all levels.
+struct LevelWArgs {
+    int nl;
+    long start[17];  // first flat index of each level
+    int nx[16];
+    const double *bx[16], *by[16], *invd[16];
+    double *w4[16];
+};
+
+__global__ void k_level_w(LevelWArgs a)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.start[a.nl]) return;
+    int l = 0;
+    while (t >= a.start[l + 1]) l++;
+    const int nx = a.nx[l];
+    const long kc = t - a.start[l];
+    const int j = (int)(kc / nx), i = (int)(kc - (long)j * nx);
+    const long kx = (long)j * (nx + 1) + i;
+    const double id = a.invd[l][kc];
+    const double w = a.bx[l][kx], e = a.bx[l][kx + 1], s = a.by[l][kc], n = a.by[l][kc + nx];
+    reinterpret_cast<double2 *>(a.w4[l])[2 * kc] = make_double2(w * id, e * id);
+    reinterpret_cast<double2 *>(a.w4[l])[2 * kc + 1] = make_double2(s * id, n * id);
 }
 
 __global__ void k_level_coeffs(int nx, int ny, int level0, const double *__restrict__ fbx,
@@ -2220,7 +2249,7 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
     const long cells = (long)v.nx * v.ny;
     switch (op) {
     case 0: smooth<float>(v, v.f, v.f.e, 2, false, s); return cells;
-    case 1: smooth<double>(v, v.d, v.d.e, 1, false, s); return cells;
+    case 1: ensure_fp64_w(mg, s); smooth<double>(v, v.d, v.d.e, 1, false, s); return cells;
     case 3:
         if (level >= mg.tail_f) return -1;
         launch_smooth2<1>(v, v.f, v.f.e, v.f.e2, mg.lv[level + 1].f.r, mg.lv[level + 1].f.e2,
@@ -2254,6 +2283,7 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
     case 7:
     case 8: {  // the fused FP64 smoothers (7: sweeps + restriction, 8: prolongation + sweeps)
         if (level >= mg.tail) return -1;
+        ensure_fp64_w(mg, s);
         Level &c = mg.lv[level + 1];
         if (op == 7)
             launch_smooth2_f64<1>(v, v.d, v.d.e, v.d.e2, c.d.r, c.d.e2, c.h * c.h, c.d.invd,
@@ -2276,9 +2306,27 @@ long mg_bench_op(MG &mg, int op, int level, cudaStream_t s)
     }
 }
 
-void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
+void ensure_fp64_w(MG &mg, cudaStream_t s)
+{
+    if (mg.fp64_w) return;
+    LevelWArgs a;
+    a.nl = mg.L;
+    a.start[0] = 0;
+    for (int l = 0; l < mg.L; l++) {
+        Level &v = mg.lv[l];
+        a.nx[l] = v.nx;
+        a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd; a.w4[l] = v.d.w;
+        a.start[l + 1] = a.start[l] + (long)v.nx * v.ny;
+    }
+    note_launch();
+    k_level_w<<<(unsigned)cdiv(a.start[mg.L], 256), 256, 0, s>>>(a);
+    mg.fp64_w = true;
+}
+
+void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s, bool with_w)
 {
     const int L = mg.L;
+    mg.fp64_w = with_w;
     // levels above 1024 cells one launch each (their FP64 work spread over
     // the SMs), the rest in one CTA
     int lsmall = 1;
@@ -2289,7 +2337,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         dim3 g(cdiv(v.nx, 128), v.ny);
         note_launch();
         k_level_coeffs<<<g, 128, 0, s>>>(v.nx, v.ny, l == 0, fbx, fby, v.d.bx, v.d.by, v.f.bx, v.f.by,
-                                         v.f.bxp, v.d.invd, v.f.invd, v.d.w);
+                                         v.f.bxp, v.d.invd, v.f.invd, with_w ? v.d.w : nullptr);
     }
     if (lsmall < L) {
         LevelCoeffArgs a;
@@ -2298,7 +2346,7 @@ void mg_build(MG &mg, const double *bx, const double *by, cudaStream_t s)
         for (int l = 0; l < L; l++) {
             Level &v = mg.lv[l];
             a.nx[l] = v.nx; a.ny[l] = v.ny;
-            a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd; a.w4[l] = v.d.w;
+            a.bx[l] = v.d.bx; a.by[l] = v.d.by; a.invd[l] = v.d.invd; a.w4[l] = with_w ? v.d.w : nullptr;
             a.bxf[l] = v.f.bx; a.byf[l] = v.f.by; a.bxp[l] = v.f.bxp; a.invdf[l] = v.f.invd;
         }
         note_launch();
@@ -2332,6 +2380,7 @@ ib_status mg_run_direct(MG &mg, const double *rhs, double *p, int precision, dou
                         int max_cycles, int nu1, int nu2, int *cycles, double *relres,
                         cudaStream_t s, std::string &err)
 {
+    if (precision == 0) ensure_fp64_w(mg, s);
     Level &v0 = mg.lv[0];
     const long n = (long)v0.nx * v0.ny;
     const int RB = mg.red_blocks;
@@ -2511,6 +2560,7 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
 {
     if (!mg.use_graphs || prof_active())
         return mg_run_direct(mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles, relres, s, err);
+    if (precision == 0) ensure_fp64_w(mg, s);  // before the graph, which reads them
     SolveGraph *sg = nullptr;
     for (auto &g : mg.graphs)
         if (g.rhs == rhs && g.p == p && g.precision == precision && g.nu1 == nu1 && g.nu2 == nu2)
