@@ -1356,9 +1356,13 @@ __device__ double gval(const double *Gc, int g, int r, int c)
 // entry by the sums of a dense Cholesky in ascending order: per column c,
 // lane 0 takes the diagonal while lanes 1..6 take the envelope rows below it
 // (c+1..c+3 and the dense last three rows), whose sums need only earlier
-// columns; their division by the diagonal follows.  Returns -1 (in every
-// lane) if not positive definite.
-__device__ int env_factor(Env &L, const double *Gc, int g, int t)
+// columns; they are then scaled by the diagonal's reciprocal, which is kept
+// in rinv[c] for the substitutions.  The columns are a serial chain of FP64
+// latencies on this part (a division costs about 1.5 k cycles there), so
+// the diagonal's reciprocal is recip_nr's (FP32 seed, two Newton steps) and
+// the entries multiply by it.  Returns -1 (in every lane) if not positive
+// definite.
+__device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
 {
     for (int c = 0; c < g; c++) {
         // envelope row of lane t (t >= 1): the (t-1)-th of the ascending walk
@@ -1381,22 +1385,24 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t)
         const double s = __shfl_sync(0xffffffffu, acc, 0);
         if (!(s > 0.0)) return -1;
         const double d = sqrt(s);
-        if (t == 0) L.set(c, c, d);
-        else if (r >= 0) L.set(r, c, acc / d);
+        const double rd = (d > 1e-30 && d < 1e30) ? recip_nr(d) : 1.0 / d;
+        if (t == 0) { L.set(c, c, d); rinv[c] = rd; }
+        else if (r >= 0) L.set(r, c, acc * rd);
         __syncwarp();
     }
     return 0;
 }
 
 // L L^T x = b for the two right-hand sides bx, by (in place), each in the
-// order of a single-right-hand-side solve.
-__device__ void env_subst(const Env &L, int g, double *bx, double *by)
+// order of a single-right-hand-side solve, scaling by the diagonal's
+// reciprocals rinv (no division on the serial chain).
+__device__ void env_subst(const Env &L, int g, const double *rinv, double *bx, double *by)
 {
     for (int r = 0; r < g; r++) {
         double s = bx[r], t = by[r];
         for (int k = L.first(r); k < r; k++) { const double l = L.get(r, k); s -= l * bx[k]; t -= l * by[k]; }
-        bx[r] = s / L.get(r, r);
-        by[r] = t / L.get(r, r);
+        bx[r] = s * rinv[r];
+        by[r] = t * rinv[r];
     }
     for (int r = g - 1; r >= 0; r--) {
         double s = bx[r], t = by[r];
@@ -1406,8 +1412,8 @@ __device__ void env_subst(const Env &L, int g, double *bx, double *by)
             s -= l * bx[k];
             t -= l * by[k];
         }
-        bx[r] = s / L.get(r, r);
-        by[r] = t / L.get(r, r);
+        bx[r] = s * rinv[r];
+        by[r] = t * rinv[r];
     }
 }
 
@@ -1508,10 +1514,11 @@ k_reloc_fit(const double *__restrict__ X, const double *__restrict__ Y,
     __syncthreads();
     if (threadIdx.x < 32) {
         Env L{g, band, dense};
-        const int f = env_factor(L, Gc, g, threadIdx.x);
+        // cum holds the diagonal's reciprocals until the arc lengths below
+        const int f = env_factor(L, Gc, g, threadIdx.x, cum);
         if (threadIdx.x == 0) {
             if (f != 0) bad = 1;
-            else env_subst(L, g, cx, cy);
+            else env_subst(L, g, cum, cx, cy);
         }
     }
     __syncthreads();
