@@ -68,6 +68,18 @@ __device__ __forceinline__ double f2d(float f)
     return (double)f;
 }
 
+// 1/sqrt(x) for x in the FP32 normal range: the FP32 estimate (rsqrtf) of
+// x's leading bits refined by two Newton steps y <- y (3/2 - x y^2 / 2) in
+// FP64 (relative error 2^-22 -> 2^-43 -> below FP64 rounding); a short chain
+// of dependent operations, for serial code where FP64 latency counts.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = f2d_exact(rsqrtf(d2f_trunc(x)));
+    const double hx = -0.5 * x;
+    y = y * fma(hx, y * y, 1.5);
+    return y * fma(hx, y * y, 1.5);
+}
+
 // 1/x for x of either sign within the FP32 normal range (about 1e-37 < |x|
 // < 1e37): the FP32 reciprocal (__frcp_rn) of x's leading bits refined by two
 // Newton-Raphson steps r <- r + r (1 - x r) in FP64; each step squares the

@@ -1359,8 +1359,8 @@ __device__ double gval(const double *Gc, int g, int r, int c)
 // columns; they are then scaled by the diagonal's reciprocal, which is kept
 // in rinv[c] for the substitutions.  The columns are a serial chain of FP64
 // latencies on this part (a division costs about 1.5 k cycles there), so
-// the diagonal's reciprocal is recip_nr's (FP32 seed, two Newton steps) and
-// the entries multiply by it.  Returns -1 (in every lane) if not positive
+// the reciprocal comes from rsqrt_nr (FP32 seed, two Newton steps), the
+// diagonal is s times it, and the entries multiply by it.  Returns -1 (in every lane) if not positive
 // definite.
 __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
 {
@@ -1384,8 +1384,11 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
         }
         const double s = __shfl_sync(0xffffffffu, acc, 0);
         if (!(s > 0.0)) return -1;
-        const double d = sqrt(s);
-        const double rd = (d > 1e-30 && d < 1e30) ? recip_nr(d) : 1.0 / d;
+        // the diagonal d = sqrt(s) and its reciprocal from one reciprocal
+        // square root (a shorter chain than a square root and a reciprocal)
+        const bool fast = s > 1e-30 && s < 1e30;
+        const double rd = fast ? rsqrt_nr(s) : 1.0 / sqrt(s);
+        const double d = fast ? s * rd : sqrt(s);
         if (t == 0) { L.set(c, c, d); rinv[c] = rd; }
         else if (r >= 0) L.set(r, c, acc * rd);
         __syncwarp();
