@@ -1375,7 +1375,27 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
             }
         }
         double acc = 0.0;
-        if (t == 0) {
+        if (c >= g - 3 && c > 32) {
+            // the last columns: the diagonal and the (dense) rows below have
+            // sums over all earlier columns; the warp takes them in strided
+            // partial sums and a shuffle tree (the same total in every lane)
+            double pd = 0.0, p1 = 0.0, p2 = 0.0;
+            for (int k = t; k < c; k += 32) {
+                const double lc = L.get(c, k);
+                pd += lc * lc;
+                if (c + 1 < g) p1 += L.get(c + 1, k) * lc;
+                if (c + 2 < g) p2 += L.get(c + 2, k) * lc;
+            }
+            for (int o = 16; o; o >>= 1) {
+                pd += __shfl_xor_sync(0xffffffffu, pd, o);
+                p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+                p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+            }
+            // rows c + 1, c + 2 are the walk's first two: lanes 1 and 2
+            if (t == 0) acc = gval(Gc, g, c, c) - pd;
+            else if (r == c + 1) acc = gval(Gc, g, r, c) - p1;
+            else if (r == c + 2) acc = gval(Gc, g, r, c) - p2;
+        } else if (t == 0) {
             acc = gval(Gc, g, c, c);
             for (int k = L.first(c); k < c; k++) { double v = L.get(c, k); acc -= v * v; }
         } else if (r >= 0) {
@@ -1396,27 +1416,47 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
     return 0;
 }
 
-// L L^T x = b for the two right-hand sides bx, by (in place), each in the
-// order of a single-right-hand-side solve, scaling by the diagonal's
-// reciprocals rinv (no division on the serial chain).
-__device__ void env_subst(const Env &L, int g, const double *rinv, double *bx, double *by)
+// L L^T x = b for the two right-hand sides bx, by (in place) by warp 0
+// (lane t): every lane runs the serial substitution, lane 0 stores each
+// entry; the long sums of the dense last rows go to the whole warp (strided
+// partial sums and a shuffle tree); scaling by the diagonal's reciprocals
+// rinv (no division on the serial chain).
+__device__ void env_subst(const Env &L, int g, const double *rinv, double *bx, double *by, int t)
 {
     for (int r = 0; r < g; r++) {
-        double s = bx[r], t = by[r];
-        for (int k = L.first(r); k < r; k++) { const double l = L.get(r, k); s -= l * bx[k]; t -= l * by[k]; }
-        bx[r] = s * rinv[r];
-        by[r] = t * rinv[r];
+        double s = bx[r], u = by[r];
+        const int k0 = L.first(r);
+        if (r - k0 > 32) {
+            double ps = 0.0, pu = 0.0;
+            for (int k = k0 + t; k < r; k += 32) { const double l = L.get(r, k); ps += l * bx[k]; pu += l * by[k]; }
+            for (int o = 16; o; o >>= 1) {
+                ps += __shfl_xor_sync(0xffffffffu, ps, o);
+                pu += __shfl_xor_sync(0xffffffffu, pu, o);
+            }
+            s -= ps;
+            u -= pu;
+        } else {
+            for (int k = k0; k < r; k++) { const double l = L.get(r, k); s -= l * bx[k]; u -= l * by[k]; }
+        }
+        s *= rinv[r];
+        u *= rinv[r];
+        __syncwarp();
+        if (t == 0) { bx[r] = s; by[r] = u; }
+        __syncwarp();
     }
     for (int r = g - 1; r >= 0; r--) {
-        double s = bx[r], t = by[r];
+        double s = bx[r], u = by[r];
         for (int k = r + 1; k < g; k = (k == r + 3 && k + 1 < g - 3) ? g - 3 : k + 1) {
             if (L.is_band(k) && k - 3 > r) continue;
             const double l = L.get(k, r);
             s -= l * bx[k];
-            t -= l * by[k];
+            u -= l * by[k];
         }
-        bx[r] = s * rinv[r];
-        by[r] = t * rinv[r];
+        s *= rinv[r];
+        u *= rinv[r];
+        __syncwarp();
+        if (t == 0) { bx[r] = s; by[r] = u; }
+        __syncwarp();
     }
 }
 
@@ -1518,10 +1558,11 @@ k_reloc_fit(const double *__restrict__ X, const double *__restrict__ Y,
     if (threadIdx.x < 32) {
         Env L{g, band, dense};
         // cum holds the diagonal's reciprocals until the arc lengths below
-        const int f = env_factor(L, Gc, g, threadIdx.x, cum);
-        if (threadIdx.x == 0) {
-            if (f != 0) bad = 1;
-            else env_subst(L, g, cum, cx, cy);
+        const int f = env_factor(L, Gc, g, threadIdx.x, cum);  // the same in every lane
+        if (f != 0) {
+            if (threadIdx.x == 0) bad = 1;
+        } else {
+            env_subst(L, g, cum, cx, cy, threadIdx.x);
         }
     }
     __syncthreads();
