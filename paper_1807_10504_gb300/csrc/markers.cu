@@ -176,8 +176,12 @@ __global__ void k_segments(int M, const int32_t *__restrict__ next, const double
     for (int q = 0; q < 8; q++) {
         d[5 * q + 0] = L[q][0]; d[5 * q + 1] = L[q][1]; d[5 * q + 2] = L[q][2];
         d[5 * q + 3] = rcp(L[q][0]); d[5 * q + 4] = rcp(L[q][1]);
+        // |n| in FP32: left_of normalised n (to a few units of 1e-16), so
+        // (float)|n| is 1.0f, or 0.0f for the zero vector of a degenerate line
+        const bool nz = ((__double_as_longlong(L[q][0]) | __double_as_longlong(L[q][1])) &
+                         0x7fffffffffffffffLL) != 0;
         slf[(long)m * 8 + q] = make_float4(d2f_rn(L[q][0]), d2f_rn(L[q][1]), d2f_rn(L[q][2]),
-                                           d2f_rn(sqrt(L[q][0] * L[q][0] + L[q][1] * L[q][1])));
+                                           nz ? 1.0f : 0.0f);
     }
     d[40] = rcp(L[0][0] * L[1][1] - L[0][1] * L[1][0]);
     for (int o = 0; o < 6; o++) {
