@@ -714,11 +714,26 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
                cell_side(st ? s_l[2][q] : L[2], fi, fj) >= 0 &&
                cell_side(st ? s_l[3][q] : L[7], fi, fj) <= 0;
     };
-    // this thread's contiguous share of the (ascending) candidate list
+    // this thread's contiguous share of the (ascending) candidate list; its
+    // test results are kept as bits in tmp (free after the gathering: four
+    // words a thread, word w of thread t at tmp[w * kPairT + t]) for the
+    // second pass, when the block has at most 4 x 128 candidates
     const int q0 = (n * sub) / kPairSub, q1 = (n * (sub + 1)) / kPairSub;
+    static_assert(kMaxCand >= 4 * kPairT, "four words of tmp per thread");
+    const bool keep = n <= kPairSub * 128;
     uint32_t c = 0;
-    if (live)
-        for (int q = q0; q < q1; q++) c += meets(q) ? 1u : 0u;
+    if (live) {
+        uint32_t word = 0;
+        for (int q = q0; q < q1; q++) {
+            const bool mt = meets(q);
+            c += mt ? 1u : 0u;
+            if (keep) {
+                const int b = q - q0;
+                word |= (mt ? 1u : 0u) << (b & 31);
+                if ((b & 31) == 31 || q + 1 == q1) { tmp[(b >> 5) * kPairT + t] = word; word = 0; }
+            }
+        }
+    }
     // exclusive scan over threads (cell-major, then share): warp scans, then
     // the warp totals
     const int lane = t & 31, warp = t >> 5;
@@ -757,7 +772,7 @@ k_band_pairs(int nx, int ny, int bnx, const uint32_t *__restrict__ bactive,
     }
     uint32_t o = base + excl;
     for (int q = q0; q < q1; q++)
-        if (meets(q)) {
+        if (keep ? ((tmp[((q - q0) >> 5) * kPairT + t] >> ((q - q0) & 31)) & 1u) : meets(q)) {
             uint32_t seg = cand[q];
             // a pair of a non-convex strip goes to the clip list of
             // k_band_area (while it has room), marked in the id's top bit
