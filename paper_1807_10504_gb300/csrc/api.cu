@@ -863,8 +863,12 @@ ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
     } else {
         c->have_pprev = false;
     }
-    st = mg_run(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
-                &c->last_cycles, &c->last_relres, c->s, c->err);
+    // the solve is queued without waiting for it: the launches after it
+    // follow at once, and its status is read at the step's one
+    // synchronisation (the flags read)
+    MgPending pend;
+    st = mg_run_launch(c->mg, c->b, c->p, g.precision, g.tol, g.max_cycles, g.nu1, g.nu2,
+                       &c->last_cycles, &c->last_relres, c->s, c->err, pend);
     if (t_solve) prof_mark(c->s, false);
     if (st != IB_OK && st != IB_ENOTCONV) return st;
     if (t_post) prof_mark(c->s, true);
@@ -876,6 +880,12 @@ ib_status step_one(ib_ctx *c, double dt, int warm, F before_flags)
     c->step++;
     before_flags();
     ib_status fs = read_flags(c);
+    if (pend.pending) {
+        // a failed solve is reported ahead of the flags (its message wins)
+        const ib_status ss = mg_run_finish(c->mg, pend, &c->last_cycles, &c->last_relres, c->err);
+        if (ss != IB_OK && ss != IB_ENOTCONV) return ss;
+        st = ss;
+    }
     if (fs != IB_OK) return fs;
     return st;
 }

@@ -292,6 +292,20 @@ void ensure_fp64_w(MG &mg, cudaStream_t s);
 ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
                  int max_cycles, int nu1, int nu2, int *cycles, double *relres,
                  cudaStream_t s, std::string &err);
+// The same in two parts, so that work queued after the solve need not wait
+// for the host: mg_run_launch queues the solve graph and returns with
+// pend.pending set (or, where it solves with direct launches, finishes and
+// returns the status with pend.pending clear); once the stream has been
+// synchronised, mg_run_finish reads the solve's status.
+struct MgPending {
+    bool pending = false;
+    double tol = 0;
+    unsigned long long outer_kernels = 0, body_kernels = 0;
+};
+ib_status mg_run_launch(MG &mg, const double *rhs, double *p, int precision, double tol,
+                        int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                        cudaStream_t s, std::string &err, MgPending &pend);
+ib_status mg_run_finish(MG &mg, const MgPending &pend, int *cycles, double *relres, std::string &err);
 
 // The same solve with one launch per kernel and a host read of the residual
 // after each cycle (no graph objects, no allocation of its own).

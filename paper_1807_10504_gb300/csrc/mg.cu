@@ -2554,10 +2554,11 @@ static cudaError_t build_solve_graph(MG &mg, SolveGraph &sg)
 
 static bool prof_active();
 
-ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
-                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
-                 cudaStream_t s, std::string &err)
+ib_status mg_run_launch(MG &mg, const double *rhs, double *p, int precision, double tol,
+                        int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                        cudaStream_t s, std::string &err, MgPending &pend)
 {
+    pend.pending = false;
     if (!mg.use_graphs || prof_active())
         return mg_run_direct(mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles, relres, s, err);
     if (precision == 0) ensure_fp64_w(mg, s);  // before the graph, which reads them
@@ -2586,18 +2587,39 @@ ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol
     mg.ctl_host->max_cycles = max_cycles;
     cudaError_t e = cudaMemcpyAsync(mg.ctl, mg.ctl_host, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaGraphLaunch(sg->exec, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { err = cudaGetErrorString(e); return IB_ECUDA; }
+    pend.pending = true;
+    pend.tol = tol;
+    pend.outer_kernels = sg->outer_kernels;
+    pend.body_kernels = sg->body_kernels;
+    return IB_OK;
+}
+
+ib_status mg_run_finish(MG &mg, const MgPending &pend, int *cycles, double *relres, std::string &err)
+{
     if (mg.ctl_host->fault) { err = fault_message(mg.ctl_host->fault); return IB_ECUDA; }
     const int c = mg.ctl_host->cycles;
     const double rr = mg.ctl_host->rr;
-    note_launch((int)(sg->outer_kernels + (unsigned long long)c * sg->body_kernels));
+    note_launch((int)(pend.outer_kernels + (unsigned long long)c * pend.body_kernels));
     if (cycles) *cycles = c;
     if (relres) *relres = rr;
     if (mg.ctl_host->zero_p) return IB_OK;
     if (!isfinite(rr)) { err = "non-finite residual"; return IB_ENAN; }
-    if (rr > tol) { err = "cycle cap reached above tolerance"; return IB_ENOTCONV; }
+    if (rr > pend.tol) { err = "cycle cap reached above tolerance"; return IB_ENOTCONV; }
     return IB_OK;
+}
+
+ib_status mg_run(MG &mg, const double *rhs, double *p, int precision, double tol,
+                 int max_cycles, int nu1, int nu2, int *cycles, double *relres,
+                 cudaStream_t s, std::string &err)
+{
+    MgPending pend;
+    const ib_status st = mg_run_launch(mg, rhs, p, precision, tol, max_cycles, nu1, nu2, cycles,
+                                       relres, s, err, pend);
+    if (!pend.pending) return st;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { err = cudaGetErrorString(e); return IB_ECUDA; }
+    return mg_run_finish(mg, pend, cycles, relres, err);
 }
 
 // Context-free launches used by the verification entry points.
