@@ -265,3 +265,51 @@ def test_static_drop_100_steps_parasitic_currents_and_laplace_jump(T, ib):
     assert conv["max_u"] > 1e-4 and conv["jump_rel_err"] < 0.05, conv
     assert rep["irrotational_relocate10"]["max_u"] < 1e-2 * rep["conventional_relocate10"]["max_u"]
     print("static drop, 100 steps:", rep)
+
+
+def test_step_reports_its_solve_status_after_the_launches_that_follow_it(T, ib):
+    """ns_step queues the pressure solve and the launches after it without a
+    host wait and reads the solve's status at the step's final
+    synchronisation.  A solve stopped by its cycle cap still reports
+    IB_ENOTCONV (and its cycle count) through the recorded graphs as through
+    direct launches; a solve whose smoother blocks time out (the staging
+    test hook, bounded waits) reports IB_ECUDA with the time-out named, ahead
+    of any marker flag the step's later launches may raise."""
+    n = 256  # levels 256^2 and 128^2 are TMA-staged
+    mk = W.static_drop(n, 0.25, 256)
+    kw = dict(nx=n, ny=n, h=1.0 / n, precision=2, tol=1e-15, max_cycles=2, relocate_every=0)
+    got = []
+    for graphs in (True, False):
+        ctx = ib.Context(ib.Config(**kw), mk.X, mk.Y, mk.drop_start)
+        ctx.use_graphs(graphs)
+        res = []
+        for _ in range(3):  # the first step runs direct, the next ones replay graphs
+            with pytest.raises(ib.IBError) as e:
+                ctx.ns_step(1e-4, 1, 1)
+            assert e.value.status == ib.IB_ENOTCONV
+            cyc, rr = C_last(ib, ctx)
+            assert cyc == 2 and rr > 1e-15
+            res.append(rr)
+        got.append(res)
+        ctx.close()
+    assert got[0] == got[1]
+    ctx = ib.Context(ib.Config(**kw), mk.X, mk.Y, mk.drop_start)
+    with pytest.raises(ib.IBError):
+        ctx.ns_step(1e-4, 1, 1)  # cycle cap, as above; the graphs are recorded
+    ib.debug_stall_staging(True)
+    try:
+        with pytest.raises(ib.IBError) as e:
+            ctx.ns_step(1e-4, 1, 1)
+        assert e.value.status == ib.IB_ECUDA
+        assert "staging wait timed out" in str(e.value)
+    finally:
+        ib.debug_stall_staging(False)
+    T.cuda.synchronize()
+    ctx.close()
+
+
+def C_last(ib, ctx):
+    import ctypes
+    cyc, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+    ib.lib().ib_last_solve(ctx._h, ctypes.byref(cyc), ctypes.byref(rr))
+    return cyc.value, rr.value
