@@ -1442,40 +1442,67 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
 // rinv (no division on the serial chain).
 __device__ void env_subst(const Env &L, int g, const double *rinv, double *bx, double *by, int t)
 {
+    // Even lanes take the x right-hand side, odd lanes the y one, so that
+    // one warp instruction advances both: on this part an FP64 warp
+    // instruction occupies the FP64 unit as long for one lane as for 32, and
+    // the passes are chains of them.  Each lane keeps its side's latest
+    // three entries (and, backwards, the dense last rows') in registers;
+    // lanes 0 and 1 store them for the long sums and the other pass, after
+    // one warp barrier a row (every lane has read the row's right-hand side).
+    double *b = (t & 1) ? by : bx;
+    double x1 = 0.0, x2 = 0.0, x3 = 0.0;  // rows r-1, r-2, r-3
     for (int r = 0; r < g; r++) {
-        double s = bx[r], u = by[r];
+        double s = b[r];
         const int k0 = L.first(r);
-        if (r - k0 > 32) {
-            double ps = 0.0, pu = 0.0;
-            for (int k = k0 + t; k < r; k += 32) { const double l = L.get(r, k); ps += l * bx[k]; pu += l * by[k]; }
-            for (int o = 16; o; o >>= 1) {
-                ps += __shfl_xor_sync(0xffffffffu, ps, o);
-                pu += __shfl_xor_sync(0xffffffffu, pu, o);
+        if (r - k0 > 3) {
+            // a dense last row: all earlier entries, from shared memory
+            __syncwarp();
+            if (r - k0 > 32) {
+                double ps = 0.0, pu = 0.0;
+                for (int k = k0 + t; k < r; k += 32) { const double l = L.get(r, k); ps += l * bx[k]; pu += l * by[k]; }
+                for (int o = 16; o; o >>= 1) {
+                    ps += __shfl_xor_sync(0xffffffffu, ps, o);
+                    pu += __shfl_xor_sync(0xffffffffu, pu, o);
+                }
+                s -= (t & 1) ? pu : ps;
+            } else {
+                for (int k = k0; k < r; k++) s -= L.get(r, k) * b[k];
             }
-            s -= ps;
-            u -= pu;
         } else {
-            for (int k = k0; k < r; k++) { const double l = L.get(r, k); s -= l * bx[k]; u -= l * by[k]; }
+            for (int k = k0; k < r; k++) {  // ascending k, the last (at most) three rows
+                const int back = r - k;
+                s -= L.get(r, k) * (back == 1 ? x1 : (back == 2 ? x2 : x3));
+            }
         }
         s *= rinv[r];
-        u *= rinv[r];
         __syncwarp();
-        if (t == 0) { bx[r] = s; by[r] = u; }
-        __syncwarp();
+        if (t < 2) b[r] = s;
+        x3 = x2; x2 = x1; x1 = s;
     }
+    __syncwarp();
+    double f1 = 0.0, f2 = 0.0, f3 = 0.0;  // rows r+1, r+2, r+3
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;  // rows g-3, g-2, g-1
     for (int r = g - 1; r >= 0; r--) {
-        double s = bx[r], u = by[r];
+        double s = b[r];
         for (int k = r + 1; k < g; k = (k == r + 3 && k + 1 < g - 3) ? g - 3 : k + 1) {
             if (L.is_band(k) && k - 3 > r) continue;
-            const double l = L.get(k, r);
-            s -= l * bx[k];
-            u -= l * by[k];
+            double xv;
+            if (k - r <= 3) {
+                const int back = k - r;
+                xv = back == 1 ? f1 : (back == 2 ? f2 : f3);
+            } else {  // k >= g - 3
+                const int q = k - (g - 3);
+                xv = q == 0 ? t0 : (q == 1 ? t1 : t2);
+            }
+            s -= L.get(k, r) * xv;
         }
         s *= rinv[r];
-        u *= rinv[r];
         __syncwarp();
-        if (t == 0) { bx[r] = s; by[r] = u; }
-        __syncwarp();
+        if (t < 2) b[r] = s;
+        f3 = f2; f2 = f1; f1 = s;
+        if (r == g - 1) t2 = s;
+        else if (r == g - 2) t1 = s;
+        else if (r == g - 3) t0 = s;
     }
 }
 
