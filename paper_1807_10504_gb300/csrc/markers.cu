@@ -1414,12 +1414,15 @@ __device__ int env_factor(Env &L, const double *Gc, int g, int t, double *rinv)
             if (t == 0) acc = gval(Gc, g, c, c) - pd;
             else if (r == c + 1) acc = gval(Gc, g, r, c) - p1;
             else if (r == c + 2) acc = gval(Gc, g, r, c) - p2;
-        } else if (t == 0) {
-            acc = gval(Gc, g, c, c);
-            for (int k = L.first(c); k < c; k++) { double v = L.get(c, k); acc -= v * v; }
-        } else if (r >= 0) {
-            acc = gval(Gc, g, r, c);
-            for (int k = max(L.first(r), L.first(c)); k < c; k++) acc -= L.get(r, k) * L.get(c, k);
+        } else {
+            // lane 0 the diagonal (its row is c), lanes 1..6 the rows below:
+            // one code path, so the same FP64 warp instructions serve all
+            // (on this part they cost the same for one lane as for 32)
+            const int rr = t == 0 ? c : r;
+            if (rr >= 0) {
+                acc = gval(Gc, g, rr, c);
+                for (int k = max(L.first(rr), L.first(c)); k < c; k++) acc -= L.get(rr, k) * L.get(c, k);
+            }
         }
         const double s = __shfl_sync(0xffffffffu, acc, 0);
         if (!(s > 0.0)) return -1;
