@@ -216,7 +216,12 @@ ib_status mg_solve(ib_ctx *ctx, const double *rhs, double *p, int precision,
  * network's estimate (square grid, side a multiple of 4), 3 the previous
  * two steps' pressures extrapolated in time, 2 p^n - p^(n-1) (p^n until two
  * exist).  The last step's cycles and residual are returned by
- * ib_last_solve.                                                           */
+ * ib_last_solve.  A step queues the launches after the pressure solve
+ * without waiting for the solve to end; the solve's status is read with the
+ * step's marker flags, so a step whose solve returns IB_ENOTCONV (or reports
+ * a smoother fault, IB_ECUDA) has still corrected the velocity with the last
+ * iterate and moved the markers.  The solve's status comes first when the
+ * marker flags also report an error; nsteps > 1 stops after that step.     */
 ib_status ns_step(ib_ctx *ctx, double dt, int nsteps, int warm);
 
 /* One time step as ns_step(ctx, dt, 1, warm) with host buffers (pinned
