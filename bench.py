@@ -192,11 +192,11 @@ def host_info():
     return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
-def oracle_rate(name, openmp, precision=2, budget_s=0.0, max_steps=1):
+def oracle_rate(name, openmp, precision=2, budget_s=0.0, max_steps=1, warmup=0):
     """Oracle time steps/s on workload `name`: serial build (one core) or the
-    OpenMP build (all host cores, bit-identical results).  Runs at least one
-    step and then as many of `max_steps` as fit in `budget_s` seconds.
-    Returns (steps/s, seconds, steps, threads)."""
+    OpenMP build (all host cores, bit-identical results).  After `warmup`
+    untimed steps, runs at least one step and then as many of `max_steps` as
+    fit in `budget_s` seconds.  Returns (steps/s, seconds, steps, threads)."""
     import oracle as O
     O.set_threads(openmp)
     try:
@@ -205,6 +205,8 @@ def oracle_rate(name, openmp, precision=2, budget_s=0.0, max_steps=1):
         nx, ny, kw, dt = problem(name)
         cfg = O.Config(nx=nx, ny=ny, precision=precision, spread=1, relocate_every=10, **kw)
         st = O.init_state(cfg, mk.X, mk.Y, mk.drop_start)
+        for _ in range(warmup):
+            O.ns_step(cfg, st, dt)
         done, t = 0, 0.0
         while done < max_steps and (done == 0 or t < budget_s):
             t0 = time.perf_counter()
@@ -256,10 +258,10 @@ def cpu_baseline(name):
 
 def run_reference(args):
     """The oracle timed as it stands on the host cores (its OpenMP build, all
-    cores; bit-identical to the serial one): as many of the K requested
-    oracle time steps as fit in a 60 s budget (at least one); the per-step
-    rate is the metric and `steps` is the number actually timed.  Rank 0
-    only."""
+    cores; bit-identical to the serial one): W untimed warm-up steps, then as
+    many of the K requested oracle time steps as fit in a 60 s budget (at
+    least one); the per-step rate is the metric and `steps` is the number
+    actually timed.  Rank 0 only."""
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
@@ -267,12 +269,14 @@ def run_reference(args):
     nx, ny, kw, dt = problem(name)
     info = host_info()
     try:
-        value, t, done, thr = oracle_rate(name, True, args.precision, 60.0, args.steps)
+        value, t, done, thr = oracle_rate(name, True, args.precision, 60.0, args.steps,
+                                          args.warmup)
     except Exception:
-        value, t, done, thr = oracle_rate(name, False, args.precision, 60.0, args.steps)
+        value, t, done, thr = oracle_rate(name, False, args.precision, 60.0, args.steps,
+                                          args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
-        "n_gpus": args.gpus, "steps": done, "warmup": 0,
+        "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / done, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32" if args.precision >= 1 else "f64",
         "data": "synthetic",
