@@ -303,8 +303,8 @@ def run_reference(args):
 # prolongation 7.
 FP64_RESTRICT = {"bytes": 80.0, "flops": 2 * 8.0 + 5.0}
 FP64_PROLONG = {"bytes": 58.0, "flops": 2 * 8.0 + 7.0}
-# Per fine cell and V(2,2) cycle: SURVEY's fused minimum (84 B per level cell
-# x 4/3 levels) and the per-kernel (unfused) accounting (212 B x 4/3); FP64
+# Per fine cell and V(2,2) cycle: the fully fused minimum of compulsory FP64
+# traffic (84 B per level cell x 4/3 levels) and the per-kernel (unfused) accounting (212 B x 4/3); FP64
 # operations of the FP64 cycle: (4 sweeps x 8 + 5 + 7) x 4/3 + the fine
 # residual norm of the convergence test (15).
 VCYCLE_BYTES_FUSED, VCYCLE_BYTES_UNFUSED = 112.0, 283.0
@@ -331,8 +331,8 @@ def timed_solve(torch, ctx, stream, flush, b, prec, start=None, reps=5, warm=3):
 
 
 def per_vcycle(entry, cells, pk, fp64_peak, fp64):
-    """Per-V-cycle time and effective bandwidth (SURVEY's 112 and 283 B per
-    fine cell) of a solve entry; FP64 cycles also against the FP64 peak."""
+    """Per-V-cycle time and effective bandwidth (the fused 112 and the unfused
+    283 B per fine cell) of a solve entry; FP64 cycles also against the FP64 peak."""
     us = 1e3 * entry["ms"] / max(entry["cycles"], 1)
     out = {"us": us}
     for label, B in (("fused_112B", VCYCLE_BYTES_FUSED), ("unfused_283B", VCYCLE_BYTES_UNFUSED)):
@@ -390,7 +390,7 @@ def solve_and_kernels(ib, torch, ctx, stream, flush, nx, ny, net, pk, fp64_peak)
 
 
 def static_drop_report(ib, steps=100):
-    """configs[0]: the 64^2 static drop (R = 0.25 centred, 128 equispaced
+    """The Laplace test of Section 5.1: the 64^2 static drop (R = 0.25 centred, 128 equispaced
     markers, density ratio 1000, viscosity ratio 100, sigma 1, FP64 solve to
     1e-10) after `steps` time steps, with the conventional and the
     irrotational spreading, markers as placed (curvature exactly 1/R) and

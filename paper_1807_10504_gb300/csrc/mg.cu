@@ -394,7 +394,7 @@ k_smooth2_f32(int nx, int ny, float h2, float ih2, const float *__restrict__ bx,
         asm volatile("cp.async.wait_all;\n" ::);
         bool ok = mbar_wait(&bar, 0, kStageWaitNs);
         if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
-        // one verdict for the whole block (each thread's wait is bounded)
+        // one outcome for the whole block (each thread's wait is bounded)
         if (__syncthreads_or(!ok)) {
             // skip the tile; the copies must land before the block leaves
             const bool landed = mbar_wait(&bar, 0, kDrainNs);
@@ -622,14 +622,14 @@ k_smooth2t_f32(int nx, int ny, float h2, float ih2, float *__restrict__ p, float
         }
     }
     // the first warp waits for the tensor copies (a bounded wait) and the
-    // block barrier of the verdict passes the copied data on to the others;
+    // block barrier of the outcome passes the copied data on to the others;
     // the other warps issue nothing while they wait there
     bool ok = true;
     if (warp == 0) {
         ok = mbar_wait(&bar, 0, kStageWaitNs);
         if (ok && g_stall_staging) ok = mbar_wait(&stall_bar, 0, kStageWaitNs);
     }
-    // one verdict for the whole block
+    // one outcome for the whole block
     if (__syncthreads_or(!ok)) {
         // skip the tile; the copies must land before the block leaves
         const bool landed = mbar_wait(&bar, 0, kDrainNs);
@@ -2081,8 +2081,9 @@ bool mg_levels(int nx, int ny, std::vector<int> &nxs, std::vector<int> &nys)
     return (long)nx * ny <= kMaxCoarsest;
 }
 
-// The driver's tensor-map encoder, looked up once through the runtime (no
-// link against the driver library); null where the driver lacks it.
+// The CUDA driver API's tensor-map encoder, looked up once through the
+// runtime (no link against the driver library); null where the installed
+// driver lacks it.
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {

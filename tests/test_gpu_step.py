@@ -251,7 +251,7 @@ def test_ns_step_io_matches_separate_calls(T, ib):
 
 
 def test_static_drop_100_steps_parasitic_currents_and_laplace_jump(T, ib):
-    """configs[0] (Section 5.1): the 64^2 static drop after 100 FP64 steps.
+    """The Laplace test (Section 5.1): the 64^2 static drop after 100 FP64 steps.
     With markers as placed (curvature exactly 1/R) the irrotational force is
     a discrete gradient balanced by the pressure: no parasitic current to
     roundoff and the jump of Eq. (sd_pres_diff) equal to sigma / R = 4; the
