@@ -88,17 +88,20 @@ __global__ void k_correct(int nx, int ny, double ih, double dt,
 // per node (four cells inside, the two wall cells on a wall), then every
 // flux that two faces share once per tile: per cell the advective flux
 // rho a^2 and the viscous flux mu du of each component, per node the
-// advective flux rho_n a_v a_u and the viscous flux mu_n du of each
-// component (the reflected ghost folded in at a wall node, zero advective
-// flux there).  Each thread then updates the x-face left of and the y-face
+// advective flux rho_n a_v a_u (one product for both components, zero
+// through a wall) and the viscous flux mu_n du of each component (the
+// reflected ghost folded in at a wall node).  Each thread then updates the x-face left of and the y-face
 // below its cell (and the wall face on the far side for the last column /
 // row) from differences of those fluxes, in the order of the per-face
 // formula, so each face gets the same value as if it formed them itself.
 // The advective fluxes are kept without their power-of-two factors (the
 // 1/2 of each face average, the 1/4 of the node density): 4 rho a^2 per
 // cell, 16 rho_n a_v a_u per node, the factors folded into 1/h of the
-// difference.  Scaling by a power of two is exact, so every rounding is as
-// in the per-face formula (fewer FP64 multiplications, the same values).
+// difference; the node viscosity is kept as 4 mu_n, its 1/4 folded into the
+// viscous difference.  Scaling by a power of two is exact, so every rounding
+// is as in the per-face formula (fewer FP64 multiplications, the same
+// values), except that the node product is formed in one order for both
+// components.
 constexpr int PX = 32, PY = 8;
 __global__ void __launch_bounds__(PX * PY)
 k_predictor(int nx, int ny, double ih, double ih2, double dt,
@@ -111,7 +114,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
 {
     constexpr int W = PX + 2, Hh = PY + 2;  // staged window: cells / faces i0-1 .. i0+PX
     __shared__ double sr[Hh][W], sm[Hh][W], su[Hh][W + 1], sv[Hh + 1][W];
-    __shared__ double nr[PY + 1][PX + 1], nm[PY + 1][PX + 1];
+    __shared__ double nm4[PY + 1][PX + 1];  // 4 mu_n
     // shared fluxes: x-momentum at cells i0-1 .. i0+PX-1 (fx, vx) and nodes
     // (i0 .. i0+PX-1, j0 .. j0+PY) (gx, wx); y-momentum at cells j0-1 ..
     // j0+PY-1 (fy, vy) and nodes (i0 .. i0+PX, j0 .. j0+PY-1) (gy, wy)
@@ -138,18 +141,25 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
     }
     __syncthreads();
     // node (I, J) = corner of cells (I-1, J-1), (I, J-1), (I-1, J), (I, J);
-    // window index of cell (gi, gj) is (gj - j0 + 1, gi - i0 + 1)
+    // window index of cell (gi, gj) is (gj - j0 + 1, gi - i0 + 1).  The
+    // advective node flux 16 rho_n a_v a_u, between u(I, J-1) and u(I, J)
+    // (window (r, c+1), (r+1, c+1)) and between v(I-1, J) and v(I, J)
+    // (window (r+1, c), (r+1, c+1)), serves the x-momentum (zero on the
+    // walls J = 0, ny) and the y-momentum (zero on the walls I = 0, nx)
     for (int k = t; k < (PY + 1) * (PX + 1); k += PX * PY) {
         const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
         if (I > nx || J > ny) continue;
         const double *r0 = &sr[r][c], *r1 = &sr[r + 1][c];  // rows J-1, J; columns I-1, I
         const double *m0 = &sm[r][c], *m1 = &sm[r + 1][c];
         const bool wx = I == 0 || I == nx, wy = J == 0 || J == ny;
-        nr[r][c] = r0[0] + r0[1] + r1[0] + r1[1];  // 4 rho_n
-        if (!wx && !wy) nm[r][c] = 0.25 * (m0[0] + m0[1] + m1[0] + m1[1]);
-        else if (wy && !wx) nm[r][c] = J == 0 ? 0.5 * (m1[0] + m1[1]) : 0.5 * (m0[0] + m0[1]);
-        else if (wx && !wy) nm[r][c] = I == 0 ? 0.5 * (m0[1] + m1[1]) : 0.5 * (m0[0] + m1[0]);
-        else nm[r][c] = 0.0;  // corner: never used
+        const double rn4 = r0[0] + r0[1] + r1[0] + r1[1];  // 4 rho_n
+        if (!wx && !wy) nm4[r][c] = m0[0] + m0[1] + m1[0] + m1[1];
+        else if (wy && !wx) nm4[r][c] = J == 0 ? 2.0 * (m1[0] + m1[1]) : 2.0 * (m0[0] + m0[1]);
+        else if (wx && !wy) nm4[r][c] = I == 0 ? 2.0 * (m0[1] + m1[1]) : 2.0 * (m0[0] + m1[0]);
+        else nm4[r][c] = 0.0;  // corner: never used
+        const double g = rn4 * (sv[r + 1][c] + sv[r + 1][c + 1]) * (su[r][c + 1] + su[r + 1][c + 1]);
+        if (c < PX) gxn[r][c] = wy ? 0.0 : g;
+        if (r < PY) gyn[r][c] = wx ? 0.0 : g;
     }
     __syncthreads();
     // cell fluxes: x-momentum of cell (i0-1+c, j0+r), window (r+1, c)
@@ -166,29 +176,24 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         fy[r][c] = sr[r][c + 1] * a * a;                   // 4 rho a^2
         vy[r][c] = sm[r][c + 1] * (sv[r + 1][c + 1] - sv[r][c + 1]);
     }
-    // node fluxes of the x-momentum at node (I, J) = (i0+c, j0+r): between
-    // u(I, J-1) (window (r, c+1)) and u(I, J) (window (r+1, c+1))
+    // viscous node fluxes (times 4) of the x-momentum at node (I, J) =
+    // (i0+c, j0+r): between u(I, J-1) (window (r, c+1)) and u(I, J) (window
+    // (r+1, c+1))
     for (int k = t; k < (PY + 1) * PX; k += PX * PY) {
         const int r = k / PX, c = k - r * PX, I = i0 + c, J = j0 + r;
         if (I > nx || J > ny) continue;
         const double ub = su[r][c + 1], ut = su[r + 1][c + 1];
-        gxn[r][c] = (J > 0 && J < ny)  // 16 rho_n a_v a_u
-                        ? nr[r][c] * (sv[r + 1][c] + sv[r + 1][c + 1]) * (ub + ut)
-                        : 0.0;
         const double uT = J < ny ? ut : -ub, uB = J > 0 ? ub : -ut;
-        wxn[r][c] = nm[r][c] * (uT - uB);
+        wxn[r][c] = nm4[r][c] * (uT - uB);
     }
-    // node fluxes of the y-momentum at node (I, J) = (i0+c, j0+r): between
-    // v(I-1, J) (window (r+1, c)) and v(I, J) (window (r+1, c+1))
+    // of the y-momentum at node (I, J) = (i0+c, j0+r): between v(I-1, J)
+    // (window (r+1, c)) and v(I, J) (window (r+1, c+1))
     for (int k = t; k < PY * (PX + 1); k += PX * PY) {
         const int r = k / (PX + 1), c = k - r * (PX + 1), I = i0 + c, J = j0 + r;
         if (I > nx || J > ny) continue;
         const double vl = sv[r + 1][c], vr = sv[r + 1][c + 1];
-        gyn[r][c] = (I > 0 && I < nx)  // 16 rho_n a_u a_v
-                        ? nr[r][c] * (su[r][c + 1] + su[r + 1][c + 1]) * (vl + vr)
-                        : 0.0;
         const double vR = I < nx ? vr : -vl, vL = I > 0 ? vl : -vr;
-        wyn[r][c] = nm[r][c] * (vR - vL);
+        wyn[r][c] = nm4[r][c] * (vR - vL);
     }
     __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y, i = i0 + tx, j = j0 + ty;
@@ -203,7 +208,8 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         } else {
             const double uc = su[R][C];
             const double adv = (fx[ty][tx + 1] - fx[ty][tx]) * ih4 + (gxn[ty + 1][tx] - gxn[ty][tx]) * ih16;
-            const double vis = (vx[ty][tx + 1] - vx[ty][tx] + wxn[ty + 1][tx] - wxn[ty][tx]) * ih2;
+            // (vx E - vx W + wx N - wx S) / h^2 with wx = wxn / 4 (exact)
+            const double vis = fma(-0.25, wxn[ty][tx], fma(0.25, wxn[ty + 1][tx], vx[ty][tx + 1] - vx[ty][tx])) * ih2;
             // 1 / rho_face: the face coefficient beta when given (the same
             // reciprocal of the same rho), else formed here
             const double irf = bx ? bx[k] : recip_nr(0.5 * (sr[R][C - 1] + sr[R][C]));
@@ -221,7 +227,7 @@ k_predictor(int nx, int ny, double ih, double ih2, double dt,
         } else {
             const double vc = sv[R][C];
             const double adv = (fy[ty + 1][tx] - fy[ty][tx]) * ih4 + (gyn[ty][tx + 1] - gyn[ty][tx]) * ih16;
-            const double vis = (vy[ty + 1][tx] - vy[ty][tx] + wyn[ty][tx + 1] - wyn[ty][tx]) * ih2;
+            const double vis = fma(-0.25, wyn[ty][tx], fma(0.25, wyn[ty][tx + 1], vy[ty + 1][tx] - vy[ty][tx])) * ih2;
             const double irf = by ? by[k] : recip_nr(0.5 * (sr[R - 1][C] + sr[R][C]));
             const double ae = have_prev ? 1.5 * adv - 0.5 * avp[k] : adv;
             vs[k] = vc + dt * ((vis - ae) * irf + gy);
