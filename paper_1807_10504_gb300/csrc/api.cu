@@ -57,6 +57,7 @@ struct ib_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     cudaEvent_t ev_sort_fork = nullptr, ev_sort_join = nullptr;  // the marker sort on s2
     cudaEvent_t ev_rows_fork = nullptr, ev_rows_join = nullptr;  // the rows inside on s3
+    cudaEvent_t ev_force_fork = nullptr;  // the face force on s3, after the Heaviside
     // recorded step phases (see run_recorded) and their capture stream
     std::vector<StepGraph> sgraphs;
     cudaStream_t cap = nullptr;
@@ -376,6 +377,16 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
     geometry(c);
     cudaStreamWaitEvent(c->s, c->ev_sort_join, 0);
     heaviside_into(c, c->H);
+    // the face force needs the geometry, the sort and H only: on s3 from
+    // here, next to the properties, the hierarchy and the predictor (after
+    // the indicator instead, which uses Fx, Fy as scratch)
+    const bool early_force = !g.indicator;
+    if (early_force) {
+        cudaEventRecord(c->ev_force_fork, c->s);
+        cudaStreamWaitEvent(c->s3, c->ev_force_fork, 0);
+        force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s3);
+        cudaEventRecord(c->ev_join3, c->s3);
+    }
     const double *prop = c->H;
     if (g.indicator) {
         ib_status is = indicator_into(c, c->mh);
@@ -393,16 +404,18 @@ ib_status step_pre(ib_ctx *c, double dt, bool reloc, bool mass, int warm)
     }
     // on two side streams, overlapping the predictor: the hierarchy of the
     // pressure coefficients (the r-weighted operator r_face beta in
-    // axisymmetric form), and the face force; neither depends on the other
-    // or on the predictor
+    // axisymmetric form), and (with the indicator) the face force; neither
+    // depends on the other or on the predictor
     if (g.axisym) launch_axi_weights(g.nx, g.ny, g.h, c->bx, c->by, c->bxa, c->bya, c->s);
     cudaEventRecord(c->ev_fork, c->s);
     cudaStreamWaitEvent(c->s2, c->ev_fork, 0);
-    cudaStreamWaitEvent(c->s3, c->ev_fork, 0);
     mg_build(c->mg, g.axisym ? c->bxa : c->bx, g.axisym ? c->bya : c->by, c->s2, g.precision == 0);
     cudaEventRecord(c->ev_join, c->s2);
-    force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s3);
-    cudaEventRecord(c->ev_join3, c->s3);
+    if (!early_force) {
+        cudaStreamWaitEvent(c->s3, c->ev_fork, 0);
+        force_into(c, g.spread, mk.fmag, c->H, c->Fx, c->Fy, c->s3);
+        cudaEventRecord(c->ev_join3, c->s3);
+    }
     if (g.axisym)
         launch_predictor_axi(g.nx, g.ny, g.h, dt, c->rho, mup, c->u, c->v, c->au, c->av, c->have_prev,
                              0.0, g.gy, g.frame ? c->frame : nullptr, c->bx, c->by, c->us, c->vs,
@@ -475,7 +488,11 @@ ib_status run_recorded(ib_ctx *c, double dt, int key, F fn)
         q.key = key;
         q.kernels = launch_count() - k0;
         note_launch(-(int)q.kernels);  // recording launches nothing
-        if (e == cudaSuccess && st == IB_OK) e = cudaGraphInstantiate(&q.exec, gr, 0);
+        // per-node priorities: the side streams' launches (hierarchy, face
+        // force) keep their higher priority inside the replayed graph, so
+        // their blocks take free SM slots ahead of the predictor's
+        if (e == cudaSuccess && st == IB_OK)
+            e = cudaGraphInstantiate(&q.exec, gr, cudaGraphInstantiateFlagUseNodePriority);
         if (gr) cudaGraphDestroy(gr);
         if (e != cudaSuccess || st != IB_OK || !q.exec) {
             cudaGetLastError();
@@ -520,6 +537,7 @@ void ib_destroy(ib_ctx *c)
     if (c->ev_sort_join) cudaEventDestroy(c->ev_sort_join);
     if (c->ev_rows_fork) cudaEventDestroy(c->ev_rows_fork);
     if (c->ev_rows_join) cudaEventDestroy(c->ev_rows_join);
+    if (c->ev_force_fork) cudaEventDestroy(c->ev_force_fork);
     if (c->s2) cudaStreamDestroy(c->s2);
     if (c->s3) cudaStreamDestroy(c->s3);
     if (c->flags_host) cudaFreeHost(c->flags_host);
@@ -639,6 +657,7 @@ ib_status ib_init(ib_ctx **out, const ib_config *cfg, const double *X, const dou
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_sort_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_rows_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_force_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->dmem, 2 * al((size_t)ndrops * 8));
     if (e == cudaSuccess) {
         c->A0 = (double *)c->dmem;
